@@ -1,0 +1,482 @@
+/*
+ * oracle.c -- CPU oracle for causal-set interval abundances and the
+ * Benincasa-Dowker (BD) action.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, obviously-correct
+ * restatement of what the CUDA path computes.  Only the test suite, the
+ * package smoke check and the benchmark's CPU-baseline / reference leg may
+ * load it.  It shares no code, header, table or helper with the CUDA library
+ * (paper_1805_04463_gb300/csrc) and the library never loads it.
+ *
+ * Source: W. J. Cunningham, "High Performance Algorithms for Quantum Gravity
+ * and Cosmology" (arXiv:1805.04463).  Each function cites the section,
+ * equation or algorithm it follows.  Where the thesis is silent (random
+ * number generator, tie-breaking, grid quantisation) the generator
+ * specification below is this project's own reading and is implemented
+ * independently on both sides.
+ *
+ * Generator specification (shared *definition*, separate implementations):
+ *   SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): state += 0x9E3779B97F4A7C15,
+ *   output = mix(state) with the published two-multiply finaliser.  Output
+ *   number n (0-based) of a generator started at state s is therefore
+ *   mix(s + (n+1)*gamma).  A draw for (seed, stream, element e, slot q) is
+ *   output (e*65536 + q) of the generator started at sigma, where sigma is
+ *   output `stream` of the generator started at `seed`.  Grid value of a
+ *   draw = draw >> 44 (20 bits, one unit of length = 2^20 grid steps).
+ *
+ * Parity pins live in tests/test_oracle_*.py; every function here is pinned
+ * by at least one check that does not re-run this file's own formulae.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#if defined(__aarch64__)
+typedef long double q128; /* binary128 on AArch64 Linux */
+#elif defined(__x86_64__)
+typedef __float128 q128;  /* binary128 via libgcc soft-float */
+#else
+#error "oracle needs a binary128 type"
+#endif
+
+#define OR_GAMMA 0x9E3779B97F4A7C15ULL
+#define OR_GRID  (1LL << 20)
+#define OR_HALF  (1LL << 19)
+#define OR_MAX_ATTEMPTS 16384
+
+enum { OR_2D_ORDER = 0, OR_2D_DIAMOND = 1, OR_4D_DIAMOND = 2 };
+enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2, OR_ERANGE = -6 };
+
+/* ------------------------------------------------------------------ PRNG */
+
+static uint64_t or_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* SplitMix64 next(): advance then mix (Steele, Lea & Flood 2014). */
+uint64_t oracle_splitmix64_next(uint64_t *state)
+{
+    *state += OR_GAMMA;
+    return or_mix(*state);
+}
+
+/* Output number n of SplitMix64 started at state s: n+1 advances, then mix. */
+static uint64_t or_output_at(uint64_t s, uint64_t n)
+{
+    uint64_t st = s;
+    st += n * OR_GAMMA; /* n advances without output */
+    return oracle_splitmix64_next(&st);
+}
+
+uint64_t oracle_draw(uint64_t seed, uint32_t stream, uint64_t elem, uint32_t slot)
+{
+    uint64_t sigma = or_output_at(seed, (uint64_t)stream);
+    return or_output_at(sigma, elem * 65536ULL + (uint64_t)slot);
+}
+
+int oracle_dim(int kind)
+{
+    if (kind == OR_2D_ORDER || kind == OR_2D_DIAMOND) return 2;
+    if (kind == OR_4D_DIAMOND) return 4;
+    return 0;
+}
+
+/* ------------------------------------------------------------ sprinkling */
+
+typedef struct { int64_t key; int64_t idx; } or_pair;
+
+static int or_cmp_pair(const void *a, const void *b)
+{
+    const or_pair *x = (const or_pair *)a, *y = (const or_pair *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
+    return 0;
+}
+
+typedef struct { uint64_t key; int64_t idx; } or_upair;
+
+static int or_cmp_upair(const void *a, const void *b)
+{
+    const or_upair *x = (const or_upair *)a, *y = (const or_upair *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
+    return 0;
+}
+
+/*
+ * Sprinkle n elements and write them, labelled in time order, as
+ * structure-of-arrays int32 coordinates: coords[c*n + label].
+ *
+ * kind 0, random 2D order: u and v are two independent uniform random
+ *   permutations (ranks of 64-bit keys from streams 0 and 1, ties broken by
+ *   element index); elements are relabelled by u, so coords[0] = 0..n-1.
+ *   A 2D order is the 1+1 Minkowski diamond in light-cone coordinates
+ *   (Appendix "Causal Set Sprinklings", 1+1 Dimensional Diamond) with only
+ *   the order of u and v kept.
+ * kind 1, 2D diamond: u, v uniform on the grid [0, 2^20) (same appendix
+ *   entry, u* = U u0 with u0 = 1), time t = u + v.
+ * kind 2, 4D diamond of height 1: rejection sampling (allowed by the
+ *   appendix's general method) in the box t in [0, 2^20),
+ *   x, y, z in [-2^19, 2^19): accept iff x^2+y^2+z^2 < min(t, 2^20-t)^2.
+ * Elements are sorted by time with ties broken by generation index
+ * (Section "Pairwise Relations": elements are sorted by their time
+ * coordinate before relations are identified).
+ */
+int oracle_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords)
+{
+    if (n < 0 || !coords) return OR_EINVAL;
+    if (n == 0) return OR_OK;
+    if (kind == OR_2D_ORDER) {
+        or_upair *ku = malloc((size_t)n * sizeof *ku);
+        or_upair *kv = malloc((size_t)n * sizeof *kv);
+        int64_t *vrank = malloc((size_t)n * sizeof *vrank);
+        if (!ku || !kv || !vrank) { free(ku); free(kv); free(vrank); return OR_ENOMEM; }
+        for (int64_t e = 0; e < n; e++) {
+            ku[e].key = oracle_draw(seed, 0, (uint64_t)e, 0); ku[e].idx = e;
+            kv[e].key = oracle_draw(seed, 1, (uint64_t)e, 0); kv[e].idx = e;
+        }
+        qsort(ku, (size_t)n, sizeof *ku, or_cmp_upair);
+        qsort(kv, (size_t)n, sizeof *kv, or_cmp_upair);
+        for (int64_t r = 0; r < n; r++) vrank[kv[r].idx] = r;
+        for (int64_t r = 0; r < n; r++) {
+            coords[r] = (int32_t)r;
+            coords[n + r] = (int32_t)vrank[ku[r].idx];
+        }
+        free(ku); free(kv); free(vrank);
+        return OR_OK;
+    }
+    if (kind == OR_2D_DIAMOND) {
+        int32_t *u = malloc((size_t)n * 4), *v = malloc((size_t)n * 4);
+        or_pair *t = malloc((size_t)n * sizeof *t);
+        if (!u || !v || !t) { free(u); free(v); free(t); return OR_ENOMEM; }
+        for (int64_t e = 0; e < n; e++) {
+            u[e] = (int32_t)(oracle_draw(seed, 2, (uint64_t)e, 0) >> 44);
+            v[e] = (int32_t)(oracle_draw(seed, 2, (uint64_t)e, 1) >> 44);
+            t[e].key = (int64_t)u[e] + v[e];
+            t[e].idx = e;
+        }
+        qsort(t, (size_t)n, sizeof *t, or_cmp_pair);
+        for (int64_t r = 0; r < n; r++) {
+            coords[r] = u[t[r].idx];
+            coords[n + r] = v[t[r].idx];
+        }
+        free(u); free(v); free(t);
+        return OR_OK;
+    }
+    if (kind == OR_4D_DIAMOND) {
+        int32_t *x = malloc((size_t)n * 4 * sizeof *x);
+        or_pair *t = malloc((size_t)n * sizeof *t);
+        if (!x || !t) { free(x); free(t); return OR_ENOMEM; }
+        int bad = 0;
+        for (int64_t e = 0; e < n && !bad; e++) {
+            int found = 0;
+            for (int a = 0; a < OR_MAX_ATTEMPTS && !found; a++) {
+                int64_t c[4];
+                for (int q = 0; q < 4; q++)
+                    c[q] = (int64_t)(oracle_draw(seed, 3, (uint64_t)e, (uint32_t)(4 * a + q)) >> 44);
+                int64_t tt = c[0];
+                int64_t xx = c[1] - OR_HALF, yy = c[2] - OR_HALF, zz = c[3] - OR_HALF;
+                int64_t h = tt < OR_GRID - tt ? tt : OR_GRID - tt;
+                if (xx * xx + yy * yy + zz * zz < h * h) {
+                    x[4 * e + 0] = (int32_t)tt; x[4 * e + 1] = (int32_t)xx;
+                    x[4 * e + 2] = (int32_t)yy; x[4 * e + 3] = (int32_t)zz;
+                    found = 1;
+                }
+            }
+            if (!found) bad = 1;
+            t[e].key = x[4 * e];
+            t[e].idx = e;
+        }
+        if (bad) { free(x); free(t); return OR_ERANGE; }
+        qsort(t, (size_t)n, sizeof *t, or_cmp_pair);
+        for (int64_t r = 0; r < n; r++)
+            for (int q = 0; q < 4; q++) coords[(int64_t)q * n + r] = x[4 * t[r].idx + q];
+        free(x); free(t);
+        return OR_OK;
+    }
+    return OR_EINVAL;
+}
+
+/* --------------------------------------------------------------- relation */
+
+/*
+ * a precedes b: timelike (Delta s^2 < 0, strictly) and future-directed
+ * (Section "Lorentzian Geometry"; the 1+1 diamond interval is ds^2 = -2 du dv).
+ */
+int oracle_precedes(int kind, int64_t n, const int32_t *coords, int64_t a, int64_t b)
+{
+    if (kind == OR_2D_ORDER || kind == OR_2D_DIAMOND) {
+        int64_t du = (int64_t)coords[b] - coords[a];
+        int64_t dv = (int64_t)coords[n + b] - coords[n + a];
+        return du > 0 && dv > 0;
+    }
+    int64_t dt = (int64_t)coords[b] - coords[a];
+    int64_t dx = (int64_t)coords[n + b] - coords[n + a];
+    int64_t dy = (int64_t)coords[2 * n + b] - coords[2 * n + a];
+    int64_t dz = (int64_t)coords[3 * n + b] - coords[3 * n + a];
+    return dt > 0 && dt * dt - (dx * dx + dy * dy + dz * dz) > 0;
+}
+
+/* Row words of the bitset: ceil(n/64) rounded up to a multiple of 16. */
+int64_t oracle_row_words(int64_t n)
+{
+    int64_t w = (n + 63) / 64;
+    return (w + 15) / 16 * 16;
+}
+
+/*
+ * Symmetrised causal matrix P + P^T as one bitset per row (Section "Data
+ * Structures for Totally Ordered Sets"): bit j of row i is 1 iff i and j
+ * are related either way.  Column j lives in word j/64, bit j%64.  All
+ * padding bits and words are zero.
+ */
+int oracle_causal_matrix(int kind, int64_t n, const int32_t *coords, uint64_t *bits, int64_t row_words)
+{
+    if (n < 0 || row_words * 64 < n) return OR_EINVAL;
+    memset(bits, 0, (size_t)n * (size_t)row_words * 8);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; i++) {
+        uint64_t *row = bits + i * row_words;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            if (oracle_precedes(kind, n, coords, i, j) || oracle_precedes(kind, n, coords, j, i))
+                row[j >> 6] |= 1ULL << (j & 63);
+        }
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------ interval counting */
+
+static int or_bit(const uint64_t *row, int64_t j)
+{
+    return (int)((row[j >> 6] >> (j & 63)) & 1ULL);
+}
+
+/*
+ * popcount(x & y) restricted to bit columns [lo, hi): the partial inner
+ * product of two bitsets (Algorithms "Vectorized Partial Intersection" and
+ * "Vectorized Inner Product", restated with a portable popcount).
+ */
+static int64_t or_partial_inner_product(const uint64_t *x, const uint64_t *y, int64_t lo, int64_t hi)
+{
+    if (hi <= lo) return 0;
+    int64_t wlo = lo >> 6, whi = (hi - 1) >> 6, c = 0;
+    for (int64_t w = wlo; w <= whi; w++) {
+        uint64_t m = ~0ULL;
+        if (w == wlo) m &= ~0ULL << (lo & 63);
+        if (w == whi) m &= ~0ULL >> (63 - ((hi - 1) & 63));
+        c += __builtin_popcountll(x[w] & y[w] & m);
+    }
+    return c;
+}
+
+/*
+ * |A_ij| for one pair i < j, or -1 if i does not precede j.  For time-sorted
+ * labels the elements between i and j in the order lie in columns i+1..j-1,
+ * where row i holds the future of i and row j the past of j (Figure
+ * "Proper distance and the order intervals"; Section "Partially Ordered Sets").
+ */
+int64_t oracle_interval_size(int64_t n, const uint64_t *bits, int64_t row_words, int64_t i, int64_t j)
+{
+    if (i < 0 || j >= n || i >= j) return -1;
+    const uint64_t *ri = bits + i * row_words, *rj = bits + j * row_words;
+    if (!or_bit(ri, j)) return -1;
+    return or_partial_inner_product(ri, rj, i + 1, j);
+}
+
+/*
+ * Interval abundances from the bitset (Algorithm "Optimized Interval
+ * Abundance Measurement"): for every related pair i < j the partial inner
+ * product of rows i and j gives m = |A_ij|; each thread keeps its own
+ * abundance array and the arrays are summed at the end (Section "Parallel
+ * Action Algorithm").  hist[k] counts pairs with |A_ij| = k, i.e. hist[k] is
+ * the thesis's n_{k+1}; hist has len = max(n-1, 1) entries.
+ *
+ * Only rows i = row_begin, row_begin + row_step, ... < row_end are visited
+ * (all rows: 0, n, 1), which lets a caller evaluate a bounded sample.
+ * threads <= 0 uses the OpenMP default.  Returns the number of threads used.
+ */
+int oracle_interval_abundance_rows(int64_t n, const uint64_t *bits, int64_t row_words,
+                                   int64_t row_begin, int64_t row_end, int64_t row_step,
+                                   int64_t *hist, int64_t len, int threads)
+{
+    if (n < 0 || len < (n > 1 ? n - 1 : 1) || row_step < 1) return OR_EINVAL;
+    memset(hist, 0, (size_t)len * 8);
+    if (n < 2) return 1;
+    int T = 1;
+#ifdef _OPENMP
+    T = threads > 0 ? threads : omp_get_max_threads();
+#endif
+    int64_t *local = calloc((size_t)T * (size_t)len, 8);
+    if (!local) return OR_ENOMEM;
+    if (row_end > n) row_end = n;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(T)
+    for (int64_t i = row_begin; i < row_end; i += row_step) {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        int64_t *h = local + (int64_t)t * len;
+        const uint64_t *ri = bits + i * row_words;
+        for (int64_t j = i + 1; j < n; j++) {
+            if (!or_bit(ri, j)) continue;
+            int64_t m = or_partial_inner_product(ri, bits + j * row_words, i + 1, j);
+            h[m]++;
+        }
+    }
+    for (int t = 0; t < T; t++)
+        for (int64_t k = 0; k < len; k++) hist[k] += local[(int64_t)t * len + k];
+    free(local);
+    return T;
+}
+
+int oracle_interval_abundance(int64_t n, const uint64_t *bits, int64_t row_words,
+                              int64_t *hist, int64_t len, int threads)
+{
+    return oracle_interval_abundance_rows(n, bits, row_words, 0, n, 1, hist, len, threads);
+}
+
+/*
+ * Brute force (Algorithm "Naive Interval Abundance Measurement"), with the
+ * relation evaluated from the coordinates instead of a stored matrix: for
+ * every related pair count the k with i < k < j, i precedes k and k precedes j.
+ * O(n^3); meant for n <= a few hundred.
+ */
+int oracle_interval_abundance_naive(int kind, int64_t n, const int32_t *coords, int64_t *hist, int64_t len)
+{
+    if (n < 0 || len < (n > 1 ? n - 1 : 1)) return OR_EINVAL;
+    memset(hist, 0, (size_t)len * 8);
+    for (int64_t i = 0; i + 1 < n; i++)
+        for (int64_t j = i + 1; j < n; j++) {
+            if (!oracle_precedes(kind, n, coords, i, j)) continue;
+            int64_t x = 0;
+            for (int64_t k = i + 1; k < j; k++)
+                if (oracle_precedes(kind, n, coords, i, k) && oracle_precedes(kind, n, coords, k, j)) x++;
+            hist[x]++;
+        }
+    return OR_OK;
+}
+
+/*
+ * 2D orders only, a structurally different count: with labels sorted by u,
+ * |A_ij| = #{i < k < j : v_i < v_k < v_j}.  For each i a Fenwick tree over v
+ * holds the v_k (k > i, v_k > v_i) seen so far; a prefix query gives the
+ * count for each later j.  O(n^2 log n), no bitsets.  Rows are sampled as in
+ * oracle_interval_abundance_rows.
+ */
+int oracle_interval_abundance_dominance2d(int64_t n, const int32_t *v, int64_t row_begin, int64_t row_end,
+                                          int64_t row_step, int64_t *hist, int64_t len)
+{
+    if (n < 0 || len < (n > 1 ? n - 1 : 1) || row_step < 1) return OR_EINVAL;
+    memset(hist, 0, (size_t)len * 8);
+    if (row_end > n) row_end = n;
+    int T = 1;
+#ifdef _OPENMP
+    T = omp_get_max_threads();
+#endif
+    int64_t *local = calloc((size_t)T * (size_t)len, 8);
+    int32_t *fen = calloc((size_t)T * (size_t)(n + 1), 4);
+    if (!local || !fen) { free(local); free(fen); return OR_ENOMEM; }
+#pragma omp parallel for schedule(dynamic, 1) num_threads(T)
+    for (int64_t i = row_begin; i < row_end; i += row_step) {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        int32_t *f = fen + (int64_t)t * (n + 1);
+        memset(f, 0, (size_t)(n + 1) * 4);
+        for (int64_t j = i + 1; j < n; j++) {
+            if (v[j] <= v[i]) continue;
+            int64_t c = 0; /* number of inserted values < v[j] */
+            for (int64_t p = v[j]; p > 0; p -= p & -p) c += f[p];
+            local[(int64_t)t * len + c]++;
+            for (int64_t p = (int64_t)v[j] + 1; p <= n; p += p & -p) f[p]++;
+        }
+    }
+    for (int t = 0; t < T; t++)
+        for (int64_t k = 0; k < len; k++) hist[k] += local[(int64_t)t * len + k];
+    free(local); free(fen);
+    return OR_OK;
+}
+
+/*
+ * 2D orders only: number of links (covering pairs, the transitive
+ * reduction).  j > i is a link from i iff v_j > v_i and v_j is below every
+ * v_k (i < k < j) that is above v_i: a running minimum, O(n^2), using
+ * neither bitsets nor interval counts.
+ */
+int64_t oracle_links_2d(int64_t n, const int32_t *v)
+{
+    int64_t links = 0;
+#pragma omp parallel for reduction(+ : links) schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; i++) {
+        int64_t lo = INT64_MAX; /* min v_k above v_i seen so far */
+        for (int64_t j = i + 1; j < n; j++) {
+            if (v[j] <= v[i]) continue;
+            if (v[j] < lo) { links++; lo = v[j]; }
+        }
+    }
+    return links;
+}
+
+/* ----------------------------------------------------------------- action */
+
+static q128 or_qsqrt(q128 x)
+{
+    if (x <= 0) return 0;
+    q128 y = (q128)__builtin_sqrt((double)x);
+    for (int it = 0; it < 3; it++) y = y - (y * y - x) / (2 * y);
+    return y;
+}
+
+/*
+ * Benincasa-Dowker action from the abundances (Section "The Benincasa-Dowker
+ * Action").  With hist[k] = n_{k+1}:
+ *   local 1+1 (Eq. s2d_local):  S = 2 (N - 2 n1 + 4 n2 - 2 n3)
+ *   local 3+1 (Eq. s4d_local):  S = 4/sqrt(6) (N - n1 + 9 n2 - 16 n3 + 8 n4),
+ *                               with (l/l_p)^2 = 1
+ *   smeared 1+1 (Eq. s2d_smeared): S = 2 eps [N - 2 eps sum_m n_m f2(m-1, eps)]
+ *   smeared 3+1 (Eq. s4d_smeared): S = 4 sqrt(eps/6) [N - eps sum_m n_m f4(m-1, eps)]
+ * with f2 and f4 evaluated as printed (divisions by 1-eps) in binary128 and
+ * (1-eps)^m built by repeated multiplication.  eps <= 0 or eps == 1 selects
+ * the local action.  bracket receives the exact integer in parentheses of
+ * the local form.  out receives S rounded to double.
+ */
+int oracle_action(int dim, int64_t n, const int64_t *hist, int64_t len, double eps, double *out,
+                  int64_t *bracket)
+{
+    if ((dim != 2 && dim != 4) || n < 0 || len < 0 || eps > 1.0 || eps != eps) return OR_EINVAL;
+    int64_t h[4] = {0, 0, 0, 0};
+    for (int k = 0; k < 4 && k < len; k++) h[k] = hist[k];
+    int64_t b = dim == 2 ? n - 2 * h[0] + 4 * h[1] - 2 * h[2]
+                         : n - h[0] + 9 * h[1] - 16 * h[2] + 8 * h[3];
+    if (bracket) *bracket = b;
+    if (eps <= 0.0 || eps == 1.0) {
+        q128 s = dim == 2 ? (q128)2 * (q128)b : (q128)4 / or_qsqrt((q128)6) * (q128)b;
+        if (out) *out = (double)s;
+        return OR_OK;
+    }
+    q128 e = (q128)eps, one_m = (q128)1 - e, p = 1, sum = 0;
+    for (int64_t k = 0; k < len; k++) { /* k = m - 1 */
+        q128 m = (q128)k, f;
+        if (dim == 2) {
+            f = p * ((q128)1 - 2 * m * e / one_m + m * (m - 1) * e * e / (2 * one_m * one_m));
+        } else {
+            f = p * ((q128)1 - 9 * m * e / one_m + 8 * m * (m - 1) * e * e / (one_m * one_m)
+                     - 4 * m * (m - 1) * (m - 2) * e * e * e / (3 * one_m * one_m * one_m));
+        }
+        sum += (q128)hist[k] * f;
+        p *= one_m;
+    }
+    q128 s = dim == 2 ? 2 * e * ((q128)n - 2 * e * sum)
+                      : 4 * or_qsqrt(e / 6) * ((q128)n - e * sum);
+    if (out) *out = (double)s;
+    return OR_OK;
+}
