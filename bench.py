@@ -1,0 +1,333 @@
+"""Benchmark: interval-count throughput of the GB300 causal-set path.
+
+One step = one pass of the whole hot path over one causal set, all on the
+device: sprinkle -> causal matrix -> interval abundances -> BD actions
+(local + smeared at eps = 0.05, 0.1, 0.2).  The default workload is the
+large random 2D order, N = 131072 (2.1 GB bitset, larger than L2).
+
+Prints one JSON line (rank 0).  value = related pairs counted per second
+(Gpairs/s) over the whole job; e2e = the same metric through the host-buffer
+entry point cs_evaluate (coordinates copied from pinned host memory, the
+histogram and actions copied back, every step); roofline = the count
+kernel's achieved rate against the POPC (or tensor) peak; cpu_baseline = the
+CPU oracle on a bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--path auto|popc|mma]
+  python bench.py --impl reference ...   # the CPU oracle as the reference arm
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (kind, n, seed, description)
+    "2d_order_131072": (0, 131072, 0xC5E70003, "random 2D order, N=131072 (2.1 GB bitset)"),
+    "4d_diamond_16384": (2, 16384, 0xC5E70002, "4D Minkowski diamond, N=16384, int32 grid 2^20"),
+    "2d_order_1024": (0, 1024, 0xC5E70001, "random 2D order, N=1024"),
+}
+EPS = (0.0, 0.05, 0.1, 0.2)
+PATHS = {"auto": 0, "popc": 1, "mma": 2}
+POPC_PER_SM_PER_CLK = 16  # 32-bit population count, per SM per clock
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def launches_per_step(kind, path):
+    """Kernels of this library launched by one step (sprinkle, relate, count, actions)."""
+    sprinkle = 1 + (2 if kind == 0 else 1) * 4 + 1
+    count = 1 if path != 2 else 2
+    return sprinkle + 1 + count + 2
+
+
+def cpu_baseline(kind, n, seed, target_s=15.0, max_rows=None):
+    """The oracle on a bounded sample of rows of the same workload (pairs/s)."""
+    import numpy as np
+    import oracle
+    coords = oracle.sprinkle(kind, n, seed)
+    bits = oracle.causal_matrix(kind, coords)
+    # calibrate on a short sample, then size the sample to ~target_s seconds
+    step = max(1, n // 64)
+    t0 = time.perf_counter()
+    h, threads = oracle.interval_abundance_threads(bits, rows=(0, n, step))
+    dt = max(time.perf_counter() - t0, 1e-3)
+    rows_done = len(range(0, n, step))
+    rows_wanted = int(rows_done * target_s / dt)
+    if max_rows:
+        rows_wanted = min(rows_wanted, max_rows)
+    step = max(1, n // max(rows_wanted, 1))
+    t0 = time.perf_counter()
+    h, threads = oracle.interval_abundance_threads(bits, rows=(0, n, step))
+    dt = time.perf_counter() - t0
+    pairs = int(np.asarray(h).sum())
+    return {"value": pairs / dt / 1e9, "unit": "Gpairs/s", "cores": threads, "kind": "oracle",
+            "sample": f"rows i = 0, {step}, {2 * step}, ... of the same set ({len(range(0, n, step))} of {n} rows, "
+                      f"{pairs} related pairs, {dt:.1f} s)", "seconds": dt, "pairs": pairs}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    kind, n, seed, desc = WORKLOADS[args.workload]
+    if rank != 0:
+        return 0
+    # Each step = one bounded sample of the workload, timed on the host cores.
+    import numpy as np
+    import oracle
+    coords = oracle.sprinkle(kind, n, seed)
+    bits = oracle.causal_matrix(kind, coords)
+    step = max(1, n // 256) if n > 4096 else 1
+    rows = (0, n, step)
+    for _ in range(args.warmup):
+        oracle.interval_abundance(bits, rows=rows)
+    times, pairs, threads = [], 0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        h, threads = oracle.interval_abundance_threads(bits, rows=rows)
+        times.append(time.perf_counter() - t0)
+        pairs = int(np.asarray(h).sum())
+    total = sum(times)
+    value = pairs * args.steps / total / 1e9
+    sample = f"rows i = 0, {step}, ... ({len(range(*rows))} of {n} rows, {pairs} related pairs per step)"
+    line = {
+        "impl": "reference", "metric": f"interval-count Gpairs/s ({desc})", "value": value, "unit": "Gpairs/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "kind": kind, "seed": seed},
+        "cpu_baseline": {"value": value, "unit": "Gpairs/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Gpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2d_order_131072", choices=sorted(WORKLOADS))
+    ap.add_argument("--path", default="auto", choices=sorted(PATHS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_1805_04463_gb300 as cs
+    from paper_1805_04463_gb300 import build as csbuild
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    csbuild.build()
+    kind, n, seed0, desc = WORKLOADS[args.workload]
+    seed = seed0 + rank  # weak scaling: one independent set per rank
+    path = PATHS[args.path]
+    buf = cs.allocate(kind, n, path=path)
+    stream = torch.cuda.current_stream()
+
+    # count-kernel timing: events on the launching stream around each count call
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def step(i=None):
+        cs.sprinkle(kind, n, seed, buf.coords, buf.workspace, stream)
+        cs.causal_matrix(kind, n, buf.coords, buf.bits, stream)
+        if i is not None:
+            ev[i][0].record(stream)
+        cs.interval_abundance(n, buf.bits, buf.hist, path, buf.workspace, stream)
+        if i is not None:
+            ev[i][1].record(stream)
+        cs.action_device(cs.dim(kind), n, buf.hist, list(EPS), buf.actions, buf.bracket, buf.workspace, stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    status = cs.workspace_status(buf.workspace)
+    if status != 0:
+        raise cs.CsError(status, "warm-up")
+
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for i in range(args.steps):
+            step(i)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed_ms = start.elapsed_time(stop)
+    count_ms = [a.elapsed_time(b) for a, b in ev]
+    hist = buf.hist.cpu().numpy()
+    pairs = int(hist.sum())
+    actions = buf.actions.cpu().numpy()[:len(EPS)].tolist()
+    t = torch.tensor([elapsed_ms, float(pairs)], dtype=torch.float64, device="cuda")
+    if dist:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        elapsed_ms, total_pairs = float(tmax[0]), float(tsum[1])
+    else:
+        total_pairs = float(pairs)
+    value = total_pairs * args.steps / (elapsed_ms / 1e3) / 1e9
+
+    # e2e through the host-buffer entry point: pinned coordinates in, histogram out
+    coords_pinned = torch.empty((cs.dim(kind), n), dtype=torch.int32, pin_memory=True)
+    coords_pinned.copy_(buf.coords.cpu())
+    cp = coords_pinned.numpy()
+    hist_pinned = torch.empty(cs.hist_len(n), dtype=torch.int64, pin_memory=True).numpy()
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
+    cs.evaluate(kind, n, 0, cp, path, EPS, stream=stream, hist_out=hist_pinned)  # warm the allocator
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        h2, _, _ = cs.evaluate(kind, n, 0, cp, path, EPS, stream=stream, hist_out=hist_pinned)
+    e2e_s = time.perf_counter() - t0
+    assert int(h2.sum()) == pairs
+    if dist:
+        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_s = float(te[0])
+    e2e_value = total_pairs * e2e_steps / e2e_s / 1e9
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, src = _peaks()
+    clocks = clk.summary()
+    # roofline of the count kernel
+    cnt_s = statistics.mean(count_ms) / 1e3
+    algo_ands = n * (n - 1) * (n - 2) / 6.0  # bit-ANDs over every pair i<j, columns strictly between
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    popc_peak = sm_count * POPC_PER_SM_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T popc32/s
+    achieved = algo_ands / 32.0 / cnt_s / 1e12
+    roofline = {"bound": "alu", "kernel": "k_count_popc", "achieved": achieved, "peak": popc_peak,
+                "unit": "T popc32/s", "frac": achieved / popc_peak, "traffic": None,
+                "peak_source": f"{sm_count} SMs x {POPC_PER_SM_PER_CLK} POPC/clk x {peaks.get('sm_max_mhz')} MHz "
+                               f"(sm_max_mhz from MEASURED_PEAKS.json, {src})",
+                "count_ms": statistics.mean(count_ms), "algorithmic_bit_ands": algo_ands}
+    line = {
+        "metric": f"interval-count Gpairs/s ({desc})", "value": value, "unit": "Gpairs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "kind": cs.KIND_NAMES[kind], "n": n, "seed": seed0,
+                   "path": args.path, "eps": list(EPS),
+                   "l2": "inputs larger than L2" if cs.bitset_bytes(n) > 129e6 else "inputs smaller than L2",
+                   "parallelism": f"replicas{args.gpus}"},
+        "actions_per_s": args.steps * ws / (elapsed_ms / 1e3),
+        "pairs_per_step": pairs, "actions": actions,
+        "e2e": {"value": e2e_value, "unit": "Gpairs/s", "h2d_bytes_per_step": int(cp.nbytes),
+                "d2h_bytes_per_step": int(hist_pinned.nbytes + 8 * len(EPS) + 8), "steps": e2e_steps},
+        "gpu_launches": launches_per_step(kind, path) * args.steps,
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        cb = cpu_baseline(kind, n, seed0)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,220 @@
+/*
+ * cs.h -- C ABI of the GB300 causal-set interval-abundance library.
+ *
+ * The library generates a causal set, builds its causal matrix as row
+ * bitsets, counts the cardinality of every causal interval, histograms the
+ * counts into interval abundances and evaluates the Benincasa-Dowker action
+ * (W. J. Cunningham, "High Performance Algorithms for Quantum Gravity and
+ * Cosmology", arXiv:1805.04463, Chapter "Causal Set Action").
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named *_dev are device (HBM) pointers; *_host are host
+ *    pointers.  The caller allocates and owns every buffer; the library never
+ *    frees caller memory.  Workspace sizes come from the *_workspace_bytes
+ *    queries; a workspace must be 256-byte aligned.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device entry points only enqueue work on it and return; they
+ *    never synchronise the device.
+ *  - Errors are returned as cs_status, never thrown or aborted.  Invalid
+ *    arguments are rejected before anything is enqueued.  A CUDA launch or
+ *    runtime error maps to CS_ECUDA.  Errors detected inside a kernel
+ *    (a bounded wait that timed out, a rejection sampler that ran out of
+ *    attempts) are written to the workspace status word and read back with
+ *    cs_workspace_status().
+ *  - Elements are labelled in time order (ties by generation index), so the
+ *    strict upper triangle of the causal matrix holds every relation i < j.
+ *  - hist[k] counts related pairs i < j whose open interval
+ *    A_ij = J+(i) cap J-(j) holds exactly k elements; it is the thesis's
+ *    n_{k+1} (Eq. IOIs, "inclusive order intervals").  Its length is
+ *    cs_hist_len(n) = max(n - 1, 1).
+ */
+#ifndef CS_H
+#define CS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CS_OK = 0,
+    CS_EINVAL = -1,        /* bad argument (size, kind, alignment, pointer) */
+    CS_ENOMEM = -2,        /* workspace too small or allocation failed */
+    CS_ECUDA = -3,         /* CUDA runtime / launch error */
+    CS_ETIMEOUT = -4,      /* a bounded in-kernel wait gave up */
+    CS_EUNSUPPORTED = -5,  /* path or feature not available on this device */
+    CS_ERANGE = -6         /* sampler exhausted its attempt budget */
+} cs_status;
+
+/* Causal-set kinds (Appendix "Causal Set Sprinklings"). */
+enum {
+    CS_2D_ORDER = 0,    /* random 2D order: two uniform random permutations u, v */
+    CS_2D_DIAMOND = 1,  /* 1+1 Minkowski diamond, light-cone coordinates on a 2^20 grid */
+    CS_4D_DIAMOND = 2   /* 3+1 Minkowski diamond of height 1, int32 grid of 2^20 per unit */
+};
+
+/* Interval-count paths. */
+enum {
+    CS_PATH_AUTO = 0,   /* pick the faster path for this n */
+    CS_PATH_POPC = 1,   /* AND + popcount tiles on the CUDA cores */
+    CS_PATH_MMA = 2     /* 0/1 operands on the tcgen05 tensor cores, fused epilogue */
+};
+
+/* ------------------------------------------------------------- layouts */
+
+/* Spacetime dimension of a kind: 2 or 4; 0 for an unknown kind. */
+int cs_dim(int kind);
+
+/* Bytes of the structure-of-arrays int32 coordinates: n * dim * 4.
+ * Layout: coords[c * n + i] is coordinate c of element i (2D kinds: u, v;
+ * 4D: t, x, y, z). */
+size_t cs_coords_bytes(int kind, int64_t n);
+
+/* 64-bit words per bitset row: ceil(n / 64) rounded up to a multiple of 16
+ * (128-byte rows). */
+int64_t cs_row_words(int64_t n);
+
+/* Bytes of the n-row causal-matrix bitset: n * cs_row_words(n) * 8. */
+size_t cs_bitset_bytes(int64_t n);
+
+/* Length of the abundance histogram: max(n - 1, 1). */
+int64_t cs_hist_len(int64_t n);
+
+/* ---------------------------------------------------------- sprinkling */
+
+/* Device workspace needed by cs_sprinkle for (kind, n). */
+size_t cs_sprinkle_workspace_bytes(int kind, int64_t n);
+
+/*
+ * Sprinkle n elements of `kind` from `seed` and write their time-sorted
+ * coordinates to coords_dev (cs_coords_bytes bytes, layout above).
+ * Section "Coordinate Generation" and Appendix "Causal Set Sprinklings"
+ * (1+1 and 3+1 Minkowski diamonds): coordinates are drawn independently per
+ * element and the elements are then sorted by time (Section "Pairwise
+ * Relations").  The random numbers are the counter-based SplitMix64 stream
+ * (draw(seed, stream, element, slot) = output element*65536+slot of the
+ * generator seeded with output `stream` of the generator seeded with seed);
+ * a 2D order is the pair of rank permutations of streams 0 and 1, relabelled
+ * by u; a 2D diamond draws u, v from stream 2; a 4D diamond rejection-samples
+ * (t, x, y, z) from stream 3 inside |x| < min(t, 1 - t).
+ * Errors: CS_EINVAL (n < 1, n > 2^22, bad kind, NULL coords),
+ * CS_ENOMEM (workspace too small), CS_ECUDA.  A 4D element that finds no
+ * point in 16384 attempts sets CS_ERANGE in the workspace status word.
+ */
+int cs_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords_dev,
+                void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------- causal matrix */
+
+/*
+ * Build the symmetrised causal matrix P + P^T (Section "Data Structures for
+ * Totally Ordered Sets": one bitset per row) from time-sorted coordinates.
+ * Bit j of row i (word j/64, bit j%64, least significant bit first) is 1 iff
+ * i and j are timelike related, Delta s^2 < 0 strictly (Section
+ * "Lorentzian Geometry"); 2D kinds: du * dv > 0; 4D: dt^2 > |dx|^2, exact in
+ * int64.  row_words must be >= cs_row_words(n) and a multiple of 16; bits_dev
+ * holds n * row_words uint64 and is fully written (padding bits zero).
+ * Errors: CS_EINVAL, CS_ECUDA.
+ */
+int cs_causal_matrix(int kind, int64_t n, const int32_t *coords_dev,
+                     uint64_t *bits_dev, int64_t row_words, void *stream);
+
+/* -------------------------------------------------- interval abundance */
+
+/* Device workspace needed by cs_interval_abundance for (n, path). */
+size_t cs_interval_abundance_workspace(int64_t n, int path);
+
+/*
+ * Interval abundances of a time-sorted causal matrix (Algorithm "Optimized
+ * Interval Abundance Measurement" and Figure "Proper distance and the order
+ * intervals": for every related pair i < j, |A_ij| is the popcount of the
+ * AND of rows i and j over columns i+1..j-1, i.e. (C.C)_ij for the strict
+ * upper triangle C).  hist_dev (cs_hist_len(n) int64) is zeroed and then
+ * filled by the callee.  path selects the kernel (CS_PATH_AUTO picks one);
+ * both paths give identical, exact results.
+ * Errors: CS_EINVAL (n < 1, n > 2^22, bad row_words, NULL or unaligned pointers), CS_ENOMEM
+ * (workspace too small), CS_EUNSUPPORTED (CS_PATH_MMA on a device without
+ * tcgen05), CS_ECUDA.  A timed-out in-kernel wait sets CS_ETIMEOUT in the
+ * workspace status word.
+ */
+int cs_interval_abundance(int64_t n, const uint64_t *bits_dev, int64_t row_words,
+                          int64_t *hist_dev, int path,
+                          void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/*
+ * Read (synchronously: waits for `stream`) and clear the status word that
+ * kernels of the last call using this workspace wrote.  Returns CS_OK, the
+ * in-kernel error, or CS_ECUDA if the stream itself failed.
+ */
+int cs_workspace_status(void *workspace_dev, void *stream);
+
+/* ----------------------------------------------------------------- action */
+
+/*
+ * Benincasa-Dowker action from host abundances (Section "The
+ * Benincasa-Dowker Action"), with hist[k] = n_{k+1}:
+ *   dim 2, local (Eq. s2d_local):   S = 2 (N - 2 n1 + 4 n2 - 2 n3)
+ *   dim 4, local (Eq. s4d_local):   S = 4/sqrt(6) (N - n1 + 9 n2 - 16 n3 + 8 n4),
+ *                                   taking (l/l_p)^2 = 1
+ *   dim 2, smeared (Eq. s2d_smeared): S = 2 eps [N - 2 eps sum_m n_m f2(m-1, eps)]
+ *   dim 4, smeared (Eq. s4d_smeared): S = 4 sqrt(eps/6) [N - eps sum_m n_m f4(m-1, eps)]
+ * eps <= 0 or eps == 1 selects the local action (the smeared forms reduce to
+ * it at eps = 1); 0 < eps < 1 the smeared one, summed over the whole
+ * histogram in double-double (compensated FP64) arithmetic.
+ * out (may be NULL) receives S; bracket_out (may be NULL) the exact integer
+ * in parentheses of the local form.  Synchronous, host only.
+ * Errors: CS_EINVAL (dim not 2 or 4, eps > 1 or NaN, n < 0, len < 0).
+ */
+int cs_action(int dim, int64_t n, const int64_t *hist_host, int64_t len,
+              double eps, double *out, int64_t *bracket_out);
+
+/* Device workspace needed by cs_action_device. */
+size_t cs_action_workspace_bytes(void);
+
+/*
+ * The same actions evaluated on the device, for n_eps values of eps at once
+ * (eps_host is read at call time): out_dev[e] receives S for eps_host[e] and
+ * *bracket_dev (may be NULL) the local bracket.  Asynchronous on `stream`;
+ * hist_dev is the device histogram written by cs_interval_abundance.  The
+ * smeared sums are split over 128 blocks whose double-double partial sums
+ * go to the workspace.
+ * Errors: CS_EINVAL (as cs_action, or n_eps outside 1..16), CS_ENOMEM
+ * (workspace too small), CS_ECUDA.
+ */
+int cs_action_device(int dim, int64_t n, const int64_t *hist_dev, int64_t len,
+                     const double *eps_host, int n_eps, double *out_dev,
+                     int64_t *bracket_dev, void *workspace_dev, size_t workspace_bytes,
+                     void *stream);
+
+/* ------------------------------------------------------- host-buffer call */
+
+/*
+ * One whole evaluation from host buffers, for callers that keep their data
+ * on the host: copies coords_host (cs_coords_bytes) to the device, builds the
+ * causal matrix, counts intervals on `path`, evaluates the actions for n_eps
+ * values of eps, and copies hist_host (cs_hist_len(n) int64), actions_host
+ * (n_eps doubles) and *bracket_host back.  If coords_host is NULL the set is
+ * sprinkled on the device from (kind, n, seed) instead.  Device memory comes
+ * from the stream-ordered allocator and is returned before the call ends.
+ * Synchronous: returns after the results are on the host.
+ * Errors: as the individual entry points, plus CS_ENOMEM.
+ */
+int cs_evaluate(int kind, int64_t n, uint64_t seed, const int32_t *coords_host, int path,
+                const double *eps_host, int n_eps, int64_t *hist_host,
+                double *actions_host, int64_t *bracket_host, void *stream);
+
+/* ------------------------------------------------------------------ misc */
+
+/* Static description of a status code. */
+const char *cs_strerror(int status);
+
+/* Library version string. */
+const char *cs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CS_H */

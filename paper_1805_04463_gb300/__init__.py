@@ -1,0 +1,237 @@
+"""GB300-native causal-set interval abundances and Benincasa-Dowker action.
+
+Thin Python binding over the C ABI declared in include/cs.h (the compiled
+library libcausetgb.so, CUDA for sm_103a).  Every function here only
+marshals arguments: buffers are torch tensors (device memory and streams
+come from PyTorch), and every step of the computation runs in the library's
+kernels.  There is no CPU fallback: if the library is missing or cannot load,
+every call raises CsError.
+
+Reference: W. J. Cunningham, "High Performance Algorithms for Quantum Gravity
+and Cosmology" (arXiv:1805.04463), Chapter "Causal Set Action".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = [
+    "KIND_2D_ORDER", "KIND_2D_DIAMOND", "KIND_4D_DIAMOND", "PATH_AUTO", "PATH_POPC", "PATH_MMA",
+    "CsError", "lib", "dim", "coords_bytes", "row_words", "bitset_bytes", "hist_len",
+    "sprinkle_workspace_bytes", "interval_abundance_workspace", "action_workspace_bytes",
+    "sprinkle", "causal_matrix", "interval_abundance", "workspace_status", "action", "action_device",
+    "evaluate", "Buffers", "allocate", "run",
+]
+
+KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND = 0, 1, 2
+PATH_AUTO, PATH_POPC, PATH_MMA = 0, 1, 2
+KIND_NAMES = {KIND_2D_ORDER: "2d_order", KIND_2D_DIAMOND: "2d_diamond", KIND_4D_DIAMOND: "4d_diamond"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "libcausetgb.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class CsError(RuntimeError):
+    """A non-zero cs_status from the library, or the library is unavailable."""
+
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = status if isinstance(status, str) else f"{what}: status {status}"
+        if not isinstance(status, str) and _lib is not None:
+            msg += " (" + _lib.cs_strerror(status).decode() + ")"
+        super().__init__(msg)
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcausetgb.so (built by paper_1805_04463_gb300.build); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIBPATH):
+            raise CsError(f"{LIBPATH} is missing: build it with paper_1805_04463_gb300.build.build() "
+                          "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIBPATH)
+        i32, i64, u64, sz, vp, dp = (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t,
+                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_double))
+        sig = {
+            "cs_dim": ([i32], i32),
+            "cs_coords_bytes": ([i32, i64], sz),
+            "cs_row_words": ([i64], i64),
+            "cs_bitset_bytes": ([i64], sz),
+            "cs_hist_len": ([i64], i64),
+            "cs_sprinkle_workspace_bytes": ([i32, i64], sz),
+            "cs_sprinkle": ([i32, i64, u64, vp, vp, sz, vp], i32),
+            "cs_causal_matrix": ([i32, i64, vp, vp, i64, vp], i32),
+            "cs_interval_abundance_workspace": ([i64, i32], sz),
+            "cs_interval_abundance": ([i64, vp, i64, vp, i32, vp, sz, vp], i32),
+            "cs_workspace_status": ([vp, vp], i32),
+            "cs_action": ([i32, i64, vp, i64, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int64)], i32),
+            "cs_action_workspace_bytes": ([], sz),
+            "cs_action_device": ([i32, i64, vp, i64, vp, i32, vp, vp, vp, sz, vp], i32),
+            "cs_evaluate": ([i32, i64, u64, vp, i32, vp, i32, vp, vp, vp, vp], i32),
+            "cs_strerror": ([i32], ctypes.c_char_p),
+            "cs_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+        return L
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise CsError(rc, what)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _nbytes(t):
+    return t.numel() * t.element_size()
+
+
+# ----------------------------------------------------------------- layouts
+
+def dim(kind: int) -> int:
+    return lib().cs_dim(kind)
+
+
+def coords_bytes(kind: int, n: int) -> int:
+    return lib().cs_coords_bytes(kind, n)
+
+
+def row_words(n: int) -> int:
+    return lib().cs_row_words(n)
+
+
+def bitset_bytes(n: int) -> int:
+    return lib().cs_bitset_bytes(n)
+
+
+def hist_len(n: int) -> int:
+    return lib().cs_hist_len(n)
+
+
+def sprinkle_workspace_bytes(kind: int, n: int) -> int:
+    return lib().cs_sprinkle_workspace_bytes(kind, n)
+
+
+def interval_abundance_workspace(n: int, path: int = PATH_AUTO) -> int:
+    return lib().cs_interval_abundance_workspace(n, path)
+
+
+def action_workspace_bytes() -> int:
+    return lib().cs_action_workspace_bytes()
+
+
+# ------------------------------------------------------------- entry points
+
+def sprinkle(kind, n, seed, coords, workspace, stream=None):
+    """cs_sprinkle: time-sorted int32 coordinates (dim, n) into `coords`."""
+    _check(lib().cs_sprinkle(kind, n, seed, _ptr(coords), _ptr(workspace), _nbytes(workspace), _stream(stream)),
+           "cs_sprinkle")
+
+
+def causal_matrix(kind, n, coords, bits, stream=None):
+    """cs_causal_matrix: symmetric row bitsets (n, row_words) into `bits` (int64 storage)."""
+    _check(lib().cs_causal_matrix(kind, n, _ptr(coords), _ptr(bits), bits.shape[-1], _stream(stream)),
+           "cs_causal_matrix")
+
+
+def interval_abundance(n, bits, hist, path=PATH_AUTO, workspace=None, stream=None):
+    """cs_interval_abundance: N_k histogram (int64, hist_len(n)) into `hist`."""
+    _check(lib().cs_interval_abundance(n, _ptr(bits), bits.shape[-1], _ptr(hist), path, _ptr(workspace),
+                                       _nbytes(workspace), _stream(stream)), "cs_interval_abundance")
+
+
+def workspace_status(workspace, stream=None) -> int:
+    """cs_workspace_status: in-kernel status of the last call on this workspace (synchronising)."""
+    return lib().cs_workspace_status(_ptr(workspace), _stream(stream))
+
+
+def action(dim_, n, hist, eps=0.0):
+    """cs_action on a host int64 numpy histogram: (S, bracket)."""
+    import numpy as np
+    h = np.ascontiguousarray(hist, dtype=np.int64)
+    out = ctypes.c_double(0.0)
+    br = ctypes.c_int64(0)
+    _check(lib().cs_action(dim_, n, h.ctypes.data if h.size else None, h.size, float(eps), ctypes.byref(out),
+                           ctypes.byref(br)), "cs_action")
+    return out.value, br.value
+
+
+def action_device(dim_, n, hist, eps, out, bracket, workspace, stream=None):
+    """cs_action_device: actions for each eps in `eps` into the float64 tensor `out`."""
+    arr = (ctypes.c_double * len(eps))(*[float(e) for e in eps])
+    _check(lib().cs_action_device(dim_, n, _ptr(hist), hist.numel(), ctypes.cast(arr, ctypes.c_void_p), len(eps),
+                                  _ptr(out), _ptr(bracket), _ptr(workspace), _nbytes(workspace), _stream(stream)),
+           "cs_action_device")
+
+
+def evaluate(kind, n, seed=0, coords_host=None, path=PATH_AUTO, eps=(), stream=None, hist_out=None):
+    """cs_evaluate from host buffers: returns (hist numpy int64, actions list, bracket).
+
+    coords_host: optional numpy int32 (dim, n) array (pinned or pageable); when None the
+    set is sprinkled on the device from (kind, n, seed).
+    """
+    import numpy as np
+    hl = hist_len(n)
+    hist = hist_out if hist_out is not None else np.zeros(hl, dtype=np.int64)
+    acts = np.zeros(max(len(eps), 1), dtype=np.float64)
+    br = ctypes.c_int64(0)
+    arr = (ctypes.c_double * max(len(eps), 1))(*([float(e) for e in eps] or [0.0]))
+    cptr = None
+    if coords_host is not None:
+        assert coords_host.dtype == np.int32 and coords_host.flags["C_CONTIGUOUS"]
+        cptr = coords_host.ctypes.data
+    _check(lib().cs_evaluate(kind, n, seed, cptr, path, ctypes.cast(arr, ctypes.c_void_p), len(eps),
+                             hist.ctypes.data, acts.ctypes.data, ctypes.byref(br), _stream(stream)),
+           "cs_evaluate")
+    return hist, [float(x) for x in acts[:len(eps)]], br.value
+
+
+# ---------------------------------------------------- device buffer helper
+
+class Buffers:
+    """Device buffers for one causal set of `kind` and size n (torch tensors)."""
+
+    def __init__(self, kind, n, device="cuda", path=PATH_AUTO):
+        import torch
+        self.kind, self.n, self.path = kind, n, path
+        self.dim = dim(kind)
+        self.rw = row_words(n)
+        self.coords = torch.empty((self.dim, n), dtype=torch.int32, device=device)
+        self.bits = torch.empty((n, self.rw), dtype=torch.int64, device=device)
+        self.hist = torch.empty(hist_len(n), dtype=torch.int64, device=device)
+        ws = max(sprinkle_workspace_bytes(kind, n), interval_abundance_workspace(n, path), action_workspace_bytes())
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=device)
+        self.actions = torch.empty(16, dtype=torch.float64, device=device)
+        self.bracket = torch.empty(1, dtype=torch.int64, device=device)
+
+
+def allocate(kind, n, device="cuda", path=PATH_AUTO) -> Buffers:
+    return Buffers(kind, n, device, path)
+
+
+def run(buf: Buffers, seed: int, eps=(0.0,), stream=None, sprinkle_=True):
+    """One whole pass on device buffers: sprinkle, relate, count, actions (all async)."""
+    if sprinkle_:
+        sprinkle(buf.kind, buf.n, seed, buf.coords, buf.workspace, stream)
+    causal_matrix(buf.kind, buf.n, buf.coords, buf.bits, stream)
+    interval_abundance(buf.n, buf.bits, buf.hist, buf.path, buf.workspace, stream)
+    if eps:
+        action_device(buf.dim, buf.n, buf.hist, list(eps), buf.actions, buf.bracket, buf.workspace, stream)

@@ -1,0 +1,241 @@
+// cs_api.cu -- the extern "C" entry points of include/cs.h: argument
+// validation, workspace bookkeeping and dispatch to the kernels.
+#include <cstring>
+
+#include "cs_kernels.cuh"
+
+namespace cs {
+namespace {
+
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+inline int from_cuda(cudaError_t e) { return e == cudaSuccess ? CS_OK : CS_ECUDA; }
+
+inline bool valid_n(int64_t n) { return n >= 1 && n <= kMaxN; }
+
+const double kZero = 0.0;
+
+// Every call that owns a workspace first clears its status word, so the word
+// always reports the last call that used the workspace.
+inline cudaError_t clear_status(void* ws, cudaStream_t st) {
+    return cudaMemsetAsync(&static_cast<WsHeader*>(ws)->status, 0, sizeof(int32_t), st);
+}
+
+}  // namespace
+
+// The tensor-core path pays a fixed O(n^2) operand expansion; below this size
+// the popcount tiles win.
+constexpr int64_t kAutoMmaMinN = 8192;
+
+int resolve_path(int64_t n, int path) {
+    if (path != CS_PATH_AUTO) return path;
+    return (n >= kAutoMmaMinN && device_has_tcgen05()) ? CS_PATH_MMA : CS_PATH_POPC;
+}
+
+}  // namespace cs
+
+using namespace cs;
+
+extern "C" {
+
+int cs_dim(int kind) {
+    if (kind == CS_2D_ORDER || kind == CS_2D_DIAMOND) return 2;
+    if (kind == CS_4D_DIAMOND) return 4;
+    return 0;
+}
+
+size_t cs_coords_bytes(int kind, int64_t n) {
+    const int d = cs_dim(kind);
+    if (d == 0 || n < 0) return 0;
+    return size_t(n) * size_t(d) * 4;
+}
+
+int64_t cs_row_words(int64_t n) {
+    if (n < 0) return 0;
+    const int64_t w = (n + 63) / 64;
+    return (w + 15) / 16 * 16;
+}
+
+size_t cs_bitset_bytes(int64_t n) { return n < 0 ? 0 : size_t(n) * size_t(cs_row_words(n)) * 8; }
+
+int64_t cs_hist_len(int64_t n) { return n > 1 ? n - 1 : 1; }
+
+size_t cs_sprinkle_workspace_bytes(int kind, int64_t n) {
+    if (cs_dim(kind) == 0 || !valid_n(n)) return 0;
+    return sprinkle_workspace_bytes(n);
+}
+
+int cs_sprinkle(int kind, int64_t n, uint64_t seed, int32_t* coords_dev, void* workspace_dev, size_t workspace_bytes,
+                void* stream) {
+    if (cs_dim(kind) == 0 || !valid_n(n) || !coords_dev || !aligned(coords_dev, 4) || !workspace_dev ||
+        !aligned(workspace_dev, 256))
+        return CS_EINVAL;
+    if (workspace_bytes < sprinkle_workspace_bytes(n)) return CS_ENOMEM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = clear_status(workspace_dev, st);
+    if (e == cudaSuccess) e = launch_sprinkle(kind, n, seed, coords_dev, workspace_dev, st);
+    return from_cuda(e);
+}
+
+int cs_causal_matrix(int kind, int64_t n, const int32_t* coords_dev, uint64_t* bits_dev, int64_t row_words,
+                     void* stream) {
+    if (cs_dim(kind) == 0 || !valid_n(n) || !coords_dev || !bits_dev || !aligned(bits_dev, 16) ||
+        row_words < cs_row_words(n) || row_words % 16 != 0)
+        return CS_EINVAL;
+    return from_cuda(launch_relate(kind, n, coords_dev, bits_dev, row_words, static_cast<cudaStream_t>(stream)));
+}
+
+size_t cs_interval_abundance_workspace(int64_t n, int path) {
+    if (!valid_n(n) || path < CS_PATH_AUTO || path > CS_PATH_MMA) return 0;
+    return resolve_path(n, path) == CS_PATH_MMA ? mma_workspace_bytes(n) : popc_workspace_bytes(n);
+}
+
+int cs_interval_abundance(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_t* hist_dev, int path,
+                          void* workspace_dev, size_t workspace_bytes, void* stream) {
+    if (!valid_n(n) || !bits_dev || !aligned(bits_dev, 128) || !hist_dev || !aligned(hist_dev, 8) ||
+        row_words < cs_row_words(n) || row_words % 16 != 0 || !workspace_dev || !aligned(workspace_dev, 256) ||
+        path < CS_PATH_AUTO || path > CS_PATH_MMA)
+        return CS_EINVAL;
+    if (workspace_bytes < cs_interval_abundance_workspace(n, path)) return CS_ENOMEM;
+    const int p = resolve_path(n, path);
+    if (p == CS_PATH_MMA && !device_has_tcgen05()) return CS_EUNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = clear_status(workspace_dev, st);
+    if (e == cudaSuccess)
+        e = p == CS_PATH_MMA ? launch_count_mma(n, bits_dev, row_words, hist_dev, workspace_dev, st)
+                             : launch_count_popc(n, bits_dev, row_words, hist_dev, workspace_dev, st);
+    return from_cuda(e);
+}
+
+int cs_workspace_status(void* workspace_dev, void* stream) {
+    if (!workspace_dev) return CS_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t status = 0;
+    if (cudaMemcpyAsync(&status, &static_cast<WsHeader*>(workspace_dev)->status, sizeof(status),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return CS_ECUDA;
+    if (clear_status(workspace_dev, st) != cudaSuccess) return CS_ECUDA;
+    return status;
+}
+
+int cs_action(int dim, int64_t n, const int64_t* hist_host, int64_t len, double eps, double* out,
+              int64_t* bracket_out) {
+    return action_host(dim, n, hist_host, len, eps, out, bracket_out);
+}
+
+size_t cs_action_workspace_bytes(void) { return action_workspace_bytes(); }
+
+int cs_action_device(int dim, int64_t n, const int64_t* hist_dev, int64_t len, const double* eps_host, int n_eps,
+                     double* out_dev, int64_t* bracket_dev, void* workspace_dev, size_t workspace_bytes,
+                     void* stream) {
+    if ((dim != 2 && dim != 4) || n < 0 || len < 1 || !hist_dev || !eps_host || n_eps < 1 || n_eps > 16 ||
+        !out_dev || !workspace_dev || !aligned(workspace_dev, 256))
+        return CS_EINVAL;
+    for (int e = 0; e < n_eps; ++e)
+        if (!(eps_host[e] <= 1.0)) return CS_EINVAL;
+    if (workspace_bytes < action_workspace_bytes()) return CS_ENOMEM;
+    return from_cuda(launch_action_device(dim, n, hist_dev, len, eps_host, n_eps, out_dev, bracket_dev,
+                                          workspace_dev, static_cast<cudaStream_t>(stream)));
+}
+
+int cs_evaluate(int kind, int64_t n, uint64_t seed, const int32_t* coords_host, int path, const double* eps_host,
+                int n_eps, int64_t* hist_host, double* actions_host, int64_t* bracket_host, void* stream) {
+    const int dim = cs_dim(kind);
+    if (dim == 0 || !valid_n(n) || n_eps < 0 || n_eps > 16 || (n_eps > 0 && (!eps_host || !actions_host)) ||
+        path < CS_PATH_AUTO || path > CS_PATH_MMA)
+        return CS_EINVAL;
+    for (int e = 0; e < n_eps; ++e)
+        if (!(eps_host[e] <= 1.0)) return CS_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // Keep freed blocks in the device's stream-ordered pool between calls.
+    static bool pool_set[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CS_ECUDA;
+    if (dev >= 0 && dev < 64 && !pool_set[dev]) {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pool_set[dev] = true;
+    }
+
+    const int64_t rw = cs_row_words(n);
+    const int64_t hl = cs_hist_len(n);
+    size_t ws_bytes = cs_interval_abundance_workspace(n, path);
+    if (cs_sprinkle_workspace_bytes(kind, n) > ws_bytes) ws_bytes = cs_sprinkle_workspace_bytes(kind, n);
+    if (action_workspace_bytes() > ws_bytes) ws_bytes = action_workspace_bytes();
+
+    int32_t* coords = nullptr;
+    uint64_t* bits = nullptr;
+    int64_t* hist = nullptr;
+    void* ws = nullptr;
+    double* out = nullptr;  // [16] actions, then the bracket as int64
+    int rc = CS_OK;
+    auto alloc = [&](void** p, size_t b) {
+        if (rc == CS_OK && cudaMallocAsync(p, b, st) != cudaSuccess) rc = CS_ENOMEM;
+    };
+    alloc(reinterpret_cast<void**>(&coords), cs_coords_bytes(kind, n));
+    alloc(reinterpret_cast<void**>(&bits), cs_bitset_bytes(n));
+    alloc(reinterpret_cast<void**>(&hist), size_t(hl) * 8);
+    alloc(&ws, ws_bytes);
+    alloc(reinterpret_cast<void**>(&out), 17 * 8);
+    int64_t* bracket = reinterpret_cast<int64_t*>(out + 16);
+
+    if (rc == CS_OK) {
+        if (coords_host)
+            rc = from_cuda(cudaMemcpyAsync(coords, coords_host, cs_coords_bytes(kind, n), cudaMemcpyHostToDevice, st));
+        else
+            rc = cs_sprinkle(kind, n, seed, coords, ws, ws_bytes, st);
+    }
+    int32_t status_sprinkle = 0;
+    if (rc == CS_OK && !coords_host)
+        rc = from_cuda(cudaMemcpyAsync(&status_sprinkle, &static_cast<WsHeader*>(ws)->status, sizeof(int32_t),
+                                       cudaMemcpyDeviceToHost, st));
+    if (rc == CS_OK) rc = cs_causal_matrix(kind, n, coords, bits, rw, st);
+    if (rc == CS_OK) rc = cs_interval_abundance(n, bits, rw, hist, path, ws, ws_bytes, st);
+    int32_t status = 0;
+    if (rc == CS_OK)
+        rc = from_cuda(cudaMemcpyAsync(&status, &static_cast<WsHeader*>(ws)->status, sizeof(status),
+                                       cudaMemcpyDeviceToHost, st));
+    if (rc == CS_OK && n_eps > 0) {
+        rc = cs_action_device(dim, n, hist, hl, eps_host, n_eps, out, bracket, ws, ws_bytes, st);
+        if (rc == CS_OK)
+            rc = from_cuda(cudaMemcpyAsync(actions_host, out, size_t(n_eps) * 8, cudaMemcpyDeviceToHost, st));
+    }
+    if (rc == CS_OK && bracket_host) {
+        if (n_eps == 0) rc = cs_action_device(dim, n, hist, hl, eps_host ? eps_host : &kZero, 1, out, bracket, ws,
+                                              ws_bytes, st);
+        if (rc == CS_OK) rc = from_cuda(cudaMemcpyAsync(bracket_host, bracket, 8, cudaMemcpyDeviceToHost, st));
+    }
+    if (rc == CS_OK && hist_host)
+        rc = from_cuda(cudaMemcpyAsync(hist_host, hist, size_t(hl) * 8, cudaMemcpyDeviceToHost, st));
+    if (coords) cudaFreeAsync(coords, st);
+    if (bits) cudaFreeAsync(bits, st);
+    if (hist) cudaFreeAsync(hist, st);
+    if (ws) cudaFreeAsync(ws, st);
+    if (out) cudaFreeAsync(out, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == CS_OK) rc = CS_ECUDA;
+    if (rc == CS_OK && status_sprinkle != 0) rc = status_sprinkle;
+    if (rc == CS_OK && status != 0) rc = status;
+    return rc;
+}
+
+const char* cs_strerror(int status) {
+    switch (status) {
+        case CS_OK: return "ok";
+        case CS_EINVAL: return "invalid argument";
+        case CS_ENOMEM: return "workspace too small or out of memory";
+        case CS_ECUDA: return "CUDA error";
+        case CS_ETIMEOUT: return "bounded in-kernel wait timed out";
+        case CS_EUNSUPPORTED: return "unsupported on this device";
+        case CS_ERANGE: return "sampler exhausted its attempt budget";
+        default: return "unknown status";
+    }
+}
+
+const char* cs_version(void) { return "causet-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,312 @@
+// cs_count_mma.cu -- interval abundances as an exact dense contraction on the
+// tcgen05 tensor cores (Figure "Proper distance and the order intervals": the
+// interval of a related pair is the inner product of rows i and j between
+// columns i and j, i.e. (C.C)_ij for the strict upper triangle C).
+//
+// Operands.  The symmetric bitset is expanded once into two K-major byte
+// matrices of 0/1 values in FP8 E4M3 (1.0 = 0x38):
+//   U[i][k] = 1 iff k > i and i, k related   (row i = future of i, F_i)
+//   L[j][k] = 1 iff k < j and j, k related   (row j = past of j,  P_j)
+// so M = U . L^T holds |A_ij| = sum_k U_ik L_jk with no masking at all: the
+// zeros of U (k <= i) and L (k >= j) restrict k to i < k < j.  Products are 0
+// or 1 and every partial sum is an integer below 2^24, so FP32 accumulation
+// is exact.
+//
+// Kernel.  A persistent grid (one CTA per SM) walks 128 x 256 output tiles
+// (128 i-rows, 256 j-rows, i-block at or before the j-block) in decreasing K
+// length, statically strided over CTAs.  Warp roles:
+//   warp 0      TMA producer: 128-row A slab and 256-row B slab of 128 K-bytes
+//               per stage (128B swizzle) into a 4-stage shared-memory ring;
+//   warp 1      TMEM allocator and MMA issuer: 4 x tcgen05.mma (M128 N256 K32)
+//               per stage into one of two TMEM accumulators (2 x 256 columns);
+//   warps 2..5  epilogue: tcgen05.ld of the finished accumulator (one TMEM
+//               lane = one row i per thread), mask by i < j < n and C_ij from
+//               the bitset, bucket k into a shared-memory histogram (global
+//               atomics above 8192), then release the accumulator.
+// The K loop of a tile runs only over the K-blocks between the i-block and the
+// end of the j-block.  C.C is never written to memory.
+#include "cs_kernels.cuh"
+
+namespace cs {
+
+namespace {
+
+constexpr int kBM = 128;                 // i rows per tile (TMEM lanes)
+constexpr int kBN = 256;                 // j rows per tile (accumulator columns)
+constexpr int kBK = 128;                 // K bytes (FP8 elements) per stage = one 128B swizzle row
+constexpr int kUK = 32;                  // K per tcgen05.mma of kind::f8f6f4
+constexpr int kStages = 4;
+constexpr int kABytes = kBM * kBK;       // 16 KiB
+constexpr int kBBytes = kBN * kBK;       // 32 KiB
+constexpr int kStageBytes = kABytes + kBBytes;
+constexpr int kHistBins = 8192;
+constexpr int kThreads = 192;
+constexpr int kTmemCols = 512;           // two 256-column FP32 accumulators
+constexpr uint32_t kIdesc = idesc_f8_f32(kBM, kBN);
+constexpr int kSmemBytes = kStages * kStageBytes + kHistBins * 4 + 256 + 1024;
+constexpr uint8_t kOne = 0x38;           // 1.0 in FP8 E4M3
+
+// Items: supertiles of 256 x 256 pairs (si <= sj) in decreasing K length,
+// each split into two 128-row halves.  Returns false for a half that lies
+// entirely beyond n.
+struct Item {
+    int64_t I0, J0;
+    int64_t kb0, kb1;  // K-blocks [kb0, kb1)
+};
+
+__device__ __forceinline__ bool decode_item(int64_t t, int64_t nsb, int64_t n, int64_t kblocks, Item& it) {
+    const int64_t st = t >> 1, half = t & 1;
+    int64_t m = int64_t((1.0 + sqrt(1.0 + 8.0 * double(st))) * 0.5);
+    while (m * (m - 1) / 2 > st) --m;
+    while (m * (m + 1) / 2 <= st) ++m;
+    const int64_t si = st - m * (m - 1) / 2;
+    const int64_t sj = si + (nsb - m);
+    it.I0 = si * 256 + half * kBM;
+    it.J0 = sj * kBN;
+    it.kb0 = it.I0 / kBK;
+    int64_t e = (it.J0 + kBN + kBK - 1) / kBK;
+    it.kb1 = e < kblocks ? e : kblocks;
+    return it.I0 < n;
+}
+
+// Spread the low 8 bits of x into 8 bytes of 0x00 / 0x38 (bit b -> byte b).
+__device__ __forceinline__ uint64_t spread_byte(uint32_t x) {
+    uint64_t y = (uint64_t(x & 0xFFu) * 0x0101010101010101ull) & 0x8040201008040201ull;
+    y = ((y + 0x7F7F7F7F7F7F7F7Full) & 0x8080808080808080ull) >> 7;  // 0x01 where the bit was set
+    return y * kOne;
+}
+
+__device__ __forceinline__ void store_expanded(uint8_t* dst, uint64_t w) {
+    uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t b = uint32_t(w >> (16 * q));
+        uint4 v;
+        const uint64_t lo = spread_byte(b & 0xFFu), hi = spread_byte((b >> 8) & 0xFFu);
+        v.x = uint32_t(lo);
+        v.y = uint32_t(lo >> 32);
+        v.z = uint32_t(hi);
+        v.w = uint32_t(hi >> 32);
+        d[q] = v;
+    }
+}
+
+// U and L rows from the symmetric bitset: one thread per 64-bit word.
+__global__ void __launch_bounds__(256) k_expand_f8(const uint64_t* __restrict__ bits, int64_t n, int64_t row_words,
+                                                   int64_t kpad, uint8_t* __restrict__ U, uint8_t* __restrict__ L) {
+    const int64_t wpr = kpad / 64;
+    const int64_t total = n * wpr;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = idx / wpr, w = idx - i * wpr;
+        const uint64_t word = bits[i * row_words + w];
+        const int64_t x = i - 64 * w;  // bit position of column i inside this word
+        const uint64_t after = x < 0 ? ~0ull : (x >= 63 ? 0ull : (~0ull << (x + 1)));
+        const uint64_t before = x <= 0 ? 0ull : (x >= 64 ? ~0ull : ((1ull << x) - 1ull));
+        store_expanded(U + i * kpad + 64 * w, word & after);
+        store_expanded(L + i * kpad + 64 * w, word & before);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_count_mma(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mapL,
+                const uint64_t* __restrict__ bits, int64_t n, int64_t row_words, int64_t nsb, int64_t nitems,
+                int64_t kblocks, unsigned long long* __restrict__ hist, int64_t hist_len, WsHeader* hdr) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes);
+    uint64_t* full = reinterpret_cast<uint64_t*>(shist + kHistBins);
+    uint64_t* empty = full + kStages;
+    uint64_t* tfull = empty + kStages;
+    uint64_t* tempty = tfull + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t hb = hist_len < kHistBins ? hist_len : kHistBins;
+
+    for (int k = tid; k < kHistBins; k += kThreads) shist[k] = 0u;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4 * 32);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------- TMA producer
+        uint32_t s = 0, ph = 0, issued = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
+            Item it;
+            if (!decode_item(t, nsb, n, kblocks, it)) continue;
+            for (int64_t kb = it.kb0; kb < it.kb1; ++kb) {
+                if (!mbar_wait_or_abort(&empty[s], ph ^ 1u, hdr, abort_flag)) { ok = false; break; }
+                uint8_t* a = smem + s * kStageBytes;
+                mbar_arrive_expect_tx(&full[s], kStageBytes);
+                tma_load_2d(a, &mapU, int32_t(kb * kBK), int32_t(it.I0), &full[s]);
+                tma_load_2d(a + kABytes, &mapL, int32_t(kb * kBK), int32_t(it.J0), &full[s]);
+                ++issued;
+                if (++s == kStages) { s = 0; ph ^= 1u; }
+            }
+        }
+        if (!ok) {
+            // Let the copies still in flight land before shared memory goes away.
+            for (uint32_t q = 0; q < kStages && q < issued; ++q) {
+                const uint32_t g = issued - 1 - q;
+                mbar_wait_bounded(&full[g % kStages], (g / kStages) & 1u, hdr);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------------- MMA issuer
+        uint32_t s = 0, ph = 0;
+        int64_t local = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
+            Item it;
+            if (!decode_item(t, nsb, n, kblocks, it)) continue;
+            const uint32_t buf = uint32_t(local & 1), use = uint32_t((local >> 1) & 1);
+            ++local;
+            if (!mbar_wait_or_abort(&tempty[buf], use ^ 1u, hdr, abort_flag)) break;
+            tc_fence_after();
+            const uint32_t d = tmem_base + buf * kBN;
+            for (int64_t kb = it.kb0; kb < it.kb1; ++kb) {
+                if (!mbar_wait_or_abort(&full[s], ph, hdr, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t a = smem_u32(smem + s * kStageBytes);
+                const uint64_t adesc = sdesc_k_sw128(a), bdesc = sdesc_k_sw128(a + kABytes);
+#pragma unroll
+                for (int kk = 0; kk < kBK / kUK; ++kk)
+                    mma_f8f6f4(d, adesc + uint64_t((kk * kUK) >> 4), bdesc + uint64_t((kk * kUK) >> 4), kIdesc,
+                               (kb > it.kb0 || kk > 0) ? 1u : 0u);
+                mma_commit(&empty[s]);
+                if (++s == kStages) { s = 0; ph ^= 1u; }
+            }
+            if (ok) mma_commit(&tfull[buf]);
+        }
+    } else if (warp >= 2) {
+        // ---------------------------------------------------- epilogue
+        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        int64_t local = 0;
+        for (int64_t t = blockIdx.x; t < nitems; t += gridDim.x) {
+            Item it;
+            if (!decode_item(t, nsb, n, kblocks, it)) continue;
+            const uint32_t buf = uint32_t(local & 1), use = uint32_t((local >> 1) & 1);
+            ++local;
+            if (!mbar_wait_or_abort(&tfull[buf], use, hdr, abort_flag)) break;
+            tc_fence_after();
+            const int64_t i = it.I0 + 32 * q + lane;
+            uint64_t cw[kBN / 64];
+#pragma unroll
+            for (int w = 0; w < kBN / 64; ++w) {
+                const int64_t word = (it.J0 >> 6) + w;
+                cw[w] = (i < n && word < row_words) ? __ldg(bits + i * row_words + word) : 0ull;
+            }
+#pragma unroll 1
+            for (int c = 0; c < kBN / 32; ++c) {
+                uint32_t v[32];
+                tmem_ld_32x32b_x32(tmem_base + (uint32_t(32 * q) << 16) + buf * kBN + uint32_t(32 * c), v);
+                tmem_ld_wait();
+                const uint32_t rel = uint32_t(cw[c >> 1] >> (32 * (c & 1)));  // C_ij for these 32 j
+#pragma unroll
+                for (int u = 0; u < 32; ++u) {
+                    const int64_t j = it.J0 + 32 * c + u;
+                    if (((rel >> u) & 1u) && j > i && j < n) {
+                        const uint32_t k = uint32_t(__uint_as_float(v[u]));
+                        if (int64_t(k) < hb)
+                            atomicAdd(&shist[k], 1u);
+                        else
+                            atomicAdd(&hist[k], 1ull);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty[buf]);
+        }
+    }
+    __syncthreads();
+    for (int64_t k = tid; k < hb; k += kThreads)
+        if (shist[k]) atomicAdd(&hist[k], (unsigned long long)shist[k]);
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+bool g_attr_set[64];
+
+struct MmaLayout {
+    int64_t kpad;
+    size_t u, l, total;
+};
+
+MmaLayout mma_layout(int64_t n) {
+    MmaLayout m;
+    m.kpad = (n + kBK - 1) / kBK * kBK;
+    m.u = sizeof(WsHeader);
+    m.l = align_up(m.u + size_t(n) * size_t(m.kpad), 1024);
+    m.total = align_up(m.l + size_t(n) * size_t(m.kpad), 256);
+    return m;
+}
+
+}  // namespace
+
+size_t mma_workspace_bytes(int64_t n) { return mma_layout(n).total; }
+
+cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* workspace,
+                             cudaStream_t st) {
+    WsHeader* hdr = static_cast<WsHeader*>(workspace);
+    const int64_t hist_len = n > 1 ? n - 1 : 1;
+    cudaError_t err = cudaMemsetAsync(hist, 0, size_t(hist_len) * 8, st);
+    if (err != cudaSuccess) return err;
+    if (n < 2) return cudaSuccess;
+    const MmaLayout lay = mma_layout(n);
+    uint8_t* U = static_cast<uint8_t*>(workspace) + lay.u;
+    uint8_t* L = static_cast<uint8_t*>(workspace) + lay.l;
+
+    const int64_t total_words = n * (lay.kpad / 64);
+    int64_t eg = (total_words + 255) / 256;
+    if (eg > int64_t(device_sm_count()) * 64) eg = int64_t(device_sm_count()) * 64;
+    k_expand_f8<<<unsigned(eg), 256, 0, st>>>(bits, n, row_words, lay.kpad, U, L);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+
+    CUtensorMap mapU, mapL;
+    if (encode_tensor_map_2d(&mapU, CU_TENSOR_MAP_DATA_TYPE_UINT8, U, uint64_t(lay.kpad), uint64_t(n),
+                             uint64_t(lay.kpad), kBK, kBM, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS ||
+        encode_tensor_map_2d(&mapL, CU_TENSOR_MAP_DATA_TYPE_UINT8, L, uint64_t(lay.kpad), uint64_t(n),
+                             uint64_t(lay.kpad), kBK, kBN, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+
+    int dev = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if (dev >= 0 && dev < 64 && !g_attr_set[dev]) {
+        err = cudaFuncSetAttribute(k_count_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (err != cudaSuccess) return err;
+        g_attr_set[dev] = true;
+    }
+    const int64_t nsb = (n + 255) / 256;
+    const int64_t nitems = nsb * (nsb + 1);  // two halves per supertile
+    const int64_t kblocks = lay.kpad / kBK;
+    int64_t grid = device_sm_count();
+    if (grid > nitems) grid = nitems;
+    k_count_mma<<<unsigned(grid), kThreads, kSmemBytes, st>>>(mapU, mapL, bits, n, row_words, nsb, nitems, kblocks,
+                                                              reinterpret_cast<unsigned long long*>(hist), hist_len,
+                                                              hdr);
+    return cudaGetLastError();
+}
+
+}  // namespace cs

@@ -1,0 +1,104 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+symbol include/cs.h declares; layout helpers; host-side action vs the oracle."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def cslib():
+    from paper_1805_04463_gb300 import build
+    build.build()
+    import paper_1805_04463_gb300 as cs
+    return cs
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(cs_\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_entry_points():
+    names = _declared_functions()
+    for want in ("cs_sprinkle", "cs_causal_matrix", "cs_interval_abundance", "cs_action", "cs_action_device",
+                 "cs_evaluate", "cs_workspace_status", "cs_strerror"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(cslib):
+    L = cslib.lib()
+    missing = [n for n in _declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_layout_helpers(cslib):
+    assert cslib.dim(0) == 2 and cslib.dim(1) == 2 and cslib.dim(2) == 4 and cslib.dim(7) == 0
+    for n, w in [(1, 16), (64, 16), (1024, 16), (1025, 32), (16384, 256), (131072, 2048), (131073, 2064)]:
+        assert cslib.row_words(n) == w
+        assert cslib.bitset_bytes(n) == n * w * 8
+    assert cslib.hist_len(1) == 1 and cslib.hist_len(1024) == 1023
+    assert cslib.coords_bytes(2, 10) == 160 and cslib.coords_bytes(0, 10) == 80
+    assert cslib.sprinkle_workspace_bytes(0, 0) == 0       # invalid n
+    assert cslib.sprinkle_workspace_bytes(5, 10) == 0      # invalid kind
+    assert cslib.interval_abundance_workspace(1000, 9) == 0
+
+
+def test_strerror_and_version(cslib):
+    L = cslib.lib()
+    assert L.cs_strerror(0) == b"ok"
+    assert L.cs_strerror(-4).startswith(b"bounded")
+    assert b"sm_103a" in L.cs_version()
+
+
+def test_host_action_matches_oracle(cslib, oracle):
+    rng = np.random.default_rng(7)
+    for dim in (2, 4):
+        for n in (1, 2, 3, 50, 1000, 20000):
+            for _ in range(3):
+                hl = max(n - 1, 1)
+                h = rng.integers(0, 10 ** 6, hl).astype(np.int64)
+                for eps in (0.0, -1.0, 1.0, 0.05, 0.1, 0.2, 0.5, 0.9, 1e-3):
+                    s_lib, b_lib = cslib.action(dim, n, h, eps)
+                    s_or, b_or = oracle.action(dim, n, h, eps)
+                    assert b_lib == b_or
+                    assert abs(s_lib - s_or) <= 1e-12 * max(1.0, abs(s_or)), (dim, n, eps, s_lib, s_or)
+
+
+def test_host_action_on_real_abundances(cslib, oracle):
+    # Abundances of an actual 2D order: the smeared sum cancels strongly.
+    c = oracle.sprinkle(0, 3000, 11)
+    h = oracle.interval_abundance(oracle.causal_matrix(0, c))
+    for eps in (0.05, 0.1, 0.2, 2.0 ** -6):
+        s_lib, _ = cslib.action(2, 3000, h, eps)
+        s_or, _ = oracle.action(2, 3000, h, eps)
+        assert abs(s_lib - s_or) <= 1e-12 * max(1.0, abs(s_or))
+    s_lib, b_lib = cslib.action(2, 3000, h, 0.0)
+    assert s_lib == 2 * b_lib
+
+
+def test_host_action_rejects_bad_arguments(cslib):
+    for args in [(3, 10, np.zeros(9, np.int64), 0.0), (2, 10, np.zeros(9, np.int64), 1.5),
+                 (2, -1, np.zeros(9, np.int64), 0.0), (2, 10, np.zeros(9, np.int64), float("nan"))]:
+        with pytest.raises(cslib.CsError):
+            cslib.action(*args)
+
+
+def test_chain_local_action_closed_form(cslib):
+    for n in (3, 10, 1000):
+        h = np.array([n - 1 - k for k in range(n - 1)], dtype=np.int64)
+        assert cslib.action(2, n, h) == (2.0 * n, n)
+        if n >= 4:
+            s, b = cslib.action(4, n, h)
+            assert b == n - 1 and abs(s - 4 / math.sqrt(6) * (n - 1)) <= 1e-15 * s

@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer results (coordinates, causal-matrix bits, every N_k, the action
+bracket) must match bit for bit; actions within 1e-12 relative.  Sizes span
+several 128-row tiles with ragged tails; the full-size workloads (N = 1024
+2D order, N = 16384 4D diamond, N = 131072 2D order) run in the launch
+configuration the benchmark times.
+"""
+import functools
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+EPS = (0.0, 0.05, 0.1, 0.2, 2.0 ** -6)
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def cs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_04463_gb300 import build
+    build.build()
+    import paper_1805_04463_gb300 as m
+    return m
+
+
+def _run(cs, kind, n, seed, path=1, coords=None):
+    import torch
+    b = cs.allocate(kind, n, path=path)
+    if coords is None:
+        cs.sprinkle(kind, n, seed, b.coords, b.workspace)
+        assert cs.workspace_status(b.workspace) == 0
+    else:
+        b.coords.copy_(torch.from_numpy(np.ascontiguousarray(coords, dtype=np.int32)))
+    cs.causal_matrix(kind, n, b.coords, b.bits)
+    cs.interval_abundance(n, b.bits, b.hist, path, b.workspace)
+    assert cs.workspace_status(b.workspace) == 0
+    torch.cuda.synchronize()
+    return b
+
+
+def _np_bits(b):
+    return b.bits.cpu().numpy().view(np.uint64)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("n", [1, 2, 3, 63, 64, 65, 129, 1000, 4097])
+def test_sprinkle_and_relate_bit_exact(cs, oracle, kind, n):
+    seed = 0xC5E70000 + 31 * n + kind
+    b = _run(cs, kind, n, seed)
+    want = oracle.sprinkle(kind, n, seed)
+    assert (b.coords.cpu().numpy() == want).all()
+    assert (_np_bits(b) == oracle.causal_matrix(kind, want)).all()
+
+
+@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("kind,n", [(0, 2), (0, 3), (0, 127), (0, 128), (0, 129), (0, 255), (0, 256), (0, 257),
+                                    (0, 300), (0, 511), (0, 1000), (0, 1024), (0, 2049), (0, 4133), (1, 129),
+                                    (1, 1500), (1, 3001), (2, 200), (2, 1111), (2, 4096), (2, 5000)])
+def test_interval_abundance_bit_exact(cs, oracle, kind, n, path):
+    seed = 0xC5E71000 + n + kind
+    b = _run(cs, kind, n, seed, path=path)
+    bits = _np_bits(b)
+    want = oracle.interval_abundance(bits)
+    assert (b.hist.cpu().numpy() == want).all()
+    if n <= 256:
+        assert (want == oracle.interval_abundance_naive(kind, b.coords.cpu().numpy())).all()
+
+
+@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("n", [4, 130, 1000, 3000])
+def test_chain_antichain_structures(cs, oracle, n, path):
+    chain = np.stack([np.arange(n), np.arange(n)]).astype(np.int32)
+    anti = np.stack([np.arange(n), np.arange(n)[::-1]]).astype(np.int32)
+    hc = _run(cs, 0, n, 0, coords=chain, path=path).hist.cpu().numpy()
+    ha = _run(cs, 0, n, 0, coords=anti, path=path).hist.cpu().numpy()
+    assert hc.tolist() == [n - 1 - k for k in range(n - 1)]
+    assert not ha.any()
+    t = (np.arange(n) * 3).astype(np.int32)
+    z = np.zeros(n, np.int32)
+    h4 = _run(cs, 2, n, 0, coords=np.stack([t, z, z, z]), path=path).hist.cpu().numpy()
+    assert h4.tolist() == hc.tolist()
+
+
+@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+def test_full_chain_131072_counts_exact(cs, path):
+    # Every pair related: |A_ij| = j - i - 1 reaches N - 2 = 131070, the
+    # largest count the N = 131072 workload can produce (exactness of the
+    # tensor-core FP32 accumulation at the top of its range).
+    n = 131072
+    chain = np.stack([np.arange(n), np.arange(n)]).astype(np.int32)
+    h = _run(cs, 0, n, 0, coords=chain, path=path).hist.cpu().numpy()
+    assert (h == np.arange(n - 1, 0, -1)).all()
+
+
+@pytest.mark.parametrize("kind,n", [(0, 1024), (2, 3000), (1, 2500)])
+def test_action_device_and_host(cs, oracle, kind, n):
+    import torch
+    seed = 77 + n
+    b = _run(cs, kind, n, seed)
+    h = b.hist.cpu().numpy()
+    d = cs.dim(kind)
+    cs.action_device(d, n, b.hist, list(EPS), b.actions, b.bracket, b.workspace)
+    torch.cuda.synchronize()
+    acts = b.actions.cpu().numpy()
+    for e, eps in enumerate(EPS):
+        s_or, br_or = oracle.action(d, n, h, eps)
+        assert abs(acts[e] - s_or) <= TOL * max(1.0, abs(s_or)), (eps, acts[e], s_or)
+        s_h, br_h = cs.action(d, n, h, eps)
+        assert abs(s_h - s_or) <= TOL * max(1.0, abs(s_or))
+        assert br_h == br_or
+    assert int(b.bracket.item()) == oracle.action(d, n, h, 0.0)[1]
+
+
+@pytest.mark.parametrize("kind,n", [(0, 1024), (2, 700)])
+def test_evaluate_host_buffers(cs, oracle, kind, n):
+    seed = 4242
+    coords = oracle.sprinkle(kind, n, seed)
+    want = oracle.interval_abundance(oracle.causal_matrix(kind, coords))
+    d = cs.dim(kind)
+    h1, a1, br1 = cs.evaluate(kind, n, seed, None, 1, EPS)          # sprinkled on the device
+    h2, a2, br2 = cs.evaluate(kind, n, 0, coords, 1, EPS)           # coordinates from the host
+    assert (h1 == want).all() and (h2 == want).all() and br1 == br2
+    for e, eps in enumerate(EPS):
+        s_or, _ = oracle.action(d, n, want, eps)
+        assert abs(a1[e] - s_or) <= TOL * max(1.0, abs(s_or))
+        assert a1[e] == a2[e]
+
+
+def test_invalid_arguments_rejected(cs):
+    import torch
+    b = cs.allocate(0, 100)
+    L = cs.lib()
+    st = torch.cuda.current_stream().cuda_stream
+    ws = b.workspace
+    assert L.cs_interval_abundance(0, b.bits.data_ptr(), b.rw, b.hist.data_ptr(), 1, ws.data_ptr(), ws.numel(), st) == -1
+    assert L.cs_interval_abundance(100, b.bits.data_ptr(), 8, b.hist.data_ptr(), 1, ws.data_ptr(), ws.numel(), st) == -1
+    assert L.cs_interval_abundance(100, b.bits.data_ptr(), b.rw, b.hist.data_ptr(), 1, ws.data_ptr(), 16, st) == -2
+    assert L.cs_sprinkle(9, 100, 1, b.coords.data_ptr(), ws.data_ptr(), ws.numel(), st) == -1
+    assert L.cs_causal_matrix(0, 100, b.coords.data_ptr(), None, b.rw, st) == -1
+
+
+# ------------------------------------------------- full-size workloads
+
+def test_full_2d_order_1024_exact(cs, oracle):
+    n, seed = 1024, 0xC5E70001
+    b = _run(cs, 0, n, seed)
+    c = oracle.sprinkle(0, n, seed)
+    assert (b.coords.cpu().numpy() == c).all()
+    h = b.hist.cpu().numpy()
+    assert (h == oracle.interval_abundance_naive(0, c)).all()
+    assert (h == oracle.interval_abundance_dominance2d(c[1])).all()
+
+
+@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+def test_full_4d_diamond_16384_exact(cs, oracle, path):
+    n, seed = 16384, 0xC5E70002
+    b = _run(cs, 2, n, seed, path=path)
+    c = oracle.sprinkle(2, n, seed)
+    assert (b.coords.cpu().numpy() == c).all()
+    bits = oracle.causal_matrix(2, c)
+    assert (_np_bits(b) == bits).all()
+    assert (b.hist.cpu().numpy() == oracle.interval_abundance(bits)).all()
+
+
+def _past_counts(v):
+    """past[m] = #{i < m : v_i < v_m} by a Fenwick tree over v."""
+    n = v.size
+    fen = np.zeros(n + 1, dtype=np.int64)
+    past = np.zeros(n, dtype=np.int64)
+    for m in range(n):
+        p, s = int(v[m]), 0
+        while p > 0:
+            s += fen[p]
+            p -= p & -p
+        past[m] = s
+        p = int(v[m]) + 1
+        while p <= n:
+            fen[p] += 1
+            p += p & -p
+    return past
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_2d_full(n, seed):
+    """Oracle sprinkle, bitset-free N_k, links and chain counts of a 2D order (cached)."""
+    import oracle as o
+    c = o.sprinkle(0, n, seed)
+    v = c[1].astype(np.int64)
+    past = _past_counts(v)
+    future = (n - 1 - v) - (np.arange(n) - past)
+    return c, o.interval_abundance_dominance2d(c[1]), o.links_2d(c[1]), int(past.sum()), int((past * future).sum())
+
+
+@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+def test_full_2d_order_131072(cs, oracle, path):
+    # Full size, bench launch configuration: every N_k against the bitset-free
+    # dominance count; also sum_k N_k = R, N_0 = links, and the first moment
+    # sum_k k N_k = sum_m |past(m)| |future(m)| (chains of three through m).
+    n, seed = 131072, 0xC5E70003
+    b = _run(cs, 0, n, seed, path=path)
+    c, h_dom, links, r, chains3 = _oracle_2d_full(n, seed)
+    assert (b.coords.cpu().numpy() == c).all()
+    h = b.hist.cpu().numpy()
+    assert int(h.sum()) == r
+    assert int((np.arange(h.size) * h).sum()) == chains3
+    assert int(h[0]) == links
+    # the GPU bitset on sampled rows, from the definition (v_i < v_j for i < j)
+    v = c[1].astype(np.int64)
+    bits = _np_bits(b)
+    idx = np.arange(n)
+    for i in range(0, n, 997):
+        rel = ((v > v[i]) & (idx > i)) | ((v < v[i]) & (idx < i))
+        want = np.zeros(b.rw, dtype=np.uint64)
+        packed = np.packbits(rel.astype(np.uint8), bitorder="little")
+        want[:packed.size // 8] = packed.view(np.uint64)
+        assert (bits[i] == want).all(), i
+    assert (h == h_dom).all()
