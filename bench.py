@@ -117,6 +117,44 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def roofline_for(resolved, n, count_s, peaks, src, sm_count):
+    """Achieved vs peak for the count call (algorithmic work: every pair i<j over the
+    columns strictly between them, C(n,3) bit-AND/popcount terms = MACs)."""
+    terms = n * (n - 1) * (n - 2) / 6.0
+    if resolved == 2:
+        # FP8 dense peak = measured bf16 sustained peak x nominal FP8/BF16 ratio (4.5/2.25)
+        peak = 2.0 * peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        achieved = 2.0 * terms / count_s / 1e12
+        return {"bound": "tensor", "kernel": "k_count_mma (+ k_expand_f8)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "algorithmic_macs": terms,
+                "peak_source": f"2 x bf16_tflops_sustained ({src}); FP8 kind::f8f6f4, 2 FLOP per MAC"}
+    peak = sm_count * POPC_PER_SM_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T popc32/s
+    achieved = terms / 32.0 / count_s / 1e12
+    return {"bound": "alu", "kernel": "k_count_popc", "achieved": achieved, "peak": peak, "unit": "T popc32/s",
+            "frac": achieved / peak, "traffic": None, "algorithmic_bit_ands": terms,
+            "peak_source": f"{sm_count} SMs x {POPC_PER_SM_PER_CLK} POPC/clk x {peaks.get('sm_max_mhz')} MHz "
+                           f"(sm_max_mhz, {src})"}
+
+
+def compare_paths(cs, torch, buf, n, stream):
+    """Count-call time of each path on the same bitset (1 warm-up + 1 timed, CUDA events)."""
+    out = {}
+    for name, p in (("popc", 1), ("mma", 2)):
+        ws = torch.empty(cs.interval_abundance_workspace(n, p), dtype=torch.uint8, device="cuda")
+        hist = torch.empty_like(buf.hist)
+        cs.interval_abundance(n, buf.bits, hist, p, ws, stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        cs.interval_abundance(n, buf.bits, hist, p, ws, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if not torch.equal(hist, buf.hist):
+            raise RuntimeError(f"path {name} disagrees with the timed path")
+        out[name] = a.elapsed_time(b)
+        del ws
+    return out
+
+
 def launches_per_step(kind, path):
     """Kernels of this library launched by one step (sprinkle, relate, count, actions)."""
     sprinkle = 1 + (2 if kind == 0 else 1) * 4 + 1
@@ -194,6 +232,8 @@ def main():
     ap.add_argument("--path", default="auto", choices=sorted(PATHS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--compare-paths", action="store_true",
+                    help="also time the other count path once on the same bitset")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -271,20 +311,21 @@ def main():
     cp = coords_pinned.numpy()
     hist_pinned = torch.empty(cs.hist_len(n), dtype=torch.int64, pin_memory=True).numpy()
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
-    cs.evaluate(kind, n, 0, cp, path, EPS, stream=stream, hist_out=hist_pinned)  # warm the allocator
+    h2, _, _ = cs.evaluate(kind, n, 0, cp, path, EPS, stream=stream, hist_out=hist_pinned)  # warm the pool
+    if int(h2.sum()) != pairs:
+        raise RuntimeError("host-buffer evaluation disagrees with the device pass")
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         h2, _, _ = cs.evaluate(kind, n, 0, cp, path, EPS, stream=stream, hist_out=hist_pinned)
-    e2e_s = time.perf_counter() - t0
-    assert int(h2.sum()) == pairs
+    e2e_s = max(time.perf_counter() - t0, 1e-9)
     if dist:
         te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e_s = float(te[0])
-    e2e_value = total_pairs * e2e_steps / e2e_s / 1e9
+    e2e_value = total_pairs * e2e_steps / e2e_s / 1e9 if e2e_steps > 0 else None
 
     if rank != 0:
         if dist:
@@ -293,30 +334,25 @@ def main():
 
     peaks, src = _peaks()
     clocks = clk.summary()
-    # roofline of the count kernel
-    cnt_s = statistics.mean(count_ms) / 1e3
-    algo_ands = n * (n - 1) * (n - 2) / 6.0  # bit-ANDs over every pair i<j, columns strictly between
-    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    popc_peak = sm_count * POPC_PER_SM_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T popc32/s
-    achieved = algo_ands / 32.0 / cnt_s / 1e12
-    roofline = {"bound": "alu", "kernel": "k_count_popc", "achieved": achieved, "peak": popc_peak,
-                "unit": "T popc32/s", "frac": achieved / popc_peak, "traffic": None,
-                "peak_source": f"{sm_count} SMs x {POPC_PER_SM_PER_CLK} POPC/clk x {peaks.get('sm_max_mhz')} MHz "
-                               f"(sm_max_mhz from MEASURED_PEAKS.json, {src})",
-                "count_ms": statistics.mean(count_ms), "algorithmic_bit_ands": algo_ands}
+    roofline = roofline_for(cs.resolved_path(n, path), n, statistics.mean(count_ms) / 1e3, peaks, src,
+                            torch.cuda.get_device_properties(local).multi_processor_count)
+    roofline["count_ms"] = statistics.mean(count_ms)
+    if args.compare_paths:
+        roofline["paths_ms"] = compare_paths(cs, torch, buf, n, stream)
     line = {
         "metric": f"interval-count Gpairs/s ({desc})", "value": value, "unit": "Gpairs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": args.workload, "kind": cs.KIND_NAMES[kind], "n": n, "seed": seed0,
-                   "path": args.path, "eps": list(EPS),
+                   "path": args.path, "resolved_path": {1: "popc", 2: "mma"}[cs.resolved_path(n, path)],
+                   "eps": list(EPS),
                    "l2": "inputs larger than L2" if cs.bitset_bytes(n) > 129e6 else "inputs smaller than L2",
                    "parallelism": f"replicas{args.gpus}"},
         "actions_per_s": args.steps * ws / (elapsed_ms / 1e3),
         "pairs_per_step": pairs, "actions": actions,
         "e2e": {"value": e2e_value, "unit": "Gpairs/s", "h2d_bytes_per_step": int(cp.nbytes),
                 "d2h_bytes_per_step": int(hist_pinned.nbytes + 8 * len(EPS) + 8), "steps": e2e_steps},
-        "gpu_launches": launches_per_step(kind, path) * args.steps,
+        "gpu_launches": launches_per_step(kind, cs.resolved_path(n, path)) * args.steps,
         "roofline": roofline,
         "clocks": clocks,
     }

@@ -123,7 +123,14 @@ int cs_causal_matrix(int kind, int64_t n, const int32_t *coords_dev,
 
 /* -------------------------------------------------- interval abundance */
 
-/* Device workspace needed by cs_interval_abundance for (n, path). */
+/* The path cs_interval_abundance runs for (n, path) on the current device:
+ * CS_PATH_POPC or CS_PATH_MMA (CS_PATH_AUTO picks the tensor-core path from
+ * n = 8192 up); -1 for invalid arguments. */
+int cs_resolved_path(int64_t n, int path);
+
+/* Device workspace needed by cs_interval_abundance for (n, path).  The
+ * tensor-core path keeps two n x ceil(n/128)*128-byte operand matrices in it
+ * (2 n^2 bytes, about 34 GB at n = 131072). */
 size_t cs_interval_abundance_workspace(int64_t n, int path);
 
 /*

@@ -19,7 +19,7 @@ import threading
 __all__ = [
     "KIND_2D_ORDER", "KIND_2D_DIAMOND", "KIND_4D_DIAMOND", "PATH_AUTO", "PATH_POPC", "PATH_MMA",
     "CsError", "lib", "dim", "coords_bytes", "row_words", "bitset_bytes", "hist_len",
-    "sprinkle_workspace_bytes", "interval_abundance_workspace", "action_workspace_bytes",
+    "sprinkle_workspace_bytes", "interval_abundance_workspace", "resolved_path", "action_workspace_bytes",
     "sprinkle", "causal_matrix", "interval_abundance", "workspace_status", "action", "action_device",
     "evaluate", "Buffers", "allocate", "run",
 ]
@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
             "cs_sprinkle": ([i32, i64, u64, vp, vp, sz, vp], i32),
             "cs_causal_matrix": ([i32, i64, vp, vp, i64, vp], i32),
             "cs_interval_abundance_workspace": ([i64, i32], sz),
+            "cs_resolved_path": ([i64, i32], i32),
             "cs_interval_abundance": ([i64, vp, i64, vp, i32, vp, sz, vp], i32),
             "cs_workspace_status": ([vp, vp], i32),
             "cs_action": ([i32, i64, vp, i64, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int64)], i32),
@@ -132,6 +133,11 @@ def sprinkle_workspace_bytes(kind: int, n: int) -> int:
 
 def interval_abundance_workspace(n: int, path: int = PATH_AUTO) -> int:
     return lib().cs_interval_abundance_workspace(n, path)
+
+
+def resolved_path(n: int, path: int = PATH_AUTO) -> int:
+    """PATH_POPC or PATH_MMA: the kernel cs_interval_abundance runs for (n, path)."""
+    return lib().cs_resolved_path(n, path)
 
 
 def action_workspace_bytes() -> int:

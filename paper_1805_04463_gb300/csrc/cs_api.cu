@@ -85,6 +85,11 @@ int cs_causal_matrix(int kind, int64_t n, const int32_t* coords_dev, uint64_t* b
     return from_cuda(launch_relate(kind, n, coords_dev, bits_dev, row_words, static_cast<cudaStream_t>(stream)));
 }
 
+int cs_resolved_path(int64_t n, int path) {
+    if (!valid_n(n) || path < CS_PATH_AUTO || path > CS_PATH_MMA) return -1;
+    return resolve_path(n, path);
+}
+
 size_t cs_interval_abundance_workspace(int64_t n, int path) {
     if (!valid_n(n) || path < CS_PATH_AUTO || path > CS_PATH_MMA) return 0;
     return resolve_path(n, path) == CS_PATH_MMA ? mma_workspace_bytes(n) : popc_workspace_bytes(n);
