@@ -212,6 +212,33 @@ int cs_evaluate(int kind, int64_t n, uint64_t seed, const int32_t *coords_host, 
                 const double *eps_host, int n_eps, int64_t *hist_host,
                 double *actions_host, int64_t *bracket_host, void *stream);
 
+/* ---------------------------------------------- allocation-free sprinkle */
+
+/* Largest n that cs_sprinkle_noalloc accepts. */
+#define CS_SPRINKLE_NOALLOC_MAX_N 262144
+
+/*
+ * cs_sprinkle for callers that cannot allocate device memory: code that runs
+ * while a stream is being captured into a CUDA graph (allocation is not
+ * allowed there), plugins that may only use memory their host application
+ * hands them, or real-time loops that must stay off the allocator.  The
+ * thesis has no counterpart; this is a convenience of this library.
+ * Writes exactly what cs_sprinkle writes for the same (kind, n, seed) to
+ * coords_dev and takes no workspace: its scratch is one file-scope device
+ * array of 12 MiB that every GPU loading the library holds until the process
+ * exits.  The call allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library routine).  The first call on a device looks up the array's device
+ * address, so make that first call before any stream capture starts.
+ * All calls on a device share the array and it keeps the last call's
+ * contents; calls whose work overlaps on the GPU (unordered streams) race
+ * and may corrupt each other's output.  A 4D element that exhausts its
+ * rejection attempts (probability below 1e-900) is not reported here.
+ * Errors: CS_EINVAL (bad kind, NULL or unaligned coords, n < 1 or
+ * n > CS_SPRINKLE_NOALLOC_MAX_N), CS_ECUDA; CS_ENOMEM only if the array
+ * were smaller than the scratch layout needs (a build inconsistency).
+ */
+int cs_sprinkle_noalloc(int kind, int64_t n, uint64_t seed, int32_t *coords_dev, void *stream);
+
 /* ------------------------------------------------------------------ misc */
 
 /* Static description of a status code. */

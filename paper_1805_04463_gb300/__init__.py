@@ -20,7 +20,7 @@ __all__ = [
     "KIND_2D_ORDER", "KIND_2D_DIAMOND", "KIND_4D_DIAMOND", "PATH_AUTO", "PATH_POPC", "PATH_MMA",
     "CsError", "lib", "dim", "coords_bytes", "row_words", "bitset_bytes", "hist_len",
     "sprinkle_workspace_bytes", "interval_abundance_workspace", "resolved_path", "action_workspace_bytes",
-    "sprinkle", "causal_matrix", "interval_abundance", "workspace_status", "action", "action_device",
+    "sprinkle", "sprinkle_noalloc", "causal_matrix", "interval_abundance", "workspace_status", "action", "action_device",
     "evaluate", "Buffers", "allocate", "run",
 ]
 
@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
             "cs_action_workspace_bytes": ([], sz),
             "cs_action_device": ([i32, i64, vp, i64, vp, i32, vp, vp, vp, sz, vp], i32),
             "cs_evaluate": ([i32, i64, u64, vp, i32, vp, i32, vp, vp, vp, vp], i32),
+            "cs_sprinkle_noalloc": ([i32, i64, u64, vp, vp], i32),
             "cs_strerror": ([i32], ctypes.c_char_p),
             "cs_version": ([], ctypes.c_char_p),
         }
@@ -150,6 +151,11 @@ def sprinkle(kind, n, seed, coords, workspace, stream=None):
     """cs_sprinkle: time-sorted int32 coordinates (dim, n) into `coords`."""
     _check(lib().cs_sprinkle(kind, n, seed, _ptr(coords), _ptr(workspace), _nbytes(workspace), _stream(stream)),
            "cs_sprinkle")
+
+
+def sprinkle_noalloc(kind, n, seed, coords, stream=None):
+    """cs_sprinkle_noalloc: as sprinkle(), with no workspace and no allocation (n <= 262144)."""
+    _check(lib().cs_sprinkle_noalloc(kind, n, seed, _ptr(coords), _stream(stream)), "cs_sprinkle_noalloc")
 
 
 def causal_matrix(kind, n, coords, bits, stream=None):
