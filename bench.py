@@ -155,6 +155,71 @@ def compare_paths(cs, torch, buf, n, stream):
     return out
 
 
+def ensemble_bench(cs, torch, path, steps=5, warmup=3):
+    """Batched ensemble (one CUDA-graph replay of cs_batch_launch per step) vs the
+    same 768 sets as one-at-a-time plain launches, on this GPU."""
+    from paper_1805_04463_gb300 import workloads
+    sets = workloads.ensemble()
+    stream = torch.cuda.Stream()
+    b = cs.Batch(sets, path=path, n_eps=len(EPS))
+    with torch.cuda.stream(stream):
+        b.launch(EPS, stream=stream)
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            b.launch(EPS, stream=stream)
+        for _ in range(warmup):
+            g.replay()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            g.replay()
+        e.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = a.elapsed_time(e) / steps
+    if b.status() != 0:
+        raise cs.CsError(b.status(), "ensemble")
+    pairs = int(b.hist.sum().item())
+    # one-at-a-time: the same sets through the single-set entry points
+    bufs = [cs.allocate(k, n, path=b.path) for k, n, _ in sets]
+    def plain():
+        for (k, n, sd), buf in zip(sets, bufs):
+            cs.run(buf, sd, eps=EPS, stream=stream)
+    with torch.cuda.stream(stream):
+        plain()
+        stream.synchronize()
+        a2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a2.record(stream)
+        plain()
+        e2.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = a2.elapsed_time(e2)
+    same = all(torch.equal(buf.hist, b.set_hist(s)) for s, buf in enumerate(bufs))
+    terms = sum(n * (n - 1) * (n - 2) / 6.0 for _, n, _ in sets)
+    return {"workload": "512 2D diamonds N~Poisson(4096) + 256 4D diamonds N~Poisson(2048)",
+            "sets": len(sets), "pairs": pairs, "path": {1: "popc", 2: "mma"}[b.path],
+            "batched_graph_ms": batched_ms, "plain_ms": plain_ms,
+            "batched_gpairs_s": pairs / batched_ms / 1e6, "plain_gpairs_s": pairs / plain_ms / 1e6,
+            "batched_actions_s": len(sets) / batched_ms * 1e3, "plain_actions_s": len(sets) / plain_ms * 1e3,
+            "speedup": plain_ms / batched_ms, "identical_results": bool(same),
+            "algorithmic_macs": terms, "achieved_tflops_whole_step": 2 * terms / batched_ms / 1e9}
+
+
+def serving_bench(path, rate=200.0, duration_s=5.0):
+    """The continuous-batching server on a Poisson trace (real time): throughput
+    and latency percentiles under a 60 GB bitset budget."""
+    from paper_1805_04463_gb300 import serve, workloads
+    srv = serve.Server(path=path)
+    srv.run(workloads.serving_requests(rate=rate, duration_s=0.1, seed=workloads.SEED_BASE + 55))  # warm-up
+    reqs = workloads.serving_requests(rate=rate, duration_s=duration_s)
+    stats, _ = srv.run(reqs)
+    offered = sum(n * (n - 1) * (n - 2) / 6.0 for _, _, n, _ in reqs) / duration_s
+    stats.update({"workload": f"Poisson arrivals {rate:g}/s for {duration_s:g} s, N = floor(2^U[10,16]), "
+                              "50/50 2D order / 4D diamond, 60 GB bitset budget",
+                  "offered_requests": len(reqs), "offered_macs_per_s": offered})
+    return stats
+
+
 def launches_per_step(kind, path):
     """Kernels of this library launched by one step (sprinkle, relate, count, actions)."""
     sprinkle = 1 + (2 if kind == 0 else 1) * 4 + 1
@@ -234,6 +299,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--compare-paths", action="store_true",
                     help="also time the other count path once on the same bitset")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -243,6 +310,7 @@ def main():
 
     import paper_1805_04463_gb300 as cs
     from paper_1805_04463_gb300 import build as csbuild
+    from paper_1805_04463_gb300 import replicas
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -294,15 +362,7 @@ def main():
     hist = buf.hist.cpu().numpy()
     pairs = int(hist.sum())
     actions = buf.actions.cpu().numpy()[:len(EPS)].tolist()
-    t = torch.tensor([elapsed_ms, float(pairs)], dtype=torch.float64, device="cuda")
-    if dist:
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        elapsed_ms, total_pairs = float(tmax[0]), float(tsum[1])
-    else:
-        total_pairs = float(pairs)
+    elapsed_ms, total_pairs = replicas.combine_timing(elapsed_ms, float(pairs), dist)
     value = total_pairs * args.steps / (elapsed_ms / 1e3) / 1e9
 
     # e2e through the host-buffer entry point: pinned coordinates in, histogram out
@@ -321,10 +381,7 @@ def main():
     for _ in range(e2e_steps):
         h2, _, _ = cs.evaluate(kind, n, 0, cp, path, EPS, stream=stream, hist_out=hist_pinned)
     e2e_s = max(time.perf_counter() - t0, 1e-9)
-    if dist:
-        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_s = float(te[0])
+    e2e_s, _ = replicas.combine_timing(e2e_s, 0.0, dist)
     e2e_value = total_pairs * e2e_steps / e2e_s / 1e9 if e2e_steps > 0 else None
 
     if rank != 0:
@@ -356,6 +413,10 @@ def main():
         "roofline": roofline,
         "clocks": clocks,
     }
+    if not args.no_ensemble:
+        line["ensemble"] = ensemble_bench(cs, torch, PATHS[args.path])
+    if not args.no_serve:
+        line["serving"] = serving_bench(PATHS[args.path])
     if not args.no_cpu_baseline:
         cb = cpu_baseline(kind, n, seed0)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

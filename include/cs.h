@@ -124,9 +124,23 @@ int cs_causal_matrix(int kind, int64_t n, const int32_t *coords_dev,
 /* -------------------------------------------------- interval abundance */
 
 /* The path cs_interval_abundance runs for (n, path) on the current device:
- * CS_PATH_POPC or CS_PATH_MMA (CS_PATH_AUTO picks the tensor-core path from
- * n = 8192 up); -1 for invalid arguments. */
+ * CS_PATH_POPC or CS_PATH_MMA (CS_PATH_AUTO follows the table below; the
+ * tensor-core path only where the device has tcgen05); -1 for invalid
+ * arguments. */
 int cs_resolved_path(int64_t n, int path);
+
+/*
+ * The CS_PATH_AUTO table, process-wide: entry e selects paths[e]
+ * (CS_PATH_POPC or CS_PATH_MMA) for n_min[e] <= n < n_min[e+1].  n_min must
+ * start at 0 and increase; at most 16 entries.  The default is {0: POPC,
+ * 8192: MMA}; the autotuner (paper_1805_04463_gb300/tune.py) installs
+ * measured thresholds.  Errors: CS_EINVAL.
+ */
+int cs_set_auto_paths(const int64_t *n_min, const int *paths, int count);
+
+/* Copy the AUTO table out; returns its entry count (nothing is copied when
+ * capacity is smaller than the count). */
+int cs_get_auto_paths(int64_t *n_min, int *paths, int capacity);
 
 /* Device workspace needed by cs_interval_abundance for (n, path).  The
  * tensor-core path keeps two n x ceil(n/128)*128-byte operand matrices in it
@@ -211,6 +225,116 @@ int cs_action_device(int dim, int64_t n, const int64_t *hist_dev, int64_t len,
 int cs_evaluate(int kind, int64_t n, uint64_t seed, const int32_t *coords_host, int path,
                 const double *eps_host, int n_eps, int64_t *hist_host,
                 double *actions_host, int64_t *bracket_host, void *stream);
+
+/* ----------------------------------------------------- batched ensembles */
+
+/* One causal set of a batch. */
+typedef struct {
+    int32_t kind;      /* CS_2D_ORDER, CS_2D_DIAMOND or CS_4D_DIAMOND */
+    int32_t reserved;  /* must be 0 */
+    int64_t n;         /* 1 .. CS_BATCH_MAX_N */
+    uint64_t seed;     /* the set equals cs_sprinkle(kind, n, seed, ...) */
+} cs_set_desc;
+
+#define CS_BATCH_MAX_N 8192
+#define CS_BATCH_MAX_SETS 1048576
+
+/* Opaque host-side plan of a batch (its device tables live in the workspace). */
+typedef struct cs_batch cs_batch;
+
+/* Device workspace for a batch of n_sets sets on `path` (0 for invalid input). */
+size_t cs_batch_workspace_bytes(const cs_set_desc *sets, int n_sets, int path);
+
+/* Entries of the batch histogram: sum over sets of cs_hist_len(n); set s
+ * starts at the sum over the earlier sets.  -1 for invalid input. */
+int64_t cs_batch_hist_len(const cs_set_desc *sets, int n_sets);
+
+/*
+ * Plan a batched ensemble: many sets of different kinds and sizes evaluated
+ * by one fixed sequence of launches (the thesis's experiments average ensembles
+ * of sprinklings, Section "Simulations and Scaling Evaluations"; a sprinkled N
+ * is Poisson distributed, Appendix "Causal Set Sprinklings").  Lays out every
+ * set's coordinates, bitset and count operands in workspace_dev (1024-byte
+ * aligned, cs_batch_workspace_bytes bytes, owned by the caller and used by the
+ * plan until cs_batch_destroy) and uploads the plan's device tables
+ * synchronously on `stream`.  *out receives a host handle.
+ * Errors: CS_EINVAL (bad sets, path, pointers, alignment), CS_ENOMEM
+ * (workspace too small or host allocation failed), CS_EUNSUPPORTED,
+ * CS_ECUDA.
+ */
+int cs_batch_create(const cs_set_desc *sets, int n_sets, int path, void *workspace_dev,
+                    size_t workspace_bytes, cs_batch **out, void *stream);
+
+/*
+ * Evaluate every set of the plan: sprinkle, causal matrix, interval
+ * abundances and actions, for all sets at once (one persistent count kernel
+ * over the tiles of all sets, largest sets first).  Enqueues memsets and
+ * kernels only, so the call can be captured into a CUDA graph and replayed.
+ * hist_dev: cs_batch_hist_len int64 (zeroed by the callee); actions_dev:
+ * n_sets x n_eps doubles, set-major (may be NULL when n_eps = 0);
+ * brackets_dev: n_sets int64 (may be NULL).  Results equal the single-set
+ * entry points' for the same (kind, n, seed).  In-kernel errors go to the
+ * workspace status word (cs_workspace_status).
+ * Errors: CS_EINVAL, CS_ECUDA.
+ */
+int cs_batch_launch(const cs_batch *b, const double *eps_host, int n_eps, int64_t *hist_dev,
+                    double *actions_dev, int64_t *brackets_dev, void *stream);
+
+/* The count path a plan runs (CS_PATH_POPC or CS_PATH_MMA), -1 for NULL. */
+int cs_batch_path(const cs_batch *b);
+
+/* Free the host handle (the workspace stays the caller's). */
+void cs_batch_destroy(cs_batch *b);
+
+/* ------------------------------------------- counting slices of many sets */
+
+/* Number of work items a set of size n splits into on `path` (tiles of its
+ * interval count); -1 for invalid input. */
+int64_t cs_count_items(int64_t n, int path);
+
+/* Bytes of the tensor-core operands of a set of size n (two n x
+ * ceil(n/128)*128-byte matrices, 1024-byte aligned). */
+size_t cs_operands_bytes(int64_t n);
+
+/*
+ * Expand a set's bitset into its tensor-core operands (0/1 FP8: U holds each
+ * row's future, L its past), once, for later cs_count_jobs slices on
+ * CS_PATH_MMA.  operands_dev: cs_operands_bytes(n), 1024-byte aligned.
+ * Asynchronous.  Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA.
+ */
+int cs_prepare_operands(int64_t n, const uint64_t *bits_dev, int64_t row_words, void *operands_dev,
+                        size_t operands_bytes, void *stream);
+
+/* One slice of one set's interval count. */
+typedef struct {
+    const uint64_t *bits;  /* the set's bitset (cs_causal_matrix) */
+    int64_t n;
+    int64_t row_words;
+    int64_t *hist;         /* the set's histogram: counts are ADDED (zero it before the first slice) */
+    void *operands;        /* CS_PATH_MMA: from cs_prepare_operands; ignored on CS_PATH_POPC */
+    int64_t item_begin;    /* slice [item_begin, item_end) of 0 .. cs_count_items(n, path) */
+    int64_t item_end;
+} cs_count_job;
+
+/* Host staging bytes (table_host) and device workspace bytes of cs_count_jobs. */
+size_t cs_count_jobs_table_bytes(int n_jobs, int path);
+size_t cs_count_jobs_workspace_bytes(int n_jobs, int path);
+
+/*
+ * Count slices of several sets in one persistent launch (Algorithm
+ * "Optimized Interval Abundance Measurement": the pairs of a set are
+ * independent, so any partition of its work items can run in any order and
+ * share a launch with other sets' items).  The job table is encoded into
+ * table_host (cs_count_jobs_table_bytes, 128-byte aligned, preferably pinned;
+ * the caller keeps it unchanged until the stream has passed this call) and
+ * copied to the workspace.  Each job's counts are added to its histogram with
+ * integer atomics, so a set's final histogram equals cs_interval_abundance's
+ * however its items are sliced.  Asynchronous.
+ * Errors: CS_EINVAL (bad jobs, slices, pointers, alignment), CS_ENOMEM,
+ * CS_EUNSUPPORTED, CS_ECUDA.
+ */
+int cs_count_jobs(const cs_count_job *jobs, int n_jobs, int path, void *table_host, void *workspace_dev,
+                  size_t workspace_bytes, void *stream);
 
 /* ---------------------------------------------- allocation-free sprinkle */
 

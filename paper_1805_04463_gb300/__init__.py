@@ -20,8 +20,10 @@ __all__ = [
     "KIND_2D_ORDER", "KIND_2D_DIAMOND", "KIND_4D_DIAMOND", "PATH_AUTO", "PATH_POPC", "PATH_MMA",
     "CsError", "lib", "dim", "coords_bytes", "row_words", "bitset_bytes", "hist_len",
     "sprinkle_workspace_bytes", "interval_abundance_workspace", "resolved_path", "action_workspace_bytes",
+    "set_auto_paths", "get_auto_paths",
     "sprinkle", "sprinkle_noalloc", "causal_matrix", "interval_abundance", "workspace_status", "action", "action_device",
-    "evaluate", "Buffers", "allocate", "run",
+    "evaluate", "Buffers", "allocate", "run", "SetDesc", "Batch", "CountJob", "count_items",
+    "operands_bytes", "prepare_operands", "count_jobs",
 ]
 
 KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND = 0, 1, 2
@@ -68,6 +70,8 @@ def lib() -> ctypes.CDLL:
             "cs_causal_matrix": ([i32, i64, vp, vp, i64, vp], i32),
             "cs_interval_abundance_workspace": ([i64, i32], sz),
             "cs_resolved_path": ([i64, i32], i32),
+            "cs_set_auto_paths": ([vp, vp, i32], i32),
+            "cs_get_auto_paths": ([vp, vp, i32], i32),
             "cs_interval_abundance": ([i64, vp, i64, vp, i32, vp, sz, vp], i32),
             "cs_workspace_status": ([vp, vp], i32),
             "cs_action": ([i32, i64, vp, i64, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int64)], i32),
@@ -75,6 +79,18 @@ def lib() -> ctypes.CDLL:
             "cs_action_device": ([i32, i64, vp, i64, vp, i32, vp, vp, vp, sz, vp], i32),
             "cs_evaluate": ([i32, i64, u64, vp, i32, vp, i32, vp, vp, vp, vp], i32),
             "cs_sprinkle_noalloc": ([i32, i64, u64, vp, vp], i32),
+            "cs_batch_workspace_bytes": ([vp, i32, i32], sz),
+            "cs_batch_hist_len": ([vp, i32], i64),
+            "cs_batch_create": ([vp, i32, i32, vp, sz, ctypes.POINTER(ctypes.c_void_p), vp], i32),
+            "cs_batch_launch": ([vp, vp, i32, vp, vp, vp, vp], i32),
+            "cs_batch_path": ([vp], i32),
+            "cs_batch_destroy": ([vp], None),
+            "cs_count_items": ([i64, i32], i64),
+            "cs_operands_bytes": ([i64], sz),
+            "cs_prepare_operands": ([i64, vp, i64, vp, sz, vp], i32),
+            "cs_count_jobs_table_bytes": ([i32, i32], sz),
+            "cs_count_jobs_workspace_bytes": ([i32, i32], sz),
+            "cs_count_jobs": ([vp, i32, i32, vp, vp, sz, vp], i32),
             "cs_strerror": ([i32], ctypes.c_char_p),
             "cs_version": ([], ctypes.c_char_p),
         }
@@ -139,6 +155,21 @@ def interval_abundance_workspace(n: int, path: int = PATH_AUTO) -> int:
 def resolved_path(n: int, path: int = PATH_AUTO) -> int:
     """PATH_POPC or PATH_MMA: the kernel cs_interval_abundance runs for (n, path)."""
     return lib().cs_resolved_path(n, path)
+
+
+def set_auto_paths(table):
+    """Install the CS_PATH_AUTO table: sequence of (n_min, path), n_min from 0 upward."""
+    n = (ctypes.c_int64 * len(table))(*[int(a) for a, _ in table])
+    p = (ctypes.c_int * len(table))(*[int(b) for _, b in table])
+    _check(lib().cs_set_auto_paths(n, p, len(table)), "cs_set_auto_paths")
+
+
+def get_auto_paths():
+    cnt = lib().cs_get_auto_paths(None, None, 0)
+    n = (ctypes.c_int64 * cnt)()
+    p = (ctypes.c_int * cnt)()
+    lib().cs_get_auto_paths(n, p, cnt)
+    return [(int(n[i]), int(p[i])) for i in range(cnt)]
 
 
 def action_workspace_bytes() -> int:
@@ -247,3 +278,103 @@ def run(buf: Buffers, seed: int, eps=(0.0,), stream=None, sprinkle_=True):
     interval_abundance(buf.n, buf.bits, buf.hist, buf.path, buf.workspace, stream)
     if eps:
         action_device(buf.dim, buf.n, buf.hist, list(eps), buf.actions, buf.bracket, buf.workspace, stream)
+
+
+# ------------------------------------------------------- batched ensembles
+
+class SetDesc(ctypes.Structure):
+    """cs_set_desc: one causal set of a batch."""
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("seed", ctypes.c_uint64)]
+
+
+def _desc_array(sets):
+    return (SetDesc * len(sets))(*[SetDesc(int(k), 0, int(n), int(sd)) for k, n, sd in sets])
+
+
+class Batch:
+    """A planned batched ensemble (cs_batch_create / cs_batch_launch).
+
+    sets: sequence of (kind, n, seed).  The device workspace, the batch
+    histogram (set s at hist_offsets[s]), actions (n_sets x n_eps) and brackets
+    are torch tensors owned by this object.  launch() enqueues kernels and
+    memsets only, so it can be captured into a CUDA graph.
+    """
+
+    def __init__(self, sets, path=PATH_AUTO, n_eps=4, device="cuda", stream=None):
+        import torch
+        self.sets = [(int(k), int(n), int(sd)) for k, n, sd in sets]
+        L = lib()
+        arr = _desc_array(self.sets)
+        self._arr = arr
+        ws = L.cs_batch_workspace_bytes(arr, len(arr), path)
+        if ws == 0:
+            raise CsError(-1, "cs_batch_workspace_bytes")
+        self.workspace = torch.empty(ws + 1024, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        self.ws_ptr = (base + 1023) // 1024 * 1024
+        self.ws_bytes = ws
+        h = ctypes.c_void_p()
+        _check(L.cs_batch_create(arr, len(arr), path, self.ws_ptr, ws, ctypes.byref(h), _stream(stream)),
+               "cs_batch_create")
+        self._h = h
+        self.path = L.cs_batch_path(h)
+        lens = [hist_len(n) for _, n, _ in self.sets]
+        self.hist_offsets = [0]
+        for x in lens[:-1]:
+            self.hist_offsets.append(self.hist_offsets[-1] + x)
+        self.hist = torch.empty(sum(lens), dtype=torch.int64, device=device)
+        self.n_eps = n_eps
+        self.actions = torch.empty((len(self.sets), max(n_eps, 1)), dtype=torch.float64, device=device)
+        self.brackets = torch.empty(len(self.sets), dtype=torch.int64, device=device)
+
+    def launch(self, eps=(0.0, 0.05, 0.1, 0.2), stream=None):
+        if len(eps) != self.n_eps:
+            raise ValueError("eps must have n_eps entries")
+        arr = (ctypes.c_double * max(len(eps), 1))(*([float(e) for e in eps] or [0.0]))
+        _check(lib().cs_batch_launch(self._h, ctypes.cast(arr, ctypes.c_void_p), len(eps), self.hist.data_ptr(),
+                                     self.actions.data_ptr() if eps else None, self.brackets.data_ptr(),
+                                     _stream(stream)), "cs_batch_launch")
+
+    def set_hist(self, s):
+        n = self.sets[s][1]
+        return self.hist[self.hist_offsets[s]:self.hist_offsets[s] + hist_len(n)]
+
+    def status(self, stream=None) -> int:
+        return lib().cs_workspace_status(self.ws_ptr, _stream(stream))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.cs_batch_destroy(h)
+            self._h = None
+
+
+# ----------------------------------------------- counting slices of many sets
+
+class CountJob(ctypes.Structure):
+    """cs_count_job: one slice [item_begin, item_end) of one set's interval count."""
+    _fields_ = [("bits", ctypes.c_void_p), ("n", ctypes.c_int64), ("row_words", ctypes.c_int64),
+                ("hist", ctypes.c_void_p), ("operands", ctypes.c_void_p), ("item_begin", ctypes.c_int64),
+                ("item_end", ctypes.c_int64)]
+
+
+def count_items(n: int, path: int = PATH_AUTO) -> int:
+    return lib().cs_count_items(n, path)
+
+
+def operands_bytes(n: int) -> int:
+    return lib().cs_operands_bytes(n)
+
+
+def prepare_operands(n, bits, operands_ptr, operands_nbytes, stream=None):
+    """cs_prepare_operands: tensor-core operands of one set (operands_ptr 1024-byte aligned)."""
+    _check(lib().cs_prepare_operands(n, _ptr(bits), bits.shape[-1], operands_ptr, operands_nbytes,
+                                     _stream(stream)), "cs_prepare_operands")
+
+
+def count_jobs(jobs, path, table_host_ptr, workspace_ptr, workspace_nbytes, stream=None):
+    """cs_count_jobs over a sequence of CountJob (table_host_ptr: pinned, 128-byte aligned)."""
+    arr = (CountJob * len(jobs))(*jobs)
+    _check(lib().cs_count_jobs(arr, len(jobs), path, table_host_ptr, workspace_ptr, workspace_nbytes,
+                               _stream(stream)), "cs_count_jobs")

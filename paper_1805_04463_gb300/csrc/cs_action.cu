@@ -10,72 +10,12 @@
 // far below a 1e-12 relative error at the largest N.
 #include <cmath>
 
+#include "cs_action.cuh"
 #include "cs_kernels.cuh"
 
 namespace cs {
 
 namespace {
-
-constexpr int kMaxEps = 16;
-constexpr int kActThreads = 256;
-constexpr int kActBlocks = 128;
-
-struct EpsArgs {
-    double v[kMaxEps];
-    int n;
-};
-
-__host__ __device__ inline dd dd_div(dd a, dd b) {
-    const double q1 = a.hi / b.hi;
-    dd r = dd_sub(a, dd_mul_d(b, q1));
-    const double q2 = r.hi / b.hi;
-    r = dd_sub(r, dd_mul_d(b, q2));
-    const double q3 = r.hi / b.hi;
-    return dd_add(dd_quick_two_sum(q1, q2), dd_from(q3));
-}
-
-// One Newton step on the correctly rounded double root: x + (a - x^2) / (2x).
-__host__ __device__ inline dd dd_sqrt(dd a) {
-    if (a.hi <= 0.0) return dd_from(0.0);
-    const double x = sqrt(a.hi);
-    const dd r = dd_sub(a, dd_two_prod(x, x));
-    return dd_quick_two_sum(x, r.hi / (2.0 * x));
-}
-
-__host__ __device__ inline int64_t bracket_of(int dim, int64_t n, const int64_t* h4) {
-    return dim == 2 ? n - 2 * h4[0] + 4 * h4[1] - 2 * h4[2] : n - h4[0] + 9 * h4[1] - 16 * h4[2] + 8 * h4[3];
-}
-
-__host__ __device__ inline bool is_local(double eps) { return eps <= 0.0 || eps == 1.0; }
-
-// Local action: 2 * bracket (1+1) or 4/sqrt(6) * bracket (3+1).
-__host__ __device__ inline dd local_action(int dim, int64_t bracket) {
-    const dd b = dd_from_i64(bracket);
-    if (dim == 2) return dd_mul_d(b, 2.0);
-    return dd_mul(dd_div(dd_from(4.0), dd_sqrt(dd_from(6.0))), b);
-}
-
-// Smeared action from sum = sum_k N_k f(k, eps):
-//   1+1: 2 eps [N - 2 eps sum];  3+1: 4 sqrt(eps/6) [N - eps sum].
-__host__ __device__ inline dd smeared_action(int dim, int64_t n, double eps, dd sum) {
-    const dd e = dd_from(eps);
-    if (dim == 2) {
-        const dd inner = dd_sub(dd_from_i64(n), dd_mul(dd_mul_d(e, 2.0), sum));
-        return dd_mul(dd_mul_d(e, 2.0), inner);
-    }
-    const dd inner = dd_sub(dd_from_i64(n), dd_mul(e, sum));
-    const dd pref = dd_mul_d(dd_sqrt(dd_div(e, dd_from(6.0))), 4.0);
-    return dd_mul(pref, inner);
-}
-
-// Beyond this k, (1-eps)^k < 1e-330: every remaining term is below the
-// double-double resolution of any non-zero sum and is dropped.
-__host__ __device__ inline int64_t smear_cutoff(double eps, int64_t len) {
-    const double l = -log1p(-eps);
-    if (!(l > 0.0)) return len;
-    const double kc = 760.0 / l + 8.0;
-    return kc < double(len) ? int64_t(kc) : len;
-}
 
 __global__ void __launch_bounds__(kActThreads) k_action_partial(int dim, const int64_t* __restrict__ hist, int64_t len,
                                                                 EpsArgs eps, dd* __restrict__ partial) {

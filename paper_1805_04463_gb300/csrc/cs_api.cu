@@ -1,6 +1,7 @@
 // cs_api.cu -- the extern "C" entry points of include/cs.h: argument
 // validation, workspace bookkeeping and dispatch to the kernels.
 #include <cstring>
+#include <mutex>
 
 #include "cs_kernels.cuh"
 
@@ -23,13 +24,25 @@ inline cudaError_t clear_status(void* ws, cudaStream_t st) {
 
 }  // namespace
 
-// The tensor-core path pays a fixed O(n^2) operand expansion; below this size
-// the popcount tiles win.
-constexpr int64_t kAutoMmaMinN = 8192;
+// CS_PATH_AUTO table: entry e applies from size n_min[e] up to the next
+// entry.  The default reflects that the tensor-core path pays a fixed O(n^2)
+// operand expansion and wins from a few thousand elements up; an autotuner
+// replaces it with measured thresholds (cs_set_auto_paths).
+constexpr int kMaxAuto = 16;
+std::mutex g_auto_mu;
+int64_t g_auto_n[kMaxAuto] = {0, 8192};
+int g_auto_p[kMaxAuto] = {CS_PATH_POPC, CS_PATH_MMA};
+int g_auto_count = 2;
 
 int resolve_path(int64_t n, int path) {
     if (path != CS_PATH_AUTO) return path;
-    return (n >= kAutoMmaMinN && device_has_tcgen05()) ? CS_PATH_MMA : CS_PATH_POPC;
+    int p = CS_PATH_POPC;
+    {
+        std::lock_guard<std::mutex> lk(g_auto_mu);
+        for (int e = 0; e < g_auto_count; ++e)
+            if (n >= g_auto_n[e]) p = g_auto_p[e];
+    }
+    return (p == CS_PATH_MMA && !device_has_tcgen05()) ? CS_PATH_POPC : p;
 }
 
 }  // namespace cs
@@ -83,6 +96,31 @@ int cs_causal_matrix(int kind, int64_t n, const int32_t* coords_dev, uint64_t* b
         row_words < cs_row_words(n) || row_words % 16 != 0)
         return CS_EINVAL;
     return from_cuda(launch_relate(kind, n, coords_dev, bits_dev, row_words, static_cast<cudaStream_t>(stream)));
+}
+
+int cs_set_auto_paths(const int64_t* n_min, const int* paths, int count) {
+    if (!n_min || !paths || count < 1 || count > kMaxAuto || n_min[0] != 0) return CS_EINVAL;
+    for (int e = 0; e < count; ++e) {
+        if (paths[e] != CS_PATH_POPC && paths[e] != CS_PATH_MMA) return CS_EINVAL;
+        if (e > 0 && n_min[e] <= n_min[e - 1]) return CS_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_auto_mu);
+    for (int e = 0; e < count; ++e) {
+        g_auto_n[e] = n_min[e];
+        g_auto_p[e] = paths[e];
+    }
+    g_auto_count = count;
+    return CS_OK;
+}
+
+int cs_get_auto_paths(int64_t* n_min, int* paths, int capacity) {
+    std::lock_guard<std::mutex> lk(g_auto_mu);
+    if (!n_min || !paths || capacity < g_auto_count) return g_auto_count;
+    for (int e = 0; e < g_auto_count; ++e) {
+        n_min[e] = g_auto_n[e];
+        paths[e] = g_auto_p[e];
+    }
+    return g_auto_count;
 }
 
 int cs_resolved_path(int64_t n, int path) {

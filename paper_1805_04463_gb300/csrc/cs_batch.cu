@@ -1,0 +1,462 @@
+// cs_batch.cu -- batched ensembles: many causal sets of different kinds and
+// sizes evaluated by one fixed sequence of launches (memsets and kernels
+// only, so the sequence can be captured into a CUDA graph and replayed).
+//
+// Pipeline per launch, every kernel covering all sets at once:
+//   k_batch_keys    per element: random keys / raw coordinates (same draws as
+//                   cs_sprinkle, so every set equals its single-set result);
+//   k_batch_rank    one CTA per set: bitonic sort of (key, index) in shared
+//                   memory gives the exact time order; scatter coordinates;
+//   k_batch_relate  every (set, 64-row, 2048-column) block of every bitset;
+//   count           the multi-set POPC kernel, or expand + multi-set tcgen05
+//                   kernel: one persistent grid over the tiles of all sets,
+//                   largest sets first (longest-processing-time order);
+//   k_batch_action  one CTA per set: bracket and smeared sums.
+// Ensembles of Poisson-sized sprinklings are the thesis's experimental unit
+// (Section "Simulations and Scaling Evaluations": ten graphs per size; the
+// appendix's sprinklings draw N from a Poisson distribution).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "cs_action.cuh"
+#include "cs_kernels.cuh"
+#include "cs_relate.cuh"
+#include "cs_sprinkle.cuh"
+
+namespace cs {
+
+namespace {
+
+// Per set, device-resident.
+struct BatchSet {
+    int32_t kind, dim;
+    int64_t n;
+    uint64_t seed;
+    int32_t* coords;
+    uint64_t* bits;
+    int64_t row_words;
+    uint64_t* key0;
+    uint64_t* key1;
+    int32_t* raw;
+    int64_t elem_begin;    // first element of this set in the concatenated element range
+    int64_t rblock_begin;  // first relate block
+    int64_t col_groups;    // relate column groups per row block
+    int64_t hist_off;      // offset of this set's histogram in the batch histogram
+};
+
+constexpr int kRankThreads = 1024;
+
+__device__ __forceinline__ int find_set_elem(const BatchSet* sets, int nsets, int64_t idx) {
+    int lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sets[mid].elem_begin <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_batch_keys(const BatchSet* __restrict__ sets, int nsets, int64_t total,
+                                                    WsHeader* hdr) {
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const BatchSet& b = sets[find_set_elem(sets, nsets, idx)];
+        const int64_t e = idx - b.elem_begin;
+        if (b.kind == CS_2D_ORDER) {
+            draw_2d_order(stream_key(b.seed, kStreamOrderU), stream_key(b.seed, kStreamOrderV), e, b.key0[e],
+                          b.key1[e]);
+        } else if (b.kind == CS_2D_DIAMOND) {
+            b.key0[e] = draw_2d_diamond(stream_key(b.seed, kStreamDiamond2), e, b.raw[e], b.raw[b.n + e]);
+        } else {
+            int32_t c[4];
+            if (!draw_4d_diamond(stream_key(b.seed, kStreamDiamond4), e, c, b.key0[e])) set_status(hdr, CS_ERANGE);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) b.raw[k * b.n + e] = c[k];
+        }
+    }
+}
+
+// Bitonic sort of P (a power of two) (key, index) pairs in shared memory,
+// ascending by key then index.  All threads of the block take part.
+__device__ void bitonic_sort(uint64_t* key, uint32_t* idx, int P) {
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const bool up = (i & k) == 0;
+                    const bool greater = key[i] > key[p] || (key[i] == key[p] && idx[i] > idx[p]);
+                    if (greater == up) {
+                        const uint64_t tk = key[i];
+                        key[i] = key[p];
+                        key[p] = tk;
+                        const uint32_t ti = idx[i];
+                        idx[i] = idx[p];
+                        idx[p] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Load one key stream of a set (padding with keys that sort last) and sort it.
+__device__ void load_and_sort(const uint64_t* src, int64_t n, int P, uint64_t* key, uint32_t* idx) {
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        key[i] = i < n ? src[i] : ~0ull;
+        idx[i] = uint32_t(i);  // padding entries carry indices >= n, so they sort after real keys
+    }
+    __syncthreads();
+    bitonic_sort(key, idx, P);
+}
+
+// One CTA per set: exact rank of each element (ties by index), then the
+// time-sorted coordinates.
+__global__ void __launch_bounds__(kRankThreads) k_batch_rank(const BatchSet* __restrict__ sets) {
+    extern __shared__ uint8_t smem_raw[];
+    const BatchSet& b = sets[blockIdx.x];
+    const int64_t n = b.n;
+    int P = 1;
+    while (P < n) P <<= 1;
+    uint64_t* key = reinterpret_cast<uint64_t*>(smem_raw);
+    uint32_t* idx = reinterpret_cast<uint32_t*>(key + P);
+    uint32_t* ru = idx + P;
+    load_and_sort(b.key0, n, P, key, idx);
+    if (b.kind == CS_2D_ORDER) {
+        for (int p = threadIdx.x; p < n; p += blockDim.x) ru[idx[p]] = uint32_t(p);  // u rank of element idx[p]
+        __syncthreads();
+        load_and_sort(b.key1, n, P, key, idx);
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const uint32_t e = idx[p];  // element with v rank p
+            b.coords[ru[e]] = int32_t(ru[e]);
+            b.coords[n + ru[e]] = p;
+        }
+    } else {
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const uint32_t e = idx[p];
+            for (int c = 0; c < b.dim; ++c) b.coords[c * n + p] = b.raw[c * n + e];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRelThreads) k_batch_relate(const BatchSet* __restrict__ sets, int nsets,
+                                                              int64_t total_blocks) {
+    __shared__ int32_t sc[4][kRelColsPerBlock];
+    for (int64_t blk = blockIdx.x; blk < total_blocks; blk += gridDim.x) {
+        int lo = 0, hi = nsets - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sets[mid].rblock_begin <= blk) lo = mid; else hi = mid - 1;
+        }
+        const BatchSet& b = sets[lo];
+        const int64_t local = blk - b.rblock_begin;
+        const int64_t rb = local / b.col_groups, cg = local - rb * b.col_groups;
+        if (b.dim == 4)
+            relate_block<4>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
+        else
+            relate_block<2>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
+        __syncthreads();  // the next block restages sc
+    }
+}
+
+// One CTA per set: bracket, local and smeared actions.  Powers of (1-eps)
+// advance by a fixed stride per thread after a direct start.
+__global__ void __launch_bounds__(kActThreads) k_batch_action(const BatchSet* __restrict__ sets,
+                                                              const int64_t* __restrict__ hist_base, EpsArgs eps,
+                                                              double* __restrict__ actions,
+                                                              int64_t* __restrict__ brackets) {
+    __shared__ dd red[kActThreads];
+    const BatchSet& b = sets[blockIdx.x];
+    const int dim = b.dim;
+    const int64_t n = b.n, len = n > 1 ? n - 1 : 1;
+    const int64_t* hist = hist_base + b.hist_off;
+    const int tid = threadIdx.x;
+    int64_t h4[4] = {0, 0, 0, 0};
+    for (int k = 0; k < 4 && k < len; ++k) h4[k] = hist[k];
+    const int64_t br = bracket_of(dim, n, h4);
+    if (tid == 0 && brackets) brackets[blockIdx.x] = br;
+    for (int e = 0; e < eps.n; ++e) {
+        const double ep = eps.v[e];
+        if (is_local(ep)) {
+            if (tid == 0 && actions) {
+                const dd s = local_action(dim, br);
+                actions[blockIdx.x * eps.n + e] = s.hi + s.lo;
+            }
+            continue;
+        }
+        const dd q = dd_two_sum(1.0, -ep);
+        const dd step = dd_pow(q, kActThreads);
+        const int64_t kend = smear_cutoff(ep, len);
+        const int64_t deg = dim == 2 ? 2 : 3;
+        dd sum = dd_from(0.0), p = dd_from(1.0);
+        for (int64_t k = tid; k < kend; k += kActThreads) {
+            // q^(k-deg) for k >= deg; a direct power until the stride applies
+            p = (k - kActThreads < deg) ? dd_pow(q, smear_qexp(dim, k)) : dd_mul(p, step);
+            const int64_t hk = hist[k];
+            if (hk != 0) sum = dd_add(sum, dd_mul(dd_from_i64(hk), dd_mul(p, smear_poly(dim, k, q, ep))));
+        }
+        red[tid] = sum;
+        __syncthreads();
+        for (int s = kActThreads / 2; s > 0; s >>= 1) {
+            if (tid < s) red[tid] = dd_add(red[tid], red[tid + s]);
+            __syncthreads();
+        }
+        if (tid == 0 && actions) {
+            const dd s = smeared_action(dim, n, ep, red[0]);
+            actions[blockIdx.x * eps.n + e] = s.hi + s.lo;
+        }
+        __syncthreads();
+    }
+}
+
+bool g_rank_attr[64];
+
+}  // namespace
+
+}  // namespace cs
+
+using namespace cs;
+
+// Host-side plan of a batch (the device tables live in the workspace).
+struct cs_batch {
+    int nsets = 0;
+    int path = CS_PATH_POPC;
+    uint8_t* ws = nullptr;
+    WsHeader* hdr = nullptr;
+    BatchSet* sets_dev = nullptr;
+    PopcSetEntry* popc_dev = nullptr;
+    MmaSetEntry* mma_dev = nullptr;
+    int64_t total_elems = 0, total_rblocks = 0, total_items = 0, total_pieces = 0, total_hist = 0;
+    int max_pow2 = 1;
+};
+
+namespace {
+
+struct Layout {
+    size_t sets, entries, total;
+    std::vector<size_t> coords, bits, key0, key1, raw, U, L;
+};
+
+bool batch_valid(const cs_set_desc* sets, int n_sets) {
+    if (!sets || n_sets < 1 || n_sets > CS_BATCH_MAX_SETS) return false;
+    for (int s = 0; s < n_sets; ++s)
+        if (cs_dim(sets[s].kind) == 0 || sets[s].n < 1 || sets[s].n > CS_BATCH_MAX_N || sets[s].reserved != 0)
+            return false;
+    return true;
+}
+
+int batch_path(const cs_set_desc* sets, int n_sets, int path) {
+    if (path != CS_PATH_AUTO) return path;
+    return device_has_tcgen05() ? CS_PATH_MMA : CS_PATH_POPC;
+}
+
+Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
+    Layout L;
+    size_t off = sizeof(WsHeader);
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + bytes, 256);
+        return at;
+    };
+    L.sets = take(sizeof(BatchSet) * size_t(n_sets));
+    off = align_up(off, 128);
+    L.entries = take((path == CS_PATH_MMA ? sizeof(MmaSetEntry) : sizeof(PopcSetEntry)) * size_t(n_sets));
+    for (int s = 0; s < n_sets; ++s) {
+        const int64_t n = sets[s].n;
+        const int dim = cs_dim(sets[s].kind);
+        L.coords.push_back(take(size_t(n) * dim * 4));
+        L.bits.push_back(take(size_t(n) * size_t(cs_row_words(n)) * 8));
+        L.key0.push_back(take(size_t(n) * 8));
+        L.key1.push_back(take(size_t(n) * 8));
+        L.raw.push_back(take(size_t(n) * 16));
+        if (path == CS_PATH_MMA) {
+            off = align_up(off, 1024);
+            L.U.push_back(take(size_t(n) * size_t(mma_kpad(n))));
+            off = align_up(off, 1024);
+            L.L.push_back(take(size_t(n) * size_t(mma_kpad(n))));
+        }
+    }
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t cs_batch_workspace_bytes(const cs_set_desc* sets, int n_sets, int path) {
+    if (!batch_valid(sets, n_sets) || path < CS_PATH_AUTO || path > CS_PATH_MMA) return 0;
+    return batch_layout(sets, n_sets, batch_path(sets, n_sets, path)).total;
+}
+
+int64_t cs_batch_hist_len(const cs_set_desc* sets, int n_sets) {
+    if (!batch_valid(sets, n_sets)) return -1;
+    int64_t t = 0;
+    for (int s = 0; s < n_sets; ++s) t += cs_hist_len(sets[s].n);
+    return t;
+}
+
+int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspace_dev, size_t workspace_bytes,
+                    cs_batch** out, void* stream) {
+    if (!out) return CS_EINVAL;
+    *out = nullptr;
+    if (!batch_valid(sets, n_sets) || path < CS_PATH_AUTO || path > CS_PATH_MMA || !workspace_dev ||
+        (reinterpret_cast<uintptr_t>(workspace_dev) % 1024) != 0)
+        return CS_EINVAL;
+    const int p = batch_path(sets, n_sets, path);
+    if (p == CS_PATH_MMA && !device_has_tcgen05()) return CS_EUNSUPPORTED;
+    const Layout L = batch_layout(sets, n_sets, p);
+    if (workspace_bytes < L.total) return CS_ENOMEM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint8_t* ws = static_cast<uint8_t*>(workspace_dev);
+
+    std::vector<BatchSet> bs(static_cast<size_t>(n_sets));
+    int64_t elem = 0, rblk = 0, hoff = 0;
+    int max_pow2 = 1;
+    for (int s = 0; s < n_sets; ++s) {
+        BatchSet& b = bs[s];
+        b.kind = sets[s].kind;
+        b.dim = cs_dim(b.kind);
+        b.n = sets[s].n;
+        b.seed = sets[s].seed;
+        b.coords = reinterpret_cast<int32_t*>(ws + L.coords[s]);
+        b.bits = reinterpret_cast<uint64_t*>(ws + L.bits[s]);
+        b.row_words = cs_row_words(b.n);
+        b.key0 = reinterpret_cast<uint64_t*>(ws + L.key0[s]);
+        b.key1 = reinterpret_cast<uint64_t*>(ws + L.key1[s]);
+        b.raw = reinterpret_cast<int32_t*>(ws + L.raw[s]);
+        b.elem_begin = elem;
+        elem += b.n;
+        b.col_groups = (b.row_words + kRelWordsPerBlock - 1) / kRelWordsPerBlock;
+        b.rblock_begin = rblk;
+        rblk += ((b.n + kRelRowsPerBlock - 1) / kRelRowsPerBlock) * b.col_groups;
+        b.hist_off = hoff;
+        hoff += cs_hist_len(b.n);
+        while (max_pow2 < b.n) max_pow2 <<= 1;
+    }
+    // Count tables in decreasing set size (the largest sets' tiles go first).
+    std::vector<int> order(static_cast<size_t>(n_sets));
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bs[a].n > bs[b].n; });
+    int64_t items = 0, words = 0;
+    std::vector<PopcSetEntry> pe;
+    std::vector<MmaSetEntry> me;
+    for (int r = 0; r < n_sets; ++r) {
+        const BatchSet& b = bs[order[r]];
+        if (p == CS_PATH_MMA) {
+            MmaSetEntry e;
+            std::memset(static_cast<void*>(&e), 0, sizeof(e));
+            if (mma_fill_entry(&e, b.bits, b.n, b.row_words, ws + L.U[order[r]], ws + L.L[order[r]]) != CUDA_SUCCESS)
+                return CS_ECUDA;
+            e.item_begin = items;
+            e.item_offset = 0;
+            items += mma_items(b.n);
+            e.hist_off = b.hist_off * 8;
+            e.word_begin = words;
+            words += b.n * (e.kpad / 16);
+            me.push_back(e);
+        } else {
+            PopcSetEntry e;
+            std::memset(static_cast<void*>(&e), 0, sizeof(e));
+            popc_fill_entry(&e, b.bits, b.n, b.row_words);
+            if (popc_encode_map(&e.map, b.bits, b.n, b.row_words) != CUDA_SUCCESS) return CS_ECUDA;
+            e.item_begin = items;
+            e.item_offset = 0;
+            items += popc_tiles(b.n);
+            e.hist_off = b.hist_off * 8;
+            pe.push_back(e);
+        }
+    }
+    cs_batch* h = new (std::nothrow) cs_batch;
+    if (!h) return CS_ENOMEM;
+    h->nsets = n_sets;
+    h->path = p;
+    h->ws = ws;
+    h->hdr = reinterpret_cast<WsHeader*>(ws);
+    h->sets_dev = reinterpret_cast<BatchSet*>(ws + L.sets);
+    h->total_elems = elem;
+    h->total_rblocks = rblk;
+    h->total_items = items;
+    h->total_pieces = words;
+    h->total_hist = hoff;
+    h->max_pow2 = max_pow2;
+    cudaError_t e = cudaMemcpyAsync(h->sets_dev, bs.data(), sizeof(BatchSet) * bs.size(), cudaMemcpyHostToDevice, st);
+    if (p == CS_PATH_MMA) {
+        h->mma_dev = reinterpret_cast<MmaSetEntry*>(ws + L.entries);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->mma_dev, me.data(), sizeof(MmaSetEntry) * me.size(), cudaMemcpyHostToDevice, st);
+    } else {
+        h->popc_dev = reinterpret_cast<PopcSetEntry*>(ws + L.entries);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->popc_dev, pe.data(), sizeof(PopcSetEntry) * pe.size(), cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host tables go out of scope
+    if (e != cudaSuccess) {
+        delete h;
+        return CS_ECUDA;
+    }
+    *out = h;
+    return CS_OK;
+}
+
+int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_t* hist_dev, double* actions_dev,
+                    int64_t* brackets_dev, void* stream) {
+    if (!b || !hist_dev || n_eps < 0 || n_eps > kMaxEps || (n_eps > 0 && (!eps_host || !actions_dev)) ||
+        (reinterpret_cast<uintptr_t>(hist_dev) % 8) != 0)
+        return CS_EINVAL;
+    EpsArgs a;
+    a.n = n_eps;
+    for (int e = 0; e < kMaxEps; ++e) {
+        a.v[e] = e < n_eps ? eps_host[e] : 0.0;
+        if (e < n_eps && !(a.v[e] <= 1.0)) return CS_EINVAL;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t err = cudaMemsetAsync(&b->hdr->status, 0, sizeof(int32_t), st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(hist_dev, 0, size_t(b->total_hist) * 8, st);
+    if (err != cudaSuccess) return CS_ECUDA;
+    const int sms = device_sm_count();
+
+    int64_t g = (b->total_elems + 255) / 256;
+    if (g > int64_t(sms) * 16) g = int64_t(sms) * 16;
+    k_batch_keys<<<unsigned(g), 256, 0, st>>>(b->sets_dev, b->nsets, b->total_elems, b->hdr);
+
+    const size_t rank_smem = size_t(b->max_pow2) * 16;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CS_ECUDA;
+    if (dev >= 0 && dev < 64 && !g_rank_attr[dev]) {
+        if (cudaFuncSetAttribute(k_batch_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(size_t(CS_BATCH_MAX_N) * 16)) != cudaSuccess)
+            return CS_ECUDA;
+        g_rank_attr[dev] = true;
+    }
+    k_batch_rank<<<unsigned(b->nsets), kRankThreads, rank_smem, st>>>(b->sets_dev);
+
+    g = b->total_rblocks < int64_t(sms) * 8 ? b->total_rblocks : int64_t(sms) * 8;
+    k_batch_relate<<<unsigned(g), kRelThreads, 0, st>>>(b->sets_dev, b->nsets, b->total_rblocks);
+    if ((err = cudaGetLastError()) != cudaSuccess) return CS_ECUDA;
+
+    if (b->path == CS_PATH_MMA) {
+        if ((err = launch_expand_multi(b->mma_dev, b->nsets, b->total_pieces, st)) != cudaSuccess) return CS_ECUDA;
+        err = launch_count_mma_multi(b->mma_dev, b->nsets, b->total_items, reinterpret_cast<uintptr_t>(hist_dev),
+                                     b->hdr, 0, st);
+    } else {
+        err = launch_count_popc_multi(b->popc_dev, b->nsets, b->total_items, reinterpret_cast<uintptr_t>(hist_dev),
+                                      b->hdr, 0, st);
+    }
+    if (err != cudaSuccess) return CS_ECUDA;
+    if (n_eps > 0 || brackets_dev) {
+        k_batch_action<<<unsigned(b->nsets), kActThreads, 0, st>>>(b->sets_dev, hist_dev, a, actions_dev,
+                                                                  brackets_dev);
+        if (cudaGetLastError() != cudaSuccess) return CS_ECUDA;
+    }
+    return CS_OK;
+}
+
+int cs_batch_path(const cs_batch* b) { return b ? b->path : -1; }
+
+void cs_batch_destroy(cs_batch* b) { delete b; }
+
+}  // extern "C"

@@ -13,8 +13,10 @@
 // is exact.
 //
 // Kernel.  A persistent grid (one CTA per SM) walks 128 x 256 output tiles
-// (128 i-rows, 256 j-rows, i-block at or before the j-block) in decreasing K
-// length, statically strided over CTAs.  Warp roles:
+// (128 i-rows, 256 j-rows, i-block at or before the j-block), rasterised in
+// 8 x 8 blocks of 256 x 256 supertiles served widest band first and
+// statically strided over CTAs, so concurrent CTAs share operand panels in
+// L2.  Warp roles:
 //   warp 0      TMA producer: 128-row A slab and 256-row B slab of 128 K-bytes
 //               per stage (128B swizzle) into a 4-stage shared-memory ring;
 //   warp 1      TMEM allocator and MMA issuer: 4 x tcgen05.mma (M128 N256 K32)
@@ -33,7 +35,7 @@ namespace {
 
 constexpr int kBM = 128;                 // i rows per tile (TMEM lanes)
 constexpr int kBN = 256;                 // j rows per tile (accumulator columns)
-constexpr int kBK = 128;                 // K bytes (FP8 elements) per stage = one 128B swizzle row
+constexpr int kBK = 128;                 // K bytes (FP8 elements) per stage = one swizzle row (128 or 64)
 constexpr int kUK = 32;                  // K per tcgen05.mma of kind::f8f6f4
 constexpr int kStages = 4;
 constexpr int kABytes = kBM * kBK;       // 16 KiB
@@ -45,28 +47,45 @@ constexpr int kTmemCols = 512;           // two 256-column FP32 accumulators
 constexpr uint32_t kIdesc = idesc_f8_f32(kBM, kBN);
 constexpr int kSmemBytes = kStages * kStageBytes + kHistBins * 4 + 256 + 1024;
 constexpr uint8_t kOne = 0x38;           // 1.0 in FP8 E4M3
+constexpr CUtensorMapSwizzle kSwizzle = kBK == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+static_assert(kBK == 128 || kBK == 64, "one 128- or 64-byte swizzle row per stage");
+static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "stage buffers stay swizzle-atom aligned");
 
-// Items: supertiles of 256 x 256 pairs (si <= sj) in decreasing K length,
-// each split into two 128-row halves.  Returns false for a half that lies
-// entirely beyond n.
+// Items.  Pairs are covered by 256 x 256 supertiles (si <= sj), each split
+// into two 128-row halves (one MMA tile each).  Supertiles are grouped into
+// kRaster x kRaster raster blocks; blocks are served from the widest band
+// (longest K) to the diagonal, and the 2 * kRaster^2 slots of a block are
+// consecutive item indices.  CTAs that run at the same time therefore share
+// A panels (same si) and B panels (same sj) through L2 instead of each
+// streaming its own operands from HBM.  Slots with si > sj, or beyond n,
+// decode to nothing and are skipped by every role alike.
+constexpr int kRaster = 8;
+constexpr int64_t kSlotsPerBlock = 2 * kRaster * kRaster;
+
 struct Item {
     int64_t I0, J0;
     int64_t kb0, kb1;  // K-blocks [kb0, kb1)
 };
 
 __device__ __forceinline__ bool decode_item(int64_t t, int64_t nsb, int64_t n, int64_t kblocks, Item& it) {
-    const int64_t st = t >> 1, half = t & 1;
-    int64_t m = int64_t((1.0 + sqrt(1.0 + 8.0 * double(st))) * 0.5);
-    while (m * (m - 1) / 2 > st) --m;
-    while (m * (m + 1) / 2 <= st) ++m;
-    const int64_t si = st - m * (m - 1) / 2;
-    const int64_t sj = si + (nsb - m);
+    const int64_t blk = t / kSlotsPerBlock, slot = t - blk * kSlotsPerBlock;
+    const int64_t nbg = (nsb + kRaster - 1) / kRaster;
+    int64_t m = int64_t((1.0 + sqrt(1.0 + 8.0 * double(blk))) * 0.5);
+    while (m * (m - 1) / 2 > blk) --m;
+    while (m * (m + 1) / 2 <= blk) ++m;
+    const int64_t gi = blk - m * (m - 1) / 2;
+    const int64_t gj = gi + (nbg - m);
+    const int64_t si = gi * kRaster + slot / (2 * kRaster);
+    const int64_t rem = slot % (2 * kRaster);
+    const int64_t sj = gj * kRaster + rem / 2, half = rem & 1;
+    if (si > sj || sj >= nsb) return false;
     it.I0 = si * 256 + half * kBM;
     it.J0 = sj * kBN;
+    if (it.I0 >= n) return false;
     it.kb0 = it.I0 / kBK;
-    int64_t e = (it.J0 + kBN + kBK - 1) / kBK;
+    const int64_t e = (it.J0 + kBN + kBK - 1) / kBK;
     it.kb1 = e < kblocks ? e : kblocks;
-    return it.I0 < n;
+    return true;
 }
 
 // Spread the low 8 bits of x into 8 bytes of 0x00 / 0x38 (bit b -> byte b).
@@ -76,42 +95,135 @@ __device__ __forceinline__ uint64_t spread_byte(uint32_t x) {
     return y * kOne;
 }
 
-__device__ __forceinline__ void store_expanded(uint8_t* dst, uint64_t w) {
-    uint4* d = reinterpret_cast<uint4*>(dst);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint32_t b = uint32_t(w >> (16 * q));
-        uint4 v;
-        const uint64_t lo = spread_byte(b & 0xFFu), hi = spread_byte((b >> 8) & 0xFFu);
-        v.x = uint32_t(lo);
-        v.y = uint32_t(lo >> 32);
-        v.z = uint32_t(hi);
-        v.w = uint32_t(hi >> 32);
-        d[q] = v;
-    }
+// 16 bits of a bitset word -> 16 operand bytes (one 16-byte store).
+__device__ __forceinline__ void store16(uint8_t* dst, uint32_t bits16) {
+    const uint64_t lo = spread_byte(bits16 & 0xFFu), hi = spread_byte((bits16 >> 8) & 0xFFu);
+    uint4 v;
+    v.x = uint32_t(lo);
+    v.y = uint32_t(lo >> 32);
+    v.z = uint32_t(hi);
+    v.w = uint32_t(hi >> 32);
+    *reinterpret_cast<uint4*>(dst) = v;
 }
 
-// U and L rows from the symmetric bitset: one thread per 64-bit word.
+// Columns [16c, 16c+16) of row i: U keeps the columns after i, L the columns
+// before i.  Consecutive threads write consecutive 16-byte pieces.
+__device__ __forceinline__ void expand_piece(const uint64_t* __restrict__ bits, int64_t row_words, int64_t kpad,
+                                             uint8_t* __restrict__ U, uint8_t* __restrict__ L, int64_t i, int64_t c) {
+    const int64_t w = c >> 2;
+    const int sh = int(c & 3) * 16;
+    const uint64_t word = __ldg(bits + i * row_words + w);
+    const int64_t x = i - 64 * w;  // bit position of column i inside this word
+    const uint64_t after = x < 0 ? ~0ull : (x >= 63 ? 0ull : (~0ull << (x + 1)));
+    const uint64_t before = x <= 0 ? 0ull : (x >= 64 ? ~0ull : ((1ull << x) - 1ull));
+    store16(U + i * kpad + 16 * c, uint32_t((word & after) >> sh) & 0xFFFFu);
+    store16(L + i * kpad + 16 * c, uint32_t((word & before) >> sh) & 0xFFFFu);
+}
+
+// U and L rows from the symmetric bitset: one thread per 16 columns.
 __global__ void __launch_bounds__(256) k_expand_f8(const uint64_t* __restrict__ bits, int64_t n, int64_t row_words,
                                                    int64_t kpad, uint8_t* __restrict__ U, uint8_t* __restrict__ L) {
-    const int64_t wpr = kpad / 64;
-    const int64_t total = n * wpr;
+    const int64_t ppr = kpad / 16;
+    const int64_t total = n * ppr;
     for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
          idx += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t i = idx / wpr, w = idx - i * wpr;
-        const uint64_t word = bits[i * row_words + w];
-        const int64_t x = i - 64 * w;  // bit position of column i inside this word
-        const uint64_t after = x < 0 ? ~0ull : (x >= 63 ? 0ull : (~0ull << (x + 1)));
-        const uint64_t before = x <= 0 ? 0ull : (x >= 64 ? ~0ull : ((1ull << x) - 1ull));
-        store_expanded(U + i * kpad + 64 * w, word & after);
-        store_expanded(L + i * kpad + 64 * w, word & before);
+        const int64_t i = idx / ppr, c = idx - i * ppr;
+        expand_piece(bits, row_words, kpad, U, L, i, c);
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    k_count_mma(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mapL,
-                const uint64_t* __restrict__ bits, int64_t n, int64_t row_words, int64_t nsb, int64_t nitems,
-                int64_t kblocks, unsigned long long* __restrict__ hist, int64_t hist_len, WsHeader* hdr) {
+// The same over many sets: piece index -> set by binary search on word_begin
+// (which counts 16-column pieces here).
+__global__ void __launch_bounds__(256) k_expand_f8_multi(const MmaSetEntry* __restrict__ sets, int nsets,
+                                                         int64_t total) {
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        int lo = 0, hi = nsets - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sets[mid].word_begin <= idx) lo = mid; else hi = mid - 1;
+        }
+        const MmaSetEntry& e = sets[lo];
+        const int64_t ppr = e.kpad / 16;
+        const int64_t r = idx - e.word_begin;
+        const int64_t i = r / ppr, c = r - i * ppr;
+        expand_piece(e.bits, e.row_words, e.kpad, e.U, e.L, i, c);
+    }
+}
+
+// One causal set as the kernel sees it.
+struct MmaView {
+    const CUtensorMap* mapU;
+    const CUtensorMap* mapL;
+    const uint64_t* bits;
+    int64_t n, row_words, nsb, kblocks;
+    unsigned long long* hist;
+    int64_t hist_len;
+};
+
+// Work source: a single set passed in kernel parameters.
+struct MmaSingle {
+    MmaView v;
+    int64_t nitems;
+    __device__ __forceinline__ int64_t total() const { return nitems; }
+    __device__ __forceinline__ int set_of(int64_t t, int64_t& local) const {
+        local = t;
+        return 0;
+    }
+    __device__ __forceinline__ MmaView view(int) const { return v; }
+};
+
+// Work source: many sets from a device table, items ordered set by set.
+struct MmaMulti {
+    const MmaSetEntry* sets;
+    int nsets;
+    int64_t nitems;
+    uintptr_t hist_base;
+    __device__ __forceinline__ int64_t total() const { return nitems; }
+    __device__ __forceinline__ int set_of(int64_t t, int64_t& local) const {
+        int lo = 0, hi = nsets - 1;  // last set with item_begin <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sets[mid].item_begin <= t) lo = mid; else hi = mid - 1;
+        }
+        local = t - sets[lo].item_begin + sets[lo].item_offset;
+        return lo;
+    }
+    __device__ __forceinline__ MmaView view(int s) const {
+        const MmaSetEntry& e = sets[s];
+        return MmaView{&e.mapU, &e.mapL, e.bits, e.n, e.row_words, e.nsb, e.kblocks,
+                       reinterpret_cast<unsigned long long*>(hist_base + uintptr_t(e.hist_off)),
+                       e.n > 1 ? e.n - 1 : 1};
+    }
+};
+
+// Barrier over the 128 epilogue threads only, built on an mbarrier so that
+// its wait is bounded and gives up once the CTA has aborted.
+__device__ __forceinline__ bool epilogue_sync(uint64_t* ebar, uint32_t& phase, WsHeader* hdr, volatile int* abort) {
+    mbar_arrive(ebar);
+    const bool ok = mbar_wait_or_abort(ebar, phase, hdr, abort);
+    phase ^= 1u;
+    return ok;
+}
+
+// Epilogue threads add the shared histogram to the set's histogram and clear
+// it.  Returns false if the CTA aborted.
+__device__ __forceinline__ bool epilogue_flush(uint32_t* shist, const MmaView& v, int etid, uint64_t* ebar,
+                                               uint32_t& phase, WsHeader* hdr, volatile int* abort) {
+    if (!epilogue_sync(ebar, phase, hdr, abort)) return false;
+    const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
+    for (int64_t k = etid; k < hb; k += 128) {
+        const uint32_t c = shist[k];
+        if (c) {
+            atomicAdd(&v.hist[k], (unsigned long long)c);
+            shist[k] = 0u;
+        }
+    }
+    return epilogue_sync(ebar, phase, hdr, abort);
+}
+
+template <class Src>
+__device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes);
@@ -119,11 +231,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* empty = full + kStages;
     uint64_t* tfull = empty + kStages;
     uint64_t* tempty = tfull + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    uint64_t* ebar = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ebar + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t hb = hist_len < kHistBins ? hist_len : kHistBins;
+    const int64_t total = src.total();
 
     for (int k = tid; k < kHistBins; k += kThreads) shist[k] = 0u;
     if (tid == 0) {
@@ -135,6 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 4 * 32);
         }
+        mbar_init(ebar, 4 * 32);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -151,15 +265,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------------------------------------------- TMA producer
         uint32_t s = 0, ph = 0, issued = 0;
         bool ok = true;
-        for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
+        int cur = -1;
+        MmaView v{};
+        for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            int64_t local;
+            const int sidx = src.set_of(t, local);
+            if (sidx != cur) {
+                cur = sidx;
+                v = src.view(sidx);
+            }
             Item it;
-            if (!decode_item(t, nsb, n, kblocks, it)) continue;
+            if (!decode_item(local, v.nsb, v.n, v.kblocks, it)) continue;
             for (int64_t kb = it.kb0; kb < it.kb1; ++kb) {
                 if (!mbar_wait_or_abort(&empty[s], ph ^ 1u, hdr, abort_flag)) { ok = false; break; }
                 uint8_t* a = smem + s * kStageBytes;
                 mbar_arrive_expect_tx(&full[s], kStageBytes);
-                tma_load_2d(a, &mapU, int32_t(kb * kBK), int32_t(it.I0), &full[s]);
-                tma_load_2d(a + kABytes, &mapL, int32_t(kb * kBK), int32_t(it.J0), &full[s]);
+                tma_load_2d(a, v.mapU, int32_t(kb * kBK), int32_t(it.I0), &full[s]);
+                tma_load_2d(a + kABytes, v.mapL, int32_t(kb * kBK), int32_t(it.J0), &full[s]);
                 ++issued;
                 if (++s == kStages) { s = 0; ph ^= 1u; }
             }
@@ -174,13 +296,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------------- MMA issuer
         uint32_t s = 0, ph = 0;
-        int64_t local = 0;
+        int64_t local_count = 0;
         bool ok = true;
-        for (int64_t t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
+        int cur = -1;
+        MmaView v{};
+        for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            int64_t local;
+            const int sidx = src.set_of(t, local);
+            if (sidx != cur) {
+                cur = sidx;
+                v = src.view(sidx);
+            }
             Item it;
-            if (!decode_item(t, nsb, n, kblocks, it)) continue;
-            const uint32_t buf = uint32_t(local & 1), use = uint32_t((local >> 1) & 1);
-            ++local;
+            if (!decode_item(local, v.nsb, v.n, v.kblocks, it)) continue;
+            const uint32_t buf = uint32_t(local_count & 1), use = uint32_t((local_count >> 1) & 1);
+            ++local_count;
             if (!mbar_wait_or_abort(&tempty[buf], use ^ 1u, hdr, abort_flag)) break;
             tc_fence_after();
             const uint32_t d = tmem_base + buf * kBN;
@@ -188,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!mbar_wait_or_abort(&full[s], ph, hdr, abort_flag)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t a = smem_u32(smem + s * kStageBytes);
-                const uint64_t adesc = sdesc_k_sw128(a), bdesc = sdesc_k_sw128(a + kABytes);
+                const uint64_t adesc = sdesc_k_swizzled(a, kBK), bdesc = sdesc_k_swizzled(a + kABytes, kBK);
 #pragma unroll
                 for (int kk = 0; kk < kBK / kUK; ++kk)
                     mma_f8f6f4(d, adesc + uint64_t((kk * kUK) >> 4), bdesc + uint64_t((kk * kUK) >> 4), kIdesc,
@@ -201,53 +331,81 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp >= 2) {
         // ---------------------------------------------------- epilogue
         const int q = warp & 3;  // TMEM lane quarter this warp may access
-        int64_t local = 0;
-        for (int64_t t = blockIdx.x; t < nitems; t += gridDim.x) {
+        const int etid = tid - 64;
+        int64_t local_count = 0;
+        int cur = -1;
+        uint32_t ephase = 0;
+        bool ok = true;
+        MmaView v{};
+        for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+            int64_t local;
+            const int sidx = src.set_of(t, local);
+            if (sidx != cur) {
+                if (cur >= 0 && !epilogue_flush(shist, v, etid, ebar, ephase, hdr, abort_flag)) { ok = false; break; }
+                cur = sidx;
+                v = src.view(sidx);
+            }
             Item it;
-            if (!decode_item(t, nsb, n, kblocks, it)) continue;
-            const uint32_t buf = uint32_t(local & 1), use = uint32_t((local >> 1) & 1);
-            ++local;
-            if (!mbar_wait_or_abort(&tfull[buf], use, hdr, abort_flag)) break;
+            if (!decode_item(local, v.nsb, v.n, v.kblocks, it)) continue;
+            const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
+            const uint32_t buf = uint32_t(local_count & 1), use = uint32_t((local_count >> 1) & 1);
+            ++local_count;
+            if (!mbar_wait_or_abort(&tfull[buf], use, hdr, abort_flag)) { ok = false; break; }
             tc_fence_after();
             const int64_t i = it.I0 + 32 * q + lane;
             uint64_t cw[kBN / 64];
 #pragma unroll
             for (int w = 0; w < kBN / 64; ++w) {
                 const int64_t word = (it.J0 >> 6) + w;
-                cw[w] = (i < n && word < row_words) ? __ldg(bits + i * row_words + word) : 0ull;
+                cw[w] = (i < v.n && word < v.row_words) ? __ldg(v.bits + i * v.row_words + word) : 0ull;
             }
 #pragma unroll 1
             for (int c = 0; c < kBN / 32; ++c) {
-                uint32_t v[32];
-                tmem_ld_32x32b_x32(tmem_base + (uint32_t(32 * q) << 16) + buf * kBN + uint32_t(32 * c), v);
+                uint32_t r[32];
+                tmem_ld_32x32b_x32(tmem_base + (uint32_t(32 * q) << 16) + buf * kBN + uint32_t(32 * c), r);
                 tmem_ld_wait();
                 const uint32_t rel = uint32_t(cw[c >> 1] >> (32 * (c & 1)));  // C_ij for these 32 j
 #pragma unroll
                 for (int u = 0; u < 32; ++u) {
                     const int64_t j = it.J0 + 32 * c + u;
-                    if (((rel >> u) & 1u) && j > i && j < n) {
-                        const uint32_t k = uint32_t(__uint_as_float(v[u]));
+                    if (((rel >> u) & 1u) && j > i && j < v.n) {
+                        const uint32_t k = uint32_t(__uint_as_float(r[u]));
                         if (int64_t(k) < hb)
                             atomicAdd(&shist[k], 1u);
                         else
-                            atomicAdd(&hist[k], 1ull);
+                            atomicAdd(&v.hist[k], 1ull);
                     }
                 }
             }
             tc_fence_before();
             mbar_arrive(&tempty[buf]);
         }
+        if (ok && cur >= 0) epilogue_flush(shist, v, etid, ebar, ephase, hdr, abort_flag);
     }
     __syncthreads();
-    for (int64_t k = tid; k < hb; k += kThreads)
-        if (shist[k]) atomicAdd(&hist[k], (unsigned long long)shist[k]);
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, kTmemCols);
     }
 }
 
+__global__ void __launch_bounds__(kThreads, 1)
+    k_count_mma(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mapL,
+                const uint64_t* __restrict__ bits, int64_t n, int64_t row_words, int64_t nsb, int64_t nitems,
+                int64_t kblocks, unsigned long long* __restrict__ hist, int64_t hist_len, WsHeader* hdr) {
+    const MmaSingle src{MmaView{&mapU, &mapL, bits, n, row_words, nsb, kblocks, hist, hist_len}, nitems};
+    mma_body(src, hdr);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_count_mma_multi(const MmaSetEntry* __restrict__ sets, int nsets, int64_t nitems, uintptr_t hist_base,
+                      WsHeader* hdr) {
+    const MmaMulti src{sets, nsets, nitems, hist_base};
+    mma_body(src, hdr);
+}
+
 bool g_attr_set[64];
+bool g_attr_multi_set[64];
 
 struct MmaLayout {
     int64_t kpad;
@@ -267,6 +425,65 @@ MmaLayout mma_layout(int64_t n) {
 
 size_t mma_workspace_bytes(int64_t n) { return mma_layout(n).total; }
 
+int64_t mma_kpad(int64_t n) { return (n + kBK - 1) / kBK * kBK; }
+
+int64_t mma_items(int64_t n) {
+    const int64_t nsb = (n + 255) / 256;
+    const int64_t nbg = (nsb + kRaster - 1) / kRaster;
+    return kSlotsPerBlock * nbg * (nbg + 1) / 2;
+}
+
+CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words, uint8_t* U,
+                        uint8_t* L) {
+    e->bits = bits;
+    e->n = n;
+    e->row_words = row_words;
+    e->nsb = (n + 255) / 256;
+    e->kpad = mma_kpad(n);
+    e->kblocks = e->kpad / kBK;
+    e->U = U;
+    e->L = L;
+    CUresult r = encode_tensor_map_2d(&e->mapU, CU_TENSOR_MAP_DATA_TYPE_UINT8, U, uint64_t(e->kpad), uint64_t(n),
+                                      uint64_t(e->kpad), kBK, kBM, kSwizzle);
+    if (r != CUDA_SUCCESS) return r;
+    return encode_tensor_map_2d(&e->mapL, CU_TENSOR_MAP_DATA_TYPE_UINT8, L, uint64_t(e->kpad), uint64_t(n),
+                                uint64_t(e->kpad), kBK, kBN, kSwizzle);
+}
+
+cudaError_t launch_expand_single(const MmaSetEntry* e, cudaStream_t st) {
+    const int64_t total_pieces = e->n * (e->kpad / 16);
+    int64_t eg = (total_pieces + 255) / 256;
+    if (eg > int64_t(device_sm_count()) * 64) eg = int64_t(device_sm_count()) * 64;
+    if (eg < 1) return cudaSuccess;
+    k_expand_f8<<<unsigned(eg), 256, 0, st>>>(e->bits, e->n, e->row_words, e->kpad, e->U, e->L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand_multi(const MmaSetEntry* sets_dev, int nsets, int64_t total_pieces, cudaStream_t st) {
+    if (total_pieces < 1) return cudaSuccess;
+    int64_t eg = (total_pieces + 255) / 256;
+    if (eg > int64_t(device_sm_count()) * 64) eg = int64_t(device_sm_count()) * 64;
+    k_expand_f8_multi<<<unsigned(eg), 256, 0, st>>>(sets_dev, nsets, total_pieces);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64_t nitems, uintptr_t hist_base,
+                                   WsHeader* hdr, int max_ctas, cudaStream_t st) {
+    if (nitems < 1) return cudaSuccess;
+    cudaError_t err;
+    int dev = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if (dev >= 0 && dev < 64 && !g_attr_multi_set[dev]) {
+        err = cudaFuncSetAttribute(k_count_mma_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (err != cudaSuccess) return err;
+        g_attr_multi_set[dev] = true;
+    }
+    int64_t grid = max_ctas > 0 ? max_ctas : device_sm_count();
+    if (grid > nitems) grid = nitems;
+    k_count_mma_multi<<<unsigned(grid), kThreads, kSmemBytes, st>>>(sets_dev, nsets, nitems, hist_base, hdr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* workspace,
                              cudaStream_t st) {
     WsHeader* hdr = static_cast<WsHeader*>(workspace);
@@ -278,17 +495,17 @@ cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words,
     uint8_t* U = static_cast<uint8_t*>(workspace) + lay.u;
     uint8_t* L = static_cast<uint8_t*>(workspace) + lay.l;
 
-    const int64_t total_words = n * (lay.kpad / 64);
-    int64_t eg = (total_words + 255) / 256;
+    const int64_t total_pieces = n * (lay.kpad / 16);
+    int64_t eg = (total_pieces + 255) / 256;
     if (eg > int64_t(device_sm_count()) * 64) eg = int64_t(device_sm_count()) * 64;
     k_expand_f8<<<unsigned(eg), 256, 0, st>>>(bits, n, row_words, lay.kpad, U, L);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
 
     CUtensorMap mapU, mapL;
     if (encode_tensor_map_2d(&mapU, CU_TENSOR_MAP_DATA_TYPE_UINT8, U, uint64_t(lay.kpad), uint64_t(n),
-                             uint64_t(lay.kpad), kBK, kBM, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS ||
+                             uint64_t(lay.kpad), kBK, kBM, kSwizzle) != CUDA_SUCCESS ||
         encode_tensor_map_2d(&mapL, CU_TENSOR_MAP_DATA_TYPE_UINT8, L, uint64_t(lay.kpad), uint64_t(n),
-                             uint64_t(lay.kpad), kBK, kBN, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+                             uint64_t(lay.kpad), kBK, kBN, kSwizzle) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
 
     int dev = 0;
@@ -299,7 +516,7 @@ cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words,
         g_attr_set[dev] = true;
     }
     const int64_t nsb = (n + 255) / 256;
-    const int64_t nitems = nsb * (nsb + 1);  // two halves per supertile
+    const int64_t nitems = mma_items(n);
     const int64_t kblocks = lay.kpad / kBK;
     int64_t grid = device_sm_count();
     if (grid > nitems) grid = nitems;

@@ -94,10 +94,67 @@ __device__ __forceinline__ void popc_chunk(const uint8_t* __restrict__ F, const 
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    k_count_popc(const __grid_constant__ CUtensorMap tmap, const uint64_t* __restrict__ bits, int64_t n,
-                 int64_t row_words, int64_t nb, int64_t ntiles, unsigned long long* __restrict__ hist,
-                 int64_t hist_len, WsHeader* hdr) {
+// One causal set as the kernel sees it.
+struct PopcView {
+    const CUtensorMap* map;
+    const uint64_t* bits;
+    int64_t n, row_words, nb;
+    unsigned long long* hist;
+    int64_t hist_len;
+};
+
+// Work source: a single set passed in kernel parameters.
+struct PopcSingle {
+    PopcView v;
+    int64_t ntiles;
+    __device__ __forceinline__ int64_t total() const { return ntiles; }
+    __device__ __forceinline__ int set_of(int64_t t, int64_t& local) const {
+        local = t;
+        return 0;
+    }
+    __device__ __forceinline__ PopcView view(int) const { return v; }
+};
+
+// Work source: many sets from a device table, items ordered set by set.
+struct PopcMulti {
+    const PopcSetEntry* sets;
+    int nsets;
+    int64_t ntiles;
+    uintptr_t hist_base;
+    __device__ __forceinline__ int64_t total() const { return ntiles; }
+    __device__ __forceinline__ int set_of(int64_t t, int64_t& local) const {
+        int lo = 0, hi = nsets - 1;  // last set with item_begin <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sets[mid].item_begin <= t) lo = mid; else hi = mid - 1;
+        }
+        local = t - sets[lo].item_begin + sets[lo].item_offset;
+        return lo;
+    }
+    __device__ __forceinline__ PopcView view(int s) const {
+        const PopcSetEntry& e = sets[s];
+        return PopcView{&e.map, e.bits, e.n, e.row_words, e.nb,
+                        reinterpret_cast<unsigned long long*>(hist_base + uintptr_t(e.hist_off)),
+                        e.n > 1 ? e.n - 1 : 1};
+    }
+};
+
+// Add the shared histogram to the set's global histogram and clear it.
+__device__ __forceinline__ void flush_hist(uint32_t* shist, const PopcView& v) {
+    __syncthreads();
+    const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
+    for (int64_t k = threadIdx.x; k < hb; k += kThreads) {
+        const uint32_t c = shist[k];
+        if (c) {
+            atomicAdd(&v.hist[k], (unsigned long long)c);
+            shist[k] = 0u;
+        }
+    }
+    __syncthreads();
+}
+
+template <class Src>
+__device__ __forceinline__ void popc_body(const Src& src, WsHeader* hdr) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes);
@@ -107,7 +164,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tj = (lane & 7) + 8 * (warp >> 2);
     const int ti = (lane >> 3) + 4 * (warp & 3);
-    const int64_t hb = hist_len < kHistBins ? hist_len : kHistBins;
 
     for (int k = tid; k < kHistBins; k += kThreads) shist[k] = 0u;
     if (tid == 0) {
@@ -116,6 +172,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
 
+    int cur = -1;  // set whose counts sit in the shared histogram
+    PopcView v{};
     uint32_t seq = 0;  // K-chunks consumed so far by this CTA: stage = seq % S, parity = (seq / S) & 1
     bool aborted = false;
     for (;;) {
@@ -123,14 +181,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         const int64_t t = *s_tile;
         __syncthreads();
-        if (t >= ntiles) break;
+        if (t >= src.total()) break;
 
+        int64_t local;
+        const int sidx = src.set_of(t, local);
+        if (sidx != cur) {
+            if (cur >= 0) flush_hist(shist, v);
+            cur = sidx;
+            v = src.view(sidx);
+        }
+        const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
         int64_t bi, bj;
-        decode_tile(t, nb, bi, bj);
+        decode_tile(local, v.nb, bi, bj);
         const int64_t I0 = bi * kBT, J0 = bj * kBT;
         const int64_t wbeg = ((I0 >> 6) / kKW) * kKW;
         int64_t wend = (J0 + kBT + 63) >> 6;
-        if (wend > row_words) wend = row_words;
+        if (wend > v.row_words) wend = v.row_words;
         const int nch = int((wend - wbeg + kKW - 1) / kKW);
 
         if (tid == 0) {
@@ -138,8 +204,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int s = int((seq + c) % kStages);
                 uint8_t* dst = smem + s * kStageBytes;
                 mbar_arrive_expect_tx(&mbar[s], kStageBytes);
-                tma_load_2d(dst, &tmap, int32_t(wbeg + int64_t(c) * kKW), int32_t(I0), &mbar[s]);
-                tma_load_2d(dst + kTileBytes, &tmap, int32_t(wbeg + int64_t(c) * kKW), int32_t(J0), &mbar[s]);
+                tma_load_2d(dst, v.map, int32_t(wbeg + int64_t(c) * kKW), int32_t(I0), &mbar[s]);
+                tma_load_2d(dst + kTileBytes, v.map, int32_t(wbeg + int64_t(c) * kKW), int32_t(J0), &mbar[s]);
             }
         }
 
@@ -178,8 +244,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint8_t* dst = smem + s * kStageBytes;
                 const int64_t wn = wbeg + int64_t(c + kStages) * kKW;
                 mbar_arrive_expect_tx(&mbar[s], kStageBytes);
-                tma_load_2d(dst, &tmap, int32_t(wn), int32_t(I0), &mbar[s]);
-                tma_load_2d(dst + kTileBytes, &tmap, int32_t(wn), int32_t(J0), &mbar[s]);
+                tma_load_2d(dst, v.map, int32_t(wn), int32_t(I0), &mbar[s]);
+                tma_load_2d(dst + kTileBytes, v.map, int32_t(wn), int32_t(J0), &mbar[s]);
             }
         }
         if (aborted) break;
@@ -188,30 +254,80 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
             const int64_t i = I0 + ti + 16 * a;
-            if (i >= n) continue;
-            const uint64_t* row = bits + i * row_words;
+            if (i >= v.n) continue;
+            const uint64_t* row = v.bits + i * v.row_words;
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
                 const int64_t j = J0 + tj + 16 * b;
-                if (j <= i || j >= n) continue;
+                if (j <= i || j >= v.n) continue;
                 if ((__ldg(row + (j >> 6)) >> (j & 63)) & 1ull) {
                     const uint32_t k = acc[a][b];
                     if (int64_t(k) < hb)
                         atomicAdd(&shist[k], 1u);
                     else
-                        atomicAdd(&hist[k], 1ull);
+                        atomicAdd(&v.hist[k], 1ull);
                 }
             }
         }
     }
-    __syncthreads();
-    for (int64_t k = tid; k < hb; k += kThreads)
-        if (shist[k]) atomicAdd(&hist[k], (unsigned long long)shist[k]);
+    if (cur >= 0) flush_hist(shist, v);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_count_popc(const __grid_constant__ CUtensorMap tmap, const uint64_t* __restrict__ bits, int64_t n,
+                 int64_t row_words, int64_t nb, int64_t ntiles, unsigned long long* __restrict__ hist,
+                 int64_t hist_len, WsHeader* hdr) {
+    const PopcSingle src{PopcView{&tmap, bits, n, row_words, nb, hist, hist_len}, ntiles};
+    popc_body(src, hdr);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_count_popc_multi(const PopcSetEntry* __restrict__ sets, int nsets, int64_t ntiles, uintptr_t hist_base,
+                       WsHeader* hdr) {
+    const PopcMulti src{sets, nsets, ntiles, hist_base};
+    popc_body(src, hdr);
 }
 
 bool g_attr_set[64];
+bool g_attr_multi_set[64];
 
 }  // namespace
+
+int64_t popc_tiles(int64_t n) {
+    const int64_t nb = (n + kBT - 1) / kBT;
+    return nb * (nb + 1) / 2;
+}
+
+void popc_fill_entry(PopcSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words) {
+    e->bits = bits;
+    e->n = n;
+    e->row_words = row_words;
+    e->nb = (n + kBT - 1) / kBT;
+}
+
+CUresult popc_encode_map(CUtensorMap* map, const uint64_t* bits, int64_t n, int64_t row_words) {
+    return encode_tensor_map_2d(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, const_cast<uint64_t*>(bits),
+                                uint64_t(row_words), uint64_t(n), uint64_t(row_words) * 8, kKW, kBT,
+                                CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+cudaError_t launch_count_popc_multi(const PopcSetEntry* sets_dev, int nsets, int64_t ntiles, uintptr_t hist_base,
+                                    WsHeader* hdr, int max_ctas, cudaStream_t st) {
+    cudaError_t err = cudaMemsetAsync(&hdr->counter, 0, sizeof(hdr->counter), st);
+    if (err != cudaSuccess) return err;
+    if (ntiles < 1) return cudaSuccess;
+    int dev = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if (dev >= 0 && dev < 64 && !g_attr_multi_set[dev]) {
+        err = cudaFuncSetAttribute(k_count_popc_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (err != cudaSuccess) return err;
+        g_attr_multi_set[dev] = true;
+    }
+    int64_t grid = max_ctas > 0 ? max_ctas : device_sm_count();
+    if (grid > ntiles) grid = ntiles;
+    k_count_popc_multi<<<unsigned(grid), kThreads, kSmemBytes, st>>>(sets_dev, nsets, ntiles, hist_base, hdr);
+    return cudaGetLastError();
+}
 
 size_t popc_workspace_bytes(int64_t) { return sizeof(WsHeader); }
 

@@ -164,18 +164,19 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Shared-memory matrix descriptor for a K-major operand tile stored by TMA
-// with 128-byte swizzle: rows of 128 bytes, 8-row (1024-byte) swizzle atoms
-// stacked at a stride of 1024 bytes.  Fields: start address >> 4 (bits 0-13),
-// leading byte offset >> 4 (16-29, unused for swizzled K-major), stride byte
-// offset >> 4 (32-45), descriptor version 1 (46-47), layout 2 = 128B swizzle
-// (61-63).  The tile base must be 1024-byte aligned.
-__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
+// with a 128- or 64-byte swizzle: rows of `row_bytes` bytes, 8-row swizzle
+// atoms stacked at a stride of 8 * row_bytes.  Fields: start address >> 4
+// (bits 0-13), leading byte offset >> 4 (16-29, unused for swizzled K-major),
+// stride byte offset >> 4 (32-45), descriptor version 1 (46-47), layout type
+// (61-63): 2 = 128B swizzle, 4 = 64B swizzle.  The tile base must be aligned
+// to the swizzle atom (1024 bytes covers both).
+__device__ __forceinline__ uint64_t sdesc_k_swizzled(uint32_t saddr, uint32_t row_bytes) {
     uint64_t d = 0;
     d |= uint64_t((saddr & 0x3FFFFu) >> 4);
     d |= uint64_t(1) << 16;
-    d |= uint64_t(1024 >> 4) << 32;
+    d |= uint64_t((8u * row_bytes) >> 4) << 32;
     d |= uint64_t(1) << 46;
-    d |= uint64_t(2) << 61;
+    d |= uint64_t(row_bytes == 128 ? 2 : 4) << 61;
     return d;
 }
 

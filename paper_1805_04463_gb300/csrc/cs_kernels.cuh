@@ -15,12 +15,52 @@ cudaError_t launch_relate(int kind, int64_t n, const int32_t* coords, uint64_t* 
                           cudaStream_t st);
 
 // cs_count_popc.cu
+// One set of a multi-set POPC count: its TMA map, bitset, size, tile range and
+// histogram offset.  128-byte aligned like the embedded tensor map.
+struct alignas(128) PopcSetEntry {
+    CUtensorMap map;
+    const uint64_t* bits;
+    int64_t n, row_words, nb;
+    int64_t item_begin;   // first tile of this set in the concatenated tile list
+    int64_t item_offset;  // tile index (within the set) of that first tile
+    int64_t hist_off;     // byte offset of this set's histogram from the launch's histogram base
+};
 size_t popc_workspace_bytes(int64_t n);
+int64_t popc_tiles(int64_t n);
+void popc_fill_entry(PopcSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words);
+CUresult popc_encode_map(CUtensorMap* map, const uint64_t* bits, int64_t n, int64_t row_words);
+cudaError_t launch_count_popc_multi(const PopcSetEntry* sets_dev, int nsets, int64_t ntiles, uintptr_t hist_base,
+                                    WsHeader* hdr, int max_ctas, cudaStream_t st);
 cudaError_t launch_count_popc(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist,
                               void* workspace, cudaStream_t st);
 
 // cs_count_mma.cu
+// One set of a multi-set tensor-core count: TMA maps of its U and L operands,
+// bitset, sizes, item range, histogram offset, and where its operands live.
+struct alignas(128) MmaSetEntry {
+    CUtensorMap mapU;
+    CUtensorMap mapL;
+    const uint64_t* bits;
+    int64_t n, row_words, nsb, kblocks;
+    int64_t item_begin;   // first item of this set in the concatenated item list
+    int64_t item_offset;  // item index (within the set) of that first item
+    int64_t hist_off;     // byte offset of this set's histogram from the launch's histogram base
+    uint8_t* U;
+    uint8_t* L;
+    int64_t kpad;
+    int64_t word_begin;  // first 16-column piece of this set in the concatenated expand range
+};
 size_t mma_workspace_bytes(int64_t n);
+int64_t mma_items(int64_t n);
+int64_t mma_kpad(int64_t n);
+// Fill sizes, operand pointers and TMA maps of an entry (item_begin, hist_off,
+// word_begin are the caller's).
+CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words, uint8_t* U,
+                        uint8_t* L);
+cudaError_t launch_expand_single(const MmaSetEntry* e, cudaStream_t st);  // uses bits, n, row_words, kpad, U, L
+cudaError_t launch_expand_multi(const MmaSetEntry* sets_dev, int nsets, int64_t total_pieces, cudaStream_t st);
+cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64_t nitems, uintptr_t hist_base,
+                                   WsHeader* hdr, int max_ctas, cudaStream_t st);
 cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist,
                              void* workspace, cudaStream_t st);
 

@@ -1,0 +1,69 @@
+// cs_relate.cuh -- one block of the causal-matrix build (2048 columns x 64
+// rows), shared by the single-set and batched relate kernels.
+#pragma once
+
+#include "cs_internal.cuh"
+
+namespace cs {
+
+constexpr int kRelColsPerBlock = 2048;
+constexpr int kRelWordsPerBlock = kRelColsPerBlock / 64;
+constexpr int kRelRowsPerBlock = 64;
+constexpr int kRelThreads = 256;
+
+// Symmetric timelike test between row element ci and staged column `col`:
+// du * dv > 0 (1+1, light-cone coordinates) or dt^2 - |dx|^2 > 0 (3+1), in int64.
+template <int DIM>
+__device__ __forceinline__ bool rel_related(const int32_t (&ci)[DIM], const int32_t (*sc)[kRelColsPerBlock], int col) {
+    if constexpr (DIM == 2) {
+        // du * dv > 0 as a sign test (|du|, |dv| < 2^21 fit int32)
+        const int32_t du = sc[0][col] - ci[0];
+        const int32_t dv = sc[1][col] - ci[1];
+        return (du ^ dv) >= 0 && du != 0 && dv != 0;
+    } else {
+        const int64_t dt = int64_t(sc[0][col]) - ci[0];
+        const int64_t dx = int64_t(sc[1][col]) - ci[1];
+        const int64_t dy = int64_t(sc[2][col]) - ci[2];
+        const int64_t dz = int64_t(sc[3][col]) - ci[3];
+        return dt * dt - (dx * dx + dy * dy + dz * dz) > 0;
+    }
+}
+
+// Rows [rb*64, rb*64+64) x words [cg*32, cg*32+32) of the bitset.  Column
+// coordinates are staged in `sc`; each warp folds 64 tests per word into a
+// uint64 with two __ballot_sync, lane w keeps word w, and a row's 32 words
+// leave in one coalesced store.  Must be called by all 256 threads.
+template <int DIM>
+__device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords, int64_t n,
+                                             uint64_t* __restrict__ bits, int64_t row_words, int64_t rb, int64_t cg,
+                                             int32_t (*sc)[kRelColsPerBlock]) {
+    const int64_t w0 = cg * kRelWordsPerBlock;
+    const int64_t c0 = w0 * 64;
+    for (int t = threadIdx.x; t < kRelColsPerBlock; t += kRelThreads) {
+        const int64_t c = c0 + t;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) sc[d][t] = c < n ? coords[d * n + c] : 0;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = rb * kRelRowsPerBlock;
+    const int64_t r1 = r0 + kRelRowsPerBlock < n ? r0 + kRelRowsPerBlock : n;
+    for (int64_t i = r0 + warp; i < r1; i += kRelThreads / 32) {
+        int32_t ci[DIM];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) ci[d] = coords[d * n + i];
+        uint64_t mine = 0;
+#pragma unroll 4
+        for (int w = 0; w < kRelWordsPerBlock; ++w) {
+            const int col = w * 64 + lane;
+            const bool b0 = c0 + col < n && rel_related<DIM>(ci, sc, col);
+            const bool b1 = c0 + col + 32 < n && rel_related<DIM>(ci, sc, col + 32);
+            const uint32_t lo = __ballot_sync(0xffffffffu, b0);
+            const uint32_t hi = __ballot_sync(0xffffffffu, b1);
+            if (lane == w) mine = (uint64_t(hi) << 32) | lo;
+        }
+        if (w0 + lane < row_words) bits[i * row_words + w0 + lane] = mine;
+    }
+}
+
+}  // namespace cs

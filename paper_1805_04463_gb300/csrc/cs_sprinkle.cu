@@ -9,6 +9,7 @@
 // only with its bucket -- O(n + 65536) work for the hashed / uniform keys used
 // here, and the same ranks for any bucket fill order.
 #include "cs_kernels.cuh"
+#include "cs_sprinkle.cuh"
 
 namespace cs {
 
@@ -18,55 +19,28 @@ constexpr int kBucketBits = 16;
 constexpr int kBuckets = 1 << kBucketBits;
 constexpr int kThreads = 256;
 
-// Stream numbers of the generator specification.
-constexpr uint32_t kStreamOrderU = 0, kStreamOrderV = 1, kStreamDiamond2 = 2, kStreamDiamond4 = 3;
-
 __global__ void k_keys_2d_order(int64_t n, uint64_t seed, uint64_t* __restrict__ key_u,
                                 uint64_t* __restrict__ key_v) {
     const uint64_t su = stream_key(seed, kStreamOrderU), sv = stream_key(seed, kStreamOrderV);
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
-        key_u[e] = draw_from(su, uint64_t(e), 0);
-        key_v[e] = draw_from(sv, uint64_t(e), 0);
-    }
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+        draw_2d_order(su, sv, e, key_u[e], key_v[e]);
 }
 
-// u, v on the 2^20 grid; key = (u + v) in the top 21 bits.
 __global__ void k_keys_2d_diamond(int64_t n, uint64_t seed, int32_t* __restrict__ raw,
                                   uint64_t* __restrict__ key) {
     const uint64_t s = stream_key(seed, kStreamDiamond2);
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
-        const uint32_t u = uint32_t(draw_from(s, uint64_t(e), 0) >> (64 - kGridBits));
-        const uint32_t v = uint32_t(draw_from(s, uint64_t(e), 1) >> (64 - kGridBits));
-        raw[e] = int32_t(u);
-        raw[n + e] = int32_t(v);
-        key[e] = uint64_t(u + v) << (64 - (kGridBits + 1));
-    }
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+        key[e] = draw_2d_diamond(s, e, raw[e], raw[n + e]);
 }
 
-// Rejection sampling in the box t in [0, 2^20), x, y, z in [-2^19, 2^19):
-// accept iff x^2 + y^2 + z^2 < min(t, 2^20 - t)^2.  key = t in the top 20 bits.
 __global__ void k_keys_4d_diamond(int64_t n, uint64_t seed, int32_t* __restrict__ raw,
                                   uint64_t* __restrict__ key, WsHeader* hdr) {
     const uint64_t s = stream_key(seed, kStreamDiamond4);
-    const int64_t half = kGrid / 2;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
-        int64_t c[4] = {0, 0, 0, 0};
-        bool found = false;
-        for (int a = 0; a < kMaxAttempts && !found; ++a) {
-            int64_t q[4];
+        int32_t c[4];
+        if (!draw_4d_diamond(s, e, c, key[e])) set_status(hdr, CS_ERANGE);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) q[k] = int64_t(draw_from(s, uint64_t(e), uint32_t(4 * a + k)) >> (64 - kGridBits));
-            const int64_t t = q[0], x = q[1] - half, y = q[2] - half, z = q[3] - half;
-            const int64_t h = t < kGrid - t ? t : kGrid - t;
-            if (x * x + y * y + z * z < h * h) {
-                c[0] = t; c[1] = x; c[2] = y; c[3] = z;
-                found = true;
-            }
-        }
-        if (!found) set_status(hdr, CS_ERANGE);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) raw[k * n + e] = int32_t(c[k]);
-        key[e] = uint64_t(c[0]) << (64 - kGridBits);
+        for (int k = 0; k < 4; ++k) raw[k * n + e] = c[k];
     }
 }
 
@@ -175,7 +149,7 @@ SprinkleLayout sprinkle_layout(int64_t n) {
 int grid_for(int64_t n) {
     int64_t b = (n + kThreads - 1) / kThreads;
     if (b < 1) b = 1;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > int64_t(device_sm_count()) * 16) b = int64_t(device_sm_count()) * 16;
     return int(b);
 }
 

@@ -1,0 +1,49 @@
+// cs_sprinkle.cuh -- per-element draws of the sprinklers (Appendix "Causal Set
+// Sprinklings"), shared by the single-set and batched sprinkle kernels.
+#pragma once
+
+#include "cs_internal.cuh"
+
+namespace cs {
+
+// Stream numbers of the generator specification.
+constexpr uint32_t kStreamOrderU = 0, kStreamOrderV = 1, kStreamDiamond2 = 2, kStreamDiamond4 = 3;
+
+// Random 2D order: the two 64-bit keys whose ranks are u and v.
+__device__ __forceinline__ void draw_2d_order(uint64_t su, uint64_t sv, int64_t e, uint64_t& ku, uint64_t& kv) {
+    ku = draw_from(su, uint64_t(e), 0);
+    kv = draw_from(sv, uint64_t(e), 0);
+}
+
+// 2D diamond: u, v on the 2^20 grid; sort key (u + v) in the top 21 bits.
+__device__ __forceinline__ uint64_t draw_2d_diamond(uint64_t s, int64_t e, int32_t& u, int32_t& v) {
+    const uint32_t uu = uint32_t(draw_from(s, uint64_t(e), 0) >> (64 - kGridBits));
+    const uint32_t vv = uint32_t(draw_from(s, uint64_t(e), 1) >> (64 - kGridBits));
+    u = int32_t(uu);
+    v = int32_t(vv);
+    return uint64_t(uu + vv) << (64 - (kGridBits + 1));
+}
+
+// 4D diamond of height 1: rejection sampling in the box t in [0, 2^20),
+// x, y, z in [-2^19, 2^19), accepting x^2+y^2+z^2 < min(t, 2^20-t)^2; sort
+// key t in the top 20 bits.  Returns false if no attempt was accepted.
+__device__ __forceinline__ bool draw_4d_diamond(uint64_t s, int64_t e, int32_t (&c)[4], uint64_t& key) {
+    const int64_t half = kGrid / 2;
+    for (int a = 0; a < kMaxAttempts; ++a) {
+        int64_t q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = int64_t(draw_from(s, uint64_t(e), uint32_t(4 * a + k)) >> (64 - kGridBits));
+        const int64_t t = q[0], x = q[1] - half, y = q[2] - half, z = q[3] - half;
+        const int64_t h = t < kGrid - t ? t : kGrid - t;
+        if (x * x + y * y + z * z < h * h) {
+            c[0] = int32_t(t); c[1] = int32_t(x); c[2] = int32_t(y); c[3] = int32_t(z);
+            key = uint64_t(t) << (64 - kGridBits);
+            return true;
+        }
+    }
+    c[0] = c[1] = c[2] = c[3] = 0;
+    key = 0;
+    return false;
+}
+
+}  // namespace cs

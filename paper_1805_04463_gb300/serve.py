@@ -1,0 +1,250 @@
+"""Serving loop: continuous batching of action requests on one GPU.
+
+Requests (kind, n, seed) arrive over time.  Each admitted request is
+sprinkled, related and -- on the tensor-core path -- expanded into its
+operands once, on a preparation stream; its causal matrix then stays resident
+in HBM while its interval count advances in slices.  Every scheduler tick
+launches ONE multi-set count kernel (cs_count_jobs) over slices of all
+prepared requests, shortest remaining work first, so requests that arrive
+while others are on the GPU join the next tick and their tiles run in the
+same launch as everyone else's.  When a request's last slice is issued, its
+actions and a copy of its histogram are queued behind it; it retires when
+that copy lands.  Admission is bounded by the bitset memory of the active
+requests (n^2/8 bytes each), by their tensor-core operand memory, and by a
+slot count.
+
+Counts are integer additions, so a request's histogram and actions are
+identical whether it runs alone or in the mix (tests/test_gpu_serve.py).
+
+The scheduling decisions are plain host logic (`admit_ok`, `plan_tick`) and
+are unit-tested on the CPU.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+
+import paper_1805_04463_gb300 as cs
+
+EPS = (0.0, 0.05, 0.1, 0.2)
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    kind: int
+    n: int
+    seed: int
+    t_arrival: float
+    # scheduler state
+    total_items: int = 0
+    next_item: int = 0
+    state: str = "queued"        # queued -> prep -> count -> finish -> done
+    t_admit: float = math.nan
+    t_done: float = math.nan
+    bitset_bytes: int = 0
+    operand_bytes: int = 0
+    # device / host buffers
+    buf: object = None
+    operands: object = None
+    operands_ptr: int = 0
+    prep_event: object = None
+    done_event: object = None
+    hist_host: object = None
+    actions_host: object = None
+
+    def remaining_work(self, unit_cost: float) -> float:
+        return (self.total_items - self.next_item) * unit_cost
+
+
+def item_cost(n: int, items: int) -> float:
+    """Average multiply-adds per work item of a set of size n (C(n,3) terms)."""
+    return n * (n - 1) * (n - 2) / 6.0 / max(items, 1)
+
+
+def admit_ok(req, used_bitset, used_operands, active, bitset_budget, operand_budget, max_active):
+    """Admission: a free slot, and the request's bitset and operands fit the budgets."""
+    return (active < max_active and used_bitset + req.bitset_bytes <= bitset_budget
+            and used_operands + req.operand_bytes <= operand_budget)
+
+
+def plan_tick(ready, budget_macs, min_items=1):
+    """Grant work items to ready requests for one tick, shortest remaining work
+    first, until the tick's multiply-add budget is spent.  Every granted slice
+    has at least `min_items` items (or the request's remainder).  Returns a
+    list of (request, item_begin, item_end)."""
+    order = sorted(ready, key=lambda r: (r.remaining_work(item_cost(r.n, r.total_items)), r.rid))
+    grants, left = [], budget_macs
+    for r in order:
+        rem = r.total_items - r.next_item
+        if rem <= 0:
+            continue
+        if left <= 0 and grants:
+            break
+        cost = item_cost(r.n, r.total_items)
+        k = max(min(rem, int(left // cost) if cost > 0 else rem), min(min_items, rem))
+        grants.append((r, r.next_item, r.next_item + k))
+        left -= k * cost
+    return grants
+
+
+class Server:
+    """Continuous-batching server over the C ABI on one GPU."""
+
+    def __init__(self, path=cs.PATH_AUTO, eps=EPS, bitset_budget=60e9, operand_budget=150e9, max_active=256,
+                 tick_macs=None, ticks_in_flight=2, max_jobs=1024, device="cuda"):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.eps = tuple(eps)
+        if path == cs.PATH_AUTO:  # the tensor-core path wherever the device has it
+            path = cs.PATH_MMA if cs.resolved_path(1 << 20) == cs.PATH_MMA else cs.PATH_POPC
+        self.count_path = path
+        self.bitset_budget = bitset_budget
+        self.operand_budget = operand_budget
+        self.max_active = max_active
+        # about 2 ms of count work per tick on either path
+        self.tick_macs = tick_macs or (2.0e12 if path == cs.PATH_MMA else 3.0e11)
+        self.ticks_in_flight = ticks_in_flight
+        self.max_jobs = max_jobs
+        self.prep_stream = torch.cuda.Stream(device=device)
+        self.count_stream = torch.cuda.Stream(device=device)
+        tb = cs.lib().cs_count_jobs_table_bytes(max_jobs, self.count_path)
+        wb = cs.lib().cs_count_jobs_workspace_bytes(max_jobs, self.count_path)
+        # one pinned table + device workspace per tick in flight
+        self.tables = [torch.empty(tb + 128, dtype=torch.uint8, pin_memory=True) for _ in range(ticks_in_flight)]
+        self.job_ws = [torch.empty(wb, dtype=torch.uint8, device=device) for _ in range(ticks_in_flight)]
+        self.slot_events = [None] * ticks_in_flight
+
+    # -- per request ------------------------------------------------------
+    def _admit(self, r, now):
+        torch = self.torch
+        r.state, r.t_admit = "prep", now
+        r.buf = cs.allocate(r.kind, r.n, device=self.device, path=cs.PATH_POPC)
+        r.total_items = cs.count_items(r.n, self.count_path)
+        with torch.cuda.stream(self.prep_stream):
+            st = self.prep_stream
+            cs.sprinkle(r.kind, r.n, r.seed, r.buf.coords, r.buf.workspace, st)
+            cs.causal_matrix(r.kind, r.n, r.buf.coords, r.buf.bits, st)
+            r.buf.hist.zero_()
+            if self.count_path == cs.PATH_MMA:
+                nb = cs.operands_bytes(r.n)
+                r.operands = torch.empty(nb + 1024, dtype=torch.uint8, device=self.device)
+                r.operands_ptr = (r.operands.data_ptr() + 1023) // 1024 * 1024
+                cs.prepare_operands(r.n, r.buf.bits, r.operands_ptr, nb, st)
+            r.prep_event = torch.cuda.Event()
+            r.prep_event.record(st)
+
+    def _finish(self, r):
+        """Queue actions and the copies home behind the request's last slice."""
+        torch = self.torch
+        st = self.count_stream
+        with torch.cuda.stream(st):
+            cs.action_device(r.buf.dim, r.n, r.buf.hist, list(self.eps), r.buf.actions, r.buf.bracket,
+                             r.buf.workspace, st)
+            r.hist_host = torch.empty(r.buf.hist.numel(), dtype=torch.int64, pin_memory=True)
+            r.actions_host = torch.empty(16, dtype=torch.float64, pin_memory=True)
+            r.hist_host.copy_(r.buf.hist, non_blocking=True)
+            r.actions_host.copy_(r.buf.actions, non_blocking=True)
+            r.done_event = torch.cuda.Event()
+            r.done_event.record(st)
+        r.state = "finish"
+
+    def _launch_tick(self, grants, slot):
+        torch = self.torch
+        st = self.count_stream
+        for r, _, _ in grants:
+            st.wait_event(r.prep_event)
+        jobs = []
+        for r, b, e in grants:
+            jobs.append(cs.CountJob(r.buf.bits.data_ptr(), r.n, r.buf.rw, r.buf.hist.data_ptr(),
+                                    r.operands_ptr or None, b, e))
+        tab = self.tables[slot]
+        tptr = (tab.data_ptr() + 127) // 128 * 128
+        ws = self.job_ws[slot]
+        cs.count_jobs(jobs, self.count_path, tptr, ws.data_ptr(), ws.numel(), st)
+        ev = torch.cuda.Event()
+        ev.record(st)
+        self.slot_events[slot] = ev
+        for r, b, e in grants:
+            r.next_item = e
+            if r.next_item >= r.total_items:
+                self._finish(r)
+
+    # -- main loop --------------------------------------------------------
+    def run(self, requests, realtime=True, poll_s=50e-6):
+        """Serve `requests` (sequence of (t_arrival, kind, n, seed)); returns stats and results."""
+        torch = self.torch
+        reqs = [Request(i, k, n, sd, t) for i, (t, k, n, sd) in enumerate(requests)]
+        for r in reqs:
+            r.bitset_bytes = cs.bitset_bytes(r.n)
+            r.operand_bytes = cs.operands_bytes(r.n) if self.count_path == cs.PATH_MMA else 0
+        queue = collections.deque(sorted(reqs, key=lambda r: (r.t_arrival, r.rid)))
+        active = []
+        used_b = used_o = 0
+        done = []
+        ticks = 0
+        t0 = time.perf_counter()
+        clock = (lambda: time.perf_counter() - t0) if realtime else (lambda: math.inf)
+        while queue or active:
+            now = clock()
+            progressed = False
+            # retire requests whose results are home
+            still = []
+            for r in active:
+                if r.state == "finish" and r.done_event.query():
+                    r.t_done = time.perf_counter() - t0
+                    r.state = "done"
+                    used_b -= r.bitset_bytes
+                    used_o -= r.operand_bytes
+                    r.buf = r.operands = None  # back to the allocator's pool
+                    done.append(r)
+                    progressed = True
+                else:
+                    still.append(r)
+            active = still
+            # admit arrivals
+            while queue and queue[0].t_arrival <= now and admit_ok(queue[0], used_b, used_o, len(active),
+                                                                  self.bitset_budget, self.operand_budget,
+                                                                  self.max_active):
+                r = queue.popleft()
+                self._admit(r, clock() if realtime else r.t_arrival)
+                used_b += r.bitset_bytes
+                used_o += r.operand_bytes
+                active.append(r)
+                progressed = True
+            # one tick over the prepared requests, when a tick slot is free
+            slot = next((i for i, ev in enumerate(self.slot_events) if ev is None or ev.query()), None)
+            if slot is not None:
+                ready = []
+                for r in active:
+                    if r.state == "prep" and r.prep_event.query():
+                        r.state = "count"
+                    if r.state == "count" and r.next_item < r.total_items:
+                        ready.append(r)
+                if ready:
+                    grants = plan_tick(ready[: self.max_jobs], self.tick_macs)
+                    self._launch_tick(grants, slot)
+                    ticks += 1
+                    progressed = True
+            if not progressed:
+                if not active and queue and realtime:
+                    time.sleep(max(0.0, min(queue[0].t_arrival - clock(), 0.01)))
+                else:
+                    time.sleep(poll_s)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        lat = sorted(r.t_done - r.t_arrival for r in done)
+        pairs = sum(int(r.hist_host.sum()) for r in done)
+
+        def pct(p):
+            return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)] if lat else math.nan
+
+        stats = {"requests": len(done), "wall_s": wall, "ticks": ticks,
+                 "throughput_req_s": len(done) / wall, "gpairs_s": pairs / wall / 1e9,
+                 "p50_ms": 1e3 * pct(50), "p99_ms": 1e3 * pct(99), "mean_ms": 1e3 * (sum(lat) / max(len(lat), 1)),
+                 "path": {cs.PATH_POPC: "popc", cs.PATH_MMA: "mma"}[self.count_path]}
+        results = {r.rid: (r.hist_host.numpy(), r.actions_host.numpy()[:len(self.eps)].copy()) for r in done}
+        return stats, results

@@ -102,3 +102,49 @@ def test_chain_local_action_closed_form(cslib):
         if n >= 4:
             s, b = cslib.action(4, n, h)
             assert b == n - 1 and abs(s - 4 / math.sqrt(6) * (n - 1)) <= 1e-15 * s
+
+
+def test_batch_sizes_on_host(cslib):
+    L = cslib.lib()
+    arr = cslib._desc_array([(1, 4096, 1), (2, 2048, 2), (0, 1, 3)])
+    assert L.cs_batch_hist_len(arr, 3) == 4095 + 2047 + 1
+    assert L.cs_batch_workspace_bytes(arr, 3, 1) > 0
+    assert L.cs_batch_workspace_bytes(arr, 3, 2) > L.cs_batch_workspace_bytes(arr, 3, 1)
+    bad = cslib._desc_array([(1, 8193, 1)])                      # n beyond CS_BATCH_MAX_N
+    assert L.cs_batch_workspace_bytes(bad, 1, 1) == 0 and L.cs_batch_hist_len(bad, 1) == -1
+    bad = cslib._desc_array([(7, 100, 1)])                       # unknown kind
+    assert L.cs_batch_workspace_bytes(bad, 1, 1) == 0
+
+
+def test_workload_generators_are_seeded():
+    from paper_1805_04463_gb300 import workloads
+    a, b = workloads.ensemble(), workloads.ensemble()
+    assert a == b and len(a) == 768
+    assert all(k == 1 for k, _, _ in a[:512]) and all(k == 2 for k, _, _ in a[512:])
+    assert abs(np.mean([n for _, n, _ in a[:512]]) - 4096) < 5 * 64 / np.sqrt(512)
+    r = workloads.serving_requests(duration_s=2.0)
+    assert r == workloads.serving_requests(duration_s=2.0)
+    assert all(1024 <= n < 65536 for _, _, n, _ in r)
+    assert abs(len(r) - 400) < 5 * 20
+
+
+def test_auto_path_table_round_trip(cslib):
+    old = cslib.get_auto_paths()
+    assert old[0][0] == 0
+    try:
+        cslib.set_auto_paths([(0, 1), (3000, 2), (50000, 1)])
+        assert cslib.get_auto_paths() == [(0, 1), (3000, 2), (50000, 1)]
+        for bad in ([(1, 1)], [(0, 1), (0, 2)], [(0, 3)], [(0, 1), (10, 2), (5, 1)]):
+            with pytest.raises(cslib.CsError):
+                cslib.set_auto_paths(bad)
+        assert cslib.get_auto_paths() == [(0, 1), (3000, 2), (50000, 1)]
+    finally:
+        cslib.set_auto_paths(old)
+
+
+def test_tuner_choice_logic():
+    from paper_1805_04463_gb300 import tune
+    m = [(1024, 0.1, 0.3), (2048, 0.3, 0.35), (4096, 1.0, 0.5), (8192, 6.0, 1.0), (65536, 900.0, 60.0)]
+    assert tune.choose(m) == [(0, 1), (4096, 2)]
+    assert tune.choose([(1024, 0.1, None)]) == [(0, 1)]
+    assert tune.choose([(1024, 0.5, 0.1), (2048, 0.4, 0.5), (4096, 2.0, 1.0)]) == [(0, 2), (2048, 1), (4096, 2)]

@@ -1,0 +1,100 @@
+"""Batched ensembles on the GPU: every set of a batch must give exactly the
+same coordinates-derived histogram, bracket and actions as the oracle (and
+as the single-set entry points), on both count paths, also when the batch
+launch is captured into a CUDA graph and replayed."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+EPS = (0.0, 0.05, 0.1, 0.2)
+TOL = 1e-12
+
+MIXED = [(0, 1, 11), (0, 2, 12), (2, 3, 13), (1, 127, 14), (0, 129, 15), (2, 1000, 16), (1, 2049, 17),
+         (0, 4096, 18), (2, 2048, 19), (1, 8192, 20), (0, 300, 21), (2, 4133, 22)]
+
+
+@pytest.fixture(scope="module")
+def cs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_04463_gb300 import build
+    build.build()
+    import paper_1805_04463_gb300 as m
+    return m
+
+
+def _check_against_oracle(cs, oracle, b):
+    hist = b.hist.cpu().numpy()
+    acts = b.actions.cpu().numpy()
+    brs = b.brackets.cpu().numpy()
+    for s, (kind, n, seed) in enumerate(b.sets):
+        c = oracle.sprinkle(kind, n, seed)
+        want = oracle.interval_abundance(oracle.causal_matrix(kind, c))
+        got = hist[b.hist_offsets[s]:b.hist_offsets[s] + want.size]
+        assert (got == want).all(), (s, kind, n)
+        d = 4 if kind == 2 else 2
+        for e, eps in enumerate(EPS):
+            so, bo = oracle.action(d, n, want, eps)
+            assert abs(acts[s, e] - so) <= TOL * max(1.0, abs(so)), (s, eps, acts[s, e], so)
+            assert brs[s] == bo
+
+
+@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+def test_mixed_batch_matches_oracle(cs, oracle, path):
+    import torch
+    b = cs.Batch(MIXED, path=path)
+    assert b.path == path
+    b.launch(EPS)
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    _check_against_oracle(cs, oracle, b)
+
+
+@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+def test_batch_equals_single_set_calls(cs, path):
+    import torch
+    sets = [(1, 4000 + 37 * s, 500 + s) for s in range(6)] + [(2, 2000 + 53 * s, 600 + s) for s in range(4)]
+    b = cs.Batch(sets, path=path)
+    b.launch(EPS)
+    torch.cuda.synchronize()
+    for s, (kind, n, seed) in enumerate(sets):
+        buf = cs.allocate(kind, n, path=path)
+        cs.run(buf, seed, eps=EPS)
+        torch.cuda.synchronize()
+        assert torch.equal(buf.hist, b.set_hist(s))
+        assert torch.equal(buf.actions[:len(EPS)].cpu(), b.actions[s].cpu())
+
+
+def test_batch_graph_replay(cs, oracle):
+    import torch
+    sets = [(1, 1500 + 100 * s, 900 + s) for s in range(5)] + [(2, 777, 950), (0, 1024, 951)]
+    b = cs.Batch(sets, path=0)
+    b.launch(EPS)  # warm-up outside capture (sets kernel attributes)
+    torch.cuda.synchronize()
+    ref = b.hist.clone()
+    b.hist.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            b.launch(EPS, stream=s)
+    for _ in range(3):
+        b.hist.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(b.hist, ref)
+    _check_against_oracle(cs, oracle, b)
+
+
+def test_ensemble_workload_sample(cs, oracle):
+    # The benchmark ensemble's first and last sets through the batch path.
+    import torch
+    from paper_1805_04463_gb300 import workloads
+    e = workloads.ensemble()
+    sets = e[:3] + e[-3:]
+    b = cs.Batch(sets, path=0)
+    b.launch(EPS)
+    torch.cuda.synchronize()
+    _check_against_oracle(cs, oracle, b)
