@@ -74,6 +74,8 @@ def _load():
         lib.oracle_interval_abundance_dominance2d.argtypes = [i64, vp, i64, i64, i64, vp, i64]
         lib.oracle_links_2d.argtypes = [i64, vp]
         lib.oracle_links_2d.restype = i64
+        lib.oracle_layer_sums.argtypes = [i64, vp, i64, vp, i32, vp]
+        lib.oracle_dalembertian.argtypes = [i32, i64, vp, vp, i32, ctypes.c_double, vp]
         lib.oracle_action.argtypes = [i32, i64, vp, i64, ctypes.c_double,
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
         _lib = lib
@@ -191,3 +193,24 @@ def action(dim_: int, n: int, hist: np.ndarray, eps: float = 0.0):
     _check(_load().oracle_action(dim_, n, _ptr(h) if h.size else None, h.size, float(eps),
                                  ctypes.byref(out), ctypes.byref(br)), "action")
     return out.value, br.value
+
+
+def layer_sums(bits: np.ndarray, kmax: int, phi=None) -> np.ndarray:
+    """S[m, j] = sum of phi(i) over i preceding j with |A_ij| = m, m = 0..kmax."""
+    n, w = bits.shape
+    out = np.zeros((kmax + 1, n), dtype=np.float64)
+    ph = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+    _check(_load().oracle_layer_sums(n, _ptr(bits), w, None if ph is None else _ptr(ph), kmax, _ptr(out)),
+           "layer_sums")
+    return out
+
+
+def dalembertian(dim_: int, layers: np.ndarray, ell: float = 1.0, phi=None) -> np.ndarray:
+    """B phi(j) (Eqs. b2d_local, b4d_local) from the layer sums."""
+    L = np.ascontiguousarray(layers, dtype=np.float64)
+    n = L.shape[1]
+    out = np.zeros(n, dtype=np.float64)
+    ph = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+    _check(_load().oracle_dalembertian(dim_, n, None if ph is None else _ptr(ph), _ptr(L), L.shape[0] - 1,
+                                       float(ell), _ptr(out)), "dalembertian")
+    return out

@@ -480,3 +480,61 @@ int oracle_action(int dim, int64_t n, const int64_t *hist, int64_t len, double e
     if (out) *out = (double)s;
     return OR_OK;
 }
+
+/* ------------------------------------------------- discrete d'Alembertian */
+
+/*
+ * Layer sums of the discrete d'Alembertian (Section "The Benincasa-Dowker
+ * Action", Eqs. b2d_local, b4d_local): for every element j and m = 0..kmax,
+ * out[m*n + j] = sum of phi(i) over the elements i preceding j with
+ * |A_ij| = m, i.e. over the inclusive order interval L_{m+1}(j) (Eq. IOIs).
+ * phi == NULL means phi = 1.  Sums are carried in binary128.
+ */
+int oracle_layer_sums(int64_t n, const uint64_t *bits, int64_t row_words, const double *phi, int kmax,
+                      double *out)
+{
+    if (n < 0 || kmax < 0 || !out) return OR_EINVAL;
+    q128 *acc = calloc((size_t)(kmax + 1) * (size_t)(n > 0 ? n : 1), sizeof *acc);
+    if (!acc) return OR_ENOMEM;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < n; j++) {
+        const uint64_t *rj = bits + j * row_words;
+        for (int64_t i = 0; i < j; i++) {
+            if (!or_bit(rj, i)) continue; /* i precedes j (time order) */
+            int64_t m = or_partial_inner_product(bits + i * row_words, rj, i + 1, j);
+            if (m <= kmax) acc[m * n + j] += phi ? (q128)phi[i] : (q128)1;
+        }
+    }
+    for (int64_t k = 0; k < (int64_t)(kmax + 1) * n; k++) out[k] = (double)acc[k];
+    free(acc);
+    return OR_OK;
+}
+
+/*
+ * B phi(j) from the layer sums S_m(j) (m = |A_ij|), Eqs. b2d_local and
+ * b4d_local with discreteness scale ell:
+ *   1+1: (2/ell^2) [-phi(j) + 2 (S_0 - 2 S_1 + S_2)]
+ *   3+1: (4/(ell^2 sqrt 6)) [-phi(j) + S_0 - 9 S_1 + 16 S_2 - 8 S_3]
+ * layers holds kmax+1 >= 3 (1+1) or >= 4 (3+1) rows of n values; phi == NULL
+ * means phi = 1.
+ */
+int oracle_dalembertian(int dim, int64_t n, const double *phi, const double *layers, int kmax, double ell,
+                        double *out)
+{
+    if ((dim != 2 && dim != 4) || n < 0 || !layers || !out || !(ell > 0)) return OR_EINVAL;
+    if (kmax < (dim == 2 ? 2 : 3)) return OR_EINVAL;
+    q128 l2 = (q128)ell * (q128)ell;
+    for (int64_t j = 0; j < n; j++) {
+        q128 p = phi ? (q128)phi[j] : (q128)1;
+        q128 s0 = layers[j], s1 = layers[n + j], s2 = layers[2 * n + j];
+        q128 b;
+        if (dim == 2) {
+            b = (q128)2 / l2 * (-p + 2 * (s0 - 2 * s1 + s2));
+        } else {
+            q128 s3 = layers[3 * n + j];
+            b = (q128)4 / (l2 * or_qsqrt((q128)6)) * (-p + s0 - 9 * s1 + 16 * s2 - 8 * s3);
+        }
+        out[j] = (double)b;
+    }
+    return OR_OK;
+}

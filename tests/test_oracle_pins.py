@@ -361,3 +361,57 @@ def test_sprinkle_follows_generator_spec(oracle, kind, n, seed):
         order = sorted(range(n), key=lambda e: (pts[e][0], e))
         for q in range(4):
             assert c[q].tolist() == [pts[e][q] for e in order]
+
+
+# ------------------------------------------------- discrete d'Alembertian
+
+def test_layer_sums_and_dalembertian_by_hand(oracle):
+    with open(os.path.join(GOLDEN, "tiny_posets.json")) as f:
+        g = json.load(f)["layers"]
+    c = _coords_2d_order(g["v"])
+    bits = oracle.causal_matrix(0, c)
+    S = oracle.layer_sums(bits, 3, np.array(g["phi"]))
+    assert S.tolist() == [[float(x) for x in row] for row in g["S"]]
+    assert oracle.dalembertian(2, S, 1.0, np.array(g["phi"])).tolist() == g["B2"]
+    b4 = oracle.dalembertian(4, S, 1.0, np.array(g["phi"]))
+    assert np.allclose(b4, np.array(g["B4_bracket"]) * 4 / math.sqrt(6), rtol=1e-15, atol=0)
+    # the discreteness scale enters as 1/ell^2
+    assert np.allclose(oracle.dalembertian(2, S, 0.5, np.array(g["phi"])), 4 * np.array(g["B2"]), rtol=1e-15)
+
+
+def test_layer_sums_chain_closed_form(oracle):
+    # In a chain L_{m+1}(j) = {j - m - 1}: S_m(j) = phi(j - m - 1).
+    n = 50
+    chain = _coords_2d_order(np.arange(n))
+    phi = np.arange(n, dtype=np.float64) * 1.5 + 0.25
+    S = oracle.layer_sums(oracle.causal_matrix(0, chain), 4, phi)
+    for m in range(5):
+        want = np.zeros(n)
+        want[m + 1:] = phi[:n - m - 1]
+        assert (S[m] == want).all()
+    anti = _coords_2d_order(np.arange(n)[::-1].copy())
+    S0 = oracle.layer_sums(oracle.causal_matrix(0, anti), 3, phi)
+    assert not S0.any()
+    assert (oracle.dalembertian(2, S0, 2.0, phi) == -2 / 4.0 * phi).all()   # B = -(2/ell^2) phi
+
+
+@pytest.mark.parametrize("kind,n", [(0, 300), (2, 250), (1, 200)])
+def test_layer_sums_match_abundances_and_definition(oracle, kind, n):
+    c = oracle.sprinkle(kind, n, 1234 + n)
+    bits = oracle.causal_matrix(kind, c)
+    S = oracle.layer_sums(bits, 5)
+    h = oracle.interval_abundance_naive(kind, c)
+    assert (S.sum(axis=1) == h[:6]).all()            # sum_j |L_{m+1}(j)| = N_m
+    if kind == 0:
+        # from the definition for 2D orders, independently of bitsets
+        v = c[1].astype(np.int64)
+        phi = np.random.default_rng(0).normal(size=n)
+        Sp = oracle.layer_sums(bits, 2, phi)
+        want = np.zeros((3, n))
+        for j in range(n):
+            for i in range(j):
+                if v[i] < v[j]:
+                    m = int(((v[i + 1:j] > v[i]) & (v[i + 1:j] < v[j])).sum())
+                    if m <= 2:
+                        want[m, j] += phi[i]
+        assert np.allclose(Sp, want, rtol=1e-14, atol=1e-14)
