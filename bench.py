@@ -136,6 +136,25 @@ def roofline_for(resolved, n, count_s, peaks, src, sm_count):
                            f"(sm_max_mhz, {src})"}
 
 
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_count_mma__2d_order_131072__dram.md")
+MMA_SOURCES = [os.path.join(ROOT, "paper_1805_04463_gb300", "csrc", f)
+               for f in ("cs_count_mma.cu", "cs_internal.cuh", "cs_kernels.cuh")]
+
+
+def recorded_traffic():
+    """DRAM bytes per full-size k_count_mma launch from the committed ncu record,
+    or None when the kernel sources changed since it was captured."""
+    import hashlib
+    try:
+        rec = dict(line.split(":", 1) for line in open(TRAFFIC_RECORD) if line.startswith(("traffic_", "kernel_")))
+        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in MMA_SOURCES)).hexdigest()[:16]
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_sources_sha256_16", "").strip() != h:
+        return None
+    return float(rec["traffic_bytes_per_launch"])
+
+
 def compare_paths(cs, torch, buf, n, stream):
     """Count-call time of each path on the same bitset (1 warm-up + 1 timed, CUDA events)."""
     out = {}
@@ -394,6 +413,12 @@ def main():
     roofline = roofline_for(cs.resolved_path(n, path), n, statistics.mean(count_ms) / 1e3, peaks, src,
                             torch.cuda.get_device_properties(local).multi_processor_count)
     roofline["count_ms"] = statistics.mean(count_ms)
+    if roofline["bound"] == "tensor" and args.workload == "2d_order_131072":
+        tr = recorded_traffic()
+        roofline["traffic"] = tr
+        roofline["traffic_source"] = ("profiles/k_count_mma__2d_order_131072__dram.md (dram__bytes_read.sum + "
+                                      "dram__bytes_write.sum, one full-size launch)" if tr else
+                                      "no capture for the current kernel sources")
     if args.compare_paths:
         roofline["paths_ms"] = compare_paths(cs, torch, buf, n, stream)
     line = {

@@ -133,7 +133,7 @@ int cs_resolved_path(int64_t n, int path);
  * The CS_PATH_AUTO table, process-wide: entry e selects paths[e]
  * (CS_PATH_POPC or CS_PATH_MMA) for n_min[e] <= n < n_min[e+1].  n_min must
  * start at 0 and increase; at most 16 entries.  The default is {0: POPC,
- * 8192: MMA}; the autotuner (paper_1805_04463_gb300/tune.py) installs
+ * 1024: MMA}; the autotuner (paper_1805_04463_gb300/tune.py) installs
  * measured thresholds.  Errors: CS_EINVAL.
  */
 int cs_set_auto_paths(const int64_t *n_min, const int *paths, int count);
@@ -163,6 +163,32 @@ size_t cs_interval_abundance_workspace(int64_t n, int path);
 int cs_interval_abundance(int64_t n, const uint64_t *bits_dev, int64_t row_words,
                           int64_t *hist_dev, int path,
                           void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/*
+ * Interval abundances plus the layer sums of the discrete d'Alembertian
+ * (Section "The Benincasa-Dowker Action", Eqs. b2d_local, b4d_local): in the
+ * same pass as cs_interval_abundance, for every element j and m = 0..kmax,
+ * layer_dev[m*n + j] = sum of phi(i) over the elements i preceding j with
+ * |A_ij| = m, i.e. over the inclusive order interval L_{m+1}(j).  phi_dev
+ * (n doubles) may be NULL for phi = 1, in which case the sums are exact
+ * element counts; otherwise they are double sums in atomic order.
+ * layer_dev: (kmax+1) * n doubles, zeroed by the callee; 0 <= kmax <= 15.
+ * Workspace and errors as cs_interval_abundance.
+ */
+int cs_layer_sums(int64_t n, const uint64_t *bits_dev, int64_t row_words, int64_t *hist_dev, int path,
+                  const double *phi_dev, int kmax, double *layer_dev, void *workspace_dev,
+                  size_t workspace_bytes, void *stream);
+
+/*
+ * The discrete d'Alembertian B phi(j) for every element from the layer sums
+ * (kmax >= 2 in 1+1, >= 3 in 3+1), with discreteness scale ell:
+ *   1+1 (Eq. b2d_local): (2/ell^2) [-phi(j) + 2 (S_0 - 2 S_1 + S_2)]
+ *   3+1 (Eq. b4d_local): (4/(ell^2 sqrt 6)) [-phi(j) + S_0 - 9 S_1 + 16 S_2 - 8 S_3]
+ * phi_dev may be NULL (phi = 1: B 1 is the element's curvature estimate).
+ * out_dev: n doubles.  Asynchronous.  Errors: CS_EINVAL, CS_ECUDA.
+ */
+int cs_dalembertian(int dim, int64_t n, const double *phi_dev, const double *layer_dev, int kmax,
+                    double ell, double *out_dev, void *stream);
 
 /*
  * Read (synchronously: waits for `stream`) and clear the status word that

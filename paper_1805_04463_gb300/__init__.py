@@ -21,7 +21,7 @@ __all__ = [
     "CsError", "lib", "dim", "coords_bytes", "row_words", "bitset_bytes", "hist_len",
     "sprinkle_workspace_bytes", "interval_abundance_workspace", "resolved_path", "action_workspace_bytes",
     "set_auto_paths", "get_auto_paths",
-    "sprinkle", "sprinkle_noalloc", "causal_matrix", "interval_abundance", "workspace_status", "action", "action_device",
+    "sprinkle", "sprinkle_noalloc", "causal_matrix", "layer_sums", "dalembertian", "interval_abundance", "workspace_status", "action", "action_device",
     "evaluate", "Buffers", "allocate", "run", "SetDesc", "Batch", "CountJob", "count_items",
     "operands_bytes", "prepare_operands", "count_jobs",
 ]
@@ -74,6 +74,8 @@ def lib() -> ctypes.CDLL:
             "cs_get_auto_paths": ([vp, vp, i32], i32),
             "cs_interval_abundance": ([i64, vp, i64, vp, i32, vp, sz, vp], i32),
             "cs_workspace_status": ([vp, vp], i32),
+            "cs_layer_sums": ([i64, vp, i64, vp, i32, vp, i32, vp, vp, sz, vp], i32),
+            "cs_dalembertian": ([i32, i64, vp, vp, i32, ctypes.c_double, vp, vp], i32),
             "cs_action": ([i32, i64, vp, i64, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int64)], i32),
             "cs_action_workspace_bytes": ([], sz),
             "cs_action_device": ([i32, i64, vp, i64, vp, i32, vp, vp, vp, sz, vp], i32),
@@ -199,6 +201,18 @@ def interval_abundance(n, bits, hist, path=PATH_AUTO, workspace=None, stream=Non
     """cs_interval_abundance: N_k histogram (int64, hist_len(n)) into `hist`."""
     _check(lib().cs_interval_abundance(n, _ptr(bits), bits.shape[-1], _ptr(hist), path, _ptr(workspace),
                                        _nbytes(workspace), _stream(stream)), "cs_interval_abundance")
+
+
+def layer_sums(n, bits, hist, layer, kmax, phi=None, path=PATH_AUTO, workspace=None, stream=None):
+    """cs_layer_sums: histogram plus d'Alembertian layer sums layer[(kmax+1), n] (float64)."""
+    _check(lib().cs_layer_sums(n, _ptr(bits), bits.shape[-1], _ptr(hist), path, _ptr(phi), kmax, _ptr(layer),
+                               _ptr(workspace), _nbytes(workspace), _stream(stream)), "cs_layer_sums")
+
+
+def dalembertian(dim_, n, layer, out, ell=1.0, phi=None, stream=None):
+    """cs_dalembertian: B phi(j) for every element into the float64 tensor `out`."""
+    _check(lib().cs_dalembertian(dim_, n, _ptr(phi), _ptr(layer), layer.shape[0] - 1, float(ell), _ptr(out),
+                                 _stream(stream)), "cs_dalembertian")
 
 
 def workspace_status(workspace, stream=None) -> int:

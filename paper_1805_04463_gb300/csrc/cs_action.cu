@@ -66,7 +66,35 @@ __global__ void k_action_final(int dim, int64_t n, const int64_t* __restrict__ h
     out[e] = s.hi + s.lo;
 }
 
+// B phi(j) from the layer sums (Eqs. b2d_local, b4d_local), one thread per element.
+__global__ void k_dalembertian(int dim, int64_t n, const double* __restrict__ phi, const double* __restrict__ layer,
+                               double scale, double* __restrict__ out) {
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        const double p = phi ? phi[j] : 1.0;
+        const double s0 = layer[j], s1 = layer[n + j], s2 = layer[2 * n + j];
+        double b;
+        if (dim == 2) {
+            b = -p + 2.0 * (s0 - 2.0 * s1 + s2);
+        } else {
+            const double s3 = layer[3 * n + j];
+            b = -p + s0 - 9.0 * s1 + 16.0 * s2 - 8.0 * s3;
+        }
+        out[j] = scale * b;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_dalembertian(int dim, int64_t n, const double* phi, const double* layer, double ell, double* out,
+                                cudaStream_t st) {
+    const dd l2 = dd_two_prod(ell, ell);
+    const dd c = dim == 2 ? dd_div(dd_from(2.0), l2) : dd_div(dd_from(4.0), dd_mul(l2, dd_sqrt(dd_from(6.0))));
+    int64_t g = (n + 255) / 256;
+    if (g > int64_t(device_sm_count()) * 8) g = int64_t(device_sm_count()) * 8;
+    if (g < 1) g = 1;
+    k_dalembertian<<<unsigned(g), 256, 0, st>>>(dim, n, phi, layer, c.hi + c.lo, out);
+    return cudaGetLastError();
+}
 
 size_t action_workspace_bytes() { return sizeof(WsHeader) + size_t(kActBlocks) * kMaxEps * sizeof(dd); }
 

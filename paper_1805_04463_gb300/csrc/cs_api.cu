@@ -25,12 +25,12 @@ inline cudaError_t clear_status(void* ws, cudaStream_t st) {
 }  // namespace
 
 // CS_PATH_AUTO table: entry e applies from size n_min[e] up to the next
-// entry.  The default reflects that the tensor-core path pays a fixed O(n^2)
-// operand expansion and wins from a few thousand elements up; an autotuner
-// replaces it with measured thresholds (cs_set_auto_paths).
+// entry.  The default follows GB300 measurements (the tensor-core path wins
+// from n = 1024 up: 0.042 vs 0.050 ms there, 32 vs 357 ms at n = 65536); the
+// autotuner replaces it with thresholds measured on the running device.
 constexpr int kMaxAuto = 16;
 std::mutex g_auto_mu;
-int64_t g_auto_n[kMaxAuto] = {0, 8192};
+int64_t g_auto_n[kMaxAuto] = {0, 1024};
 int g_auto_p[kMaxAuto] = {CS_PATH_POPC, CS_PATH_MMA};
 int g_auto_count = 2;
 
@@ -148,6 +148,35 @@ int cs_interval_abundance(int64_t n, const uint64_t* bits_dev, int64_t row_words
         e = p == CS_PATH_MMA ? launch_count_mma(n, bits_dev, row_words, hist_dev, workspace_dev, st)
                              : launch_count_popc(n, bits_dev, row_words, hist_dev, workspace_dev, st);
     return from_cuda(e);
+}
+
+int cs_layer_sums(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_t* hist_dev, int path,
+                  const double* phi_dev, int kmax, double* layer_dev, void* workspace_dev, size_t workspace_bytes,
+                  void* stream) {
+    if (!valid_n(n) || !bits_dev || !aligned(bits_dev, 128) || !hist_dev || !aligned(hist_dev, 8) ||
+        row_words < cs_row_words(n) || row_words % 16 != 0 || !workspace_dev || !aligned(workspace_dev, 256) ||
+        path < CS_PATH_AUTO || path > CS_PATH_MMA || kmax < 0 || kmax > 15 || !layer_dev ||
+        !aligned(layer_dev, 8) || (phi_dev && !aligned(phi_dev, 8)))
+        return CS_EINVAL;
+    if (workspace_bytes < cs_interval_abundance_workspace(n, path)) return CS_ENOMEM;
+    const int p = resolve_path(n, path);
+    if (p == CS_PATH_MMA && !device_has_tcgen05()) return CS_EUNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = clear_status(workspace_dev, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(layer_dev, 0, size_t(kmax + 1) * size_t(n) * 8, st);
+    if (e == cudaSuccess)
+        e = p == CS_PATH_MMA
+                ? launch_count_mma(n, bits_dev, row_words, hist_dev, workspace_dev, st, phi_dev, layer_dev, kmax)
+                : launch_count_popc(n, bits_dev, row_words, hist_dev, workspace_dev, st, phi_dev, layer_dev, kmax);
+    return from_cuda(e);
+}
+
+int cs_dalembertian(int dim, int64_t n, const double* phi_dev, const double* layer_dev, int kmax, double ell,
+                    double* out_dev, void* stream) {
+    if ((dim != 2 && dim != 4) || !valid_n(n) || !layer_dev || !out_dev || !(ell > 0.0) ||
+        kmax < (dim == 2 ? 2 : 3))
+        return CS_EINVAL;
+    return from_cuda(launch_dalembertian(dim, n, phi_dev, layer_dev, ell, out_dev, static_cast<cudaStream_t>(stream)));
 }
 
 int cs_workspace_status(void* workspace_dev, void* stream) {

@@ -14,11 +14,13 @@
 //
 // Kernel.  A persistent grid (one CTA per SM) walks 128 x 256 output tiles
 // (128 i-rows, 256 j-rows, i-block at or before the j-block), rasterised in
-// 8 x 8 blocks of 256 x 256 supertiles served widest band first and
-// statically strided over CTAs, so concurrent CTAs share operand panels in
+// 8 x 8 blocks of 256 x 256 supertiles served widest band first from one
+// global queue, so the CTAs running at any moment share operand panels in
 // L2.  Warp roles:
-//   warp 0      TMA producer: 128-row A slab and 256-row B slab of 128 K-bytes
-//               per stage (128B swizzle) into a 4-stage shared-memory ring;
+//   warp 0      queue and TMA producer: takes the next item, hands its index
+//               to the other roles through a 4-slot shared ring, and loads a
+//               128-row A slab and a 256-row B slab of 128 K-bytes per stage
+//               (128B swizzle) into a 4-stage shared-memory ring;
 //   warp 1      TMEM allocator and MMA issuer: 4 x tcgen05.mma (M128 N256 K32)
 //               per stage into one of two TMEM accumulators (2 x 256 columns);
 //   warps 2..5  epilogue: tcgen05.ld of the finished accumulator (one TMEM
@@ -45,6 +47,7 @@ constexpr int kHistBins = 8192;
 constexpr int kThreads = 192;
 constexpr int kTmemCols = 512;           // two 256-column FP32 accumulators
 constexpr uint32_t kIdesc = idesc_f8_f32(kBM, kBN);
+constexpr int kRing = 4;                 // item indices in flight between the roles
 constexpr int kSmemBytes = kStages * kStageBytes + kHistBins * 4 + 256 + 1024;
 constexpr uint8_t kOne = 0x38;           // 1.0 in FP8 E4M3
 constexpr CUtensorMapSwizzle kSwizzle = kBK == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
@@ -159,6 +162,9 @@ struct MmaView {
     int64_t n, row_words, nsb, kblocks;
     unsigned long long* hist;
     int64_t hist_len;
+    const double* phi;  // d'Alembertian field (NULL = 1)
+    double* layer;      // layer sums [kmax+1][n], or NULL
+    int kmax;           // < 0: no layer sums
 };
 
 // Work source: a single set passed in kernel parameters.
@@ -193,7 +199,7 @@ struct MmaMulti {
         const MmaSetEntry& e = sets[s];
         return MmaView{&e.mapU, &e.mapL, e.bits, e.n, e.row_words, e.nsb, e.kblocks,
                        reinterpret_cast<unsigned long long*>(hist_base + uintptr_t(e.hist_off)),
-                       e.n > 1 ? e.n - 1 : 1};
+                       e.n > 1 ? e.n - 1 : 1, e.phi, e.layer, int(e.kmax)};
     }
 };
 
@@ -232,7 +238,10 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
     uint64_t* tfull = empty + kStages;
     uint64_t* tempty = tfull + 2;
     uint64_t* ebar = tempty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ebar + 1);
+    uint64_t* ifull = ebar + 1;         // item ring: slot published by the producer
+    uint64_t* iempty = ifull + kRing;   // item ring: slot read by the MMA thread and all epilogue threads
+    volatile int64_t* ring = reinterpret_cast<volatile int64_t*>(iempty + kRing);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(const_cast<int64_t*>(ring) + kRing);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -249,6 +258,10 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             mbar_init(&tempty[b], 4 * 32);
         }
         mbar_init(ebar, 4 * 32);
+        for (int r = 0; r < kRing; ++r) {
+            mbar_init(&ifull[r], 1);
+            mbar_init(&iempty[r], 1 + 4 * 32);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -263,11 +276,20 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------- TMA producer
+        // Pulls items from the global queue (consecutive indices are
+        // raster-local, so the CTAs running at any moment share operand
+        // panels in L2) and publishes each index to the other roles.
         uint32_t s = 0, ph = 0, issued = 0;
         bool ok = true;
         int cur = -1;
         MmaView v{};
-        for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        for (uint32_t q = 0; ok; ++q) {
+            const uint32_t slot = q % kRing, use = (q / kRing) & 1u;
+            if (!mbar_wait_or_abort(&iempty[slot], use ^ 1u, hdr, abort_flag)) { ok = false; break; }
+            const int64_t t = int64_t(atomicAdd(&hdr->counter, 1ull));
+            ring[slot] = t;
+            mbar_arrive(&ifull[slot]);
+            if (t >= total) break;
             int64_t local;
             const int sidx = src.set_of(t, local);
             if (sidx != cur) {
@@ -300,7 +322,12 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         bool ok = true;
         int cur = -1;
         MmaView v{};
-        for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        for (uint32_t q = 0; ok; ++q) {
+            const uint32_t slot = q % kRing, use = (q / kRing) & 1u;
+            if (!mbar_wait_or_abort(&ifull[slot], use, hdr, abort_flag)) break;
+            const int64_t t = ring[slot];
+            mbar_arrive(&iempty[slot]);
+            if (t >= total) break;
             int64_t local;
             const int sidx = src.set_of(t, local);
             if (sidx != cur) {
@@ -309,9 +336,9 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             }
             Item it;
             if (!decode_item(local, v.nsb, v.n, v.kblocks, it)) continue;
-            const uint32_t buf = uint32_t(local_count & 1), use = uint32_t((local_count >> 1) & 1);
+            const uint32_t buf = uint32_t(local_count & 1), bu = uint32_t((local_count >> 1) & 1);
             ++local_count;
-            if (!mbar_wait_or_abort(&tempty[buf], use ^ 1u, hdr, abort_flag)) break;
+            if (!mbar_wait_or_abort(&tempty[buf], bu ^ 1u, hdr, abort_flag)) break;
             tc_fence_after();
             const uint32_t d = tmem_base + buf * kBN;
             for (int64_t kb = it.kb0; kb < it.kb1; ++kb) {
@@ -337,7 +364,12 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         uint32_t ephase = 0;
         bool ok = true;
         MmaView v{};
-        for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        for (uint32_t qi = 0; ok; ++qi) {
+            const uint32_t slot = qi % kRing, ru = (qi / kRing) & 1u;
+            if (!mbar_wait_or_abort(&ifull[slot], ru, hdr, abort_flag)) { ok = false; break; }
+            const int64_t t = ring[slot];
+            mbar_arrive(&iempty[slot]);
+            if (t >= total) break;
             int64_t local;
             const int sidx = src.set_of(t, local);
             if (sidx != cur) {
@@ -374,6 +406,8 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                             atomicAdd(&shist[k], 1u);
                         else
                             atomicAdd(&v.hist[k], 1ull);
+                        if (int(k) <= v.kmax)  // i is in L_{k+1}(j)
+                            atomicAdd(&v.layer[int64_t(k) * v.n + j], v.phi ? __ldg(v.phi + i) : 1.0);
                     }
                 }
             }
@@ -392,8 +426,10 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
 __global__ void __launch_bounds__(kThreads, 1)
     k_count_mma(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mapL,
                 const uint64_t* __restrict__ bits, int64_t n, int64_t row_words, int64_t nsb, int64_t nitems,
-                int64_t kblocks, unsigned long long* __restrict__ hist, int64_t hist_len, WsHeader* hdr) {
-    const MmaSingle src{MmaView{&mapU, &mapL, bits, n, row_words, nsb, kblocks, hist, hist_len}, nitems};
+                int64_t kblocks, unsigned long long* __restrict__ hist, int64_t hist_len, const double* phi,
+                double* layer, int kmax, WsHeader* hdr) {
+    const MmaSingle src{MmaView{&mapU, &mapL, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax},
+                        nitems};
     mma_body(src, hdr);
 }
 
@@ -435,6 +471,7 @@ int64_t mma_items(int64_t n) {
 
 CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words, uint8_t* U,
                         uint8_t* L) {
+    e->kmax = -1;
     e->bits = bits;
     e->n = n;
     e->row_words = row_words;
@@ -470,7 +507,8 @@ cudaError_t launch_expand_multi(const MmaSetEntry* sets_dev, int nsets, int64_t 
 cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64_t nitems, uintptr_t hist_base,
                                    WsHeader* hdr, int max_ctas, cudaStream_t st) {
     if (nitems < 1) return cudaSuccess;
-    cudaError_t err;
+    cudaError_t err = cudaMemsetAsync(&hdr->counter, 0, sizeof(hdr->counter), st);
+    if (err != cudaSuccess) return err;
     int dev = 0;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if (dev >= 0 && dev < 64 && !g_attr_multi_set[dev]) {
@@ -485,11 +523,12 @@ cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64
 }
 
 cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* workspace,
-                             cudaStream_t st) {
+                             cudaStream_t st, const double* phi, double* layer, int kmax) {
     WsHeader* hdr = static_cast<WsHeader*>(workspace);
     const int64_t hist_len = n > 1 ? n - 1 : 1;
     cudaError_t err = cudaMemsetAsync(hist, 0, size_t(hist_len) * 8, st);
     if (err != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(&hdr->counter, 0, sizeof(hdr->counter), st)) != cudaSuccess) return err;
     if (n < 2) return cudaSuccess;
     const MmaLayout lay = mma_layout(n);
     uint8_t* U = static_cast<uint8_t*>(workspace) + lay.u;
@@ -522,7 +561,7 @@ cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words,
     if (grid > nitems) grid = nitems;
     k_count_mma<<<unsigned(grid), kThreads, kSmemBytes, st>>>(mapU, mapL, bits, n, row_words, nsb, nitems, kblocks,
                                                               reinterpret_cast<unsigned long long*>(hist), hist_len,
-                                                              hdr);
+                                                              phi, layer, kmax, hdr);
     return cudaGetLastError();
 }
 

@@ -101,6 +101,9 @@ struct PopcView {
     int64_t n, row_words, nb;
     unsigned long long* hist;
     int64_t hist_len;
+    const double* phi;  // d'Alembertian field (NULL = 1)
+    double* layer;      // layer sums [kmax+1][n], or NULL
+    int kmax;           // < 0: no layer sums
 };
 
 // Work source: a single set passed in kernel parameters.
@@ -135,7 +138,7 @@ struct PopcMulti {
         const PopcSetEntry& e = sets[s];
         return PopcView{&e.map, e.bits, e.n, e.row_words, e.nb,
                         reinterpret_cast<unsigned long long*>(hist_base + uintptr_t(e.hist_off)),
-                        e.n > 1 ? e.n - 1 : 1};
+                        e.n > 1 ? e.n - 1 : 1, e.phi, e.layer, int(e.kmax)};
     }
 };
 
@@ -266,6 +269,8 @@ __device__ __forceinline__ void popc_body(const Src& src, WsHeader* hdr) {
                         atomicAdd(&shist[k], 1u);
                     else
                         atomicAdd(&v.hist[k], 1ull);
+                    if (int(k) <= v.kmax)  // i is in L_{k+1}(j)
+                        atomicAdd(&v.layer[int64_t(k) * v.n + j], v.phi ? __ldg(v.phi + i) : 1.0);
                 }
             }
         }
@@ -276,8 +281,8 @@ __device__ __forceinline__ void popc_body(const Src& src, WsHeader* hdr) {
 __global__ void __launch_bounds__(kThreads, 1)
     k_count_popc(const __grid_constant__ CUtensorMap tmap, const uint64_t* __restrict__ bits, int64_t n,
                  int64_t row_words, int64_t nb, int64_t ntiles, unsigned long long* __restrict__ hist,
-                 int64_t hist_len, WsHeader* hdr) {
-    const PopcSingle src{PopcView{&tmap, bits, n, row_words, nb, hist, hist_len}, ntiles};
+                 int64_t hist_len, const double* phi, double* layer, int kmax, WsHeader* hdr) {
+    const PopcSingle src{PopcView{&tmap, bits, n, row_words, nb, hist, hist_len, phi, layer, kmax}, ntiles};
     popc_body(src, hdr);
 }
 
@@ -299,6 +304,7 @@ int64_t popc_tiles(int64_t n) {
 }
 
 void popc_fill_entry(PopcSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words) {
+    e->kmax = -1;
     e->bits = bits;
     e->n = n;
     e->row_words = row_words;
@@ -332,7 +338,7 @@ cudaError_t launch_count_popc_multi(const PopcSetEntry* sets_dev, int nsets, int
 size_t popc_workspace_bytes(int64_t) { return sizeof(WsHeader); }
 
 cudaError_t launch_count_popc(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist,
-                              void* workspace, cudaStream_t st) {
+                              void* workspace, cudaStream_t st, const double* phi, double* layer, int kmax) {
     WsHeader* hdr = static_cast<WsHeader*>(workspace);
     const int64_t hist_len = n > 1 ? n - 1 : 1;
     cudaError_t err = cudaMemsetAsync(hist, 0, size_t(hist_len) * 8, st);
@@ -357,7 +363,8 @@ cudaError_t launch_count_popc(int64_t n, const uint64_t* bits, int64_t row_words
     int64_t grid = device_sm_count();
     if (grid > ntiles) grid = ntiles;
     k_count_popc<<<unsigned(grid), kThreads, kSmemBytes, st>>>(
-        map, bits, n, row_words, nb, ntiles, reinterpret_cast<unsigned long long*>(hist), hist_len, hdr);
+        map, bits, n, row_words, nb, ntiles, reinterpret_cast<unsigned long long*>(hist), hist_len, phi, layer, kmax,
+        hdr);
     return cudaGetLastError();
 }
 

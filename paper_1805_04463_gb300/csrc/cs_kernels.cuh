@@ -24,6 +24,9 @@ struct alignas(128) PopcSetEntry {
     int64_t item_begin;   // first tile of this set in the concatenated tile list
     int64_t item_offset;  // tile index (within the set) of that first tile
     int64_t hist_off;     // byte offset of this set's histogram from the launch's histogram base
+    const double* phi;    // d'Alembertian layer sums: field (NULL = 1),
+    double* layer;        //   sums [kmax+1][n],
+    int64_t kmax;         //   highest layer (< 0: none)
 };
 size_t popc_workspace_bytes(int64_t n);
 int64_t popc_tiles(int64_t n);
@@ -32,7 +35,8 @@ CUresult popc_encode_map(CUtensorMap* map, const uint64_t* bits, int64_t n, int6
 cudaError_t launch_count_popc_multi(const PopcSetEntry* sets_dev, int nsets, int64_t ntiles, uintptr_t hist_base,
                                     WsHeader* hdr, int max_ctas, cudaStream_t st);
 cudaError_t launch_count_popc(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist,
-                              void* workspace, cudaStream_t st);
+                              void* workspace, cudaStream_t st, const double* phi = nullptr, double* layer = nullptr,
+                              int kmax = -1);
 
 // cs_count_mma.cu
 // One set of a multi-set tensor-core count: TMA maps of its U and L operands,
@@ -49,6 +53,9 @@ struct alignas(128) MmaSetEntry {
     uint8_t* L;
     int64_t kpad;
     int64_t word_begin;  // first 16-column piece of this set in the concatenated expand range
+    const double* phi;   // d'Alembertian layer sums: field (NULL = 1),
+    double* layer;       //   sums [kmax+1][n],
+    int64_t kmax;        //   highest layer (< 0: none)
 };
 size_t mma_workspace_bytes(int64_t n);
 int64_t mma_items(int64_t n);
@@ -62,7 +69,8 @@ cudaError_t launch_expand_multi(const MmaSetEntry* sets_dev, int nsets, int64_t 
 cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64_t nitems, uintptr_t hist_base,
                                    WsHeader* hdr, int max_ctas, cudaStream_t st);
 cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist,
-                             void* workspace, cudaStream_t st);
+                             void* workspace, cudaStream_t st, const double* phi = nullptr, double* layer = nullptr,
+                             int kmax = -1);
 
 // Path chosen for CS_PATH_AUTO at size n.
 int resolve_path(int64_t n, int path);
@@ -73,6 +81,9 @@ int action_host(int dim, int64_t n, const int64_t* hist, int64_t len, double eps
 size_t action_workspace_bytes();
 cudaError_t launch_action_device(int dim, int64_t n, const int64_t* hist, int64_t len, const double* eps,
                                  int n_eps, double* out, int64_t* bracket, void* workspace, cudaStream_t st);
+
+cudaError_t launch_dalembertian(int dim, int64_t n, const double* phi, const double* layer, double ell, double* out,
+                                cudaStream_t st);
 
 // Device properties cached per device.
 int device_sm_count();

@@ -102,3 +102,26 @@ def test_item_shards_sum_to_the_full_count(cs, path):
             cs.prepare_operands(n, b.bits, ptr, nb)
         total += replicas.count_sharded(cs, b, path, 3, rank, dist=None, operands_ptr=ptr)
     assert torch.equal(total, full.hist)
+
+
+def test_autotuner_installs_a_measured_table(cs, tmp_path):
+    import torch
+    from paper_1805_04463_gb300 import tune
+    old = cs.get_auto_paths()
+    try:
+        table, m = tune.autotune(sizes=(1024, 4096, 16384), path=str(tmp_path / "tune.json"))
+        assert cs.get_auto_paths() == [tuple(x) for x in table]
+        assert [x[0] for x in m] == [1024, 4096, 16384] and all(x[1] > 0 and x[2] > 0 for x in m)
+        cs.set_auto_paths(old)
+        assert tune.load(str(tmp_path / "tune.json")) == [tuple(x) for x in table]
+        # AUTO under the tuned table gives the same counts as both explicit paths
+        for n in (1024, 16384):
+            hs = []
+            for p in (0, 1, 2):
+                b = cs.allocate(0, n, path=p)
+                cs.run(b, 5, eps=())
+                torch.cuda.synchronize()
+                hs.append(b.hist.clone())
+            assert torch.equal(hs[0], hs[1]) and torch.equal(hs[1], hs[2])
+    finally:
+        cs.set_auto_paths(old)
