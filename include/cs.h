@@ -389,6 +389,28 @@ int cs_count_jobs(const cs_count_job *jobs, int n_jobs, int path, void *table_ho
  */
 int cs_sprinkle_noalloc(int kind, int64_t n, uint64_t seed, int32_t *coords_dev, void *stream);
 
+/* ---------------------------------------------------- failure detection */
+
+/*
+ * Bounded-wait self test: one warp waits on an mbarrier through the same
+ * bounded-wait path the pipelines use, with a limit of limit_s seconds
+ * (0 < limit_s <= 10).  With complete = 0 nothing completes the barrier, so
+ * the wait gives up, CS_ETIMEOUT lands in the workspace status word
+ * (cs_workspace_status) and the kernel returns normally: the context stays
+ * usable.  With complete != 0 the barrier completes first and the status
+ * stays CS_OK.  The thesis has no counterpart (failure detection of this
+ * library).  Errors: CS_EINVAL, CS_ECUDA.
+ */
+int cs_selftest_wait(void *workspace_dev, double limit_s, int complete, void *stream);
+
+/* Host-side fault injection for tests: the next `count` times the step
+ * `where` runs it fails as if its CUDA call had failed (count = 0 clears).
+ * CS_FAULT_ALLOC: the device allocations of cs_evaluate (-> CS_ENOMEM);
+ * CS_FAULT_LAUNCH: the kernel launches of cs_interval_abundance (-> CS_ECUDA). */
+#define CS_FAULT_ALLOC 1
+#define CS_FAULT_LAUNCH 2
+int cs_inject_fault(int where, int count);
+
 /* ------------------------------------------------------------------ misc */
 
 /* Static description of a status code. */

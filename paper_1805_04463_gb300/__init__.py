@@ -23,11 +23,13 @@ __all__ = [
     "set_auto_paths", "get_auto_paths",
     "sprinkle", "sprinkle_noalloc", "causal_matrix", "layer_sums", "dalembertian", "interval_abundance", "workspace_status", "action", "action_device",
     "evaluate", "Buffers", "allocate", "run", "SetDesc", "Batch", "CountJob", "count_items",
-    "operands_bytes", "prepare_operands", "count_jobs",
+    "operands_bytes", "prepare_operands", "count_jobs", "FAULT_ALLOC", "FAULT_LAUNCH", "selftest_wait",
+    "inject_fault",
 ]
 
 KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND = 0, 1, 2
 PATH_AUTO, PATH_POPC, PATH_MMA = 0, 1, 2
+FAULT_ALLOC, FAULT_LAUNCH = 1, 2
 KIND_NAMES = {KIND_2D_ORDER: "2d_order", KIND_2D_DIAMOND: "2d_diamond", KIND_4D_DIAMOND: "4d_diamond"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -93,6 +95,8 @@ def lib() -> ctypes.CDLL:
             "cs_count_jobs_table_bytes": ([i32, i32], sz),
             "cs_count_jobs_workspace_bytes": ([i32, i32], sz),
             "cs_count_jobs": ([vp, i32, i32, vp, vp, sz, vp], i32),
+            "cs_selftest_wait": ([vp, ctypes.c_double, i32, vp], i32),
+            "cs_inject_fault": ([i32, i32], i32),
             "cs_strerror": ([i32], ctypes.c_char_p),
             "cs_version": ([], ctypes.c_char_p),
         }
@@ -392,3 +396,17 @@ def count_jobs(jobs, path, table_host_ptr, workspace_ptr, workspace_nbytes, stre
     arr = (CountJob * len(jobs))(*jobs)
     _check(lib().cs_count_jobs(arr, len(jobs), path, table_host_ptr, workspace_ptr, workspace_nbytes,
                                _stream(stream)), "cs_count_jobs")
+
+
+# ------------------------------------------------------ failure detection
+
+def selftest_wait(workspace, limit_s, complete=False, stream=None):
+    """cs_selftest_wait: a bounded mbarrier wait that times out unless `complete`;
+    read the outcome with workspace_status()."""
+    _check(lib().cs_selftest_wait(_ptr(workspace), float(limit_s), 1 if complete else 0, _stream(stream)),
+           "cs_selftest_wait")
+
+
+def inject_fault(where, count=1):
+    """cs_inject_fault: make the next `count` runs of step `where` (FAULT_*) fail; count=0 clears."""
+    _check(lib().cs_inject_fault(where, count), "cs_inject_fault")

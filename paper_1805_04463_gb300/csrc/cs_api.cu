@@ -143,6 +143,7 @@ int cs_interval_abundance(int64_t n, const uint64_t* bits_dev, int64_t row_words
     const int p = resolve_path(n, path);
     if (p == CS_PATH_MMA && !device_has_tcgen05()) return CS_EUNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (fault_injected(CS_FAULT_LAUNCH)) return CS_ECUDA;
     cudaError_t e = clear_status(workspace_dev, st);
     if (e == cudaSuccess)
         e = p == CS_PATH_MMA ? launch_count_mma(n, bits_dev, row_words, hist_dev, workspace_dev, st)
@@ -247,7 +248,8 @@ int cs_evaluate(int kind, int64_t n, uint64_t seed, const int32_t* coords_host, 
     double* out = nullptr;  // [16] actions, then the bracket as int64
     int rc = CS_OK;
     auto alloc = [&](void** p, size_t b) {
-        if (rc == CS_OK && cudaMallocAsync(p, b, st) != cudaSuccess) rc = CS_ENOMEM;
+        if (rc == CS_OK && (fault_injected(CS_FAULT_ALLOC) || cudaMallocAsync(p, b, st) != cudaSuccess))
+            rc = CS_ENOMEM;
     };
     alloc(reinterpret_cast<void**>(&coords), cs_coords_bytes(kind, n));
     alloc(reinterpret_cast<void**>(&bits), cs_bitset_bytes(n));

@@ -85,6 +85,10 @@ cudaError_t launch_action_device(int dim, int64_t n, const int64_t* hist, int64_
 cudaError_t launch_dalembertian(int dim, int64_t n, const double* phi, const double* layer, double ell, double* out,
                                 cudaStream_t st);
 
+// cs_selftest.cu: host fault injection (cs_inject_fault).  True when the
+// step `where` (a CS_FAULT_* bit) must fail this time.
+bool fault_injected(int where);
+
 // Device properties cached per device.
 int device_sm_count();
 bool device_has_tcgen05();

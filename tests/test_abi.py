@@ -148,3 +148,14 @@ def test_tuner_choice_logic():
     assert tune.choose(m) == [(0, 1), (4096, 2)]
     assert tune.choose([(1024, 0.1, None)]) == [(0, 1)]
     assert tune.choose([(1024, 0.5, 0.1), (2048, 0.4, 0.5), (4096, 2.0, 1.0)]) == [(0, 2), (2048, 1), (4096, 2)]
+
+
+def test_failure_detection_entry_points_reject_bad_arguments(cslib):
+    L = cslib.lib()
+    assert L.cs_selftest_wait(None, 0.1, 0, None) == -1        # no workspace
+    assert L.cs_selftest_wait(256, 0.0, 0, None) == -1         # limit must be > 0
+    assert L.cs_selftest_wait(256, 11.0, 0, None) == -1        # and at most 10 s
+    assert L.cs_selftest_wait(257, 0.1, 0, None) == -1         # 256-byte aligned
+    assert L.cs_inject_fault(-1, 1) == -1
+    assert L.cs_inject_fault(cslib.FAULT_ALLOC, -1) == -1
+    assert L.cs_inject_fault(cslib.FAULT_ALLOC, 0) == 0
