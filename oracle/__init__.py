@@ -32,7 +32,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND = 0, 1, 2
+KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND = 0, 1, 2, 3
 GRID = 1 << 20
 
 
@@ -94,7 +94,7 @@ def _check(rc: int, what: str) -> int:
 
 
 def dim(kind: int) -> int:
-    return 4 if kind == KIND_4D_DIAMOND else 2
+    return {KIND_4D_DIAMOND: 4, KIND_3D_DIAMOND: 3}.get(kind, 2)
 
 
 def splitmix64_outputs(state: int, count: int) -> list[int]:

@@ -27,6 +27,7 @@
  * Parity pins live in tests/test_oracle_*.py; every function here is pinned
  * by at least one check that does not re-run this file's own formulae.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -47,7 +48,7 @@ typedef __float128 q128;  /* binary128 via libgcc soft-float */
 #define OR_HALF  (1LL << 19)
 #define OR_MAX_ATTEMPTS 16384
 
-enum { OR_2D_ORDER = 0, OR_2D_DIAMOND = 1, OR_4D_DIAMOND = 2 };
+enum { OR_2D_ORDER = 0, OR_2D_DIAMOND = 1, OR_4D_DIAMOND = 2, OR_3D_DIAMOND = 3 };
 enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2, OR_ERANGE = -6 };
 
 /* ------------------------------------------------------------------ PRNG */
@@ -83,6 +84,7 @@ uint64_t oracle_draw(uint64_t seed, uint32_t stream, uint64_t elem, uint32_t slo
 int oracle_dim(int kind)
 {
     if (kind == OR_2D_ORDER || kind == OR_2D_DIAMOND) return 2;
+    if (kind == OR_3D_DIAMOND) return 3;
     if (kind == OR_4D_DIAMOND) return 4;
     return 0;
 }
@@ -124,6 +126,12 @@ static int or_cmp_upair(const void *a, const void *b)
  * kind 2, 4D diamond of height 1: rejection sampling (allowed by the
  *   appendix's general method) in the box t in [0, 2^20),
  *   x, y, z in [-2^19, 2^19): accept iff x^2+y^2+z^2 < min(t, 2^20-t)^2.
+ *   Attempt a of element e uses slots 4a..4a+3 of stream 3.
+ * kind 3, 3D (2+1) diamond of height 1: the same rejection method in the box
+ *   t in [0, 2^20), x, y in [-2^19, 2^19): accept iff
+ *   x^2+y^2 < min(t, 2^20-t)^2 (Appendix "Causal Set Sprinklings", 2+1
+ *   Dimensional Diamond, volume pi/(3 sqrt 2) u0^3 = pi/12 for height 1).
+ *   Attempt a of element e uses slots 3a..3a+2 of stream 4.
  * Elements are sorted by time with ties broken by generation index
  * (Section "Pairwise Relations": elements are sorted by their time
  * coordinate before relations are identified).
@@ -169,34 +177,38 @@ int oracle_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords)
         free(u); free(v); free(t);
         return OR_OK;
     }
-    if (kind == OR_4D_DIAMOND) {
-        int32_t *x = malloc((size_t)n * 4 * sizeof *x);
+    if (kind == OR_4D_DIAMOND || kind == OR_3D_DIAMOND) {
+        const int d = oracle_dim(kind);
+        const uint32_t stream = kind == OR_4D_DIAMOND ? 3 : 4;
+        int32_t *x = malloc((size_t)n * (size_t)d * sizeof *x);
         or_pair *t = malloc((size_t)n * sizeof *t);
         if (!x || !t) { free(x); free(t); return OR_ENOMEM; }
         int bad = 0;
         for (int64_t e = 0; e < n && !bad; e++) {
             int found = 0;
             for (int a = 0; a < OR_MAX_ATTEMPTS && !found; a++) {
-                int64_t c[4];
-                for (int q = 0; q < 4; q++)
-                    c[q] = (int64_t)(oracle_draw(seed, 3, (uint64_t)e, (uint32_t)(4 * a + q)) >> 44);
+                int64_t c[4] = {0, 0, 0, 0}, r2 = 0;
+                for (int q = 0; q < d; q++)
+                    c[q] = (int64_t)(oracle_draw(seed, stream, (uint64_t)e, (uint32_t)(d * a + q)) >> 44);
                 int64_t tt = c[0];
-                int64_t xx = c[1] - OR_HALF, yy = c[2] - OR_HALF, zz = c[3] - OR_HALF;
+                for (int q = 1; q < d; q++) {
+                    c[q] -= OR_HALF;
+                    r2 += c[q] * c[q];
+                }
                 int64_t h = tt < OR_GRID - tt ? tt : OR_GRID - tt;
-                if (xx * xx + yy * yy + zz * zz < h * h) {
-                    x[4 * e + 0] = (int32_t)tt; x[4 * e + 1] = (int32_t)xx;
-                    x[4 * e + 2] = (int32_t)yy; x[4 * e + 3] = (int32_t)zz;
+                if (r2 < h * h) {
+                    for (int q = 0; q < d; q++) x[(int64_t)d * e + q] = (int32_t)c[q];
                     found = 1;
                 }
             }
             if (!found) bad = 1;
-            t[e].key = x[4 * e];
+            t[e].key = x[(int64_t)d * e];
             t[e].idx = e;
         }
         if (bad) { free(x); free(t); return OR_ERANGE; }
         qsort(t, (size_t)n, sizeof *t, or_cmp_pair);
         for (int64_t r = 0; r < n; r++)
-            for (int q = 0; q < 4; q++) coords[(int64_t)q * n + r] = x[4 * t[r].idx + q];
+            for (int q = 0; q < d; q++) coords[(int64_t)q * n + r] = x[(int64_t)d * t[r].idx + q];
         free(x); free(t);
         return OR_OK;
     }
@@ -216,11 +228,13 @@ int oracle_precedes(int kind, int64_t n, const int32_t *coords, int64_t a, int64
         int64_t dv = (int64_t)coords[n + b] - coords[n + a];
         return du > 0 && dv > 0;
     }
-    int64_t dt = (int64_t)coords[b] - coords[a];
-    int64_t dx = (int64_t)coords[n + b] - coords[n + a];
-    int64_t dy = (int64_t)coords[2 * n + b] - coords[2 * n + a];
-    int64_t dz = (int64_t)coords[3 * n + b] - coords[3 * n + a];
-    return dt > 0 && dt * dt - (dx * dx + dy * dy + dz * dz) > 0;
+    int d = oracle_dim(kind);
+    int64_t dt = (int64_t)coords[b] - coords[a], r2 = 0;
+    for (int q = 1; q < d; q++) {
+        int64_t dx = (int64_t)coords[q * n + b] - coords[q * n + a];
+        r2 += dx * dx;
+    }
+    return dt > 0 && dt * dt - r2 > 0;
 }
 
 /* Row words of the bitset: ceil(n/64) rounded up to a multiple of 16. */
@@ -440,26 +454,36 @@ static q128 or_qsqrt(q128 x)
  * Benincasa-Dowker action from the abundances (Section "The Benincasa-Dowker
  * Action").  With hist[k] = n_{k+1}:
  *   local 1+1 (Eq. s2d_local):  S = 2 (N - 2 n1 + 4 n2 - 2 n3)
+ *   local 2+1 (Eq. s3d_local):  S = c3 (N - n1 + 27/8 n2 - 9/4 n3),
+ *                               c3 = (pi/(3 sqrt 2))^(2/3) / Gamma(5/3), l/l_p = 1
  *   local 3+1 (Eq. s4d_local):  S = 4/sqrt(6) (N - n1 + 9 n2 - 16 n3 + 8 n4),
  *                               with (l/l_p)^2 = 1
  *   smeared 1+1 (Eq. s2d_smeared): S = 2 eps [N - 2 eps sum_m n_m f2(m-1, eps)]
+ *   smeared 2+1:                   S = c3 eps^(2/3) [N - eps sum_m n_m f3(m-1, eps)]
  *   smeared 3+1 (Eq. s4d_smeared): S = 4 sqrt(eps/6) [N - eps sum_m n_m f4(m-1, eps)]
- * with f2 and f4 evaluated as printed (divisions by 1-eps) in binary128 and
- * (1-eps)^m built by repeated multiplication.  eps <= 0 or eps == 1 selects
- * the local action.  bracket receives the exact integer in parentheses of
- * the local form.  out receives S rounded to double.
+ * with f2, f3 and f4 evaluated as printed (divisions by 1-eps) in binary128
+ * and (1-eps)^m built by repeated multiplication.  eps <= 0 or eps == 1
+ * selects the local action.  bracket receives the exact integer in
+ * parentheses of the local form (2+1: eight times it, 8N - 8n1 + 27n2 - 18n3,
+ * so that it stays an integer).  out receives S rounded to double.  The 2+1
+ * constant c3 and eps^(2/3) come from libm in double (relative error near
+ * 1e-16, a constant factor on an otherwise binary128 result).
  */
 int oracle_action(int dim, int64_t n, const int64_t *hist, int64_t len, double eps, double *out,
                   int64_t *bracket)
 {
-    if ((dim != 2 && dim != 4) || n < 0 || len < 0 || eps > 1.0 || eps != eps) return OR_EINVAL;
+    if ((dim < 2 || dim > 4) || n < 0 || len < 0 || eps > 1.0 || eps != eps) return OR_EINVAL;
     int64_t h[4] = {0, 0, 0, 0};
     for (int k = 0; k < 4 && k < len; k++) h[k] = hist[k];
     int64_t b = dim == 2 ? n - 2 * h[0] + 4 * h[1] - 2 * h[2]
+              : dim == 3 ? 8 * n - 8 * h[0] + 27 * h[1] - 18 * h[2]
                          : n - h[0] + 9 * h[1] - 16 * h[2] + 8 * h[3];
     if (bracket) *bracket = b;
+    q128 c3 = (q128)(pow(M_PI / (3.0 * sqrt(2.0)), 2.0 / 3.0) / tgamma(5.0 / 3.0));
     if (eps <= 0.0 || eps == 1.0) {
-        q128 s = dim == 2 ? (q128)2 * (q128)b : (q128)4 / or_qsqrt((q128)6) * (q128)b;
+        q128 s = dim == 2 ? (q128)2 * (q128)b
+               : dim == 3 ? c3 * (q128)b / 8
+                          : (q128)4 / or_qsqrt((q128)6) * (q128)b;
         if (out) *out = (double)s;
         return OR_OK;
     }
@@ -468,6 +492,8 @@ int oracle_action(int dim, int64_t n, const int64_t *hist, int64_t len, double e
         q128 m = (q128)k, f;
         if (dim == 2) {
             f = p * ((q128)1 - 2 * m * e / one_m + m * (m - 1) * e * e / (2 * one_m * one_m));
+        } else if (dim == 3) {
+            f = p * ((q128)1 - 27 * m * e / (8 * one_m) + 9 * m * (m - 1) * e * e / (8 * one_m * one_m));
         } else {
             f = p * ((q128)1 - 9 * m * e / one_m + 8 * m * (m - 1) * e * e / (one_m * one_m)
                      - 4 * m * (m - 1) * (m - 2) * e * e * e / (3 * one_m * one_m * one_m));
@@ -476,6 +502,7 @@ int oracle_action(int dim, int64_t n, const int64_t *hist, int64_t len, double e
         p *= one_m;
     }
     q128 s = dim == 2 ? 2 * e * ((q128)n - 2 * e * sum)
+           : dim == 3 ? c3 * (q128)pow(eps, 2.0 / 3.0) * ((q128)n - e * sum)
                       : 4 * or_qsqrt(e / 6) * ((q128)n - e * sum);
     if (out) *out = (double)s;
     return OR_OK;
@@ -511,18 +538,21 @@ int oracle_layer_sums(int64_t n, const uint64_t *bits, int64_t row_words, const 
 }
 
 /*
- * B phi(j) from the layer sums S_m(j) (m = |A_ij|), Eqs. b2d_local and
- * b4d_local with discreteness scale ell:
+ * B phi(j) from the layer sums S_m(j) (m = |A_ij|), Eqs. b2d_local,
+ * b3d_local and b4d_local with discreteness scale ell:
  *   1+1: (2/ell^2) [-phi(j) + 2 (S_0 - 2 S_1 + S_2)]
+ *   2+1: (c3/ell^2) [-phi(j) + S_0 - 27/8 S_1 + 9/4 S_2],
+ *        c3 = (pi/(3 sqrt 2))^(2/3) / Gamma(5/3)
  *   3+1: (4/(ell^2 sqrt 6)) [-phi(j) + S_0 - 9 S_1 + 16 S_2 - 8 S_3]
- * layers holds kmax+1 >= 3 (1+1) or >= 4 (3+1) rows of n values; phi == NULL
- * means phi = 1.
+ * layers holds kmax+1 >= 3 (1+1, 2+1) or >= 4 (3+1) rows of n values;
+ * phi == NULL means phi = 1.
  */
 int oracle_dalembertian(int dim, int64_t n, const double *phi, const double *layers, int kmax, double ell,
                         double *out)
 {
-    if ((dim != 2 && dim != 4) || n < 0 || !layers || !out || !(ell > 0)) return OR_EINVAL;
-    if (kmax < (dim == 2 ? 2 : 3)) return OR_EINVAL;
+    if ((dim < 2 || dim > 4) || n < 0 || !layers || !out || !(ell > 0)) return OR_EINVAL;
+    if (kmax < (dim == 4 ? 3 : 2)) return OR_EINVAL;
+    q128 c3 = (q128)(pow(M_PI / (3.0 * sqrt(2.0)), 2.0 / 3.0) / tgamma(5.0 / 3.0));
     q128 l2 = (q128)ell * (q128)ell;
     for (int64_t j = 0; j < n; j++) {
         q128 p = phi ? (q128)phi[j] : (q128)1;
@@ -530,6 +560,8 @@ int oracle_dalembertian(int dim, int64_t n, const double *phi, const double *lay
         q128 b;
         if (dim == 2) {
             b = (q128)2 / l2 * (-p + 2 * (s0 - 2 * s1 + s2));
+        } else if (dim == 3) {
+            b = c3 / l2 * (-p + s0 - (q128)27 / 8 * s1 + (q128)9 / 4 * s2);
         } else {
             q128 s3 = layers[3 * n + j];
             b = (q128)4 / (l2 * or_qsqrt((q128)6)) * (-p + s0 - 9 * s1 + 16 * s2 - 8 * s3);

@@ -116,6 +116,31 @@ def test_4d_diamond_inside_and_time_distribution(oracle):
     assert abs(acc / m - pa) < 5 * math.sqrt(pa * (1 - pa) / m)
 
 
+def test_3d_diamond_inside_and_time_distribution(oracle):
+    n = 16384
+    c = oracle.sprinkle(oracle.KIND_3D_DIAMOND, n, 6).astype(np.int64)
+    assert c.shape == (3, n)
+    t, x, y = c
+    g = oracle.GRID
+    assert (np.diff(t) >= 0).all()
+    h = np.minimum(t, g - t)
+    assert (x * x + y * y < h * h).all()
+    # Uniform in the 2+1 diamond: P(t < 1/4) = (1/4)^3 / (2 (1/2)^3) = 1/16.
+    p = 1 / 16
+    frac = (t < g // 4).mean()
+    assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / n)
+    # Acceptance volume of the first attempt: two cones of height and
+    # radius 1/2, 2 (1/3) pi (1/2)^3 = pi/12 of the unit box.
+    m = 20000
+    acc = 0
+    for e in range(m):
+        tt, xx, yy = [oracle.draw(6, 4, e, k) >> 44 for k in range(3)]
+        xx, yy = xx - g // 2, yy - g // 2
+        acc += xx * xx + yy * yy < min(tt, g - tt) ** 2
+    pa = math.pi / 12
+    assert abs(acc / m - pa) < 5 * math.sqrt(pa * (1 - pa) / m)
+
+
 # ------------------------------------------------------------- causal matrix
 
 def _unpack(bits, n):
@@ -123,7 +148,7 @@ def _unpack(bits, n):
     return b[:, :n].astype(bool), b[:, n:]
 
 
-@pytest.mark.parametrize("kind,n", [(0, 300), (1, 300), (2, 400), (0, 129), (2, 1)])
+@pytest.mark.parametrize("kind,n", [(0, 300), (1, 300), (2, 400), (0, 129), (2, 1), (3, 350), (3, 2)])
 def test_causal_matrix_invariants(oracle, kind, n):
     c = oracle.sprinkle(kind, n, 99)
     bits = oracle.causal_matrix(kind, c)
@@ -152,11 +177,12 @@ def test_causal_matrix_2d_order_relation_count(oracle):
     assert np.triu(m, 1).sum() == n * (n - 1) // 2 - _inversions(c[1])
 
 
-@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("kind", [1, 2, 3])
 def test_ordering_fraction_closed_form(oracle, kind):
     # Myrheim-Meyer: fraction of related pairs in a d-dim Minkowski interval
-    # is Gamma(d+1) Gamma(d/2) / (2 Gamma(3d/2)): 1/2 for d = 2, 1/10 for d = 4.
-    d = 2 if kind == 1 else 4
+    # is Gamma(d+1) Gamma(d/2) / (2 Gamma(3d/2)): 1/2 for d = 2, 8/35 for
+    # d = 3, 1/10 for d = 4.
+    d = oracle.dim(kind)
     want = math.gamma(d + 1) * math.gamma(d / 2) / (2 * math.gamma(3 * d / 2))
     n = 1024
     fr = []
@@ -192,7 +218,7 @@ def test_tiny_posets_by_hand(oracle):
 
 
 @pytest.mark.parametrize("kind,n,seed", [(0, 200, 1), (0, 256, 2), (1, 180, 3), (2, 220, 4), (2, 256, 5),
-                                         (0, 65, 6), (0, 2, 7), (2, 3, 8)])
+                                         (0, 65, 6), (0, 2, 7), (2, 3, 8), (3, 240, 9), (3, 129, 10)])
 def test_bitset_count_matches_brute_force(oracle, kind, n, seed):
     c = oracle.sprinkle(kind, n, seed)
     bits = oracle.causal_matrix(kind, c)
@@ -251,6 +277,18 @@ def test_chain_and_antichain_closed_forms(oracle, n):
         # 4D antichain: all at one time
         c4a = np.stack([z + 5, np.arange(n, dtype=np.int32), z, z])
         assert not oracle.interval_abundance(oracle.causal_matrix(2, c4a)).any()
+        # 2+1 chain on the t axis: N - n1 + 27/8 n2 - 9/4 n3 = 1 + 9N/8,
+        # bracket (eight times it) 8 + 9N; 2+1 antichain: bracket 8N.
+        c3 = (math.pi / (3 * math.sqrt(2))) ** (2 / 3) / math.gamma(5 / 3)
+        h3 = oracle.interval_abundance(oracle.causal_matrix(3, np.stack([t, z, z])))
+        assert h3.tolist() == hc.tolist()
+        s, br = oracle.action(3, n, h3)
+        assert br == 8 + 9 * n
+        assert abs(s - c3 * (1 + 9 * n / 8)) <= 1e-14 * abs(s)
+        h3a = oracle.interval_abundance(oracle.causal_matrix(3, np.stack([z + 5, np.arange(n, dtype=np.int32), z])))
+        assert not h3a.any()
+        s, br = oracle.action(3, n, h3a)
+        assert br == 8 * n and abs(s - c3 * n) <= 1e-14 * abs(s)
 
 
 # ------------------------------------------------------------------- action
@@ -259,7 +297,7 @@ def test_smeared_tends_to_local_as_eps_to_one(oracle):
     # f2(., 1) = (1,-2,1,0,...) and f4(., 1) = (1,-9,16,-8,0,...) make the
     # smeared action continuous onto the local one at eps = 1.
     rng = np.random.default_rng(2)
-    for dim in (2, 4):
+    for dim in (2, 3, 4):
         for _ in range(5):
             n = int(rng.integers(50, 500))
             h = rng.integers(0, 1000, n - 1).astype(np.int64)
@@ -277,10 +315,19 @@ def test_smearing_functions_sum_to_zero(oracle):
         for dim in (2, 4):
             s, _ = oracle.action(dim, 0, h, eps)
             assert abs(s) < 1e-20, (dim, eps, s)
+        # 2+1: sum_m f3(m, eps) = (1 - 27/8 + 9/8 * 2)/eps = -1/(8 eps), so the
+        # action with N = 0 is c3 eps^(2/3) * eps/(8 eps) = c3 eps^(2/3) / 8.
+        c3 = (math.pi / (3 * math.sqrt(2))) ** (2 / 3) / math.gamma(5 / 3)
+        s, _ = oracle.action(3, 0, h, eps)
+        assert abs(s - c3 * eps ** (2 / 3) / 8) <= 1e-14, (eps, s)
 
 
 def _f2(m, e):
     return (1 - e) ** m * (1 - 2 * m * e / (1 - e) + m * (m - 1) * e * e / (2 * (1 - e) ** 2))
+
+
+def _f3(m, e):
+    return (1 - e) ** m * (1 - Fraction(27, 8) * m * e / (1 - e) + Fraction(9, 8) * m * (m - 1) * e * e / (1 - e) ** 2)
 
 
 def _f4(m, e):
@@ -302,11 +349,17 @@ def test_smeared_chain_exact_rational(oracle, eps):
         want4 = 4 * math.sqrt(float(e) / 6) * float(s4_inner)
         got4, _ = oracle.action(4, n, np.array(hist, dtype=np.int64), float(eps))
         assert abs(got4 - want4) <= 1e-12 * max(1.0, abs(want4))
+        s3_inner = n - e * sum(hk * _f3(k, e) for k, hk in enumerate(hist))
+        c3 = (math.pi / (3 * math.sqrt(2))) ** (2 / 3) / math.gamma(5 / 3)
+        want3 = c3 * float(e) ** (2 / 3) * float(s3_inner)
+        got3, _ = oracle.action(3, n, np.array(hist, dtype=np.int64), float(eps))
+        assert abs(got3 - want3) <= 1e-12 * max(1.0, abs(want3))
 
 
 def test_action_rejects_bad_arguments(oracle):
-    with pytest.raises(RuntimeError):
-        oracle.action(3, 10, np.zeros(9, dtype=np.int64))
+    for bad_dim in (1, 5):
+        with pytest.raises(RuntimeError):
+            oracle.action(bad_dim, 10, np.zeros(9, dtype=np.int64))
     with pytest.raises(RuntimeError):
         oracle.action(2, 10, np.zeros(9, dtype=np.int64), 1.5)
 
@@ -327,9 +380,18 @@ def test_null_and_equal_time_pairs_are_unrelated(oracle):
     assert oracle.precedes(2, c4, 0, 4)
     assert not oracle.precedes(2, c4, 1, 2)    # equal time
     assert not oracle.precedes(2, c4, 4, 0)    # past-directed
+    c3 = np.array([[0, 5, 5, 6, 6],
+                   [0, 3, 5, 3, 0],
+                   [0, 4, 0, 4, 0]], dtype=np.int32)                 # (t, x, y)
+    assert not oracle.precedes(3, c3, 0, 1)    # 3^2 + 4^2 = 5^2
+    assert not oracle.precedes(3, c3, 0, 2)    # dt = dx
+    assert oracle.precedes(3, c3, 0, 3) and oracle.precedes(3, c3, 0, 4)
+    assert oracle.precedes(3, c3, 1, 3)        # dt = 1 at the same place
+    assert not oracle.precedes(3, c3, 2, 3)    # dt = 1 < |(-2, 4)|
+    assert not oracle.precedes(3, c3, 3, 0)    # past-directed
 
 
-@pytest.mark.parametrize("kind,n,seed", [(0, 50, 123), (1, 50, 124), (2, 30, 125)])
+@pytest.mark.parametrize("kind,n,seed", [(0, 50, 123), (1, 50, 124), (2, 30, 125), (3, 40, 126)])
 def test_sprinkle_follows_generator_spec(oracle, kind, n, seed):
     # The thesis does not fix the random numbers, so the generator's own
     # specification is pinned here from the (already pinned) draws: ranks of
@@ -347,6 +409,20 @@ def test_sprinkle_follows_generator_spec(oracle, kind, n, seed):
         order = sorted(range(n), key=lambda e: (pts[e][0] + pts[e][1], e))
         assert c[0].tolist() == [pts[e][0] for e in order]
         assert c[1].tolist() == [pts[e][1] for e in order]
+    elif kind == 3:
+        pts = []
+        for e in range(n):
+            a = 0
+            while True:
+                t, x, y = [oracle.draw(seed, 4, e, 3 * a + q) >> 44 for q in range(3)]
+                x, y = x - half, y - half
+                if x * x + y * y < min(t, g - t) ** 2:
+                    pts.append((t, x, y))
+                    break
+                a += 1
+        order = sorted(range(n), key=lambda e: (pts[e][0], e))
+        for q in range(3):
+            assert c[q].tolist() == [pts[e][q] for e in order]
     else:
         pts = []
         for e in range(n):
@@ -375,6 +451,9 @@ def test_layer_sums_and_dalembertian_by_hand(oracle):
     assert oracle.dalembertian(2, S, 1.0, np.array(g["phi"])).tolist() == g["B2"]
     b4 = oracle.dalembertian(4, S, 1.0, np.array(g["phi"]))
     assert np.allclose(b4, np.array(g["B4_bracket"]) * 4 / math.sqrt(6), rtol=1e-15, atol=0)
+    c3 = (math.pi / (3 * math.sqrt(2))) ** (2 / 3) / math.gamma(5 / 3)
+    b3 = oracle.dalembertian(3, S, 1.0, np.array(g["phi"]))
+    assert np.allclose(b3, np.array(g["B3_bracket8"]) / 8 * c3, rtol=1e-14, atol=0)
     # the discreteness scale enters as 1/ell^2
     assert np.allclose(oracle.dalembertian(2, S, 0.5, np.array(g["phi"])), 4 * np.array(g["B2"]), rtol=1e-15)
 
@@ -395,7 +474,7 @@ def test_layer_sums_chain_closed_form(oracle):
     assert (oracle.dalembertian(2, S0, 2.0, phi) == -2 / 4.0 * phi).all()   # B = -(2/ell^2) phi
 
 
-@pytest.mark.parametrize("kind,n", [(0, 300), (2, 250), (1, 200)])
+@pytest.mark.parametrize("kind,n", [(0, 300), (2, 250), (1, 200), (3, 220)])
 def test_layer_sums_match_abundances_and_definition(oracle, kind, n):
     c = oracle.sprinkle(kind, n, 1234 + n)
     bits = oracle.causal_matrix(kind, c)
