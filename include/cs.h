@@ -52,7 +52,8 @@ typedef enum {
 enum {
     CS_2D_ORDER = 0,    /* random 2D order: two uniform random permutations u, v */
     CS_2D_DIAMOND = 1,  /* 1+1 Minkowski diamond, light-cone coordinates on a 2^20 grid */
-    CS_4D_DIAMOND = 2   /* 3+1 Minkowski diamond of height 1, int32 grid of 2^20 per unit */
+    CS_4D_DIAMOND = 2,  /* 3+1 Minkowski diamond of height 1, int32 grid of 2^20 per unit */
+    CS_3D_DIAMOND = 3   /* 2+1 Minkowski diamond of height 1, int32 grid of 2^20 per unit */
 };
 
 /* Interval-count paths. */
@@ -64,7 +65,7 @@ enum {
 
 /* ------------------------------------------------------------- layouts */
 
-/* Spacetime dimension of a kind: 2 or 4; 0 for an unknown kind. */
+/* Spacetime dimension of a kind: 2, 3 or 4; 0 for an unknown kind. */
 int cs_dim(int kind);
 
 /* Bytes of the structure-of-arrays int32 coordinates: n * dim * 4.
@@ -181,8 +182,10 @@ int cs_layer_sums(int64_t n, const uint64_t *bits_dev, int64_t row_words, int64_
 
 /*
  * The discrete d'Alembertian B phi(j) for every element from the layer sums
- * (kmax >= 2 in 1+1, >= 3 in 3+1), with discreteness scale ell:
+ * (kmax >= 2 in 1+1 and 2+1, >= 3 in 3+1), with discreteness scale ell:
  *   1+1 (Eq. b2d_local): (2/ell^2) [-phi(j) + 2 (S_0 - 2 S_1 + S_2)]
+ *   2+1 (Eq. b3d_local): (c3/ell^2) [-phi(j) + S_0 - 27/8 S_1 + 9/4 S_2],
+ *                        c3 = (pi/(3 sqrt 2))^(2/3) / Gamma(5/3)
  *   3+1 (Eq. b4d_local): (4/(ell^2 sqrt 6)) [-phi(j) + S_0 - 9 S_1 + 16 S_2 - 8 S_3]
  * phi_dev may be NULL (phi = 1: B 1 is the element's curvature estimate).
  * out_dev: n doubles.  Asynchronous.  Errors: CS_EINVAL, CS_ECUDA.
@@ -203,16 +206,20 @@ int cs_workspace_status(void *workspace_dev, void *stream);
  * Benincasa-Dowker action from host abundances (Section "The
  * Benincasa-Dowker Action"), with hist[k] = n_{k+1}:
  *   dim 2, local (Eq. s2d_local):   S = 2 (N - 2 n1 + 4 n2 - 2 n3)
+ *   dim 3, local (Eq. s3d_local):   S = c3 (N - n1 + 27/8 n2 - 9/4 n3),
+ *                                   c3 = (pi/(3 sqrt 2))^(2/3) / Gamma(5/3), l/l_p = 1
  *   dim 4, local (Eq. s4d_local):   S = 4/sqrt(6) (N - n1 + 9 n2 - 16 n3 + 8 n4),
  *                                   taking (l/l_p)^2 = 1
  *   dim 2, smeared (Eq. s2d_smeared): S = 2 eps [N - 2 eps sum_m n_m f2(m-1, eps)]
+ *   dim 3, smeared:                   S = c3 eps^(2/3) [N - eps sum_m n_m f3(m-1, eps)]
  *   dim 4, smeared (Eq. s4d_smeared): S = 4 sqrt(eps/6) [N - eps sum_m n_m f4(m-1, eps)]
  * eps <= 0 or eps == 1 selects the local action (the smeared forms reduce to
  * it at eps = 1); 0 < eps < 1 the smeared one, summed over the whole
  * histogram in double-double (compensated FP64) arithmetic.
  * out (may be NULL) receives S; bracket_out (may be NULL) the exact integer
- * in parentheses of the local form.  Synchronous, host only.
- * Errors: CS_EINVAL (dim not 2 or 4, eps > 1 or NaN, n < 0, len < 0).
+ * in parentheses of the local form (dim 3: eight times it,
+ * 8N - 8n1 + 27n2 - 18n3).  Synchronous, host only.
+ * Errors: CS_EINVAL (dim not 2, 3 or 4, eps > 1 or NaN, n < 0, len < 0).
  */
 int cs_action(int dim, int64_t n, const int64_t *hist_host, int64_t len,
               double eps, double *out, int64_t *bracket_out);
@@ -256,7 +263,7 @@ int cs_evaluate(int kind, int64_t n, uint64_t seed, const int32_t *coords_host, 
 
 /* One causal set of a batch. */
 typedef struct {
-    int32_t kind;      /* CS_2D_ORDER, CS_2D_DIAMOND or CS_4D_DIAMOND */
+    int32_t kind;      /* CS_2D_ORDER, CS_2D_DIAMOND, CS_4D_DIAMOND or CS_3D_DIAMOND */
     int32_t reserved;  /* must be 0 */
     int64_t n;         /* 1 .. CS_BATCH_MAX_N */
     uint64_t seed;     /* the set equals cs_sprinkle(kind, n, seed, ...) */

@@ -1,6 +1,6 @@
 // cs_action.cu -- Benincasa-Dowker action from the interval abundances
-// (Section "The Benincasa-Dowker Action": Eqs. s2d_local, s4d_local,
-// s2d_smeared, s4d_smeared and the smearing functions f2, f4).
+// (Section "The Benincasa-Dowker Action": Eqs. s2d_local, s3d_local,
+// s4d_local, the smeared actions and the smearing functions f2, f3, f4).
 //
 // The local action is an exact integer bracket times a constant.  The
 // smeared action sums N_k f(k, eps) over the whole histogram; those terms are
@@ -66,7 +66,8 @@ __global__ void k_action_final(int dim, int64_t n, const int64_t* __restrict__ h
     out[e] = s.hi + s.lo;
 }
 
-// B phi(j) from the layer sums (Eqs. b2d_local, b4d_local), one thread per element.
+// B phi(j) from the layer sums (Eqs. b2d_local, b3d_local, b4d_local), one
+// thread per element.
 __global__ void k_dalembertian(int dim, int64_t n, const double* __restrict__ phi, const double* __restrict__ layer,
                                double scale, double* __restrict__ out) {
     for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
@@ -75,6 +76,8 @@ __global__ void k_dalembertian(int dim, int64_t n, const double* __restrict__ ph
         double b;
         if (dim == 2) {
             b = -p + 2.0 * (s0 - 2.0 * s1 + s2);
+        } else if (dim == 3) {
+            b = -p + s0 - 3.375 * s1 + 2.25 * s2;
         } else {
             const double s3 = layer[3 * n + j];
             b = -p + s0 - 9.0 * s1 + 16.0 * s2 - 8.0 * s3;
@@ -88,7 +91,9 @@ __global__ void k_dalembertian(int dim, int64_t n, const double* __restrict__ ph
 cudaError_t launch_dalembertian(int dim, int64_t n, const double* phi, const double* layer, double ell, double* out,
                                 cudaStream_t st) {
     const dd l2 = dd_two_prod(ell, ell);
-    const dd c = dim == 2 ? dd_div(dd_from(2.0), l2) : dd_div(dd_from(4.0), dd_mul(l2, dd_sqrt(dd_from(6.0))));
+    const dd c = dim == 2   ? dd_div(dd_from(2.0), l2)
+                 : dim == 3 ? dd_div(dd_from(c3_const()), l2)
+                            : dd_div(dd_from(4.0), dd_mul(l2, dd_sqrt(dd_from(6.0))));
     int64_t g = (n + 255) / 256;
     if (g > int64_t(device_sm_count()) * 8) g = int64_t(device_sm_count()) * 8;
     if (g < 1) g = 1;
@@ -99,7 +104,7 @@ cudaError_t launch_dalembertian(int dim, int64_t n, const double* phi, const dou
 size_t action_workspace_bytes() { return sizeof(WsHeader) + size_t(kActBlocks) * kMaxEps * sizeof(dd); }
 
 int action_host(int dim, int64_t n, const int64_t* hist, int64_t len, double eps, double* out, int64_t* bracket) {
-    if ((dim != 2 && dim != 4) || n < 0 || len < 0 || !(eps <= 1.0) || (len > 0 && !hist)) return CS_EINVAL;
+    if (dim < 2 || dim > 4 || n < 0 || len < 0 || !(eps <= 1.0) || (len > 0 && !hist)) return CS_EINVAL;
     int64_t h4[4] = {0, 0, 0, 0};
     for (int k = 0; k < 4 && k < len; ++k) h4[k] = hist[k];
     const int64_t b = bracket_of(dim, n, h4);
@@ -111,7 +116,7 @@ int action_host(int dim, int64_t n, const int64_t* hist, int64_t len, double eps
         const dd q = dd_two_sum(1.0, -eps);
         const int64_t kend = smear_cutoff(eps, len);
         dd sum = dd_from(0.0), p = dd_from(1.0);  // p = q^(max(0, k - deg))
-        const int64_t deg = dim == 2 ? 2 : 3;
+        const int64_t deg = smear_deg(dim);
         for (int64_t k = 0; k < kend; ++k) {
             if (hist[k] != 0) sum = dd_add(sum, dd_mul(dd_from_i64(hist[k]), dd_mul(p, smear_poly(dim, k, q, eps))));
             if (k >= deg) p = dd_mul(p, q);

@@ -35,21 +35,36 @@ __host__ __device__ inline dd dd_sqrt(dd a) {
     return dd_quick_two_sum(x, r.hi / (2.0 * x));
 }
 
+// The integer in parentheses of the local action; in 2+1 eight times it
+// (8N - 8n1 + 27n2 - 18n3) so that it stays an integer.
 __host__ __device__ inline int64_t bracket_of(int dim, int64_t n, const int64_t* h4) {
-    return dim == 2 ? n - 2 * h4[0] + 4 * h4[1] - 2 * h4[2] : n - h4[0] + 9 * h4[1] - 16 * h4[2] + 8 * h4[3];
+    if (dim == 2) return n - 2 * h4[0] + 4 * h4[1] - 2 * h4[2];
+    if (dim == 3) return 8 * n - 8 * h4[0] + 27 * h4[1] - 18 * h4[2];
+    return n - h4[0] + 9 * h4[1] - 16 * h4[2] + 8 * h4[3];
+}
+
+// The 2+1 constant (pi/(3 sqrt 2))^(2/3) / Gamma(5/3) of Eqs. s3d_local and
+// b3d_local, from the math library in double (a constant factor; its
+// rounding is ~1e-16 relative).
+__host__ __device__ inline double c3_const() {
+    const double v = cbrt(3.14159265358979323846 / (3.0 * sqrt(2.0)));
+    return v * v / tgamma(5.0 / 3.0);
 }
 
 __host__ __device__ inline bool is_local(double eps) { return eps <= 0.0 || eps == 1.0; }
 
-// Local action: 2 * bracket (1+1) or 4/sqrt(6) * bracket (3+1).
+// Local action: 2 * bracket (1+1), c3 * bracket / 8 (2+1) or
+// 4/sqrt(6) * bracket (3+1).
 __host__ __device__ inline dd local_action(int dim, int64_t bracket) {
     const dd b = dd_from_i64(bracket);
     if (dim == 2) return dd_mul_d(b, 2.0);
+    if (dim == 3) return dd_mul_d(b, c3_const() * 0.125);
     return dd_mul(dd_div(dd_from(4.0), dd_sqrt(dd_from(6.0))), b);
 }
 
 // Smeared action from sum = sum_k N_k f(k, eps):
-//   1+1: 2 eps [N - 2 eps sum];  3+1: 4 sqrt(eps/6) [N - eps sum].
+//   1+1: 2 eps [N - 2 eps sum];  2+1: c3 eps^(2/3) [N - eps sum];
+//   3+1: 4 sqrt(eps/6) [N - eps sum].
 __host__ __device__ inline dd smeared_action(int dim, int64_t n, double eps, dd sum) {
     const dd e = dd_from(eps);
     if (dim == 2) {
@@ -57,6 +72,10 @@ __host__ __device__ inline dd smeared_action(int dim, int64_t n, double eps, dd 
         return dd_mul(dd_mul_d(e, 2.0), inner);
     }
     const dd inner = dd_sub(dd_from_i64(n), dd_mul(e, sum));
+    if (dim == 3) {
+        const double r = cbrt(eps);
+        return dd_mul_d(inner, c3_const() * (r * r));
+    }
     const dd pref = dd_mul_d(dd_sqrt(dd_div(e, dd_from(6.0))), 4.0);
     return dd_mul(pref, inner);
 }

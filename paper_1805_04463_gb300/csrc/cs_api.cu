@@ -53,6 +53,7 @@ extern "C" {
 
 int cs_dim(int kind) {
     if (kind == CS_2D_ORDER || kind == CS_2D_DIAMOND) return 2;
+    if (kind == CS_3D_DIAMOND) return 3;
     if (kind == CS_4D_DIAMOND) return 4;
     return 0;
 }
@@ -174,8 +175,8 @@ int cs_layer_sums(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_
 
 int cs_dalembertian(int dim, int64_t n, const double* phi_dev, const double* layer_dev, int kmax, double ell,
                     double* out_dev, void* stream) {
-    if ((dim != 2 && dim != 4) || !valid_n(n) || !layer_dev || !out_dev || !(ell > 0.0) ||
-        kmax < (dim == 2 ? 2 : 3))
+    if (dim < 2 || dim > 4 || !valid_n(n) || !layer_dev || !out_dev || !(ell > 0.0) ||
+        kmax < (dim == 4 ? 3 : 2))
         return CS_EINVAL;
     return from_cuda(launch_dalembertian(dim, n, phi_dev, layer_dev, ell, out_dev, static_cast<cudaStream_t>(stream)));
 }
@@ -202,7 +203,7 @@ size_t cs_action_workspace_bytes(void) { return action_workspace_bytes(); }
 int cs_action_device(int dim, int64_t n, const int64_t* hist_dev, int64_t len, const double* eps_host, int n_eps,
                      double* out_dev, int64_t* bracket_dev, void* workspace_dev, size_t workspace_bytes,
                      void* stream) {
-    if ((dim != 2 && dim != 4) || n < 0 || len < 1 || !hist_dev || !eps_host || n_eps < 1 || n_eps > 16 ||
+    if (dim < 2 || dim > 4 || n < 0 || len < 1 || !hist_dev || !eps_host || n_eps < 1 || n_eps > 16 ||
         !out_dev || !workspace_dev || !aligned(workspace_dev, 256))
         return CS_EINVAL;
     for (int e = 0; e < n_eps; ++e)

@@ -71,9 +71,11 @@ __global__ void __launch_bounds__(256) k_batch_keys(const BatchSet* __restrict__
             b.key0[e] = draw_2d_diamond(stream_key(b.seed, kStreamDiamond2), e, b.raw[e], b.raw[b.n + e]);
         } else {
             int32_t c[4];
-            if (!draw_4d_diamond(stream_key(b.seed, kStreamDiamond4), e, c, b.key0[e])) set_status(hdr, CS_ERANGE);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) b.raw[k * b.n + e] = c[k];
+            const bool ok = b.kind == CS_3D_DIAMOND
+                                ? draw_3d_diamond(stream_key(b.seed, kStreamDiamond3), e, c, b.key0[e])
+                                : draw_4d_diamond(stream_key(b.seed, kStreamDiamond4), e, c, b.key0[e]);
+            if (!ok) set_status(hdr, CS_ERANGE);
+            for (int k = 0; k < b.dim; ++k) b.raw[k * b.n + e] = c[k];
         }
     }
 }
@@ -156,6 +158,8 @@ __global__ void __launch_bounds__(kRelThreads) k_batch_relate(const BatchSet* __
         const int64_t rb = local / b.col_groups, cg = local - rb * b.col_groups;
         if (b.dim == 4)
             relate_block<4>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
+        else if (b.dim == 3)
+            relate_block<3>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
         else
             relate_block<2>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
         __syncthreads();  // the next block restages sc
@@ -190,7 +194,7 @@ __global__ void __launch_bounds__(kActThreads) k_batch_action(const BatchSet* __
         const dd q = dd_two_sum(1.0, -ep);
         const dd step = dd_pow(q, kActThreads);
         const int64_t kend = smear_cutoff(ep, len);
-        const int64_t deg = dim == 2 ? 2 : 3;
+        const int64_t deg = smear_deg(dim);
         dd sum = dd_from(0.0), p = dd_from(1.0);
         for (int64_t k = tid; k < kend; k += kActThreads) {
             // q^(k-deg) for k >= deg; a direct power until the stride applies

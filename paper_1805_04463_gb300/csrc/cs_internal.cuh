@@ -299,6 +299,7 @@ __host__ __device__ inline dd dd_pow(dd x, int64_t k) {
 // Smearing functions with the (1-eps) denominators cleared, so that they are
 // exact at eps = 1 (Section "The Benincasa-Dowker Action"):
 //   f2(k) = q^(k-2) [q^2 - 2 k eps q + k(k-1)/2 eps^2],                 q = 1 - eps
+//   f3(k) = q^(k-2) [q^2 - 27/8 k eps q + 9/8 k(k-1) eps^2]
 //   f4(k) = q^(k-3) [q^3 - 9 k eps q^2 + 8 k(k-1) eps^2 q - 8 C(k,3) eps^3]
 // (4/3 k(k-1)(k-2) = 8 C(k,3) is an integer).  qpow = q^(k - deg) for the
 // general branch; the small-k branches expand the printed forms directly.
@@ -310,6 +311,15 @@ __host__ __device__ inline dd smear_poly(int dim, int64_t k, dd q, double eps) {
         dd a = dd_mul(q, q);
         dd b = dd_mul(dd_mul_d(e, 2.0 * static_cast<double>(k)), q);
         dd c = dd_mul(dd_mul(e, e), dd_from_i64(k * (k - 1) / 2));
+        return dd_add(dd_sub(a, b), c);
+    }
+    if (dim == 3) {
+        if (k == 0) return dd_from(1.0);
+        if (k == 1) return dd_sub(q, dd_mul_d(e, 3.375));            // (1-eps) - 27/8 eps
+        // 27 k / 8 and 9 k(k-1)/8 are exact doubles for k < 2^22
+        dd a = dd_mul(q, q);
+        dd b = dd_mul(dd_mul_d(e, 3.375 * static_cast<double>(k)), q);
+        dd c = dd_mul(dd_mul(e, e), dd_from(2.25 * static_cast<double>(k * (k - 1) / 2)));
         return dd_add(dd_sub(a, b), c);
     }
     // dim == 4
@@ -335,9 +345,12 @@ __host__ __device__ inline dd smear_poly(int dim, int64_t k, dd q, double eps) {
     return dd_sub(dd_add(dd_sub(a, b), c), d);
 }
 
+// Degree of the polynomial factor of f_d (the power of 1/(1-eps) pulled out).
+__host__ __device__ __forceinline__ int64_t smear_deg(int dim) { return dim == 4 ? 3 : 2; }
+
 // Exponent of q multiplying smear_poly for index k.
 __host__ __device__ __forceinline__ int64_t smear_qexp(int dim, int64_t k) {
-    const int64_t deg = dim == 2 ? 2 : 3;
+    const int64_t deg = smear_deg(dim);
     return k >= deg ? k - deg : 0;
 }
 

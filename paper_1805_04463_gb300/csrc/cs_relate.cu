@@ -29,6 +29,8 @@ cudaError_t launch_relate(int kind, int64_t n, const int32_t* coords, uint64_t* 
               unsigned((row_words + kRelWordsPerBlock - 1) / kRelWordsPerBlock));
     if (kind == CS_4D_DIAMOND)
         k_relate<4><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words);
+    else if (kind == CS_3D_DIAMOND)
+        k_relate<3><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words);
     else
         k_relate<2><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words);
     return cudaGetLastError();

@@ -12,7 +12,8 @@ constexpr int kRelRowsPerBlock = 64;
 constexpr int kRelThreads = 256;
 
 // Symmetric timelike test between row element ci and staged column `col`:
-// du * dv > 0 (1+1, light-cone coordinates) or dt^2 - |dx|^2 > 0 (3+1), in int64.
+// du * dv > 0 (1+1, light-cone coordinates) or dt^2 - |dx|^2 > 0 (2+1, 3+1),
+// in int64.
 template <int DIM>
 __device__ __forceinline__ bool rel_related(const int32_t (&ci)[DIM], const int32_t (*sc)[kRelColsPerBlock], int col) {
     if constexpr (DIM == 2) {
@@ -22,10 +23,13 @@ __device__ __forceinline__ bool rel_related(const int32_t (&ci)[DIM], const int3
         return (du ^ dv) >= 0 && du != 0 && dv != 0;
     } else {
         const int64_t dt = int64_t(sc[0][col]) - ci[0];
-        const int64_t dx = int64_t(sc[1][col]) - ci[1];
-        const int64_t dy = int64_t(sc[2][col]) - ci[2];
-        const int64_t dz = int64_t(sc[3][col]) - ci[3];
-        return dt * dt - (dx * dx + dy * dy + dz * dz) > 0;
+        int64_t r2 = 0;
+#pragma unroll
+        for (int d = 1; d < DIM; ++d) {
+            const int64_t dx = int64_t(sc[d][col]) - ci[d];
+            r2 += dx * dx;
+        }
+        return dt * dt - r2 > 0;
     }
 }
 

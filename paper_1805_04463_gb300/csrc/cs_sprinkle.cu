@@ -1,5 +1,5 @@
 // cs_sprinkle.cu -- sprinkling on the device (Section "Coordinate Generation",
-// Appendix "Causal Set Sprinklings": 1+1 and 3+1 Minkowski diamonds).
+// Appendix "Causal Set Sprinklings": 1+1, 2+1 and 3+1 Minkowski diamonds).
 //
 // Coordinates are drawn independently per element from the counter-based
 // generator, then elements are sorted by time (Section "Pairwise
@@ -33,14 +33,15 @@ __global__ void k_keys_2d_diamond(int64_t n, uint64_t seed, int32_t* __restrict_
         key[e] = draw_2d_diamond(s, e, raw[e], raw[n + e]);
 }
 
-__global__ void k_keys_4d_diamond(int64_t n, uint64_t seed, int32_t* __restrict__ raw,
-                                  uint64_t* __restrict__ key, WsHeader* hdr) {
-    const uint64_t s = stream_key(seed, kStreamDiamond4);
+template <int D>
+__global__ void k_keys_diamond(int64_t n, uint64_t seed, int32_t* __restrict__ raw, uint64_t* __restrict__ key,
+                               WsHeader* hdr) {
+    const uint64_t s = stream_key(seed, D == 4 ? kStreamDiamond4 : kStreamDiamond3);
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
         int32_t c[4];
-        if (!draw_4d_diamond(s, e, c, key[e])) set_status(hdr, CS_ERANGE);
+        if (!draw_diamond<D>(s, e, c, key[e])) set_status(hdr, CS_ERANGE);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) raw[k * n + e] = c[k];
+        for (int k = 0; k < D; ++k) raw[k * n + e] = c[k];
     }
 }
 
@@ -194,10 +195,12 @@ cudaError_t launch_sprinkle(int kind, int64_t n, uint64_t seed, int32_t* coords,
     }
     if (kind == CS_2D_DIAMOND)
         k_keys_2d_diamond<<<g, kThreads, 0, st>>>(n, seed, raw, key0);
+    else if (kind == CS_3D_DIAMOND)
+        k_keys_diamond<3><<<g, kThreads, 0, st>>>(n, seed, raw, key0, hdr);
     else
-        k_keys_4d_diamond<<<g, kThreads, 0, st>>>(n, seed, raw, key0, hdr);
+        k_keys_diamond<4><<<g, kThreads, 0, st>>>(n, seed, raw, key0, hdr);
     if ((err = rank_keys(n, key0, rank0, ws, L, st)) != cudaSuccess) return err;
-    k_scatter_raw<<<g, kThreads, 0, st>>>(n, kind == CS_4D_DIAMOND ? 4 : 2, rank0, raw, coords);
+    k_scatter_raw<<<g, kThreads, 0, st>>>(n, cs_dim(kind), rank0, raw, coords);
     return cudaGetLastError();
 }
 

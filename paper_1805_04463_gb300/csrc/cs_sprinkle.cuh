@@ -7,7 +7,8 @@
 namespace cs {
 
 // Stream numbers of the generator specification.
-constexpr uint32_t kStreamOrderU = 0, kStreamOrderV = 1, kStreamDiamond2 = 2, kStreamDiamond4 = 3;
+constexpr uint32_t kStreamOrderU = 0, kStreamOrderV = 1, kStreamDiamond2 = 2, kStreamDiamond4 = 3,
+                   kStreamDiamond3 = 4;
 
 // Random 2D order: the two 64-bit keys whose ranks are u and v.
 __device__ __forceinline__ void draw_2d_order(uint64_t su, uint64_t sv, int64_t e, uint64_t& ku, uint64_t& kv) {
@@ -24,19 +25,28 @@ __device__ __forceinline__ uint64_t draw_2d_diamond(uint64_t s, int64_t e, int32
     return uint64_t(uu + vv) << (64 - (kGridBits + 1));
 }
 
-// 4D diamond of height 1: rejection sampling in the box t in [0, 2^20),
-// x, y, z in [-2^19, 2^19), accepting x^2+y^2+z^2 < min(t, 2^20-t)^2; sort
-// key t in the top 20 bits.  Returns false if no attempt was accepted.
-__device__ __forceinline__ bool draw_4d_diamond(uint64_t s, int64_t e, int32_t (&c)[4], uint64_t& key) {
+// D-dimensional diamond of height 1 (D = 3: 2+1, D = 4: 3+1): rejection
+// sampling in the box t in [0, 2^20), spatial coordinates in [-2^19, 2^19),
+// accepting |x|^2 < min(t, 2^20-t)^2; attempt a uses slots D*a .. D*a+D-1.
+// Sort key t in the top 20 bits.  Returns false if no attempt was accepted.
+template <int D>
+__device__ __forceinline__ bool draw_diamond(uint64_t s, int64_t e, int32_t (&c)[4], uint64_t& key) {
     const int64_t half = kGrid / 2;
     for (int a = 0; a < kMaxAttempts; ++a) {
-        int64_t q[4];
+        int64_t q[D];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) q[k] = int64_t(draw_from(s, uint64_t(e), uint32_t(4 * a + k)) >> (64 - kGridBits));
-        const int64_t t = q[0], x = q[1] - half, y = q[2] - half, z = q[3] - half;
+        for (int k = 0; k < D; ++k) q[k] = int64_t(draw_from(s, uint64_t(e), uint32_t(D * a + k)) >> (64 - kGridBits));
+        int64_t r2 = 0;
+#pragma unroll
+        for (int k = 1; k < D; ++k) {
+            q[k] -= half;
+            r2 += q[k] * q[k];
+        }
+        const int64_t t = q[0];
         const int64_t h = t < kGrid - t ? t : kGrid - t;
-        if (x * x + y * y + z * z < h * h) {
-            c[0] = int32_t(t); c[1] = int32_t(x); c[2] = int32_t(y); c[3] = int32_t(z);
+        if (r2 < h * h) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) c[k] = k < D ? int32_t(q[k < D ? k : 0]) : 0;
             key = uint64_t(t) << (64 - kGridBits);
             return true;
         }
@@ -44,6 +54,14 @@ __device__ __forceinline__ bool draw_4d_diamond(uint64_t s, int64_t e, int32_t (
     c[0] = c[1] = c[2] = c[3] = 0;
     key = 0;
     return false;
+}
+
+__device__ __forceinline__ bool draw_4d_diamond(uint64_t s, int64_t e, int32_t (&c)[4], uint64_t& key) {
+    return draw_diamond<4>(s, e, c, key);
+}
+
+__device__ __forceinline__ bool draw_3d_diamond(uint64_t s, int64_t e, int32_t (&c)[4], uint64_t& key) {
+    return draw_diamond<3>(s, e, c, key);
 }
 
 }  // namespace cs

@@ -64,7 +64,7 @@ def test_strerror_and_version(cslib):
 
 def test_host_action_matches_oracle(cslib, oracle):
     rng = np.random.default_rng(7)
-    for dim in (2, 4):
+    for dim in (2, 3, 4):
         for n in (1, 2, 3, 50, 1000, 20000):
             for _ in range(3):
                 hl = max(n - 1, 1)
@@ -89,7 +89,8 @@ def test_host_action_on_real_abundances(cslib, oracle):
 
 
 def test_host_action_rejects_bad_arguments(cslib):
-    for args in [(3, 10, np.zeros(9, np.int64), 0.0), (2, 10, np.zeros(9, np.int64), 1.5),
+    for args in [(1, 10, np.zeros(9, np.int64), 0.0), (5, 10, np.zeros(9, np.int64), 0.0),
+                 (2, 10, np.zeros(9, np.int64), 1.5),
                  (2, -1, np.zeros(9, np.int64), 0.0), (2, 10, np.zeros(9, np.int64), float("nan"))]:
         with pytest.raises(cslib.CsError):
             cslib.action(*args)
@@ -102,6 +103,10 @@ def test_chain_local_action_closed_form(cslib):
         if n >= 4:
             s, b = cslib.action(4, n, h)
             assert b == n - 1 and abs(s - 4 / math.sqrt(6) * (n - 1)) <= 1e-15 * s
+        # 2+1: N - n1 + 27/8 n2 - 9/4 n3 = 1 + 9N/8 (bracket reported times 8)
+        c3 = (math.pi / (3 * math.sqrt(2))) ** (2 / 3) / math.gamma(5 / 3)
+        s, b = cslib.action(3, n, h)
+        assert b == 8 + 9 * n and abs(s - c3 * (1 + 9 * n / 8)) <= 1e-14 * s
 
 
 def test_batch_sizes_on_host(cslib):

@@ -11,7 +11,8 @@ EPS = (0.0, 0.05, 0.1, 0.2)
 TOL = 1e-12
 
 MIXED = [(0, 1, 11), (0, 2, 12), (2, 3, 13), (1, 127, 14), (0, 129, 15), (2, 1000, 16), (1, 2049, 17),
-         (0, 4096, 18), (2, 2048, 19), (1, 8192, 20), (0, 300, 21), (2, 4133, 22)]
+         (0, 4096, 18), (2, 2048, 19), (1, 8192, 20), (0, 300, 21), (2, 4133, 22), (3, 2, 23), (3, 1500, 24),
+         (3, 4099, 25)]
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +35,7 @@ def _check_against_oracle(cs, oracle, b):
         want = oracle.interval_abundance(oracle.causal_matrix(kind, c))
         got = hist[b.hist_offsets[s]:b.hist_offsets[s] + want.size]
         assert (got == want).all(), (s, kind, n)
-        d = 4 if kind == 2 else 2
+        d = oracle.dim(kind)
         for e, eps in enumerate(EPS):
             so, bo = oracle.action(d, n, want, eps)
             assert abs(acts[s, e] - so) <= TOL * max(1.0, abs(so)), (s, eps, acts[s, e], so)

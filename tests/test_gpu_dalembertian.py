@@ -34,7 +34,7 @@ def _layers(cs, kind, n, seed, path, kmax, phi=None):
 
 
 @pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
-@pytest.mark.parametrize("kind,n", [(0, 300), (0, 2049), (2, 1500), (1, 4096)])
+@pytest.mark.parametrize("kind,n", [(0, 300), (0, 2049), (2, 1500), (1, 4096), (3, 2500)])
 def test_layer_sums_exact_for_unit_field(cs, oracle, kind, n, path):
     import torch
     b, layer, _ = _layers(cs, kind, n, 40 + n, path, 4)
