@@ -16,8 +16,63 @@ Two ways to use several GPUs (one process per GPU):
 The thesis distributes its pair loop across computers with MPI (Section
 "MPI Optimization"); here the unit is a tile of the count, and the only
 exchange is the final histogram.
+
+Failure detection between ranks is host-side: each rank posts a heartbeat
+(its step number) to the process group's key-value store before every
+launch, and `check_peers` confirms, with a time limit, that every other rank
+has reached the same step -- or raises `PeerLost` naming the rank that left
+or fell silent -- so no rank launches work whose exchange would wait on a
+dead peer.  Ranks leave only between steps (`leave`).
 """
 from __future__ import annotations
+
+import time
+
+
+class PeerLost(RuntimeError):
+    """Another rank left the job or stopped posting heartbeats."""
+
+    def __init__(self, rank, why):
+        self.rank = rank
+        super().__init__(f"rank {rank} {why}")
+
+
+def _hb_key(rank):
+    return f"cs_hb/{rank}"
+
+
+def heartbeat(store, rank: int, step: int):
+    """Post that `rank` is about to run step `step`."""
+    store.set(_hb_key(rank), str(step))
+
+
+def leave(store, rank: int):
+    """Post that `rank` leaves the job (call between steps only)."""
+    store.set(_hb_key(rank), "left")
+
+
+def check_peers(store, world: int, rank: int, step: int, timeout_s: float = 2.0, poll_s: float = 0.005):
+    """Wait until every other rank has posted a heartbeat for a step >= `step`.
+    Raises PeerLost for a rank that posted `leave` or did not reach `step`
+    within `timeout_s` seconds."""
+    deadline = time.monotonic() + timeout_s
+    pending = [r for r in range(world) if r != rank]
+    while pending:
+        still = []
+        for r in pending:
+            key = _hb_key(r)
+            if store.check([key]):
+                v = store.get(key).decode()
+                if v == "left":
+                    raise PeerLost(r, "left the job")
+                if int(v) >= step:
+                    continue
+            still.append(r)
+        pending = still
+        if pending:
+            if time.monotonic() > deadline:
+                raise PeerLost(pending[0], f"posted no heartbeat for step {step} within {timeout_s} s")
+            time.sleep(poll_s)
 
 
 def shard_chunks(total_items: int, world: int, rank: int, rounds: int = 16):

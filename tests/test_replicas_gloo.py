@@ -1,8 +1,11 @@
 """Multi-rank host logic on CPU ranks (gloo, world size 2): item sharding
-covers every work item exactly once with balanced shares, and the histogram
-all-reduce / timing combine give the whole-job result."""
+covers every work item exactly once with balanced shares, the histogram
+all-reduce / timing combine give the whole-job result, and the loss of a rank
+(one that leaves, one that falls silent, one gone during a collective) is
+detected on the host within a bounded time instead of hanging the others."""
 import os
 import socket
+import time
 
 import numpy as np
 import pytest
@@ -66,3 +69,59 @@ def test_gloo_two_ranks_allreduce_and_timing():
 
 def test_combine_timing_without_group():
     assert combine_timing(5.0, 7.0, None) == (5.0, 7.0)
+
+
+def _worker_failure(rank, world, port, out, mode):
+    import datetime
+
+    import torch
+    import torch.distributed as dist
+    from paper_1805_04463_gb300.replicas import PeerLost, allreduce_hist, check_peers, heartbeat, leave
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    store = dist.TCPStore("127.0.0.1", port + 1, world, rank == 0, timeout=datetime.timedelta(seconds=30))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    h = torch.ones(5, dtype=torch.int64)
+    for step in range(3):
+        if rank == 1 and step == 2:
+            # rank 1 stops between steps, with nothing in flight
+            if mode == "leave":
+                leave(store, rank)
+            elif mode == "silent":
+                time.sleep(3.0)      # alive, but posts nothing for step 2
+            out[rank] = "stopped"
+            return
+        heartbeat(store, rank, step)
+        t0 = time.monotonic()
+        try:
+            if mode == "collective" and step == 2:
+                allreduce_hist(h, dist)     # the peer is gone: must fail, not hang
+            else:
+                check_peers(store, world, rank, step, timeout_s=1.0)
+                allreduce_hist(h, dist)
+        except PeerLost as e:
+            out[rank] = ("peer_lost", e.rank, step, time.monotonic() - t0)
+            return
+        except RuntimeError as e:       # gloo: the process-group timeout or a closed peer
+            out[rank] = ("collective_failed", step, time.monotonic() - t0, type(e).__name__)
+            return
+    out[rank] = ("finished",)
+
+
+@pytest.mark.timeout(120)
+@pytest.mark.parametrize("mode", ["leave", "silent", "collective"])
+def test_gloo_rank_loss_detected_on_host(mode):
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    port = _free_port()
+    while port >= 65535:
+        port = _free_port()
+    mp.spawn(_worker_failure, args=(world, port, out, mode), nprocs=world, join=True)
+    assert out[1] == "stopped"
+    r0 = out[0]
+    if mode == "collective":
+        assert r0[0] == "collective_failed" and r0[1] == 2 and r0[2] < 30.0
+    else:
+        assert r0[0] == "peer_lost" and r0[1] == 1 and r0[2] == 2
+        assert r0[3] < (0.5 if mode == "leave" else 5.0)
