@@ -32,7 +32,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND = 0, 1, 2, 3
+KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND, KIND_2D_DS_SLAB = 0, 1, 2, 3, 4
+DS_CELLS = 83443  # eta_0 = 0.5 rad on the grid of 2 pi / 2^20 rad
 GRID = 1 << 20
 
 
@@ -61,6 +62,8 @@ def _load():
         lib.oracle_splitmix64_next.restype = u64
         lib.oracle_draw.argtypes = [u64, u32, u64, u32]
         lib.oracle_draw.restype = u64
+        lib.oracle_ds_threshold.argtypes = [i64]
+        lib.oracle_ds_threshold.restype = u64
         lib.oracle_sprinkle.argtypes = [i32, i64, u64, vp]
         lib.oracle_precedes.argtypes = [i32, i64, vp, i64, i64]
         lib.oracle_row_words.argtypes = [i64]
@@ -105,6 +108,11 @@ def splitmix64_outputs(state: int, count: int) -> list[int]:
 
 def draw(seed: int, stream: int, elem: int, slot: int) -> int:
     return int(_load().oracle_draw(seed, stream, elem, slot))
+
+
+def ds_threshold(g: int) -> int:
+    """Cumulative sec^2 mass (scaled to 2^53) of the de Sitter slab up to the end of eta cell g."""
+    return int(_load().oracle_ds_threshold(g))
 
 
 def sprinkle(kind: int, n: int, seed: int) -> np.ndarray:

@@ -48,7 +48,13 @@ typedef __float128 q128;  /* binary128 via libgcc soft-float */
 #define OR_HALF  (1LL << 19)
 #define OR_MAX_ATTEMPTS 16384
 
-enum { OR_2D_ORDER = 0, OR_2D_DIAMOND = 1, OR_4D_DIAMOND = 2, OR_3D_DIAMOND = 3 };
+enum { OR_2D_ORDER = 0, OR_2D_DIAMOND = 1, OR_4D_DIAMOND = 2, OR_3D_DIAMOND = 3, OR_2D_DS_SLAB = 4 };
+
+/* de Sitter slab: eta and theta share the grid unit 2 pi / 2^20 rad; the slab
+ * is the eta cells -OR_DS_G .. OR_DS_G, i.e. |eta| <= (OR_DS_G + 1/2) units,
+ * and OR_DS_G = round(0.5 rad / unit) sets eta_0 = 0.5. */
+#define OR_DS_G 83443
+#define OR_TURN (1LL << 20)
 enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2, OR_ERANGE = -6 };
 
 /* ------------------------------------------------------------------ PRNG */
@@ -83,7 +89,7 @@ uint64_t oracle_draw(uint64_t seed, uint32_t stream, uint64_t elem, uint32_t slo
 
 int oracle_dim(int kind)
 {
-    if (kind == OR_2D_ORDER || kind == OR_2D_DIAMOND) return 2;
+    if (kind == OR_2D_ORDER || kind == OR_2D_DIAMOND || kind == OR_2D_DS_SLAB) return 2;
     if (kind == OR_3D_DIAMOND) return 3;
     if (kind == OR_4D_DIAMOND) return 4;
     return 0;
@@ -112,6 +118,20 @@ static int or_cmp_upair(const void *a, const void *b)
 }
 
 /*
+ * Cumulative sec^2 mass of the de Sitter slab up to the end of eta cell g,
+ * scaled to 2^53 (see kind 4 below).  The expression and its evaluation order
+ * are part of the generator specification, so that any implementation using
+ * the same libm tan reaches the same integers.
+ */
+uint64_t oracle_ds_threshold(int64_t g)
+{
+    double unit = 2.0 * M_PI / 1048576.0;
+    double t0 = tan(((double)OR_DS_G + 0.5) * unit);
+    double x = (tan(((double)g + 0.5) * unit) + t0) / (2.0 * t0);
+    return (uint64_t)(x * 9007199254740992.0);
+}
+
+/*
  * Sprinkle n elements and write them, labelled in time order, as
  * structure-of-arrays int32 coordinates: coords[c*n + label].
  *
@@ -132,6 +152,17 @@ static int or_cmp_upair(const void *a, const void *b)
  *   x^2+y^2 < min(t, 2^20-t)^2 (Appendix "Causal Set Sprinklings", 2+1
  *   Dimensional Diamond, volume pi/(3 sqrt 2) u0^3 = pi/12 for height 1).
  *   Attempt a of element e uses slots 3a..3a+2 of stream 4.
+ * kind 4, 1+1 de Sitter slab in the spherical foliation (Section "Spacetime
+ *   Region Considered", Eq. ds_metric; Appendix "Causal Set Sprinklings", de
+ *   Sitter 1+1 Dimensional Slab) with eta_0 = 0.5 and pseudo-radius 1:
+ *   theta uniform, eta with density sec^2(eta) / (2 tan eta_0), both on the
+ *   grid of 2 pi / 2^20 rad.  theta = draw(stream 5, slot 0) >> 44.  eta is
+ *   the inverse CDF of the cell masses: cell g (|g| <= G = 83443) covers
+ *   [(g - 1/2), (g + 1/2)] units, and with t0 = tan((G + 1/2) unit) the
+ *   cumulative mass up to the end of cell g is
+ *   x_g = (tan((g + 1/2) unit) + t0) / (2 t0) (exactly 1 for g = G);
+ *   eta = the smallest g with U < floor(x_g 2^53), U = draw(stream 5, slot 1)
+ *   >> 11.  Coordinates: coords[0] = eta cell, coords[1] = theta.
  * Elements are sorted by time with ties broken by generation index
  * (Section "Pairwise Relations": elements are sorted by their time
  * coordinate before relations are identified).
@@ -175,6 +206,30 @@ int oracle_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords)
             coords[n + r] = v[t[r].idx];
         }
         free(u); free(v); free(t);
+        return OR_OK;
+    }
+    if (kind == OR_2D_DS_SLAB) {
+        int32_t *eta = malloc((size_t)n * 4), *th = malloc((size_t)n * 4);
+        or_pair *t = malloc((size_t)n * sizeof *t);
+        if (!eta || !th || !t) { free(eta); free(th); free(t); return OR_ENOMEM; }
+        for (int64_t e = 0; e < n; e++) {
+            th[e] = (int32_t)(oracle_draw(seed, 5, (uint64_t)e, 0) >> 44);
+            uint64_t u = oracle_draw(seed, 5, (uint64_t)e, 1) >> 11;
+            int64_t lo = -OR_DS_G, hi = OR_DS_G; /* answer in [lo, hi] */
+            while (lo < hi) {
+                int64_t mid = lo + (hi - lo) / 2;
+                if (u < oracle_ds_threshold(mid)) hi = mid; else lo = mid + 1;
+            }
+            eta[e] = (int32_t)lo;
+            t[e].key = lo;
+            t[e].idx = e;
+        }
+        qsort(t, (size_t)n, sizeof *t, or_cmp_pair);
+        for (int64_t r = 0; r < n; r++) {
+            coords[r] = eta[t[r].idx];
+            coords[n + r] = th[t[r].idx];
+        }
+        free(eta); free(th); free(t);
         return OR_OK;
     }
     if (kind == OR_4D_DIAMOND || kind == OR_3D_DIAMOND) {
@@ -223,6 +278,14 @@ int oracle_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords)
  */
 int oracle_precedes(int kind, int64_t n, const int32_t *coords, int64_t a, int64_t b)
 {
+    if (kind == OR_2D_DS_SLAB) {
+        /* timelike iff the angular separation on the circle is below the
+         * conformal-time separation: pi - |pi - |dtheta|| < |deta| */
+        int64_t deta = (int64_t)coords[b] - coords[a];
+        int64_t dth = llabs((int64_t)coords[n + b] - coords[n + a]);
+        int64_t circ = dth < OR_TURN - dth ? dth : OR_TURN - dth;
+        return deta > 0 && circ < deta;
+    }
     if (kind == OR_2D_ORDER || kind == OR_2D_DIAMOND) {
         int64_t du = (int64_t)coords[b] - coords[a];
         int64_t dv = (int64_t)coords[n + b] - coords[n + a];

@@ -141,6 +141,47 @@ def test_3d_diamond_inside_and_time_distribution(oracle):
     assert abs(acc / m - pa) < 5 * math.sqrt(pa * (1 - pa) / m)
 
 
+def test_ds_slab_thresholds_and_eta_distribution(oracle):
+    # The cumulative sec^2 mass: ends at exactly 2^53, increases, and is
+    # symmetric about eta = 0 (cells -1 and 0 straddle one half).
+    G = oracle.DS_CELLS
+    assert oracle.ds_threshold(G) == 2 ** 53
+    ts = [oracle.ds_threshold(g) for g in range(-G, G + 1, 997)]
+    assert all(a < b for a, b in zip(ts, ts[1:]))
+    assert oracle.ds_threshold(-1) < 2 ** 52 < oracle.ds_threshold(0)
+    assert abs(oracle.ds_threshold(-1) + oracle.ds_threshold(0) - 2 ** 53) <= 2
+    # Sampled eta: P(|eta| < 1/4 rad) = tan(1/4) / tan(eta_0) for the density
+    # sec^2(eta) / (2 tan eta_0); theta uniform on the circle.
+    n = 20000
+    c = oracle.sprinkle(oracle.KIND_2D_DS_SLAB, n, 8).astype(np.int64)
+    eta, th = c
+    assert (np.diff(eta) >= 0).all() and (np.abs(eta) <= G).all()
+    assert ((th >= 0) & (th < 2 ** 20)).all()
+    unit = 2 * math.pi / 2 ** 20
+    e0 = (G + 0.5) * unit
+    p = math.tan(0.25) / math.tan(e0)
+    frac = (np.abs(eta * unit) < 0.25).mean()
+    assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / n)
+    q = (th < 2 ** 18).mean()
+    assert abs(q - 0.25) < 5 * math.sqrt(0.25 * 0.75 / n)
+
+
+def test_ds_slab_relation_fraction(oracle):
+    # Two independent elements are related iff the angle between them on the
+    # circle (uniform on [0, pi]) is below |eta_1 - eta_2|, so the related
+    # fraction is E|eta_1 - eta_2| / pi under the sec^2 density; the double
+    # integral by quadrature gives 0.34485701553 / pi = 0.109771397.
+    want = 0.34485701553285986 / math.pi
+    n = 1024
+    fr = []
+    for s in range(12):
+        c = oracle.sprinkle(oracle.KIND_2D_DS_SLAB, n, 2000 + s)
+        m, _ = _unpack(oracle.causal_matrix(oracle.KIND_2D_DS_SLAB, c), n)
+        fr.append(np.triu(m, 1).sum() / (n * (n - 1) / 2))
+    se = np.std(fr, ddof=1) / math.sqrt(len(fr))
+    assert abs(np.mean(fr) - want) < max(5 * se, 0.002)
+
+
 # ------------------------------------------------------------- causal matrix
 
 def _unpack(bits, n):
@@ -148,7 +189,8 @@ def _unpack(bits, n):
     return b[:, :n].astype(bool), b[:, n:]
 
 
-@pytest.mark.parametrize("kind,n", [(0, 300), (1, 300), (2, 400), (0, 129), (2, 1), (3, 350), (3, 2)])
+@pytest.mark.parametrize("kind,n", [(0, 300), (1, 300), (2, 400), (0, 129), (2, 1), (3, 350), (3, 2), (4, 400),
+                                    (4, 1)])
 def test_causal_matrix_invariants(oracle, kind, n):
     c = oracle.sprinkle(kind, n, 99)
     bits = oracle.causal_matrix(kind, c)
@@ -218,7 +260,8 @@ def test_tiny_posets_by_hand(oracle):
 
 
 @pytest.mark.parametrize("kind,n,seed", [(0, 200, 1), (0, 256, 2), (1, 180, 3), (2, 220, 4), (2, 256, 5),
-                                         (0, 65, 6), (0, 2, 7), (2, 3, 8), (3, 240, 9), (3, 129, 10)])
+                                         (0, 65, 6), (0, 2, 7), (2, 3, 8), (3, 240, 9), (3, 129, 10),
+                                         (4, 256, 11), (4, 200, 12)])
 def test_bitset_count_matches_brute_force(oracle, kind, n, seed):
     c = oracle.sprinkle(kind, n, seed)
     bits = oracle.causal_matrix(kind, c)
@@ -386,12 +429,23 @@ def test_null_and_equal_time_pairs_are_unrelated(oracle):
     assert not oracle.precedes(3, c3, 0, 1)    # 3^2 + 4^2 = 5^2
     assert not oracle.precedes(3, c3, 0, 2)    # dt = dx
     assert oracle.precedes(3, c3, 0, 3) and oracle.precedes(3, c3, 0, 4)
+    # de Sitter slab (eta, theta) on the conformal grid: the angle is taken
+    # around the circle of 2^20 cells
+    T = 2 ** 20
+    cds = np.array([[0, 10, 10, 11, 9, 0],
+                    [5, 15, 5, T - 5, T - 5, 6]], dtype=np.int32)
+    assert not oracle.precedes(4, cds, 0, 1)   # angle 10 = deta 10: null
+    assert oracle.precedes(4, cds, 0, 2)       # same angle, later
+    assert oracle.precedes(4, cds, 0, 3)       # angle 10 across theta = 0 < deta 11
+    assert not oracle.precedes(4, cds, 0, 4)   # angle 10 across theta = 0 > deta 9
+    assert not oracle.precedes(4, cds, 0, 5)   # equal time
+    assert not oracle.precedes(4, cds, 2, 0)   # past-directed
     assert oracle.precedes(3, c3, 1, 3)        # dt = 1 at the same place
     assert not oracle.precedes(3, c3, 2, 3)    # dt = 1 < |(-2, 4)|
     assert not oracle.precedes(3, c3, 3, 0)    # past-directed
 
 
-@pytest.mark.parametrize("kind,n,seed", [(0, 50, 123), (1, 50, 124), (2, 30, 125), (3, 40, 126)])
+@pytest.mark.parametrize("kind,n,seed", [(0, 50, 123), (1, 50, 124), (2, 30, 125), (3, 40, 126), (4, 60, 127)])
 def test_sprinkle_follows_generator_spec(oracle, kind, n, seed):
     # The thesis does not fix the random numbers, so the generator's own
     # specification is pinned here from the (already pinned) draws: ranks of
@@ -407,6 +461,30 @@ def test_sprinkle_follows_generator_spec(oracle, kind, n, seed):
     elif kind == 1:
         pts = [(oracle.draw(seed, 2, e, 0) >> 44, oracle.draw(seed, 2, e, 1) >> 44) for e in range(n)]
         order = sorted(range(n), key=lambda e: (pts[e][0] + pts[e][1], e))
+        assert c[0].tolist() == [pts[e][0] for e in order]
+        assert c[1].tolist() == [pts[e][1] for e in order]
+    elif kind == 4:
+        G = oracle.DS_CELLS
+        thr = {}
+
+        def threshold(g):
+            if g not in thr:
+                thr[g] = oracle.ds_threshold(g)
+            return thr[g]
+        pts = []
+        for e in range(n):
+            th = oracle.draw(seed, 5, e, 0) >> 44
+            u = oracle.draw(seed, 5, e, 1) >> 11
+            lo, hi = -G, G
+            while lo < hi:                      # smallest g with u < threshold(g)
+                mid = (lo + hi) // 2
+                if u < threshold(mid):
+                    hi = mid
+                else:
+                    lo = mid + 1
+            assert u < threshold(lo) and (lo == -G or u >= threshold(lo - 1))
+            pts.append((lo, th))
+        order = sorted(range(n), key=lambda e: (pts[e][0], e))
         assert c[0].tolist() == [pts[e][0] for e in order]
         assert c[1].tolist() == [pts[e][1] for e in order]
     elif kind == 3:
