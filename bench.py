@@ -298,7 +298,7 @@ def run_reference(args):
         "impl": "reference", "metric": f"interval-count Gpairs/s ({desc})", "value": value, "unit": "Gpairs/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": args.workload, "kind": ["2d_order", "2d_diamond", "4d_diamond", "3d_diamond"][kind], "n": n,
+        "config": {"workload": args.workload, "kind": ["2d_order", "2d_diamond", "4d_diamond", "3d_diamond", "2d_ds_slab"][kind], "n": n,
                    "seed": seed, "path": "cpu oracle", "eps": list(EPS),
                    "l2": "inputs larger than L2" if n * ((n + 63) // 64) * 8 > 129e6 else "inputs smaller than L2",
                    "parallelism": "replicas1"},

@@ -53,7 +53,12 @@ enum {
     CS_2D_ORDER = 0,    /* random 2D order: two uniform random permutations u, v */
     CS_2D_DIAMOND = 1,  /* 1+1 Minkowski diamond, light-cone coordinates on a 2^20 grid */
     CS_4D_DIAMOND = 2,  /* 3+1 Minkowski diamond of height 1, int32 grid of 2^20 per unit */
-    CS_3D_DIAMOND = 3   /* 2+1 Minkowski diamond of height 1, int32 grid of 2^20 per unit */
+    CS_3D_DIAMOND = 3,  /* 2+1 Minkowski diamond of height 1, int32 grid of 2^20 per unit */
+    CS_2D_DS_SLAB = 4   /* 1+1 de Sitter slab |eta| <= 0.5 (spherical foliation, pseudo-radius 1),
+                           Section "Spacetime Region Considered": coords[0] = eta (int32),
+                           coords[1] = theta (uint32 bits, a full turn = 2^32), both in units of
+                           2 pi / 2^32 rad.  The first sprinkle of this kind on a device uploads a
+                           1.3 MB constant table synchronously (do it before any stream capture). */
 };
 
 /* Interval-count paths. */
@@ -263,7 +268,7 @@ int cs_evaluate(int kind, int64_t n, uint64_t seed, const int32_t *coords_host, 
 
 /* One causal set of a batch. */
 typedef struct {
-    int32_t kind;      /* CS_2D_ORDER, CS_2D_DIAMOND, CS_4D_DIAMOND or CS_3D_DIAMOND */
+    int32_t kind;      /* a CS_* kind */
     int32_t reserved;  /* must be 0 */
     int64_t n;         /* 1 .. CS_BATCH_MAX_N */
     uint64_t seed;     /* the set equals cs_sprinkle(kind, n, seed, ...) */

@@ -50,11 +50,13 @@ typedef __float128 q128;  /* binary128 via libgcc soft-float */
 
 enum { OR_2D_ORDER = 0, OR_2D_DIAMOND = 1, OR_4D_DIAMOND = 2, OR_3D_DIAMOND = 3, OR_2D_DS_SLAB = 4 };
 
-/* de Sitter slab: eta and theta share the grid unit 2 pi / 2^20 rad; the slab
- * is the eta cells -OR_DS_G .. OR_DS_G, i.e. |eta| <= (OR_DS_G + 1/2) units,
- * and OR_DS_G = round(0.5 rad / unit) sets eta_0 = 0.5. */
+/* de Sitter slab: eta is drawn in coarse cells of 2 pi / 2^20 rad, the cells
+ * -OR_DS_G .. OR_DS_G, i.e. |eta| <= (OR_DS_G + 1/2) coarse units, and
+ * OR_DS_G = round(0.5 rad / coarse unit) sets eta_0 = 0.5.  Stored
+ * coordinates use the fine unit 2 pi / 2^32 rad (OR_DS_SUB fine units per
+ * coarse cell). */
 #define OR_DS_G 83443
-#define OR_TURN (1LL << 20)
+#define OR_DS_SUB 4096
 enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2, OR_ERANGE = -6 };
 
 /* ------------------------------------------------------------------ PRNG */
@@ -156,13 +158,18 @@ uint64_t oracle_ds_threshold(int64_t g)
  *   Region Considered", Eq. ds_metric; Appendix "Causal Set Sprinklings", de
  *   Sitter 1+1 Dimensional Slab) with eta_0 = 0.5 and pseudo-radius 1:
  *   theta uniform, eta with density sec^2(eta) / (2 tan eta_0), both on the
- *   grid of 2 pi / 2^20 rad.  theta = draw(stream 5, slot 0) >> 44.  eta is
- *   the inverse CDF of the cell masses: cell g (|g| <= G = 83443) covers
- *   [(g - 1/2), (g + 1/2)] units, and with t0 = tan((G + 1/2) unit) the
+ *   grid of 2 pi / 2^32 rad (the fine unit).  theta = draw(stream 5, slot 0)
+ *   >> 32, a full turn being 2^32 (stored as the int32 bit pattern).  eta
+ *   first picks a coarse cell of 4096 fine units by the inverse CDF of the
+ *   cell masses: coarse cell g (|g| <= G = 83443) covers [(g - 1/2),
+ *   (g + 1/2)] coarse units, and with t0 = tan((G + 1/2) coarse unit) the
  *   cumulative mass up to the end of cell g is
- *   x_g = (tan((g + 1/2) unit) + t0) / (2 t0) (exactly 1 for g = G);
- *   eta = the smallest g with U < floor(x_g 2^53), U = draw(stream 5, slot 1)
- *   >> 11.  Coordinates: coords[0] = eta cell, coords[1] = theta.
+ *   x_g = (tan((g + 1/2) coarse unit) + t0) / (2 t0) (exactly 1 for g = G);
+ *   g = the smallest cell with U < floor(x_g 2^53), U = draw(stream 5,
+ *   slot 1) >> 11.  Within the cell eta is uniform on the fine grid:
+ *   eta = 4096 g - 2048 + (draw(stream 5, slot 2) >> 52).  (sec^2 varies by
+ *   less than 1e-5 across one cell.)  Coordinates: coords[0] = eta,
+ *   coords[1] = theta, both in fine units.
  * Elements are sorted by time with ties broken by generation index
  * (Section "Pairwise Relations": elements are sorted by their time
  * coordinate before relations are identified).
@@ -213,15 +220,16 @@ int oracle_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords)
         or_pair *t = malloc((size_t)n * sizeof *t);
         if (!eta || !th || !t) { free(eta); free(th); free(t); return OR_ENOMEM; }
         for (int64_t e = 0; e < n; e++) {
-            th[e] = (int32_t)(oracle_draw(seed, 5, (uint64_t)e, 0) >> 44);
+            th[e] = (int32_t)(uint32_t)(oracle_draw(seed, 5, (uint64_t)e, 0) >> 32);
             uint64_t u = oracle_draw(seed, 5, (uint64_t)e, 1) >> 11;
             int64_t lo = -OR_DS_G, hi = OR_DS_G; /* answer in [lo, hi] */
             while (lo < hi) {
                 int64_t mid = lo + (hi - lo) / 2;
                 if (u < oracle_ds_threshold(mid)) hi = mid; else lo = mid + 1;
             }
-            eta[e] = (int32_t)lo;
-            t[e].key = lo;
+            int64_t off = (int64_t)(oracle_draw(seed, 5, (uint64_t)e, 2) >> 52);
+            eta[e] = (int32_t)(lo * OR_DS_SUB - OR_DS_SUB / 2 + off);
+            t[e].key = eta[e];
             t[e].idx = e;
         }
         qsort(t, (size_t)n, sizeof *t, or_cmp_pair);
@@ -280,10 +288,12 @@ int oracle_precedes(int kind, int64_t n, const int32_t *coords, int64_t a, int64
 {
     if (kind == OR_2D_DS_SLAB) {
         /* timelike iff the angular separation on the circle is below the
-         * conformal-time separation: pi - |pi - |dtheta|| < |deta| */
+         * conformal-time separation: pi - |pi - |dtheta|| < |deta|, with a
+         * full turn of 2^32 fine units */
         int64_t deta = (int64_t)coords[b] - coords[a];
-        int64_t dth = llabs((int64_t)coords[n + b] - coords[n + a]);
-        int64_t circ = dth < OR_TURN - dth ? dth : OR_TURN - dth;
+        int64_t ta = (int64_t)(uint32_t)coords[n + a], tb = (int64_t)(uint32_t)coords[n + b];
+        int64_t dth = tb > ta ? tb - ta : ta - tb;
+        int64_t circ = dth < (1LL << 32) - dth ? dth : (1LL << 32) - dth;
         return deta > 0 && circ < deta;
     }
     if (kind == OR_2D_ORDER || kind == OR_2D_DIAMOND) {

@@ -17,7 +17,7 @@ import os
 import threading
 
 __all__ = [
-    "KIND_2D_ORDER", "KIND_2D_DIAMOND", "KIND_4D_DIAMOND", "KIND_3D_DIAMOND", "PATH_AUTO", "PATH_POPC", "PATH_MMA",
+    "KIND_2D_ORDER", "KIND_2D_DIAMOND", "KIND_4D_DIAMOND", "KIND_3D_DIAMOND", "KIND_2D_DS_SLAB", "PATH_AUTO", "PATH_POPC", "PATH_MMA",
     "CsError", "lib", "dim", "coords_bytes", "row_words", "bitset_bytes", "hist_len",
     "sprinkle_workspace_bytes", "interval_abundance_workspace", "resolved_path", "action_workspace_bytes",
     "set_auto_paths", "get_auto_paths",
@@ -27,11 +27,11 @@ __all__ = [
     "inject_fault",
 ]
 
-KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND = 0, 1, 2, 3
+KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND, KIND_2D_DS_SLAB = 0, 1, 2, 3, 4
 PATH_AUTO, PATH_POPC, PATH_MMA = 0, 1, 2
 FAULT_ALLOC, FAULT_LAUNCH = 1, 2
 KIND_NAMES = {KIND_2D_ORDER: "2d_order", KIND_2D_DIAMOND: "2d_diamond", KIND_4D_DIAMOND: "4d_diamond",
-              KIND_3D_DIAMOND: "3d_diamond"}
+              KIND_3D_DIAMOND: "3d_diamond", KIND_2D_DS_SLAB: "2d_ds_slab"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(_HERE, "libcausetgb.so")

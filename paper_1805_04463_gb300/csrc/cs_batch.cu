@@ -59,7 +59,7 @@ __device__ __forceinline__ int find_set_elem(const BatchSet* sets, int nsets, in
 }
 
 __global__ void __launch_bounds__(256) k_batch_keys(const BatchSet* __restrict__ sets, int nsets, int64_t total,
-                                                    WsHeader* hdr) {
+                                                    const uint64_t* __restrict__ ds_thr, WsHeader* hdr) {
     for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
          idx += int64_t(gridDim.x) * blockDim.x) {
         const BatchSet& b = sets[find_set_elem(sets, nsets, idx)];
@@ -69,6 +69,8 @@ __global__ void __launch_bounds__(256) k_batch_keys(const BatchSet* __restrict__
                           b.key1[e]);
         } else if (b.kind == CS_2D_DIAMOND) {
             b.key0[e] = draw_2d_diamond(stream_key(b.seed, kStreamDiamond2), e, b.raw[e], b.raw[b.n + e]);
+        } else if (b.kind == CS_2D_DS_SLAB) {
+            b.key0[e] = draw_ds_slab(stream_key(b.seed, kStreamDeSitter), e, ds_thr, b.raw[e], b.raw[b.n + e]);
         } else {
             int32_t c[4];
             const bool ok = b.kind == CS_3D_DIAMOND
@@ -156,12 +158,14 @@ __global__ void __launch_bounds__(kRelThreads) k_batch_relate(const BatchSet* __
         const BatchSet& b = sets[lo];
         const int64_t local = blk - b.rblock_begin;
         const int64_t rb = local / b.col_groups, cg = local - rb * b.col_groups;
-        if (b.dim == 4)
-            relate_block<4>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
-        else if (b.dim == 3)
-            relate_block<3>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
+        if (b.kind == CS_4D_DIAMOND)
+            relate_block<kGeom4>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
+        else if (b.kind == CS_3D_DIAMOND)
+            relate_block<kGeom3>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
+        else if (b.kind == CS_2D_DS_SLAB)
+            relate_block<kGeomDeSitter>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
         else
-            relate_block<2>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
+            relate_block<kGeomLightCone>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
         __syncthreads();  // the next block restages sc
     }
 }
@@ -235,6 +239,7 @@ struct cs_batch {
     MmaSetEntry* mma_dev = nullptr;
     int64_t total_elems = 0, total_rblocks = 0, total_items = 0, total_pieces = 0, total_hist = 0;
     int max_pow2 = 1;
+    const uint64_t* ds_thr = nullptr;  // de Sitter thresholds, when a set needs them
 };
 
 namespace {
@@ -314,6 +319,9 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     if (p == CS_PATH_MMA && !device_has_tcgen05()) return CS_EUNSUPPORTED;
     const Layout L = batch_layout(sets, n_sets, p);
     if (workspace_bytes < L.total) return CS_ENOMEM;
+    const uint64_t* ds_thr = nullptr;
+    for (int s = 0; s < n_sets && !ds_thr; ++s)
+        if (sets[s].kind == CS_2D_DS_SLAB && !(ds_thr = ds_table_device())) return CS_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint8_t* ws = static_cast<uint8_t*>(workspace_dev);
 
@@ -387,6 +395,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     h->total_pieces = words;
     h->total_hist = hoff;
     h->max_pow2 = max_pow2;
+    h->ds_thr = ds_thr;
     cudaError_t e = cudaMemcpyAsync(h->sets_dev, bs.data(), sizeof(BatchSet) * bs.size(), cudaMemcpyHostToDevice, st);
     if (p == CS_PATH_MMA) {
         h->mma_dev = reinterpret_cast<MmaSetEntry*>(ws + L.entries);
@@ -425,7 +434,7 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
 
     int64_t g = (b->total_elems + 255) / 256;
     if (g > int64_t(sms) * 16) g = int64_t(sms) * 16;
-    k_batch_keys<<<unsigned(g), 256, 0, st>>>(b->sets_dev, b->nsets, b->total_elems, b->hdr);
+    k_batch_keys<<<unsigned(g), 256, 0, st>>>(b->sets_dev, b->nsets, b->total_elems, b->ds_thr, b->hdr);
 
     const size_t rank_smem = size_t(b->max_pow2) * 16;
     int dev = 0;

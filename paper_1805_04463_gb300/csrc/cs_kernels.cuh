@@ -7,6 +7,9 @@ namespace cs {
 
 // cs_sprinkle.cu
 size_t sprinkle_workspace_bytes(int64_t n);
+// Device copy of the de Sitter slab's cumulative eta thresholds (uploaded
+// once per device, synchronously, on first use); nullptr on failure.
+const uint64_t* ds_table_device();
 cudaError_t launch_sprinkle(int kind, int64_t n, uint64_t seed, int32_t* coords, void* workspace,
                             cudaStream_t st);
 

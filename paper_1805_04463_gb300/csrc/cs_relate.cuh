@@ -11,12 +11,25 @@ constexpr int kRelWordsPerBlock = kRelColsPerBlock / 64;
 constexpr int kRelRowsPerBlock = 64;
 constexpr int kRelThreads = 256;
 
+// Geometries of the relation test; the number of coordinates is geom_dim(G).
+constexpr int kGeomLightCone = 2, kGeom3 = 3, kGeom4 = 4, kGeomDeSitter = 5;
+constexpr int geom_dim(int g) { return g == kGeomDeSitter ? 2 : g; }
+
 // Symmetric timelike test between row element ci and staged column `col`:
-// du * dv > 0 (1+1, light-cone coordinates) or dt^2 - |dx|^2 > 0 (2+1, 3+1),
-// in int64.
-template <int DIM>
-__device__ __forceinline__ bool rel_related(const int32_t (&ci)[DIM], const int32_t (*sc)[kRelColsPerBlock], int col) {
-    if constexpr (DIM == 2) {
+// du * dv > 0 (1+1, light-cone coordinates), dt^2 - |dx|^2 > 0 (2+1, 3+1) in
+// int64, or, on the de Sitter slab's conformal grid (Eq. ds_metric), the
+// angular separation on the circle below the conformal-time separation.
+template <int G>
+__device__ __forceinline__ bool rel_related(const int32_t (&ci)[geom_dim(G)], const int32_t (*sc)[kRelColsPerBlock],
+                                            int col) {
+    if constexpr (G == kGeomDeSitter) {
+        // |eta| < 2^29, so de fits int32; theta differences wrap modulo 2^32,
+        // one full turn.
+        const int32_t de = sc[0][col] - ci[0];
+        const uint32_t d = uint32_t(sc[1][col]) - uint32_t(ci[1]);
+        const uint32_t circ = min(d, 0u - d);
+        return circ < uint32_t(abs(de));
+    } else if constexpr (G == kGeomLightCone) {
         // du * dv > 0 as a sign test (|du|, |dv| < 2^21 fit int32)
         const int32_t du = sc[0][col] - ci[0];
         const int32_t dv = sc[1][col] - ci[1];
@@ -25,7 +38,7 @@ __device__ __forceinline__ bool rel_related(const int32_t (&ci)[DIM], const int3
         const int64_t dt = int64_t(sc[0][col]) - ci[0];
         int64_t r2 = 0;
 #pragma unroll
-        for (int d = 1; d < DIM; ++d) {
+        for (int d = 1; d < G; ++d) {
             const int64_t dx = int64_t(sc[d][col]) - ci[d];
             r2 += dx * dx;
         }
@@ -37,10 +50,11 @@ __device__ __forceinline__ bool rel_related(const int32_t (&ci)[DIM], const int3
 // coordinates are staged in `sc`; each warp folds 64 tests per word into a
 // uint64 with two __ballot_sync, lane w keeps word w, and a row's 32 words
 // leave in one coalesced store.  Must be called by all 256 threads.
-template <int DIM>
+template <int G>
 __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords, int64_t n,
                                              uint64_t* __restrict__ bits, int64_t row_words, int64_t rb, int64_t cg,
                                              int32_t (*sc)[kRelColsPerBlock]) {
+    constexpr int DIM = geom_dim(G);
     const int64_t w0 = cg * kRelWordsPerBlock;
     const int64_t c0 = w0 * 64;
     for (int t = threadIdx.x; t < kRelColsPerBlock; t += kRelThreads) {
@@ -60,8 +74,8 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
 #pragma unroll 4
         for (int w = 0; w < kRelWordsPerBlock; ++w) {
             const int col = w * 64 + lane;
-            const bool b0 = c0 + col < n && rel_related<DIM>(ci, sc, col);
-            const bool b1 = c0 + col + 32 < n && rel_related<DIM>(ci, sc, col + 32);
+            const bool b0 = c0 + col < n && rel_related<G>(ci, sc, col);
+            const bool b1 = c0 + col + 32 < n && rel_related<G>(ci, sc, col + 32);
             const uint32_t lo = __ballot_sync(0xffffffffu, b0);
             const uint32_t hi = __ballot_sync(0xffffffffu, b1);
             if (lane == w) mine = (uint64_t(hi) << 32) | lo;

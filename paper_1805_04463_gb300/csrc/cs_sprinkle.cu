@@ -1,5 +1,6 @@
 // cs_sprinkle.cu -- sprinkling on the device (Section "Coordinate Generation",
-// Appendix "Causal Set Sprinklings": 1+1, 2+1 and 3+1 Minkowski diamonds).
+// Appendix "Causal Set Sprinklings": 1+1, 2+1 and 3+1 Minkowski diamonds and
+// the 1+1 de Sitter slab of Section "Spacetime Region Considered").
 //
 // Coordinates are drawn independently per element from the counter-based
 // generator, then elements are sorted by time (Section "Pairwise
@@ -8,12 +9,47 @@
 // bits (a counting pass, a scan, a fill), and each element compares itself
 // only with its bucket -- O(n + 65536) work for the hashed / uniform keys used
 // here, and the same ranks for any bucket fill order.
+#include <cmath>
+#include <mutex>
+#include <vector>
+
 #include "cs_kernels.cuh"
 #include "cs_sprinkle.cuh"
 
 namespace cs {
 
 namespace {
+
+constexpr int kMaxDevices = 64;
+
+// Cumulative sec^2 mass of the slab up to the end of each eta cell, scaled to
+// 2^53.  With unit = 2 pi / 2^20 and t0 = tan((G + 1/2) unit), cell g ends
+// at x_g = (tan((g + 1/2) unit) + t0) / (2 t0) (the density sec^2(eta) /
+// (2 tan eta_0) integrated from -eta_0); this exact expression, in double
+// with the C library's tan, is part of the generator's definition, so the
+// table is built on the host.
+static __device__ uint64_t g_ds_thresholds[kDsTable];
+const uint64_t* g_ds_ptr[kMaxDevices];
+std::once_flag g_ds_once[kMaxDevices];
+
+std::vector<uint64_t> ds_thresholds_host() {
+    std::vector<uint64_t> t(kDsTable);
+    const double unit = 2.0 * 3.14159265358979323846 / 1048576.0;
+    const double t0 = std::tan((double(kDsCells) + 0.5) * unit);
+    for (int i = 0; i < kDsTable; ++i) {
+        const double g = double(i - kDsCells);
+        const double x = (std::tan((g + 0.5) * unit) + t0) / (2.0 * t0);
+        t[i] = static_cast<uint64_t>(x * 9007199254740992.0);  // x * 2^53
+    }
+    return t;
+}
+
+__global__ void k_keys_ds_slab(int64_t n, uint64_t seed, const uint64_t* __restrict__ thr,
+                               int32_t* __restrict__ raw, uint64_t* __restrict__ key) {
+    const uint64_t s = stream_key(seed, kStreamDeSitter);
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+        key[e] = draw_ds_slab(s, e, thr, raw[e], raw[n + e]);
+}
 
 constexpr int kBucketBits = 16;
 constexpr int kBuckets = 1 << kBucketBits;
@@ -172,6 +208,19 @@ cudaError_t rank_keys(int64_t n, const uint64_t* key, uint32_t* rank, uint8_t* w
 
 }  // namespace
 
+const uint64_t* ds_table_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::call_once(g_ds_once[dev], [dev] {
+        static const std::vector<uint64_t> host = ds_thresholds_host();
+        void* p = nullptr;
+        if (cudaMemcpyToSymbol(g_ds_thresholds, host.data(), host.size() * sizeof(uint64_t)) == cudaSuccess &&
+            cudaGetSymbolAddress(&p, g_ds_thresholds) == cudaSuccess)
+            g_ds_ptr[dev] = static_cast<const uint64_t*>(p);
+    });
+    return g_ds_ptr[dev];
+}
+
 size_t sprinkle_workspace_bytes(int64_t n) { return sprinkle_layout(n).total; }
 
 cudaError_t launch_sprinkle(int kind, int64_t n, uint64_t seed, int32_t* coords, void* workspace,
@@ -193,12 +242,17 @@ cudaError_t launch_sprinkle(int kind, int64_t n, uint64_t seed, int32_t* coords,
         k_scatter_2d_order<<<g, kThreads, 0, st>>>(n, rank0, rank1, coords);
         return cudaGetLastError();
     }
-    if (kind == CS_2D_DIAMOND)
+    if (kind == CS_2D_DIAMOND) {
         k_keys_2d_diamond<<<g, kThreads, 0, st>>>(n, seed, raw, key0);
-    else if (kind == CS_3D_DIAMOND)
+    } else if (kind == CS_2D_DS_SLAB) {
+        const uint64_t* thr = ds_table_device();
+        if (!thr) return cudaErrorInvalidValue;
+        k_keys_ds_slab<<<g, kThreads, 0, st>>>(n, seed, thr, raw, key0);
+    } else if (kind == CS_3D_DIAMOND) {
         k_keys_diamond<3><<<g, kThreads, 0, st>>>(n, seed, raw, key0, hdr);
-    else
+    } else {
         k_keys_diamond<4><<<g, kThreads, 0, st>>>(n, seed, raw, key0, hdr);
+    }
     if ((err = rank_keys(n, key0, rank0, ws, L, st)) != cudaSuccess) return err;
     k_scatter_raw<<<g, kThreads, 0, st>>>(n, cs_dim(kind), rank0, raw, coords);
     return cudaGetLastError();

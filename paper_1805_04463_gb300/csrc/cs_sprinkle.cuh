@@ -8,7 +8,14 @@ namespace cs {
 
 // Stream numbers of the generator specification.
 constexpr uint32_t kStreamOrderU = 0, kStreamOrderV = 1, kStreamDiamond2 = 2, kStreamDiamond4 = 3,
-                   kStreamDiamond3 = 4;
+                   kStreamDiamond3 = 4, kStreamDeSitter = 5;
+
+// de Sitter slab: eta is drawn in coarse cells -kDsCells .. kDsCells of
+// 2 pi / 2^20 rad (eta_0 = 0.5 rad), then uniformly among the kDsSub fine
+// units (2 pi / 2^32 rad) of the cell; theta is a uint32, a full turn 2^32.
+constexpr int kDsCells = 83443;
+constexpr int kDsTable = 2 * kDsCells + 1;
+constexpr int kDsSub = 4096;
 
 // Random 2D order: the two 64-bit keys whose ranks are u and v.
 __device__ __forceinline__ void draw_2d_order(uint64_t su, uint64_t sv, int64_t e, uint64_t& ku, uint64_t& kv) {
@@ -62,6 +69,26 @@ __device__ __forceinline__ bool draw_4d_diamond(uint64_t s, int64_t e, int32_t (
 
 __device__ __forceinline__ bool draw_3d_diamond(uint64_t s, int64_t e, int32_t (&c)[4], uint64_t& key) {
     return draw_diamond<3>(s, e, c, key);
+}
+
+// 1+1 de Sitter slab (spherical foliation, Eq. ds_metric): theta uniform on
+// 2^32 fine units; the coarse eta cell is the inverse CDF of the sec^2 mass,
+// found by a binary search of the 53-bit uniform U against the cumulative
+// thresholds `thr` (thr[g + kDsCells] for cell g, the last one 2^53), and eta
+// is uniform among the cell's fine units.  Sort key: eta + 2^31 in the top
+// 32 bits.
+__device__ __forceinline__ uint64_t draw_ds_slab(uint64_t s, int64_t e, const uint64_t* __restrict__ thr,
+                                                 int32_t& eta, int32_t& theta) {
+    theta = int32_t(uint32_t(draw_from(s, uint64_t(e), 0) >> 32));
+    const uint64_t u = draw_from(s, uint64_t(e), 1) >> 11;
+    int lo = 0, hi = kDsTable - 1;  // smallest index with u < thr[index]
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (u < thr[mid]) hi = mid; else lo = mid + 1;
+    }
+    const int32_t off = int32_t(draw_from(s, uint64_t(e), 2) >> 52);
+    eta = (lo - kDsCells) * kDsSub - kDsSub / 2 + off;
+    return uint64_t(uint32_t(eta) ^ 0x80000000u) << 32;
 }
 
 }  // namespace cs

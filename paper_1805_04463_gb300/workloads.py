@@ -11,7 +11,7 @@ from __future__ import annotations
 import numpy as np
 
 SEED_BASE = 0xC5E70000
-KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND = 0, 1, 2, 3
+KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND, KIND_2D_DS_SLAB = 0, 1, 2, 3, 4
 
 # name: (kind, n, seed, description)
 SINGLE = {

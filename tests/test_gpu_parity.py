@@ -48,7 +48,7 @@ def _np_bits(b):
     return b.bits.cpu().numpy().view(np.uint64)
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("n", [1, 2, 3, 63, 64, 65, 129, 1000, 4097])
 def test_sprinkle_and_relate_bit_exact(cs, oracle, kind, n):
     seed = 0xC5E70000 + 31 * n + kind
@@ -62,7 +62,7 @@ def test_sprinkle_and_relate_bit_exact(cs, oracle, kind, n):
 @pytest.mark.parametrize("kind,n", [(0, 2), (0, 3), (0, 127), (0, 128), (0, 129), (0, 255), (0, 256), (0, 257),
                                     (0, 300), (0, 511), (0, 1000), (0, 1024), (0, 2049), (0, 4133), (1, 129),
                                     (1, 1500), (1, 3001), (2, 200), (2, 1111), (2, 4096), (2, 5000),
-                                    (3, 250), (3, 1777), (3, 4096), (3, 6000)])
+                                    (3, 250), (3, 1777), (3, 4096), (3, 6000), (4, 255), (4, 2500), (4, 5003)])
 def test_interval_abundance_bit_exact(cs, oracle, kind, n, path):
     seed = 0xC5E71000 + n + kind
     b = _run(cs, kind, n, seed, path=path)
@@ -103,7 +103,7 @@ def test_full_chain_131072_counts_exact(cs, path):
     assert (h == np.arange(n - 1, 0, -1)).all()
 
 
-@pytest.mark.parametrize("kind,n", [(0, 1024), (2, 3000), (1, 2500), (3, 3000)])
+@pytest.mark.parametrize("kind,n", [(0, 1024), (2, 3000), (1, 2500), (3, 3000), (4, 4000)])
 def test_action_device_and_host(cs, oracle, kind, n):
     import torch
     seed = 77 + n

@@ -153,17 +153,21 @@ def test_ds_slab_thresholds_and_eta_distribution(oracle):
     # Sampled eta: P(|eta| < 1/4 rad) = tan(1/4) / tan(eta_0) for the density
     # sec^2(eta) / (2 tan eta_0); theta uniform on the circle.
     n = 20000
-    c = oracle.sprinkle(oracle.KIND_2D_DS_SLAB, n, 8).astype(np.int64)
-    eta, th = c
-    assert (np.diff(eta) >= 0).all() and (np.abs(eta) <= G).all()
-    assert ((th >= 0) & (th < 2 ** 20)).all()
-    unit = 2 * math.pi / 2 ** 20
-    e0 = (G + 0.5) * unit
+    c = oracle.sprinkle(oracle.KIND_2D_DS_SLAB, n, 8)
+    eta = c[0].astype(np.int64)
+    th = c[1].view(np.uint32).astype(np.int64)          # a full turn is 2^32
+    S = oracle.DS_SUB
+    assert (np.diff(eta) >= 0).all() and (np.abs(eta) <= G * S + S // 2).all()
+    unit = 2 * math.pi / 2 ** 32
+    e0 = (G + 0.5) * S * unit
     p = math.tan(0.25) / math.tan(e0)
     frac = (np.abs(eta * unit) < 0.25).mean()
     assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / n)
-    q = (th < 2 ** 18).mean()
+    q = (th < 2 ** 30).mean()
     assert abs(q - 0.25) < 5 * math.sqrt(0.25 * 0.75 / n)
+    # within a coarse cell eta is uniform on the fine grid
+    off = (eta + S // 2) % S
+    assert abs(off.mean() / S - 0.5) < 5 * math.sqrt(1 / 12 / n)
 
 
 def test_ds_slab_relation_fraction(oracle):
@@ -430,10 +434,10 @@ def test_null_and_equal_time_pairs_are_unrelated(oracle):
     assert not oracle.precedes(3, c3, 0, 2)    # dt = dx
     assert oracle.precedes(3, c3, 0, 3) and oracle.precedes(3, c3, 0, 4)
     # de Sitter slab (eta, theta) on the conformal grid: the angle is taken
-    # around the circle of 2^20 cells
-    T = 2 ** 20
+    # around the circle of 2^32 fine units (theta stored as uint32 bits)
+    T = 2 ** 32
     cds = np.array([[0, 10, 10, 11, 9, 0],
-                    [5, 15, 5, T - 5, T - 5, 6]], dtype=np.int32)
+                    np.array([5, 15, 5, T - 5, T - 5, 6], dtype=np.uint32).view(np.int32)], dtype=np.int32)
     assert not oracle.precedes(4, cds, 0, 1)   # angle 10 = deta 10: null
     assert oracle.precedes(4, cds, 0, 2)       # same angle, later
     assert oracle.precedes(4, cds, 0, 3)       # angle 10 across theta = 0 < deta 11
@@ -472,8 +476,9 @@ def test_sprinkle_follows_generator_spec(oracle, kind, n, seed):
                 thr[g] = oracle.ds_threshold(g)
             return thr[g]
         pts = []
+        S = oracle.DS_SUB
         for e in range(n):
-            th = oracle.draw(seed, 5, e, 0) >> 44
+            th = oracle.draw(seed, 5, e, 0) >> 32
             u = oracle.draw(seed, 5, e, 1) >> 11
             lo, hi = -G, G
             while lo < hi:                      # smallest g with u < threshold(g)
@@ -483,10 +488,11 @@ def test_sprinkle_follows_generator_spec(oracle, kind, n, seed):
                 else:
                     lo = mid + 1
             assert u < threshold(lo) and (lo == -G or u >= threshold(lo - 1))
-            pts.append((lo, th))
+            eta = lo * S - S // 2 + (oracle.draw(seed, 5, e, 2) >> 52)
+            pts.append((eta, th))
         order = sorted(range(n), key=lambda e: (pts[e][0], e))
         assert c[0].tolist() == [pts[e][0] for e in order]
-        assert c[1].tolist() == [pts[e][1] for e in order]
+        assert c[1].view(np.uint32).tolist() == [pts[e][1] for e in order]
     elif kind == 3:
         pts = []
         for e in range(n):
