@@ -143,8 +143,11 @@ uint64_t oracle_ds_threshold(int64_t g)
  *   A 2D order is the 1+1 Minkowski diamond in light-cone coordinates
  *   (Appendix "Causal Set Sprinklings", 1+1 Dimensional Diamond) with only
  *   the order of u and v kept.
- * kind 1, 2D diamond: u, v uniform on the grid [0, 2^20) (same appendix
- *   entry, u* = U u0 with u0 = 1), time t = u + v.
+ * kind 1, 2D diamond: u, v uniform on the grid [0, 2^31) (same appendix
+ *   entry, u* = U u0 with u0 = 1; u, v = draw >> 33), time t = u + v.  The
+ *   grid is fine enough that grid-null pairs (du = 0 or dv = 0, unrelated)
+ *   are negligible: about N^2 / 2^31 of them, against N^2 / 2^20 on a 2^20
+ *   grid, which at N = 2^17 would remove ~10^4 near-null links.
  * kind 2, 4D diamond of height 1: rejection sampling (allowed by the
  *   appendix's general method) in the box t in [0, 2^20),
  *   x, y, z in [-2^19, 2^19): accept iff x^2+y^2+z^2 < min(t, 2^20-t)^2.
@@ -202,8 +205,8 @@ int oracle_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords)
         or_pair *t = malloc((size_t)n * sizeof *t);
         if (!u || !v || !t) { free(u); free(v); free(t); return OR_ENOMEM; }
         for (int64_t e = 0; e < n; e++) {
-            u[e] = (int32_t)(oracle_draw(seed, 2, (uint64_t)e, 0) >> 44);
-            v[e] = (int32_t)(oracle_draw(seed, 2, (uint64_t)e, 1) >> 44);
+            u[e] = (int32_t)(oracle_draw(seed, 2, (uint64_t)e, 0) >> 33);
+            v[e] = (int32_t)(oracle_draw(seed, 2, (uint64_t)e, 1) >> 33);
             t[e].key = (int64_t)u[e] + v[e];
             t[e].idx = e;
         }

@@ -83,13 +83,14 @@ def test_2d_diamond_grid_and_time_order(oracle):
     n = 20000
     c = oracle.sprinkle(oracle.KIND_2D_DIAMOND, n, 11)
     u, v = c[0].astype(np.int64), c[1].astype(np.int64)
-    assert u.min() >= 0 and v.min() >= 0 and u.max() < oracle.GRID and v.max() < oracle.GRID
+    g = 2 ** 31
+    assert u.min() >= 0 and v.min() >= 0 and u.max() < g and v.max() < g
     t = u + v
     assert (np.diff(t) >= 0).all()
-    # uniform marginals on [0, 2^20): mean 2^19, s.e. 2^20/sqrt(12 n)
-    se = oracle.GRID / math.sqrt(12 * n)
-    assert abs(u.mean() - oracle.GRID / 2) < 5 * se
-    assert abs(v.mean() - oracle.GRID / 2) < 5 * se
+    # uniform marginals on [0, 2^31): mean 2^30, s.e. 2^31/sqrt(12 n)
+    se = g / math.sqrt(12 * n)
+    assert abs(u.mean() - g / 2) < 5 * se
+    assert abs(v.mean() - g / 2) < 5 * se
 
 
 def test_4d_diamond_inside_and_time_distribution(oracle):
@@ -463,7 +464,7 @@ def test_sprinkle_follows_generator_spec(oracle, kind, n, seed):
         want_v = [vrank[e] for _, e in sorted(ku)]
         assert c[0].tolist() == list(range(n)) and c[1].tolist() == want_v
     elif kind == 1:
-        pts = [(oracle.draw(seed, 2, e, 0) >> 44, oracle.draw(seed, 2, e, 1) >> 44) for e in range(n)]
+        pts = [(oracle.draw(seed, 2, e, 0) >> 33, oracle.draw(seed, 2, e, 1) >> 33) for e in range(n)]
         order = sorted(range(n), key=lambda e: (pts[e][0] + pts[e][1], e))
         assert c[0].tolist() == [pts[e][0] for e in order]
         assert c[1].tolist() == [pts[e][1] for e in order]
