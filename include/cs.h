@@ -51,7 +51,7 @@ typedef enum {
 /* Causal-set kinds (Appendix "Causal Set Sprinklings"). */
 enum {
     CS_2D_ORDER = 0,    /* random 2D order: two uniform random permutations u, v */
-    CS_2D_DIAMOND = 1,  /* 1+1 Minkowski diamond, light-cone coordinates on a 2^20 grid */
+    CS_2D_DIAMOND = 1,  /* 1+1 Minkowski diamond, light-cone coordinates u, v on a 2^31 grid */
     CS_4D_DIAMOND = 2,  /* 3+1 Minkowski diamond of height 1, int32 grid of 2^20 per unit */
     CS_3D_DIAMOND = 3,  /* 2+1 Minkowski diamond of height 1, int32 grid of 2^20 per unit */
     CS_2D_DS_SLAB = 4   /* 1+1 de Sitter slab |eta| <= 0.5 (spherical foliation, pseudo-radius 1),

@@ -30,7 +30,7 @@ __device__ __forceinline__ bool rel_related(const int32_t (&ci)[geom_dim(G)], co
         const uint32_t circ = min(d, 0u - d);
         return circ < uint32_t(abs(de));
     } else if constexpr (G == kGeomLightCone) {
-        // du * dv > 0 as a sign test (|du|, |dv| < 2^21 fit int32)
+        // du * dv > 0 as a sign test (|du|, |dv| < 2^31 fit int32)
         const int32_t du = sc[0][col] - ci[0];
         const int32_t dv = sc[1][col] - ci[1];
         return (du ^ dv) >= 0 && du != 0 && dv != 0;

@@ -23,13 +23,14 @@ __device__ __forceinline__ void draw_2d_order(uint64_t su, uint64_t sv, int64_t 
     kv = draw_from(sv, uint64_t(e), 0);
 }
 
-// 2D diamond: u, v on the 2^20 grid; sort key (u + v) in the top 21 bits.
+// 2D diamond: u, v on the 2^31 grid (grid-null pairs, du = 0 or dv = 0, are
+// then negligible); sort key (u + v) in the top 32 bits.
 __device__ __forceinline__ uint64_t draw_2d_diamond(uint64_t s, int64_t e, int32_t& u, int32_t& v) {
-    const uint32_t uu = uint32_t(draw_from(s, uint64_t(e), 0) >> (64 - kGridBits));
-    const uint32_t vv = uint32_t(draw_from(s, uint64_t(e), 1) >> (64 - kGridBits));
+    const uint32_t uu = uint32_t(draw_from(s, uint64_t(e), 0) >> 33);
+    const uint32_t vv = uint32_t(draw_from(s, uint64_t(e), 1) >> 33);
     u = int32_t(uu);
     v = int32_t(vv);
-    return uint64_t(uu + vv) << (64 - (kGridBits + 1));
+    return uint64_t(uu + vv) << 32;
 }
 
 // D-dimensional diamond of height 1 (D = 3: 2+1, D = 4: 3+1): rejection
