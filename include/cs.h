@@ -97,17 +97,19 @@ size_t cs_sprinkle_workspace_bytes(int kind, int64_t n);
  * Sprinkle n elements of `kind` from `seed` and write their time-sorted
  * coordinates to coords_dev (cs_coords_bytes bytes, layout above).
  * Section "Coordinate Generation" and Appendix "Causal Set Sprinklings"
- * (1+1 and 3+1 Minkowski diamonds): coordinates are drawn independently per
- * element and the elements are then sorted by time (Section "Pairwise
- * Relations").  The random numbers are the counter-based SplitMix64 stream
- * (draw(seed, stream, element, slot) = output element*65536+slot of the
- * generator seeded with output `stream` of the generator seeded with seed);
- * a 2D order is the pair of rank permutations of streams 0 and 1, relabelled
- * by u; a 2D diamond draws u, v from stream 2; a 4D diamond rejection-samples
- * (t, x, y, z) from stream 3 inside |x| < min(t, 1 - t).
+ * (1+1, 2+1 and 3+1 Minkowski diamonds, the 1+1 de Sitter slab):
+ * coordinates are drawn independently per element and the elements are then
+ * sorted by time (Section "Pairwise Relations").  The random numbers are the
+ * counter-based SplitMix64 stream (draw(seed, stream, element, slot) = output
+ * element*65536+slot of the generator seeded with output `stream` of the
+ * generator seeded with seed); a 2D order is the pair of rank permutations
+ * of streams 0 and 1, relabelled by u (coords[0] = 0..n-1); a 2D diamond
+ * draws u, v from stream 2 (draw >> 33); a 4D (3D) diamond rejection-samples
+ * (t, x, y, z) from stream 3 ((t, x, y) from stream 4) inside
+ * |x| < min(t, 1 - t); the de Sitter slab draws theta and eta from stream 5.
  * Errors: CS_EINVAL (n < 1, n > 2^22, bad kind, NULL coords),
- * CS_ENOMEM (workspace too small), CS_ECUDA.  A 4D element that finds no
- * point in 16384 attempts sets CS_ERANGE in the workspace status word.
+ * CS_ENOMEM (workspace too small), CS_ECUDA.  A 3D or 4D element that finds
+ * no point in 16384 attempts sets CS_ERANGE in the workspace status word.
  */
 int cs_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords_dev,
                 void *workspace_dev, size_t workspace_bytes, void *stream);
@@ -119,9 +121,12 @@ int cs_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords_dev,
  * Totally Ordered Sets": one bitset per row) from time-sorted coordinates.
  * Bit j of row i (word j/64, bit j%64, least significant bit first) is 1 iff
  * i and j are timelike related, Delta s^2 < 0 strictly (Section
- * "Lorentzian Geometry"); 2D kinds: du * dv > 0; 4D: dt^2 > |dx|^2, exact in
- * int64.  row_words must be >= cs_row_words(n) and a multiple of 16; bits_dev
- * holds n * row_words uint64 and is fully written (padding bits zero).
+ * "Lorentzian Geometry"); 1+1 diamond and 2D order: du * dv > 0; 3D and 4D:
+ * dt^2 > |dx|^2, exact in int64; de Sitter slab: the angle around the circle
+ * (mod 2^32) is below |d eta|.  For CS_2D_ORDER, coords[0] must increase
+ * strictly with the label (as cs_sprinkle writes it: 0..n-1).  row_words
+ * must be >= cs_row_words(n) and a multiple of 16; bits_dev holds
+ * n * row_words uint64 and is fully written (padding bits zero).
  * Errors: CS_EINVAL, CS_ECUDA.
  */
 int cs_causal_matrix(int kind, int64_t n, const int32_t *coords_dev,
@@ -238,7 +243,10 @@ size_t cs_action_workspace_bytes(void);
  * *bracket_dev (may be NULL) the local bracket.  Asynchronous on `stream`;
  * hist_dev is the device histogram written by cs_interval_abundance.  The
  * smeared sums are split over 128 blocks whose double-double partial sums
- * go to the workspace.
+ * go to the workspace.  Both action entry points stop each smeared sum at
+ * the first k past which the remaining terms provably move S by less than
+ * 1e-15 (bounding the abundances' sum by n(n-1)/2 here, by the histogram's
+ * own sum in cs_action).
  * Errors: CS_EINVAL (as cs_action, or n_eps outside 1..16), CS_ENOMEM
  * (workspace too small), CS_ECUDA.
  */

@@ -17,8 +17,8 @@ namespace cs {
 
 namespace {
 
-__global__ void __launch_bounds__(kActThreads) k_action_partial(int dim, const int64_t* __restrict__ hist, int64_t len,
-                                                                EpsArgs eps, dd* __restrict__ partial) {
+__global__ void __launch_bounds__(kActThreads) k_action_partial(int dim, int64_t n, const int64_t* __restrict__ hist,
+                                                                int64_t len, EpsArgs eps, dd* __restrict__ partial) {
     __shared__ dd red[kActThreads];
     const int tid = threadIdx.x;
     const int64_t stride = int64_t(gridDim.x) * kActThreads;
@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(kActThreads) k_action_partial(int dim, const i
         const double ep = eps.v[e];
         if (is_local(ep)) continue;  // uniform across the grid
         const dd q = dd_two_sum(1.0, -ep);
-        const int64_t kend = smear_cutoff(ep, len);
+        const int64_t kend = eps.kend[e];
         dd sum = dd_from(0.0);
         for (int64_t k = blockIdx.x * int64_t(kActThreads) + tid; k < kend; k += stride) {
             const int64_t hk = hist[k];
@@ -114,7 +114,9 @@ int action_host(int dim, int64_t n, const int64_t* hist, int64_t len, double eps
         s = local_action(dim, b);
     } else {
         const dd q = dd_two_sum(1.0, -eps);
-        const int64_t kend = smear_cutoff(eps, len);
+        double R = 0.0;  // any histogram may come in here: bound by its own sum
+        for (int64_t k = 0; k < len; ++k) R += fabs(double(hist[k]));
+        const int64_t kend = smear_cutoff(dim, eps, R, len);
         dd sum = dd_from(0.0), p = dd_from(1.0);  // p = q^(max(0, k - deg))
         const int64_t deg = smear_deg(dim);
         for (int64_t k = 0; k < kend; ++k) {
@@ -134,10 +136,11 @@ cudaError_t launch_action_device(int dim, int64_t n, const int64_t* hist, int64_
     bool any_smeared = false;
     for (int e = 0; e < kMaxEps; ++e) {
         a.v[e] = e < n_eps ? eps[e] : 0.0;
+        a.kend[e] = is_local(a.v[e]) ? 0 : smear_cutoff(dim, a.v[e], 0.5 * double(n) * double(n), len);
         if (e < n_eps && !is_local(a.v[e])) any_smeared = true;
     }
     dd* partial = reinterpret_cast<dd*>(static_cast<uint8_t*>(workspace) + sizeof(WsHeader));
-    if (any_smeared) k_action_partial<<<kActBlocks, kActThreads, 0, st>>>(dim, hist, len, a, partial);
+    if (any_smeared) k_action_partial<<<kActBlocks, kActThreads, 0, st>>>(dim, n, hist, len, a, partial);
     k_action_final<<<1, 32, 0, st>>>(dim, n, hist, len, a, partial, kActBlocks, out, bracket);
     return cudaGetLastError();
 }

@@ -15,6 +15,7 @@ constexpr int kActBlocks = 128;
 
 struct EpsArgs {
     double v[kMaxEps];
+    int64_t kend[kMaxEps];  // smeared-sum cutoffs (single-set kernels; set on the host)
     int n;
 };
 
@@ -80,13 +81,29 @@ __host__ __device__ inline dd smeared_action(int dim, int64_t n, double eps, dd 
     return dd_mul(pref, inner);
 }
 
-// Beyond this k, (1-eps)^k < 1e-330: every remaining term is below the
-// double-double resolution of any non-zero sum and is dropped.
-__host__ __device__ inline int64_t smear_cutoff(double eps, int64_t len) {
-    const double l = -log1p(-eps);
-    if (!(l > 0.0)) return len;
-    const double kc = 760.0 / l + 8.0;
-    return kc < double(len) ? int64_t(kc) : len;
+// Terms k >= K of the smeared sum that can be dropped.  For k >= deg,
+// f_d(k) = q^(k-deg) poly_d(k) with q = 1 - eps and
+//   |poly_2| <= (1 + k eps)^2, |poly_3| <= 3.375 (1 + k eps)^2,
+//   |poly_4| <= 9 (1 + k eps)^3,
+// so |f_d(k)| <= B(k) = C (1 + k eps)^m q^(k-deg), which decreases for
+// k >= m / eps.  With R >= the sum of the abundances (n(n-1)/2 bounds it for
+// any histogram of n elements) the dropped tail is at most R B(K), and the
+// sum enters S multiplied by at most 4 (4 eps^2, c3 eps^(5/3) or
+// 4 sqrt(eps/6) eps).  K is the first k >= max(deg, m/eps) with
+// 4 R B(K) <= 1e-15: the truncation moves S by less than 1e-15.
+__host__ __device__ inline int64_t smear_cutoff(int dim, double eps, double R, int64_t len) {
+    const double lq = log1p(-eps);  // ln q < 0
+    if (!(lq < 0.0)) return len;
+    const double C = dim == 2 ? 1.0 : (dim == 3 ? 3.375 : 9.0);
+    const double m = dim == 4 ? 3.0 : 2.0;
+    const double deg = dim == 4 ? 3.0 : 2.0;
+    const double lhs0 = log(4.0 * fmax(R, 1.0) * C) + 34.6;  // ln(4 R C) - ln(1e-15)
+    double k = fmax(deg, ceil(m / eps));
+    // Fixed point of k = deg + (lhs0 + m ln(1 + k eps)) / (-ln q), approached
+    // from below; the map's slope there is about m / (1 + k eps) < 0.1.
+    for (int it = 0; it < 24; ++it) k = fmax(k, deg + (lhs0 + m * log1p(k * eps)) / -lq);
+    k = ceil(k) + 8.0;
+    return k < double(len) ? int64_t(k) : len;
 }
 
 

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kRelThreads) k_batch_relate(const BatchSet* __
         else if (b.kind == CS_2D_DS_SLAB)
             relate_block<kGeomDeSitter>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
         else
-            relate_block<kGeomLightCone>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
+            relate_block<kGeomLightCone>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc, b.kind == CS_2D_ORDER);
         __syncthreads();  // the next block restages sc
     }
 }
@@ -177,9 +177,17 @@ __global__ void __launch_bounds__(kActThreads) k_batch_action(const BatchSet* __
                                                               double* __restrict__ actions,
                                                               int64_t* __restrict__ brackets) {
     __shared__ dd red[kActThreads];
+    __shared__ int64_t kends[kMaxEps];
     const BatchSet& b = sets[blockIdx.x];
     const int dim = b.dim;
     const int64_t n = b.n, len = n > 1 ? n - 1 : 1;
+    // cutoffs of this set, one thread per eps (the first barrier below
+    // publishes them)
+    if (threadIdx.x < eps.n)
+        kends[threadIdx.x] = is_local(eps.v[threadIdx.x])
+                                 ? 0
+                                 : smear_cutoff(dim, eps.v[threadIdx.x], 0.5 * double(n) * double(n), len);
+    __syncthreads();
     const int64_t* hist = hist_base + b.hist_off;
     const int tid = threadIdx.x;
     int64_t h4[4] = {0, 0, 0, 0};
@@ -197,7 +205,7 @@ __global__ void __launch_bounds__(kActThreads) k_batch_action(const BatchSet* __
         }
         const dd q = dd_two_sum(1.0, -ep);
         const dd step = dd_pow(q, kActThreads);
-        const int64_t kend = smear_cutoff(ep, len);
+        const int64_t kend = kends[e];
         const int64_t deg = smear_deg(dim);
         dd sum = dd_from(0.0), p = dd_from(1.0);
         for (int64_t k = tid; k < kend; k += kActThreads) {
@@ -237,7 +245,7 @@ struct cs_batch {
     BatchSet* sets_dev = nullptr;
     PopcSetEntry* popc_dev = nullptr;
     MmaSetEntry* mma_dev = nullptr;
-    int64_t total_elems = 0, total_rblocks = 0, total_items = 0, total_pieces = 0, total_hist = 0;
+    int64_t total_elems = 0, total_rblocks = 0, total_items = 0, total_rows = 0, total_hist = 0;
     int max_pow2 = 1;
     const uint64_t* ds_thr = nullptr;  // de Sitter thresholds, when a set needs them
 };
@@ -353,7 +361,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     std::vector<int> order(static_cast<size_t>(n_sets));
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bs[a].n > bs[b].n; });
-    int64_t items = 0, words = 0;
+    int64_t items = 0, rows = 0;
     std::vector<PopcSetEntry> pe;
     std::vector<MmaSetEntry> me;
     for (int r = 0; r < n_sets; ++r) {
@@ -367,8 +375,8 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
             e.item_offset = 0;
             items += mma_items(b.n);
             e.hist_off = b.hist_off * 8;
-            e.word_begin = words;
-            words += b.n * (e.kpad / 16);
+            e.row_begin = rows;
+            rows += b.n;
             me.push_back(e);
         } else {
             PopcSetEntry e;
@@ -392,7 +400,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     h->total_elems = elem;
     h->total_rblocks = rblk;
     h->total_items = items;
-    h->total_pieces = words;
+    h->total_rows = rows;
     h->total_hist = hoff;
     h->max_pow2 = max_pow2;
     h->ds_thr = ds_thr;
@@ -424,6 +432,7 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
     a.n = n_eps;
     for (int e = 0; e < kMaxEps; ++e) {
         a.v[e] = e < n_eps ? eps_host[e] : 0.0;
+        a.kend[e] = 0;  // per set, in the kernel
         if (e < n_eps && !(a.v[e] <= 1.0)) return CS_EINVAL;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -452,7 +461,7 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
     if ((err = cudaGetLastError()) != cudaSuccess) return CS_ECUDA;
 
     if (b->path == CS_PATH_MMA) {
-        if ((err = launch_expand_multi(b->mma_dev, b->nsets, b->total_pieces, st)) != cudaSuccess) return CS_ECUDA;
+        if ((err = launch_expand_multi(b->mma_dev, b->nsets, b->total_rows, st)) != cudaSuccess) return CS_ECUDA;
         err = launch_count_mma_multi(b->mma_dev, b->nsets, b->total_items, reinterpret_cast<uintptr_t>(hist_dev),
                                      b->hdr, 0, st);
     } else {

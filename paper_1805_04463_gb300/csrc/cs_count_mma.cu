@@ -23,10 +23,11 @@
 //               (128B swizzle) into a 4-stage shared-memory ring;
 //   warp 1      TMEM allocator and MMA issuer: 4 x tcgen05.mma (M128 N256 K32)
 //               per stage into one of two TMEM accumulators (2 x 256 columns);
-//   warps 2..5  epilogue: tcgen05.ld of the finished accumulator (one TMEM
-//               lane = one row i per thread), mask by i < j < n and C_ij from
-//               the bitset, bucket k into a shared-memory histogram (global
-//               atomics above 8192), then release the accumulator.
+//   warps 2..9  epilogue: tcgen05.ld of the finished accumulator (one TMEM
+//               lane = one row i per thread; two warps per lane quarter, each
+//               taking half of the 256 columns), mask by i < j < n and C_ij
+//               from the bitset, bucket k into a shared-memory histogram
+//               (global atomics above 8192), then release the accumulator.
 // The K loop of a tile runs only over the K-blocks between the i-block and the
 // end of the j-block.  C.C is never written to memory.
 #include "cs_kernels.cuh"
@@ -44,7 +45,11 @@ constexpr int kABytes = kBM * kBK;       // 16 KiB
 constexpr int kBBytes = kBN * kBK;       // 32 KiB
 constexpr int kStageBytes = kABytes + kBBytes;
 constexpr int kHistBins = 8192;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;             // two epilogue warps per TMEM lane quarter
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = 64 + kEpiThreads;
+constexpr int kEpiChunks = (kBN / 32) / (kEpiWarps / 4);  // 32-column chunks per epilogue warp
+static_assert(kEpiWarps % 4 == 0 && (kBN / 32) % (kEpiWarps / 4) == 0, "epilogue warps split the columns evenly");
 constexpr int kTmemCols = 512;           // two 256-column FP32 accumulators
 constexpr uint32_t kIdesc = idesc_f8_f32(kBM, kBN);
 constexpr int kRing = 4;                 // item indices in flight between the roles
@@ -109,8 +114,18 @@ __device__ __forceinline__ void store16(uint8_t* dst, uint32_t bits16) {
     *reinterpret_cast<uint4*>(dst) = v;
 }
 
+// The parts of the operands any tile reads (decode_item): row i of U is an A
+// row of the tile starting at I0 = 128 * floor(i / 128), whose K range starts
+// at I0; row j of L is a B row of the tile starting at J0 = 256 * floor(j /
+// 256), whose K range ends at J0 + 256.  In 16-column pieces: U row i from
+// piece u_first_piece(i), L row j below piece l_end_piece(j).  Nothing reads
+// the rest, so the expansion leaves it unwritten (half of the 2 n^2 bytes).
+__device__ __forceinline__ int64_t u_first_piece(int64_t i) { return (i / kBM) * (kBM / 16); }
+__device__ __forceinline__ int64_t l_end_piece(int64_t j) { return (j / kBN + 1) * (kBN / 16); }
+
 // Columns [16c, 16c+16) of row i: U keeps the columns after i, L the columns
-// before i.  Consecutive threads write consecutive 16-byte pieces.
+// before i, each only where a tile reads it.  Consecutive threads write
+// consecutive 16-byte pieces.
 __device__ __forceinline__ void expand_piece(const uint64_t* __restrict__ bits, int64_t row_words, int64_t kpad,
                                              uint8_t* __restrict__ U, uint8_t* __restrict__ L, int64_t i, int64_t c) {
     const int64_t w = c >> 2;
@@ -119,39 +134,66 @@ __device__ __forceinline__ void expand_piece(const uint64_t* __restrict__ bits, 
     const int64_t x = i - 64 * w;  // bit position of column i inside this word
     const uint64_t after = x < 0 ? ~0ull : (x >= 63 ? 0ull : (~0ull << (x + 1)));
     const uint64_t before = x <= 0 ? 0ull : (x >= 64 ? ~0ull : ((1ull << x) - 1ull));
-    store16(U + i * kpad + 16 * c, uint32_t((word & after) >> sh) & 0xFFFFu);
-    store16(L + i * kpad + 16 * c, uint32_t((word & before) >> sh) & 0xFFFFu);
+    if (c >= u_first_piece(i)) store16(U + i * kpad + 16 * c, uint32_t((word & after) >> sh) & 0xFFFFu);
+    if (c < l_end_piece(i)) store16(L + i * kpad + 16 * c, uint32_t((word & before) >> sh) & 0xFFFFu);
 }
 
 // U and L rows from the symmetric bitset: one thread per 16 columns.
-__global__ void __launch_bounds__(256) k_expand_f8(const uint64_t* __restrict__ bits, int64_t n, int64_t row_words,
-                                                   int64_t kpad, uint8_t* __restrict__ U, uint8_t* __restrict__ L) {
-    const int64_t ppr = kpad / 16;
-    const int64_t total = n * ppr;
-    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
-         idx += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t i = idx / ppr, c = idx - i * ppr;
-        expand_piece(bits, row_words, kpad, U, L, i, c);
+// Rows [r0, r1) of one set.  Long rows (at least 4 pieces per thread): the
+// block sweeps each row.  Shorter rows: (row, piece) pairs are flattened over
+// the block, so every thread still has independent loads and stores in
+// flight.
+__device__ __forceinline__ void expand_rows(const uint64_t* __restrict__ bits, int64_t row_words, int64_t kpad,
+                                            uint8_t* __restrict__ U, uint8_t* __restrict__ L, int64_t r0,
+                                            int64_t r1) {
+    const int ppr = int(kpad / 16);
+    if (ppr >= 4 * int(blockDim.x)) {
+        for (int64_t i = r0; i < r1; ++i)
+            for (int c = threadIdx.x; c < ppr; c += blockDim.x) expand_piece(bits, row_words, kpad, U, L, i, c);
+        return;
+    }
+    const int cnt = int(r1 - r0) * ppr;  // at most kExpandRows * ppr < 2^31
+    for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+        const int rr = p / ppr;
+        expand_piece(bits, row_words, kpad, U, L, r0 + rr, p - rr * ppr);
     }
 }
 
-// The same over many sets: piece index -> set by binary search on word_begin
-// (which counts 16-column pieces here).
+constexpr int kExpandRows = 16;  // rows per block step
+
+__global__ void __launch_bounds__(256) k_expand_f8(const uint64_t* __restrict__ bits, int64_t n, int64_t row_words,
+                                                   int64_t kpad, uint8_t* __restrict__ U, uint8_t* __restrict__ L) {
+    for (int64_t r0 = int64_t(blockIdx.x) * kExpandRows; r0 < n; r0 += int64_t(gridDim.x) * kExpandRows)
+        expand_rows(bits, row_words, kpad, U, L, r0, r0 + kExpandRows < n ? r0 + kExpandRows : n);
+}
+
+// The same over many sets: a block step covers kExpandRows consecutive rows of
+// the concatenated row range; the set of its first row comes from a binary
+// search on row_begin, later sets by stepping.
 __global__ void __launch_bounds__(256) k_expand_f8_multi(const MmaSetEntry* __restrict__ sets, int nsets,
-                                                         int64_t total) {
-    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
-         idx += int64_t(gridDim.x) * blockDim.x) {
+                                                         int64_t total_rows) {
+    for (int64_t r0 = int64_t(blockIdx.x) * kExpandRows; r0 < total_rows;
+         r0 += int64_t(gridDim.x) * kExpandRows) {
+        const int64_t r1 = r0 + kExpandRows < total_rows ? r0 + kExpandRows : total_rows;
         int lo = 0, hi = nsets - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (sets[mid].word_begin <= idx) lo = mid; else hi = mid - 1;
+            if (sets[mid].row_begin <= r0) lo = mid; else hi = mid - 1;
         }
-        const MmaSetEntry& e = sets[lo];
-        const int64_t ppr = e.kpad / 16;
-        const int64_t r = idx - e.word_begin;
-        const int64_t i = r / ppr, c = r - i * ppr;
-        expand_piece(e.bits, e.row_words, e.kpad, e.U, e.L, i, c);
+        for (int64_t row = r0; row < r1; ++lo) {
+            const MmaSetEntry& e = sets[lo];
+            const int64_t end = e.row_begin + e.n < r1 ? e.row_begin + e.n : r1;
+            expand_rows(e.bits, e.row_words, e.kpad, e.U, e.L, row - e.row_begin, end - e.row_begin);
+            row = end;
+        }
     }
+}
+
+int expand_grid(int64_t rows) {
+    int64_t g = int64_t(device_sm_count()) * 16;
+    const int64_t steps = (rows + kExpandRows - 1) / kExpandRows;
+    if (g > steps) g = steps;
+    return int(g < 1 ? 1 : g);
 }
 
 // One causal set as the kernel sees it.
@@ -203,7 +245,7 @@ struct MmaMulti {
     }
 };
 
-// Barrier over the 128 epilogue threads only, built on an mbarrier so that
+// Barrier over the epilogue threads only, built on an mbarrier so that
 // its wait is bounded and gives up once the CTA has aborted.
 __device__ __forceinline__ bool epilogue_sync(uint64_t* ebar, uint32_t& phase, WsHeader* hdr, volatile int* abort) {
     mbar_arrive(ebar);
@@ -218,7 +260,7 @@ __device__ __forceinline__ bool epilogue_flush(uint32_t* shist, const MmaView& v
                                                uint32_t& phase, WsHeader* hdr, volatile int* abort) {
     if (!epilogue_sync(ebar, phase, hdr, abort)) return false;
     const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
-    for (int64_t k = etid; k < hb; k += 128) {
+    for (int64_t k = etid; k < hb; k += kEpiThreads) {
         const uint32_t c = shist[k];
         if (c) {
             atomicAdd(&v.hist[k], (unsigned long long)c);
@@ -255,12 +297,12 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4 * 32);
+            mbar_init(&tempty[b], kEpiThreads);
         }
-        mbar_init(ebar, 4 * 32);
+        mbar_init(ebar, kEpiThreads);
         for (int r = 0; r < kRing; ++r) {
             mbar_init(&ifull[r], 1);
-            mbar_init(&iempty[r], 1 + 4 * 32);
+            mbar_init(&iempty[r], 1 + kEpiThreads);
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -357,7 +399,8 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         }
     } else if (warp >= 2) {
         // ---------------------------------------------------- epilogue
-        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        const int q = warp & 3;            // TMEM lane quarter this warp may access
+        const int c0 = ((warp - 2) >> 2) * kEpiChunks;  // first of its 32-column chunks
         const int etid = tid - 64;
         int64_t local_count = 0;
         int cur = -1;
@@ -385,29 +428,48 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             if (!mbar_wait_or_abort(&tfull[buf], use, hdr, abort_flag)) { ok = false; break; }
             tc_fence_after();
             const int64_t i = it.I0 + 32 * q + lane;
-            uint64_t cw[kBN / 64];
-#pragma unroll
-            for (int w = 0; w < kBN / 64; ++w) {
-                const int64_t word = (it.J0 >> 6) + w;
-                cw[w] = (i < v.n && word < v.row_words) ? __ldg(v.bits + i * v.row_words + word) : 0ull;
-            }
+            // C_ij words of this warp's 128 columns (registers, not an array:
+            // the chunk loop below is not unrolled)
+            static_assert(kEpiChunks == 4, "two bitset words per epilogue warp");
+            const int64_t word0 = (it.J0 + 32 * c0) >> 6;
+            const uint64_t cw0 = (i < v.n && word0 < v.row_words) ? __ldg(v.bits + i * v.row_words + word0) : 0ull;
+            const uint64_t cw1 =
+                (i < v.n && word0 + 1 < v.row_words) ? __ldg(v.bits + i * v.row_words + word0 + 1) : 0ull;
+            // Every count of this set lands in the shared histogram and there
+            // are no layer sums: the common case, kept branch-free.
+            const bool simple = v.kmax < 0 && v.hist_len <= kHistBins;
 #pragma unroll 1
-            for (int c = 0; c < kBN / 32; ++c) {
+            for (int c = c0; c < c0 + kEpiChunks; ++c) {
                 uint32_t r[32];
                 tmem_ld_32x32b_x32(tmem_base + (uint32_t(32 * q) << 16) + buf * kBN + uint32_t(32 * c), r);
                 tmem_ld_wait();
-                const uint32_t rel = uint32_t(cw[c >> 1] >> (32 * (c & 1)));  // C_ij for these 32 j
+                // pairs to count among these 32 j: C_ij, i < j < n
+                const int64_t jb = it.J0 + 32 * c;
+                uint32_t m = uint32_t(((c - c0) < 2 ? cw0 : cw1) >> (32 * (c & 1)));
+                const int64_t lo = i - jb + 1;  // first u with j > i
+                m &= lo <= 0 ? ~0u : (lo >= 32 ? 0u : (~0u << lo));
+                const int64_t hi = v.n - jb;    // u < hi keeps j < n
+                m &= hi >= 32 ? ~0u : (hi <= 0 ? 0u : ((1u << hi) - 1u));
+                if (m == 0u) continue;
+                if (simple) {
+                    // counts are integers below 2^23: adding 2^23 puts k in the
+                    // low mantissa bits, exactly
+#pragma unroll
+                    for (int u = 0; u < 32; ++u)
+                        if ((m >> u) & 1u)
+                            atomicAdd(&shist[__float_as_uint(__uint_as_float(r[u]) + 8388608.0f) - 0x4B000000u], 1u);
+                    continue;
+                }
 #pragma unroll
                 for (int u = 0; u < 32; ++u) {
-                    const int64_t j = it.J0 + 32 * c + u;
-                    if (((rel >> u) & 1u) && j > i && j < v.n) {
-                        const uint32_t k = uint32_t(__uint_as_float(r[u]));
+                    if ((m >> u) & 1u) {
+                        const uint32_t k = __float_as_uint(__uint_as_float(r[u]) + 8388608.0f) - 0x4B000000u;
                         if (int64_t(k) < hb)
                             atomicAdd(&shist[k], 1u);
                         else
                             atomicAdd(&v.hist[k], 1ull);
                         if (int(k) <= v.kmax)  // i is in L_{k+1}(j)
-                            atomicAdd(&v.layer[int64_t(k) * v.n + j], v.phi ? __ldg(v.phi + i) : 1.0);
+                            atomicAdd(&v.layer[int64_t(k) * v.n + jb + u], v.phi ? __ldg(v.phi + i) : 1.0);
                     }
                 }
             }
@@ -488,19 +550,14 @@ CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t
 }
 
 cudaError_t launch_expand_single(const MmaSetEntry* e, cudaStream_t st) {
-    const int64_t total_pieces = e->n * (e->kpad / 16);
-    int64_t eg = (total_pieces + 255) / 256;
-    if (eg > int64_t(device_sm_count()) * 64) eg = int64_t(device_sm_count()) * 64;
-    if (eg < 1) return cudaSuccess;
-    k_expand_f8<<<unsigned(eg), 256, 0, st>>>(e->bits, e->n, e->row_words, e->kpad, e->U, e->L);
+    if (e->n < 1) return cudaSuccess;
+    k_expand_f8<<<unsigned(expand_grid(e->n)), 256, 0, st>>>(e->bits, e->n, e->row_words, e->kpad, e->U, e->L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_expand_multi(const MmaSetEntry* sets_dev, int nsets, int64_t total_pieces, cudaStream_t st) {
-    if (total_pieces < 1) return cudaSuccess;
-    int64_t eg = (total_pieces + 255) / 256;
-    if (eg > int64_t(device_sm_count()) * 64) eg = int64_t(device_sm_count()) * 64;
-    k_expand_f8_multi<<<unsigned(eg), 256, 0, st>>>(sets_dev, nsets, total_pieces);
+cudaError_t launch_expand_multi(const MmaSetEntry* sets_dev, int nsets, int64_t total_rows, cudaStream_t st) {
+    if (total_rows < 1) return cudaSuccess;
+    k_expand_f8_multi<<<unsigned(expand_grid(total_rows)), 256, 0, st>>>(sets_dev, nsets, total_rows);
     return cudaGetLastError();
 }
 
@@ -534,10 +591,7 @@ cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words,
     uint8_t* U = static_cast<uint8_t*>(workspace) + lay.u;
     uint8_t* L = static_cast<uint8_t*>(workspace) + lay.l;
 
-    const int64_t total_pieces = n * (lay.kpad / 16);
-    int64_t eg = (total_pieces + 255) / 256;
-    if (eg > int64_t(device_sm_count()) * 64) eg = int64_t(device_sm_count()) * 64;
-    k_expand_f8<<<unsigned(eg), 256, 0, st>>>(bits, n, row_words, lay.kpad, U, L);
+    k_expand_f8<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, U, L);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
 
     CUtensorMap mapU, mapL;

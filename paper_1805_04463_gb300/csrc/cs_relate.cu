@@ -16,9 +16,9 @@ namespace {
 
 template <int G>
 __global__ void __launch_bounds__(kRelThreads) k_relate(const int32_t* __restrict__ coords, int64_t n,
-                                                        uint64_t* __restrict__ bits, int64_t row_words) {
+                                                        uint64_t* __restrict__ bits, int64_t row_words, bool order2d) {
     __shared__ int32_t sc[geom_dim(G)][kRelColsPerBlock];
-    relate_block<G>(coords, n, bits, row_words, blockIdx.x, blockIdx.y, sc);
+    relate_block<G>(coords, n, bits, row_words, blockIdx.x, blockIdx.y, sc, order2d);
 }
 
 }  // namespace
@@ -28,13 +28,13 @@ cudaError_t launch_relate(int kind, int64_t n, const int32_t* coords, uint64_t* 
     dim3 grid(unsigned((n + kRelRowsPerBlock - 1) / kRelRowsPerBlock),
               unsigned((row_words + kRelWordsPerBlock - 1) / kRelWordsPerBlock));
     if (kind == CS_4D_DIAMOND)
-        k_relate<kGeom4><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words);
+        k_relate<kGeom4><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words, false);
     else if (kind == CS_3D_DIAMOND)
-        k_relate<kGeom3><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words);
+        k_relate<kGeom3><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words, false);
     else if (kind == CS_2D_DS_SLAB)
-        k_relate<kGeomDeSitter><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words);
+        k_relate<kGeomDeSitter><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words, false);
     else
-        k_relate<kGeomLightCone><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words);
+        k_relate<kGeomLightCone><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words, kind == CS_2D_ORDER);
     return cudaGetLastError();
 }
 

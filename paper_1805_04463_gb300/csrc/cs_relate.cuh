@@ -46,14 +46,85 @@ __device__ __forceinline__ bool rel_related(const int32_t (&ci)[geom_dim(G)], co
     }
 }
 
+// Light-cone kinds, a block that lies wholly above (UPPER) or below the
+// diagonal.  Labels are in time order, so above the diagonal only the future
+// cone can hold (u_j > u_i and v_j > v_i) and below it only the past cone;
+// for a random 2D order labelled by u the u test is implied by j > i and only
+// v is compared (USE_U = false).  Each warp handles two rows at a time, so
+// every staged coordinate feeds four tests.
+template <bool UPPER, bool CHECK, bool USE_U>
+__device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coords, int64_t n,
+                                                 uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
+                                                 int64_t c0, int64_t r0, int64_t r1,
+                                                 const int32_t (*sc)[kRelColsPerBlock]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kWarps = kRelThreads / 32;
+    auto cone = [](int32_t xu, int32_t xv, int32_t cu, int32_t cv) {
+        const bool bv = UPPER ? xv > cv : xv < cv;
+        if constexpr (USE_U) return bv && (UPPER ? xu > cu : xu < cu);
+        else return bv;
+    };
+    for (int64_t i = r0 + warp; i < r1; i += 2 * kWarps) {
+        const int64_t i2 = i + kWarps;
+        const bool has2 = i2 < r1;
+        const int32_t ua = USE_U ? coords[i] : 0, va = coords[n + i];
+        const int32_t ub = USE_U && has2 ? coords[i2] : 0, vb = has2 ? coords[n + i2] : 0;
+        uint64_t mine_a = 0, mine_b = 0;
+#pragma unroll 8
+        for (int w = 0; w < kRelWordsPerBlock; ++w) {
+            const int col = w * 64 + lane;
+            const int32_t v0 = sc[1][col], v1 = sc[1][col + 32];
+            const int32_t u0 = USE_U ? sc[0][col] : 0, u1 = USE_U ? sc[0][col + 32] : 0;
+            bool a0 = cone(u0, v0, ua, va), a1 = cone(u1, v1, ua, va);
+            bool b0 = cone(u0, v0, ub, vb), b1 = cone(u1, v1, ub, vb);
+            if (CHECK) {
+                const bool in0 = c0 + col < n, in1 = c0 + col + 32 < n;
+                a0 = a0 && in0; a1 = a1 && in1; b0 = b0 && in0; b1 = b1 && in1;
+            }
+            const uint64_t wa = (uint64_t(__ballot_sync(0xffffffffu, a1)) << 32) | __ballot_sync(0xffffffffu, a0);
+            const uint64_t wb = (uint64_t(__ballot_sync(0xffffffffu, b1)) << 32) | __ballot_sync(0xffffffffu, b0);
+            if (lane == w) {
+                mine_a = wa;
+                mine_b = wb;
+            }
+        }
+        if (w0 + lane < row_words) {
+            bits[i * row_words + w0 + lane] = mine_a;
+            if (has2) bits[i2 * row_words + w0 + lane] = mine_b;
+        }
+    }
+}
+
+template <bool USE_U>
+__device__ __forceinline__ bool relate_cone_block(const int32_t* __restrict__ coords, int64_t n,
+                                                  uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
+                                                  int64_t c0, int64_t r0, int64_t r1,
+                                                  const int32_t (*sc)[kRelColsPerBlock]) {
+    if (c0 >= r1) {  // every column after every row
+        if (c0 + kRelColsPerBlock <= n)
+            relate_rows_cone<true, false, USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
+        else
+            relate_rows_cone<true, true, USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
+        return true;
+    }
+    if (c0 + kRelColsPerBlock <= r0) {  // every column before every row (never past n)
+        relate_rows_cone<false, false, USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
+        return true;
+    }
+    return false;
+}
+
 // Rows [rb*64, rb*64+64) x words [cg*32, cg*32+32) of the bitset.  Column
 // coordinates are staged in `sc`; each warp folds 64 tests per word into a
 // uint64 with two __ballot_sync, lane w keeps word w, and a row's 32 words
-// leave in one coalesced store.  Must be called by all 256 threads.
+// leave in one coalesced store.  Off-diagonal blocks of the light-cone kinds
+// test one cone only (relate_rows_cone); order2d: the set is a random 2D
+// order whose coords[0] (u) increases strictly with the label, which also
+// drops the u test there.  Must be called by all 256 threads.
 template <int G>
 __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords, int64_t n,
                                              uint64_t* __restrict__ bits, int64_t row_words, int64_t rb, int64_t cg,
-                                             int32_t (*sc)[kRelColsPerBlock]) {
+                                             int32_t (*sc)[kRelColsPerBlock], bool order2d = false) {
     constexpr int DIM = geom_dim(G);
     const int64_t w0 = cg * kRelWordsPerBlock;
     const int64_t c0 = w0 * 64;
@@ -66,6 +137,11 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = rb * kRelRowsPerBlock;
     const int64_t r1 = r0 + kRelRowsPerBlock < n ? r0 + kRelRowsPerBlock : n;
+    if constexpr (G == kGeomLightCone) {
+        if (order2d ? relate_cone_block<false>(coords, n, bits, row_words, w0, c0, r0, r1, sc)
+                    : relate_cone_block<true>(coords, n, bits, row_words, w0, c0, r0, r1, sc))
+            return;
+    }
     for (int64_t i = r0 + warp; i < r1; i += kRelThreads / 32) {
         int32_t ci[DIM];
 #pragma unroll
