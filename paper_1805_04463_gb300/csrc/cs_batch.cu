@@ -146,16 +146,14 @@ __global__ void __launch_bounds__(kRankThreads) k_batch_rank(const BatchSet* __r
     }
 }
 
-__global__ void __launch_bounds__(kRelThreads) k_batch_relate(const BatchSet* __restrict__ sets, int nsets,
-                                                              int64_t total_blocks) {
+// One block per relate block of one set, the set read from a table built at
+// create time (no search).
+__global__ void __launch_bounds__(kRelThreads) k_batch_relate(const BatchSet* __restrict__ sets,
+                                                              const int32_t* __restrict__ rblock_set) {
     __shared__ int32_t sc[4][kRelColsPerBlock];
-    for (int64_t blk = blockIdx.x; blk < total_blocks; blk += gridDim.x) {
-        int lo = 0, hi = nsets - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sets[mid].rblock_begin <= blk) lo = mid; else hi = mid - 1;
-        }
-        const BatchSet& b = sets[lo];
+    {
+        const int64_t blk = blockIdx.x;
+        const BatchSet& b = sets[rblock_set[blk]];
         const int64_t local = blk - b.rblock_begin;
         const int64_t rb = local / b.col_groups, cg = local - rb * b.col_groups;
         if (b.kind == CS_4D_DIAMOND)
@@ -166,7 +164,6 @@ __global__ void __launch_bounds__(kRelThreads) k_batch_relate(const BatchSet* __
             relate_block<kGeomDeSitter>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
         else
             relate_block<kGeomLightCone>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc, b.kind == CS_2D_ORDER);
-        __syncthreads();  // the next block restages sc
     }
 }
 
@@ -245,7 +242,9 @@ struct cs_batch {
     BatchSet* sets_dev = nullptr;
     PopcSetEntry* popc_dev = nullptr;
     MmaSetEntry* mma_dev = nullptr;
-    int64_t total_elems = 0, total_rblocks = 0, total_items = 0, total_rows = 0, total_hist = 0;
+    int64_t total_elems = 0, total_rblocks = 0, total_items = 0, total_chunks = 0, total_hist = 0;
+    int32_t* rtab = nullptr;  // relate block -> set
+    int32_t* etab = nullptr;  // expansion chunk -> count-table entry
     int max_pow2 = 1;
     const uint64_t* ds_thr = nullptr;  // de Sitter thresholds, when a set needs them
 };
@@ -253,7 +252,7 @@ struct cs_batch {
 namespace {
 
 struct Layout {
-    size_t sets, entries, total;
+    size_t sets, entries, rtab, etab, total;
     std::vector<size_t> coords, bits, key0, key1, raw, U, L;
 };
 
@@ -281,6 +280,15 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
     L.sets = take(sizeof(BatchSet) * size_t(n_sets));
     off = align_up(off, 128);
     L.entries = take((path == CS_PATH_MMA ? sizeof(MmaSetEntry) : sizeof(PopcSetEntry)) * size_t(n_sets));
+    int64_t rblocks = 0, chunks = 0;
+    for (int s = 0; s < n_sets; ++s) {
+        const int64_t n = sets[s].n;
+        rblocks += ((n + kRelRowsPerBlock - 1) / kRelRowsPerBlock) *
+                   ((cs_row_words(n) + kRelWordsPerBlock - 1) / kRelWordsPerBlock);
+        if (path == CS_PATH_MMA) chunks += mma_expand_chunks(n);
+    }
+    L.rtab = take(size_t(rblocks) * 4);  // relate block -> set
+    L.etab = take(size_t(chunks) * 4);   // expansion chunk -> set
     for (int s = 0; s < n_sets; ++s) {
         const int64_t n = sets[s].n;
         const int dim = cs_dim(sets[s].kind);
@@ -361,7 +369,13 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     std::vector<int> order(static_cast<size_t>(n_sets));
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bs[a].n > bs[b].n; });
-    int64_t items = 0, rows = 0;
+    int64_t items = 0, chunks = 0;
+    std::vector<int32_t> rtab(static_cast<size_t>(rblk)), etab;
+    for (int s = 0; s < n_sets; ++s)
+        std::fill(rtab.begin() + bs[s].rblock_begin,
+                  rtab.begin() + bs[s].rblock_begin +
+                      ((bs[s].n + kRelRowsPerBlock - 1) / kRelRowsPerBlock) * bs[s].col_groups,
+                  int32_t(s));
     std::vector<PopcSetEntry> pe;
     std::vector<MmaSetEntry> me;
     for (int r = 0; r < n_sets; ++r) {
@@ -375,8 +389,9 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
             e.item_offset = 0;
             items += mma_items(b.n);
             e.hist_off = b.hist_off * 8;
-            e.row_begin = rows;
-            rows += b.n;
+            e.chunk_begin = chunks;
+            chunks += mma_expand_chunks(b.n);
+            etab.insert(etab.end(), size_t(mma_expand_chunks(b.n)), int32_t(r));  // entry r of the table
             me.push_back(e);
         } else {
             PopcSetEntry e;
@@ -400,11 +415,17 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     h->total_elems = elem;
     h->total_rblocks = rblk;
     h->total_items = items;
-    h->total_rows = rows;
+    h->total_chunks = chunks;
+    h->rtab = reinterpret_cast<int32_t*>(ws + L.rtab);
+    h->etab = reinterpret_cast<int32_t*>(ws + L.etab);
     h->total_hist = hoff;
     h->max_pow2 = max_pow2;
     h->ds_thr = ds_thr;
     cudaError_t e = cudaMemcpyAsync(h->sets_dev, bs.data(), sizeof(BatchSet) * bs.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !rtab.empty())
+        e = cudaMemcpyAsync(h->rtab, rtab.data(), rtab.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !etab.empty())
+        e = cudaMemcpyAsync(h->etab, etab.data(), etab.size() * 4, cudaMemcpyHostToDevice, st);
     if (p == CS_PATH_MMA) {
         h->mma_dev = reinterpret_cast<MmaSetEntry*>(ws + L.entries);
         if (e == cudaSuccess)
@@ -456,12 +477,12 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
     }
     k_batch_rank<<<unsigned(b->nsets), kRankThreads, rank_smem, st>>>(b->sets_dev);
 
-    g = b->total_rblocks < int64_t(sms) * 8 ? b->total_rblocks : int64_t(sms) * 8;
-    k_batch_relate<<<unsigned(g), kRelThreads, 0, st>>>(b->sets_dev, b->nsets, b->total_rblocks);
+    if (b->total_rblocks > int64_t(0x7fffffff)) return CS_EINVAL;
+    k_batch_relate<<<unsigned(b->total_rblocks), kRelThreads, 0, st>>>(b->sets_dev, b->rtab);
     if ((err = cudaGetLastError()) != cudaSuccess) return CS_ECUDA;
 
     if (b->path == CS_PATH_MMA) {
-        if ((err = launch_expand_multi(b->mma_dev, b->nsets, b->total_rows, st)) != cudaSuccess) return CS_ECUDA;
+        if ((err = launch_expand_multi(b->mma_dev, b->etab, b->total_chunks, st)) != cudaSuccess) return CS_ECUDA;
         err = launch_count_mma_multi(b->mma_dev, b->nsets, b->total_items, reinterpret_cast<uintptr_t>(hist_dev),
                                      b->hdr, 0, st);
     } else {

@@ -78,7 +78,7 @@ struct Item {
 __device__ __forceinline__ bool decode_item(int64_t t, int64_t nsb, int64_t n, int64_t kblocks, Item& it) {
     const int64_t blk = t / kSlotsPerBlock, slot = t - blk * kSlotsPerBlock;
     const int64_t nbg = (nsb + kRaster - 1) / kRaster;
-    int64_t m = int64_t((1.0 + sqrt(1.0 + 8.0 * double(blk))) * 0.5);
+    int64_t m = int64_t((1.0f + sqrtf(1.0f + 8.0f * float(blk))) * 0.5f);  // corrected below
     while (m * (m - 1) / 2 > blk) --m;
     while (m * (m + 1) / 2 <= blk) ++m;
     const int64_t gi = blk - m * (m - 1) / 2;
@@ -167,26 +167,13 @@ __global__ void __launch_bounds__(256) k_expand_f8(const uint64_t* __restrict__ 
         expand_rows(bits, row_words, kpad, U, L, r0, r0 + kExpandRows < n ? r0 + kExpandRows : n);
 }
 
-// The same over many sets: a block step covers kExpandRows consecutive rows of
-// the concatenated row range; the set of its first row comes from a binary
-// search on row_begin, later sets by stepping.
-__global__ void __launch_bounds__(256) k_expand_f8_multi(const MmaSetEntry* __restrict__ sets, int nsets,
-                                                         int64_t total_rows) {
-    for (int64_t r0 = int64_t(blockIdx.x) * kExpandRows; r0 < total_rows;
-         r0 += int64_t(gridDim.x) * kExpandRows) {
-        const int64_t r1 = r0 + kExpandRows < total_rows ? r0 + kExpandRows : total_rows;
-        int lo = 0, hi = nsets - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sets[mid].row_begin <= r0) lo = mid; else hi = mid - 1;
-        }
-        for (int64_t row = r0; row < r1; ++lo) {
-            const MmaSetEntry& e = sets[lo];
-            const int64_t end = e.row_begin + e.n < r1 ? e.row_begin + e.n : r1;
-            expand_rows(e.bits, e.row_words, e.kpad, e.U, e.L, row - e.row_begin, end - e.row_begin);
-            row = end;
-        }
-    }
+// The same over many sets: one block per chunk of kExpandRows rows of one
+// set, the set read from the caller's chunk table (no search).
+__global__ void __launch_bounds__(256) k_expand_f8_multi(const MmaSetEntry* __restrict__ sets,
+                                                         const int32_t* __restrict__ chunk_set) {
+    const MmaSetEntry& e = sets[chunk_set[blockIdx.x]];
+    const int64_t r0 = (int64_t(blockIdx.x) - e.chunk_begin) * kExpandRows;
+    expand_rows(e.bits, e.row_words, e.kpad, e.U, e.L, r0, r0 + kExpandRows < e.n ? r0 + kExpandRows : e.n);
 }
 
 int expand_grid(int64_t rows) {
@@ -209,11 +196,14 @@ struct MmaView {
     int kmax;           // < 0: no layer sums
 };
 
-// Work source: a single set passed in kernel parameters.
+// Work source: a single set passed in kernel parameters.  The queue hands out
+// one item at a time, so the CTAs running at any moment stay on consecutive,
+// raster-local items.
 struct MmaSingle {
     MmaView v;
     int64_t nitems;
     __device__ __forceinline__ int64_t total() const { return nitems; }
+    __device__ __forceinline__ int64_t chunk() const { return 1; }
     __device__ __forceinline__ int set_of(int64_t t, int64_t& local) const {
         local = t;
         return 0;
@@ -221,13 +211,18 @@ struct MmaSingle {
     __device__ __forceinline__ MmaView view(int) const { return v; }
 };
 
-// Work source: many sets from a device table, items ordered set by set.
+// Work source: many sets from a device table, items ordered set by set.  The
+// queue hands out runs of `run` consecutive items (up to 16, at least 8 runs
+// per CTA), so a small set is spread over few CTAs and each CTA flushes its
+// shared histogram into few sets, while a short launch still fills the GPU.
 struct MmaMulti {
     const MmaSetEntry* sets;
     int nsets;
     int64_t nitems;
     uintptr_t hist_base;
+    int64_t run;
     __device__ __forceinline__ int64_t total() const { return nitems; }
+    __device__ __forceinline__ int64_t chunk() const { return run; }
     __device__ __forceinline__ int set_of(int64_t t, int64_t& local) const {
         int lo = 0, hi = nsets - 1;  // last set with item_begin <= t
         while (lo < hi) {
@@ -325,10 +320,15 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         bool ok = true;
         int cur = -1;
         MmaView v{};
+        int64_t next = 0, end = 0;  // the current run of items from the queue
         for (uint32_t q = 0; ok; ++q) {
             const uint32_t slot = q % kRing, use = (q / kRing) & 1u;
             if (!mbar_wait_or_abort(&iempty[slot], use ^ 1u, hdr, abort_flag)) { ok = false; break; }
-            const int64_t t = int64_t(atomicAdd(&hdr->counter, 1ull));
+            if (next >= end) {
+                next = int64_t(atomicAdd(&hdr->counter, 1ull)) * src.chunk();
+                end = next + src.chunk();
+            }
+            const int64_t t = next++;
             ring[slot] = t;
             mbar_arrive(&ifull[slot]);
             if (t >= total) break;
@@ -425,16 +425,17 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
             const uint32_t buf = uint32_t(local_count & 1), use = uint32_t((local_count >> 1) & 1);
             ++local_count;
-            if (!mbar_wait_or_abort(&tfull[buf], use, hdr, abort_flag)) { ok = false; break; }
-            tc_fence_after();
             const int64_t i = it.I0 + 32 * q + lane;
             // C_ij words of this warp's 128 columns (registers, not an array:
-            // the chunk loop below is not unrolled)
+            // the chunk loop below is not unrolled), loaded before the wait
+            // for the accumulator so that their latency hides behind the MMAs
             static_assert(kEpiChunks == 4, "two bitset words per epilogue warp");
             const int64_t word0 = (it.J0 + 32 * c0) >> 6;
             const uint64_t cw0 = (i < v.n && word0 < v.row_words) ? __ldg(v.bits + i * v.row_words + word0) : 0ull;
             const uint64_t cw1 =
                 (i < v.n && word0 + 1 < v.row_words) ? __ldg(v.bits + i * v.row_words + word0 + 1) : 0ull;
+            if (!mbar_wait_or_abort(&tfull[buf], use, hdr, abort_flag)) { ok = false; break; }
+            tc_fence_after();
             // Every count of this set lands in the shared histogram and there
             // are no layer sums: the common case, kept branch-free.
             const bool simple = v.kmax < 0 && v.hist_len <= kHistBins;
@@ -497,8 +498,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_count_mma_multi(const MmaSetEntry* __restrict__ sets, int nsets, int64_t nitems, uintptr_t hist_base,
-                      WsHeader* hdr) {
-    const MmaMulti src{sets, nsets, nitems, hist_base};
+                      int64_t run, WsHeader* hdr) {
+    const MmaMulti src{sets, nsets, nitems, hist_base, run};
     mma_body(src, hdr);
 }
 
@@ -555,9 +556,13 @@ cudaError_t launch_expand_single(const MmaSetEntry* e, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_expand_multi(const MmaSetEntry* sets_dev, int nsets, int64_t total_rows, cudaStream_t st) {
-    if (total_rows < 1) return cudaSuccess;
-    k_expand_f8_multi<<<unsigned(expand_grid(total_rows)), 256, 0, st>>>(sets_dev, nsets, total_rows);
+int64_t mma_expand_chunks(int64_t n) { return (n + kExpandRows - 1) / kExpandRows; }
+
+cudaError_t launch_expand_multi(const MmaSetEntry* sets_dev, const int32_t* chunk_set, int64_t total_chunks,
+                                cudaStream_t st) {
+    if (total_chunks < 1) return cudaSuccess;
+    if (total_chunks > int64_t(0x7fffffff)) return cudaErrorInvalidValue;
+    k_expand_f8_multi<<<unsigned(total_chunks), 256, 0, st>>>(sets_dev, chunk_set);
     return cudaGetLastError();
 }
 
@@ -575,7 +580,9 @@ cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64
     }
     int64_t grid = max_ctas > 0 ? max_ctas : device_sm_count();
     if (grid > nitems) grid = nitems;
-    k_count_mma_multi<<<unsigned(grid), kThreads, kSmemBytes, st>>>(sets_dev, nsets, nitems, hist_base, hdr);
+    int64_t run = nitems / (grid * 8);
+    run = run < 1 ? 1 : (run > 16 ? 16 : run);
+    k_count_mma_multi<<<unsigned(grid), kThreads, kSmemBytes, st>>>(sets_dev, nsets, nitems, hist_base, run, hdr);
     return cudaGetLastError();
 }
 

@@ -55,7 +55,7 @@ struct alignas(128) MmaSetEntry {
     uint8_t* U;
     uint8_t* L;
     int64_t kpad;
-    int64_t row_begin;   // first row of this set in the concatenated expand range
+    int64_t chunk_begin;  // first expansion chunk of this set (multi-set expansion)
     const double* phi;   // d'Alembertian layer sums: field (NULL = 1),
     double* layer;       //   sums [kmax+1][n],
     int64_t kmax;        //   highest layer (< 0: none)
@@ -64,11 +64,16 @@ size_t mma_workspace_bytes(int64_t n);
 int64_t mma_items(int64_t n);
 int64_t mma_kpad(int64_t n);
 // Fill sizes, operand pointers and TMA maps of an entry (item_begin, hist_off,
-// row_begin are the caller's).
+// chunk_begin are the caller's).
 CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words, uint8_t* U,
                         uint8_t* L);
 cudaError_t launch_expand_single(const MmaSetEntry* e, cudaStream_t st);  // uses bits, n, row_words, kpad, U, L
-cudaError_t launch_expand_multi(const MmaSetEntry* sets_dev, int nsets, int64_t total_rows, cudaStream_t st);
+// Expansion of many sets: chunk c of the concatenated chunk range belongs to
+// set chunk_set[c] (a table the caller builds; mma_expand_chunks(n) chunks per
+// set, numbered from the set's chunk_begin).
+int64_t mma_expand_chunks(int64_t n);
+cudaError_t launch_expand_multi(const MmaSetEntry* sets_dev, const int32_t* chunk_set, int64_t total_chunks,
+                                cudaStream_t st);
 cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64_t nitems, uintptr_t hist_base,
                                    WsHeader* hdr, int max_ctas, cudaStream_t st);
 cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist,

@@ -95,6 +95,40 @@ __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coo
     }
 }
 
+// Light-cone kinds, a block that straddles the diagonal: row i splits its 32
+// words into those wholly before column i (past cone only), the word holding
+// column i (full test) and those wholly after it (future cone only).  The
+// split point is the same for the whole warp, so the three loops do not
+// diverge.
+template <bool USE_U>
+__device__ __forceinline__ void relate_rows_cone_diag(const int32_t* __restrict__ coords, int64_t n,
+                                                      uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
+                                                      int64_t c0, int64_t r0, int64_t r1,
+                                                      const int32_t (*sc)[kRelColsPerBlock]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t i = r0 + warp; i < r1; i += kRelThreads / 32) {
+        const int32_t ci[2] = {coords[i], coords[n + i]};
+        const int64_t off = i - c0;
+        const int wd = off < 0 ? -1 : (off >= kRelColsPerBlock ? kRelWordsPerBlock : int(off >> 6));
+        uint64_t mine = 0;
+        auto word = [&](int w, auto test) {
+            const int col = w * 64 + lane;
+            const bool b0 = c0 + col < n && test(col);
+            const bool b1 = c0 + col + 32 < n && test(col + 32);
+            const uint64_t x = (uint64_t(__ballot_sync(0xffffffffu, b1)) << 32) | __ballot_sync(0xffffffffu, b0);
+            if (lane == w) mine = x;
+        };
+        auto past = [&](int col) { return sc[1][col] < ci[1] && (!USE_U || sc[0][col] < ci[0]); };
+        auto future = [&](int col) { return sc[1][col] > ci[1] && (!USE_U || sc[0][col] > ci[0]); };
+        auto full = [&](int col) { return rel_related<kGeomLightCone>(ci, sc, col); };
+        const int wlo = wd < kRelWordsPerBlock ? wd : kRelWordsPerBlock;
+        for (int w = 0; w < wlo; ++w) word(w, past);
+        if (wd >= 0 && wd < kRelWordsPerBlock) word(wd, full);
+        for (int w = wd + 1 > 0 ? wd + 1 : 0; w < kRelWordsPerBlock; ++w) word(w, future);
+        if (w0 + lane < row_words) bits[i * row_words + w0 + lane] = mine;
+    }
+}
+
 template <bool USE_U>
 __device__ __forceinline__ bool relate_cone_block(const int32_t* __restrict__ coords, int64_t n,
                                                   uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
@@ -111,7 +145,8 @@ __device__ __forceinline__ bool relate_cone_block(const int32_t* __restrict__ co
         relate_rows_cone<false, false, USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
         return true;
     }
-    return false;
+    relate_rows_cone_diag<USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
+    return true;
 }
 
 // Rows [rb*64, rb*64+64) x words [cg*32, cg*32+32) of the bitset.  Column
