@@ -174,11 +174,11 @@ def compare_paths(cs, torch, buf, n, stream):
     return out
 
 
-def ensemble_bench(cs, torch, path, steps=5, warmup=3):
+def ensemble_bench(cs, torch, path, steps=5, warmup=3, n2d=512, n4d=256):
     """Batched ensemble (one CUDA-graph replay of cs_batch_launch per step) vs the
-    same 768 sets as one-at-a-time plain launches, on this GPU."""
+    same sets as one-at-a-time plain launches, on this GPU."""
     from paper_1805_04463_gb300 import workloads
-    sets = workloads.ensemble()
+    sets = workloads.ensemble(n2d=n2d, n4d=n4d)
     stream = torch.cuda.Stream()
     b = cs.Batch(sets, path=path, n_eps=len(EPS))
     with torch.cuda.stream(stream):
@@ -215,7 +215,7 @@ def ensemble_bench(cs, torch, path, steps=5, warmup=3):
     plain_ms = a2.elapsed_time(e2)
     same = all(torch.equal(buf.hist, b.set_hist(s)) for s, buf in enumerate(bufs))
     terms = sum(n * (n - 1) * (n - 2) / 6.0 for _, n, _ in sets)
-    return {"workload": "512 2D diamonds N~Poisson(4096) + 256 4D diamonds N~Poisson(2048)",
+    return {"workload": f"{n2d} 2D diamonds N~Poisson(4096) + {n4d} 4D diamonds N~Poisson(2048)",
             "sets": len(sets), "pairs": pairs, "path": {1: "popc", 2: "mma"}[b.path],
             "batched_graph_ms": batched_ms, "plain_ms": plain_ms,
             "batched_gpairs_s": pairs / batched_ms / 1e6, "plain_gpairs_s": pairs / plain_ms / 1e6,
@@ -323,6 +323,8 @@ def main():
                     help="also time the other count path once on the same bitset")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--ensemble-sets", default="512,256",
+                    help="ensemble size: number of 2D diamonds, number of 4D diamonds (profiling runs use a sample)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -442,7 +444,8 @@ def main():
         "clocks": clocks,
     }
     if not args.no_ensemble:
-        line["ensemble"] = ensemble_bench(cs, torch, PATHS[args.path])
+        n2d, n4d = (int(x) for x in args.ensemble_sets.split(","))
+        line["ensemble"] = ensemble_bench(cs, torch, PATHS[args.path], n2d=n2d, n4d=n4d)
     if not args.no_serve:
         line["serving"] = serving_bench(PATHS[args.path])
     if not args.no_cpu_baseline:
