@@ -78,6 +78,8 @@ def _load():
         lib.oracle_interval_abundance_dominance2d.argtypes = [i64, vp, i64, i64, i64, vp, i64]
         lib.oracle_links_2d.argtypes = [i64, vp]
         lib.oracle_links_2d.restype = i64
+        lib.oracle_degrees.argtypes = [i64, vp, i64, vp, vp]
+        lib.oracle_sparse_relations.argtypes = [i64, vp, i64, i32, vp, vp, i64]
         lib.oracle_layer_sums.argtypes = [i64, vp, i64, vp, i32, vp]
         lib.oracle_dalembertian.argtypes = [i32, i64, vp, vp, i32, ctypes.c_double, vp]
         lib.oracle_action.argtypes = [i32, i64, vp, i64, ctypes.c_double,
@@ -202,6 +204,27 @@ def action(dim_: int, n: int, hist: np.ndarray, eps: float = 0.0):
     _check(_load().oracle_action(dim_, n, _ptr(h) if h.size else None, h.size, float(eps),
                                  ctypes.byref(out), ctypes.byref(br)), "action")
     return out.value, br.value
+
+
+def degrees(bits: np.ndarray):
+    """(kin, kout) int32: past and future relation counts of every element."""
+    n, w = bits.shape
+    kin = np.zeros(n, dtype=np.int32)
+    kout = np.zeros(n, dtype=np.int32)
+    _check(_load().oracle_degrees(n, _ptr(bits), w, _ptr(kin), _ptr(kout)), "degrees")
+    return kin, kout
+
+
+def sparse_relations(bits: np.ndarray, direction: int):
+    """(offsets int64[n+1], cols int32): past (0) or future (1) relation lists."""
+    n, w = bits.shape
+    offsets = np.zeros(n + 1, dtype=np.int64)
+    lib = _load()
+    _check(lib.oracle_sparse_relations(n, _ptr(bits), w, direction, _ptr(offsets), None, 0), "sparse_relations")
+    cols = np.zeros(max(int(offsets[n]), 1), dtype=np.int32)
+    _check(lib.oracle_sparse_relations(n, _ptr(bits), w, direction, _ptr(offsets), _ptr(cols), cols.size),
+           "sparse_relations")
+    return offsets, cols[:int(offsets[n])]
 
 
 def layer_sums(bits: np.ndarray, kmax: int, phi=None) -> np.ndarray:

@@ -584,6 +584,62 @@ int oracle_action(int dim, int64_t n, const int64_t *hist, int64_t len, double e
     return OR_OK;
 }
 
+/* --------------------------------------------- degrees and sparse lists */
+
+/*
+ * In- and out-degree vectors (Section "Optimized GPU Linking Algorithm",
+ * Algorithm "Write Operations for Degrees"): with time-sorted labels,
+ * kin[j] = #{i < j : i precedes j} (past relations of j) and
+ * kout[i] = #{j > i : i precedes j} (future relations of i), read bit by
+ * bit from the symmetric bitset.
+ */
+int oracle_degrees(int64_t n, const uint64_t *bits, int64_t row_words, int32_t *kin, int32_t *kout)
+{
+    if (n < 0 || !bits || !kin || !kout) return OR_EINVAL;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t past = 0, future = 0;
+        const uint64_t *row = bits + i * row_words;
+        for (int64_t j = 0; j < n; j++) {
+            if (!or_bit(row, j)) continue;
+            if (j < i) past++; else if (j > i) future++;
+        }
+        kin[i] = (int32_t)past;
+        kout[i] = (int32_t)future;
+    }
+    return OR_OK;
+}
+
+/*
+ * The past (direction 0) or future (direction 1) sparse relation lists in
+ * compressed-row form (Section "GPU Linking Algorithm": the relation list is
+ * decoded into past and future sparse lists): row i owns
+ * cols[offsets[i] .. offsets[i+1]), the labels related to i before
+ * (direction 0) or after (direction 1) it, in increasing order.  offsets
+ * has n+1 entries; cols may be NULL to get the offsets alone.  cols_capacity
+ * is the room in cols; returns OR_ENOMEM if the lists do not fit.
+ */
+int oracle_sparse_relations(int64_t n, const uint64_t *bits, int64_t row_words, int direction, int64_t *offsets,
+                            int32_t *cols, int64_t cols_capacity)
+{
+    if (n < 0 || !bits || !offsets || (direction != 0 && direction != 1)) return OR_EINVAL;
+    int64_t pos = 0;
+    for (int64_t i = 0; i < n; i++) {
+        offsets[i] = pos;
+        const uint64_t *row = bits + i * row_words;
+        int64_t lo = direction ? i + 1 : 0, hi = direction ? n : i;
+        for (int64_t j = lo; j < hi; j++) {
+            if (!or_bit(row, j)) continue;
+            if (cols) {
+                if (pos >= cols_capacity) return OR_ENOMEM;
+                cols[pos] = (int32_t)j;
+            }
+            pos++;
+        }
+    }
+    offsets[n] = pos;
+    return OR_OK;
+}
+
 /* ------------------------------------------------- discrete d'Alembertian */
 
 /*

@@ -579,3 +579,47 @@ def test_layer_sums_match_abundances_and_definition(oracle, kind, n):
                     if m <= 2:
                         want[m, j] += phi[i]
         assert np.allclose(Sp, want, rtol=1e-14, atol=1e-14)
+
+
+# ------------------------------------------------ degrees and sparse lists
+
+def _future_2d(v, i):
+    return [j for j in range(i + 1, v.size) if v[j] > v[i]]
+
+
+@pytest.mark.parametrize("n,seed", [(300, 1), (129, 2), (1, 3)])
+def test_degrees_and_sparse_lists_from_the_2d_order_definition(oracle, n, seed):
+    # For a 2D order labelled by u, i precedes j iff i < j and v_i < v_j: the
+    # lists come straight from the coordinates, with no bitset.
+    c = oracle.sprinkle(0, n, seed)
+    v = c[1].astype(np.int64)
+    bits = oracle.causal_matrix(0, c)
+    kin, kout = oracle.degrees(bits)
+    off_f, cols_f = oracle.sparse_relations(bits, 1)
+    off_p, cols_p = oracle.sparse_relations(bits, 0)
+    for i in range(n):
+        fut = _future_2d(v, i)
+        past = [j for j in range(i) if v[j] < v[i]]
+        assert kout[i] == len(fut) and kin[i] == len(past)
+        assert cols_f[off_f[i]:off_f[i + 1]].tolist() == fut
+        assert cols_p[off_p[i]:off_p[i + 1]].tolist() == past
+    R = n * (n - 1) // 2 - _inversions(c[1])
+    assert kin.sum() == kout.sum() == R == off_f[n] == off_p[n]
+
+
+def test_degrees_closed_forms(oracle):
+    n = 100
+    chain = _coords_2d_order(np.arange(n))
+    kin, kout = oracle.degrees(oracle.causal_matrix(0, chain))
+    assert kin.tolist() == list(range(n)) and kout.tolist() == list(range(n - 1, -1, -1))
+    anti = _coords_2d_order(np.arange(n)[::-1].copy())
+    kin, kout = oracle.degrees(oracle.causal_matrix(0, anti))
+    assert not kin.any() and not kout.any()
+    # in a 2D order the past list of j and the future list of i are transposes
+    c = oracle.sprinkle(0, 200, 9)
+    bits = oracle.causal_matrix(0, c)
+    off_f, cols_f = oracle.sparse_relations(bits, 1)
+    off_p, cols_p = oracle.sparse_relations(bits, 0)
+    fwd = {(i, int(j)) for i in range(200) for j in cols_f[off_f[i]:off_f[i + 1]]}
+    bwd = {(int(i), j) for j in range(200) for i in cols_p[off_p[j]:off_p[j + 1]]}
+    assert fwd == bwd
