@@ -409,6 +409,40 @@ int cs_count_jobs(const cs_count_job *jobs, int n_jobs, int path, void *table_ho
  */
 int cs_sprinkle_noalloc(int kind, int64_t n, uint64_t seed, int32_t *coords_dev, void *stream);
 
+/* ------------------------------------------ degrees and sparse lists */
+
+/*
+ * In- and out-degree vectors (Section "Optimized GPU Linking Algorithm",
+ * Algorithm "Write Operations for Degrees") from the symmetric bitset of
+ * time-sorted labels: in_dev[j] = number of i < j related to j (its past),
+ * out_dev[i] = number of j > i related to i (its future).  int32, n each;
+ * either may be NULL.  Asynchronous.  Errors: CS_EINVAL, CS_ECUDA.
+ */
+int cs_degrees(int64_t n, const uint64_t *bits_dev, int64_t row_words, int32_t *in_dev, int32_t *out_dev,
+               void *stream);
+
+/* Device workspace for cs_sparse_offsets / cs_sparse_columns. */
+size_t cs_sparse_workspace_bytes(int64_t n);
+
+/*
+ * The past (direction 0) or future (direction 1) sparse relation lists in
+ * compressed-row form (the thesis decodes its relation list into past and
+ * future sparse lists, Section "GPU Linking Algorithm").  Row i owns
+ * cols[offsets[i] .. offsets[i+1]): the labels related to i before (0) or
+ * after (1) it, increasing.  Two calls: cs_sparse_offsets writes the n+1
+ * int64 offsets (offsets_dev[n] = the list length, an exclusive scan of the
+ * row counts); the caller reads offsets_dev[n], provides cols_dev with room
+ * for that many int32 and calls cs_sparse_columns with the same bitset.
+ * A row whose list would end past cols_capacity is skipped and CS_ENOMEM is
+ * recorded in the workspace status word (cs_workspace_status).
+ * Asynchronous.  Errors: CS_EINVAL, CS_ENOMEM (workspace too small), CS_ECUDA.
+ */
+int cs_sparse_offsets(int64_t n, const uint64_t *bits_dev, int64_t row_words, int direction,
+                      int64_t *offsets_dev, void *workspace_dev, size_t workspace_bytes, void *stream);
+int cs_sparse_columns(int64_t n, const uint64_t *bits_dev, int64_t row_words, int direction,
+                      const int64_t *offsets_dev, int32_t *cols_dev, int64_t cols_capacity,
+                      void *workspace_dev, size_t workspace_bytes, void *stream);
+
 /* ---------------------------------------------------- failure detection */
 
 /*

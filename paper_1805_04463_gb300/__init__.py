@@ -23,7 +23,7 @@ __all__ = [
     "set_auto_paths", "get_auto_paths",
     "sprinkle", "sprinkle_noalloc", "causal_matrix", "layer_sums", "dalembertian", "interval_abundance", "workspace_status", "action", "action_device",
     "evaluate", "Buffers", "allocate", "run", "SetDesc", "Batch", "CountJob", "count_items",
-    "operands_bytes", "prepare_operands", "count_jobs", "FAULT_ALLOC", "FAULT_LAUNCH", "selftest_wait",
+    "operands_bytes", "prepare_operands", "count_jobs", "degrees", "sparse_relations", "FAULT_ALLOC", "FAULT_LAUNCH", "selftest_wait",
     "inject_fault",
 ]
 
@@ -96,6 +96,10 @@ def lib() -> ctypes.CDLL:
             "cs_count_jobs_table_bytes": ([i32, i32], sz),
             "cs_count_jobs_workspace_bytes": ([i32, i32], sz),
             "cs_count_jobs": ([vp, i32, i32, vp, vp, sz, vp], i32),
+            "cs_degrees": ([i64, vp, i64, vp, vp, vp], i32),
+            "cs_sparse_workspace_bytes": ([i64], ctypes.c_size_t),
+            "cs_sparse_offsets": ([i64, vp, i64, i32, vp, vp, ctypes.c_size_t, vp], i32),
+            "cs_sparse_columns": ([i64, vp, i64, i32, vp, vp, i64, vp, ctypes.c_size_t, vp], i32),
             "cs_selftest_wait": ([vp, ctypes.c_double, i32, vp], i32),
             "cs_inject_fault": ([i32, i32], i32),
             "cs_strerror": ([i32], ctypes.c_char_p),
@@ -397,6 +401,32 @@ def count_jobs(jobs, path, table_host_ptr, workspace_ptr, workspace_nbytes, stre
     arr = (CountJob * len(jobs))(*jobs)
     _check(lib().cs_count_jobs(arr, len(jobs), path, table_host_ptr, workspace_ptr, workspace_nbytes,
                                _stream(stream)), "cs_count_jobs")
+
+
+# ------------------------------------------- degrees and sparse lists
+
+def degrees(n, bits, kin, kout, stream=None):
+    """cs_degrees: past (kin) and future (kout) relation counts, int32 tensors (either may be None)."""
+    _check(lib().cs_degrees(n, _ptr(bits), bits.shape[-1], _ptr(kin), _ptr(kout), _stream(stream)), "cs_degrees")
+
+
+def sparse_relations(n, bits, direction, stream=None):
+    """Past (0) or future (1) sparse relation lists: (offsets int64[n+1], cols int32) device tensors.
+    Synchronises once to size the column array."""
+    import torch
+    L = lib()
+    ws = torch.empty(L.cs_sparse_workspace_bytes(n), dtype=torch.uint8, device=bits.device)
+    offsets = torch.empty(n + 1, dtype=torch.int64, device=bits.device)
+    _check(L.cs_sparse_offsets(n, _ptr(bits), bits.shape[-1], direction, _ptr(offsets), _ptr(ws), ws.numel(),
+                               _stream(stream)), "cs_sparse_offsets")
+    total = int(offsets[n].item())
+    cols = torch.empty(max(total, 1), dtype=torch.int32, device=bits.device)
+    _check(L.cs_sparse_columns(n, _ptr(bits), bits.shape[-1], direction, _ptr(offsets), _ptr(cols), total,
+                               _ptr(ws), ws.numel(), _stream(stream)), "cs_sparse_columns")
+    st = workspace_status(ws, stream)
+    if st != 0:
+        raise CsError(st, "cs_sparse_columns")
+    return offsets, cols[:total]
 
 
 # ------------------------------------------------------ failure detection
