@@ -80,6 +80,10 @@ def _load():
         lib.oracle_links_2d.restype = i64
         lib.oracle_degrees.argtypes = [i64, vp, i64, vp, vp]
         lib.oracle_sparse_relations.argtypes = [i64, vp, i64, i32, vp, vp, i64]
+        lib.oracle_longest_chain.argtypes = [i64, vp, i64, i64, i64]
+        lib.oracle_longest_chain.restype = i64
+        lib.oracle_greedy_antichain.argtypes = [i64, vp, i64, i64, vp]
+        lib.oracle_greedy_antichain.restype = i64
         lib.oracle_layer_sums.argtypes = [i64, vp, i64, vp, i32, vp]
         lib.oracle_dalembertian.argtypes = [i32, i64, vp, vp, i32, ctypes.c_double, vp]
         lib.oracle_action.argtypes = [i32, i64, vp, i64, ctypes.c_double,
@@ -225,6 +229,21 @@ def sparse_relations(bits: np.ndarray, direction: int):
     _check(lib.oracle_sparse_relations(n, _ptr(bits), w, direction, _ptr(offsets), _ptr(cols), cols.size),
            "sparse_relations")
     return offsets, cols[:int(offsets[n])]
+
+
+def longest_chain(bits: np.ndarray, i: int = -1, j: int = -1) -> int:
+    """Longest chain from i to j in relations (-1 if i does not precede j);
+    i = j = -1: the height of the whole set in elements."""
+    n, w = bits.shape
+    return int(_load().oracle_longest_chain(n, _ptr(bits), w, i, j))
+
+
+def greedy_antichain(bits: np.ndarray, seed: int):
+    """(size, member bitset uint64[row_words]) of the greedy maximal antichain from `seed`."""
+    n, w = bits.shape
+    out = np.zeros(w, dtype=np.uint64)
+    size = int(_load().oracle_greedy_antichain(n, _ptr(bits), w, seed, _ptr(out)))
+    return size, out
 
 
 def layer_sums(bits: np.ndarray, kmax: int, phi=None) -> np.ndarray:

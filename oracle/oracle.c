@@ -640,6 +640,96 @@ int oracle_sparse_relations(int64_t n, const uint64_t *bits, int64_t row_words, 
     return OR_OK;
 }
 
+/* ------------------------------------------------- chains and antichains */
+
+/*
+ * Longest chain (Section "Set Partitions", Algorithm "Maximal Chain
+ * Length"), written as its definition: with time-sorted labels the longest
+ * path from i to k, in relations, is d(k) = 1 + max d(m) over m in
+ * {i} + A_ij preceding k (d(i) = 0), filled in label order.  Returns d(j)
+ * for a related pair i < j and -1 if i does not precede j.  With i = j = -1
+ * returns the height of the whole set: the number of elements of its longest
+ * chain (0 for n = 0).
+ */
+int64_t oracle_longest_chain(int64_t n, const uint64_t *bits, int64_t row_words, int64_t i, int64_t j)
+{
+    if (n < 0 || !bits) return -2;
+    int64_t *d = malloc((size_t)(n > 0 ? n : 1) * sizeof *d);
+    if (!d) return -2;
+    int64_t best = 0;
+    if (i < 0 && j < 0) {
+        for (int64_t k = 0; k < n; k++) {
+            int64_t dk = 1;
+            for (int64_t m = 0; m < k; m++)
+                if (or_bit(bits + k * row_words, m) && d[m] + 1 > dk) dk = d[m] + 1;
+            d[k] = dk;
+            if (dk > best) best = dk;
+        }
+        free(d);
+        return best;
+    }
+    if (i < 0 || j <= i || j >= n || !or_bit(bits + i * row_words, j)) {
+        free(d);
+        return -1;
+    }
+    const uint64_t *ri = bits + i * row_words, *rj = bits + j * row_words;
+    d[i] = 0;
+    for (int64_t k = i + 1; k <= j; k++) {
+        d[k] = -1;
+        if (k < j && !(or_bit(ri, k) && or_bit(rj, k))) continue; /* k not in A_ij */
+        int64_t dk = 1;                                          /* from i directly */
+        for (int64_t m = i + 1; m < k; m++)
+            if (d[m] >= 0 && or_bit(bits + k * row_words, m) && d[m] + 1 > dk) dk = d[m] + 1;
+        d[k] = dk;
+    }
+    best = d[j];
+    free(d);
+    return best;
+}
+
+/*
+ * Greedy maximal antichain (Section "Set Partitions", Algorithm "Maximal
+ * Antichain"): candidates X = the elements unrelated to the seed, the
+ * antichain A = X + {seed}; while X is not empty, take the candidate k that
+ * leaves the most elements in A when its relations J(k) are removed
+ * (c = |A - J(k)|, the first such k in label order on ties), then remove
+ * J(k) from A and J(k) + {k} from X.  out (row_words words) receives A as a
+ * bitset; returns |A|, or -1 for a bad seed.
+ */
+int64_t oracle_greedy_antichain(int64_t n, const uint64_t *bits, int64_t row_words, int64_t seed, uint64_t *out)
+{
+    if (n < 1 || !bits || !out || seed < 0 || seed >= n) return -1;
+    uint64_t *X = calloc((size_t)row_words, 8);
+    if (!X) return -2;
+    const uint64_t *rs = bits + seed * row_words;
+    memset(out, 0, (size_t)row_words * 8);
+    for (int64_t k = 0; k < n; k++)
+        if (k != seed && !or_bit(rs, k)) X[k >> 6] |= 1ULL << (k & 63);
+    for (int64_t w = 0; w < row_words; w++) out[w] = X[w];
+    out[seed >> 6] |= 1ULL << (seed & 63);
+    for (;;) {
+        int64_t bestk = -1, bestc = -1;
+        for (int64_t k = 0; k < n; k++) {
+            if (!((X[k >> 6] >> (k & 63)) & 1ULL)) continue;
+            const uint64_t *rk = bits + k * row_words;
+            int64_t c = 0;
+            for (int64_t w = 0; w < row_words; w++) c += __builtin_popcountll(out[w] & ~rk[w]);
+            if (c > bestc) { bestc = c; bestk = k; }
+        }
+        if (bestk < 0) break;
+        const uint64_t *rk = bits + bestk * row_words;
+        for (int64_t w = 0; w < row_words; w++) {
+            out[w] &= ~rk[w];
+            X[w] &= ~rk[w];
+        }
+        X[bestk >> 6] &= ~(1ULL << (bestk & 63));
+    }
+    int64_t size = 0;
+    for (int64_t w = 0; w < row_words; w++) size += __builtin_popcountll(out[w]);
+    free(X);
+    return size;
+}
+
 /* ------------------------------------------------- discrete d'Alembertian */
 
 /*

@@ -623,3 +623,76 @@ def test_degrees_closed_forms(oracle):
     fwd = {(i, int(j)) for i in range(200) for j in cols_f[off_f[i]:off_f[i + 1]]}
     bwd = {(int(i), j) for j in range(200) for i in cols_p[off_p[j]:off_p[j + 1]]}
     assert fwd == bwd
+
+
+# --------------------------------------------------- chains and antichains
+
+def _lis(seq, strict=True):
+    import bisect
+    tails = []
+    for x in seq:
+        k = bisect.bisect_left(tails, x) if strict else bisect.bisect_right(tails, x)
+        if k == len(tails):
+            tails.append(x)
+        else:
+            tails[k] = x
+    return len(tails)
+
+
+@pytest.mark.parametrize("n,seed", [(400, 1), (1000, 2), (3, 3), (1, 4)])
+def test_longest_chain_is_longest_increasing_subsequence(oracle, n, seed):
+    # In a 2D order labelled by u a chain is an increasing subsequence of v
+    # (patience sorting, no bitsets); between a related pair i < j it runs
+    # through the elements with v_i < v_k < v_j.
+    c = oracle.sprinkle(0, n, seed)
+    v = c[1].astype(np.int64)
+    bits = oracle.causal_matrix(0, c)
+    assert oracle.longest_chain(bits) == _lis(v.tolist())
+    rng = np.random.default_rng(seed)
+    for _ in range(40):
+        if n < 2:
+            break
+        i, j = sorted(rng.integers(0, n, 2).tolist())
+        if i == j or v[i] > v[j]:
+            assert oracle.longest_chain(bits, i, j) == -1
+            continue
+        mid = [x for x in v[i + 1:j].tolist() if v[i] < x < v[j]]
+        assert oracle.longest_chain(bits, i, j) == 1 + _lis(mid)
+
+
+def test_chain_closed_forms_and_tiny_poset(oracle):
+    n = 50
+    chain = oracle.causal_matrix(0, _coords_2d_order(np.arange(n)))
+    assert oracle.longest_chain(chain) == n and oracle.longest_chain(chain, 3, 40) == 37
+    anti = oracle.causal_matrix(0, _coords_2d_order(np.arange(n)[::-1].copy()))
+    assert oracle.longest_chain(anti) == 1 and oracle.longest_chain(anti, 0, 1) == -1
+    with open(os.path.join(GOLDEN, "tiny_posets.json")) as f:
+        g = json.load(f)["greedy_antichain"]
+    bits = oracle.causal_matrix(0, _coords_2d_order(g["v"]))
+    assert oracle.longest_chain(bits) == g["height"]
+    assert oracle.longest_chain(bits, 1, 2) == g["chain_1_2"] and oracle.longest_chain(bits, 0, 3) == g["chain_0_3"]
+    for case in g["cases"]:
+        size, members = oracle.greedy_antichain(bits, case["seed"])
+        got = [k for k in range(4) if (int(members[k >> 6]) >> (k & 63)) & 1]
+        assert got == case["antichain"] and size == len(got)
+
+
+@pytest.mark.parametrize("kind,n,seed", [(0, 500, 1), (1, 400, 2), (2, 300, 3), (0, 1, 4)])
+def test_greedy_antichain_is_a_maximal_antichain(oracle, kind, n, seed):
+    c = oracle.sprinkle(kind, n, seed)
+    bits = oracle.causal_matrix(kind, c)
+    m, _ = _unpack(bits, n)
+    for s in sorted({0, n // 2, n - 1}):
+        size, members = oracle.greedy_antichain(bits, s)
+        a = np.unpackbits(members.view(np.uint8), bitorder="little")[:n].astype(bool)
+        assert a[s] and a.sum() == size
+        idx = np.nonzero(a)[0]
+        assert not m[np.ix_(idx, idx)].any()                        # pairwise unrelated
+        outside = np.nonzero(~a)[0]
+        assert m[np.ix_(outside, idx)].any(axis=1).all()           # maximal
+        if kind == 0:   # a 2D order's antichains are decreasing runs of v
+            v = c[1].astype(np.int64)
+            assert size <= _lis((-v).tolist())
+    chain = oracle.causal_matrix(0, _coords_2d_order(np.arange(20)))
+    anti = oracle.causal_matrix(0, _coords_2d_order(np.arange(20)[::-1].copy()))
+    assert oracle.greedy_antichain(chain, 7)[0] == 1 and oracle.greedy_antichain(anti, 7)[0] == 20
