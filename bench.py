@@ -224,6 +224,62 @@ def ensemble_bench(cs, torch, path, steps=5, warmup=3, n2d=512, n4d=256):
             "algorithmic_macs": terms, "achieved_tflops_whole_step": 2 * terms / batched_ms / 1e9}
 
 
+def extras_bench(cs, torch, buf, kind, n, path, stream, peaks):
+    """The next-row outputs on the bench set, each timed with CUDA events on the
+    launching stream after a warm-up: degree vectors and the future sparse
+    relation list (HBM-bound row scans: roofline against the copy bandwidth),
+    and the d'Alembertian layer sums (the count with the per-element epilogue)."""
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    out = {}
+    L = cs.lib()
+    words = (n + 63) // 64
+    kin = torch.empty(n, dtype=torch.int32, device="cuda")
+    kout = torch.empty(n, dtype=torch.int32, device="cuda")
+    deg_ms = timed(lambda: cs.degrees(n, buf.bits, kin, kout, stream))
+    deg_bytes = n * words * 8 + 8 * n
+    ws = torch.empty(L.cs_sparse_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    L.cs_sparse_offsets(n, buf.bits.data_ptr(), buf.rw, 1, off.data_ptr(), ws.data_ptr(), ws.numel(), stream.cuda_stream)
+    total = int(off[n].item())
+    cols = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
+
+    def csr():
+        L.cs_sparse_offsets(n, buf.bits.data_ptr(), buf.rw, 1, off.data_ptr(), ws.data_ptr(), ws.numel(),
+                            stream.cuda_stream)
+        L.cs_sparse_columns(n, buf.bits.data_ptr(), buf.rw, 1, off.data_ptr(), cols.data_ptr(), total,
+                            ws.data_ptr(), ws.numel(), stream.cuda_stream)
+    csr_ms = timed(csr)
+    if cs.workspace_status(ws) != 0 or int(kout.sum().item()) != total:
+        raise RuntimeError("sparse lists disagree with the degrees")
+    csr_bytes = n * words * 4 + 4 * total + 8 * (n + 1)  # upper half of the bitset read once, lists written
+    hbm = peaks.get("hbm_gbs")
+    out["sparse"] = {
+        "degrees_ms": deg_ms, "degrees_gbs": deg_bytes / deg_ms / 1e6,
+        "future_csr_ms": csr_ms, "future_relations": total, "future_csr_gbs": csr_bytes / csr_ms / 1e6,
+        "roofline": {"bound": "hbm", "peak": hbm, "unit": "GB/s",
+                     "frac_degrees": deg_bytes / deg_ms / 1e6 / hbm if hbm else None,
+                     "frac_future_csr": csr_bytes / csr_ms / 1e6 / hbm if hbm else None,
+                     "bytes": {"degrees": deg_bytes, "future_csr": csr_bytes}},
+    }
+    del cols
+    # d'Alembertian layer sums (phi = 1, kmax = 3) against the plain count
+    layer = torch.empty((4, n), dtype=torch.float64, device="cuda")
+    lay_ms = timed(lambda: cs.layer_sums(n, buf.bits, buf.hist, layer, 3, None, path, buf.workspace, stream), reps=1)
+    cnt_ms = timed(lambda: cs.interval_abundance(n, buf.bits, buf.hist, path, buf.workspace, stream), reps=1)
+    out["dalembertian"] = {"layer_sums_ms": lay_ms, "count_only_ms": cnt_ms, "overhead": lay_ms / cnt_ms - 1.0,
+                           "kmax": 3}
+    return out
+
+
 def serving_bench(path, rate=200.0, duration_s=5.0):
     """The continuous-batching server on a Poisson trace (real time): throughput
     and latency percentiles under a 60 GB bitset budget."""
@@ -323,6 +379,8 @@ def main():
                     help="also time the other count path once on the same bitset")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the degree / sparse-list / d'Alembertian measurements")
     ap.add_argument("--ensemble-sets", default="512,256",
                     help="ensemble size: number of 2D diamonds, number of 4D diamonds (profiling runs use a sample)")
     args = ap.parse_args()
@@ -443,6 +501,8 @@ def main():
         "roofline": roofline,
         "clocks": clocks,
     }
+    if not args.no_extras:
+        line.update(extras_bench(cs, torch, buf, kind, n, path, stream, peaks))
     if not args.no_ensemble:
         n2d, n4d = (int(x) for x in args.ensemble_sets.split(","))
         line["ensemble"] = ensemble_bench(cs, torch, PATHS[args.path], n2d=n2d, n4d=n4d)

@@ -443,6 +443,38 @@ int cs_sparse_columns(int64_t n, const uint64_t *bits_dev, int64_t row_words, in
                       const int64_t *offsets_dev, int32_t *cols_dev, int64_t cols_capacity,
                       void *workspace_dev, size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------- chains and antichains */
+
+/* Device workspace for cs_longest_chain and cs_greedy_antichain. */
+size_t cs_chain_workspace_bytes(int64_t n);
+
+/*
+ * Longest chain (Section "Set Partitions", Algorithm "Maximal Chain
+ * Length") on the symmetric bitset of time-sorted labels.  For a pair
+ * i < j: *length = the number of relations on the longest chain from i to j
+ * (1 for a link), or -1 if i does not precede j (also for j <= i).  With
+ * i = j = -1: *length = the height of the whole set, the number of elements
+ * of its longest chain.  Computed by peeling the minimal elements of the
+ * Alexandroff set (or of the whole set) round by round.  Synchronous (the
+ * host checks the rounds in batches).  Errors: CS_EINVAL, CS_ENOMEM
+ * (workspace too small), CS_ECUDA.
+ */
+int cs_longest_chain(int64_t n, const uint64_t *bits_dev, int64_t row_words, int64_t i, int64_t j,
+                     int64_t *length, void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/*
+ * Greedy maximal antichain (Section "Set Partitions", Algorithm "Maximal
+ * Antichain") grown from `seed`: the candidates are the elements unrelated
+ * to the seed; each round keeps the candidate k that leaves the most
+ * elements when its relations are removed (the smallest label on ties) and
+ * removes its relations.  members_dev (row_words words, 8-byte aligned)
+ * receives the antichain as a bitset, *size its size.  Synchronous.
+ * Errors: CS_EINVAL, CS_ENOMEM (workspace too small), CS_ECUDA.
+ */
+int cs_greedy_antichain(int64_t n, const uint64_t *bits_dev, int64_t row_words, int64_t seed,
+                        uint64_t *members_dev, int64_t *size, void *workspace_dev, size_t workspace_bytes,
+                        void *stream);
+
 /* ---------------------------------------------------- failure detection */
 
 /*

@@ -23,7 +23,7 @@ __all__ = [
     "set_auto_paths", "get_auto_paths",
     "sprinkle", "sprinkle_noalloc", "causal_matrix", "layer_sums", "dalembertian", "interval_abundance", "workspace_status", "action", "action_device",
     "evaluate", "Buffers", "allocate", "run", "SetDesc", "Batch", "CountJob", "count_items",
-    "operands_bytes", "prepare_operands", "count_jobs", "degrees", "sparse_relations", "FAULT_ALLOC", "FAULT_LAUNCH", "selftest_wait",
+    "operands_bytes", "prepare_operands", "count_jobs", "degrees", "sparse_relations", "longest_chain", "greedy_antichain", "FAULT_ALLOC", "FAULT_LAUNCH", "selftest_wait",
     "inject_fault",
 ]
 
@@ -100,6 +100,11 @@ def lib() -> ctypes.CDLL:
             "cs_sparse_workspace_bytes": ([i64], ctypes.c_size_t),
             "cs_sparse_offsets": ([i64, vp, i64, i32, vp, vp, ctypes.c_size_t, vp], i32),
             "cs_sparse_columns": ([i64, vp, i64, i32, vp, vp, i64, vp, ctypes.c_size_t, vp], i32),
+            "cs_chain_workspace_bytes": ([i64], ctypes.c_size_t),
+            "cs_longest_chain": ([i64, vp, i64, i64, i64, ctypes.POINTER(ctypes.c_int64), vp, ctypes.c_size_t, vp],
+                                 i32),
+            "cs_greedy_antichain": ([i64, vp, i64, i64, vp, ctypes.POINTER(ctypes.c_int64), vp, ctypes.c_size_t,
+                                     vp], i32),
             "cs_selftest_wait": ([vp, ctypes.c_double, i32, vp], i32),
             "cs_inject_fault": ([i32, i32], i32),
             "cs_strerror": ([i32], ctypes.c_char_p),
@@ -427,6 +432,34 @@ def sparse_relations(n, bits, direction, stream=None):
     if st != 0:
         raise CsError(st, "cs_sparse_columns")
     return offsets, cols[:total]
+
+
+# ------------------------------------------------ chains and antichains
+
+def _chain_ws(n, device):
+    import torch
+    return torch.empty(lib().cs_chain_workspace_bytes(n), dtype=torch.uint8, device=device)
+
+
+def longest_chain(n, bits, i=-1, j=-1, stream=None):
+    """cs_longest_chain: relations on the longest chain from i to j (-1 if unrelated);
+    i = j = -1: the height of the whole set in elements."""
+    ws = _chain_ws(n, bits.device)
+    out = ctypes.c_int64(0)
+    _check(lib().cs_longest_chain(n, _ptr(bits), bits.shape[-1], i, j, ctypes.byref(out), _ptr(ws), ws.numel(),
+                                  _stream(stream)), "cs_longest_chain")
+    return out.value
+
+
+def greedy_antichain(n, bits, seed, stream=None):
+    """cs_greedy_antichain: (size, member bitset as an int64 device tensor of row_words words)."""
+    import torch
+    ws = _chain_ws(n, bits.device)
+    members = torch.empty(bits.shape[-1], dtype=torch.int64, device=bits.device)
+    out = ctypes.c_int64(0)
+    _check(lib().cs_greedy_antichain(n, _ptr(bits), bits.shape[-1], seed, _ptr(members), ctypes.byref(out),
+                                     _ptr(ws), ws.numel(), _stream(stream)), "cs_greedy_antichain")
+    return out.value, members
 
 
 # ------------------------------------------------------ failure detection

@@ -1,0 +1,308 @@
+// cs_chains.cu -- longest chains and greedy maximal antichains on the bitset
+// (Section "Set Partitions": Algorithms "Maximal Chain Length" and "Maximal
+// Antichain").
+//
+// Longest chain.  The thesis recurses through the Alexandroff set, caching
+// the distance of each element to the top.  On the GPU the same length comes
+// from peeling: the set S (A_ij for a pair, every element for the whole set)
+// loses all its minimal elements -- those with no predecessor left in S --
+// once per round; the number of rounds is the number of elements of the
+// longest chain in S.  A round is one warp per element of S testing
+// P_k & S over the words before k, then one block clearing the removed bits.
+//
+// Greedy antichain.  Each round scores every candidate j by
+// c_j = |A - J(j)| (one warp per candidate, popcounts of A & ~row_j), keeps
+// the best with one 64-bit atomicMax on (c_j, -j) -- the largest c, the
+// smallest label on ties, as in the algorithm's scan -- and one block
+// removes J(k) from A and J(k) + {k} from the candidates.
+//
+// Both run rounds in batches of kBatch launches between host checks of the
+// number of elements left; rounds after the last one find nothing to do.
+#include "cs_kernels.cuh"
+
+namespace cs {
+
+namespace {
+
+constexpr int kBatch = 32;
+
+struct ChainState {
+    unsigned long long best;  // antichain: packed (c, ~label) of the best candidate
+    int32_t found;            // chain: this round removed something
+    int32_t related;          // chain: i precedes j
+    int64_t rounds;           // rounds that removed something
+    int64_t left;             // elements left in S (chain) or candidates left (antichain)
+};
+
+struct ChainLayout {
+    size_t state, s, m, total;
+};
+
+ChainLayout chain_layout(int64_t row_words) {
+    ChainLayout L;
+    size_t off = sizeof(WsHeader);
+    L.state = off;
+    off = align_up(off + sizeof(ChainState), 256);
+    L.s = off;
+    off = align_up(off + size_t(row_words) * 8, 256);
+    L.m = off;
+    off = align_up(off + size_t(row_words) * 8, 256);
+    L.total = off;
+    return L;
+}
+
+__device__ __forceinline__ bool bit_of(const uint64_t* row, int64_t k) { return (row[k >> 6] >> (k & 63)) & 1ull; }
+
+// Bits of word w strictly between columns lo and hi (lo < col < hi).
+__device__ __forceinline__ uint64_t between_mask(int64_t w, int64_t lo, int64_t hi) {
+    const int64_t c0 = 64 * w;
+    uint64_t m = ~0ull;
+    if (lo + 1 > c0) m = lo + 1 - c0 >= 64 ? 0ull : m & (~0ull << (lo + 1 - c0));
+    if (hi < c0 + 64) m = hi <= c0 ? 0ull : m & (~0ull >> (c0 + 64 - hi));
+    return m;
+}
+
+__device__ __forceinline__ int warp_or(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// S = A_ij (bits strictly between i and j set in both rows), or all of [0, n).
+__global__ void k_chain_init(const uint64_t* __restrict__ bits, int64_t n, int64_t row_words, int64_t i, int64_t j,
+                             uint64_t* __restrict__ S, uint64_t* __restrict__ M, ChainState* st) {
+    const bool whole = i < 0;
+    const int64_t lo = whole ? -1 : i, hi = whole ? n : j;
+    for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < row_words;
+         w += int64_t(gridDim.x) * blockDim.x) {
+        uint64_t x = between_mask(w, lo, hi);
+        if (!whole) x &= __ldg(bits + i * row_words + w) & __ldg(bits + j * row_words + w);
+        S[w] = x;
+        M[w] = 0ull;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->found = 0;
+        st->rounds = 0;
+        st->related = whole ? 1 : int(bit_of(bits + i * row_words, j));
+        st->left = 1;
+    }
+}
+
+// One peeling round: the elements of S with no predecessor in S go to M.
+__global__ void __launch_bounds__(256) k_chain_peel(const uint64_t* __restrict__ bits, int64_t row_words,
+                                                    int64_t lo, int64_t hi, const uint64_t* __restrict__ S,
+                                                    uint64_t* __restrict__ M, ChainState* st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    const int64_t wlo = lo < 0 ? 0 : lo >> 6;
+    for (int64_t k = lo + 1 + int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); k < hi; k += warps) {
+        if (!bit_of(S, k)) continue;  // warp-uniform
+        const int64_t wk = k >> 6;
+        int any = 0;
+        for (int64_t w = wlo + lane; w <= wk && !any; w += 32) {
+            uint64_t x = __ldg(bits + k * row_words + w) & S[w];
+            if (w == wk) x &= (k & 63) ? ((1ull << (k & 63)) - 1ull) : 0ull;  // predecessors only
+            any = x != 0ull;
+        }
+        if (!warp_or(any) && lane == 0) {
+            atomicOr(reinterpret_cast<unsigned long long*>(M + wk), 1ull << (k & 63));
+            st->found = 1;
+        }
+    }
+}
+
+// Close a round: S -= M, count it if it removed anything, count what is left.
+__global__ void __launch_bounds__(1024) k_chain_apply(int64_t row_words, uint64_t* __restrict__ S,
+                                                      uint64_t* __restrict__ M, ChainState* st) {
+    __shared__ unsigned long long left;
+    __shared__ int found;
+    if (threadIdx.x == 0) {
+        left = 0;
+        found = st->found;
+    }
+    __syncthreads();
+    unsigned long long mine = 0;
+    for (int64_t w = threadIdx.x; w < row_words; w += blockDim.x) {
+        const uint64_t x = S[w] & ~M[w];
+        S[w] = x;
+        M[w] = 0ull;
+        mine += __popcll(x);
+    }
+    atomicAdd(&left, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (found) st->rounds += 1;
+        st->found = 0;
+        st->left = int64_t(left);
+    }
+}
+
+// Antichain start: X = elements unrelated to the seed, A = X + {seed}.
+__global__ void k_anti_init(const uint64_t* __restrict__ bits, int64_t n, int64_t row_words, int64_t seed,
+                            uint64_t* __restrict__ A, uint64_t* __restrict__ X, ChainState* st) {
+    for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < row_words;
+         w += int64_t(gridDim.x) * blockDim.x) {
+        uint64_t x = ~__ldg(bits + seed * row_words + w) & between_mask(w, -1, n);
+        if (w == (seed >> 6)) x &= ~(1ull << (seed & 63));
+        X[w] = x;
+        A[w] = w == (seed >> 6) ? x | (1ull << (seed & 63)) : x;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->best = 0ull;
+        st->left = 1;
+    }
+}
+
+// Score every candidate j by |A - J(j)|; keep the best (largest, then first).
+__global__ void __launch_bounds__(256) k_anti_score(const uint64_t* __restrict__ bits, int64_t n, int64_t row_words,
+                                                    const uint64_t* __restrict__ A, const uint64_t* __restrict__ X,
+                                                    ChainState* st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (n + 63) >> 6;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t k = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n; k += warps) {
+        if (!bit_of(X, k)) continue;  // warp-uniform
+        int c = 0;
+        for (int64_t w = lane; w < nw; w += 32) c += __popcll(A[w] & ~__ldg(bits + k * row_words + w));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0)
+            atomicMax(&st->best, (static_cast<unsigned long long>(c) << 32) | (0xFFFFFFFFull - uint64_t(k)));
+    }
+}
+
+// Take the best candidate k: A -= J(k), X -= J(k) + {k}.
+__global__ void __launch_bounds__(1024) k_anti_apply(const uint64_t* __restrict__ bits, int64_t row_words,
+                                                     uint64_t* __restrict__ A, uint64_t* __restrict__ X,
+                                                     ChainState* st) {
+    __shared__ unsigned long long left;
+    __shared__ unsigned long long best;
+    if (threadIdx.x == 0) {
+        left = 0;
+        best = st->best;
+    }
+    __syncthreads();
+    const bool take = best != 0ull;
+    const int64_t k = int64_t(0xFFFFFFFFull - (best & 0xFFFFFFFFull));
+    unsigned long long mine = 0;
+    for (int64_t w = threadIdx.x; w < row_words; w += blockDim.x) {
+        uint64_t x = X[w];
+        if (take) {
+            const uint64_t r = __ldg(bits + k * row_words + w);
+            A[w] &= ~r;
+            x &= ~r;
+            if (w == (k >> 6)) x &= ~(1ull << (k & 63));
+            X[w] = x;
+        }
+        mine += __popcll(x);
+    }
+    atomicAdd(&left, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->best = 0ull;
+        st->left = int64_t(left);
+    }
+}
+
+// Number of set bits of a bitset into st->rounds.
+__global__ void __launch_bounds__(1024) k_count_bits(const uint64_t* __restrict__ A, int64_t row_words,
+                                                     ChainState* st) {
+    __shared__ unsigned long long total;
+    if (threadIdx.x == 0) total = 0;
+    __syncthreads();
+    unsigned long long mine = 0;
+    for (int64_t w = threadIdx.x; w < row_words; w += blockDim.x) mine += __popcll(A[w]);
+    atomicAdd(&total, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) st->rounds = int64_t(total);
+}
+
+int warp_grid(int64_t rows) {
+    int64_t g = (rows + 7) / 8;
+    const int64_t cap = int64_t(device_sm_count()) * 16;
+    return int(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+bool chain_args_ok(int64_t n, const uint64_t* bits, int64_t row_words, void* ws) {
+    return n >= 1 && n <= kMaxN && bits && (reinterpret_cast<uintptr_t>(bits) % 16) == 0 &&
+           row_words >= cs_row_words(n) && row_words % 16 == 0 && ws && (reinterpret_cast<uintptr_t>(ws) % 256) == 0;
+}
+
+cudaError_t read_state(const ChainState* dev, ChainState* host, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(host, dev, sizeof(ChainState), cudaMemcpyDeviceToHost, st);
+    return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+}
+
+}  // namespace
+
+}  // namespace cs
+
+using namespace cs;
+
+extern "C" size_t cs_chain_workspace_bytes(int64_t n) {
+    if (n < 1 || n > kMaxN) return 0;
+    return chain_layout(cs_row_words(n)).total;
+}
+
+extern "C" int cs_longest_chain(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_t i, int64_t j,
+                                int64_t* length, void* workspace_dev, size_t workspace_bytes, void* stream) {
+    if (!chain_args_ok(n, bits_dev, row_words, workspace_dev) || !length) return CS_EINVAL;
+    const bool whole = i < 0 && j < 0;
+    if (!whole && (i < 0 || j < 0 || i >= n || j >= n)) return CS_EINVAL;
+    const ChainLayout L = chain_layout(row_words);
+    if (workspace_bytes < L.total) return CS_ENOMEM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint8_t* ws = static_cast<uint8_t*>(workspace_dev);
+    ChainState* sd = reinterpret_cast<ChainState*>(ws + L.state);
+    uint64_t* S = reinterpret_cast<uint64_t*>(ws + L.s);
+    uint64_t* M = reinterpret_cast<uint64_t*>(ws + L.m);
+    if (!whole && j <= i) {
+        *length = -1;
+        return CS_OK;
+    }
+    const int64_t lo = whole ? -1 : i, hi = whole ? n : j;
+    int64_t g = (row_words + 255) / 256;
+    k_chain_init<<<unsigned(g < 1 ? 1 : g), 256, 0, st>>>(bits_dev, n, row_words, whole ? -1 : i, j, S, M, sd);
+    ChainState h{};
+    for (int64_t done = 0; done <= n; done += kBatch) {  // at most n + 1 rounds remove anything
+        for (int r = 0; r < kBatch; ++r) {
+            k_chain_peel<<<warp_grid(hi - lo - 1), 256, 0, st>>>(bits_dev, row_words, lo, hi, S, M, sd);
+            k_chain_apply<<<1, 1024, 0, st>>>(row_words, S, M, sd);
+        }
+        if (cudaGetLastError() != cudaSuccess || read_state(sd, &h, st) != cudaSuccess) return CS_ECUDA;
+        if (h.left == 0 || !h.related) break;
+    }
+    if (h.left != 0 && h.related) return CS_ERANGE;  // cannot happen for a transitive relation
+    *length = whole ? h.rounds : (h.related ? h.rounds + 1 : -1);
+    return CS_OK;
+}
+
+extern "C" int cs_greedy_antichain(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_t seed,
+                                   uint64_t* members_dev, int64_t* size, void* workspace_dev, size_t workspace_bytes,
+                                   void* stream) {
+    if (!chain_args_ok(n, bits_dev, row_words, workspace_dev) || seed < 0 || seed >= n || !members_dev ||
+        (reinterpret_cast<uintptr_t>(members_dev) % 8) != 0 || !size)
+        return CS_EINVAL;
+    const ChainLayout L = chain_layout(row_words);
+    if (workspace_bytes < L.total) return CS_ENOMEM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint8_t* ws = static_cast<uint8_t*>(workspace_dev);
+    ChainState* sd = reinterpret_cast<ChainState*>(ws + L.state);
+    uint64_t* X = reinterpret_cast<uint64_t*>(ws + L.s);
+    int64_t g = (row_words + 255) / 256;
+    k_anti_init<<<unsigned(g < 1 ? 1 : g), 256, 0, st>>>(bits_dev, n, row_words, seed, members_dev, X, sd);
+    ChainState h{};
+    for (int64_t done = 0; done <= n; done += kBatch) {  // every round with a candidate removes one
+        for (int r = 0; r < kBatch; ++r) {
+            k_anti_score<<<warp_grid(n), 256, 0, st>>>(bits_dev, n, row_words, members_dev, X, sd);
+            k_anti_apply<<<1, 1024, 0, st>>>(bits_dev, row_words, members_dev, X, sd);
+        }
+        if (cudaGetLastError() != cudaSuccess || read_state(sd, &h, st) != cudaSuccess) return CS_ECUDA;
+        if (h.left == 0) break;
+    }
+    if (h.left != 0) return CS_ERANGE;
+    k_count_bits<<<1, 1024, 0, st>>>(members_dev, row_words, sd);
+    if (cudaGetLastError() != cudaSuccess || read_state(sd, &h, st) != cudaSuccess) return CS_ECUDA;
+    *size = h.rounds;
+    return CS_OK;
+}
