@@ -277,6 +277,17 @@ def extras_bench(cs, torch, buf, kind, n, path, stream, peaks):
     cnt_ms = timed(lambda: cs.interval_abundance(n, buf.bits, buf.hist, path, buf.workspace, stream), reps=1)
     out["dalembertian"] = {"layer_sums_ms": lay_ms, "count_only_ms": cnt_ms, "overhead": lay_ms / cnt_ms - 1.0,
                            "kmax": 3}
+    # chains and antichains (synchronous entry points: wall time around the call)
+    def wall(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        return r, (time.perf_counter() - t0) * 1e3
+    height, h_ms = wall(lambda: cs.longest_chain(n, buf.bits))
+    (asize, _), a_ms = wall(lambda: cs.greedy_antichain(n, buf.bits, n // 2))
+    out["chains"] = {"height": height, "height_ms": h_ms, "antichain_seed": n // 2, "antichain_size": asize,
+                     "antichain_ms": a_ms}
     return out
 
 

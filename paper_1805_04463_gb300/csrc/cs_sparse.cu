@@ -8,9 +8,9 @@
 // bitset with time-sorted labels, so both come from row scans: the future
 // list of i is the set bits of row i above column i, the past list the set
 // bits below it.  One warp owns a row: each lane loads one 64-bit word per
-// step (coalesced), popcounts give the degrees, a warp scan of the per-word
-// counts gives every lane its output position, and each lane writes the
-// column indices of its word's set bits in increasing order.  The row
+// step (coalesced) and popcounts give the degrees; for the lists, the warp
+// takes the words one 32-bit half at a time, every lane owning one bit, so
+// each half's column indices leave in one coalesced run of stores.  The row
 // offsets are an exclusive scan of the degrees (three small kernels).
 #include "cs_kernels.cuh"
 
@@ -163,12 +163,16 @@ __global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* 
 
 // Column indices of each row's relations on one side, in increasing order,
 // at cols[offsets[i] ..).  A row whose list would end past cols_capacity is
-// skipped and CS_ENOMEM recorded.
+// skipped and CS_ENOMEM recorded.  The warp walks its row 32 words at a time;
+// for each 32-bit half-word in turn every lane owns one bit, so the set bits
+// of a half-word go out as one coalesced run of stores (rank of a bit = the
+// popcount of the lower lanes' bits).
 __global__ void __launch_bounds__(256) k_side_columns(const uint64_t* __restrict__ bits, int64_t n,
                                                       int64_t row_words, bool future,
                                                       const int64_t* __restrict__ offsets, int32_t* __restrict__ cols,
                                                       int64_t cols_capacity, WsHeader* hdr) {
     const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;  // lanes under this one
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
     for (int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
         if (offsets[i + 1] > cols_capacity || offsets[i + 1] < offsets[i]) {
@@ -181,18 +185,20 @@ __global__ void __launch_bounds__(256) k_side_columns(const uint64_t* __restrict
         const int64_t end = offsets[i + 1];
         for (int64_t w0 = wlo; w0 < whi; w0 += 32) {
             const int64_t w = w0 + lane;
-            uint64_t x = w < whi ? __ldg(bits + i * row_words + w) & side_mask(i, w, future) : 0ull;
-            const int c = __popcll(x);
-            int inc = c;  // inclusive warp scan of the counts
+            const uint64_t x = w < whi ? __ldg(bits + i * row_words + w) & side_mask(i, w, future) : 0ull;
+            const int64_t nword = whi - w0 < 32 ? whi - w0 : 32;
+            for (int q = 0; q < nword; ++q) {  // warp-uniform
+                const uint64_t y = __shfl_sync(0xffffffffu, x, q);
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t half = uint32_t(y >> (32 * h));
+                    if (half == 0u) continue;  // warp-uniform
+                    const int64_t p = pos + __popc(half & below);
+                    if (((half >> lane) & 1u) && p < end)  // p < end unless the bitset changed
+                        cols[p] = int32_t(64 * (w0 + q) + 32 * h + lane);
+                    pos += __popc(half);
+                }
             }
-            int64_t p = pos + inc - c;
-            for (; x; x &= x - 1ull, ++p)  // p < end unless the bitset changed since the offsets
-                if (p < end) cols[p] = int32_t(64 * w + __ffsll(static_cast<long long>(x)) - 1);
-            pos += __shfl_sync(0xffffffffu, inc, 31);
         }
     }
 }
