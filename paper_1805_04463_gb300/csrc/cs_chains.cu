@@ -16,8 +16,10 @@
 // smallest label on ties, as in the algorithm's scan -- and one block
 // removes J(k) from A and J(k) + {k} from the candidates.
 //
-// Both run rounds in batches of kBatch launches between host checks of the
-// number of elements left; rounds after the last one find nothing to do.
+// Both run all their rounds in one cooperative launch, the rounds separated
+// by bounded grid barriers; where a cooperative launch is not available they
+// fall back to batches of kBatch launches between host checks of the number
+// of elements left (rounds after the last one find nothing to do).
 #include "cs_kernels.cuh"
 
 namespace cs {
@@ -32,6 +34,10 @@ struct ChainState {
     int32_t related;          // chain: i precedes j
     int64_t rounds;           // rounds that removed something
     int64_t left;             // elements left in S (chain) or candidates left (antichain)
+    // persistent (cooperative) kernels: grid barrier and per-round-parity counters
+    unsigned int bar_count, bar_gen;
+    unsigned long long left2[2];
+    unsigned long long best2[2];
 };
 
 struct ChainLayout {
@@ -217,6 +223,148 @@ __global__ void __launch_bounds__(1024) k_count_bits(const uint64_t* __restrict_
     if (threadIdx.x == 0) st->rounds = int64_t(total);
 }
 
+// ------------------------------------------- persistent (cooperative) rounds
+//
+// With a cooperative launch every block is resident, so the rounds can run in
+// one kernel separated by grid barriers instead of two launches per round.
+// The barrier's wait is bounded: after 4 s it records CS_ETIMEOUT and the
+// kernel returns (every later barrier of the other blocks then times out
+// too), so a fault cannot hang the GPU.
+
+__device__ bool grid_barrier(ChainState* st, unsigned int nblocks, WsHeader* hdr) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int* gen = &st->bar_gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(&st->bar_count, 1u) == nblocks - 1u) {
+            st->bar_count = 0u;
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = global_timer_ns();
+            while (*gen == g) {
+                if (global_timer_ns() - t0 > kWaitLimitNs) {
+                    set_status(hdr, CS_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+__device__ __forceinline__ unsigned long long block_sum_to(unsigned long long v, unsigned long long* dst) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+    return v;
+}
+
+// All peeling rounds: peel (as k_chain_peel), barrier, S -= M with the count
+// of what is left, barrier, stop when nothing is left.  rounds = the number
+// of rounds run (S is not empty at the start).
+__global__ void __launch_bounds__(256) k_chain_persist(const uint64_t* __restrict__ bits, int64_t row_words,
+                                                       int64_t lo, int64_t hi, int64_t max_rounds, uint64_t* S,
+                                                       uint64_t* M, ChainState* st, WsHeader* hdr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    const int64_t gwarp = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t gthread = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nthreads = int64_t(gridDim.x) * blockDim.x;
+    const int64_t wlo = lo < 0 ? 0 : lo >> 6;
+    for (int64_t r = 0; r < max_rounds; ++r) {
+        for (int64_t k = lo + 1 + gwarp; k < hi; k += warps) {
+            if (!bit_of(S, k)) continue;  // warp-uniform
+            const int64_t wk = k >> 6;
+            int any = 0;
+            for (int64_t w = wk - lane; w >= wlo && !any; w -= 32) {  // nearest predecessors first
+                uint64_t x = __ldg(bits + k * row_words + w) & S[w];
+                if (w == wk) x &= (k & 63) ? ((1ull << (k & 63)) - 1ull) : 0ull;
+                any = x != 0ull;
+            }
+            if (!warp_or(any) && lane == 0) atomicOr(reinterpret_cast<unsigned long long*>(M + wk), 1ull << (k & 63));
+        }
+        if (!grid_barrier(st, gridDim.x, hdr)) return;
+        unsigned long long mine = 0;
+        for (int64_t w = gthread; w < row_words; w += nthreads) {
+            const uint64_t x = S[w] & ~M[w];
+            S[w] = x;
+            M[w] = 0ull;
+            mine += __popcll(x);
+        }
+        block_sum_to(mine, &st->left2[r & 1]);
+        if (gthread == 0) st->left2[(r + 1) & 1] = 0ull;  // last read before the previous barrier
+        if (!grid_barrier(st, gridDim.x, hdr)) return;
+        if (*reinterpret_cast<volatile unsigned long long*>(&st->left2[r & 1]) == 0ull) {
+            if (gthread == 0) st->rounds = r + 1;
+            return;
+        }
+    }
+}
+
+// All greedy rounds: score into best2[r & 1], barrier, apply the best, count
+// the candidates left, barrier, stop when none are left.
+__global__ void __launch_bounds__(256) k_anti_persist(const uint64_t* __restrict__ bits, int64_t n,
+                                                      int64_t row_words, int64_t max_rounds, uint64_t* A,
+                                                      uint64_t* X, ChainState* st, WsHeader* hdr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (n + 63) >> 6;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    const int64_t gwarp = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t gthread = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nthreads = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t r = 0; r < max_rounds; ++r) {
+        for (int64_t k = gwarp; k < n; k += warps) {
+            if (!bit_of(X, k)) continue;  // warp-uniform
+            int c = 0;
+            for (int64_t w = lane; w < nw; w += 32) c += __popcll(A[w] & ~__ldg(bits + k * row_words + w));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane == 0)
+                atomicMax(&st->best2[r & 1], (static_cast<unsigned long long>(c) << 32) | (0xFFFFFFFFull - uint64_t(k)));
+        }
+        if (gthread == 0) st->best2[(r + 1) & 1] = 0ull;  // last read before the previous barrier
+        if (!grid_barrier(st, gridDim.x, hdr)) return;
+        const unsigned long long best = *reinterpret_cast<volatile unsigned long long*>(&st->best2[r & 1]);
+        if (best == 0ull) return;  // no candidates (all blocks see the same value)
+        const int64_t k = int64_t(0xFFFFFFFFull - (best & 0xFFFFFFFFull));
+        unsigned long long mine = 0;
+        for (int64_t w = gthread; w < row_words; w += nthreads) {
+            const uint64_t rk = __ldg(bits + k * row_words + w);
+            uint64_t x = X[w] & ~rk;
+            if (w == (k >> 6)) x &= ~(1ull << (k & 63));
+            X[w] = x;
+            A[w] &= ~rk;
+            mine += __popcll(x);
+        }
+        block_sum_to(mine, &st->left2[r & 1]);
+        if (gthread == 0) st->left2[(r + 1) & 1] = 0ull;
+        if (!grid_barrier(st, gridDim.x, hdr)) return;
+        if (*reinterpret_cast<volatile unsigned long long*>(&st->left2[r & 1]) == 0ull) return;
+    }
+}
+
+// Blocks of a cooperative launch of `kernel` (all resident), capped by the work.
+int coop_grid(const void* kernel, int64_t warps_of_work) {
+    int dev = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1)
+        return 0;
+    int64_t g = int64_t(per_sm) * device_sm_count();
+    const int64_t need = (warps_of_work + 7) / 8;
+    if (g > need) g = need;
+    return int(g < 1 ? 1 : g);
+}
+
 int warp_grid(int64_t rows) {
     int64_t g = (rows + 7) / 8;
     const int64_t cap = int64_t(device_sm_count()) * 16;
@@ -264,6 +412,42 @@ extern "C" int cs_longest_chain(int64_t n, const uint64_t* bits_dev, int64_t row
     int64_t g = (row_words + 255) / 256;
     k_chain_init<<<unsigned(g < 1 ? 1 : g), 256, 0, st>>>(bits_dev, n, row_words, whole ? -1 : i, j, S, M, sd);
     ChainState h{};
+    // one cooperative launch for all rounds when the device allows it
+    const int cg = coop_grid(reinterpret_cast<const void*>(k_chain_persist), hi - lo - 1);
+    if (cg > 0) {
+        k_count_bits<<<1, 1024, 0, st>>>(S, row_words, sd);  // |S| at the start into rounds
+        if (cudaGetLastError() != cudaSuccess || read_state(sd, &h, st) != cudaSuccess) return CS_ECUDA;
+        if (!h.related) {
+            *length = -1;
+            return CS_OK;
+        }
+        if (h.rounds == 0) {  // empty interval: a link, or an empty set
+            *length = whole ? 0 : 1;
+            return CS_OK;
+        }
+        WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+        if (cudaMemsetAsync(&sd->bar_count, 0, sizeof(unsigned int) * 2 + sizeof(unsigned long long) * 4, st) !=
+                cudaSuccess ||
+            cudaMemsetAsync(&sd->rounds, 0xFF, sizeof(int64_t), st) != cudaSuccess ||  // -1 until the last round
+            cudaMemsetAsync(&hdr->status, 0, sizeof(int32_t), st) != cudaSuccess)
+            return CS_ECUDA;
+        int64_t max_rounds = n + 1;
+        void* args[] = {const_cast<uint64_t**>(&bits_dev), &row_words, const_cast<int64_t*>(&lo),
+                        const_cast<int64_t*>(&hi), &max_rounds, &S, &M, &sd, &hdr};
+        if (cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_chain_persist), dim3(unsigned(cg)), dim3(256),
+                                        args, 0, st) == cudaSuccess) {
+            int32_t status = 0;
+            if (read_state(sd, &h, st) != cudaSuccess ||
+                cudaMemcpy(&status, &hdr->status, sizeof(status), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return CS_ECUDA;
+            if (status != 0) return status;
+            if (h.rounds < 0) return CS_ERANGE;  // cannot happen for a transitive relation
+            *length = whole ? h.rounds : h.rounds + 1;
+            return CS_OK;
+        }
+        cudaGetLastError();  // not launched: clear and take the multi-launch path
+        k_chain_init<<<unsigned(g < 1 ? 1 : g), 256, 0, st>>>(bits_dev, n, row_words, whole ? -1 : i, j, S, M, sd);
+    }
     for (int64_t done = 0; done <= n; done += kBatch) {  // at most n + 1 rounds remove anything
         for (int r = 0; r < kBatch; ++r) {
             k_chain_peel<<<warp_grid(hi - lo - 1), 256, 0, st>>>(bits_dev, row_words, lo, hi, S, M, sd);
@@ -292,17 +476,41 @@ extern "C" int cs_greedy_antichain(int64_t n, const uint64_t* bits_dev, int64_t 
     int64_t g = (row_words + 255) / 256;
     k_anti_init<<<unsigned(g < 1 ? 1 : g), 256, 0, st>>>(bits_dev, n, row_words, seed, members_dev, X, sd);
     ChainState h{};
-    for (int64_t done = 0; done <= n; done += kBatch) {  // every round with a candidate removes one
+    const int cg = coop_grid(reinterpret_cast<const void*>(k_anti_persist), n);
+    bool done = false;
+    if (cg > 0) {
+        WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+        if (cudaMemsetAsync(&sd->bar_count, 0, sizeof(unsigned int) * 2 + sizeof(unsigned long long) * 4, st) !=
+                cudaSuccess ||
+            cudaMemsetAsync(&hdr->status, 0, sizeof(int32_t), st) != cudaSuccess)
+            return CS_ECUDA;
+        int64_t max_rounds = n + 1;
+        void* args[] = {const_cast<uint64_t**>(&bits_dev), &n, &row_words, &max_rounds, &members_dev, &X, &sd, &hdr};
+        if (cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_anti_persist), dim3(unsigned(cg)), dim3(256),
+                                        args, 0, st) == cudaSuccess) {
+            int32_t status = 0;
+            if (cudaStreamSynchronize(st) != cudaSuccess ||
+                cudaMemcpy(&status, &hdr->status, sizeof(status), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return CS_ECUDA;
+            if (status != 0) return status;
+            done = true;
+        } else {
+            cudaGetLastError();
+            k_anti_init<<<unsigned(g < 1 ? 1 : g), 256, 0, st>>>(bits_dev, n, row_words, seed, members_dev, X, sd);
+        }
+    }
+    for (int64_t rounds = 0; !done && rounds <= n; rounds += kBatch) {  // multi-launch path
         for (int r = 0; r < kBatch; ++r) {
             k_anti_score<<<warp_grid(n), 256, 0, st>>>(bits_dev, n, row_words, members_dev, X, sd);
             k_anti_apply<<<1, 1024, 0, st>>>(bits_dev, row_words, members_dev, X, sd);
         }
         if (cudaGetLastError() != cudaSuccess || read_state(sd, &h, st) != cudaSuccess) return CS_ECUDA;
-        if (h.left == 0) break;
+        if (h.left == 0) done = true;
     }
-    if (h.left != 0) return CS_ERANGE;
+    if (!done) return CS_ERANGE;
     k_count_bits<<<1, 1024, 0, st>>>(members_dev, row_words, sd);
     if (cudaGetLastError() != cudaSuccess || read_state(sd, &h, st) != cudaSuccess) return CS_ECUDA;
     *size = h.rounds;
     return CS_OK;
 }
+
