@@ -452,6 +452,21 @@ def main():
         dist.barrier()
     elapsed_ms = start.elapsed_time(stop)
     count_ms = [a.elapsed_time(b) for a, b in ev]
+
+    # per-stage times of one more step (events between the stages, outside the timed region)
+    se = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    se[0].record(stream)
+    cs.sprinkle(kind, n, seed, buf.coords, buf.workspace, stream)
+    se[1].record(stream)
+    cs.causal_matrix(kind, n, buf.coords, buf.bits, stream)
+    se[2].record(stream)
+    cs.interval_abundance(n, buf.bits, buf.hist, path, buf.workspace, stream)
+    se[3].record(stream)
+    cs.action_device(cs.dim(kind), n, buf.hist, list(EPS), buf.actions, buf.bracket, buf.workspace, stream)
+    se[4].record(stream)
+    torch.cuda.synchronize()
+    stages_ms = {name: se[k].elapsed_time(se[k + 1])
+                 for k, name in enumerate(("sprinkle", "relate", "count", "action"))}
     hist = buf.hist.cpu().numpy()
     pairs = int(hist.sum())
     actions = buf.actions.cpu().numpy()[:len(EPS)].tolist()
@@ -511,6 +526,7 @@ def main():
         "gpu_launches": launches_per_step(kind, cs.resolved_path(n, path)) * args.steps,
         "roofline": roofline,
         "clocks": clocks,
+        "stages_ms": stages_ms,
     }
     if not args.no_extras:
         line.update(extras_bench(cs, torch, buf, kind, n, path, stream, peaks))

@@ -23,13 +23,14 @@ __all__ = [
     "set_auto_paths", "get_auto_paths",
     "sprinkle", "sprinkle_noalloc", "causal_matrix", "layer_sums", "dalembertian", "interval_abundance", "workspace_status", "action", "action_device",
     "evaluate", "Buffers", "allocate", "run", "SetDesc", "Batch", "CountJob", "count_items",
-    "operands_bytes", "prepare_operands", "count_jobs", "degrees", "sparse_relations", "longest_chain", "greedy_antichain", "FAULT_ALLOC", "FAULT_LAUNCH", "selftest_wait",
+    "operands_bytes", "prepare_operands", "count_jobs", "degrees", "sparse_relations", "longest_chain", "greedy_antichain", "BATCH_MAX_N", "FAULT_ALLOC", "FAULT_LAUNCH", "selftest_wait",
     "inject_fault",
 ]
 
 KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND, KIND_2D_DS_SLAB = 0, 1, 2, 3, 4
 PATH_AUTO, PATH_POPC, PATH_MMA = 0, 1, 2
 FAULT_ALLOC, FAULT_LAUNCH = 1, 2
+BATCH_MAX_N = 8192  # CS_BATCH_MAX_N: largest set a batch takes
 KIND_NAMES = {KIND_2D_ORDER: "2d_order", KIND_2D_DIAMOND: "2d_diamond", KIND_4D_DIAMOND: "4d_diamond",
               KIND_3D_DIAMOND: "3d_diamond", KIND_2D_DS_SLAB: "2d_ds_slab"}
 

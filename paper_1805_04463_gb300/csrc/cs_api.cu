@@ -81,6 +81,7 @@ size_t cs_sprinkle_workspace_bytes(int kind, int64_t n) {
 
 int cs_sprinkle(int kind, int64_t n, uint64_t seed, int32_t* coords_dev, void* workspace_dev, size_t workspace_bytes,
                 void* stream) {
+    CS_TRACE("cs_sprinkle");
     if (cs_dim(kind) == 0 || !valid_n(n) || !coords_dev || !aligned(coords_dev, 4) || !workspace_dev ||
         !aligned(workspace_dev, 256))
         return CS_EINVAL;
@@ -93,6 +94,7 @@ int cs_sprinkle(int kind, int64_t n, uint64_t seed, int32_t* coords_dev, void* w
 
 int cs_causal_matrix(int kind, int64_t n, const int32_t* coords_dev, uint64_t* bits_dev, int64_t row_words,
                      void* stream) {
+    CS_TRACE("cs_causal_matrix");
     if (cs_dim(kind) == 0 || !valid_n(n) || !coords_dev || !bits_dev || !aligned(bits_dev, 16) ||
         row_words < cs_row_words(n) || row_words % 16 != 0)
         return CS_EINVAL;
@@ -136,6 +138,7 @@ size_t cs_interval_abundance_workspace(int64_t n, int path) {
 
 int cs_interval_abundance(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_t* hist_dev, int path,
                           void* workspace_dev, size_t workspace_bytes, void* stream) {
+    CS_TRACE("cs_interval_abundance");
     if (!valid_n(n) || !bits_dev || !aligned(bits_dev, 128) || !hist_dev || !aligned(hist_dev, 8) ||
         row_words < cs_row_words(n) || row_words % 16 != 0 || !workspace_dev || !aligned(workspace_dev, 256) ||
         path < CS_PATH_AUTO || path > CS_PATH_MMA)
@@ -155,6 +158,7 @@ int cs_interval_abundance(int64_t n, const uint64_t* bits_dev, int64_t row_words
 int cs_layer_sums(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_t* hist_dev, int path,
                   const double* phi_dev, int kmax, double* layer_dev, void* workspace_dev, size_t workspace_bytes,
                   void* stream) {
+    CS_TRACE("cs_layer_sums");
     if (!valid_n(n) || !bits_dev || !aligned(bits_dev, 128) || !hist_dev || !aligned(hist_dev, 8) ||
         row_words < cs_row_words(n) || row_words % 16 != 0 || !workspace_dev || !aligned(workspace_dev, 256) ||
         path < CS_PATH_AUTO || path > CS_PATH_MMA || kmax < 0 || kmax > 15 || !layer_dev ||
@@ -175,6 +179,7 @@ int cs_layer_sums(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_
 
 int cs_dalembertian(int dim, int64_t n, const double* phi_dev, const double* layer_dev, int kmax, double ell,
                     double* out_dev, void* stream) {
+    CS_TRACE("cs_dalembertian");
     if (dim < 2 || dim > 4 || !valid_n(n) || !layer_dev || !out_dev || !(ell > 0.0) ||
         kmax < (dim == 4 ? 3 : 2))
         return CS_EINVAL;
@@ -203,6 +208,7 @@ size_t cs_action_workspace_bytes(void) { return action_workspace_bytes(); }
 int cs_action_device(int dim, int64_t n, const int64_t* hist_dev, int64_t len, const double* eps_host, int n_eps,
                      double* out_dev, int64_t* bracket_dev, void* workspace_dev, size_t workspace_bytes,
                      void* stream) {
+    CS_TRACE("cs_action_device");
     if (dim < 2 || dim > 4 || n < 0 || len < 1 || !hist_dev || !eps_host || n_eps < 1 || n_eps > 16 ||
         !out_dev || !workspace_dev || !aligned(workspace_dev, 256))
         return CS_EINVAL;
@@ -215,6 +221,7 @@ int cs_action_device(int dim, int64_t n, const int64_t* hist_dev, int64_t len, c
 
 int cs_evaluate(int kind, int64_t n, uint64_t seed, const int32_t* coords_host, int path, const double* eps_host,
                 int n_eps, int64_t* hist_host, double* actions_host, int64_t* bracket_host, void* stream) {
+    CS_TRACE("cs_evaluate");
     const int dim = cs_dim(kind);
     if (dim == 0 || !valid_n(n) || n_eps < 0 || n_eps > 16 || (n_eps > 0 && (!eps_host || !actions_host)) ||
         path < CS_PATH_AUTO || path > CS_PATH_MMA)

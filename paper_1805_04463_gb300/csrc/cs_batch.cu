@@ -326,6 +326,7 @@ int64_t cs_batch_hist_len(const cs_set_desc* sets, int n_sets) {
 
 int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspace_dev, size_t workspace_bytes,
                     cs_batch** out, void* stream) {
+    CS_TRACE("cs_batch_create");
     if (!out) return CS_EINVAL;
     *out = nullptr;
     if (!batch_valid(sets, n_sets) || path < CS_PATH_AUTO || path > CS_PATH_MMA || !workspace_dev ||
@@ -446,6 +447,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
 
 int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_t* hist_dev, double* actions_dev,
                     int64_t* brackets_dev, void* stream) {
+    CS_TRACE("cs_batch_launch");
     if (!b || !hist_dev || n_eps < 0 || n_eps > kMaxEps || (n_eps > 0 && (!eps_host || !actions_dev)) ||
         (reinterpret_cast<uintptr_t>(hist_dev) % 8) != 0)
         return CS_EINVAL;

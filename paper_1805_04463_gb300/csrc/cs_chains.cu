@@ -394,6 +394,7 @@ extern "C" size_t cs_chain_workspace_bytes(int64_t n) {
 
 extern "C" int cs_longest_chain(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_t i, int64_t j,
                                 int64_t* length, void* workspace_dev, size_t workspace_bytes, void* stream) {
+    CS_TRACE("cs_longest_chain");
     if (!chain_args_ok(n, bits_dev, row_words, workspace_dev) || !length) return CS_EINVAL;
     const bool whole = i < 0 && j < 0;
     if (!whole && (i < 0 || j < 0 || i >= n || j >= n)) return CS_EINVAL;
@@ -464,6 +465,7 @@ extern "C" int cs_longest_chain(int64_t n, const uint64_t* bits_dev, int64_t row
 extern "C" int cs_greedy_antichain(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_t seed,
                                    uint64_t* members_dev, int64_t* size, void* workspace_dev, size_t workspace_bytes,
                                    void* stream) {
+    CS_TRACE("cs_greedy_antichain");
     if (!chain_args_ok(n, bits_dev, row_words, workspace_dev) || seed < 0 || seed >= n || !members_dev ||
         (reinterpret_cast<uintptr_t>(members_dev) % 8) != 0 || !size)
         return CS_EINVAL;

@@ -6,6 +6,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/cs.h"
@@ -55,6 +56,16 @@ __device__ __forceinline__ void set_status(WsHeader* h, int code) {
 }
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Tracing: every C-ABI entry point that enqueues GPU work opens an NVTX range
+// named after itself (header-only NVTX; a no-op unless a profiler attaches).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define CS_TRACE(name) ::cs::NvtxRange cs_trace_range_(name)
 
 // --------------------------------------------------------------- PTX glue
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -39,6 +39,7 @@ size_t cs_operands_bytes(int64_t n) {
 
 int cs_prepare_operands(int64_t n, const uint64_t* bits_dev, int64_t row_words, void* operands_dev,
                         size_t operands_bytes, void* stream) {
+    CS_TRACE("cs_prepare_operands");
     if (n < 1 || n > kMaxN || !bits_dev || row_words < cs_row_words(n) || row_words % 16 != 0 || !operands_dev ||
         (reinterpret_cast<uintptr_t>(operands_dev) % 1024) != 0)
         return CS_EINVAL;
@@ -68,6 +69,7 @@ size_t cs_count_jobs_workspace_bytes(int n_jobs, int path) {
 
 int cs_count_jobs(const cs_count_job* jobs, int n_jobs, int path, void* table_host, void* workspace_dev,
                   size_t workspace_bytes, void* stream) {
+    CS_TRACE("cs_count_jobs");
     if (!jobs || n_jobs < 1 || path < CS_PATH_AUTO || path > CS_PATH_MMA || !table_host || !workspace_dev ||
         (reinterpret_cast<uintptr_t>(workspace_dev) % 256) != 0 || (reinterpret_cast<uintptr_t>(table_host) % 128) != 0)
         return CS_EINVAL;

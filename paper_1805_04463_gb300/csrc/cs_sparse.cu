@@ -222,6 +222,7 @@ using namespace cs;
 
 extern "C" int cs_degrees(int64_t n, const uint64_t* bits_dev, int64_t row_words, int32_t* in_dev, int32_t* out_dev,
                           void* stream) {
+    CS_TRACE("cs_degrees");
     if (!bits_ok(n, bits_dev, row_words) || (!in_dev && !out_dev)) return CS_EINVAL;
     k_degrees<<<row_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(bits_dev, n, row_words, in_dev, out_dev);
     return cudaGetLastError() == cudaSuccess ? CS_OK : CS_ECUDA;
@@ -234,6 +235,7 @@ extern "C" size_t cs_sparse_workspace_bytes(int64_t n) {
 
 extern "C" int cs_sparse_offsets(int64_t n, const uint64_t* bits_dev, int64_t row_words, int direction,
                                  int64_t* offsets_dev, void* workspace_dev, size_t workspace_bytes, void* stream) {
+    CS_TRACE("cs_sparse_offsets");
     if (!bits_ok(n, bits_dev, row_words) || (direction != 0 && direction != 1) || !offsets_dev ||
         (reinterpret_cast<uintptr_t>(offsets_dev) % 8) != 0 || !workspace_dev ||
         (reinterpret_cast<uintptr_t>(workspace_dev) % 256) != 0)
@@ -259,6 +261,7 @@ extern "C" int cs_sparse_offsets(int64_t n, const uint64_t* bits_dev, int64_t ro
 extern "C" int cs_sparse_columns(int64_t n, const uint64_t* bits_dev, int64_t row_words, int direction,
                                  const int64_t* offsets_dev, int32_t* cols_dev, int64_t cols_capacity,
                                  void* workspace_dev, size_t workspace_bytes, void* stream) {
+    CS_TRACE("cs_sparse_columns");
     if (!bits_ok(n, bits_dev, row_words) || (direction != 0 && direction != 1) || !offsets_dev ||
         (reinterpret_cast<uintptr_t>(offsets_dev) % 8) != 0 || cols_capacity < 0 || (cols_capacity > 0 && !cols_dev) ||
         !workspace_dev || (reinterpret_cast<uintptr_t>(workspace_dev) % 256) != 0 || workspace_bytes < sizeof(WsHeader))

@@ -61,6 +61,7 @@ cudaError_t scratch_for_current_device(void** out) {
 using namespace cs;
 
 extern "C" int cs_sprinkle_noalloc(int kind, int64_t n, uint64_t seed, int32_t* coords_dev, void* stream) {
+    CS_TRACE("cs_sprinkle_noalloc");
     if (cs_dim(kind) == 0 || n < 1 || n > CS_SPRINKLE_NOALLOC_MAX_N || !coords_dev ||
         (reinterpret_cast<uintptr_t>(coords_dev) % 4) != 0)
         return CS_EINVAL;

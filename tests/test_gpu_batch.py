@@ -99,3 +99,18 @@ def test_ensemble_workload_sample(cs, oracle):
     b.launch(EPS)
     torch.cuda.synchronize()
     _check_against_oracle(cs, oracle, b)
+
+
+def test_ensemble_driver_resumes_on_the_gpu(cs, oracle, tmp_path):
+    from paper_1805_04463_gb300 import ensemble
+    sets = [(1, 700 + 13 * s, 3100 + s) for s in range(5)] + [(4, 900, 3200), (0, 9000, 3300)]
+    out = tmp_path / "ens.jsonl"
+    first = ensemble.run(sets[:3], str(out), eps=(0.0, 0.1), chunk=2)
+    recs = ensemble.run(sets, str(out), eps=(0.0, 0.1), chunk=2)   # resumes: only the last four run
+    assert recs[:3] == first
+    for (kind, n, seed), r in zip(sets, recs):
+        c = oracle.sprinkle(kind, n, seed)
+        want = oracle.interval_abundance(oracle.causal_matrix(kind, c))
+        assert r["pairs"] == int(want.sum()) and r["hist_head"] == want[:64].tolist()
+        s_or, br = oracle.action(oracle.dim(kind), n, want, 0.1)
+        assert r["bracket"] == br and abs(r["actions"]["0.1"] - s_or) <= 1e-12 * max(1.0, abs(s_or))
