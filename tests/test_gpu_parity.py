@@ -226,3 +226,33 @@ def test_full_2d_order_131072(cs, oracle, path):
         want[:packed.size // 8] = packed.view(np.uint64)
         assert (bits[i] == want).all(), i
     assert (h == h_dom).all()
+
+
+def test_largest_set_262144_mma(cs, oracle):
+    # n = 2^18, the largest 2D order whose tensor-core operands (137 GB) fit
+    # beside its bitset on one GPU: the total and the first moment of N_k from
+    # the coordinates (sum_k N_k = R, sum_k k N_k = chains of three), sampled
+    # bitset rows from the definition, and a full chain at this size, whose
+    # counts run up to n - 2 = 262142.
+    import torch
+    n, seed = 1 << 18, 0xC5E70007
+    b = _run(cs, 0, n, seed, path=2)
+    c = oracle.sprinkle(0, n, seed)
+    assert (b.coords.cpu().numpy() == c).all()
+    v = c[1].astype(np.int64)
+    past = _past_counts(v)
+    future = (n - 1 - v) - (np.arange(n) - past)
+    h = b.hist.cpu().numpy()
+    assert int(h.sum()) == int(past.sum())
+    assert int((np.arange(h.size) * h).sum()) == int((past * future).sum())
+    bits = b.bits.cpu().numpy().view(np.uint64)
+    idx = np.arange(n)
+    for i in range(0, n, 8191):
+        rel = ((v > v[i]) & (idx > i)) | ((v < v[i]) & (idx < i))
+        packed = np.packbits(rel.astype(np.uint8), bitorder="little").view(np.uint64)
+        assert (bits[i, :packed.size] == packed).all() and not bits[i, packed.size:].any(), i
+    del b, bits
+    torch.cuda.empty_cache()
+    chain = np.stack([np.arange(n), np.arange(n)]).astype(np.int32)
+    hc = _run(cs, 0, n, 0, coords=chain, path=2).hist.cpu().numpy()
+    assert (hc == np.arange(n - 1, 0, -1)).all()
