@@ -333,9 +333,17 @@ def cpu_baseline(kind, n, seed, target_s=15.0, max_rows=None):
     h, threads = oracle.interval_abundance_threads(bits, rows=(0, n, step))
     dt = time.perf_counter() - t0
     pairs = int(np.asarray(h).sum())
+    # one thread on a smaller sample of the same rows (about target_s / 4)
+    step1 = max(1, int(step * max(1.0, threads / 4.0)))
+    t0 = time.perf_counter()
+    h1, _ = oracle.interval_abundance_threads(bits, threads=1, rows=(0, n, step1))
+    dt1 = max(time.perf_counter() - t0, 1e-9)
+    pairs1 = int(np.asarray(h1).sum())
     return {"value": pairs / dt / 1e9, "unit": "Gpairs/s", "cores": threads, "kind": "oracle",
             "sample": f"rows i = 0, {step}, {2 * step}, ... of the same set ({len(range(0, n, step))} of {n} rows, "
-                      f"{pairs} related pairs, {dt:.1f} s)", "seconds": dt, "pairs": pairs}
+                      f"{pairs} related pairs, {dt:.1f} s)", "seconds": dt, "pairs": pairs,
+            "single_thread": {"value": pairs1 / dt1 / 1e9, "unit": "Gpairs/s",
+                              "sample": f"every {step1}th row ({pairs1} related pairs, {dt1:.1f} s)"}}
 
 
 def run_reference(args):
@@ -537,7 +545,7 @@ def main():
         line["serving"] = serving_bench(PATHS[args.path])
     if not args.no_cpu_baseline:
         cb = cpu_baseline(kind, n, seed0)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "single_thread")}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
