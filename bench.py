@@ -333,8 +333,8 @@ def cpu_baseline(kind, n, seed, target_s=15.0, max_rows=None):
     h, threads = oracle.interval_abundance_threads(bits, rows=(0, n, step))
     dt = time.perf_counter() - t0
     pairs = int(np.asarray(h).sum())
-    # one thread on a smaller sample of the same rows (about target_s / 4)
-    step1 = max(1, int(step * max(1.0, threads / 4.0)))
+    # one thread on a sample of the same rows sized to about half the time
+    step1 = max(1, int(step * max(1.0, 2.0 * threads)))
     t0 = time.perf_counter()
     h1, _ = oracle.interval_abundance_threads(bits, threads=1, rows=(0, n, step1))
     dt1 = max(time.perf_counter() - t0, 1e-9)
