@@ -521,7 +521,10 @@ def main():
     line = {
         "metric": f"interval-count Gpairs/s ({desc})", "value": value, "unit": "Gpairs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        # the count's arithmetic: 0/1 E4M3 products summed in FP32 on the tensor path,
+        # AND + popcount on 64-bit words on the POPC path
+        "dtype": "fp8e4m3" if cs.resolved_path(n, path) == 2 else "u64", "data": "synthetic",
         "config": {"workload": args.workload, "kind": cs.KIND_NAMES[kind], "n": n, "seed": seed0,
                    "path": args.path, "resolved_path": {1: "popc", 2: "mma"}[cs.resolved_path(n, path)],
                    "eps": list(EPS),
