@@ -130,7 +130,7 @@ __device__ __forceinline__ void relate_rows_cone_diag(const int32_t* __restrict_
 }
 
 template <bool USE_U>
-__device__ __forceinline__ bool relate_cone_block(const int32_t* __restrict__ coords, int64_t n,
+__device__ __forceinline__ void relate_cone_block(const int32_t* __restrict__ coords, int64_t n,
                                                   uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
                                                   int64_t c0, int64_t r0, int64_t r1,
                                                   const int32_t (*sc)[kRelColsPerBlock]) {
@@ -139,14 +139,11 @@ __device__ __forceinline__ bool relate_cone_block(const int32_t* __restrict__ co
             relate_rows_cone<true, false, USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
         else
             relate_rows_cone<true, true, USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
-        return true;
-    }
-    if (c0 + kRelColsPerBlock <= r0) {  // every column before every row (never past n)
+    } else if (c0 + kRelColsPerBlock <= r0) {  // every column before every row (never past n)
         relate_rows_cone<false, false, USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
-        return true;
+    } else {
+        relate_rows_cone_diag<USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
     }
-    relate_rows_cone_diag<USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
-    return true;
 }
 
 // Rows [rb*64, rb*64+64) x words [cg*32, cg*32+32) of the bitset.  Column
@@ -172,26 +169,28 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = rb * kRelRowsPerBlock;
     const int64_t r1 = r0 + kRelRowsPerBlock < n ? r0 + kRelRowsPerBlock : n;
-    if constexpr (G == kGeomLightCone) {
-        if (order2d ? relate_cone_block<false>(coords, n, bits, row_words, w0, c0, r0, r1, sc)
-                    : relate_cone_block<true>(coords, n, bits, row_words, w0, c0, r0, r1, sc))
-            return;
-    }
-    for (int64_t i = r0 + warp; i < r1; i += kRelThreads / 32) {
-        int32_t ci[DIM];
+    if constexpr (G == kGeomLightCone) {  // time order: one cone per word, see above
+        if (order2d)
+            relate_cone_block<false>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
+        else
+            relate_cone_block<true>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
+    } else {
+        for (int64_t i = r0 + warp; i < r1; i += kRelThreads / 32) {
+            int32_t ci[DIM];
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) ci[d] = coords[d * n + i];
-        uint64_t mine = 0;
+            for (int d = 0; d < DIM; ++d) ci[d] = coords[d * n + i];
+            uint64_t mine = 0;
 #pragma unroll 4
-        for (int w = 0; w < kRelWordsPerBlock; ++w) {
-            const int col = w * 64 + lane;
-            const bool b0 = c0 + col < n && rel_related<G>(ci, sc, col);
-            const bool b1 = c0 + col + 32 < n && rel_related<G>(ci, sc, col + 32);
-            const uint32_t lo = __ballot_sync(0xffffffffu, b0);
-            const uint32_t hi = __ballot_sync(0xffffffffu, b1);
-            if (lane == w) mine = (uint64_t(hi) << 32) | lo;
+            for (int w = 0; w < kRelWordsPerBlock; ++w) {
+                const int col = w * 64 + lane;
+                const bool b0 = c0 + col < n && rel_related<G>(ci, sc, col);
+                const bool b1 = c0 + col + 32 < n && rel_related<G>(ci, sc, col + 32);
+                const uint32_t lo = __ballot_sync(0xffffffffu, b0);
+                const uint32_t hi = __ballot_sync(0xffffffffu, b1);
+                if (lane == w) mine = (uint64_t(hi) << 32) | lo;
+            }
+            if (w0 + lane < row_words) bits[i * row_words + w0 + lane] = mine;
         }
-        if (w0 + lane < row_words) bits[i * row_words + w0 + lane] = mine;
     }
 }
 
