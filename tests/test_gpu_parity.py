@@ -256,3 +256,29 @@ def test_largest_set_262144_mma(cs, oracle):
     chain = np.stack([np.arange(n), np.arange(n)]).astype(np.int32)
     hc = _run(cs, 0, n, 0, coords=chain, path=2).hist.cpu().numpy()
     assert (hc == np.arange(n - 1, 0, -1)).all()
+
+
+@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+def test_random_kinds_and_sizes(cs, oracle, path):
+    # 40 seeded random (kind, n) pairs, n from 1 to 3000: coordinates,
+    # bitsets, every N_k and the actions against the oracle.
+    import torch
+    rng = np.random.default_rng(20261203 + path)
+    for t in range(40):
+        kind = int(rng.integers(0, 5))
+        n = int(rng.integers(1, 3001))
+        seed = int(rng.integers(0, 2 ** 62))
+        b = _run(cs, kind, n, seed, path=path)
+        c = oracle.sprinkle(kind, n, seed)
+        assert (b.coords.cpu().numpy() == c).all(), (kind, n, seed)
+        bits = oracle.causal_matrix(kind, c)
+        assert (_np_bits(b) == bits).all(), (kind, n, seed)
+        want = oracle.interval_abundance(bits)
+        assert (b.hist.cpu().numpy() == want).all(), (kind, n, seed)
+        d = cs.dim(kind)
+        cs.action_device(d, n, b.hist, list(EPS), b.actions, b.bracket, b.workspace)
+        torch.cuda.synchronize()
+        acts = b.actions.cpu().numpy()
+        for e, eps in enumerate(EPS):
+            s_or, _ = oracle.action(d, n, want, eps)
+            assert abs(acts[e] - s_or) <= TOL * max(1.0, abs(s_or)), (kind, n, seed, eps)
