@@ -38,10 +38,11 @@ struct ChainState {
     unsigned int bar_count, bar_gen;
     unsigned long long left2[2];
     unsigned long long best2[2];
+    unsigned int rcount[2];   // antichain: candidates removed this round (list length)
 };
 
 struct ChainLayout {
-    size_t state, s, m, total;
+    size_t state, s, m, over, rlist, total;
 };
 
 ChainLayout chain_layout(int64_t row_words) {
@@ -53,6 +54,10 @@ ChainLayout chain_layout(int64_t row_words) {
     off = align_up(off + size_t(row_words) * 8, 256);
     L.m = off;
     off = align_up(off + size_t(row_words) * 8, 256);
+    L.over = off;  // antichain: overlap |A & J(j)| of every candidate j
+    off = align_up(off + size_t(row_words) * 64 * 4, 256);
+    L.rlist = off;  // antichain: the candidates removed in a round
+    off = align_up(off + size_t(row_words) * 64 * 4, 256);
     L.total = off;
     return L;
 }
@@ -310,45 +315,85 @@ __global__ void __launch_bounds__(256) k_chain_persist(const uint64_t* __restric
     }
 }
 
-// All greedy rounds: score into best2[r & 1], barrier, apply the best, count
-// the candidates left, barrier, stop when none are left.
+// All greedy rounds, with incremental scores.  Maximising c_j = |A - J(j)|
+// is minimising the overlap o_j = |A & J(j)|.  When k is taken, A loses
+// R = A & J(k), which are exactly the candidates related to k (the members
+// are unrelated to every candidate), so every remaining o_j drops by the
+// number of R's elements related to j.  Per round: the smallest (o_j, j) by
+// one 64-bit atomicMin, barrier; remove J(k) from A and J(k) + {k} from X
+// and list R, barrier; stop if X is empty; subtract R's contributions from
+// the o_j of the remaining candidates (a thread per column, the list read
+// in step), barrier.  The overlaps are computed in full once, at the start.
 __global__ void __launch_bounds__(256) k_anti_persist(const uint64_t* __restrict__ bits, int64_t n,
                                                       int64_t row_words, int64_t max_rounds, uint64_t* A,
-                                                      uint64_t* X, ChainState* st, WsHeader* hdr) {
+                                                      uint64_t* X, int32_t* over, int32_t* rlist, ChainState* st,
+                                                      WsHeader* hdr) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (n + 63) >> 6;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
     const int64_t gwarp = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t gthread = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t nthreads = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t r = 0; r < max_rounds; ++r) {
-        for (int64_t k = gwarp; k < n; k += warps) {
-            if (!bit_of(X, k)) continue;  // warp-uniform
-            int c = 0;
-            for (int64_t w = lane; w < nw; w += 32) c += __popcll(A[w] & ~__ldg(bits + k * row_words + w));
+    for (int64_t k = gwarp; k < n; k += warps) {  // o_j for every candidate, once
+        if (!bit_of(X, k)) continue;               // warp-uniform
+        int c = 0;
+        for (int64_t w = lane; w < nw; w += 32) c += __popcll(A[w] & __ldg(bits + k * row_words + w));
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-            if (lane == 0)
-                atomicMax(&st->best2[r & 1], (static_cast<unsigned long long>(c) << 32) | (0xFFFFFFFFull - uint64_t(k)));
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) over[k] = c;
+    }
+    if (!grid_barrier(st, gridDim.x, hdr)) return;
+    for (int64_t r = 0; r < max_rounds; ++r) {
+        // the candidate with the smallest overlap, the smallest label on ties
+        unsigned long long mine = ~0ull;
+        for (int64_t j = gthread; j < n; j += nthreads)
+            if (bit_of(X, j)) {
+                const unsigned long long key = (static_cast<unsigned long long>(over[j]) << 32) | uint64_t(j);
+                mine = key < mine ? key : mine;
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, mine, o);
+            mine = y < mine ? y : mine;
         }
-        if (gthread == 0) st->best2[(r + 1) & 1] = 0ull;  // last read before the previous barrier
+        if (lane == 0 && mine != ~0ull) atomicMin(&st->best2[r & 1], mine);
+        if (gthread == 0) {
+            st->best2[(r + 1) & 1] = ~0ull;  // last read before the previous round's second barrier
+            st->rcount[(r + 1) & 1] = 0u;
+            st->left2[(r + 1) & 1] = 0ull;
+        }
         if (!grid_barrier(st, gridDim.x, hdr)) return;
         const unsigned long long best = *reinterpret_cast<volatile unsigned long long*>(&st->best2[r & 1]);
-        if (best == 0ull) return;  // no candidates (all blocks see the same value)
-        const int64_t k = int64_t(0xFFFFFFFFull - (best & 0xFFFFFFFFull));
-        unsigned long long mine = 0;
+        if (best == ~0ull) return;  // no candidates (every block sees the same value)
+        const int64_t k = int64_t(best & 0xFFFFFFFFull);
+        unsigned long long left = 0;
         for (int64_t w = gthread; w < row_words; w += nthreads) {
             const uint64_t rk = __ldg(bits + k * row_words + w);
-            uint64_t x = X[w] & ~rk;
-            if (w == (k >> 6)) x &= ~(1ull << (k & 63));
-            X[w] = x;
+            const uint64_t x = X[w];
+            uint64_t removed = x & rk;
+            uint64_t nx = x & ~rk;
+            if (w == (k >> 6)) nx &= ~(1ull << (k & 63));
+            X[w] = nx;
             A[w] &= ~rk;
-            mine += __popcll(x);
+            left += __popcll(nx);
+            if (removed) {
+                unsigned int pos = atomicAdd(&st->rcount[r & 1], unsigned(__popcll(removed)));
+                for (; removed; removed &= removed - 1ull)
+                    rlist[pos++] = int32_t(64 * w + __ffsll(static_cast<long long>(removed)) - 1);
+            }
         }
-        block_sum_to(mine, &st->left2[r & 1]);
-        if (gthread == 0) st->left2[(r + 1) & 1] = 0ull;
+        block_sum_to(left, &st->left2[r & 1]);
         if (!grid_barrier(st, gridDim.x, hdr)) return;
         if (*reinterpret_cast<volatile unsigned long long*>(&st->left2[r & 1]) == 0ull) return;
+        const unsigned int nr = *reinterpret_cast<volatile unsigned int*>(&st->rcount[r & 1]);
+        for (int64_t j = gthread; j < n; j += nthreads) {
+            if (!bit_of(X, j)) continue;
+            int d = 0;
+            for (unsigned int t = 0; t < nr; ++t)
+                d += int((__ldg(bits + int64_t(rlist[t]) * row_words + (j >> 6)) >> (j & 63)) & 1ull);
+            over[j] -= d;
+        }
+        if (!grid_barrier(st, gridDim.x, hdr)) return;
     }
 }
 
@@ -482,12 +527,17 @@ extern "C" int cs_greedy_antichain(int64_t n, const uint64_t* bits_dev, int64_t 
     bool done = false;
     if (cg > 0) {
         WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
-        if (cudaMemsetAsync(&sd->bar_count, 0, sizeof(unsigned int) * 2 + sizeof(unsigned long long) * 4, st) !=
+        int32_t* over = reinterpret_cast<int32_t*>(ws + L.over);
+        int32_t* rlist = reinterpret_cast<int32_t*>(ws + L.rlist);
+        if (cudaMemsetAsync(&sd->bar_count, 0, sizeof(unsigned int) * 2 + sizeof(unsigned long long) * 2, st) !=
                 cudaSuccess ||
+            cudaMemsetAsync(&sd->best2[0], 0xFF, sizeof(unsigned long long), st) != cudaSuccess ||  // no best yet
+            cudaMemsetAsync(&sd->rcount[0], 0, sizeof(unsigned int) * 2, st) != cudaSuccess ||
             cudaMemsetAsync(&hdr->status, 0, sizeof(int32_t), st) != cudaSuccess)
             return CS_ECUDA;
         int64_t max_rounds = n + 1;
-        void* args[] = {const_cast<uint64_t**>(&bits_dev), &n, &row_words, &max_rounds, &members_dev, &X, &sd, &hdr};
+        void* args[] = {const_cast<uint64_t**>(&bits_dev), &n, &row_words, &max_rounds, &members_dev, &X,
+                        &over, &rlist, &sd, &hdr};
         if (cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_anti_persist), dim3(unsigned(cg)), dim3(256),
                                         args, 0, st) == cudaSuccess) {
             int32_t status = 0;
