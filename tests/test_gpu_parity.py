@@ -122,7 +122,7 @@ def test_action_device_and_host(cs, oracle, kind, n):
     assert int(b.bracket.item()) == oracle.action(d, n, h, 0.0)[1]
 
 
-@pytest.mark.parametrize("kind,n", [(0, 1024), (2, 700), (3, 900)])
+@pytest.mark.parametrize("kind,n", [(0, 1024), (2, 700), (3, 900), (4, 800)])
 def test_evaluate_host_buffers(cs, oracle, kind, n):
     seed = 4242
     coords = oracle.sprinkle(kind, n, seed)
