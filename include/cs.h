@@ -398,7 +398,8 @@ int cs_count_jobs(const cs_count_job *jobs, int n_jobs, int path, void *table_ho
  * array of 12 MiB that every GPU loading the library holds until the process
  * exits.  The call allocates nothing (no cudaMalloc, cudaFree or allocating
  * library routine).  The first call on a device looks up the array's device
- * address, so make that first call before any stream capture starts.
+ * address (and, for CS_2D_DS_SLAB, uploads that kind's 1.3 MB constant
+ * table), so make that first call before any stream capture starts.
  * All calls on a device share the array and it keeps the last call's
  * contents; calls whose work overlaps on the GPU (unordered streams) race
  * and may corrupt each other's output.  A 4D element that exhausts its

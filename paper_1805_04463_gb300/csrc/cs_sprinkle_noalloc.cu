@@ -15,10 +15,12 @@
 // zero, and the array keeps the last call's contents afterwards.  Two calls
 // whose work overlaps on the GPU (different streams without ordering between
 // them) race on the array and may corrupt each other's result.  The first
-// call on a device looks up the array's device address; make that first call
+// call on a device looks up the array's device address (and, for the de
+// Sitter slab, uploads that kind's constant table); make that first call
 // before any stream capture begins.  The in-kernel status word (set only if
-// a 4D element exhausts its 16384 rejection attempts, which has probability
-// below 1e-900) lands in the array and is not reported by this entry point.
+// a 3D or 4D element exhausts its 16384 rejection attempts, which has
+// probability below 1e-900) lands in the array and is not reported by this
+// entry point.
 #include <mutex>
 
 #include "cs_kernels.cuh"
