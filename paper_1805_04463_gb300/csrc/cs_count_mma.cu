@@ -52,7 +52,8 @@ constexpr int kEpiChunks = (kBN / 32) / (kEpiWarps / 4);  // 32-column chunks pe
 static_assert(kEpiWarps % 4 == 0 && (kBN / 32) % (kEpiWarps / 4) == 0, "epilogue warps split the columns evenly");
 constexpr int kTmemCols = 512;           // two 256-column FP32 accumulators
 constexpr uint32_t kIdesc = idesc_f8_f32(kBM, kBN);
-constexpr int kRing = 4;                 // item indices in flight between the roles
+constexpr int kRing = 4;                 // items in flight between the roles
+constexpr int kLocalBits = 40;           // ring entry = set << 40 | item within the set; -1 = no more items
 constexpr int kSmemBytes = kStages * kStageBytes + kHistBins * 4 + 256 + 1024;
 constexpr uint8_t kOne = 0x38;           // 1.0 in FP8 E4M3
 constexpr CUtensorMapSwizzle kSwizzle = kBK == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
@@ -204,7 +205,7 @@ struct MmaSingle {
     int64_t nitems;
     __device__ __forceinline__ int64_t total() const { return nitems; }
     __device__ __forceinline__ int64_t chunk() const { return 1; }
-    __device__ __forceinline__ int set_of(int64_t t, int64_t& local) const {
+    __device__ __forceinline__ int set_of(int64_t t, int64_t& local, int) const {
         local = t;
         return 0;
     }
@@ -223,11 +224,23 @@ struct MmaMulti {
     int64_t run;
     __device__ __forceinline__ int64_t total() const { return nitems; }
     __device__ __forceinline__ int64_t chunk() const { return run; }
-    __device__ __forceinline__ int set_of(int64_t t, int64_t& local) const {
-        int lo = 0, hi = nsets - 1;  // last set with item_begin <= t
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sets[mid].item_begin <= t) lo = mid; else hi = mid - 1;
+    // The set holding item t: the hint (the previous item's set) or the next
+    // set when t is still there, else a binary search.
+    __device__ __forceinline__ int set_of(int64_t t, int64_t& local, int hint) const {
+        int lo = -1;
+        if (hint >= 0 && sets[hint].item_begin <= t) {
+            if (hint + 1 == nsets || t < sets[hint + 1].item_begin)
+                lo = hint;
+            else if (hint + 2 == nsets || t < sets[hint + 2].item_begin)
+                lo = hint + 1;
+        }
+        if (lo < 0) {
+            int a = 0, b = nsets - 1;  // last set with item_begin <= t
+            while (a < b) {
+                const int mid = (a + b + 1) >> 1;
+                if (sets[mid].item_begin <= t) a = mid; else b = mid - 1;
+            }
+            lo = a;
         }
         local = t - sets[lo].item_begin + sets[lo].item_offset;
         return lo;
@@ -329,11 +342,16 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 end = next + src.chunk();
             }
             const int64_t t = next++;
-            ring[slot] = t;
-            mbar_arrive(&ifull[slot]);
-            if (t >= total) break;
+            if (t >= total) {
+                ring[slot] = -1;
+                mbar_arrive(&ifull[slot]);
+                break;
+            }
+            // the producer alone finds the item's set and hands it on
             int64_t local;
-            const int sidx = src.set_of(t, local);
+            const int sidx = src.set_of(t, local, cur);
+            ring[slot] = (int64_t(sidx) << kLocalBits) | local;
+            mbar_arrive(&ifull[slot]);
             if (sidx != cur) {
                 cur = sidx;
                 v = src.view(sidx);
@@ -367,11 +385,11 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         for (uint32_t q = 0; ok; ++q) {
             const uint32_t slot = q % kRing, use = (q / kRing) & 1u;
             if (!mbar_wait_or_abort(&ifull[slot], use, hdr, abort_flag)) break;
-            const int64_t t = ring[slot];
+            const int64_t e = ring[slot];
             mbar_arrive(&iempty[slot]);
-            if (t >= total) break;
-            int64_t local;
-            const int sidx = src.set_of(t, local);
+            if (e < 0) break;
+            const int sidx = int(e >> kLocalBits);
+            const int64_t local = e & ((int64_t(1) << kLocalBits) - 1);
             if (sidx != cur) {
                 cur = sidx;
                 v = src.view(sidx);
@@ -410,11 +428,11 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         for (uint32_t qi = 0; ok; ++qi) {
             const uint32_t slot = qi % kRing, ru = (qi / kRing) & 1u;
             if (!mbar_wait_or_abort(&ifull[slot], ru, hdr, abort_flag)) { ok = false; break; }
-            const int64_t t = ring[slot];
+            const int64_t e = ring[slot];
             mbar_arrive(&iempty[slot]);
-            if (t >= total) break;
-            int64_t local;
-            const int sidx = src.set_of(t, local);
+            if (e < 0) break;
+            const int sidx = int(e >> kLocalBits);
+            const int64_t local = e & ((int64_t(1) << kLocalBits) - 1);
             if (sidx != cur) {
                 if (cur >= 0 && !epilogue_flush(shist, v, etid, ebar, ephase, hdr, abort_flag)) { ok = false; break; }
                 cur = sidx;
