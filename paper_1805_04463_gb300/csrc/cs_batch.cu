@@ -22,6 +22,8 @@
 #include <vector>
 
 #include "cs_action.cuh"
+#include <atomic>
+
 #include "cs_kernels.cuh"
 #include "cs_relate.cuh"
 #include "cs_sprinkle.cuh"
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kActThreads) k_batch_action(const BatchSet* __
     }
 }
 
-bool g_rank_attr[64];
+std::atomic<bool> g_rank_attr[64];  // per device: the sort kernel's shared-memory attribute is set
 
 }  // namespace
 

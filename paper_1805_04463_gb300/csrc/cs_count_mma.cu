@@ -30,6 +30,8 @@
 //               (global atomics above 8192), then release the accumulator.
 // The K loop of a tile runs only over the K-blocks between the i-block and the
 // end of the j-block.  C.C is never written to memory.
+#include <atomic>
+
 #include "cs_kernels.cuh"
 
 namespace cs {
@@ -521,8 +523,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     mma_body(src, hdr);
 }
 
-bool g_attr_set[64];
-bool g_attr_multi_set[64];
+std::atomic<bool> g_attr_set[64];  // per device: the large-shared-memory attribute is set
+std::atomic<bool> g_attr_multi_set[64];
 
 struct MmaLayout {
     int64_t kpad;

@@ -23,6 +23,8 @@
 // goes to a 8192-bin shared-memory histogram (global 64-bit atomics above
 // that).  The kernel is persistent: CTAs pull tiles from a queue ordered by
 // decreasing K length (largest first), and flush their shared histogram once.
+#include <atomic>
+
 #include "cs_kernels.cuh"
 
 namespace cs {
@@ -293,8 +295,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     popc_body(src, hdr);
 }
 
-bool g_attr_set[64];
-bool g_attr_multi_set[64];
+std::atomic<bool> g_attr_set[64];  // per device: the large-shared-memory attribute is set
+std::atomic<bool> g_attr_multi_set[64];
 
 }  // namespace
 
