@@ -46,6 +46,8 @@ struct BatchSet {
     int64_t elem_begin;    // first element of this set in the concatenated element range
     int64_t rblock_begin;  // first relate block
     int64_t col_groups;    // relate column groups per row block
+    int64_t mblock_begin;  // first mirror block (lower part by symmetry)
+    int64_t mir_side;      // mirror super-tiles per side
     int64_t hist_off;      // offset of this set's histogram in the batch histogram
 };
 
@@ -169,6 +171,16 @@ __global__ void __launch_bounds__(kRelThreads) k_batch_relate(const BatchSet* __
     }
 }
 
+// One block per mirror super-tile of one set (the lower part of its bitset
+// as the transpose of the upper part), the set read from a table.
+__global__ void __launch_bounds__(kRelThreads) k_batch_mirror(const BatchSet* __restrict__ sets,
+                                                              const int32_t* __restrict__ mblock_set) {
+    __shared__ uint64_t sm[kMirRows][kMirTiles + 1];
+    const BatchSet& b = sets[mblock_set[blockIdx.x]];
+    const int64_t local = int64_t(blockIdx.x) - b.mblock_begin;
+    mirror_block(b.bits, b.n, b.row_words, local / b.mir_side, local % b.mir_side, sm);
+}
+
 // One CTA per set: bracket, local and smeared actions.  Powers of (1-eps)
 // advance by a fixed stride per thread after a direct start.
 __global__ void __launch_bounds__(kActThreads) k_batch_action(const BatchSet* __restrict__ sets,
@@ -247,6 +259,8 @@ struct cs_batch {
     int64_t total_elems = 0, total_rblocks = 0, total_items = 0, total_chunks = 0, total_hist = 0;
     int32_t* rtab = nullptr;  // relate block -> set
     int32_t* etab = nullptr;  // expansion chunk -> count-table entry
+    int32_t* mtab = nullptr;  // mirror block -> set
+    int64_t total_mblocks = 0;
     int max_pow2 = 1;
     const uint64_t* ds_thr = nullptr;  // de Sitter thresholds, when a set needs them
 };
@@ -254,7 +268,7 @@ struct cs_batch {
 namespace {
 
 struct Layout {
-    size_t sets, entries, rtab, etab, total;
+    size_t sets, entries, rtab, etab, mtab, total;
     std::vector<size_t> coords, bits, key0, key1, raw, U, L;
 };
 
@@ -282,15 +296,18 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
     L.sets = take(sizeof(BatchSet) * size_t(n_sets));
     off = align_up(off, 128);
     L.entries = take((path == CS_PATH_MMA ? sizeof(MmaSetEntry) : sizeof(PopcSetEntry)) * size_t(n_sets));
-    int64_t rblocks = 0, chunks = 0;
+    int64_t rblocks = 0, chunks = 0, mblocks = 0;
     for (int s = 0; s < n_sets; ++s) {
         const int64_t n = sets[s].n;
         rblocks += ((n + kRelRowsPerBlock - 1) / kRelRowsPerBlock) *
                    ((cs_row_words(n) + kRelWordsPerBlock - 1) / kRelWordsPerBlock);
+        const int64_t side = ((n + 63) / 64 + kMirTiles - 1) / kMirTiles;
+        mblocks += side * side;
         if (path == CS_PATH_MMA) chunks += mma_expand_chunks(n);
     }
     L.rtab = take(size_t(rblocks) * 4);  // relate block -> set
     L.etab = take(size_t(chunks) * 4);   // expansion chunk -> set
+    L.mtab = take(size_t(mblocks) * 4);  // mirror block -> set
     for (int s = 0; s < n_sets; ++s) {
         const int64_t n = sets[s].n;
         const int dim = cs_dim(sets[s].kind);
@@ -345,7 +362,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     uint8_t* ws = static_cast<uint8_t*>(workspace_dev);
 
     std::vector<BatchSet> bs(static_cast<size_t>(n_sets));
-    int64_t elem = 0, rblk = 0, hoff = 0;
+    int64_t elem = 0, rblk = 0, mblk = 0, hoff = 0;
     int max_pow2 = 1;
     for (int s = 0; s < n_sets; ++s) {
         BatchSet& b = bs[s];
@@ -364,6 +381,9 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
         b.col_groups = (b.row_words + kRelWordsPerBlock - 1) / kRelWordsPerBlock;
         b.rblock_begin = rblk;
         rblk += ((b.n + kRelRowsPerBlock - 1) / kRelRowsPerBlock) * b.col_groups;
+        b.mir_side = ((b.n + 63) / 64 + kMirTiles - 1) / kMirTiles;
+        b.mblock_begin = mblk;
+        mblk += b.mir_side * b.mir_side;
         b.hist_off = hoff;
         hoff += cs_hist_len(b.n);
         while (max_pow2 < b.n) max_pow2 <<= 1;
@@ -373,7 +393,10 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bs[a].n > bs[b].n; });
     int64_t items = 0, chunks = 0;
-    std::vector<int32_t> rtab(static_cast<size_t>(rblk)), etab;
+    std::vector<int32_t> rtab(static_cast<size_t>(rblk)), etab, mtab(static_cast<size_t>(mblk));
+    for (int s = 0; s < n_sets; ++s)
+        std::fill(mtab.begin() + bs[s].mblock_begin, mtab.begin() + bs[s].mblock_begin + bs[s].mir_side * bs[s].mir_side,
+                  int32_t(s));
     for (int s = 0; s < n_sets; ++s)
         std::fill(rtab.begin() + bs[s].rblock_begin,
                   rtab.begin() + bs[s].rblock_begin +
@@ -420,6 +443,8 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     h->total_items = items;
     h->total_chunks = chunks;
     h->rtab = reinterpret_cast<int32_t*>(ws + L.rtab);
+    h->mtab = reinterpret_cast<int32_t*>(ws + L.mtab);
+    h->total_mblocks = mblk;
     h->etab = reinterpret_cast<int32_t*>(ws + L.etab);
     h->total_hist = hoff;
     h->max_pow2 = max_pow2;
@@ -427,6 +452,8 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     cudaError_t e = cudaMemcpyAsync(h->sets_dev, bs.data(), sizeof(BatchSet) * bs.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !rtab.empty())
         e = cudaMemcpyAsync(h->rtab, rtab.data(), rtab.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !mtab.empty())
+        e = cudaMemcpyAsync(h->mtab, mtab.data(), mtab.size() * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !etab.empty())
         e = cudaMemcpyAsync(h->etab, etab.data(), etab.size() * 4, cudaMemcpyHostToDevice, st);
     if (p == CS_PATH_MMA) {
@@ -483,6 +510,8 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
 
     if (b->total_rblocks > int64_t(0x7fffffff)) return CS_EINVAL;
     k_batch_relate<<<unsigned(b->total_rblocks), kRelThreads, 0, st>>>(b->sets_dev, b->rtab);
+    if (b->total_mblocks > int64_t(0x7fffffff)) return CS_EINVAL;
+    k_batch_mirror<<<unsigned(b->total_mblocks), kRelThreads, 0, st>>>(b->sets_dev, b->mtab);
     if ((err = cudaGetLastError()) != cudaSuccess) return CS_ECUDA;
 
     if (b->path == CS_PATH_MMA) {

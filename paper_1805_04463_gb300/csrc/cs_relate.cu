@@ -5,8 +5,9 @@
 // A block owns 2048 columns (32 words) and 64 rows (relate_block): column
 // coordinates are staged once in shared memory, each warp folds 64 tests per
 // word into a uint64 with two __ballot_sync, and a row's 32 words leave in
-// one coalesced 256-byte store.  The tests are symmetric and exact in int64,
-// so no branch on i < j is needed.
+// one coalesced 256-byte store.  Blocks wholly below the diagonal are not
+// tested: k_mirror fills them as transposes of the blocks above (the
+// relation is symmetric), which halves the tests.
 #include "cs_kernels.cuh"
 #include "cs_relate.cuh"
 
@@ -19,6 +20,11 @@ __global__ void __launch_bounds__(kRelThreads) k_relate(const int32_t* __restric
                                                         uint64_t* __restrict__ bits, int64_t row_words, bool order2d) {
     __shared__ int32_t sc[geom_dim(G)][kRelColsPerBlock];
     relate_block<G>(coords, n, bits, row_words, blockIdx.x, blockIdx.y, sc, order2d);
+}
+
+__global__ void __launch_bounds__(kRelThreads) k_mirror(uint64_t* __restrict__ bits, int64_t n, int64_t row_words) {
+    __shared__ uint64_t sm[kMirRows][kMirTiles + 1];
+    mirror_block(bits, n, row_words, blockIdx.x, blockIdx.y, sm);
 }
 
 }  // namespace
@@ -35,6 +41,8 @@ cudaError_t launch_relate(int kind, int64_t n, const int32_t* coords, uint64_t* 
         k_relate<kGeomDeSitter><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words, false);
     else
         k_relate<kGeomLightCone><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words, kind == CS_2D_ORDER);
+    const int64_t st8 = ((n + 63) / 64 + kMirTiles - 1) / kMirTiles;  // super-tiles per side
+    if (st8 > 0) k_mirror<<<dim3(unsigned(st8), unsigned(st8)), kRelThreads, 0, st>>>(bits, n, row_words);
     return cudaGetLastError();
 }
 

@@ -160,6 +160,9 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
     constexpr int DIM = geom_dim(G);
     const int64_t w0 = cg * kRelWordsPerBlock;
     const int64_t c0 = w0 * 64;
+    // Blocks wholly below the diagonal are left to mirror_block: the relation
+    // is symmetric, so they are the transposes of computed blocks.
+    if (c0 + kRelColsPerBlock <= rb * kRelRowsPerBlock) return;
     for (int t = threadIdx.x; t < kRelColsPerBlock; t += kRelThreads) {
         const int64_t c = c0 + t;
 #pragma unroll
@@ -190,6 +193,87 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
                 if (lane == w) mine = (uint64_t(hi) << 32) | lo;
             }
             if (w0 + lane < row_words) bits[i * row_words + w0 + lane] = mine;
+        }
+    }
+}
+
+// ------------------------------------------------ the lower part by symmetry
+//
+// A relate block wholly below the diagonal (rows [64 rb, 64 rb + 64), words
+// [32 cg, 32 cg + 32), 32 (cg + 1) <= rb) is the transpose of blocks above
+// it.  mirror_block fills one super-tile of 512 output rows x 8 output words
+// (8 x 8 tiles of 64 x 64 bits): the 512 source rows x 8 source words land
+// in shared memory with 64-byte reads, each warp transposes its output row
+// tile's 8 tiles in registers (six butterfly stages, five of them across
+// lanes) and writes 64 contiguous bytes per output row.
+constexpr int kMirTiles = 8;                    // tiles per super-tile side
+constexpr int kMirRows = 64 * kMirTiles;        // 512 source / output rows
+
+__device__ __forceinline__ bool mirror_needed(int64_t A, int64_t B) {  // output row tile A, output word B
+    return (B / kRelWordsPerBlock + 1) * kRelWordsPerBlock <= A;
+}
+
+__device__ __forceinline__ uint64_t tr_step(uint64_t v, int j, uint64_t m, bool low) {
+    const uint64_t p = __shfl_xor_sync(0xffffffffu, v, j);
+    return low ? v ^ ((((v >> j) ^ p) & m) << j) : v ^ (((p >> j) ^ v) & m);
+}
+
+// Transpose the 64 x 64 bit tile whose rows l and l + 32 lane l holds.
+__device__ __forceinline__ void transpose64(uint64_t& x, uint64_t& y) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t t = ((x >> 32) ^ y) & 0x00000000FFFFFFFFull;
+    y ^= t;
+    x ^= t << 32;
+    const uint64_t masks[5] = {0x0000FFFF0000FFFFull, 0x00FF00FF00FF00FFull, 0x0F0F0F0F0F0F0F0Full,
+                               0x3333333333333333ull, 0x5555555555555555ull};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int j = 16 >> s;
+        const bool low = (lane & j) == 0;
+        x = tr_step(x, j, masks[s], low);
+        y = tr_step(y, j, masks[s], low);
+    }
+}
+
+// Super-tile (A8, B8): output rows [512 A8, 512 A8 + 512), output words
+// [8 B8, 8 B8 + 8).  sm: 512 x 9 words of shared memory.  All 256 threads.
+__device__ __forceinline__ void mirror_block(uint64_t* __restrict__ bits, int64_t n, int64_t row_words, int64_t A8,
+                                             int64_t B8, uint64_t (*sm)[kMirTiles + 1]) {
+    const int64_t tiles = (n + 63) >> 6;  // row tiles = valid words
+    const int64_t A0 = A8 * kMirTiles, B0 = B8 * kMirTiles;
+    // anything to do here? (uniform)
+    if (!mirror_needed(A0 + kMirTiles - 1 < tiles ? A0 + kMirTiles - 1 : tiles - 1, B0) || A0 >= tiles) return;
+    // source rows 64 B0 .. + 512, source words A0 .. A0 + 8
+    for (int t = threadIdx.x; t < kMirRows * kMirTiles; t += blockDim.x) {
+        const int r = t / kMirTiles, w = t % kMirTiles;
+        const int64_t row = 64 * B0 + r, word = A0 + w;
+        sm[r][w] = (row < n && word < tiles) ? bits[row * row_words + word] : 0ull;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t A = A0 + warp;  // this warp's output row tile
+    if (A < tiles && mirror_needed(A, B0)) {
+        uint64_t ox[kMirTiles], oy[kMirTiles];
+#pragma unroll
+        for (int qb = 0; qb < kMirTiles; ++qb) {
+            uint64_t x = sm[64 * qb + lane][warp], y = sm[64 * qb + lane + 32][warp];
+            transpose64(x, y);
+            ox[qb] = x;
+            oy[qb] = y;
+        }
+        const int64_t rx = 64 * A + lane, ry = rx + 32;
+        // (a needed tile's 8 words all lie below the diagonal, so inside the
+        // row; 64 contiguous bytes per row as four 16-byte stores)
+        uint4* px = reinterpret_cast<uint4*>(bits + rx * row_words + B0);
+        uint4* py = reinterpret_cast<uint4*>(bits + ry * row_words + B0);
+#pragma unroll
+        for (int h = 0; h < kMirTiles / 2; ++h) {
+            if (rx < n)
+                px[h] = make_uint4(uint32_t(ox[2 * h]), uint32_t(ox[2 * h] >> 32), uint32_t(ox[2 * h + 1]),
+                                   uint32_t(ox[2 * h + 1] >> 32));
+            if (ry < n)
+                py[h] = make_uint4(uint32_t(oy[2 * h]), uint32_t(oy[2 * h] >> 32), uint32_t(oy[2 * h + 1]),
+                                   uint32_t(oy[2 * h + 1] >> 32));
         }
     }
 }
