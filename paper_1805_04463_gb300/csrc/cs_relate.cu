@@ -5,8 +5,8 @@
 // A block owns 2048 columns (32 words) and 64 rows (relate_block): column
 // coordinates are staged once in shared memory, each warp folds 64 tests per
 // word into a uint64 with two __ballot_sync, and a row's 32 words leave in
-// one coalesced 256-byte store.  Blocks wholly below the diagonal are not
-// tested: k_mirror fills them as transposes of the blocks above (the
+// one coalesced 256-byte store.  64 x 64 tiles wholly below the diagonal
+// are not tested: k_mirror fills them as transposes of the tiles above (the
 // relation is symmetric), which halves the tests.
 #include "cs_kernels.cuh"
 #include "cs_relate.cuh"

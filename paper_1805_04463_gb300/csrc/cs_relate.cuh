@@ -46,37 +46,49 @@ __device__ __forceinline__ bool rel_related(const int32_t (&ci)[geom_dim(G)], co
     }
 }
 
-// Light-cone kinds, a block that lies wholly above (UPPER) or below the
-// diagonal.  Labels are in time order, so above the diagonal only the future
-// cone can hold (u_j > u_i and v_j > v_i) and below it only the past cone;
-// for a random 2D order labelled by u the u test is implied by j > i and only
-// v is compared (USE_U = false).  Each warp handles two rows at a time, so
-// every staged coordinate feeds four tests.
-template <bool UPPER, bool CHECK, bool USE_U>
+// Light-cone kinds.  Labels are in time order, so in a word wholly after
+// the row tile only the future cone can hold (u_j > u_i and v_j > v_i); for
+// a random 2D order labelled by u the u test is implied by j > i and only v
+// is compared (USE_U = false).  Words before the row tile are left to
+// mirror_block; word `ws` (the row tile's own word, when the block holds it)
+// takes the full test.  Each warp handles two rows at a time, so every
+// staged coordinate feeds four tests.
+template <bool CHECK, bool USE_U>
 __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coords, int64_t n,
                                                  uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
-                                                 int64_t c0, int64_t r0, int64_t r1,
+                                                 int64_t c0, int64_t r0, int64_t r1, int ws,
                                                  const int32_t (*sc)[kRelColsPerBlock]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kWarps = kRelThreads / 32;
-    auto cone = [](int32_t xu, int32_t xv, int32_t cu, int32_t cv) {
-        const bool bv = UPPER ? xv > cv : xv < cv;
-        if constexpr (USE_U) return bv && (UPPER ? xu > cu : xu < cu);
-        else return bv;
+    auto future = [](int32_t xu, int32_t xv, int32_t cu, int32_t cv) {
+        if constexpr (USE_U) return xv > cv && xu > cu;
+        else return xv > cv;
     };
+    auto full = [](int32_t xu, int32_t xv, int32_t cu, int32_t cv) {
+        const int32_t du = xu - cu, dv = xv - cv;
+        return (du ^ dv) >= 0 && du != 0 && dv != 0;
+    };
+    const int wbeg = ws > 0 ? ws : 0;
     for (int64_t i = r0 + warp; i < r1; i += 2 * kWarps) {
         const int64_t i2 = i + kWarps;
         const bool has2 = i2 < r1;
-        const int32_t ua = USE_U ? coords[i] : 0, va = coords[n + i];
-        const int32_t ub = USE_U && has2 ? coords[i2] : 0, vb = has2 ? coords[n + i2] : 0;
+        const int32_t ua = coords[i], va = coords[n + i];
+        const int32_t ub = has2 ? coords[i2] : 0, vb = has2 ? coords[n + i2] : 0;
         uint64_t mine_a = 0, mine_b = 0;
 #pragma unroll 8
-        for (int w = 0; w < kRelWordsPerBlock; ++w) {
+        for (int w = wbeg; w < kRelWordsPerBlock; ++w) {
             const int col = w * 64 + lane;
             const int32_t v0 = sc[1][col], v1 = sc[1][col + 32];
-            const int32_t u0 = USE_U ? sc[0][col] : 0, u1 = USE_U ? sc[0][col + 32] : 0;
-            bool a0 = cone(u0, v0, ua, va), a1 = cone(u1, v1, ua, va);
-            bool b0 = cone(u0, v0, ub, vb), b1 = cone(u1, v1, ub, vb);
+            bool a0, a1, b0, b1;
+            if (w == ws) {  // warp-uniform
+                const int32_t u0 = sc[0][col], u1 = sc[0][col + 32];
+                a0 = full(u0, v0, ua, va); a1 = full(u1, v1, ua, va);
+                b0 = full(u0, v0, ub, vb); b1 = full(u1, v1, ub, vb);
+            } else {
+                const int32_t u0 = USE_U ? sc[0][col] : 0, u1 = USE_U ? sc[0][col + 32] : 0;
+                a0 = future(u0, v0, ua, va); a1 = future(u1, v1, ua, va);
+                b0 = future(u0, v0, ub, vb); b1 = future(u1, v1, ub, vb);
+            }
             if (CHECK) {
                 const bool in0 = c0 + col < n, in1 = c0 + col + 32 < n;
                 a0 = a0 && in0; a1 = a1 && in1; b0 = b0 && in0; b1 = b1 && in1;
@@ -88,71 +100,22 @@ __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coo
                 mine_b = wb;
             }
         }
-        if (w0 + lane < row_words) {
+        if (lane >= wbeg && w0 + lane < row_words) {
             bits[i * row_words + w0 + lane] = mine_a;
             if (has2) bits[i2 * row_words + w0 + lane] = mine_b;
         }
     }
 }
 
-// Light-cone kinds, a block that straddles the diagonal: row i splits its 32
-// words into those wholly before column i (past cone only), the word holding
-// column i (full test) and those wholly after it (future cone only).  The
-// split point is the same for the whole warp, so the three loops do not
-// diverge.
-template <bool USE_U>
-__device__ __forceinline__ void relate_rows_cone_diag(const int32_t* __restrict__ coords, int64_t n,
-                                                      uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
-                                                      int64_t c0, int64_t r0, int64_t r1,
-                                                      const int32_t (*sc)[kRelColsPerBlock]) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t i = r0 + warp; i < r1; i += kRelThreads / 32) {
-        const int32_t ci[2] = {coords[i], coords[n + i]};
-        const int64_t off = i - c0;
-        const int wd = off < 0 ? -1 : (off >= kRelColsPerBlock ? kRelWordsPerBlock : int(off >> 6));
-        uint64_t mine = 0;
-        auto word = [&](int w, auto test) {
-            const int col = w * 64 + lane;
-            const bool b0 = c0 + col < n && test(col);
-            const bool b1 = c0 + col + 32 < n && test(col + 32);
-            const uint64_t x = (uint64_t(__ballot_sync(0xffffffffu, b1)) << 32) | __ballot_sync(0xffffffffu, b0);
-            if (lane == w) mine = x;
-        };
-        auto past = [&](int col) { return sc[1][col] < ci[1] && (!USE_U || sc[0][col] < ci[0]); };
-        auto future = [&](int col) { return sc[1][col] > ci[1] && (!USE_U || sc[0][col] > ci[0]); };
-        auto full = [&](int col) { return rel_related<kGeomLightCone>(ci, sc, col); };
-        const int wlo = wd < kRelWordsPerBlock ? wd : kRelWordsPerBlock;
-        for (int w = 0; w < wlo; ++w) word(w, past);
-        if (wd >= 0 && wd < kRelWordsPerBlock) word(wd, full);
-        for (int w = wd + 1 > 0 ? wd + 1 : 0; w < kRelWordsPerBlock; ++w) word(w, future);
-        if (w0 + lane < row_words) bits[i * row_words + w0 + lane] = mine;
-    }
-}
-
-template <bool USE_U>
-__device__ __forceinline__ void relate_cone_block(const int32_t* __restrict__ coords, int64_t n,
-                                                  uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
-                                                  int64_t c0, int64_t r0, int64_t r1,
-                                                  const int32_t (*sc)[kRelColsPerBlock]) {
-    if (c0 >= r1) {  // every column after every row
-        if (c0 + kRelColsPerBlock <= n)
-            relate_rows_cone<true, false, USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
-        else
-            relate_rows_cone<true, true, USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
-    } else if (c0 + kRelColsPerBlock <= r0) {  // every column before every row (never past n)
-        relate_rows_cone<false, false, USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
-    } else {
-        relate_rows_cone_diag<USE_U>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
-    }
-}
-
-// Rows [rb*64, rb*64+64) x words [cg*32, cg*32+32) of the bitset.  Column
-// coordinates are staged in `sc`; each warp folds 64 tests per word into a
-// uint64 with two __ballot_sync, lane w keeps word w, and a row's 32 words
-// leave in one coalesced store.  Off-diagonal blocks of the light-cone kinds
-// test one cone only (relate_rows_cone); order2d: the set is a random 2D
-// order whose coords[0] (u) increases strictly with the label, which also
-// drops the u test there.  Must be called by all 256 threads.
+// Rows [rb*64, rb*64+64) x words [cg*32, cg*32+32) of the bitset, less the
+// words wholly before the row tile (word < rb): the relation is symmetric,
+// so mirror_block fills those as transposes.  Column coordinates are staged
+// in `sc`; each warp folds 64 tests per word into a uint64 with two
+// __ballot_sync, lane w keeps word w, and a row's words leave in one
+// coalesced store.  The light-cone kinds test one cone per word
+// (relate_rows_cone); order2d: the set is a random 2D order whose coords[0]
+// (u) increases strictly with the label, which also drops the u test there.
+// Must be called by all 256 threads.
 template <int G>
 __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords, int64_t n,
                                              uint64_t* __restrict__ bits, int64_t row_words, int64_t rb, int64_t cg,
@@ -160,10 +123,11 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
     constexpr int DIM = geom_dim(G);
     const int64_t w0 = cg * kRelWordsPerBlock;
     const int64_t c0 = w0 * 64;
-    // Blocks wholly below the diagonal are left to mirror_block: the relation
-    // is symmetric, so they are the transposes of computed blocks.
-    if (c0 + kRelColsPerBlock <= rb * kRelRowsPerBlock) return;
-    for (int t = threadIdx.x; t < kRelColsPerBlock; t += kRelThreads) {
+    if (w0 + kRelWordsPerBlock <= rb) return;  // wholly below the diagonal
+    // first word of the block at or after the row tile (< 0: all of them)
+    const int ws = rb - w0 < 0 ? -1 : int(rb - w0);
+    const int wbeg = ws > 0 ? ws : 0;
+    for (int t = threadIdx.x + 64 * wbeg; t < kRelColsPerBlock; t += kRelThreads) {
         const int64_t c = c0 + t;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) sc[d][t] = c < n ? coords[d * n + c] : 0;
@@ -173,10 +137,14 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
     const int64_t r0 = rb * kRelRowsPerBlock;
     const int64_t r1 = r0 + kRelRowsPerBlock < n ? r0 + kRelRowsPerBlock : n;
     if constexpr (G == kGeomLightCone) {  // time order: one cone per word, see above
-        if (order2d)
-            relate_cone_block<false>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
-        else
-            relate_cone_block<true>(coords, n, bits, row_words, w0, c0, r0, r1, sc);
+        const bool check = c0 + kRelColsPerBlock > n;
+        if (order2d) {
+            if (check) relate_rows_cone<true, false>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
+            else relate_rows_cone<false, false>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
+        } else {
+            if (check) relate_rows_cone<true, true>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
+            else relate_rows_cone<false, true>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
+        }
     } else {
         for (int64_t i = r0 + warp; i < r1; i += kRelThreads / 32) {
             int32_t ci[DIM];
@@ -184,7 +152,7 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
             for (int d = 0; d < DIM; ++d) ci[d] = coords[d * n + i];
             uint64_t mine = 0;
 #pragma unroll 4
-            for (int w = 0; w < kRelWordsPerBlock; ++w) {
+            for (int w = wbeg; w < kRelWordsPerBlock; ++w) {
                 const int col = w * 64 + lane;
                 const bool b0 = c0 + col < n && rel_related<G>(ci, sc, col);
                 const bool b1 = c0 + col + 32 < n && rel_related<G>(ci, sc, col + 32);
@@ -192,26 +160,23 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
                 const uint32_t hi = __ballot_sync(0xffffffffu, b1);
                 if (lane == w) mine = (uint64_t(hi) << 32) | lo;
             }
-            if (w0 + lane < row_words) bits[i * row_words + w0 + lane] = mine;
+            if (lane >= wbeg && w0 + lane < row_words) bits[i * row_words + w0 + lane] = mine;
         }
     }
 }
 
 // ------------------------------------------------ the lower part by symmetry
 //
-// A relate block wholly below the diagonal (rows [64 rb, 64 rb + 64), words
-// [32 cg, 32 cg + 32), 32 (cg + 1) <= rb) is the transpose of blocks above
-// it.  mirror_block fills one super-tile of 512 output rows x 8 output words
-// (8 x 8 tiles of 64 x 64 bits): the 512 source rows x 8 source words land
-// in shared memory with 64-byte reads, each warp transposes its output row
-// tile's 8 tiles in registers (six butterfly stages, five of them across
-// lanes) and writes 64 contiguous bytes per output row.
+// A 64 x 64 tile wholly below the diagonal (row tile A, word B < A) is the
+// transpose of tile (B, A) above it.  mirror_block fills one super-tile of
+// 512 output rows x 8 output words (8 x 8 tiles): the 512 source rows x 8
+// source words land in shared memory with 64-byte reads, each warp
+// transposes its output row tile's 8 tiles in registers (six butterfly
+// stages, five of them across lanes) and writes its row tile's words
+// below the diagonal, 64 contiguous bytes per output row off the diagonal
+// super-tiles.
 constexpr int kMirTiles = 8;                    // tiles per super-tile side
 constexpr int kMirRows = 64 * kMirTiles;        // 512 source / output rows
-
-__device__ __forceinline__ bool mirror_needed(int64_t A, int64_t B) {  // output row tile A, output word B
-    return (B / kRelWordsPerBlock + 1) * kRelWordsPerBlock <= A;
-}
 
 __device__ __forceinline__ uint64_t tr_step(uint64_t v, int j, uint64_t m, bool low) {
     const uint64_t p = __shfl_xor_sync(0xffffffffu, v, j);
@@ -241,8 +206,8 @@ __device__ __forceinline__ void mirror_block(uint64_t* __restrict__ bits, int64_
                                              int64_t B8, uint64_t (*sm)[kMirTiles + 1]) {
     const int64_t tiles = (n + 63) >> 6;  // row tiles = valid words
     const int64_t A0 = A8 * kMirTiles, B0 = B8 * kMirTiles;
-    // anything to do here? (uniform)
-    if (!mirror_needed(A0 + kMirTiles - 1 < tiles ? A0 + kMirTiles - 1 : tiles - 1, B0) || A0 >= tiles) return;
+    // anything to do here? (uniform: some tile with B < A < tiles)
+    if (A0 >= tiles || B0 >= (A0 + kMirTiles - 1 < tiles ? A0 + kMirTiles - 1 : tiles - 1)) return;
     // source rows 64 B0 .. + 512, source words A0 .. A0 + 8
     for (int t = threadIdx.x; t < kMirRows * kMirTiles; t += blockDim.x) {
         const int r = t / kMirTiles, w = t % kMirTiles;
@@ -252,7 +217,7 @@ __device__ __forceinline__ void mirror_block(uint64_t* __restrict__ bits, int64_
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t A = A0 + warp;  // this warp's output row tile
-    if (A < tiles && mirror_needed(A, B0)) {
+    if (A < tiles && B0 < A) {
         uint64_t ox[kMirTiles], oy[kMirTiles];
 #pragma unroll
         for (int qb = 0; qb < kMirTiles; ++qb) {
@@ -262,18 +227,23 @@ __device__ __forceinline__ void mirror_block(uint64_t* __restrict__ bits, int64_
             oy[qb] = y;
         }
         const int64_t rx = 64 * A + lane, ry = rx + 32;
-        // (a needed tile's 8 words all lie below the diagonal, so inside the
-        // row; 64 contiguous bytes per row as four 16-byte stores)
-        uint4* px = reinterpret_cast<uint4*>(bits + rx * row_words + B0);
-        uint4* py = reinterpret_cast<uint4*>(bits + ry * row_words + B0);
+        // words B0 + qb < A only (all inside the row: B < A < tiles); pairs
+        // of them as 16-byte stores
+        uint64_t* px = bits + rx * row_words + B0;
+        uint64_t* py = bits + ry * row_words + B0;
 #pragma unroll
         for (int h = 0; h < kMirTiles / 2; ++h) {
-            if (rx < n)
-                px[h] = make_uint4(uint32_t(ox[2 * h]), uint32_t(ox[2 * h] >> 32), uint32_t(ox[2 * h + 1]),
-                                   uint32_t(ox[2 * h + 1] >> 32));
-            if (ry < n)
-                py[h] = make_uint4(uint32_t(oy[2 * h]), uint32_t(oy[2 * h] >> 32), uint32_t(oy[2 * h + 1]),
-                                   uint32_t(oy[2 * h + 1] >> 32));
+            if (B0 + 2 * h + 1 < A) {
+                if (rx < n)
+                    reinterpret_cast<uint4*>(px)[h] = make_uint4(uint32_t(ox[2 * h]), uint32_t(ox[2 * h] >> 32),
+                                                                 uint32_t(ox[2 * h + 1]), uint32_t(ox[2 * h + 1] >> 32));
+                if (ry < n)
+                    reinterpret_cast<uint4*>(py)[h] = make_uint4(uint32_t(oy[2 * h]), uint32_t(oy[2 * h] >> 32),
+                                                                 uint32_t(oy[2 * h + 1]), uint32_t(oy[2 * h + 1] >> 32));
+            } else if (B0 + 2 * h < A) {
+                if (rx < n) px[2 * h] = ox[2 * h];
+                if (ry < n) py[2 * h] = oy[2 * h];
+            }
         }
     }
 }
