@@ -122,7 +122,8 @@ int cs_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords_dev,
  * Bit j of row i (word j/64, bit j%64, least significant bit first) is 1 iff
  * i and j are timelike related, Delta s^2 < 0 strictly (Section
  * "Lorentzian Geometry"); 1+1 diamond and 2D order: du * dv > 0; 3D and 4D:
- * dt^2 > |dx|^2, exact in int64; de Sitter slab: the angle around the circle
+ * dt^2 > |dx|^2, exact in int64 for |coordinates| < 2^29 (the sprinkled
+ * diamonds stay within [-2^20, 2^20]); de Sitter slab: the angle around the circle
  * (mod 2^32) is below |d eta|.  For CS_2D_ORDER, coords[0] must increase
  * strictly with the label (as cs_sprinkle writes it: 0..n-1).  row_words
  * must be >= cs_row_words(n) and a multiple of 16; bits_dev holds

@@ -23,9 +23,9 @@
 //               (128B swizzle) into a 4-stage shared-memory ring;
 //   warp 1      TMEM allocator and MMA issuer: 4 x tcgen05.mma (M128 N256 K32)
 //               per stage into one of two TMEM accumulators (2 x 256 columns);
-//   warps 2..9  epilogue: tcgen05.ld of the finished accumulator (one TMEM
-//               lane = one row i per thread; two warps per lane quarter, each
-//               taking half of the 256 columns), mask by i < j < n and C_ij
+//   warps 2..17 epilogue: tcgen05.ld of the finished accumulator (one TMEM
+//               lane = one row i per thread; four warps per lane quarter, each
+//               taking a quarter of the 256 columns), mask by i < j < n and C_ij
 //               from the bitset, bucket k into a shared-memory histogram
 //               (global atomics above 8192), then release the accumulator.
 // The K loop of a tile runs only over the K-blocks between the i-block and the
@@ -47,7 +47,7 @@ constexpr int kABytes = kBM * kBK;       // 16 KiB
 constexpr int kBBytes = kBN * kBK;       // 32 KiB
 constexpr int kStageBytes = kABytes + kBBytes;
 constexpr int kHistBins = 8192;
-constexpr int kEpiWarps = 8;             // two epilogue warps per TMEM lane quarter
+constexpr int kEpiWarps = 16;            // four epilogue warps per TMEM lane quarter
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
 constexpr int kEpiChunks = (kBN / 32) / (kEpiWarps / 4);  // 32-column chunks per epilogue warp
@@ -446,14 +446,11 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             const uint32_t buf = uint32_t(local_count & 1), use = uint32_t((local_count >> 1) & 1);
             ++local_count;
             const int64_t i = it.I0 + 32 * q + lane;
-            // C_ij words of this warp's 128 columns (registers, not an array:
-            // the chunk loop below is not unrolled), loaded before the wait
-            // for the accumulator so that their latency hides behind the MMAs
-            static_assert(kEpiChunks == 4, "two bitset words per epilogue warp");
+            // the C_ij word of this warp's 64 columns, loaded before the wait
+            // for the accumulator so that its latency hides behind the MMAs
+            static_assert(kEpiChunks == 2, "one bitset word per epilogue warp");
             const int64_t word0 = (it.J0 + 32 * c0) >> 6;
-            const uint64_t cw0 = (i < v.n && word0 < v.row_words) ? __ldg(v.bits + i * v.row_words + word0) : 0ull;
-            const uint64_t cw1 =
-                (i < v.n && word0 + 1 < v.row_words) ? __ldg(v.bits + i * v.row_words + word0 + 1) : 0ull;
+            const uint64_t cw = (i < v.n && word0 < v.row_words) ? __ldg(v.bits + i * v.row_words + word0) : 0ull;
             if (!mbar_wait_or_abort(&tfull[buf], use, hdr, abort_flag)) { ok = false; break; }
             tc_fence_after();
             // Every count of this set lands in the shared histogram and there
@@ -466,7 +463,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 tmem_ld_wait();
                 // pairs to count among these 32 j: C_ij, i < j < n
                 const int64_t jb = it.J0 + 32 * c;
-                uint32_t m = uint32_t(((c - c0) < 2 ? cw0 : cw1) >> (32 * (c & 1)));
+                uint32_t m = uint32_t(cw >> (32 * (c & 1)));
                 const int64_t lo = i - jb + 1;  // first u with j > i
                 m &= lo <= 0 ? ~0u : (lo >= 32 ? 0u : (~0u << lo));
                 const int64_t hi = v.n - jb;    // u < hi keeps j < n

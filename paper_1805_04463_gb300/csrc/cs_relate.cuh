@@ -16,8 +16,8 @@ constexpr int kGeomLightCone = 2, kGeom3 = 3, kGeom4 = 4, kGeomDeSitter = 5;
 constexpr int geom_dim(int g) { return g == kGeomDeSitter ? 2 : g; }
 
 // Symmetric timelike test between row element ci and staged column `col`:
-// du * dv > 0 (1+1, light-cone coordinates), dt^2 - |dx|^2 > 0 (2+1, 3+1) in
-// int64, or, on the de Sitter slab's conformal grid (Eq. ds_metric), the
+// du * dv > 0 (1+1, light-cone coordinates), dt^2 - |dx|^2 > 0 (2+1, 3+1)
+// exact in int64, or, on the de Sitter slab's conformal grid (Eq. ds_metric), the
 // angular separation on the circle below the conformal-time separation.
 template <int G>
 __device__ __forceinline__ bool rel_related(const int32_t (&ci)[geom_dim(G)], const int32_t (*sc)[kRelColsPerBlock],
@@ -35,14 +35,16 @@ __device__ __forceinline__ bool rel_related(const int32_t (&ci)[geom_dim(G)], co
         const int32_t dv = sc[1][col] - ci[1];
         return (du ^ dv) >= 0 && du != 0 && dv != 0;
     } else {
-        const int64_t dt = int64_t(sc[0][col]) - ci[0];
-        int64_t r2 = 0;
+        // |coordinates| < 2^29: differences fit int32 and each square is one
+        // widening multiply-add into the int64 sum (< 2^62, exact)
+        const int32_t dt = sc[0][col] - ci[0];
+        int64_t s2 = int64_t(dt) * dt;
 #pragma unroll
         for (int d = 1; d < G; ++d) {
-            const int64_t dx = int64_t(sc[d][col]) - ci[d];
-            r2 += dx * dx;
+            const int32_t dx = sc[d][col] - ci[d];
+            s2 -= int64_t(dx) * dx;
         }
-        return dt * dt - r2 > 0;
+        return s2 > 0;
     }
 }
 
