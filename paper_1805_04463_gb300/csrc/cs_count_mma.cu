@@ -422,6 +422,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         const int q = warp & 3;            // TMEM lane quarter this warp may access
         const int c0 = ((warp - 2) >> 2) * kEpiChunks;  // first of its 32-column chunks
         const int etid = tid - 64;
+        const uint32_t shist_s = smem_u32(shist);
         int64_t local_count = 0;
         int cur = -1;
         uint32_t ephase = 0;
@@ -475,7 +476,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
 #pragma unroll
                     for (int u = 0; u < 32; ++u)
                         if ((m >> u) & 1u)
-                            atomicAdd(&shist[__float_as_uint(__uint_as_float(r[u]) + 8388608.0f) - 0x4B000000u], 1u);
+                            red_shared_add(shist_s + 4u * (__float_as_uint(__uint_as_float(r[u]) + 8388608.0f) - 0x4B000000u), 1u);
                     continue;
                 }
 #pragma unroll
@@ -483,7 +484,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                     if ((m >> u) & 1u) {
                         const uint32_t k = __float_as_uint(__uint_as_float(r[u]) + 8388608.0f) - 0x4B000000u;
                         if (int64_t(k) < hb)
-                            atomicAdd(&shist[k], 1u);
+                            red_shared_add(shist_s + 4u * k, 1u);
                         else
                             atomicAdd(&v.hist[k], 1ull);
                         if (int(k) <= v.kmax)  // i is in L_{k+1}(j)

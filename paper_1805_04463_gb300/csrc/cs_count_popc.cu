@@ -268,7 +268,7 @@ __device__ __forceinline__ void popc_body(const Src& src, WsHeader* hdr) {
                 if ((__ldg(row + (j >> 6)) >> (j & 63)) & 1ull) {
                     const uint32_t k = acc[a][b];
                     if (int64_t(k) < hb)
-                        atomicAdd(&shist[k], 1u);
+                        red_shared_add(smem_u32(shist) + 4u * k, 1u);
                     else
                         atomicAdd(&v.hist[k], 1ull);
                     if (int(k) <= v.kmax)  // i is in L_{k+1}(j)
