@@ -99,22 +99,17 @@ __device__ __forceinline__ bool decode_item(int64_t t, int64_t nsb, int64_t n, i
     return true;
 }
 
-// Spread the low 8 bits of x into 8 bytes of 0x00 / 0x38 (bit b -> byte b).
-__device__ __forceinline__ uint64_t spread_byte(uint32_t x) {
-    uint64_t y = (uint64_t(x & 0xFFu) * 0x0101010101010101ull) & 0x8040201008040201ull;
-    y = ((y + 0x7F7F7F7F7F7F7F7Full) & 0x8080808080808080ull) >> 7;  // 0x01 where the bit was set
-    return y * kOne;
+// Bits 0..3 of x -> 4 bytes of 0x00 / 0x38 (bit b -> byte b).  The product
+// x + (x << 7) + (x << 14) + (x << 21) has its four copies in the disjoint
+// bit ranges 0-3, 7-10, 14-17, 21-24 (no carries), and copy b puts bit b at
+// bit 8b; the mask keeps those four bits.
+__device__ __forceinline__ uint32_t spread4(uint32_t x) {
+    return (((x & 0xFu) * 0x00204081u) & 0x01010101u) * kOne;
 }
 
-// 16 bits of a bitset word -> 16 operand bytes (one 16-byte store).
-__device__ __forceinline__ void store16(uint8_t* dst, uint32_t bits16) {
-    const uint64_t lo = spread_byte(bits16 & 0xFFu), hi = spread_byte((bits16 >> 8) & 0xFFu);
-    uint4 v;
-    v.x = uint32_t(lo);
-    v.y = uint32_t(lo >> 32);
-    v.z = uint32_t(hi);
-    v.w = uint32_t(hi >> 32);
-    *reinterpret_cast<uint4*>(dst) = v;
+// 16 bits of a bitset row -> 16 operand bytes.
+__device__ __forceinline__ uint4 spread16(uint32_t b) {
+    return make_uint4(spread4(b), spread4(b >> 4), spread4(b >> 8), spread4(b >> 12));
 }
 
 // The parts of the operands any tile reads (decode_item): row i of U is an A
@@ -126,40 +121,44 @@ __device__ __forceinline__ void store16(uint8_t* dst, uint32_t bits16) {
 __device__ __forceinline__ int64_t u_first_piece(int64_t i) { return (i / kBM) * (kBM / 16); }
 __device__ __forceinline__ int64_t l_end_piece(int64_t j) { return (j / kBN + 1) * (kBN / 16); }
 
-// Columns [16c, 16c+16) of row i: U keeps the columns after i, L the columns
-// before i, each only where a tile reads it.  Consecutive threads write
-// consecutive 16-byte pieces.
-__device__ __forceinline__ void expand_piece(const uint64_t* __restrict__ bits, int64_t row_words, int64_t kpad,
-                                             uint8_t* __restrict__ U, uint8_t* __restrict__ L, int64_t i, int64_t c) {
-    const int64_t w = c >> 2;
-    const int sh = int(c & 3) * 16;
-    const uint64_t word = __ldg(bits + i * row_words + w);
-    const int64_t x = i - 64 * w;  // bit position of column i inside this word
-    const uint64_t after = x < 0 ? ~0ull : (x >= 63 ? 0ull : (~0ull << (x + 1)));
-    const uint64_t before = x <= 0 ? 0ull : (x >= 64 ? ~0ull : ((1ull << x) - 1ull));
-    if (c >= u_first_piece(i)) store16(U + i * kpad + 16 * c, uint32_t((word & after) >> sh) & 0xFFFFu);
-    if (c < l_end_piece(i)) store16(L + i * kpad + 16 * c, uint32_t((word & before) >> sh) & 0xFFFFu);
+// Row i of U (the columns after i) and of L (the columns before i), each
+// only where a tile reads it, in 16-column pieces handed out to thread t of
+// a team of `size`: consecutive threads load consecutive 32-bit halves of
+// the row's words and store consecutive 16-byte pieces.
+__device__ __forceinline__ void expand_row(const uint64_t* __restrict__ bits, int64_t row_words, int64_t kpad,
+                                           uint8_t* __restrict__ U, uint8_t* __restrict__ L, int64_t i, int t,
+                                           int size) {
+    const int ppr = int(kpad / 16);
+    const uint32_t* brow = reinterpret_cast<const uint32_t*>(bits + i * row_words);
+    uint4* urow = reinterpret_cast<uint4*>(U + i * kpad);
+    uint4* lrow = reinterpret_cast<uint4*>(L + i * kpad);
+    const int ii = int(i);  // n < 2^31
+    auto piece = [&](int c) { return (__ldg(brow + (c >> 1)) >> (16 * (c & 1))) & 0xFFFFu; };
+    for (int c = int(u_first_piece(i)) + t; c < ppr; c += size) {
+        const int d = ii - 16 * c;  // column i relative to the piece's first column
+        const uint32_t keep = d < 0 ? 0xFFFFu : (d >= 15 ? 0u : (0xFFFFu << (d + 1)) & 0xFFFFu);
+        urow[c] = spread16(piece(c) & keep);
+    }
+    const int le = int(l_end_piece(i)) < ppr ? int(l_end_piece(i)) : ppr;
+    for (int c = t; c < le; c += size) {
+        const int d = ii - 16 * c;
+        const uint32_t keep = d >= 16 ? 0xFFFFu : (d <= 0 ? 0u : (1u << d) - 1u);
+        lrow[c] = spread16(piece(c) & keep);
+    }
 }
 
-// U and L rows from the symmetric bitset: one thread per 16 columns.
-// Rows [r0, r1) of one set.  Long rows (at least 4 pieces per thread): the
-// block sweeps each row.  Shorter rows: (row, piece) pairs are flattened over
-// the block, so every thread still has independent loads and stores in
-// flight.
+// U and L rows [r0, r1) of one set from the symmetric bitset.  Long rows (at
+// least 4 pieces per thread of the block): the block sweeps each row;
+// shorter rows: one warp per row.
 __device__ __forceinline__ void expand_rows(const uint64_t* __restrict__ bits, int64_t row_words, int64_t kpad,
                                             uint8_t* __restrict__ U, uint8_t* __restrict__ L, int64_t r0,
                                             int64_t r1) {
-    const int ppr = int(kpad / 16);
-    if (ppr >= 4 * int(blockDim.x)) {
-        for (int64_t i = r0; i < r1; ++i)
-            for (int c = threadIdx.x; c < ppr; c += blockDim.x) expand_piece(bits, row_words, kpad, U, L, i, c);
+    if (kpad / 16 >= 4 * int64_t(blockDim.x)) {
+        for (int64_t i = r0; i < r1; ++i) expand_row(bits, row_words, kpad, U, L, i, threadIdx.x, blockDim.x);
         return;
     }
-    const int cnt = int(r1 - r0) * ppr;  // at most kExpandRows * ppr < 2^31
-    for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-        const int rr = p / ppr;
-        expand_piece(bits, row_words, kpad, U, L, r0 + rr, p - rr * ppr);
-    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int64_t i = r0 + warp; i < r1; i += nw) expand_row(bits, row_words, kpad, U, L, i, lane, 32);
 }
 
 constexpr int kExpandRows = 16;  // rows per block step
