@@ -181,23 +181,51 @@ __global__ void __launch_bounds__(kRelThreads) k_batch_mirror(const BatchSet* __
     mirror_block(b.bits, b.n, b.row_words, local / b.mir_side, local % b.mir_side, sm);
 }
 
-// One CTA per set: bracket, local and smeared actions.  Powers of (1-eps)
-// advance by a fixed stride per thread after a direct start.
+// Smeared-sum coefficients f_d(k, eps) (Eqs. f2, f3, f4), one table per
+// dimension present and eps, shared by every set of that dimension: a set's
+// cutoff never exceeds that of the dimension's largest set (smear_cutoff
+// grows with n), which sizes the table.  Dimension slot: d - 2.
+constexpr int kDimSlots = 3;
+struct CoefArgs {
+    int64_t base[kDimSlots];              // first table entry of the slot
+    int64_t stride[kDimSlots];            // entries per eps (the slot's largest n)
+    int64_t kcap[kDimSlots][kMaxEps];     // entries computed per (slot, eps)
+    int64_t seg[kDimSlots * kMaxEps + 1];  // prefix sums of kcap in (slot, eps) order
+};
+
+__global__ void __launch_bounds__(256) k_batch_coef(dd* __restrict__ coef, CoefArgs c, EpsArgs eps) {
+    const int64_t total = c.seg[kDimSlots * kMaxEps];
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+        int g = 0;
+        while (c.seg[g + 1] <= t) ++g;  // at most 48 segments
+        const int slot = g / kMaxEps, e = g % kMaxEps, dim = slot + 2;
+        const int64_t k = t - c.seg[g];
+        const double ep = eps.v[e];
+        const dd q = dd_two_sum(1.0, -ep);
+        coef[c.base[slot] + e * c.stride[slot] + k] =
+            dd_mul(dd_pow(q, smear_qexp(dim, k)), smear_poly(dim, k, q, ep));
+    }
+}
+
+// One CTA per set: bracket, local and smeared actions; the smeared sums take
+// their coefficients from the shared table.
 __global__ void __launch_bounds__(kActThreads) k_batch_action(const BatchSet* __restrict__ sets,
                                                               const int64_t* __restrict__ hist_base, EpsArgs eps,
+                                                              const dd* __restrict__ coef, CoefArgs c,
                                                               double* __restrict__ actions,
                                                               int64_t* __restrict__ brackets) {
     __shared__ dd red[kActThreads];
     __shared__ int64_t kends[kMaxEps];
     const BatchSet& b = sets[blockIdx.x];
-    const int dim = b.dim;
+    const int dim = b.dim, slot = dim - 2;
     const int64_t n = b.n, len = n > 1 ? n - 1 : 1;
     // cutoffs of this set, one thread per eps (the first barrier below
-    // publishes them)
-    if (threadIdx.x < eps.n)
-        kends[threadIdx.x] = is_local(eps.v[threadIdx.x])
-                                 ? 0
-                                 : smear_cutoff(dim, eps.v[threadIdx.x], 0.5 * double(n) * double(n), len);
+    // publishes them); never beyond the table
+    if (threadIdx.x < eps.n) {
+        const double ep = eps.v[threadIdx.x];
+        const int64_t k = is_local(ep) ? 0 : smear_cutoff(dim, ep, 0.5 * double(n) * double(n), len);
+        kends[threadIdx.x] = k < c.kcap[slot][threadIdx.x] ? k : c.kcap[slot][threadIdx.x];
+    }
     __syncthreads();
     const int64_t* hist = hist_base + b.hist_off;
     const int tid = threadIdx.x;
@@ -214,16 +242,12 @@ __global__ void __launch_bounds__(kActThreads) k_batch_action(const BatchSet* __
             }
             continue;
         }
-        const dd q = dd_two_sum(1.0, -ep);
-        const dd step = dd_pow(q, kActThreads);
+        const dd* f = coef + c.base[slot] + e * c.stride[slot];
         const int64_t kend = kends[e];
-        const int64_t deg = smear_deg(dim);
-        dd sum = dd_from(0.0), p = dd_from(1.0);
+        dd sum = dd_from(0.0);
         for (int64_t k = tid; k < kend; k += kActThreads) {
-            // q^(k-deg) for k >= deg; a direct power until the stride applies
-            p = (k - kActThreads < deg) ? dd_pow(q, smear_qexp(dim, k)) : dd_mul(p, step);
             const int64_t hk = hist[k];
-            if (hk != 0) sum = dd_add(sum, dd_mul(dd_from_i64(hk), dd_mul(p, smear_poly(dim, k, q, ep))));
+            if (hk != 0) sum = dd_add(sum, dd_mul(dd_from_i64(hk), f[k]));
         }
         red[tid] = sum;
         __syncthreads();
@@ -263,12 +287,15 @@ struct cs_batch {
     int64_t total_mblocks = 0;
     int max_pow2 = 1;
     const uint64_t* ds_thr = nullptr;  // de Sitter thresholds, when a set needs them
+    dd* coef = nullptr;                 // smeared-sum coefficient tables
+    int64_t nmax[kDimSlots] = {0, 0, 0};  // largest n per dimension slot (0: absent)
+    int64_t coef_base[kDimSlots] = {0, 0, 0};
 };
 
 namespace {
 
 struct Layout {
-    size_t sets, entries, rtab, etab, mtab, total;
+    size_t sets, entries, rtab, etab, mtab, coef, total;
     std::vector<size_t> coords, bits, key0, key1, raw, U, L;
 };
 
@@ -308,6 +335,12 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
     L.rtab = take(size_t(rblocks) * 4);  // relate block -> set
     L.etab = take(size_t(chunks) * 4);   // expansion chunk -> set
     L.mtab = take(size_t(mblocks) * 4);  // mirror block -> set
+    int64_t nmax[kDimSlots] = {0, 0, 0};
+    for (int s = 0; s < n_sets; ++s) {
+        int64_t& m = nmax[cs_dim(sets[s].kind) - 2];
+        m = sets[s].n > m ? sets[s].n : m;
+    }
+    L.coef = take(size_t(nmax[0] + nmax[1] + nmax[2]) * kMaxEps * sizeof(dd));  // coefficient tables
     for (int s = 0; s < n_sets; ++s) {
         const int64_t n = sets[s].n;
         const int dim = cs_dim(sets[s].kind);
@@ -449,6 +482,16 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     h->total_hist = hoff;
     h->max_pow2 = max_pow2;
     h->ds_thr = ds_thr;
+    h->coef = reinterpret_cast<dd*>(ws + L.coef);
+    for (int s = 0; s < n_sets; ++s) {
+        int64_t& m = h->nmax[bs[s].dim - 2];
+        m = bs[s].n > m ? bs[s].n : m;
+    }
+    int64_t at = 0;
+    for (int d = 0; d < kDimSlots; ++d) {
+        h->coef_base[d] = at;
+        at += h->nmax[d] * kMaxEps;
+    }
     cudaError_t e = cudaMemcpyAsync(h->sets_dev, bs.data(), sizeof(BatchSet) * bs.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !rtab.empty())
         e = cudaMemcpyAsync(h->rtab, rtab.data(), rtab.size() * 4, cudaMemcpyHostToDevice, st);
@@ -524,8 +567,29 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
     }
     if (err != cudaSuccess) return CS_ECUDA;
     if (n_eps > 0 || brackets_dev) {
-        k_batch_action<<<unsigned(b->nsets), kActThreads, 0, st>>>(b->sets_dev, hist_dev, a, actions_dev,
-                                                                  brackets_dev);
+        CoefArgs c;
+        std::memset(static_cast<void*>(&c), 0, sizeof(c));
+        int64_t at = 0;
+        for (int d = 0; d < kDimSlots; ++d) {
+            c.base[d] = b->coef_base[d];
+            c.stride[d] = b->nmax[d];
+            const int64_t nm = b->nmax[d], len = nm > 1 ? nm - 1 : 1;
+            for (int e = 0; e < kMaxEps; ++e) {
+                c.kcap[d][e] = (nm > 0 && e < n_eps && !is_local(a.v[e]))
+                                   ? smear_cutoff(d + 2, a.v[e], 0.5 * double(nm) * double(nm), len)
+                                   : 0;
+                c.seg[d * kMaxEps + e] = at;
+                at += c.kcap[d][e];
+            }
+        }
+        c.seg[kDimSlots * kMaxEps] = at;
+        if (at > 0) {
+            int64_t g = (at + 255) / 256;
+            if (g > int64_t(sms) * 4) g = int64_t(sms) * 4;
+            k_batch_coef<<<unsigned(g), 256, 0, st>>>(b->coef, c, a);
+        }
+        k_batch_action<<<unsigned(b->nsets), kActThreads, 0, st>>>(b->sets_dev, hist_dev, a, b->coef, c,
+                                                                  actions_dev, brackets_dev);
         if (cudaGetLastError() != cudaSuccess) return CS_ECUDA;
     }
     return CS_OK;
