@@ -12,7 +12,7 @@ histogram and actions copied back, every step); roofline = the count
 kernel's achieved rate against the POPC (or tensor) peak; cpu_baseline = the
 CPU oracle on a bounded sample of the same workload.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--path auto|popc|mma]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--path auto|popc|mma|mma4]
   python bench.py --impl reference ...   # the CPU oracle as the reference arm
 """
 from __future__ import annotations
@@ -37,7 +37,8 @@ WORKLOADS = {
     "2d_order_1024": (0, 1024, 0xC5E70001, "random 2D order, N=1024"),
 }
 EPS = (0.0, 0.05, 0.1, 0.2)
-PATHS = {"auto": 0, "popc": 1, "mma": 2}
+PATHS = {"auto": 0, "popc": 1, "mma": 2, "mma4": 3}
+PATH_NAMES = {1: "popc", 2: "mma", 3: "mma4"}
 POPC_PER_SM_PER_CLK = 16  # 32-bit population count, per SM per clock
 
 
@@ -121,6 +122,13 @@ def roofline_for(resolved, n, count_s, peaks, src, sm_count):
     """Achieved vs peak for the count call (algorithmic work: every pair i<j over the
     columns strictly between them, C(n,3) bit-AND/popcount terms = MACs)."""
     terms = n * (n - 1) * (n - 2) / 6.0
+    if resolved == 3:
+        # FP4 dense peak = measured bf16 sustained peak x nominal FP4/BF16 ratio (13.5/2.25)
+        peak = 6.0 * peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        achieved = 2.0 * terms / count_s / 1e12
+        return {"bound": "tensor", "kernel": "k_count_mma4 (+ k_expand_f4)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "algorithmic_macs": terms,
+                "peak_source": f"6 x bf16_tflops_sustained ({src}); FP4 kind::mxf4, 2 FLOP per MAC"}
     if resolved == 2:
         # FP8 dense peak = measured bf16 sustained peak x nominal FP8/BF16 ratio (4.5/2.25)
         peak = 2.0 * peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
@@ -136,19 +144,20 @@ def roofline_for(resolved, n, count_s, peaks, src, sm_count):
                            f"(sm_max_mhz, {src})"}
 
 
-TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_count_mma__2d_order_131072__dram.md")
+TRAFFIC_RECORDS = {2: "k_count_mma__2d_order_131072__dram.md", 3: "k_count_mma4__2d_order_131072__dram.md"}
 MMA_SOURCES = [os.path.join(ROOT, "paper_1805_04463_gb300", "csrc", f)
                for f in ("cs_count_mma.cu", "cs_internal.cuh", "cs_kernels.cuh")]
 
 
-def recorded_traffic():
-    """DRAM bytes per full-size k_count_mma launch from the committed ncu record,
-    or None when the kernel sources changed since it was captured."""
+def recorded_traffic(resolved):
+    """DRAM bytes per full-size count launch (k_count_mma or k_count_mma4) from the
+    committed ncu record, or None when the kernel sources changed since it was captured."""
     import hashlib
     try:
-        rec = dict(line.split(":", 1) for line in open(TRAFFIC_RECORD) if line.startswith(("traffic_", "kernel_")))
+        path = os.path.join(ROOT, "profiles", TRAFFIC_RECORDS[resolved])
+        rec = dict(line.split(":", 1) for line in open(path) if line.startswith(("traffic_", "kernel_")))
         h = hashlib.sha256(b"".join(open(f, "rb").read() for f in MMA_SOURCES)).hexdigest()[:16]
-    except (OSError, ValueError):
+    except (OSError, ValueError, KeyError):
         return None
     if rec.get("kernel_sources_sha256_16", "").strip() != h:
         return None
@@ -158,7 +167,7 @@ def recorded_traffic():
 def compare_paths(cs, torch, buf, n, stream):
     """Count-call time of each path on the same bitset (1 warm-up + 1 timed, CUDA events)."""
     out = {}
-    for name, p in (("popc", 1), ("mma", 2)):
+    for name, p in (("popc", 1), ("mma", 2), ("mma4", 3)):
         ws = torch.empty(cs.interval_abundance_workspace(n, p), dtype=torch.uint8, device="cuda")
         hist = torch.empty_like(buf.hist)
         cs.interval_abundance(n, buf.bits, hist, p, ws, stream)
@@ -216,7 +225,7 @@ def ensemble_bench(cs, torch, path, steps=5, warmup=3, n2d=512, n4d=256):
     same = all(torch.equal(buf.hist, b.set_hist(s)) for s, buf in enumerate(bufs))
     terms = sum(n * (n - 1) * (n - 2) / 6.0 for _, n, _ in sets)
     return {"workload": f"{n2d} 2D diamonds N~Poisson(4096) + {n4d} 4D diamonds N~Poisson(2048)",
-            "sets": len(sets), "pairs": pairs, "path": {1: "popc", 2: "mma"}[b.path],
+            "sets": len(sets), "pairs": pairs, "path": PATH_NAMES[b.path],
             "batched_graph_ms": batched_ms, "plain_ms": plain_ms,
             "batched_gpairs_s": pairs / batched_ms / 1e6, "plain_gpairs_s": pairs / plain_ms / 1e6,
             "batched_actions_s": len(sets) / batched_ms * 1e3, "plain_actions_s": len(sets) / plain_ms * 1e3,
@@ -306,10 +315,17 @@ def serving_bench(path, rate=200.0, duration_s=5.0):
     return stats
 
 
+def batch_path(name):
+    """The path the batch and serving entry points take for --path (they count on
+    POPC or FP8 tiles; the FP4 path is a single-set path)."""
+    p = PATHS[name]
+    return 2 if p == 3 else p
+
+
 def launches_per_step(kind, path):
     """Kernels of this library launched by one step (sprinkle, relate, count, actions)."""
     sprinkle = 1 + (2 if kind == 0 else 1) * 4 + 1
-    count = 1 if path != 2 else 2
+    count = 1 if path == 1 else 2  # the tensor paths expand the operands first
     return sprinkle + 1 + count + 2
 
 
@@ -510,10 +526,11 @@ def main():
     roofline = roofline_for(cs.resolved_path(n, path), n, statistics.mean(count_ms) / 1e3, peaks, src,
                             torch.cuda.get_device_properties(local).multi_processor_count)
     roofline["count_ms"] = statistics.mean(count_ms)
+    resolved = cs.resolved_path(n, path)
     if roofline["bound"] == "tensor" and args.workload == "2d_order_131072":
-        tr = recorded_traffic()
+        tr = recorded_traffic(resolved)
         roofline["traffic"] = tr
-        roofline["traffic_source"] = ("profiles/k_count_mma__2d_order_131072__dram.md (dram__bytes_read.sum + "
+        roofline["traffic_source"] = (f"profiles/{TRAFFIC_RECORDS[resolved]} (dram__bytes_read.sum + "
                                       "dram__bytes_write.sum, one full-size launch)" if tr else
                                       "no capture for the current kernel sources")
     if args.compare_paths:
@@ -522,11 +539,11 @@ def main():
         "metric": f"interval-count Gpairs/s ({desc})", "value": value, "unit": "Gpairs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        # the count's arithmetic: 0/1 E4M3 products summed in FP32 on the tensor path,
-        # AND + popcount on 64-bit words on the POPC path
-        "dtype": "fp8e4m3" if cs.resolved_path(n, path) == 2 else "u64", "data": "synthetic",
+        # the count's arithmetic: 0/1 E4M3 (FP8 path) or E2M1 (FP4 path) products summed
+        # in FP32 on the tensor paths, AND + popcount on 64-bit words on the POPC path
+        "dtype": {1: "u64", 2: "fp8e4m3", 3: "fp4e2m1"}[cs.resolved_path(n, path)], "data": "synthetic",
         "config": {"workload": args.workload, "kind": cs.KIND_NAMES[kind], "n": n, "seed": seed0,
-                   "path": args.path, "resolved_path": {1: "popc", 2: "mma"}[cs.resolved_path(n, path)],
+                   "path": args.path, "resolved_path": PATH_NAMES[cs.resolved_path(n, path)],
                    "eps": list(EPS),
                    "l2": "inputs larger than L2" if cs.bitset_bytes(n) > 129e6 else "inputs smaller than L2",
                    "parallelism": f"replicas{args.gpus}"},
@@ -543,9 +560,9 @@ def main():
         line.update(extras_bench(cs, torch, buf, kind, n, path, stream, peaks))
     if not args.no_ensemble:
         n2d, n4d = (int(x) for x in args.ensemble_sets.split(","))
-        line["ensemble"] = ensemble_bench(cs, torch, PATHS[args.path], n2d=n2d, n4d=n4d)
+        line["ensemble"] = ensemble_bench(cs, torch, batch_path(args.path), n2d=n2d, n4d=n4d)
     if not args.no_serve:
-        line["serving"] = serving_bench(PATHS[args.path])
+        line["serving"] = serving_bench(batch_path(args.path))
     if not args.no_cpu_baseline:
         cb = cpu_baseline(kind, n, seed0)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "single_thread")}

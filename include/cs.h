@@ -65,7 +65,11 @@ enum {
 enum {
     CS_PATH_AUTO = 0,   /* pick the faster path for this n */
     CS_PATH_POPC = 1,   /* AND + popcount tiles on the CUDA cores */
-    CS_PATH_MMA = 2     /* 0/1 operands on the tcgen05 tensor cores, fused epilogue */
+    CS_PATH_MMA = 2,    /* 0/1 operands as FP8 E4M3 on the tcgen05 tensor cores, fused epilogue */
+    CS_PATH_MMA4 = 3    /* 0/1 operands as packed FP4 E2M1 (block-scaled kind::mxf4, every scale
+                           factor 1): half the operand bytes, the FP4 tensor rate.  Single-set
+                           calls only (cs_interval_abundance, cs_layer_sums, cs_evaluate); the
+                           batch and job entry points take CS_PATH_POPC / CS_PATH_MMA. */
 };
 
 /* ------------------------------------------------------------- layouts */
@@ -136,17 +140,17 @@ int cs_causal_matrix(int kind, int64_t n, const int32_t *coords_dev,
 /* -------------------------------------------------- interval abundance */
 
 /* The path cs_interval_abundance runs for (n, path) on the current device:
- * CS_PATH_POPC or CS_PATH_MMA (CS_PATH_AUTO follows the table below; the
- * tensor-core path only where the device has tcgen05); -1 for invalid
- * arguments. */
+ * CS_PATH_POPC, CS_PATH_MMA or CS_PATH_MMA4 (CS_PATH_AUTO follows the table
+ * below; the tensor-core paths only where the device has tcgen05); -1 for
+ * invalid arguments. */
 int cs_resolved_path(int64_t n, int path);
 
 /*
  * The CS_PATH_AUTO table, process-wide: entry e selects paths[e]
- * (CS_PATH_POPC or CS_PATH_MMA) for n_min[e] <= n < n_min[e+1].  n_min must
- * start at 0 and increase; at most 16 entries.  The default is {0: POPC,
- * 1024: MMA}; the autotuner (paper_1805_04463_gb300/tune.py) installs
- * measured thresholds.  Errors: CS_EINVAL.
+ * (CS_PATH_POPC, CS_PATH_MMA or CS_PATH_MMA4) for n_min[e] <= n < n_min[e+1].
+ * n_min must start at 0 and increase; at most 16 entries.  The default is
+ * {0: POPC, 1024: MMA}; the autotuner (paper_1805_04463_gb300/tune.py)
+ * installs measured thresholds.  Errors: CS_EINVAL.
  */
 int cs_set_auto_paths(const int64_t *n_min, const int *paths, int count);
 
@@ -154,9 +158,10 @@ int cs_set_auto_paths(const int64_t *n_min, const int *paths, int count);
  * capacity is smaller than the count). */
 int cs_get_auto_paths(int64_t *n_min, int *paths, int capacity);
 
-/* Device workspace needed by cs_interval_abundance for (n, path).  The
+/* Device workspace needed by cs_interval_abundance for (n, path).  The FP8
  * tensor-core path keeps two n x ceil(n/128)*128-byte operand matrices in it
- * (2 n^2 bytes, about 34 GB at n = 131072). */
+ * (2 n^2 bytes, about 34 GB at n = 131072); the FP4 path two
+ * n x ceil(n/256)*128-byte ones (n^2 bytes, about 17 GB at n = 131072). */
 size_t cs_interval_abundance_workspace(int64_t n, int path);
 
 /*
@@ -166,10 +171,11 @@ size_t cs_interval_abundance_workspace(int64_t n, int path);
  * AND of rows i and j over columns i+1..j-1, i.e. (C.C)_ij for the strict
  * upper triangle C).  hist_dev (cs_hist_len(n) int64) is zeroed and then
  * filled by the callee.  path selects the kernel (CS_PATH_AUTO picks one);
- * both paths give identical, exact results.
+ * every path gives identical, exact results (the tensor paths multiply 0/1
+ * values and accumulate integers below 2^23 in FP32).
  * Errors: CS_EINVAL (n < 1, n > 2^22, bad row_words, NULL or unaligned pointers), CS_ENOMEM
- * (workspace too small), CS_EUNSUPPORTED (CS_PATH_MMA on a device without
- * tcgen05), CS_ECUDA.  A timed-out in-kernel wait sets CS_ETIMEOUT in the
+ * (workspace too small), CS_EUNSUPPORTED (CS_PATH_MMA or CS_PATH_MMA4 on a
+ * device without tcgen05), CS_ECUDA.  A timed-out in-kernel wait sets CS_ETIMEOUT in the
  * workspace status word.
  */
 int cs_interval_abundance(int64_t n, const uint64_t *bits_dev, int64_t row_words,
@@ -506,6 +512,13 @@ const char *cs_strerror(int status);
 
 /* Library version string. */
 const char *cs_version(void);
+
+/* Description of the last CUDA runtime error that made a single-set entry
+ * point (cs_sprinkle, cs_causal_matrix, cs_interval_abundance,
+ * cs_layer_sums, cs_dalembertian, cs_action_device, cs_evaluate) return
+ * CS_ECUDA on the calling host thread; "no error" if there was none.  The
+ * string is static; the record is never cleared. */
+const char *cs_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

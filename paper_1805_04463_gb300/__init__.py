@@ -17,7 +17,7 @@ import os
 import threading
 
 __all__ = [
-    "KIND_2D_ORDER", "KIND_2D_DIAMOND", "KIND_4D_DIAMOND", "KIND_3D_DIAMOND", "KIND_2D_DS_SLAB", "PATH_AUTO", "PATH_POPC", "PATH_MMA",
+    "KIND_2D_ORDER", "KIND_2D_DIAMOND", "KIND_4D_DIAMOND", "KIND_3D_DIAMOND", "KIND_2D_DS_SLAB", "PATH_AUTO", "PATH_POPC", "PATH_MMA", "PATH_MMA4",
     "CsError", "lib", "dim", "coords_bytes", "row_words", "bitset_bytes", "hist_len",
     "sprinkle_workspace_bytes", "interval_abundance_workspace", "resolved_path", "action_workspace_bytes",
     "set_auto_paths", "get_auto_paths",
@@ -28,7 +28,7 @@ __all__ = [
 ]
 
 KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND, KIND_2D_DS_SLAB = 0, 1, 2, 3, 4
-PATH_AUTO, PATH_POPC, PATH_MMA = 0, 1, 2
+PATH_AUTO, PATH_POPC, PATH_MMA, PATH_MMA4 = 0, 1, 2, 3
 FAULT_ALLOC, FAULT_LAUNCH = 1, 2
 BATCH_MAX_N = 8192  # CS_BATCH_MAX_N: largest set a batch takes
 KIND_NAMES = {KIND_2D_ORDER: "2d_order", KIND_2D_DIAMOND: "2d_diamond", KIND_4D_DIAMOND: "4d_diamond",
@@ -48,6 +48,8 @@ class CsError(RuntimeError):
         msg = status if isinstance(status, str) else f"{what}: status {status}"
         if not isinstance(status, str) and _lib is not None:
             msg += " (" + _lib.cs_strerror(status).decode() + ")"
+            if status == -3:  # CS_ECUDA: name the CUDA error behind it
+                msg += ": " + _lib.cs_last_cuda_error().decode()
         super().__init__(msg)
 
 
@@ -110,6 +112,7 @@ def lib() -> ctypes.CDLL:
             "cs_inject_fault": ([i32, i32], i32),
             "cs_strerror": ([i32], ctypes.c_char_p),
             "cs_version": ([], ctypes.c_char_p),
+            "cs_last_cuda_error": ([], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -170,7 +173,7 @@ def interval_abundance_workspace(n: int, path: int = PATH_AUTO) -> int:
 
 
 def resolved_path(n: int, path: int = PATH_AUTO) -> int:
-    """PATH_POPC or PATH_MMA: the kernel cs_interval_abundance runs for (n, path)."""
+    """PATH_POPC, PATH_MMA or PATH_MMA4: the kernel cs_interval_abundance runs for (n, path)."""
     return lib().cs_resolved_path(n, path)
 
 

@@ -10,7 +10,14 @@ namespace {
 
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-inline int from_cuda(cudaError_t e) { return e == cudaSuccess ? CS_OK : CS_ECUDA; }
+// The last CUDA error an entry point turned into CS_ECUDA, per host thread.
+thread_local cudaError_t t_last_cuda = cudaSuccess;
+
+inline int from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return CS_OK;
+    t_last_cuda = e;
+    return CS_ECUDA;
+}
 
 inline bool valid_n(int64_t n) { return n >= 1 && n <= kMaxN; }
 
@@ -42,7 +49,7 @@ int resolve_path(int64_t n, int path) {
         for (int e = 0; e < g_auto_count; ++e)
             if (n >= g_auto_n[e]) p = g_auto_p[e];
     }
-    return (p == CS_PATH_MMA && !device_has_tcgen05()) ? CS_PATH_POPC : p;
+    return ((p == CS_PATH_MMA || p == CS_PATH_MMA4) && !device_has_tcgen05()) ? CS_PATH_POPC : p;
 }
 
 }  // namespace cs
@@ -104,7 +111,7 @@ int cs_causal_matrix(int kind, int64_t n, const int32_t* coords_dev, uint64_t* b
 int cs_set_auto_paths(const int64_t* n_min, const int* paths, int count) {
     if (!n_min || !paths || count < 1 || count > kMaxAuto || n_min[0] != 0) return CS_EINVAL;
     for (int e = 0; e < count; ++e) {
-        if (paths[e] != CS_PATH_POPC && paths[e] != CS_PATH_MMA) return CS_EINVAL;
+        if (paths[e] != CS_PATH_POPC && paths[e] != CS_PATH_MMA && paths[e] != CS_PATH_MMA4) return CS_EINVAL;
         if (e > 0 && n_min[e] <= n_min[e - 1]) return CS_EINVAL;
     }
     std::lock_guard<std::mutex> lk(g_auto_mu);
@@ -127,31 +134,43 @@ int cs_get_auto_paths(int64_t* n_min, int* paths, int capacity) {
 }
 
 int cs_resolved_path(int64_t n, int path) {
-    if (!valid_n(n) || path < CS_PATH_AUTO || path > CS_PATH_MMA) return -1;
+    if (!valid_n(n) || path < CS_PATH_AUTO || path > CS_PATH_MMA4) return -1;
     return resolve_path(n, path);
 }
 
 size_t cs_interval_abundance_workspace(int64_t n, int path) {
-    if (!valid_n(n) || path < CS_PATH_AUTO || path > CS_PATH_MMA) return 0;
-    return resolve_path(n, path) == CS_PATH_MMA ? mma_workspace_bytes(n) : popc_workspace_bytes(n);
+    if (!valid_n(n) || path < CS_PATH_AUTO || path > CS_PATH_MMA4) return 0;
+    const int p = resolve_path(n, path);
+    return p == CS_PATH_MMA ? mma_workspace_bytes(n) : p == CS_PATH_MMA4 ? mma4_workspace_bytes(n)
+                                                                          : popc_workspace_bytes(n);
 }
+
+namespace {
+
+// The count kernels of a resolved path.
+cudaError_t launch_count(int p, int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* ws,
+                         cudaStream_t st, const double* phi = nullptr, double* layer = nullptr, int kmax = -1) {
+    if (p == CS_PATH_MMA) return launch_count_mma(n, bits, row_words, hist, ws, st, phi, layer, kmax);
+    if (p == CS_PATH_MMA4) return launch_count_mma4(n, bits, row_words, hist, ws, st, phi, layer, kmax);
+    return launch_count_popc(n, bits, row_words, hist, ws, st, phi, layer, kmax);
+}
+
+}  // namespace
 
 int cs_interval_abundance(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_t* hist_dev, int path,
                           void* workspace_dev, size_t workspace_bytes, void* stream) {
     CS_TRACE("cs_interval_abundance");
     if (!valid_n(n) || !bits_dev || !aligned(bits_dev, 128) || !hist_dev || !aligned(hist_dev, 8) ||
         row_words < cs_row_words(n) || row_words % 16 != 0 || !workspace_dev || !aligned(workspace_dev, 256) ||
-        path < CS_PATH_AUTO || path > CS_PATH_MMA)
+        path < CS_PATH_AUTO || path > CS_PATH_MMA4)
         return CS_EINVAL;
     if (workspace_bytes < cs_interval_abundance_workspace(n, path)) return CS_ENOMEM;
     const int p = resolve_path(n, path);
-    if (p == CS_PATH_MMA && !device_has_tcgen05()) return CS_EUNSUPPORTED;
+    if ((p == CS_PATH_MMA || p == CS_PATH_MMA4) && !device_has_tcgen05()) return CS_EUNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (fault_injected(CS_FAULT_LAUNCH)) return CS_ECUDA;
     cudaError_t e = clear_status(workspace_dev, st);
-    if (e == cudaSuccess)
-        e = p == CS_PATH_MMA ? launch_count_mma(n, bits_dev, row_words, hist_dev, workspace_dev, st)
-                             : launch_count_popc(n, bits_dev, row_words, hist_dev, workspace_dev, st);
+    if (e == cudaSuccess) e = launch_count(p, n, bits_dev, row_words, hist_dev, workspace_dev, st);
     return from_cuda(e);
 }
 
@@ -161,19 +180,17 @@ int cs_layer_sums(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_
     CS_TRACE("cs_layer_sums");
     if (!valid_n(n) || !bits_dev || !aligned(bits_dev, 128) || !hist_dev || !aligned(hist_dev, 8) ||
         row_words < cs_row_words(n) || row_words % 16 != 0 || !workspace_dev || !aligned(workspace_dev, 256) ||
-        path < CS_PATH_AUTO || path > CS_PATH_MMA || kmax < 0 || kmax > 15 || !layer_dev ||
+        path < CS_PATH_AUTO || path > CS_PATH_MMA4 || kmax < 0 || kmax > 15 || !layer_dev ||
         !aligned(layer_dev, 8) || (phi_dev && !aligned(phi_dev, 8)))
         return CS_EINVAL;
     if (workspace_bytes < cs_interval_abundance_workspace(n, path)) return CS_ENOMEM;
     const int p = resolve_path(n, path);
-    if (p == CS_PATH_MMA && !device_has_tcgen05()) return CS_EUNSUPPORTED;
+    if ((p == CS_PATH_MMA || p == CS_PATH_MMA4) && !device_has_tcgen05()) return CS_EUNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = clear_status(workspace_dev, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(layer_dev, 0, size_t(kmax + 1) * size_t(n) * 8, st);
     if (e == cudaSuccess)
-        e = p == CS_PATH_MMA
-                ? launch_count_mma(n, bits_dev, row_words, hist_dev, workspace_dev, st, phi_dev, layer_dev, kmax)
-                : launch_count_popc(n, bits_dev, row_words, hist_dev, workspace_dev, st, phi_dev, layer_dev, kmax);
+        e = launch_count(p, n, bits_dev, row_words, hist_dev, workspace_dev, st, phi_dev, layer_dev, kmax);
     return from_cuda(e);
 }
 
@@ -224,7 +241,7 @@ int cs_evaluate(int kind, int64_t n, uint64_t seed, const int32_t* coords_host, 
     CS_TRACE("cs_evaluate");
     const int dim = cs_dim(kind);
     if (dim == 0 || !valid_n(n) || n_eps < 0 || n_eps > 16 || (n_eps > 0 && (!eps_host || !actions_host)) ||
-        path < CS_PATH_AUTO || path > CS_PATH_MMA)
+        path < CS_PATH_AUTO || path > CS_PATH_MMA4)
         return CS_EINVAL;
     for (int e = 0; e < n_eps; ++e)
         if (!(eps_host[e] <= 1.0)) return CS_EINVAL;
@@ -319,5 +336,9 @@ const char* cs_strerror(int status) {
 }
 
 const char* cs_version(void) { return "causet-gb300 0.1 (sm_103a)"; }
+
+const char* cs_last_cuda_error(void) {
+    return t_last_cuda == cudaSuccess ? "no error" : cudaGetErrorString(t_last_cuda);
+}
 
 }  // extern "C"

@@ -40,8 +40,8 @@ namespace {
 
 constexpr int kBM = 128;                 // i rows per tile (TMEM lanes)
 constexpr int kBN = 256;                 // j rows per tile (accumulator columns)
-constexpr int kBK = 128;                 // K bytes (FP8 elements) per stage = one swizzle row (128 or 64)
-constexpr int kUK = 32;                  // K per tcgen05.mma of kind::f8f6f4
+constexpr int kBK = 128;                 // K bytes per stage and operand row = one swizzle row (128 or 64)
+constexpr int kUK = 32;                  // K bytes per tcgen05.mma (K32 FP8 or K64 packed FP4)
 constexpr int kStages = 4;
 constexpr int kABytes = kBM * kBK;       // 16 KiB
 constexpr int kBBytes = kBN * kBK;       // 32 KiB
@@ -52,12 +52,42 @@ constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
 constexpr int kEpiChunks = (kBN / 32) / (kEpiWarps / 4);  // 32-column chunks per epilogue warp
 static_assert(kEpiWarps % 4 == 0 && (kBN / 32) % (kEpiWarps / 4) == 0, "epilogue warps split the columns evenly");
-constexpr int kTmemCols = 512;           // two 256-column FP32 accumulators
+constexpr int kTmemCols = 512;           // two 256-column FP32 accumulators, or one and the FP4 scales
 constexpr uint32_t kIdesc = idesc_f8_f32(kBM, kBN);
+constexpr uint32_t kIdesc4 = idesc_mxf4_f32(kBM, kBN);
+constexpr uint32_t kSfCol = 256;         // FP4: scale factors of A at this TMEM column, of B 16 further
+constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;  // four UE8M0 scale factors 2^0 = 1
 constexpr int kRing = 4;                 // items in flight between the roles
 constexpr int kLocalBits = 40;           // ring entry = set << 40 | item within the set; -1 = no more items
 constexpr int kSmemBytes = kStages * kStageBytes + kHistBins * 4 + 256 + 1024;
 constexpr uint8_t kOne = 0x38;           // 1.0 in FP8 E4M3
+
+// Operand formats.  A stage holds one 128-byte swizzle row of K per operand
+// row in both; they differ in how many K elements those bytes carry.
+//   FmtF8: kind::f8f6f4, one E4M3 byte per element, two TMEM accumulators
+//          (the epilogue of one tile overlaps the MMAs of the next).
+//   FmtF4: kind::mxf4 (block-scaled), two E2M1 nibbles per byte (1.0 = 0x2)
+//          with every scale factor 1, so products are again 0 or 1; one
+//          accumulator, because the scale factors take TMEM columns too --
+//          the epilogue copies it to registers and releases it at once.
+// kLayers: the kernel may add d'Alembertian layer sums (kmax >= 0);
+// kSmallSet: it has the branch-free epilogue for sets whose histogram fits
+// in shared memory.  The FP4 kernel holds 64 accumulator values per thread
+// and needs every register for them, so it comes in two builds: counts only
+// (the large sets it is for) and counts with layer sums.
+struct FmtF8 {
+    static constexpr int kKE = kBK;      // K elements per stage
+    static constexpr int kAcc = 2;
+    static constexpr bool kLayers = true, kSmallSet = true;
+};
+struct FmtF4 {
+    static constexpr int kKE = 2 * kBK;
+    static constexpr int kAcc = 1;
+    static constexpr bool kLayers = false, kSmallSet = false;
+};
+struct FmtF4Layers : FmtF4 {
+    static constexpr bool kLayers = true;
+};
 constexpr CUtensorMapSwizzle kSwizzle = kBK == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
 static_assert(kBK == 128 || kBK == 64, "one 128- or 64-byte swizzle row per stage");
 static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "stage buffers stay swizzle-atom aligned");
@@ -78,6 +108,7 @@ struct Item {
     int64_t kb0, kb1;  // K-blocks [kb0, kb1)
 };
 
+template <int KE>
 __device__ __forceinline__ bool decode_item(int64_t t, int64_t nsb, int64_t n, int64_t kblocks, Item& it) {
     const int64_t blk = t / kSlotsPerBlock, slot = t - blk * kSlotsPerBlock;
     const int64_t nbg = (nsb + kRaster - 1) / kRaster;
@@ -93,8 +124,8 @@ __device__ __forceinline__ bool decode_item(int64_t t, int64_t nsb, int64_t n, i
     it.I0 = si * 256 + half * kBM;
     it.J0 = sj * kBN;
     if (it.I0 >= n) return false;
-    it.kb0 = it.I0 / kBK;
-    const int64_t e = (it.J0 + kBN + kBK - 1) / kBK;
+    it.kb0 = it.I0 / KE;
+    const int64_t e = (it.J0 + kBN + KE - 1) / KE;
     it.kb1 = e < kblocks ? e : kblocks;
     return true;
 }
@@ -176,6 +207,70 @@ __global__ void __launch_bounds__(256) k_expand_f8_multi(const MmaSetEntry* __re
     const MmaSetEntry& e = sets[chunk_set[blockIdx.x]];
     const int64_t r0 = (int64_t(blockIdx.x) - e.chunk_begin) * kExpandRows;
     expand_rows(e.bits, e.row_words, e.kpad, e.U, e.L, r0, r0 + kExpandRows < e.n ? r0 + kExpandRows : e.n);
+}
+
+// ------------------------------------------------ packed FP4 operands
+// Bits 0..7 of x -> 8 nibbles of 0x0 / 0x2 (bit b -> nibble b): three
+// shift-and-mask steps move bit groups of 4, 2 and 1 apart (no carries), then
+// the shift by one turns each 1 into 0x2 = 1.0 in E2M1.  Element k of a row
+// sits in byte k/2, low nibble for even k; A and B use the same packing, so
+// every product pairs the same columns whatever nibble order the MMA reads.
+__device__ __forceinline__ uint32_t spread8_e2m1(uint32_t x) {
+    x &= 0xFFu;
+    x = (x | (x << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    x = (x | (x << 3)) & 0x11111111u;
+    return x << 1;
+}
+
+// 32 bits of a bitset row -> 16 operand bytes.
+__device__ __forceinline__ uint4 spread32_e2m1(uint32_t b) {
+    return make_uint4(spread8_e2m1(b), spread8_e2m1(b >> 8), spread8_e2m1(b >> 16), spread8_e2m1(b >> 24));
+}
+
+// The parts of the FP4 operands any tile reads: a K-block holds 256 columns,
+// so the A rows of the tiles at I0 = 128 floor(i / 128) start at column
+// 256 floor(i / 256), and the B rows of the tile at J0 = 256 floor(j / 256)
+// end at J0 + 256.  In 32-column pieces (one 32-bit half of a bitset word,
+// 16 operand bytes).
+__device__ __forceinline__ int64_t u4_first_piece(int64_t i) { return (i / 256) * 8; }
+__device__ __forceinline__ int64_t l4_end_piece(int64_t j) { return (j / 256 + 1) * 8; }
+
+// Row i of the packed U and L (row bytes kpad / 2), pieces handed out to
+// thread t of a team of `size`.
+__device__ __forceinline__ void expand_row_f4(const uint64_t* __restrict__ bits, int64_t row_words, int64_t kpad,
+                                              uint8_t* __restrict__ U, uint8_t* __restrict__ L, int64_t i, int t,
+                                              int size) {
+    const int ppr = int(kpad / 32);
+    const uint32_t* brow = reinterpret_cast<const uint32_t*>(bits + i * row_words);
+    uint4* urow = reinterpret_cast<uint4*>(U + i * (kpad / 2));
+    uint4* lrow = reinterpret_cast<uint4*>(L + i * (kpad / 2));
+    const int ii = int(i);  // n < 2^31
+    for (int c = int(u4_first_piece(i)) + t; c < ppr; c += size) {
+        const int d = ii - 32 * c;  // column i relative to the piece's first column
+        const uint32_t keep = d < 0 ? ~0u : (d >= 31 ? 0u : (~0u << (d + 1)));
+        urow[c] = spread32_e2m1(__ldg(brow + c) & keep);
+    }
+    const int le = int(l4_end_piece(i)) < ppr ? int(l4_end_piece(i)) : ppr;
+    for (int c = t; c < le; c += size) {
+        const int d = ii - 32 * c;
+        const uint32_t keep = d >= 32 ? ~0u : (d <= 0 ? 0u : (1u << d) - 1u);
+        lrow[c] = spread32_e2m1(__ldg(brow + c) & keep);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_expand_f4(const uint64_t* __restrict__ bits, int64_t n, int64_t row_words,
+                                                   int64_t kpad, uint8_t* __restrict__ U, uint8_t* __restrict__ L) {
+    const bool long_rows = kpad / 32 >= 4 * int64_t(blockDim.x);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int64_t r0 = int64_t(blockIdx.x) * kExpandRows; r0 < n; r0 += int64_t(gridDim.x) * kExpandRows) {
+        const int64_t r1 = r0 + kExpandRows < n ? r0 + kExpandRows : n;
+        if (long_rows) {
+            for (int64_t i = r0; i < r1; ++i) expand_row_f4(bits, row_words, kpad, U, L, i, threadIdx.x, blockDim.x);
+        } else {
+            for (int64_t i = r0 + warp; i < r1; i += nw) expand_row_f4(bits, row_words, kpad, U, L, i, lane, 32);
+        }
+    }
 }
 
 int expand_grid(int64_t rows) {
@@ -279,8 +374,9 @@ __device__ __forceinline__ bool epilogue_flush(uint32_t* shist, const MmaView& v
     return epilogue_sync(ebar, phase, hdr, abort);
 }
 
-template <class Src>
+template <class Fmt, class Src>
 __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
+    constexpr bool kF4 = Fmt::kAcc == 1;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes);
@@ -324,6 +420,17 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    if constexpr (kF4) {
+        // Every scale factor the MMAs may read (A at kSfCol, B at kSfCol + 16,
+        // all 128 lanes, 32 columns) is 1; one warp per TMEM lane quarter.
+        if (warp >= 2 && warp < 6) {
+            tmem_st_32x32b_x32_fill(tmem_base + (uint32_t(32 * (warp & 3)) << 16) + kSfCol, kScaleOne);
+            tmem_st_wait();
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------- TMA producer
@@ -358,7 +465,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 v = src.view(sidx);
             }
             Item it;
-            if (!decode_item(local, v.nsb, v.n, v.kblocks, it)) continue;
+            if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
             for (int64_t kb = it.kb0; kb < it.kb1; ++kb) {
                 if (!mbar_wait_or_abort(&empty[s], ph ^ 1u, hdr, abort_flag)) { ok = false; break; }
                 uint8_t* a = smem + s * kStageBytes;
@@ -396,8 +503,8 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 v = src.view(sidx);
             }
             Item it;
-            if (!decode_item(local, v.nsb, v.n, v.kblocks, it)) continue;
-            const uint32_t buf = uint32_t(local_count & 1), bu = uint32_t((local_count >> 1) & 1);
+            if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
+            const uint32_t buf = uint32_t(local_count % Fmt::kAcc), bu = uint32_t((local_count / Fmt::kAcc) & 1);
             ++local_count;
             if (!mbar_wait_or_abort(&tempty[buf], bu ^ 1u, hdr, abort_flag)) break;
             tc_fence_after();
@@ -408,9 +515,14 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 const uint32_t a = smem_u32(smem + s * kStageBytes);
                 const uint64_t adesc = sdesc_k_swizzled(a, kBK), bdesc = sdesc_k_swizzled(a + kABytes, kBK);
 #pragma unroll
-                for (int kk = 0; kk < kBK / kUK; ++kk)
-                    mma_f8f6f4(d, adesc + uint64_t((kk * kUK) >> 4), bdesc + uint64_t((kk * kUK) >> 4), kIdesc,
-                               (kb > it.kb0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < kBK / kUK; ++kk) {
+                    if constexpr (kF4)
+                        mma_mxf4(d, adesc + uint64_t((kk * kUK) >> 4), bdesc + uint64_t((kk * kUK) >> 4), kIdesc4,
+                                 tmem_base + kSfCol, tmem_base + kSfCol + 16, (kb > it.kb0 || kk > 0) ? 1u : 0u);
+                    else
+                        mma_f8f6f4(d, adesc + uint64_t((kk * kUK) >> 4), bdesc + uint64_t((kk * kUK) >> 4), kIdesc,
+                                   (kb > it.kb0 || kk > 0) ? 1u : 0u);
+                }
                 mma_commit(&empty[s]);
                 if (++s == kStages) { s = 0; ph ^= 1u; }
             }
@@ -441,9 +553,9 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 v = src.view(sidx);
             }
             Item it;
-            if (!decode_item(local, v.nsb, v.n, v.kblocks, it)) continue;
+            if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
             const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
-            const uint32_t buf = uint32_t(local_count & 1), use = uint32_t((local_count >> 1) & 1);
+            const uint32_t buf = uint32_t(local_count % Fmt::kAcc), use = uint32_t((local_count / Fmt::kAcc) & 1);
             ++local_count;
             const int64_t i = it.I0 + 32 * q + lane;
             // the C_ij word of this warp's 64 columns, loaded before the wait
@@ -456,43 +568,75 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             // Every count of this set lands in the shared histogram and there
             // are no layer sums: the common case, kept branch-free.
             const bool simple = v.kmax < 0 && v.hist_len <= kHistBins;
-#pragma unroll 1
-            for (int c = c0; c < c0 + kEpiChunks; ++c) {
-                uint32_t r[32];
-                tmem_ld_32x32b_x32(tmem_base + (uint32_t(32 * q) << 16) + buf * kBN + uint32_t(32 * c), r);
-                tmem_ld_wait();
+            // Histogram the 32 counts r of chunk c (columns J0 + 32c ..); index
+            // arithmetic in 32 bits (n <= 2^22).
+            const int ii = int(i), nn = int(v.n), hb32 = int(hb);
+            auto chunk = [&](int c, const uint32_t (&r)[32]) {
                 // pairs to count among these 32 j: C_ij, i < j < n
-                const int64_t jb = it.J0 + 32 * c;
+                const int jb = int(it.J0) + 32 * c;
                 uint32_t m = uint32_t(cw >> (32 * (c & 1)));
-                const int64_t lo = i - jb + 1;  // first u with j > i
+                const int lo = ii - jb + 1;  // first u with j > i
                 m &= lo <= 0 ? ~0u : (lo >= 32 ? 0u : (~0u << lo));
-                const int64_t hi = v.n - jb;    // u < hi keeps j < n
+                const int hi = nn - jb;      // u < hi keeps j < n
                 m &= hi >= 32 ? ~0u : (hi <= 0 ? 0u : ((1u << hi) - 1u));
-                if (m == 0u) continue;
-                if (simple) {
-                    // counts are integers below 2^23: adding 2^23 puts k in the
-                    // low mantissa bits, exactly
+                if (m == 0u) return;
+                // counts are integers below 2^23: adding 2^23 puts k in the
+                // low mantissa bits, exactly
+                if (Fmt::kSmallSet && simple) {
 #pragma unroll
                     for (int u = 0; u < 32; ++u)
                         if ((m >> u) & 1u)
                             red_shared_add(shist_s + 4u * (__float_as_uint(__uint_as_float(r[u]) + 8388608.0f) - 0x4B000000u), 1u);
-                    continue;
+                    return;
+                }
+                if (!Fmt::kLayers || v.kmax < 0) {
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        if ((m >> u) & 1u) {
+                            const int k = int(__float_as_uint(__uint_as_float(r[u]) + 8388608.0f) - 0x4B000000u);
+                            if (k < hb32)
+                                red_shared_add(shist_s + 4u * uint32_t(k), 1u);
+                            else
+                                atomicAdd(&v.hist[k], 1ull);
+                        }
+                    }
+                    return;
                 }
 #pragma unroll
                 for (int u = 0; u < 32; ++u) {
                     if ((m >> u) & 1u) {
-                        const uint32_t k = __float_as_uint(__uint_as_float(r[u]) + 8388608.0f) - 0x4B000000u;
-                        if (int64_t(k) < hb)
-                            red_shared_add(shist_s + 4u * k, 1u);
+                        const int k = int(__float_as_uint(__uint_as_float(r[u]) + 8388608.0f) - 0x4B000000u);
+                        if (k < hb32)
+                            red_shared_add(shist_s + 4u * uint32_t(k), 1u);
                         else
                             atomicAdd(&v.hist[k], 1ull);
-                        if (int(k) <= v.kmax)  // i is in L_{k+1}(j)
-                            atomicAdd(&v.layer[int64_t(k) * v.n + jb + u], v.phi ? __ldg(v.phi + i) : 1.0);
+                        if (k <= v.kmax)  // i is in L_{k+1}(j)
+                            atomicAdd(&v.layer[int64_t(k) * nn + jb + u], v.phi ? __ldg(v.phi + i) : 1.0);
                     }
                 }
+            };
+            if constexpr (kF4) {
+                // The single accumulator goes to registers and is released
+                // before the histogram work, so the next tile's MMAs start at once.
+                uint32_t r0[32], r1[32];
+                tmem_ld_32x32b_x32(tmem_base + (uint32_t(32 * q) << 16) + uint32_t(32 * c0), r0);
+                tmem_ld_32x32b_x32(tmem_base + (uint32_t(32 * q) << 16) + uint32_t(32 * (c0 + 1)), r1);
+                tmem_ld_wait();
+                tc_fence_before();
+                mbar_arrive(&tempty[buf]);
+                chunk(c0, r0);
+                chunk(c0 + 1, r1);
+            } else {
+#pragma unroll 1
+                for (int c = c0; c < c0 + kEpiChunks; ++c) {
+                    uint32_t r[32];
+                    tmem_ld_32x32b_x32(tmem_base + (uint32_t(32 * q) << 16) + buf * kBN + uint32_t(32 * c), r);
+                    tmem_ld_wait();
+                    chunk(c, r);
+                }
+                tc_fence_before();
+                mbar_arrive(&tempty[buf]);
             }
-            tc_fence_before();
-            mbar_arrive(&tempty[buf]);
         }
         if (ok && cur >= 0) epilogue_flush(shist, v, etid, ebar, ephase, hdr, abort_flag);
     }
@@ -510,36 +654,57 @@ __global__ void __launch_bounds__(kThreads, 1)
                 double* layer, int kmax, WsHeader* hdr) {
     const MmaSingle src{MmaView{&mapU, &mapL, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax},
                         nitems};
-    mma_body(src, hdr);
+    mma_body<FmtF8>(src, hdr);
+}
+
+// The same count on packed FP4 operands (kind::mxf4): counts only, and
+// counts with layer sums.
+template <class Fmt>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_count_mma4(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mapL,
+                 const uint64_t* __restrict__ bits, int64_t n, int64_t row_words, int64_t nsb, int64_t nitems,
+                 int64_t kblocks, unsigned long long* __restrict__ hist, int64_t hist_len, const double* phi,
+                 double* layer, int kmax, WsHeader* hdr) {
+    const MmaSingle src{MmaView{&mapU, &mapL, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax},
+                        nitems};
+    mma_body<Fmt>(src, hdr);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_count_mma_multi(const MmaSetEntry* __restrict__ sets, int nsets, int64_t nitems, uintptr_t hist_base,
                       int64_t run, WsHeader* hdr) {
     const MmaMulti src{sets, nsets, nitems, hist_base, run};
-    mma_body(src, hdr);
+    mma_body<FmtF8>(src, hdr);
 }
 
 std::atomic<bool> g_attr_set[64];  // per device: the large-shared-memory attribute is set
 std::atomic<bool> g_attr_multi_set[64];
+std::atomic<bool> g_attr4_set[64];
+std::atomic<bool> g_attr4l_set[64];
 
+// Workspace: header, then U and L, each n rows of `row` bytes holding kpad
+// K elements (one byte each in FP8, two per byte in FP4).
 struct MmaLayout {
-    int64_t kpad;
+    int64_t kpad, row;
     size_t u, l, total;
 };
 
-MmaLayout mma_layout(int64_t n) {
+MmaLayout mma_layout(int64_t n, bool fp4) {
     MmaLayout m;
-    m.kpad = (n + kBK - 1) / kBK * kBK;
+    const int64_t ke = fp4 ? FmtF4::kKE : FmtF8::kKE;
+    m.kpad = (n + ke - 1) / ke * ke;
+    m.row = fp4 ? m.kpad / 2 : m.kpad;
     m.u = sizeof(WsHeader);
-    m.l = align_up(m.u + size_t(n) * size_t(m.kpad), 1024);
-    m.total = align_up(m.l + size_t(n) * size_t(m.kpad), 256);
+    m.l = align_up(m.u + size_t(n) * size_t(m.row), 1024);
+    m.total = align_up(m.l + size_t(n) * size_t(m.row), 256);
     return m;
 }
 
 }  // namespace
 
-size_t mma_workspace_bytes(int64_t n) { return mma_layout(n).total; }
+size_t mma_workspace_bytes(int64_t n) { return mma_layout(n, false).total; }
+
+size_t mma4_workspace_bytes(int64_t n) { return mma_layout(n, true).total; }
 
 int64_t mma_kpad(int64_t n) { return (n + kBK - 1) / kBK * kBK; }
 
@@ -603,44 +768,64 @@ cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* workspace,
-                             cudaStream_t st, const double* phi, double* layer, int kmax) {
+namespace {
+
+template <bool kFp4>
+cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* workspace,
+                                cudaStream_t st, const double* phi, double* layer, int kmax) {
     WsHeader* hdr = static_cast<WsHeader*>(workspace);
     const int64_t hist_len = n > 1 ? n - 1 : 1;
     cudaError_t err = cudaMemsetAsync(hist, 0, size_t(hist_len) * 8, st);
     if (err != cudaSuccess) return err;
     if ((err = cudaMemsetAsync(&hdr->counter, 0, sizeof(hdr->counter), st)) != cudaSuccess) return err;
     if (n < 2) return cudaSuccess;
-    const MmaLayout lay = mma_layout(n);
+    const MmaLayout lay = mma_layout(n, kFp4);
     uint8_t* U = static_cast<uint8_t*>(workspace) + lay.u;
     uint8_t* L = static_cast<uint8_t*>(workspace) + lay.l;
 
-    k_expand_f8<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, U, L);
+    if constexpr (kFp4)
+        k_expand_f4<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, U, L);
+    else
+        k_expand_f8<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, U, L);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
 
     CUtensorMap mapU, mapL;
-    if (encode_tensor_map_2d(&mapU, CU_TENSOR_MAP_DATA_TYPE_UINT8, U, uint64_t(lay.kpad), uint64_t(n),
-                             uint64_t(lay.kpad), kBK, kBM, kSwizzle) != CUDA_SUCCESS ||
-        encode_tensor_map_2d(&mapL, CU_TENSOR_MAP_DATA_TYPE_UINT8, L, uint64_t(lay.kpad), uint64_t(n),
-                             uint64_t(lay.kpad), kBK, kBN, kSwizzle) != CUDA_SUCCESS)
+    if (encode_tensor_map_2d(&mapU, CU_TENSOR_MAP_DATA_TYPE_UINT8, U, uint64_t(lay.row), uint64_t(n),
+                             uint64_t(lay.row), kBK, kBM, kSwizzle) != CUDA_SUCCESS ||
+        encode_tensor_map_2d(&mapL, CU_TENSOR_MAP_DATA_TYPE_UINT8, L, uint64_t(lay.row), uint64_t(n),
+                             uint64_t(lay.row), kBK, kBN, kSwizzle) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
 
+    auto kernel = !kFp4 ? k_count_mma : kmax >= 0 ? k_count_mma4<FmtF4Layers> : k_count_mma4<FmtF4>;
+    std::atomic<bool>* attr = !kFp4 ? g_attr_set : kmax >= 0 ? g_attr4l_set : g_attr4_set;
     int dev = 0;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
-    if (dev >= 0 && dev < 64 && !g_attr_set[dev]) {
-        err = cudaFuncSetAttribute(k_count_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         if (err != cudaSuccess) return err;
-        g_attr_set[dev] = true;
+        attr[dev] = true;
     }
     const int64_t nsb = (n + 255) / 256;
     const int64_t nitems = mma_items(n);
-    const int64_t kblocks = lay.kpad / kBK;
+    const int64_t kblocks = lay.row / kBK;
     int64_t grid = device_sm_count();
     if (grid > nitems) grid = nitems;
-    k_count_mma<<<unsigned(grid), kThreads, kSmemBytes, st>>>(mapU, mapL, bits, n, row_words, nsb, nitems, kblocks,
-                                                              reinterpret_cast<unsigned long long*>(hist), hist_len,
-                                                              phi, layer, kmax, hdr);
+    kernel<<<unsigned(grid), kThreads, kSmemBytes, st>>>(mapU, mapL, bits, n, row_words, nsb, nitems, kblocks,
+                                                         reinterpret_cast<unsigned long long*>(hist), hist_len, phi,
+                                                         layer, kmax, hdr);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* workspace,
+                             cudaStream_t st, const double* phi, double* layer, int kmax) {
+    return launch_count_tensor<false>(n, bits, row_words, hist, workspace, st, phi, layer, kmax);
+}
+
+cudaError_t launch_count_mma4(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* workspace,
+                              cudaStream_t st, const double* phi, double* layer, int kmax) {
+    return launch_count_tensor<true>(n, bits, row_words, hist, workspace, st, phi, layer, kmax);
 }
 
 }  // namespace cs

@@ -79,6 +79,11 @@ cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64
 cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist,
                              void* workspace, cudaStream_t st, const double* phi = nullptr, double* layer = nullptr,
                              int kmax = -1);
+// The single-set count on packed FP4 operands (kind::mxf4, unit scales).
+size_t mma4_workspace_bytes(int64_t n);
+cudaError_t launch_count_mma4(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist,
+                              void* workspace, cudaStream_t st, const double* phi = nullptr, double* layer = nullptr,
+                              int kmax = -1);
 
 // Path chosen for CS_PATH_AUTO at size n.
 int resolve_path(int64_t n, int path);

@@ -139,7 +139,7 @@ def test_auto_path_table_round_trip(cslib):
     try:
         cslib.set_auto_paths([(0, 1), (3000, 2), (50000, 1)])
         assert cslib.get_auto_paths() == [(0, 1), (3000, 2), (50000, 1)]
-        for bad in ([(1, 1)], [(0, 1), (0, 2)], [(0, 3)], [(0, 1), (10, 2), (5, 1)]):
+        for bad in ([(1, 1)], [(0, 1), (0, 2)], [(0, 4)], [(0, 1), (10, 2), (5, 1)]):
             with pytest.raises(cslib.CsError):
                 cslib.set_auto_paths(bad)
         assert cslib.get_auto_paths() == [(0, 1), (3000, 2), (50000, 1)]

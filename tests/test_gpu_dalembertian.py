@@ -33,7 +33,7 @@ def _layers(cs, kind, n, seed, path, kmax, phi=None):
     return b, layer, ph
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 @pytest.mark.parametrize("kind,n", [(0, 300), (0, 2049), (2, 1500), (1, 4096), (3, 2500)])
 def test_layer_sums_exact_for_unit_field(cs, oracle, kind, n, path):
     import torch
@@ -51,7 +51,7 @@ def test_layer_sums_exact_for_unit_field(cs, oracle, kind, n, path):
     assert np.allclose(out.cpu().numpy(), ref, rtol=1e-14, atol=0)
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 def test_layer_sums_general_field(cs, oracle, path):
     import torch
     kind, n = 2, 3000

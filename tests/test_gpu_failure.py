@@ -67,7 +67,7 @@ def test_injected_allocation_failure(cs, oracle):
     assert (hist == oracle.interval_abundance(oracle.causal_matrix(0, c))).all()
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 def test_injected_launch_failure(cs, oracle, path):
     import torch
     n = 1200

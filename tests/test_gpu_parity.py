@@ -58,7 +58,7 @@ def test_sprinkle_and_relate_bit_exact(cs, oracle, kind, n):
     assert (_np_bits(b) == oracle.causal_matrix(kind, want)).all()
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 @pytest.mark.parametrize("kind,n", [(0, 2), (0, 3), (0, 127), (0, 128), (0, 129), (0, 255), (0, 256), (0, 257),
                                     (0, 300), (0, 511), (0, 1000), (0, 1024), (0, 2049), (0, 4133), (1, 129),
                                     (1, 1500), (1, 3001), (2, 200), (2, 1111), (2, 4096), (2, 5000),
@@ -73,7 +73,7 @@ def test_interval_abundance_bit_exact(cs, oracle, kind, n, path):
         assert (want == oracle.interval_abundance_naive(kind, b.coords.cpu().numpy())).all()
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 @pytest.mark.parametrize("n", [4, 130, 1000, 3000])
 def test_chain_antichain_structures(cs, oracle, n, path):
     chain = np.stack([np.arange(n), np.arange(n)]).astype(np.int32)
@@ -92,7 +92,7 @@ def test_chain_antichain_structures(cs, oracle, n, path):
     assert not h3a.hist.cpu().numpy().any()
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 def test_full_chain_131072_counts_exact(cs, path):
     # Every pair related: |A_ij| = j - i - 1 reaches N - 2 = 131070, the
     # largest count the N = 131072 workload can produce (exactness of the
@@ -130,7 +130,9 @@ def test_evaluate_host_buffers(cs, oracle, kind, n):
     d = cs.dim(kind)
     h1, a1, br1 = cs.evaluate(kind, n, seed, None, 1, EPS)          # sprinkled on the device
     h2, a2, br2 = cs.evaluate(kind, n, 0, coords, 1, EPS)           # coordinates from the host
+    h3, a3, br3 = cs.evaluate(kind, n, seed, None, 3, EPS)          # FP4 tensor path
     assert (h1 == want).all() and (h2 == want).all() and br1 == br2
+    assert (h3 == want).all() and br3 == br1 and list(a3) == list(a1)
     for e, eps in enumerate(EPS):
         s_or, _ = oracle.action(d, n, want, eps)
         assert abs(a1[e] - s_or) <= TOL * max(1.0, abs(s_or))
@@ -162,7 +164,7 @@ def test_full_2d_order_1024_exact(cs, oracle):
     assert (h == oracle.interval_abundance_dominance2d(c[1])).all()
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 def test_full_4d_diamond_16384_exact(cs, oracle, path):
     n, seed = 16384, 0xC5E70002
     b = _run(cs, 2, n, seed, path=path)
@@ -202,7 +204,7 @@ def _oracle_2d_full(n, seed):
     return c, o.interval_abundance_dominance2d(c[1]), o.links_2d(c[1]), int(past.sum()), int((past * future).sum())
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 def test_full_2d_order_131072(cs, oracle, path):
     # Full size, bench launch configuration: every N_k against the bitset-free
     # dominance count; also sum_k N_k = R, N_0 = links, and the first moment
@@ -228,15 +230,16 @@ def test_full_2d_order_131072(cs, oracle, path):
     assert (h == h_dom).all()
 
 
-def test_largest_set_262144_mma(cs, oracle):
-    # n = 2^18, the largest 2D order whose tensor-core operands (137 GB) fit
-    # beside its bitset on one GPU: the total and the first moment of N_k from
+@pytest.mark.parametrize("path", [2, 3], ids=["mma", "mma4"])
+def test_largest_set_262144(cs, oracle, path):
+    # n = 2^18, the largest 2D order whose FP8 tensor-core operands (137 GB;
+    # 69 GB in FP4) fit beside its bitset on one GPU: the total and the first moment of N_k from
     # the coordinates (sum_k N_k = R, sum_k k N_k = chains of three), sampled
     # bitset rows from the definition, and a full chain at this size, whose
     # counts run up to n - 2 = 262142.
     import torch
     n, seed = 1 << 18, 0xC5E70007
-    b = _run(cs, 0, n, seed, path=2)
+    b = _run(cs, 0, n, seed, path=path)
     c = oracle.sprinkle(0, n, seed)
     assert (b.coords.cpu().numpy() == c).all()
     v = c[1].astype(np.int64)
@@ -254,11 +257,11 @@ def test_largest_set_262144_mma(cs, oracle):
     del b, bits
     torch.cuda.empty_cache()
     chain = np.stack([np.arange(n), np.arange(n)]).astype(np.int32)
-    hc = _run(cs, 0, n, 0, coords=chain, path=2).hist.cpu().numpy()
+    hc = _run(cs, 0, n, 0, coords=chain, path=path).hist.cpu().numpy()
     assert (hc == np.arange(n - 1, 0, -1)).all()
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 def test_random_kinds_and_sizes(cs, oracle, path):
     # 40 seeded random (kind, n) pairs, n from 1 to 3000: coordinates,
     # bitsets, every N_k and the actions against the oracle.
