@@ -35,6 +35,8 @@ WORKLOADS = {
     "2d_order_131072": (0, 131072, 0xC5E70003, "random 2D order, N=131072 (2.1 GB bitset)"),
     "4d_diamond_16384": (2, 16384, 0xC5E70002, "4D Minkowski diamond, N=16384, int32 grid 2^20"),
     "2d_order_1024": (0, 1024, 0xC5E70001, "random 2D order, N=1024"),
+    # a mid-size order for profiling captures (operands 1 GB in FP4, above L2)
+    "2d_order_32768": (0, 32768, 0xC5E70009, "random 2D order, N=32768"),
 }
 EPS = (0.0, 0.05, 0.1, 0.2)
 PATHS = {"auto": 0, "popc": 1, "mma": 2, "mma4": 3}

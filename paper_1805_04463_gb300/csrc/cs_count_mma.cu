@@ -75,15 +75,23 @@ constexpr uint8_t kOne = 0x38;           // 1.0 in FP8 E4M3
 // in shared memory.  The FP4 kernel holds 64 accumulator values per thread
 // and needs every register for them, so it comes in two builds: counts only
 // (the large sets it is for) and counts with layer sums.
+// kCl: CTAs per cluster.  With 2, the CTAs of a pair take the two 128-row
+// halves of one 256 x 256 supertile; each loads its own A slab and one half
+// of the shared B slab, multicast to both, so a stage costs each SM 32 KiB of
+// L2 reads instead of 48 (the FP4 kernel is otherwise bound by L2 -> SM
+// bandwidth).  Both halves then run the same K range, which needs K-blocks
+// of at least 256 elements (FP4).
 struct FmtF8 {
     static constexpr int kKE = kBK;      // K elements per stage
     static constexpr int kAcc = 2;
     static constexpr bool kLayers = true, kSmallSet = true;
+    static constexpr int kCl = 1;
 };
 struct FmtF4 {
     static constexpr int kKE = 2 * kBK;
     static constexpr int kAcc = 1;
     static constexpr bool kLayers = false, kSmallSet = false;
+    static constexpr int kCl = 2;
 };
 struct FmtF4Layers : FmtF4 {
     static constexpr bool kLayers = true;
@@ -108,7 +116,9 @@ struct Item {
     int64_t kb0, kb1;  // K-blocks [kb0, kb1)
 };
 
-template <int KE>
+// kKeepEmpty: keep a lower half whose rows all lie at or beyond n (a CTA
+// pair must run every supertile in both CTAs; such a tile counts nothing).
+template <int KE, bool kKeepEmpty = false>
 __device__ __forceinline__ bool decode_item(int64_t t, int64_t nsb, int64_t n, int64_t kblocks, Item& it) {
     const int64_t blk = t / kSlotsPerBlock, slot = t - blk * kSlotsPerBlock;
     const int64_t nbg = (nsb + kRaster - 1) / kRaster;
@@ -123,7 +133,7 @@ __device__ __forceinline__ bool decode_item(int64_t t, int64_t nsb, int64_t n, i
     if (si > sj || sj >= nsb) return false;
     it.I0 = si * 256 + half * kBM;
     it.J0 = sj * kBN;
-    if (it.I0 >= n) return false;
+    if (!kKeepEmpty && it.I0 >= n) return false;
     it.kb0 = it.I0 / KE;
     const int64_t e = (it.J0 + kBN + KE - 1) / KE;
     it.kb1 = e < kblocks ? e : kblocks;
@@ -377,6 +387,8 @@ __device__ __forceinline__ bool epilogue_flush(uint32_t* shist, const MmaView& v
 template <class Fmt, class Src>
 __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
     constexpr bool kF4 = Fmt::kAcc == 1;
+    constexpr int kCl = Fmt::kCl;
+    static_assert(kCl == 1 || (kCl == 2 && Fmt::kKE >= kBN), "a CTA pair needs equal K ranges for both halves");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes);
@@ -393,21 +405,24 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t total = src.total();
+    const uint32_t crank = kCl > 1 ? cluster_ctarank() : 0u;
 
     for (int k = tid; k < kHistBins; k += kThreads) shist[k] = 0u;
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], kCl);  // the MMA commits of every CTA of the cluster
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], kEpiThreads);
         }
         mbar_init(ebar, kEpiThreads);
+        // In a pair, rank 0's iempty also counts rank 1's producer, MMA
+        // thread and epilogue threads (rank 1's own iempty is unused).
         for (int r = 0; r < kRing; ++r) {
             mbar_init(&ifull[r], 1);
-            mbar_init(&iempty[r], 1 + kEpiThreads);
+            mbar_init(&iempty[r], kCl == 1 ? 1 + kEpiThreads : 2 * (1 + kEpiThreads) + 1);
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -431,6 +446,26 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         __syncthreads();
         tc_fence_after();
     }
+    // The peer's barriers are initialised before anyone signals them.
+    if constexpr (kCl > 1) cluster_sync();
+
+    // Item ring.  One CTA: the producer publishes each item to its own MMA
+    // and epilogue threads.  A pair: rank 0's producer publishes each
+    // supertile to both CTAs (its own slot and, through the cluster window,
+    // rank 1's) and every consumer of either CTA -- rank 1's producer too --
+    // releases the slot on rank 0's iempty.  A ring entry is
+    // set << kLocalBits | unit; a CTA's item is unit * kCl + its rank.
+    const uint32_t iempty0 = kCl > 1 ? cluster_map(iempty, 0) : 0u;
+    auto ring_wait = [&](uint32_t slot, uint32_t use) {
+        return mbar_wait_or_abort<(kCl > 1)>(&ifull[slot], use, hdr, abort_flag);
+    };
+    auto ring_release = [&](uint32_t slot) {
+        if (kCl > 1 && crank != 0)
+            mbar_arrive_cluster(iempty0 + 8u * slot, 1u);
+        else
+            mbar_arrive(&iempty[slot]);
+    };
+    constexpr int64_t kUnitMask = (int64_t(1) << kLocalBits) - 1;
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------- TMA producer
@@ -441,37 +476,56 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         bool ok = true;
         int cur = -1;
         MmaView v{};
-        int64_t next = 0, end = 0;  // the current run of items from the queue
+        int64_t next = 0, end = 0;  // the current run of units from the queue
+        const int64_t units = total / kCl;
         for (uint32_t q = 0; ok; ++q) {
             const uint32_t slot = q % kRing, use = (q / kRing) & 1u;
-            if (!mbar_wait_or_abort(&iempty[slot], use ^ 1u, hdr, abort_flag)) { ok = false; break; }
-            if (next >= end) {
-                next = int64_t(atomicAdd(&hdr->counter, 1ull)) * src.chunk();
-                end = next + src.chunk();
-            }
-            const int64_t t = next++;
-            if (t >= total) {
-                ring[slot] = -1;
+            int64_t e;
+            if (kCl == 1 || crank == 0) {
+                if (!mbar_wait_or_abort<(kCl > 1)>(&iempty[slot], use ^ 1u, hdr, abort_flag)) { ok = false; break; }
+                if (next >= end) {
+                    next = int64_t(atomicAdd(&hdr->counter, 1ull)) * src.chunk();
+                    end = next + src.chunk();
+                }
+                const int64_t t = next++;
+                if (t >= units) {
+                    e = -1;
+                } else {
+                    // the producer alone finds the unit's set and hands it on
+                    int64_t lu;
+                    const int sidx = src.set_of(t, lu, cur);
+                    e = (int64_t(sidx) << kLocalBits) | lu;
+                }
+                ring[slot] = e;
                 mbar_arrive(&ifull[slot]);
-                break;
+                if constexpr (kCl > 1) {
+                    st_cluster_s64(cluster_map(const_cast<int64_t*>(&ring[slot]), 1), e);
+                    mbar_arrive_cluster(cluster_map(&ifull[slot], 1), 1u);
+                }
+            } else {
+                if (!ring_wait(slot, use)) { ok = false; break; }
+                e = ring[slot];
+                ring_release(slot);
             }
-            // the producer alone finds the item's set and hands it on
-            int64_t local;
-            const int sidx = src.set_of(t, local, cur);
-            ring[slot] = (int64_t(sidx) << kLocalBits) | local;
-            mbar_arrive(&ifull[slot]);
+            if (e < 0) break;
+            const int sidx = int(e >> kLocalBits);
+            const int64_t local = (e & kUnitMask) * kCl + crank;
             if (sidx != cur) {
                 cur = sidx;
                 v = src.view(sidx);
             }
             Item it;
-            if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
+            if (!decode_item<Fmt::kKE, (kCl > 1)>(local, v.nsb, v.n, v.kblocks, it)) continue;
             for (int64_t kb = it.kb0; kb < it.kb1; ++kb) {
                 if (!mbar_wait_or_abort(&empty[s], ph ^ 1u, hdr, abort_flag)) { ok = false; break; }
                 uint8_t* a = smem + s * kStageBytes;
-                mbar_arrive_expect_tx(&full[s], kStageBytes);
+                mbar_arrive_expect_tx(&full[s], kStageBytes);  // in a pair: own A, both B halves
                 tma_load_2d(a, v.mapU, int32_t(kb * kBK), int32_t(it.I0), &full[s]);
-                tma_load_2d(a + kABytes, v.mapL, int32_t(kb * kBK), int32_t(it.J0), &full[s]);
+                if constexpr (kCl > 1)
+                    tma_load_2d_mc(a + kABytes + crank * (kBBytes / kCl), v.mapL, int32_t(kb * kBK),
+                                   int32_t(it.J0 + crank * (kBN / kCl)), &full[s], uint16_t((1u << kCl) - 1u));
+                else
+                    tma_load_2d(a + kABytes, v.mapL, int32_t(kb * kBK), int32_t(it.J0), &full[s]);
                 ++issued;
                 if (++s == kStages) { s = 0; ph ^= 1u; }
             }
@@ -483,6 +537,15 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 mbar_wait_bounded(&full[g % kStages], (g / kStages) & 1u, hdr);
             }
         }
+        if constexpr (kCl > 1) {
+            // Every stage is released by the MMA commits of both CTAs; wait
+            // for the last ones, so that no arrival is still on its way to
+            // this CTA when it leaves (shorter limit once aborted).
+            for (int k = 0; k < kStages; ++k) {
+                mbar_wait_bounded(&empty[s], ph ^ 1u, hdr, ok ? kWaitLimitNs : kWaitLimitNs / 40);
+                if (++s == kStages) { s = 0; ph ^= 1u; }
+            }
+        }
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------------- MMA issuer
         uint32_t s = 0, ph = 0;
@@ -492,18 +555,18 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         MmaView v{};
         for (uint32_t q = 0; ok; ++q) {
             const uint32_t slot = q % kRing, use = (q / kRing) & 1u;
-            if (!mbar_wait_or_abort(&ifull[slot], use, hdr, abort_flag)) break;
+            if (!ring_wait(slot, use)) break;
             const int64_t e = ring[slot];
-            mbar_arrive(&iempty[slot]);
+            ring_release(slot);
             if (e < 0) break;
             const int sidx = int(e >> kLocalBits);
-            const int64_t local = e & ((int64_t(1) << kLocalBits) - 1);
+            const int64_t local = (e & kUnitMask) * kCl + crank;
             if (sidx != cur) {
                 cur = sidx;
                 v = src.view(sidx);
             }
             Item it;
-            if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
+            if (!decode_item<Fmt::kKE, (kCl > 1)>(local, v.nsb, v.n, v.kblocks, it)) continue;
             const uint32_t buf = uint32_t(local_count % Fmt::kAcc), bu = uint32_t((local_count / Fmt::kAcc) & 1);
             ++local_count;
             if (!mbar_wait_or_abort(&tempty[buf], bu ^ 1u, hdr, abort_flag)) break;
@@ -523,7 +586,10 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                         mma_f8f6f4(d, adesc + uint64_t((kk * kUK) >> 4), bdesc + uint64_t((kk * kUK) >> 4), kIdesc,
                                    (kb > it.kb0 || kk > 0) ? 1u : 0u);
                 }
-                mma_commit(&empty[s]);
+                if constexpr (kCl > 1)
+                    mma_commit_mc(&empty[s], uint16_t((1u << kCl) - 1u));  // the stage is free in both CTAs
+                else
+                    mma_commit(&empty[s]);
                 if (++s == kStages) { s = 0; ph ^= 1u; }
             }
             if (ok) mma_commit(&tfull[buf]);
@@ -541,19 +607,19 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         MmaView v{};
         for (uint32_t qi = 0; ok; ++qi) {
             const uint32_t slot = qi % kRing, ru = (qi / kRing) & 1u;
-            if (!mbar_wait_or_abort(&ifull[slot], ru, hdr, abort_flag)) { ok = false; break; }
+            if (!ring_wait(slot, ru)) { ok = false; break; }
             const int64_t e = ring[slot];
-            mbar_arrive(&iempty[slot]);
+            ring_release(slot);
             if (e < 0) break;
             const int sidx = int(e >> kLocalBits);
-            const int64_t local = e & ((int64_t(1) << kLocalBits) - 1);
+            const int64_t local = (e & kUnitMask) * kCl + crank;
             if (sidx != cur) {
                 if (cur >= 0 && !epilogue_flush(shist, v, etid, ebar, ephase, hdr, abort_flag)) { ok = false; break; }
                 cur = sidx;
                 v = src.view(sidx);
             }
             Item it;
-            if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
+            if (!decode_item<Fmt::kKE, (kCl > 1)>(local, v.nsb, v.n, v.kblocks, it)) continue;
             const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
             const uint32_t buf = uint32_t(local_count % Fmt::kAcc), use = uint32_t((local_count / Fmt::kAcc) & 1);
             ++local_count;
@@ -589,18 +655,22 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                             red_shared_add(shist_s + 4u * (__float_as_uint(__uint_as_float(r[u]) + 8388608.0f) - 0x4B000000u), 1u);
                     return;
                 }
-                if (!Fmt::kLayers || v.kmax < 0) {
+                if constexpr (Fmt::kLayers) {
+                    if (v.kmax >= 0) {
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) {
-                        if ((m >> u) & 1u) {
-                            const int k = int(__float_as_uint(__uint_as_float(r[u]) + 8388608.0f) - 0x4B000000u);
-                            if (k < hb32)
-                                red_shared_add(shist_s + 4u * uint32_t(k), 1u);
-                            else
-                                atomicAdd(&v.hist[k], 1ull);
+                        for (int u = 0; u < 32; ++u) {
+                            if ((m >> u) & 1u) {
+                                const int k = int(__float_as_uint(__uint_as_float(r[u]) + 8388608.0f) - 0x4B000000u);
+                                if (k < hb32)
+                                    red_shared_add(shist_s + 4u * uint32_t(k), 1u);
+                                else
+                                    atomicAdd(&v.hist[k], 1ull);
+                                if (k <= v.kmax)  // i is in L_{k+1}(j)
+                                    atomicAdd(&v.layer[int64_t(k) * nn + jb + u], v.phi ? __ldg(v.phi + i) : 1.0);
+                            }
                         }
+                        return;
                     }
-                    return;
                 }
 #pragma unroll
                 for (int u = 0; u < 32; ++u) {
@@ -610,8 +680,6 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                             red_shared_add(shist_s + 4u * uint32_t(k), 1u);
                         else
                             atomicAdd(&v.hist[k], 1ull);
-                        if (k <= v.kmax)  // i is in L_{k+1}(j)
-                            atomicAdd(&v.layer[int64_t(k) * nn + jb + u], v.phi ? __ldg(v.phi + i) : 1.0);
                     }
                 }
             };
@@ -641,6 +709,8 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         if (ok && cur >= 0) epilogue_flush(shist, v, etid, ebar, ephase, hdr, abort_flag);
     }
     __syncthreads();
+    // No CTA of a pair leaves while the other may still signal it.
+    if constexpr (kCl > 1) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, kTmemCols);
@@ -681,6 +751,8 @@ std::atomic<bool> g_attr_set[64];  // per device: the large-shared-memory attrib
 std::atomic<bool> g_attr_multi_set[64];
 std::atomic<bool> g_attr4_set[64];
 std::atomic<bool> g_attr4l_set[64];
+std::atomic<int> g_clusters4[64];   // per device: CTA pairs of the FP4 kernels resident at once (0 = not queried)
+std::atomic<int> g_clusters4l[64];
 
 // Workspace: header, then U and L, each n rows of `row` bytes holding kpad
 // K elements (one byte each in FP8, two per byte in FP4).
@@ -789,18 +861,21 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
         k_expand_f8<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, U, L);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
 
+    // The B box is a whole 256-row slab, or in a CTA pair the half each CTA loads.
+    constexpr int kCl = kFp4 ? FmtF4::kCl : FmtF8::kCl;
     CUtensorMap mapU, mapL;
     if (encode_tensor_map_2d(&mapU, CU_TENSOR_MAP_DATA_TYPE_UINT8, U, uint64_t(lay.row), uint64_t(n),
                              uint64_t(lay.row), kBK, kBM, kSwizzle) != CUDA_SUCCESS ||
         encode_tensor_map_2d(&mapL, CU_TENSOR_MAP_DATA_TYPE_UINT8, L, uint64_t(lay.row), uint64_t(n),
-                             uint64_t(lay.row), kBK, kBN, kSwizzle) != CUDA_SUCCESS)
+                             uint64_t(lay.row), kBK, kBN / kCl, kSwizzle) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
 
     auto kernel = !kFp4 ? k_count_mma : kmax >= 0 ? k_count_mma4<FmtF4Layers> : k_count_mma4<FmtF4>;
     std::atomic<bool>* attr = !kFp4 ? g_attr_set : kmax >= 0 ? g_attr4l_set : g_attr4_set;
     int dev = 0;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
-    if (dev >= 0 && dev < 64 && !attr[dev]) {
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
         err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         if (err != cudaSuccess) return err;
         attr[dev] = true;
@@ -808,12 +883,39 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
     const int64_t nsb = (n + 255) / 256;
     const int64_t nitems = mma_items(n);
     const int64_t kblocks = lay.row / kBK;
-    int64_t grid = device_sm_count();
-    if (grid > nitems) grid = nitems;
-    kernel<<<unsigned(grid), kThreads, kSmemBytes, st>>>(mapU, mapL, bits, n, row_words, nsb, nitems, kblocks,
-                                                         reinterpret_cast<unsigned long long*>(hist), hist_len, phi,
-                                                         layer, kmax, hdr);
-    return cudaGetLastError();
+    unsigned long long* h = reinterpret_cast<unsigned long long*>(hist);
+    if constexpr (kCl == 1) {
+        int64_t grid = device_sm_count();
+        if (grid > nitems) grid = nitems;
+        kernel<<<unsigned(grid), kThreads, kSmemBytes, st>>>(mapU, mapL, bits, n, row_words, nsb, nitems, kblocks, h,
+                                                             hist_len, phi, layer, kmax, hdr);
+        return cudaGetLastError();
+    } else {
+        // Persistent grid of CTA pairs: as many clusters as fit at once.
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kCl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(device_sm_count() / kCl * kCl));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = kSmemBytes;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        std::atomic<int>* cached = kmax >= 0 ? g_clusters4l : g_clusters4;
+        int clusters = cached[dev];
+        if (clusters == 0) {
+            if ((err = cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg)) != cudaSuccess) return err;
+            if (clusters < 1) return cudaErrorNotSupported;
+            cached[dev] = clusters;
+        }
+        const int64_t units = nitems / kCl;
+        cfg.gridDim = dim3(unsigned((clusters < units ? clusters : units) * kCl));
+        return cudaLaunchKernelEx(&cfg, kernel, mapU, mapL, bits, n, row_words, nsb, nitems, kblocks, h, hist_len,
+                                  phi, layer, kmax, hdr);
+    }
 }
 
 }  // namespace

@@ -142,14 +142,75 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* m
         : "memory");
 }
 
+// ------------------------------------------------ thread-block clusters
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// All threads of every CTA of the cluster; orders the memory operations
+// before it (local and remote shared memory, mbarrier arrivals) before those
+// after it.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The shared::cluster address of the same shared-memory offset in CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_map(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_cluster_s64(uint32_t caddr, int64_t v) {
+    asm volatile("st.shared::cluster.s64 [%0], %1;" ::"r"(caddr), "l"(v) : "memory");
+}
+
+// `count` arrivals on an mbarrier anywhere in the cluster, release at
+// cluster scope (orders this thread's earlier accesses before them).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr, uint32_t count) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(caddr), "r"(count)
+                 : "memory");
+}
+
+// try_wait with acquire at cluster scope: for phases completed by arrivals
+// of other CTAs whose earlier shared-memory writes must be visible.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 2D tiled TMA load multicast to the CTAs of `mask`: the box lands at the same
+// shared-memory offset in each, and each one's mbarrier at `bar`'s offset
+// receives the byte count.
+__device__ __forceinline__ void tma_load_2d_mc(void* smem_dst, const CUtensorMap* map, int32_t x, int32_t y,
+                                               uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
+        "[%0], [%1, {%2, %3}], [%4], %5;"
+        ::"r"(smem_u32(smem_dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
 // Wait like mbar_wait_bounded, but also give up early once another warp of
 // the CTA has raised *abort (set after its own wait timed out).
+// kCluster: acquire at cluster scope (phases completed by other CTAs).
+template <bool kCluster = false>
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, WsHeader* h,
                                                    volatile int* abort) {
-    if (mbar_try_wait(bar, parity)) return true;
+    auto ready = [&] { return kCluster ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity); };
+    if (ready()) return true;
     const unsigned long long t0 = global_timer_ns();
     for (uint32_t spin = 0;; ++spin) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (ready()) return true;
         if ((spin & 63u) == 0u) {
             if (*abort) return false;
             if (global_timer_ns() - t0 > kWaitLimitNs) {
@@ -257,6 +318,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
                  : "memory");
+}
+
+// The same arrival on the mbarrier at `bar`'s offset in every CTA of `mask`.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
 }
 
 // Each lane reads 32 consecutive 32-bit columns of its TMEM lane.
