@@ -75,23 +75,26 @@ constexpr uint8_t kOne = 0x38;           // 1.0 in FP8 E4M3
 // in shared memory.  The FP4 kernel holds 64 accumulator values per thread
 // and needs every register for them, so it comes in two builds: counts only
 // (the large sets it is for) and counts with layer sums.
-// kCl: CTAs per cluster.  With 2, the CTAs of a pair take the two 128-row
-// halves of one 256 x 256 supertile; each loads its own A slab and one half
-// of the shared B slab, multicast to both, so a stage costs each SM 32 KiB of
-// L2 reads instead of 48 (the FP4 kernel is otherwise bound by L2 -> SM
-// bandwidth).  Both halves then run the same K range, which needs K-blocks
-// of at least 256 elements (FP4).
+// kPair: a CTA pair (a cluster of two) runs each 256 x 256 supertile as one
+// 2-SM MMA (tcgen05 cta_group::2, M = 256): CTA r loads A rows 128r.. and B
+// rows 128r.. of the supertile into its own shared memory, rank 0 issues
+// the MMAs, which read both CTAs' halves, and each CTA's TMEM receives its
+// 128 accumulator rows.  A stage then costs each SM 32 KiB (16 of A, 16 of
+// B) for the multiply-adds that take 48 KiB on one SM: the single-SM
+// kernels are bound by shared-memory traffic per MAC (TMA writes plus
+// tensor-core reads), and six stages fit instead of four.  Both halves run
+// the same K range, which wastes nothing when K-blocks hold 256 elements.
 struct FmtF8 {
     static constexpr int kKE = kBK;      // K elements per stage
     static constexpr int kAcc = 2;
-    static constexpr bool kLayers = true, kSmallSet = true;
-    static constexpr int kCl = 1;
+    static constexpr bool kLayers = true, kSmallSet = true, kPair = false;
+    static constexpr int kStages = 4;
 };
 struct FmtF4 {
     static constexpr int kKE = 2 * kBK;
     static constexpr int kAcc = 1;
-    static constexpr bool kLayers = false, kSmallSet = false;
-    static constexpr int kCl = 2;
+    static constexpr bool kLayers = false, kSmallSet = false, kPair = true;
+    static constexpr int kStages = 6;
 };
 struct FmtF4Layers : FmtF4 {
     static constexpr bool kLayers = true;
@@ -116,9 +119,7 @@ struct Item {
     int64_t kb0, kb1;  // K-blocks [kb0, kb1)
 };
 
-// kKeepEmpty: keep a lower half whose rows all lie at or beyond n (a CTA
-// pair must run every supertile in both CTAs; such a tile counts nothing).
-template <int KE, bool kKeepEmpty = false>
+template <int KE>
 __device__ __forceinline__ bool decode_item(int64_t t, int64_t nsb, int64_t n, int64_t kblocks, Item& it) {
     const int64_t blk = t / kSlotsPerBlock, slot = t - blk * kSlotsPerBlock;
     const int64_t nbg = (nsb + kRaster - 1) / kRaster;
@@ -133,7 +134,7 @@ __device__ __forceinline__ bool decode_item(int64_t t, int64_t nsb, int64_t n, i
     if (si > sj || sj >= nsb) return false;
     it.I0 = si * 256 + half * kBM;
     it.J0 = sj * kBN;
-    if (!kKeepEmpty && it.I0 >= n) return false;
+    if (it.I0 >= n) return false;
     it.kb0 = it.I0 / KE;
     const int64_t e = (it.J0 + kBN + KE - 1) / KE;
     it.kb1 = e < kblocks ? e : kblocks;
@@ -387,49 +388,63 @@ __device__ __forceinline__ bool epilogue_flush(uint32_t* shist, const MmaView& v
 template <class Fmt, class Src>
 __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
     constexpr bool kF4 = Fmt::kAcc == 1;
-    constexpr int kCl = Fmt::kCl;
-    static_assert(kCl == 1 || (kCl == 2 && Fmt::kKE >= kBN), "a CTA pair needs equal K ranges for both halves");
+    constexpr bool kPair = Fmt::kPair;
+    constexpr int kCl = kPair ? 2 : 1;                        // CTAs per cluster
+    constexpr int kNS = Fmt::kStages;
+    constexpr int kBRows = kPair ? kBN / 2 : kBN;             // B rows each CTA holds per stage
+    constexpr int kSB = kABytes + kBRows * kBK;               // stage bytes per CTA
+    constexpr int kMmaM = kPair ? 2 * kBM : kBM;
+    static_assert(kNS * kSB <= kStages * kStageBytes, "the stages fit the shared-memory carve-out");
+    static_assert(kSB % 1024 == 0, "stage buffers stay swizzle-atom aligned");
+    static_assert(!kPair || Fmt::kKE >= kBN, "both halves of a pair run the same K range");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes);
     uint64_t* full = reinterpret_cast<uint64_t*>(shist + kHistBins);
-    uint64_t* empty = full + kStages;
-    uint64_t* tfull = empty + kStages;
+    uint64_t* empty = full + kNS;
+    uint64_t* tfull = empty + kNS;
     uint64_t* tempty = tfull + 2;
     uint64_t* ebar = tempty + 2;
     uint64_t* ifull = ebar + 1;         // item ring: slot published by the producer
-    uint64_t* iempty = ifull + kRing;   // item ring: slot read by the MMA thread and all epilogue threads
+    uint64_t* iempty = ifull + kRing;   // item ring: slot read by its consumers
     volatile int64_t* ring = reinterpret_cast<volatile int64_t*>(iempty + kRing);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(const_cast<int64_t*>(ring) + kRing);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    static_assert((2 * kNS + 5 + 2 * kRing) * 8 + kRing * 8 + 8 <= 256, "barriers fit their 256 bytes");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t total = src.total();
-    const uint32_t crank = kCl > 1 ? cluster_ctarank() : 0u;
+    const uint32_t crank = kPair ? cluster_ctarank() : 0u;
+    const bool leader = crank == 0;
 
     for (int k = tid; k < kHistBins; k += kThreads) shist[k] = 0u;
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kCl);  // the MMA commits of every CTA of the cluster
+        for (int s = 0; s < kNS; ++s) {
+            mbar_init(&full[s], 1);   // pair: rank 0's receives both CTAs' bytes
+            mbar_init(&empty[s], 1);  // the MMA commit (pair: rank 0's, multicast to both)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], kEpiThreads);
+            mbar_init(&tempty[b], kCl * kEpiThreads);  // pair: both CTAs' epilogues, on rank 0
         }
         mbar_init(ebar, kEpiThreads);
-        // In a pair, rank 0's iempty also counts rank 1's producer, MMA
-        // thread and epilogue threads (rank 1's own iempty is unused).
+        // Pair: rank 0's iempty counts its MMA thread and epilogue and rank
+        // 1's producer and epilogue (rank 1's own iempty is unused).
         for (int r = 0; r < kRing; ++r) {
             mbar_init(&ifull[r], 1);
-            mbar_init(&iempty[r], kCl == 1 ? 1 + kEpiThreads : 2 * (1 + kEpiThreads) + 1);
+            mbar_init(&iempty[r], kPair ? 2 * (1 + kEpiThreads) : 1 + kEpiThreads);
         }
         *abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, kTmemCols);
-        tmem_relinquish();
+        if constexpr (kPair) {
+            tmem_alloc_pair(tmem_slot, kTmemCols);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(tmem_slot, kTmemCols);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -446,32 +461,36 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         __syncthreads();
         tc_fence_after();
     }
-    // The peer's barriers are initialised before anyone signals them.
-    if constexpr (kCl > 1) cluster_sync();
+    // The peer's barriers and TMEM are ready before anyone signals them.
+    if constexpr (kPair) cluster_sync();
 
     // Item ring.  One CTA: the producer publishes each item to its own MMA
     // and epilogue threads.  A pair: rank 0's producer publishes each
     // supertile to both CTAs (its own slot and, through the cluster window,
-    // rank 1's) and every consumer of either CTA -- rank 1's producer too --
+    // rank 1's), and every consumer of either CTA -- rank 1's producer too --
     // releases the slot on rank 0's iempty.  A ring entry is
-    // set << kLocalBits | unit; a CTA's item is unit * kCl + its rank.
-    const uint32_t iempty0 = kCl > 1 ? cluster_map(iempty, 0) : 0u;
+    // set << kLocalBits | unit; the unit is an item (one CTA) or a supertile
+    // (a pair, which runs it as item 2 * unit, its upper half's index).
+    const uint32_t iempty0 = kPair ? cluster_map(iempty, 0) : 0u;
+    const uint32_t tempty0 = kPair ? cluster_map(tempty, 0) : 0u;
     auto ring_wait = [&](uint32_t slot, uint32_t use) {
-        return mbar_wait_or_abort<(kCl > 1)>(&ifull[slot], use, hdr, abort_flag);
+        return mbar_wait_or_abort<kPair>(&ifull[slot], use, hdr, abort_flag);
     };
     auto ring_release = [&](uint32_t slot) {
-        if (kCl > 1 && crank != 0)
+        if (kPair && !leader)
             mbar_arrive_cluster(iempty0 + 8u * slot, 1u);
         else
             mbar_arrive(&iempty[slot]);
     };
     constexpr int64_t kUnitMask = (int64_t(1) << kLocalBits) - 1;
+    // This CTA's first A row and B row within an item.
+    const int64_t row_off = kPair ? int64_t(crank) * kBM : 0;
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------- TMA producer
-        // Pulls items from the global queue (consecutive indices are
+        // Pulls units from the global queue (consecutive indices are
         // raster-local, so the CTAs running at any moment share operand
-        // panels in L2) and publishes each index to the other roles.
+        // panels in L2) and publishes each to the other roles.
         uint32_t s = 0, ph = 0, issued = 0;
         bool ok = true;
         int cur = -1;
@@ -481,8 +500,8 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         for (uint32_t q = 0; ok; ++q) {
             const uint32_t slot = q % kRing, use = (q / kRing) & 1u;
             int64_t e;
-            if (kCl == 1 || crank == 0) {
-                if (!mbar_wait_or_abort<(kCl > 1)>(&iempty[slot], use ^ 1u, hdr, abort_flag)) { ok = false; break; }
+            if (leader) {
+                if (!mbar_wait_or_abort<kPair>(&iempty[slot], use ^ 1u, hdr, abort_flag)) { ok = false; break; }
                 if (next >= end) {
                     next = int64_t(atomicAdd(&hdr->counter, 1ull)) * src.chunk();
                     end = next + src.chunk();
@@ -498,7 +517,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 }
                 ring[slot] = e;
                 mbar_arrive(&ifull[slot]);
-                if constexpr (kCl > 1) {
+                if constexpr (kPair) {
                     st_cluster_s64(cluster_map(const_cast<int64_t*>(&ring[slot]), 1), e);
                     mbar_arrive_cluster(cluster_map(&ifull[slot], 1), 1u);
                 }
@@ -509,45 +528,51 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             }
             if (e < 0) break;
             const int sidx = int(e >> kLocalBits);
-            const int64_t local = (e & kUnitMask) * kCl + crank;
+            const int64_t local = (e & kUnitMask) * kCl;
             if (sidx != cur) {
                 cur = sidx;
                 v = src.view(sidx);
             }
             Item it;
-            if (!decode_item<Fmt::kKE, (kCl > 1)>(local, v.nsb, v.n, v.kblocks, it)) continue;
+            if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
             for (int64_t kb = it.kb0; kb < it.kb1; ++kb) {
                 if (!mbar_wait_or_abort(&empty[s], ph ^ 1u, hdr, abort_flag)) { ok = false; break; }
-                uint8_t* a = smem + s * kStageBytes;
-                mbar_arrive_expect_tx(&full[s], kStageBytes);  // in a pair: own A, both B halves
-                tma_load_2d(a, v.mapU, int32_t(kb * kBK), int32_t(it.I0), &full[s]);
-                if constexpr (kCl > 1)
-                    tma_load_2d_mc(a + kABytes + crank * (kBBytes / kCl), v.mapL, int32_t(kb * kBK),
-                                   int32_t(it.J0 + crank * (kBN / kCl)), &full[s], uint16_t((1u << kCl) - 1u));
-                else
+                uint8_t* a = smem + s * kSB;
+                if constexpr (kPair) {
+                    // Both CTAs' bytes land on rank 0's full barrier.
+                    const uint32_t fb = cluster_map(&full[s], 0);
+                    if (leader) mbar_arrive_expect_tx(&full[s], 2 * kSB);
+                    tma_load_2d_pair(a, v.mapU, int32_t(kb * kBK), int32_t(it.I0 + row_off), fb);
+                    tma_load_2d_pair(a + kABytes, v.mapL, int32_t(kb * kBK), int32_t(it.J0 + row_off), fb);
+                } else {
+                    mbar_arrive_expect_tx(&full[s], kSB);
+                    tma_load_2d(a, v.mapU, int32_t(kb * kBK), int32_t(it.I0), &full[s]);
                     tma_load_2d(a + kABytes, v.mapL, int32_t(kb * kBK), int32_t(it.J0), &full[s]);
+                }
                 ++issued;
-                if (++s == kStages) { s = 0; ph ^= 1u; }
+                if (++s == kNS) { s = 0; ph ^= 1u; }
             }
         }
-        if (!ok) {
+        if (!ok && (!kPair || leader)) {
             // Let the copies still in flight land before shared memory goes away.
-            for (uint32_t q = 0; q < kStages && q < issued; ++q) {
+            for (uint32_t q = 0; q < kNS && q < issued; ++q) {
                 const uint32_t g = issued - 1 - q;
-                mbar_wait_bounded(&full[g % kStages], (g / kStages) & 1u, hdr);
+                mbar_wait_bounded(&full[g % kNS], (g / kNS) & 1u, hdr);
             }
         }
-        if constexpr (kCl > 1) {
-            // Every stage is released by the MMA commits of both CTAs; wait
-            // for the last ones, so that no arrival is still on its way to
-            // this CTA when it leaves (shorter limit once aborted).
-            for (int k = 0; k < kStages; ++k) {
+        if constexpr (kPair) {
+            // Each stage is released by the pair's MMA commit, which lands in
+            // both CTAs; wait for the last ones (their data has landed by
+            // then), so that nothing is still on its way to this CTA when it
+            // leaves (shorter limit once aborted).
+            for (int k = 0; k < kNS; ++k) {
                 mbar_wait_bounded(&empty[s], ph ^ 1u, hdr, ok ? kWaitLimitNs : kWaitLimitNs / 40);
-                if (++s == kStages) { s = 0; ph ^= 1u; }
+                if (++s == kNS) { s = 0; ph ^= 1u; }
             }
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 1 && lane == 0 && leader) {
         // ---------------------------------------------------- MMA issuer
+        // (a pair: rank 0's, for both CTAs)
         uint32_t s = 0, ph = 0;
         int64_t local_count = 0;
         bool ok = true;
@@ -560,39 +585,47 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             ring_release(slot);
             if (e < 0) break;
             const int sidx = int(e >> kLocalBits);
-            const int64_t local = (e & kUnitMask) * kCl + crank;
+            const int64_t local = (e & kUnitMask) * kCl;
             if (sidx != cur) {
                 cur = sidx;
                 v = src.view(sidx);
             }
             Item it;
-            if (!decode_item<Fmt::kKE, (kCl > 1)>(local, v.nsb, v.n, v.kblocks, it)) continue;
+            if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
             const uint32_t buf = uint32_t(local_count % Fmt::kAcc), bu = uint32_t((local_count / Fmt::kAcc) & 1);
             ++local_count;
-            if (!mbar_wait_or_abort(&tempty[buf], bu ^ 1u, hdr, abort_flag)) break;
+            if (!mbar_wait_or_abort<kPair>(&tempty[buf], bu ^ 1u, hdr, abort_flag)) break;
             tc_fence_after();
             const uint32_t d = tmem_base + buf * kBN;
             for (int64_t kb = it.kb0; kb < it.kb1; ++kb) {
-                if (!mbar_wait_or_abort(&full[s], ph, hdr, abort_flag)) { ok = false; break; }
+                if (!mbar_wait_or_abort<kPair>(&full[s], ph, hdr, abort_flag)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t a = smem_u32(smem + s * kStageBytes);
+                const uint32_t a = smem_u32(smem + s * kSB);
                 const uint64_t adesc = sdesc_k_swizzled(a, kBK), bdesc = sdesc_k_swizzled(a + kABytes, kBK);
 #pragma unroll
                 for (int kk = 0; kk < kBK / kUK; ++kk) {
-                    if constexpr (kF4)
-                        mma_mxf4(d, adesc + uint64_t((kk * kUK) >> 4), bdesc + uint64_t((kk * kUK) >> 4), kIdesc4,
-                                 tmem_base + kSfCol, tmem_base + kSfCol + 16, (kb > it.kb0 || kk > 0) ? 1u : 0u);
+                    const uint32_t acc = (kb > it.kb0 || kk > 0) ? 1u : 0u;
+                    const uint64_t ad = adesc + uint64_t((kk * kUK) >> 4), bd = bdesc + uint64_t((kk * kUK) >> 4);
+                    if constexpr (kPair)
+                        mma_mxf4_pair(d, ad, bd, idesc_mxf4_f32(kMmaM, kBN), tmem_base + kSfCol,
+                                      tmem_base + kSfCol + 16, acc);
+                    else if constexpr (kF4)
+                        mma_mxf4(d, ad, bd, kIdesc4, tmem_base + kSfCol, tmem_base + kSfCol + 16, acc);
                     else
-                        mma_f8f6f4(d, adesc + uint64_t((kk * kUK) >> 4), bdesc + uint64_t((kk * kUK) >> 4), kIdesc,
-                                   (kb > it.kb0 || kk > 0) ? 1u : 0u);
+                        mma_f8f6f4(d, ad, bd, kIdesc, acc);
                 }
-                if constexpr (kCl > 1)
-                    mma_commit_mc(&empty[s], uint16_t((1u << kCl) - 1u));  // the stage is free in both CTAs
+                if constexpr (kPair)
+                    mma_commit_pair_mc(&empty[s], 0x3);  // the stage is free in both CTAs
                 else
                     mma_commit(&empty[s]);
-                if (++s == kStages) { s = 0; ph ^= 1u; }
+                if (++s == kNS) { s = 0; ph ^= 1u; }
             }
-            if (ok) mma_commit(&tfull[buf]);
+            if (ok) {
+                if constexpr (kPair)
+                    mma_commit_pair_mc(&tfull[buf], 0x3);
+                else
+                    mma_commit(&tfull[buf]);
+            }
         }
     } else if (warp >= 2) {
         // ---------------------------------------------------- epilogue
@@ -605,6 +638,14 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         uint32_t ephase = 0;
         bool ok = true;
         MmaView v{};
+        // Release the accumulator to the MMA issuer (a pair: rank 0's).
+        auto acc_release = [&](uint32_t buf) {
+            tc_fence_before();
+            if (kPair && !leader)
+                mbar_arrive_cluster(tempty0 + 8u * buf, 1u);
+            else
+                mbar_arrive(&tempty[buf]);
+        };
         for (uint32_t qi = 0; ok; ++qi) {
             const uint32_t slot = qi % kRing, ru = (qi / kRing) & 1u;
             if (!ring_wait(slot, ru)) { ok = false; break; }
@@ -612,24 +653,24 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             ring_release(slot);
             if (e < 0) break;
             const int sidx = int(e >> kLocalBits);
-            const int64_t local = (e & kUnitMask) * kCl + crank;
+            const int64_t local = (e & kUnitMask) * kCl;
             if (sidx != cur) {
                 if (cur >= 0 && !epilogue_flush(shist, v, etid, ebar, ephase, hdr, abort_flag)) { ok = false; break; }
                 cur = sidx;
                 v = src.view(sidx);
             }
             Item it;
-            if (!decode_item<Fmt::kKE, (kCl > 1)>(local, v.nsb, v.n, v.kblocks, it)) continue;
+            if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
             const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
             const uint32_t buf = uint32_t(local_count % Fmt::kAcc), use = uint32_t((local_count / Fmt::kAcc) & 1);
             ++local_count;
-            const int64_t i = it.I0 + 32 * q + lane;
+            const int64_t i = it.I0 + row_off + 32 * q + lane;
             // the C_ij word of this warp's 64 columns, loaded before the wait
             // for the accumulator so that its latency hides behind the MMAs
             static_assert(kEpiChunks == 2, "one bitset word per epilogue warp");
             const int64_t word0 = (it.J0 + 32 * c0) >> 6;
             const uint64_t cw = (i < v.n && word0 < v.row_words) ? __ldg(v.bits + i * v.row_words + word0) : 0ull;
-            if (!mbar_wait_or_abort(&tfull[buf], use, hdr, abort_flag)) { ok = false; break; }
+            if (!mbar_wait_or_abort<kPair>(&tfull[buf], use, hdr, abort_flag)) { ok = false; break; }
             tc_fence_after();
             // Every count of this set lands in the shared histogram and there
             // are no layer sums: the common case, kept branch-free.
@@ -690,8 +731,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 tmem_ld_32x32b_x32(tmem_base + (uint32_t(32 * q) << 16) + uint32_t(32 * c0), r0);
                 tmem_ld_32x32b_x32(tmem_base + (uint32_t(32 * q) << 16) + uint32_t(32 * (c0 + 1)), r1);
                 tmem_ld_wait();
-                tc_fence_before();
-                mbar_arrive(&tempty[buf]);
+                acc_release(buf);
                 chunk(c0, r0);
                 chunk(c0 + 1, r1);
             } else {
@@ -702,18 +742,21 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                     tmem_ld_wait();
                     chunk(c, r);
                 }
-                tc_fence_before();
-                mbar_arrive(&tempty[buf]);
+                acc_release(buf);
             }
         }
         if (ok && cur >= 0) epilogue_flush(shist, v, etid, ebar, ephase, hdr, abort_flag);
     }
     __syncthreads();
-    // No CTA of a pair leaves while the other may still signal it.
-    if constexpr (kCl > 1) cluster_sync();
+    // No CTA of a pair leaves (or frees the pair's TMEM) while the other
+    // may still signal it or its MMAs may still run.
+    if constexpr (kPair) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem_base, kTmemCols);
+        if constexpr (kPair)
+            tmem_dealloc_pair(tmem_base, kTmemCols);
+        else
+            tmem_dealloc(tmem_base, kTmemCols);
     }
 }
 
@@ -862,7 +905,7 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
 
     // The B box is a whole 256-row slab, or in a CTA pair the half each CTA loads.
-    constexpr int kCl = kFp4 ? FmtF4::kCl : FmtF8::kCl;
+    constexpr int kCl = (kFp4 ? FmtF4::kPair : FmtF8::kPair) ? 2 : 1;
     CUtensorMap mapU, mapL;
     if (encode_tensor_map_2d(&mapU, CU_TENSOR_MAP_DATA_TYPE_UINT8, U, uint64_t(lay.row), uint64_t(n),
                              uint64_t(lay.row), kBK, kBM, kSwizzle) != CUDA_SUCCESS ||
