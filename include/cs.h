@@ -149,8 +149,9 @@ int cs_resolved_path(int64_t n, int path);
  * The CS_PATH_AUTO table, process-wide: entry e selects paths[e]
  * (CS_PATH_POPC, CS_PATH_MMA or CS_PATH_MMA4) for n_min[e] <= n < n_min[e+1].
  * n_min must start at 0 and increase; at most 16 entries.  The default is
- * {0: POPC, 1024: MMA}; the autotuner (paper_1805_04463_gb300/tune.py)
- * installs measured thresholds.  Errors: CS_EINVAL.
+ * {0: POPC, 1024: MMA, 4096: MMA4}; the autotuner
+ * (paper_1805_04463_gb300/tune.py) installs measured thresholds.
+ * Errors: CS_EINVAL.
  */
 int cs_set_auto_paths(const int64_t *n_min, const int *paths, int count);
 

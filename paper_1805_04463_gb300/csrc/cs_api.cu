@@ -32,14 +32,16 @@ inline cudaError_t clear_status(void* ws, cudaStream_t st) {
 }  // namespace
 
 // CS_PATH_AUTO table: entry e applies from size n_min[e] up to the next
-// entry.  The default follows GB300 measurements (the tensor-core path wins
-// from n = 1024 up: 0.042 vs 0.050 ms there, 32 vs 357 ms at n = 65536); the
-// autotuner replaces it with thresholds measured on the running device.
+// entry.  The default follows GB300 measurements of random 2D orders: the
+// FP8 tensor path beats POPC from n = 1024 (0.032 vs 0.042 ms), the FP4 pair
+// path beats FP8 from n = 4096 (0.038 vs 0.044 ms; 12.1 vs 27.3 ms at
+// 65536, 89.5 vs 224 ms at 131072); the autotuner replaces it with
+// thresholds measured on the running device.
 constexpr int kMaxAuto = 16;
 std::mutex g_auto_mu;
-int64_t g_auto_n[kMaxAuto] = {0, 1024};
-int g_auto_p[kMaxAuto] = {CS_PATH_POPC, CS_PATH_MMA};
-int g_auto_count = 2;
+int64_t g_auto_n[kMaxAuto] = {0, 1024, 4096};
+int g_auto_p[kMaxAuto] = {CS_PATH_POPC, CS_PATH_MMA, CS_PATH_MMA4};
+int g_auto_count = 3;
 
 int resolve_path(int64_t n, int path) {
     if (path != CS_PATH_AUTO) return path;

@@ -1,11 +1,12 @@
 """Autotuner: which interval-count path to run for which set size.
 
 For each size bucket the tuner builds a random 2D order on the device, times
-cs_interval_abundance on both paths (CUDA events on the launching stream,
-after a warm-up), checks that the two histograms agree, and keeps the faster
-path.  The resulting table (n_min -> path) is installed as the library's
-CS_PATH_AUTO policy (cs_set_auto_paths) and persisted as JSON keyed by the
-device name, so a later process can load it instead of measuring again.
+cs_interval_abundance on every path (POPC, FP8 tensor, FP4 tensor; CUDA
+events on the launching stream, after a warm-up), checks that the
+histograms agree, and keeps the fastest path.  The resulting table
+(n_min -> path) is installed as the library's CS_PATH_AUTO policy
+(cs_set_auto_paths) and persisted as JSON keyed by the device name, so a
+later process can load it instead of measuring again.
 
     python -m paper_1805_04463_gb300.tune          # measure, install, save
 """
@@ -18,15 +19,19 @@ import paper_1805_04463_gb300 as cs
 
 DEFAULT_SIZES = (1024, 2048, 4096, 8192, 16384, 32768, 65536)
 DEFAULT_FILE = os.path.join(os.path.expanduser("~"), ".cache", "causet_gb300", "tune.json")
+PATHS = (cs.PATH_POPC, cs.PATH_MMA, cs.PATH_MMA4)
 
 
 def choose(measurements):
-    """Measurements [(n, popc_ms, mma_ms)] -> AUTO table [(n_min, path)]: the
-    faster path per size, runs of equal choices merged, the first entry at 0."""
-    ms = sorted(measurements)
+    """Measurements [(n, popc_ms, mma_ms[, mma4_ms])] (None = path not run) ->
+    AUTO table [(n_min, path)]: the fastest path per size (POPC on ties), runs
+    of equal choices merged, the first entry at 0."""
+    ms = sorted(measurements, key=lambda m: m[0])
     table = []
-    for n, popc_ms, mma_ms in ms:
-        path = cs.PATH_MMA if (mma_ms is not None and mma_ms < popc_ms) else cs.PATH_POPC
+    for m in ms:
+        n = m[0]
+        times = [(t, p) for p, t in zip(PATHS, m[1:]) if t is not None]
+        path = min(times, key=lambda x: (x[0], x[1]))[1] if times else cs.PATH_POPC
         if not table:
             table.append((0, path))
         elif table[-1][1] != path:
@@ -35,7 +40,7 @@ def choose(measurements):
 
 
 def measure(sizes=DEFAULT_SIZES, reps=3, seed=0x7E57):
-    """Time both count paths on a random 2D order of each size."""
+    """Time every count path on a random 2D order of each size."""
     import torch
     out = []
     for n in sizes:
@@ -43,7 +48,7 @@ def measure(sizes=DEFAULT_SIZES, reps=3, seed=0x7E57):
         cs.sprinkle(cs.KIND_2D_ORDER, n, seed, buf.coords, buf.workspace)
         cs.causal_matrix(cs.KIND_2D_ORDER, n, buf.coords, buf.bits)
         times, hists = {}, {}
-        for path in (cs.PATH_POPC, cs.PATH_MMA):
+        for path in PATHS:
             if cs.resolved_path(n, path) != path:
                 times[path] = None
                 continue
@@ -61,9 +66,10 @@ def measure(sizes=DEFAULT_SIZES, reps=3, seed=0x7E57):
                 best = t if best is None else min(best, t)
             times[path], hists[path] = best, hist
             del ws
-        if len(hists) == 2 and not torch.equal(hists[cs.PATH_POPC], hists[cs.PATH_MMA]):
+        ref = next(iter(hists.values()))
+        if any(not torch.equal(ref, h) for h in hists.values()):
             raise RuntimeError(f"paths disagree at n={n}")
-        out.append((n, times[cs.PATH_POPC], times[cs.PATH_MMA]))
+        out.append((n,) + tuple(times[p] for p in PATHS))
     return out
 
 
@@ -109,6 +115,7 @@ def autotune(sizes=DEFAULT_SIZES, install=True, persist=True, path=DEFAULT_FILE)
 
 if __name__ == "__main__":
     t, m = autotune()
-    for n, a, b in m:
-        print(f"n={n:7d}  popc {a:9.3f} ms  mma {b if b is None else round(b, 3)} ms")
+    for n, *ts in m:
+        print(f"n={n:7d}  " + "  ".join(f"{name} {t if t is None else round(t, 3)} ms"
+                                        for name, t in zip(("popc", "mma", "mma4"), ts)))
     print("AUTO table:", t)

@@ -153,6 +153,10 @@ def test_tuner_choice_logic():
     assert tune.choose(m) == [(0, 1), (4096, 2)]
     assert tune.choose([(1024, 0.1, None)]) == [(0, 1)]
     assert tune.choose([(1024, 0.5, 0.1), (2048, 0.4, 0.5), (4096, 2.0, 1.0)]) == [(0, 2), (2048, 1), (4096, 2)]
+    # with the FP4 path: the fastest of three, None where a path was not run
+    assert tune.choose([(1024, 0.1, 0.3, 0.4), (8192, 6.0, 1.0, 1.2), (32768, 90.0, 4.0, 2.0)]) == \
+        [(0, 1), (8192, 2), (32768, 3)]
+    assert tune.choose([(1024, 0.5, None, 0.2), (2048, 0.4, 0.3, None)]) == [(0, 3), (2048, 2)]
 
 
 def test_failure_detection_entry_points_reject_bad_arguments(cslib):

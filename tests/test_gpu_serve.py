@@ -117,11 +117,11 @@ def test_autotuner_installs_a_measured_table(cs, tmp_path):
         # AUTO under the tuned table gives the same counts as both explicit paths
         for n in (1024, 16384):
             hs = []
-            for p in (0, 1, 2):
+            for p in (0, 1, 2, 3):
                 b = cs.allocate(0, n, path=p)
                 cs.run(b, 5, eps=())
                 torch.cuda.synchronize()
                 hs.append(b.hist.clone())
-            assert torch.equal(hs[0], hs[1]) and torch.equal(hs[1], hs[2])
+            assert all(torch.equal(hs[0], h) for h in hs[1:])
     finally:
         cs.set_auto_paths(old)
