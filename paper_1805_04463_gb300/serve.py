@@ -99,8 +99,8 @@ class Server:
         self.torch = torch
         self.device = device
         self.eps = tuple(eps)
-        if path == cs.PATH_AUTO:  # the tensor-core path wherever the device has it
-            path = cs.PATH_MMA if cs.resolved_path(1 << 20) == cs.PATH_MMA else cs.PATH_POPC
+        if path == cs.PATH_AUTO:  # the (FP8) tensor-core path wherever the device has one
+            path = cs.PATH_MMA if cs.resolved_path(1 << 20) in (cs.PATH_MMA, cs.PATH_MMA4) else cs.PATH_POPC
         self.count_path = path
         self.bitset_budget = bitset_budget
         self.operand_budget = operand_budget

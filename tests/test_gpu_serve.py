@@ -125,3 +125,11 @@ def test_autotuner_installs_a_measured_table(cs, tmp_path):
             assert all(torch.equal(hs[0], h) for h in hs[1:])
     finally:
         cs.set_auto_paths(old)
+
+
+def test_auto_server_counts_on_the_tensor_path(cs):
+    # AUTO resolves large single sets to the FP4 pair path; the server's job
+    # kernel runs FP8 tiles, which it must still pick on a tcgen05 device.
+    from paper_1805_04463_gb300 import serve
+    assert cs.resolved_path(1 << 20) == cs.PATH_MMA4
+    assert serve.Server().count_path == cs.PATH_MMA
