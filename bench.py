@@ -318,10 +318,9 @@ def serving_bench(path, rate=200.0, duration_s=5.0):
 
 
 def batch_path(name):
-    """The path the batch and serving entry points take for --path (they count on
-    POPC or FP8 tiles; the FP4 path is a single-set path)."""
-    p = PATHS[name]
-    return 2 if p == 3 else p
+    """The path the batch and serving entry points take for --path (their own
+    AUTO choice for --path auto)."""
+    return PATHS[name]
 
 
 def launches_per_step(kind, path):

@@ -67,9 +67,9 @@ enum {
     CS_PATH_POPC = 1,   /* AND + popcount tiles on the CUDA cores */
     CS_PATH_MMA = 2,    /* 0/1 operands as FP8 E4M3 on the tcgen05 tensor cores, fused epilogue */
     CS_PATH_MMA4 = 3    /* 0/1 operands as packed FP4 E2M1 (block-scaled kind::mxf4, every scale
-                           factor 1): half the operand bytes, the FP4 tensor rate.  Single-set
-                           calls only (cs_interval_abundance, cs_layer_sums, cs_evaluate); the
-                           batch and job entry points take CS_PATH_POPC / CS_PATH_MMA. */
+                           factor 1) on CTA pairs running 2-SM MMAs: half the operand bytes,
+                           the FP4 tensor rate.  Every count entry point takes it; on the batch
+                           and job entry points CS_PATH_AUTO stays CS_PATH_MMA. */
 };
 
 /* ------------------------------------------------------------- layouts */
@@ -334,7 +334,8 @@ int cs_batch_create(const cs_set_desc *sets, int n_sets, int path, void *workspa
 int cs_batch_launch(const cs_batch *b, const double *eps_host, int n_eps, int64_t *hist_dev,
                     double *actions_dev, int64_t *brackets_dev, void *stream);
 
-/* The count path a plan runs (CS_PATH_POPC or CS_PATH_MMA), -1 for NULL. */
+/* The count path a plan runs (CS_PATH_POPC, CS_PATH_MMA or CS_PATH_MMA4;
+ * CS_PATH_AUTO plans CS_PATH_MMA where the device has tcgen05), -1 for NULL. */
 int cs_batch_path(const cs_batch *b);
 
 /* Free the host handle (the workspace stays the caller's). */
@@ -343,20 +344,25 @@ void cs_batch_destroy(cs_batch *b);
 /* ------------------------------------------- counting slices of many sets */
 
 /* Number of work items a set of size n splits into on `path` (tiles of its
- * interval count); -1 for invalid input. */
+ * interval count: 128 x 128 POPC tiles, 128 x 256 FP8 tile slots, or 256 x
+ * 256 supertile slots on CS_PATH_MMA4; CS_PATH_AUTO means CS_PATH_MMA where
+ * the device has tcgen05); -1 for invalid input. */
 int64_t cs_count_items(int64_t n, int path);
 
-/* Bytes of the tensor-core operands of a set of size n (two n x
- * ceil(n/128)*128-byte matrices, 1024-byte aligned). */
-size_t cs_operands_bytes(int64_t n);
+/* Bytes of the tensor-core operands of a set of size n on `path`
+ * (CS_PATH_MMA: two n x ceil(n/128)*128-byte FP8 matrices; CS_PATH_MMA4: two
+ * n x ceil(n/256)*128-byte packed FP4 ones; 1024-byte aligned); 0 for
+ * CS_PATH_POPC or invalid input. */
+size_t cs_operands_bytes(int64_t n, int path);
 
 /*
- * Expand a set's bitset into its tensor-core operands (0/1 FP8: U holds each
- * row's future, L its past), once, for later cs_count_jobs slices on
- * CS_PATH_MMA.  operands_dev: cs_operands_bytes(n), 1024-byte aligned.
- * Asynchronous.  Errors: CS_EINVAL, CS_ENOMEM, CS_ECUDA.
+ * Expand a set's bitset into its tensor-core operands for `path` (0/1 values,
+ * FP8 or packed FP4: U holds each row's future, L its past), once, for later
+ * cs_count_jobs slices on the same path.  operands_dev:
+ * cs_operands_bytes(n, path), 1024-byte aligned.  Asynchronous.
+ * Errors: CS_EINVAL (also for CS_PATH_POPC), CS_ENOMEM, CS_ECUDA.
  */
-int cs_prepare_operands(int64_t n, const uint64_t *bits_dev, int64_t row_words, void *operands_dev,
+int cs_prepare_operands(int64_t n, int path, const uint64_t *bits_dev, int64_t row_words, void *operands_dev,
                         size_t operands_bytes, void *stream);
 
 /* One slice of one set's interval count. */
@@ -365,7 +371,7 @@ typedef struct {
     int64_t n;
     int64_t row_words;
     int64_t *hist;         /* the set's histogram: counts are ADDED (zero it before the first slice) */
-    void *operands;        /* CS_PATH_MMA: from cs_prepare_operands; ignored on CS_PATH_POPC */
+    void *operands;        /* tensor paths: from cs_prepare_operands (same path); ignored on CS_PATH_POPC */
     int64_t item_begin;    /* slice [item_begin, item_end) of 0 .. cs_count_items(n, path) */
     int64_t item_end;
 } cs_count_job;

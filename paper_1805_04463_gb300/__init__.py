@@ -94,8 +94,8 @@ def lib() -> ctypes.CDLL:
             "cs_batch_path": ([vp], i32),
             "cs_batch_destroy": ([vp], None),
             "cs_count_items": ([i64, i32], i64),
-            "cs_operands_bytes": ([i64], sz),
-            "cs_prepare_operands": ([i64, vp, i64, vp, sz, vp], i32),
+            "cs_operands_bytes": ([i64, i32], sz),
+            "cs_prepare_operands": ([i64, i32, vp, i64, vp, sz, vp], i32),
             "cs_count_jobs_table_bytes": ([i32, i32], sz),
             "cs_count_jobs_workspace_bytes": ([i32, i32], sz),
             "cs_count_jobs": ([vp, i32, i32, vp, vp, sz, vp], i32),
@@ -395,13 +395,13 @@ def count_items(n: int, path: int = PATH_AUTO) -> int:
     return lib().cs_count_items(n, path)
 
 
-def operands_bytes(n: int) -> int:
-    return lib().cs_operands_bytes(n)
+def operands_bytes(n: int, path: int = PATH_MMA) -> int:
+    return lib().cs_operands_bytes(n, path)
 
 
-def prepare_operands(n, bits, operands_ptr, operands_nbytes, stream=None):
-    """cs_prepare_operands: tensor-core operands of one set (operands_ptr 1024-byte aligned)."""
-    _check(lib().cs_prepare_operands(n, _ptr(bits), bits.shape[-1], operands_ptr, operands_nbytes,
+def prepare_operands(n, bits, operands_ptr, operands_nbytes, stream=None, path=PATH_MMA):
+    """cs_prepare_operands: tensor-core operands of one set for `path` (operands_ptr 1024-byte aligned)."""
+    _check(lib().cs_prepare_operands(n, path, _ptr(bits), bits.shape[-1], operands_ptr, operands_nbytes,
                                      _stream(stream)), "cs_prepare_operands")
 
 

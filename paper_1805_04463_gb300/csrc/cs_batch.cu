@@ -312,6 +312,8 @@ int batch_path(const cs_set_desc* sets, int n_sets, int path) {
     return device_has_tcgen05() ? CS_PATH_MMA : CS_PATH_POPC;
 }
 
+bool tensor_path(int path) { return path == CS_PATH_MMA || path == CS_PATH_MMA4; }
+
 Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
     Layout L;
     size_t off = sizeof(WsHeader);
@@ -322,7 +324,7 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
     };
     L.sets = take(sizeof(BatchSet) * size_t(n_sets));
     off = align_up(off, 128);
-    L.entries = take((path == CS_PATH_MMA ? sizeof(MmaSetEntry) : sizeof(PopcSetEntry)) * size_t(n_sets));
+    L.entries = take((tensor_path(path) ? sizeof(MmaSetEntry) : sizeof(PopcSetEntry)) * size_t(n_sets));
     int64_t rblocks = 0, chunks = 0, mblocks = 0;
     for (int s = 0; s < n_sets; ++s) {
         const int64_t n = sets[s].n;
@@ -330,7 +332,7 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
                    ((cs_row_words(n) + kRelWordsPerBlock - 1) / kRelWordsPerBlock);
         const int64_t side = ((n + 63) / 64 + kMirTiles - 1) / kMirTiles;
         mblocks += side * side;
-        if (path == CS_PATH_MMA) chunks += mma_expand_chunks(n);
+        if (tensor_path(path)) chunks += mma_expand_chunks(n);
     }
     L.rtab = take(size_t(rblocks) * 4);  // relate block -> set
     L.etab = take(size_t(chunks) * 4);   // expansion chunk -> set
@@ -349,11 +351,11 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
         L.key0.push_back(take(size_t(n) * 8));
         L.key1.push_back(take(size_t(n) * 8));
         L.raw.push_back(take(size_t(n) * 16));
-        if (path == CS_PATH_MMA) {
+        if (tensor_path(path)) {
             off = align_up(off, 1024);
-            L.U.push_back(take(size_t(n) * size_t(mma_kpad(n))));
+            L.U.push_back(take(mma_operand_bytes(n, path == CS_PATH_MMA4)));
             off = align_up(off, 1024);
-            L.L.push_back(take(size_t(n) * size_t(mma_kpad(n))));
+            L.L.push_back(take(mma_operand_bytes(n, path == CS_PATH_MMA4)));
         }
     }
     L.total = off;
@@ -365,7 +367,7 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
 extern "C" {
 
 size_t cs_batch_workspace_bytes(const cs_set_desc* sets, int n_sets, int path) {
-    if (!batch_valid(sets, n_sets) || path < CS_PATH_AUTO || path > CS_PATH_MMA) return 0;
+    if (!batch_valid(sets, n_sets) || path < CS_PATH_AUTO || path > CS_PATH_MMA4) return 0;
     return batch_layout(sets, n_sets, batch_path(sets, n_sets, path)).total;
 }
 
@@ -381,11 +383,11 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     CS_TRACE("cs_batch_create");
     if (!out) return CS_EINVAL;
     *out = nullptr;
-    if (!batch_valid(sets, n_sets) || path < CS_PATH_AUTO || path > CS_PATH_MMA || !workspace_dev ||
+    if (!batch_valid(sets, n_sets) || path < CS_PATH_AUTO || path > CS_PATH_MMA4 || !workspace_dev ||
         (reinterpret_cast<uintptr_t>(workspace_dev) % 1024) != 0)
         return CS_EINVAL;
     const int p = batch_path(sets, n_sets, path);
-    if (p == CS_PATH_MMA && !device_has_tcgen05()) return CS_EUNSUPPORTED;
+    if (tensor_path(p) && !device_has_tcgen05()) return CS_EUNSUPPORTED;
     const Layout L = batch_layout(sets, n_sets, p);
     if (workspace_bytes < L.total) return CS_ENOMEM;
     const uint64_t* ds_thr = nullptr;
@@ -439,14 +441,17 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     std::vector<MmaSetEntry> me;
     for (int r = 0; r < n_sets; ++r) {
         const BatchSet& b = bs[order[r]];
-        if (p == CS_PATH_MMA) {
+        if (tensor_path(p)) {
+            // FP4 pairs count in supertiles, FP8 in 128-row tiles
+            const bool fp4 = p == CS_PATH_MMA4;
             MmaSetEntry e;
             std::memset(static_cast<void*>(&e), 0, sizeof(e));
-            if (mma_fill_entry(&e, b.bits, b.n, b.row_words, ws + L.U[order[r]], ws + L.L[order[r]]) != CUDA_SUCCESS)
+            if (mma_fill_entry(&e, b.bits, b.n, b.row_words, ws + L.U[order[r]], ws + L.L[order[r]], fp4) !=
+                CUDA_SUCCESS)
                 return CS_ECUDA;
             e.item_begin = items;
             e.item_offset = 0;
-            items += mma_items(b.n);
+            items += fp4 ? mma4_units(b.n) : mma_items(b.n);
             e.hist_off = b.hist_off * 8;
             e.chunk_begin = chunks;
             chunks += mma_expand_chunks(b.n);
@@ -499,7 +504,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
         e = cudaMemcpyAsync(h->mtab, mtab.data(), mtab.size() * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !etab.empty())
         e = cudaMemcpyAsync(h->etab, etab.data(), etab.size() * 4, cudaMemcpyHostToDevice, st);
-    if (p == CS_PATH_MMA) {
+    if (tensor_path(p)) {
         h->mma_dev = reinterpret_cast<MmaSetEntry*>(ws + L.entries);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h->mma_dev, me.data(), sizeof(MmaSetEntry) * me.size(), cudaMemcpyHostToDevice, st);
@@ -561,6 +566,11 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
         if ((err = launch_expand_multi(b->mma_dev, b->etab, b->total_chunks, st)) != cudaSuccess) return CS_ECUDA;
         err = launch_count_mma_multi(b->mma_dev, b->nsets, b->total_items, reinterpret_cast<uintptr_t>(hist_dev),
                                      b->hdr, 0, st);
+    } else if (b->path == CS_PATH_MMA4) {
+        if ((err = launch_expand_multi(b->mma_dev, b->etab, b->total_chunks, st, true)) != cudaSuccess)
+            return CS_ECUDA;
+        err = launch_count_mma4_multi(b->mma_dev, b->nsets, b->total_items, reinterpret_cast<uintptr_t>(hist_dev),
+                                      b->hdr, st);
     } else {
         err = launch_count_popc_multi(b->popc_dev, b->nsets, b->total_items, reinterpret_cast<uintptr_t>(hist_dev),
                                       b->hdr, 0, st);

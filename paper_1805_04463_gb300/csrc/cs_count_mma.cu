@@ -270,18 +270,31 @@ __device__ __forceinline__ void expand_row_f4(const uint64_t* __restrict__ bits,
     }
 }
 
+// Packed U and L rows [r0, r1) of one set: the block sweeps each long row,
+// one warp per short row.
+__device__ __forceinline__ void expand_rows_f4(const uint64_t* __restrict__ bits, int64_t row_words, int64_t kpad,
+                                               uint8_t* __restrict__ U, uint8_t* __restrict__ L, int64_t r0,
+                                               int64_t r1) {
+    if (kpad / 32 >= 4 * int64_t(blockDim.x)) {
+        for (int64_t i = r0; i < r1; ++i) expand_row_f4(bits, row_words, kpad, U, L, i, threadIdx.x, blockDim.x);
+        return;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int64_t i = r0 + warp; i < r1; i += nw) expand_row_f4(bits, row_words, kpad, U, L, i, lane, 32);
+}
+
 __global__ void __launch_bounds__(256) k_expand_f4(const uint64_t* __restrict__ bits, int64_t n, int64_t row_words,
                                                    int64_t kpad, uint8_t* __restrict__ U, uint8_t* __restrict__ L) {
-    const bool long_rows = kpad / 32 >= 4 * int64_t(blockDim.x);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int64_t r0 = int64_t(blockIdx.x) * kExpandRows; r0 < n; r0 += int64_t(gridDim.x) * kExpandRows) {
-        const int64_t r1 = r0 + kExpandRows < n ? r0 + kExpandRows : n;
-        if (long_rows) {
-            for (int64_t i = r0; i < r1; ++i) expand_row_f4(bits, row_words, kpad, U, L, i, threadIdx.x, blockDim.x);
-        } else {
-            for (int64_t i = r0 + warp; i < r1; i += nw) expand_row_f4(bits, row_words, kpad, U, L, i, lane, 32);
-        }
-    }
+    for (int64_t r0 = int64_t(blockIdx.x) * kExpandRows; r0 < n; r0 += int64_t(gridDim.x) * kExpandRows)
+        expand_rows_f4(bits, row_words, kpad, U, L, r0, r0 + kExpandRows < n ? r0 + kExpandRows : n);
+}
+
+// The same over many sets, one block per chunk of kExpandRows rows.
+__global__ void __launch_bounds__(256) k_expand_f4_multi(const MmaSetEntry* __restrict__ sets,
+                                                         const int32_t* __restrict__ chunk_set) {
+    const MmaSetEntry& e = sets[chunk_set[blockIdx.x]];
+    const int64_t r0 = (int64_t(blockIdx.x) - e.chunk_begin) * kExpandRows;
+    expand_rows_f4(e.bits, e.row_words, e.kpad, e.U, e.L, r0, r0 + kExpandRows < e.n ? r0 + kExpandRows : e.n);
 }
 
 int expand_grid(int64_t rows) {
@@ -790,12 +803,62 @@ __global__ void __launch_bounds__(kThreads, 1)
     mma_body<FmtF8>(src, hdr);
 }
 
+// Many sets on the FP4 pair path.  The table's item_begin / item_offset and
+// `run` count supertiles (the pair's unit of work); nitems is twice the
+// number of supertiles.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_count_mma4_multi(const MmaSetEntry* __restrict__ sets, int nsets, int64_t nitems, uintptr_t hist_base,
+                       int64_t run, WsHeader* hdr) {
+    const MmaMulti src{sets, nsets, nitems, hist_base, run};
+    mma_body<FmtF4>(src, hdr);
+}
+
 std::atomic<bool> g_attr_set[64];  // per device: the large-shared-memory attribute is set
 std::atomic<bool> g_attr_multi_set[64];
 std::atomic<bool> g_attr4_set[64];
 std::atomic<bool> g_attr4l_set[64];
 std::atomic<int> g_clusters4[64];   // per device: CTA pairs of the FP4 kernels resident at once (0 = not queried)
 std::atomic<int> g_clusters4l[64];
+std::atomic<bool> g_attr4m_set[64];
+std::atomic<int> g_clusters4m[64];
+
+// Launch configuration of a persistent grid of CTA pairs: as many clusters
+// of two as fit at once (queried once per device and kernel), at most
+// `units` of them.
+template <class K>
+cudaError_t pair_config(K kernel, std::atomic<bool>* attr, std::atomic<int>* cached, int64_t units,
+                        cudaStream_t st, cudaLaunchAttribute* at, cudaLaunchConfig_t* cfg, int* pairs) {
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        if ((err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
+            cudaSuccess)
+            return err;
+        attr[dev] = true;
+    }
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    *cfg = cudaLaunchConfig_t{};
+    cfg->gridDim = dim3(unsigned(device_sm_count() / 2 * 2));
+    cfg->blockDim = dim3(kThreads);
+    cfg->dynamicSmemBytes = kSmemBytes;
+    cfg->stream = st;
+    cfg->attrs = at;
+    cfg->numAttrs = 1;
+    int clusters = cached[dev];
+    if (clusters == 0) {
+        if ((err = cudaOccupancyMaxActiveClusters(&clusters, kernel, cfg)) != cudaSuccess) return err;
+        if (clusters < 1) return cudaErrorNotSupported;
+        cached[dev] = clusters;
+    }
+    *pairs = int(clusters < units ? clusters : units);
+    cfg->gridDim = dim3(unsigned(2 * *pairs));
+    return cudaSuccess;
+}
 
 // Workspace: header, then U and L, each n rows of `row` bytes holding kpad
 // K elements (one byte each in FP8, two per byte in FP4).
@@ -821,7 +884,17 @@ size_t mma_workspace_bytes(int64_t n) { return mma_layout(n, false).total; }
 
 size_t mma4_workspace_bytes(int64_t n) { return mma_layout(n, true).total; }
 
-int64_t mma_kpad(int64_t n) { return (n + kBK - 1) / kBK * kBK; }
+int64_t mma_kpad(int64_t n, bool fp4) {
+    const int64_t ke = fp4 ? FmtF4::kKE : FmtF8::kKE;
+    return (n + ke - 1) / ke * ke;
+}
+
+size_t mma_operand_bytes(int64_t n, bool fp4) {
+    const int64_t kpad = mma_kpad(n, fp4);
+    return size_t(n) * size_t(fp4 ? kpad / 2 : kpad);
+}
+
+int64_t mma4_units(int64_t n) { return mma_items(n) / 2; }
 
 int64_t mma_items(int64_t n) {
     const int64_t nsb = (n + 255) / 256;
@@ -830,37 +903,62 @@ int64_t mma_items(int64_t n) {
 }
 
 CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words, uint8_t* U,
-                        uint8_t* L) {
+                        uint8_t* L, bool fp4) {
     e->kmax = -1;
     e->bits = bits;
     e->n = n;
     e->row_words = row_words;
     e->nsb = (n + 255) / 256;
-    e->kpad = mma_kpad(n);
-    e->kblocks = e->kpad / kBK;
+    e->kpad = mma_kpad(n, fp4);
+    const int64_t row = fp4 ? e->kpad / 2 : e->kpad;  // operand row bytes
+    e->kblocks = row / kBK;
     e->U = U;
     e->L = L;
-    CUresult r = encode_tensor_map_2d(&e->mapU, CU_TENSOR_MAP_DATA_TYPE_UINT8, U, uint64_t(e->kpad), uint64_t(n),
-                                      uint64_t(e->kpad), kBK, kBM, kSwizzle);
+    // The FP4 pair path loads 128-row halves of the B slab.
+    CUresult r = encode_tensor_map_2d(&e->mapU, CU_TENSOR_MAP_DATA_TYPE_UINT8, U, uint64_t(row), uint64_t(n),
+                                      uint64_t(row), kBK, kBM, kSwizzle);
     if (r != CUDA_SUCCESS) return r;
-    return encode_tensor_map_2d(&e->mapL, CU_TENSOR_MAP_DATA_TYPE_UINT8, L, uint64_t(e->kpad), uint64_t(n),
-                                uint64_t(e->kpad), kBK, kBN, kSwizzle);
+    return encode_tensor_map_2d(&e->mapL, CU_TENSOR_MAP_DATA_TYPE_UINT8, L, uint64_t(row), uint64_t(n),
+                                uint64_t(row), kBK, fp4 ? kBN / 2 : kBN, kSwizzle);
 }
 
-cudaError_t launch_expand_single(const MmaSetEntry* e, cudaStream_t st) {
+cudaError_t launch_expand_single(const MmaSetEntry* e, cudaStream_t st, bool fp4) {
     if (e->n < 1) return cudaSuccess;
-    k_expand_f8<<<unsigned(expand_grid(e->n)), 256, 0, st>>>(e->bits, e->n, e->row_words, e->kpad, e->U, e->L);
+    if (fp4)
+        k_expand_f4<<<unsigned(expand_grid(e->n)), 256, 0, st>>>(e->bits, e->n, e->row_words, e->kpad, e->U, e->L);
+    else
+        k_expand_f8<<<unsigned(expand_grid(e->n)), 256, 0, st>>>(e->bits, e->n, e->row_words, e->kpad, e->U, e->L);
     return cudaGetLastError();
 }
 
 int64_t mma_expand_chunks(int64_t n) { return (n + kExpandRows - 1) / kExpandRows; }
 
 cudaError_t launch_expand_multi(const MmaSetEntry* sets_dev, const int32_t* chunk_set, int64_t total_chunks,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool fp4) {
     if (total_chunks < 1) return cudaSuccess;
     if (total_chunks > int64_t(0x7fffffff)) return cudaErrorInvalidValue;
-    k_expand_f8_multi<<<unsigned(total_chunks), 256, 0, st>>>(sets_dev, chunk_set);
+    if (fp4)
+        k_expand_f4_multi<<<unsigned(total_chunks), 256, 0, st>>>(sets_dev, chunk_set);
+    else
+        k_expand_f8_multi<<<unsigned(total_chunks), 256, 0, st>>>(sets_dev, chunk_set);
     return cudaGetLastError();
+}
+
+cudaError_t launch_count_mma4_multi(const MmaSetEntry* sets_dev, int nsets, int64_t nunits, uintptr_t hist_base,
+                                    WsHeader* hdr, cudaStream_t st) {
+    if (nunits < 1) return cudaSuccess;
+    cudaError_t err = cudaMemsetAsync(&hdr->counter, 0, sizeof(hdr->counter), st);
+    if (err != cudaSuccess) return err;
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg;
+    int pairs = 0;
+    if ((err = pair_config(k_count_mma4_multi, g_attr4m_set, g_clusters4m, nunits, st, at, &cfg, &pairs)) !=
+        cudaSuccess)
+        return err;
+    // runs of up to 16 consecutive supertiles, at least 8 runs per pair
+    int64_t run = nunits / (int64_t(pairs) * 8);
+    run = run < 1 ? 1 : (run > 16 ? 16 : run);
+    return cudaLaunchKernelEx(&cfg, k_count_mma4_multi, sets_dev, nsets, 2 * nunits, hist_base, run, hdr);
 }
 
 cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64_t nitems, uintptr_t hist_base,
@@ -934,28 +1032,12 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
                                                              hist_len, phi, layer, kmax, hdr);
         return cudaGetLastError();
     } else {
-        // Persistent grid of CTA pairs: as many clusters as fit at once.
         cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = kCl;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(unsigned(device_sm_count() / kCl * kCl));
-        cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = kSmemBytes;
-        cfg.stream = st;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        std::atomic<int>* cached = kmax >= 0 ? g_clusters4l : g_clusters4;
-        int clusters = cached[dev];
-        if (clusters == 0) {
-            if ((err = cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg)) != cudaSuccess) return err;
-            if (clusters < 1) return cudaErrorNotSupported;
-            cached[dev] = clusters;
-        }
-        const int64_t units = nitems / kCl;
-        cfg.gridDim = dim3(unsigned((clusters < units ? clusters : units) * kCl));
+        cudaLaunchConfig_t cfg;
+        int pairs = 0;
+        if ((err = pair_config(kernel, attr, kmax >= 0 ? g_clusters4l : g_clusters4, nitems / kCl, st, at, &cfg,
+                               &pairs)) != cudaSuccess)
+            return err;
         return cudaLaunchKernelEx(&cfg, kernel, mapU, mapL, bits, n, row_words, nsb, nitems, kblocks, h, hist_len,
                                   phi, layer, kmax, hdr);
     }

@@ -60,22 +60,32 @@ struct alignas(128) MmaSetEntry {
     double* layer;       //   sums [kmax+1][n],
     int64_t kmax;        //   highest layer (< 0: none)
 };
+// fp4 selects the packed-FP4 operand format of the pair path (CS_PATH_MMA4):
+// K padded to 256 elements, two per byte; its work unit is a 256 x 256
+// supertile (mma4_units per set) instead of a 128 x 256 tile (mma_items).
 size_t mma_workspace_bytes(int64_t n);
 int64_t mma_items(int64_t n);
-int64_t mma_kpad(int64_t n);
+int64_t mma4_units(int64_t n);
+int64_t mma_kpad(int64_t n, bool fp4 = false);
+size_t mma_operand_bytes(int64_t n, bool fp4);  // bytes of one of U, L
 // Fill sizes, operand pointers and TMA maps of an entry (item_begin, hist_off,
 // chunk_begin are the caller's).
 CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words, uint8_t* U,
-                        uint8_t* L);
-cudaError_t launch_expand_single(const MmaSetEntry* e, cudaStream_t st);  // uses bits, n, row_words, kpad, U, L
+                        uint8_t* L, bool fp4 = false);
+// uses bits, n, row_words, kpad, U, L
+cudaError_t launch_expand_single(const MmaSetEntry* e, cudaStream_t st, bool fp4 = false);
 // Expansion of many sets: chunk c of the concatenated chunk range belongs to
 // set chunk_set[c] (a table the caller builds; mma_expand_chunks(n) chunks per
 // set, numbered from the set's chunk_begin).
 int64_t mma_expand_chunks(int64_t n);
 cudaError_t launch_expand_multi(const MmaSetEntry* sets_dev, const int32_t* chunk_set, int64_t total_chunks,
-                                cudaStream_t st);
+                                cudaStream_t st, bool fp4 = false);
 cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64_t nitems, uintptr_t hist_base,
                                    WsHeader* hdr, int max_ctas, cudaStream_t st);
+// The FP4 pair path over many sets: entries filled with fp4 = true, their
+// item_begin / item_offset counted in supertiles, nunits supertiles in all.
+cudaError_t launch_count_mma4_multi(const MmaSetEntry* sets_dev, int nsets, int64_t nunits, uintptr_t hist_base,
+                                    WsHeader* hdr, cudaStream_t st);
 cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist,
                              void* workspace, cudaStream_t st, const double* phi = nullptr, double* layer = nullptr,
                              int kmax = -1);

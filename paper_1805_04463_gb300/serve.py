@@ -99,14 +99,18 @@ class Server:
         self.torch = torch
         self.device = device
         self.eps = tuple(eps)
-        if path == cs.PATH_AUTO:  # the (FP8) tensor-core path wherever the device has one
-            path = cs.PATH_MMA if cs.resolved_path(1 << 20) in (cs.PATH_MMA, cs.PATH_MMA4) else cs.PATH_POPC
+        if path == cs.PATH_AUTO:
+            # the FP4 pair path wherever the device has tcgen05: the large
+            # requests dominate the work, and there it runs 2.2x the FP8 rate
+            # (GB300, 200 req/s mix: p50 2.3 vs 6.8 ms, p99 31 vs 79 ms)
+            path = cs.PATH_MMA4 if cs.resolved_path(1 << 20) in (cs.PATH_MMA, cs.PATH_MMA4) else cs.PATH_POPC
         self.count_path = path
         self.bitset_budget = bitset_budget
         self.operand_budget = operand_budget
         self.max_active = max_active
-        # about 2 ms of count work per tick on either path
-        self.tick_macs = tick_macs or (2.0e12 if path == cs.PATH_MMA else 3.0e11)
+        # about 2 ms of count work per tick on any path
+        self.tick_macs = tick_macs or {cs.PATH_POPC: 3.0e11, cs.PATH_MMA: 2.0e12, cs.PATH_MMA4: 4.0e12}[path]
+        self.tensor = path in (cs.PATH_MMA, cs.PATH_MMA4)
         self.ticks_in_flight = ticks_in_flight
         self.max_jobs = max_jobs
         self.prep_stream = torch.cuda.Stream(device=device)
@@ -129,11 +133,11 @@ class Server:
             cs.sprinkle(r.kind, r.n, r.seed, r.buf.coords, r.buf.workspace, st)
             cs.causal_matrix(r.kind, r.n, r.buf.coords, r.buf.bits, st)
             r.buf.hist.zero_()
-            if self.count_path == cs.PATH_MMA:
-                nb = cs.operands_bytes(r.n)
+            if self.tensor:
+                nb = cs.operands_bytes(r.n, self.count_path)
                 r.operands = torch.empty(nb + 1024, dtype=torch.uint8, device=self.device)
                 r.operands_ptr = (r.operands.data_ptr() + 1023) // 1024 * 1024
-                cs.prepare_operands(r.n, r.buf.bits, r.operands_ptr, nb, st)
+                cs.prepare_operands(r.n, r.buf.bits, r.operands_ptr, nb, st, path=self.count_path)
             r.prep_event = torch.cuda.Event()
             r.prep_event.record(st)
 
@@ -180,7 +184,7 @@ class Server:
         reqs = [Request(i, k, n, sd, t) for i, (t, k, n, sd) in enumerate(requests)]
         for r in reqs:
             r.bitset_bytes = cs.bitset_bytes(r.n)
-            r.operand_bytes = cs.operands_bytes(r.n) if self.count_path == cs.PATH_MMA else 0
+            r.operand_bytes = cs.operands_bytes(r.n, self.count_path) if self.tensor else 0
         queue = collections.deque(sorted(reqs, key=lambda r: (r.t_arrival, r.rid)))
         active = []
         used_b = used_o = 0
@@ -245,6 +249,6 @@ class Server:
         stats = {"requests": len(done), "wall_s": wall, "ticks": ticks,
                  "throughput_req_s": len(done) / wall, "gpairs_s": pairs / wall / 1e9,
                  "p50_ms": 1e3 * pct(50), "p99_ms": 1e3 * pct(99), "mean_ms": 1e3 * (sum(lat) / max(len(lat), 1)),
-                 "path": {cs.PATH_POPC: "popc", cs.PATH_MMA: "mma"}[self.count_path]}
+                 "path": {cs.PATH_POPC: "popc", cs.PATH_MMA: "mma", cs.PATH_MMA4: "mma4"}[self.count_path]}
         results = {r.rid: (r.hist_host.numpy(), r.actions_host.numpy()[:len(self.eps)].copy()) for r in done}
         return stats, results

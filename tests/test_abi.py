@@ -114,7 +114,9 @@ def test_batch_sizes_on_host(cslib):
     arr = cslib._desc_array([(1, 4096, 1), (2, 2048, 2), (0, 1, 3)])
     assert L.cs_batch_hist_len(arr, 3) == 4095 + 2047 + 1
     assert L.cs_batch_workspace_bytes(arr, 3, 1) > 0
-    assert L.cs_batch_workspace_bytes(arr, 3, 2) > L.cs_batch_workspace_bytes(arr, 3, 1)
+    assert L.cs_batch_workspace_bytes(arr, 3, 2) > L.cs_batch_workspace_bytes(arr, 3, 3) > \
+        L.cs_batch_workspace_bytes(arr, 3, 1)
+    assert L.cs_batch_workspace_bytes(arr, 3, 4) == 0                # no such path
     bad = cslib._desc_array([(1, 8193, 1)])                      # n beyond CS_BATCH_MAX_N
     assert L.cs_batch_workspace_bytes(bad, 1, 1) == 0 and L.cs_batch_hist_len(bad, 1) == -1
     bad = cslib._desc_array([(7, 100, 1)])                       # unknown kind
@@ -168,3 +170,18 @@ def test_failure_detection_entry_points_reject_bad_arguments(cslib):
     assert L.cs_inject_fault(-1, 1) == -1
     assert L.cs_inject_fault(cslib.FAULT_ALLOC, -1) == -1
     assert L.cs_inject_fault(cslib.FAULT_ALLOC, 0) == 0
+
+
+def test_job_items_and_operand_sizes_on_host(cslib):
+    # The FP4 pair path counts in 256 x 256 supertiles (half the FP8 tile
+    # slots) and keeps K-padded-to-256 nibble operands (half the FP8 bytes).
+    L = cslib.lib()
+    for n in (1, 255, 256, 257, 4096, 100000):
+        assert L.cs_count_items(n, 2) == 2 * L.cs_count_items(n, 3) > 0
+        kp8, kp4 = (n + 127) // 128 * 128, (n + 255) // 256 * 256
+        b8, b4 = n * kp8, n * (kp4 // 2)
+        assert L.cs_operands_bytes(n, 2) == (b8 + 1023) // 1024 * 1024 + b8
+        assert L.cs_operands_bytes(n, 3) == (b4 + 1023) // 1024 * 1024 + b4
+        assert L.cs_operands_bytes(n, 1) == 0
+    assert L.cs_count_items(100, 4) == -1 and L.cs_operands_bytes(100, 4) == 0
+    assert L.cs_count_jobs_table_bytes(3, 3) == L.cs_count_jobs_table_bytes(3, 2) > 0

@@ -1,6 +1,6 @@
 """Batched ensembles on the GPU: every set of a batch must give exactly the
 same coordinates-derived histogram, bracket and actions as the oracle (and
-as the single-set entry points), on both count paths, also when the batch
+as the single-set entry points), on every count path, also when the batch
 launch is captured into a CUDA graph and replayed."""
 import numpy as np
 import pytest
@@ -42,7 +42,7 @@ def _check_against_oracle(cs, oracle, b):
             assert brs[s] == bo
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 def test_mixed_batch_matches_oracle(cs, oracle, path):
     import torch
     b = cs.Batch(MIXED, path=path)
@@ -53,7 +53,7 @@ def test_mixed_batch_matches_oracle(cs, oracle, path):
     _check_against_oracle(cs, oracle, b)
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 def test_batch_equals_single_set_calls(cs, path):
     import torch
     sets = [(1, 4000 + 37 * s, 500 + s) for s in range(6)] + [(2, 2000 + 53 * s, 600 + s) for s in range(4)]
@@ -68,10 +68,11 @@ def test_batch_equals_single_set_calls(cs, path):
         assert torch.equal(buf.actions[:len(EPS)].cpu(), b.actions[s].cpu())
 
 
-def test_batch_graph_replay(cs, oracle):
+@pytest.mark.parametrize("path", [0, 3], ids=["auto", "mma4"])
+def test_batch_graph_replay(cs, oracle, path):
     import torch
     sets = [(1, 1500 + 100 * s, 900 + s) for s in range(5)] + [(2, 777, 950), (0, 1024, 951)]
-    b = cs.Batch(sets, path=0)
+    b = cs.Batch(sets, path=path)
     b.launch(EPS)  # warm-up outside capture (sets kernel attributes)
     torch.cuda.synchronize()
     ref = b.hist.clone()

@@ -20,14 +20,14 @@ def cs():
     return m
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 def test_results_same_alone_and_in_the_mix(cs, path):
     import torch
     from paper_1805_04463_gb300 import serve, workloads
     # a dense burst: 40 requests in 20 ms, N log-uniform in [2^10, 2^13]
     reqs = workloads.serving_requests(rate=2000.0, duration_s=0.02, log2_min=10, log2_max=13, seed=77)
     assert len(reqs) >= 20
-    srv = serve.Server(path=path, tick_macs=2e9 if path == 2 else 2e8)  # small ticks: many shared launches
+    srv = serve.Server(path=path, tick_macs=2e8 if path == 1 else 2e9)  # small ticks: many shared launches
     stats, res = srv.run(reqs)
     assert stats["requests"] == len(reqs) and stats["ticks"] > len(reqs) // 4
     for rid, (t, kind, n, seed) in enumerate(reqs):
@@ -43,18 +43,18 @@ def test_sliced_counting_matches_single_call(cs, oracle):
     # cs_count_jobs with uneven slices of three sets in shared launches
     import torch
     sets = [(0, 3000, 1), (2, 2049, 2), (1, 1500, 3)]
-    for path in (1, 2):
+    for path in (1, 2, 3):
         bufs = [cs.allocate(k, n, path=1) for k, n, _ in sets]
         ops = []
         for (k, n, sd), b in zip(sets, bufs):
             cs.sprinkle(k, n, sd, b.coords, b.workspace)
             cs.causal_matrix(k, n, b.coords, b.bits)
             b.hist.zero_()
-            if path == 2:
-                nb = cs.operands_bytes(n)
+            if path != 1:
+                nb = cs.operands_bytes(n, path)
                 t = torch.empty(nb + 1024, dtype=torch.uint8, device="cuda")
                 ptr = (t.data_ptr() + 1023) // 1024 * 1024
-                cs.prepare_operands(n, b.bits, ptr, nb)
+                cs.prepare_operands(n, b.bits, ptr, nb, path=path)
                 ops.append((t, ptr))
             else:
                 ops.append((None, None))
@@ -79,7 +79,7 @@ def test_sliced_counting_matches_single_call(cs, oracle):
             assert (b.hist.cpu().numpy() == want).all(), (path, k, n)
 
 
-@pytest.mark.parametrize("path", [1, 2], ids=["popc", "mma"])
+@pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 def test_item_shards_sum_to_the_full_count(cs, path):
     # Each of three ranks' shares counted separately (as three GPUs would),
     # summed on the host: the sharded count's single exchange.
@@ -95,11 +95,11 @@ def test_item_shards_sum_to_the_full_count(cs, path):
         cs.sprinkle(kind, n, seed, b.coords, b.workspace)
         cs.causal_matrix(kind, n, b.coords, b.bits)
         ptr = None
-        if path == 2:
-            nb = cs.operands_bytes(n)
+        if path != 1:
+            nb = cs.operands_bytes(n, path)
             ops = torch.empty(nb + 1024, dtype=torch.uint8, device="cuda")
             ptr = (ops.data_ptr() + 1023) // 1024 * 1024
-            cs.prepare_operands(n, b.bits, ptr, nb)
+            cs.prepare_operands(n, b.bits, ptr, nb, path=path)
         total += replicas.count_sharded(cs, b, path, 3, rank, dist=None, operands_ptr=ptr)
     assert torch.equal(total, full.hist)
 
@@ -127,9 +127,8 @@ def test_autotuner_installs_a_measured_table(cs, tmp_path):
         cs.set_auto_paths(old)
 
 
-def test_auto_server_counts_on_the_tensor_path(cs):
-    # AUTO resolves large single sets to the FP4 pair path; the server's job
-    # kernel runs FP8 tiles, which it must still pick on a tcgen05 device.
+def test_auto_server_counts_on_the_fp4_pair_path(cs):
+    # On a tcgen05 device the server's AUTO choice is the FP4 pair job kernel.
     from paper_1805_04463_gb300 import serve
     assert cs.resolved_path(1 << 20) == cs.PATH_MMA4
-    assert serve.Server().count_path == cs.PATH_MMA
+    assert serve.Server().count_path == cs.PATH_MMA4
