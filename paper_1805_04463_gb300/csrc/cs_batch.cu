@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kRankThreads) k_batch_rank(const BatchSet* __r
 // create time (no search).
 __global__ void __launch_bounds__(kRelThreads) k_batch_relate(const BatchSet* __restrict__ sets,
                                                               const int32_t* __restrict__ rblock_set) {
-    __shared__ int32_t sc[4][kRelColsPerBlock];
+    __shared__ __align__(16) int32_t sc[kStageInts];
     {
         const int64_t blk = blockIdx.x;
         const BatchSet& b = sets[rblock_set[blk]];

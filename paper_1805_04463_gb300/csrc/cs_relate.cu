@@ -18,7 +18,9 @@ namespace {
 template <int G>
 __global__ void __launch_bounds__(kRelThreads) k_relate(const int32_t* __restrict__ coords, int64_t n,
                                                         uint64_t* __restrict__ bits, int64_t row_words, bool order2d) {
-    __shared__ int32_t sc[geom_dim(G)][kRelColsPerBlock];
+    // the light-cone kinds stage (u, v) transposed: 64 x 33 int2
+    constexpr int kInts = G == kGeomLightCone ? 2 * 64 * kConePitch : geom_dim(G) * kRelColsPerBlock;
+    __shared__ __align__(16) int32_t sc[kInts];
     relate_block<G>(coords, n, bits, row_words, blockIdx.x, blockIdx.y, sc, order2d);
 }
 

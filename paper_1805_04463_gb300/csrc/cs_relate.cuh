@@ -51,60 +51,87 @@ __device__ __forceinline__ bool rel_related(const int32_t (&ci)[geom_dim(G)], co
 // Light-cone kinds.  Labels are in time order, so in a word wholly after
 // the row tile only the future cone can hold (u_j > u_i and v_j > v_i); for
 // a random 2D order labelled by u the u test is implied by j > i and only v
-// is compared (USE_U = false).  Words before the row tile are left to
-// mirror_block; word `ws` (the row tile's own word, when the block holds it)
-// takes the full test.  Each warp handles two rows at a time, so every
-// staged coordinate feeds four tests.
-template <bool CHECK, bool USE_U>
+// is compared (USE_U = false).  Each lane owns one word (64 columns) of the
+// block and tests its columns one by one, for four rows at a time, so a
+// test costs a compare (two with u) and a predicated OR, with no ballots.
+// The column coordinates are staged transposed, st[c][w] = column 64 w + c
+// (row pitch kConePitch: the lanes' reads of one offset c hit consecutive
+// banks); columns at or beyond n are staged as 0, which no cone test
+// passes (coordinates are non-negative).  The row tile's own word (lane
+// ws) takes the full symmetric test by ballots; words before the row tile
+// are left to mirror_block.
+constexpr int kConePitch = kRelWordsPerBlock + 1;  // staged words per column offset
+constexpr int kConeRows = 4;                        // rows a lane tests together
+constexpr int kStageInts = 4 * kRelColsPerBlock;    // staging ints any geometry needs
+static_assert(kStageInts >= 2 * 64 * kConePitch, "the transposed (u, v) staging fits");
+
+template <bool USE_U>
 __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coords, int64_t n,
                                                  uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
                                                  int64_t c0, int64_t r0, int64_t r1, int ws,
-                                                 const int32_t (*sc)[kRelColsPerBlock]) {
+                                                 const int32_t* __restrict__ st) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kWarps = kRelThreads / 32;
-    auto future = [](int32_t xu, int32_t xv, int32_t cu, int32_t cv) {
-        if constexpr (USE_U) return xv > cv && xu > cu;
-        else return xv > cv;
-    };
-    auto full = [](int32_t xu, int32_t xv, int32_t cu, int32_t cv) {
-        const int32_t du = xu - cu, dv = xv - cv;
-        return (du ^ dv) >= 0 && du != 0 && dv != 0;
-    };
+    const int2* st2 = reinterpret_cast<const int2*>(st);  // USE_U: (u, v) pairs
     const int wbeg = ws > 0 ? ws : 0;
-    for (int64_t i = r0 + warp; i < r1; i += 2 * kWarps) {
-        const int64_t i2 = i + kWarps;
-        const bool has2 = i2 < r1;
-        const int32_t ua = coords[i], va = coords[n + i];
-        const int32_t ub = has2 ? coords[i2] : 0, vb = has2 ? coords[n + i2] : 0;
-        uint64_t mine_a = 0, mine_b = 0;
+    for (int64_t ib = r0 + int64_t(warp) * kConeRows; ib < r1; ib += int64_t(kWarps) * kConeRows) {
+        int32_t ru[kConeRows], rv[kConeRows];
+        uint32_t lo[kConeRows], hi[kConeRows];
+#pragma unroll
+        for (int r = 0; r < kConeRows; ++r) {
+            const int64_t i = ib + r;
+            ru[r] = i < r1 ? coords[i] : INT32_MAX;  // a missing row passes no test
+            rv[r] = i < r1 ? coords[n + i] : INT32_MAX;
+            lo[r] = hi[r] = 0u;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // the word's low and high halves
+            uint32_t m = 1u;           // bit of the current column in the half
 #pragma unroll 8
-        for (int w = wbeg; w < kRelWordsPerBlock; ++w) {
-            const int col = w * 64 + lane;
-            const int32_t v0 = sc[1][col], v1 = sc[1][col + 32];
-            bool a0, a1, b0, b1;
-            if (w == ws) {  // warp-uniform
-                const int32_t u0 = sc[0][col], u1 = sc[0][col + 32];
-                a0 = full(u0, v0, ua, va); a1 = full(u1, v1, ua, va);
-                b0 = full(u0, v0, ub, vb); b1 = full(u1, v1, ub, vb);
-            } else {
-                const int32_t u0 = USE_U ? sc[0][col] : 0, u1 = USE_U ? sc[0][col + 32] : 0;
-                a0 = future(u0, v0, ua, va); a1 = future(u1, v1, ua, va);
-                b0 = future(u0, v0, ub, vb); b1 = future(u1, v1, ub, vb);
-            }
-            if (CHECK) {
-                const bool in0 = c0 + col < n, in1 = c0 + col + 32 < n;
-                a0 = a0 && in0; a1 = a1 && in1; b0 = b0 && in0; b1 = b1 && in1;
-            }
-            const uint64_t wa = (uint64_t(__ballot_sync(0xffffffffu, a1)) << 32) | __ballot_sync(0xffffffffu, a0);
-            const uint64_t wb = (uint64_t(__ballot_sync(0xffffffffu, b1)) << 32) | __ballot_sync(0xffffffffu, b0);
-            if (lane == w) {
-                mine_a = wa;
-                mine_b = wb;
+            for (int c = 32 * h; c < 32 * h + 32; ++c) {
+                int32_t xu = 0, xv;
+                if constexpr (USE_U) {
+                    const int2 x = st2[c * kConePitch + lane];
+                    xu = x.x;
+                    xv = x.y;
+                } else {
+                    xv = st[c * kConePitch + lane];
+                }
+#pragma unroll
+                for (int r = 0; r < kConeRows; ++r) {
+                    const bool p = USE_U ? (xv > rv[r] && xu > ru[r]) : xv > rv[r];
+                    if (p) {
+                        if (h == 0) lo[r] |= m;
+                        else hi[r] |= m;
+                    }
+                }
+                m <<= 1;
             }
         }
-        if (lane >= wbeg && w0 + lane < row_words) {
-            bits[i * row_words + w0 + lane] = mine_a;
-            if (has2) bits[i2 * row_words + w0 + lane] = mine_b;
+#pragma unroll
+        for (int r = 0; r < kConeRows; ++r) {
+            const int64_t i = ib + r;
+            if (i >= r1) break;  // warp-uniform
+            uint64_t word = (uint64_t(hi[r]) << 32) | lo[r];
+            if (ws >= 0) {  // the row tile's own word: full test (warp-uniform)
+                bool b[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = lane + 32 * h;  // column offset in the word
+                    const int64_t j = c0 + int64_t(ws) * 64 + k;
+                    if constexpr (USE_U) {
+                        const int2 x = st2[k * kConePitch + ws];
+                        const int32_t du = x.x - ru[r], dv = x.y - rv[r];
+                        b[h] = j < n && (du ^ dv) >= 0 && du != 0 && dv != 0;
+                    } else {  // u increases with the label
+                        const int32_t xv = st[k * kConePitch + ws];
+                        b[h] = j < n && (j > i ? xv > rv[r] : (j < i && xv < rv[r]));
+                    }
+                }
+                const uint64_t d = (uint64_t(__ballot_sync(0xffffffffu, b[1])) << 32) | __ballot_sync(0xffffffffu, b[0]);
+                if (lane == ws) word = d;
+            }
+            if (lane >= wbeg && w0 + lane < row_words) bits[i * row_words + w0 + lane] = word;
         }
     }
 }
@@ -112,16 +139,17 @@ __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coo
 // Rows [rb*64, rb*64+64) x words [cg*32, cg*32+32) of the bitset, less the
 // words wholly before the row tile (word < rb): the relation is symmetric,
 // so mirror_block fills those as transposes.  Column coordinates are staged
-// in `sc`; each warp folds 64 tests per word into a uint64 with two
+// in shared memory `sc` (kStageInts ints, 16-byte aligned).  The light-cone
+// kinds test one cone per word (relate_rows_cone); order2d: the set is a
+// random 2D order whose coords[0] (u) increases strictly with the label,
+// which also drops the u test there.  The other geometries stage sc[d][col]
+// and each warp folds 64 tests per word into a uint64 with two
 // __ballot_sync, lane w keeps word w, and a row's words leave in one
-// coalesced store.  The light-cone kinds test one cone per word
-// (relate_rows_cone); order2d: the set is a random 2D order whose coords[0]
-// (u) increases strictly with the label, which also drops the u test there.
-// Must be called by all 256 threads.
+// coalesced store.  Must be called by all 256 threads.
 template <int G>
 __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords, int64_t n,
                                              uint64_t* __restrict__ bits, int64_t row_words, int64_t rb, int64_t cg,
-                                             int32_t (*sc)[kRelColsPerBlock], bool order2d = false) {
+                                             int32_t* sc, bool order2d = false) {
     constexpr int DIM = geom_dim(G);
     const int64_t w0 = cg * kRelWordsPerBlock;
     const int64_t c0 = w0 * 64;
@@ -129,25 +157,32 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
     // first word of the block at or after the row tile (< 0: all of them)
     const int ws = rb - w0 < 0 ? -1 : int(rb - w0);
     const int wbeg = ws > 0 ? ws : 0;
-    for (int t = threadIdx.x + 64 * wbeg; t < kRelColsPerBlock; t += kRelThreads) {
-        const int64_t c = c0 + t;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) sc[d][t] = c < n ? coords[d * n + c] : 0;
-    }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = rb * kRelRowsPerBlock;
     const int64_t r1 = r0 + kRelRowsPerBlock < n ? r0 + kRelRowsPerBlock : n;
     if constexpr (G == kGeomLightCone) {  // time order: one cone per word, see above
-        const bool check = c0 + kRelColsPerBlock > n;
-        if (order2d) {
-            if (check) relate_rows_cone<true, false>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
-            else relate_rows_cone<false, false>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
-        } else {
-            if (check) relate_rows_cone<true, true>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
-            else relate_rows_cone<false, true>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
+        // transposed staging, word w of the block at row offset c: column 64 w + c
+        for (int t = threadIdx.x + 64 * wbeg; t < kRelColsPerBlock; t += kRelThreads) {
+            const int64_t col = c0 + t;
+            const int at = (t & 63) * kConePitch + (t >> 6);
+            if (order2d) {
+                sc[at] = col < n ? coords[n + col] : 0;
+            } else {
+                reinterpret_cast<int2*>(sc)[at] =
+                    col < n ? make_int2(coords[col], coords[n + col]) : make_int2(0, 0);
+            }
         }
+        __syncthreads();
+        if (order2d) relate_rows_cone<false>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
+        else relate_rows_cone<true>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
     } else {
+        auto sd = reinterpret_cast<int32_t(*)[kRelColsPerBlock]>(sc);
+        for (int t = threadIdx.x + 64 * wbeg; t < kRelColsPerBlock; t += kRelThreads) {
+            const int64_t c = c0 + t;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) sd[d][t] = c < n ? coords[d * n + c] : 0;
+        }
+        __syncthreads();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         for (int64_t i = r0 + warp; i < r1; i += kRelThreads / 32) {
             int32_t ci[DIM];
 #pragma unroll
@@ -156,8 +191,8 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
 #pragma unroll 4
             for (int w = wbeg; w < kRelWordsPerBlock; ++w) {
                 const int col = w * 64 + lane;
-                const bool b0 = c0 + col < n && rel_related<G>(ci, sc, col);
-                const bool b1 = c0 + col + 32 < n && rel_related<G>(ci, sc, col + 32);
+                const bool b0 = c0 + col < n && rel_related<G>(ci, sd, col);
+                const bool b1 = c0 + col + 32 < n && rel_related<G>(ci, sd, col + 32);
                 const uint32_t lo = __ballot_sync(0xffffffffu, b0);
                 const uint32_t hi = __ballot_sync(0xffffffffu, b1);
                 if (lane == w) mine = (uint64_t(hi) << 32) | lo;
