@@ -651,19 +651,41 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         uint32_t ephase = 0;
         bool ok = true;
         MmaView v{};
-        // Release the accumulator to the MMA issuer (a pair: rank 0's).
+        // Release the accumulator to the MMA issuer (a pair: rank 0's), one
+        // arrival of 32 per warp once all its lanes' TMEM reads are done.
         auto acc_release = [&](uint32_t buf) {
             tc_fence_before();
-            if (kPair && !leader)
-                mbar_arrive_cluster(tempty0 + 8u * buf, 1u);
-            else
+            if constexpr (kPair) {
+                __syncwarp();
+                if (lane == 0) {
+                    if (leader)
+                        mbar_arrive_cnt(&tempty[buf], 32u);
+                    else
+                        mbar_arrive_cluster(tempty0 + 8u * buf, 32u);
+                }
+            } else {
                 mbar_arrive(&tempty[buf]);
+            }
+        };
+        // Release an item-ring slot, likewise one arrival of 32 per warp in a pair.
+        auto epi_ring_release = [&](uint32_t slot) {
+            if constexpr (kPair) {
+                __syncwarp();
+                if (lane == 0) {
+                    if (leader)
+                        mbar_arrive_cnt(&iempty[slot], 32u);
+                    else
+                        mbar_arrive_cluster(iempty0 + 8u * slot, 32u);
+                }
+            } else {
+                mbar_arrive(&iempty[slot]);
+            }
         };
         for (uint32_t qi = 0; ok; ++qi) {
             const uint32_t slot = qi % kRing, ru = (qi / kRing) & 1u;
             if (!ring_wait(slot, ru)) { ok = false; break; }
             const int64_t e = ring[slot];
-            ring_release(slot);
+            epi_ring_release(slot);
             if (e < 0) break;
             const int sidx = int(e >> kLocalBits);
             const int64_t local = (e & kUnitMask) * kCl;
