@@ -48,6 +48,37 @@ __device__ __forceinline__ bool rel_related(const int32_t (&ci)[geom_dim(G)], co
     }
 }
 
+// FP32 filter for the 2+1 and 3+1 tests.  With every coordinate in
+// [-kFilterRange, kFilterRange] = [-2^20, 2^20] the coordinates and their
+// differences (|d| <= 2^21) are exact in FP32, every partial result of
+// dt^2 - dx^2 - ... is below 2^44 in magnitude, so each of the (at most
+// five) roundings is at most 2^20 and the FP32 value lies within
+// kFilterSlack = 2^23 of the exact one: above it the pair is related, below
+// its negative it is not, and only in between the exact int64 test runs.
+constexpr int32_t kFilterRange = 1 << 20;
+constexpr float kFilterSlack = 8388608.0f;  // 2^23
+
+template <int G>
+__device__ __forceinline__ bool rel_filtered(const float (&cf)[G], const float (*sf)[kRelColsPerBlock], int col) {
+    const float dt = sf[0][col] - cf[0];
+    float s2 = dt * dt;
+#pragma unroll
+    for (int d = 1; d < G; ++d) {
+        const float dx = sf[d][col] - cf[d];
+        s2 = fmaf(-dx, dx, s2);
+    }
+    if (s2 > kFilterSlack) return true;
+    if (s2 < -kFilterSlack) return false;
+    // near the light cone: the exact test on the same (integral) coordinates
+    int64_t e2 = 0;
+#pragma unroll
+    for (int d = 0; d < G; ++d) {
+        const int32_t dx = int32_t(sf[d][col]) - int32_t(cf[d]);
+        e2 += (d == 0 ? 1 : -1) * int64_t(dx) * dx;
+    }
+    return e2 > 0;
+}
+
 // Light-cone kinds.  Labels are in time order, so in a word wholly after
 // the row tile only the future cone can hold (u_j > u_i and v_j > v_i); for
 // a random 2D order labelled by u the u test is implied by j > i and only v
@@ -176,13 +207,61 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
         else relate_rows_cone<true>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
     } else {
         auto sd = reinterpret_cast<int32_t(*)[kRelColsPerBlock]>(sc);
-        for (int t = threadIdx.x + 64 * wbeg; t < kRelColsPerBlock; t += kRelThreads) {
+        // 2+1 and 3+1: when the block's columns and rows all lie within
+        // kFilterRange the columns are staged as floats for the FP32 filter.
+        constexpr bool kFilter = G == kGeom3 || G == kGeom4;
+        constexpr int kPer = kRelColsPerBlock / kRelThreads;  // staged columns per thread
+        int32_t v[kPer][DIM];
+        int out = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int t = threadIdx.x + q * kRelThreads;
             const int64_t c = c0 + t;
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) sd[d][t] = c < n ? coords[d * n + c] : 0;
+            for (int d = 0; d < DIM; ++d) {
+                v[q][d] = (t >= 64 * wbeg && c < n) ? coords[d * n + c] : 0;
+                out |= v[q][d] < -kFilterRange || v[q][d] > kFilterRange;
+            }
+        }
+        if (kFilter && threadIdx.x < r1 - r0) {
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                const int32_t x = coords[d * n + r0 + threadIdx.x];
+                out |= x < -kFilterRange || x > kFilterRange;
+            }
+        }
+        const bool fast = kFilter && !__syncthreads_or(out);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int t = threadIdx.x + q * kRelThreads;
+            if (t < 64 * wbeg) continue;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) sd[d][t] = fast ? __float_as_int(float(v[q][d])) : v[q][d];
         }
         __syncthreads();
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if constexpr (kFilter) {
+            if (fast) {
+                auto sf = reinterpret_cast<const float(*)[kRelColsPerBlock]>(sc);
+                for (int64_t i = r0 + warp; i < r1; i += kRelThreads / 32) {
+                    float cf[DIM];
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) cf[d] = float(coords[d * n + i]);
+                    uint64_t mine = 0;
+#pragma unroll 4
+                    for (int w = wbeg; w < kRelWordsPerBlock; ++w) {
+                        const int col = w * 64 + lane;
+                        const bool b0 = c0 + col < n && rel_filtered<DIM>(cf, sf, col);
+                        const bool b1 = c0 + col + 32 < n && rel_filtered<DIM>(cf, sf, col + 32);
+                        const uint32_t lo = __ballot_sync(0xffffffffu, b0);
+                        const uint32_t hi = __ballot_sync(0xffffffffu, b1);
+                        if (lane == w) mine = (uint64_t(hi) << 32) | lo;
+                    }
+                    if (lane >= wbeg && w0 + lane < row_words) bits[i * row_words + w0 + lane] = mine;
+                }
+                return;
+            }
+        }
         for (int64_t i = r0 + warp; i < r1; i += kRelThreads / 32) {
             int32_t ci[DIM];
 #pragma unroll

@@ -139,6 +139,36 @@ def test_evaluate_host_buffers(cs, oracle, kind, n):
         assert a1[e] == a2[e]
 
 
+def _light_ray_points(kind, n, seed, scale):
+    """Time-sorted 2+1 / 3+1 points, half on light rays x = t + e (e in
+    {-1, 0, 1}, other spatial coordinates 0): pairs on one ray are exactly
+    null or within a few 2^21 of it; half uniform in the diamond's box."""
+    rng = np.random.default_rng(seed)
+    d = 3 if kind == 3 else 4
+    t = np.sort(rng.integers(0, 1 << 20, n))
+    c = np.zeros((d, n), dtype=np.int64)
+    c[0] = t
+    ray = rng.random(n) < 0.5
+    c[1] = np.where(ray, t - (1 << 19) + rng.integers(-1, 2, n), rng.integers(-(1 << 19), 1 << 19, n))
+    for k in range(2, d):
+        c[k] = np.where(ray, 0, rng.integers(-(1 << 19), 1 << 19, n))
+    return (c * scale).astype(np.int32)
+
+
+@pytest.mark.parametrize("kind", [2, 3], ids=["3+1", "2+1"])
+@pytest.mark.parametrize("scale", [1, 1 << 8], ids=["in_fp32_range", "beyond"])
+def test_relate_near_light_cone(cs, oracle, kind, scale):
+    # The 2+1 and 3+1 relate decides most pairs in FP32 and the ones within
+    # its error bound of the light cone exactly; coordinates beyond 2^20 take
+    # the exact path throughout.  Null pairs must stay unrelated.
+    n = 1500
+    c = _light_ray_points(kind, n, 99 + kind, scale)
+    b = _run(cs, kind, n, 0, coords=c)
+    want = oracle.causal_matrix(kind, c)
+    assert (_np_bits(b) == want).all()
+    assert (b.hist.cpu().numpy() == oracle.interval_abundance(want)).all()
+
+
 def test_invalid_arguments_rejected(cs):
     import torch
     b = cs.allocate(0, 100)
