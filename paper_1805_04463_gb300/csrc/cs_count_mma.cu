@@ -47,6 +47,9 @@ constexpr int kABytes = kBM * kBK;       // 16 KiB
 constexpr int kBBytes = kBN * kBK;       // 32 KiB
 constexpr int kStageBytes = kABytes + kBBytes;
 constexpr int kHistBins = 8192;
+// A tile adds at most 128 x 256 to a CTA's shared bin; flushing every 32768
+// tiles keeps the 32-bit bins below 2^30 whatever the order.
+constexpr int64_t kFlushTiles = 32768;
 constexpr int kEpiWarps = 16;            // four epilogue warps per TMEM lane quarter
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
@@ -647,6 +650,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         const int etid = tid - 64;
         const uint32_t shist_s = smem_u32(shist);
         int64_t local_count = 0;
+        int64_t since_flush = 0;  // tiles counted into the shared histogram since its last flush
         int cur = -1;
         uint32_t ephase = 0;
         bool ok = true;
@@ -689,13 +693,15 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             if (e < 0) break;
             const int sidx = int(e >> kLocalBits);
             const int64_t local = (e & kUnitMask) * kCl;
-            if (sidx != cur) {
+            if (sidx != cur || since_flush == kFlushTiles) {
                 if (cur >= 0 && !epilogue_flush(shist, v, etid, ebar, ephase, hdr, abort_flag)) { ok = false; break; }
                 cur = sidx;
                 v = src.view(sidx);
+                since_flush = 0;
             }
             Item it;
             if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
+            ++since_flush;
             const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
             const uint32_t buf = uint32_t(local_count % Fmt::kAcc), use = uint32_t((local_count / Fmt::kAcc) & 1);
             ++local_count;

@@ -38,6 +38,11 @@ constexpr int kThreads = 256;
 constexpr int kTileBytes = kBT * kKW * 8;    // 16 KiB
 constexpr int kStageBytes = 2 * kTileBytes;  // F slab + P slab
 constexpr int kHistBins = 8192;
+// A tile adds at most 128 x 128 to a shared bin, so flushing every 65536
+// tiles keeps the 32-bit bins below 2^30 whatever the order (a bin could
+// otherwise wrap on sets of more than about 10^6 elements whose pairs
+// nearly all share one interval size).
+constexpr uint32_t kFlushTiles = 65536;
 constexpr int kSmemBytes = kStages * kStageBytes + kHistBins * 4 + kStages * 8 + 64 + 1024;
 
 // Byte offset of word w of row r inside a [128][16] uint64 slab written by TMA
@@ -180,6 +185,7 @@ __device__ __forceinline__ void popc_body(const Src& src, WsHeader* hdr) {
     int cur = -1;  // set whose counts sit in the shared histogram
     PopcView v{};
     uint32_t seq = 0;  // K-chunks consumed so far by this CTA: stage = seq % S, parity = (seq / S) & 1
+    uint32_t since_flush = 0;  // tiles counted into the shared histogram since its last flush
     bool aborted = false;
     for (;;) {
         if (tid == 0) *s_tile = int64_t(atomicAdd(&hdr->counter, 1ull));
@@ -190,11 +196,13 @@ __device__ __forceinline__ void popc_body(const Src& src, WsHeader* hdr) {
 
         int64_t local;
         const int sidx = src.set_of(t, local);
-        if (sidx != cur) {
+        if (sidx != cur || since_flush == kFlushTiles) {
             if (cur >= 0) flush_hist(shist, v);
             cur = sidx;
             v = src.view(sidx);
+            since_flush = 0;
         }
+        ++since_flush;
         const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
         int64_t bi, bj;
         decode_tile(local, v.nb, bi, bj);
