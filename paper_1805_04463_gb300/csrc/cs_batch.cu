@@ -45,7 +45,7 @@ struct BatchSet {
     int32_t* raw;
     int64_t elem_begin;    // first element of this set in the concatenated element range
     int64_t rblock_begin;  // first relate block
-    int64_t col_groups;    // relate column groups per row block
+    int64_t vwords;        // valid words per row = row tiles = ceil(n / 64)
     int64_t mblock_begin;  // first mirror block (lower part by symmetry)
     int64_t mir_side;      // mirror super-tiles per side
     int64_t hist_off;      // offset of this set's histogram in the batch histogram
@@ -150,8 +150,20 @@ __global__ void __launch_bounds__(kRankThreads) k_batch_rank(const BatchSet* __r
     }
 }
 
-// One block per relate block of one set, the set read from a table built at
-// create time (no search).
+// Relate chunks.  Row tile rb of a set with V valid words needs words
+// [rb, V) (the words before it are mirrored); they are covered by
+// ceil((V - rb) / 32) chunks of 32 words starting at the diagonal word, so
+// no block holds words before its row tile or whole groups of padding.
+// chunk_sum(x) = sum_{m=1..x} ceil(m / 32); the chunks of row tiles < rb
+// number chunk_sum(V) - chunk_sum(V - rb).
+__host__ __device__ __forceinline__ int64_t chunk_sum(int64_t x) {
+    const int64_t a = x / kRelWordsPerBlock, b = x % kRelWordsPerBlock;
+    return kRelWordsPerBlock * a * (a + 1) / 2 + b * (a + 1);
+}
+
+// One block per relate chunk of one set, the set read from a table built at
+// create time, the (row tile, chunk) by a binary search over row tiles.  The
+// last chunk of a row tile also zeroes the row's padding words.
 __global__ void __launch_bounds__(kRelThreads) k_batch_relate(const BatchSet* __restrict__ sets,
                                                               const int32_t* __restrict__ rblock_set) {
     __shared__ __align__(16) int32_t sc[kStageInts];
@@ -159,15 +171,24 @@ __global__ void __launch_bounds__(kRelThreads) k_batch_relate(const BatchSet* __
         const int64_t blk = blockIdx.x;
         const BatchSet& b = sets[rblock_set[blk]];
         const int64_t local = blk - b.rblock_begin;
-        const int64_t rb = local / b.col_groups, cg = local - rb * b.col_groups;
+        const int64_t V = b.vwords, total = chunk_sum(V);
+        int64_t lo = 0, hi = V - 1;  // last row tile whose first chunk is at or before `local`
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (total - chunk_sum(V - mid) <= local) lo = mid; else hi = mid - 1;
+        }
+        const int64_t rb = lo;
+        const int64_t w0 = rb + (local - (total - chunk_sum(V - rb))) * kRelWordsPerBlock;
+        const int64_t zero_from = w0 + kRelWordsPerBlock >= V ? w0 + kRelWordsPerBlock : -1;
         if (b.kind == CS_4D_DIAMOND)
-            relate_block<kGeom4>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
+            relate_block<kGeom4>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, false, zero_from);
         else if (b.kind == CS_3D_DIAMOND)
-            relate_block<kGeom3>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
+            relate_block<kGeom3>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, false, zero_from);
         else if (b.kind == CS_2D_DS_SLAB)
-            relate_block<kGeomDeSitter>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc);
+            relate_block<kGeomDeSitter>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, false, zero_from);
         else
-            relate_block<kGeomLightCone>(b.coords, b.n, b.bits, b.row_words, rb, cg, sc, b.kind == CS_2D_ORDER);
+            relate_block<kGeomLightCone>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, b.kind == CS_2D_ORDER,
+                                         zero_from);
     }
 }
 
@@ -328,8 +349,7 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
     int64_t rblocks = 0, chunks = 0, mblocks = 0;
     for (int s = 0; s < n_sets; ++s) {
         const int64_t n = sets[s].n;
-        rblocks += ((n + kRelRowsPerBlock - 1) / kRelRowsPerBlock) *
-                   ((cs_row_words(n) + kRelWordsPerBlock - 1) / kRelWordsPerBlock);
+        rblocks += chunk_sum((n + 63) / 64);
         const int64_t side = ((n + 63) / 64 + kMirTiles - 1) / kMirTiles;
         mblocks += side * side;
         if (tensor_path(path)) chunks += mma_expand_chunks(n);
@@ -413,9 +433,9 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
         b.raw = reinterpret_cast<int32_t*>(ws + L.raw[s]);
         b.elem_begin = elem;
         elem += b.n;
-        b.col_groups = (b.row_words + kRelWordsPerBlock - 1) / kRelWordsPerBlock;
+        b.vwords = (b.n + 63) / 64;
         b.rblock_begin = rblk;
-        rblk += ((b.n + kRelRowsPerBlock - 1) / kRelRowsPerBlock) * b.col_groups;
+        rblk += chunk_sum(b.vwords);
         b.mir_side = ((b.n + 63) / 64 + kMirTiles - 1) / kMirTiles;
         b.mblock_begin = mblk;
         mblk += b.mir_side * b.mir_side;
@@ -433,9 +453,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
         std::fill(mtab.begin() + bs[s].mblock_begin, mtab.begin() + bs[s].mblock_begin + bs[s].mir_side * bs[s].mir_side,
                   int32_t(s));
     for (int s = 0; s < n_sets; ++s)
-        std::fill(rtab.begin() + bs[s].rblock_begin,
-                  rtab.begin() + bs[s].rblock_begin +
-                      ((bs[s].n + kRelRowsPerBlock - 1) / kRelRowsPerBlock) * bs[s].col_groups,
+        std::fill(rtab.begin() + bs[s].rblock_begin, rtab.begin() + bs[s].rblock_begin + chunk_sum(bs[s].vwords),
                   int32_t(s));
     std::vector<PopcSetEntry> pe;
     std::vector<MmaSetEntry> me;

@@ -96,11 +96,20 @@ constexpr int kConeRows = 4;                        // rows a lane tests togethe
 constexpr int kStageInts = 4 * kRelColsPerBlock;    // staging ints any geometry needs
 static_assert(kStageInts >= 2 * 64 * kConePitch, "the transposed (u, v) staging fits");
 
+// Lane `lane` stores word w0 + lane of row i (words before the row tile are
+// mirror_block's), and, when zero_from >= 0, zeroes word zero_from + lane
+// (padding words past the last chunk of a row, fewer than 32).
+__device__ __forceinline__ void store_row_words(uint64_t* __restrict__ bits, int64_t i, int64_t row_words, int64_t w0,
+                                                int lane, int wbeg, uint64_t word, int64_t zero_from) {
+    if (lane >= wbeg && w0 + lane < row_words) bits[i * row_words + w0 + lane] = word;
+    if (zero_from >= 0 && zero_from + lane < row_words) bits[i * row_words + zero_from + lane] = 0ull;
+}
+
 template <bool USE_U>
 __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coords, int64_t n,
                                                  uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
                                                  int64_t c0, int64_t r0, int64_t r1, int ws,
-                                                 const int32_t* __restrict__ st) {
+                                                 const int32_t* __restrict__ st, int64_t zero_from) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kWarps = kRelThreads / 32;
     const int2* st2 = reinterpret_cast<const int2*>(st);  // USE_U: (u, v) pairs
@@ -162,12 +171,12 @@ __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coo
                 const uint64_t d = (uint64_t(__ballot_sync(0xffffffffu, b[1])) << 32) | __ballot_sync(0xffffffffu, b[0]);
                 if (lane == ws) word = d;
             }
-            if (lane >= wbeg && w0 + lane < row_words) bits[i * row_words + w0 + lane] = word;
+            store_row_words(bits, i, row_words, w0, lane, wbeg, word, zero_from);
         }
     }
 }
 
-// Rows [rb*64, rb*64+64) x words [cg*32, cg*32+32) of the bitset, less the
+// Rows [rb*64, rb*64+64) x words [w0, w0+32) of the bitset, less the
 // words wholly before the row tile (word < rb): the relation is symmetric,
 // so mirror_block fills those as transposes.  Column coordinates are staged
 // in shared memory `sc` (kStageInts ints, 16-byte aligned).  The light-cone
@@ -176,13 +185,14 @@ __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coo
 // which also drops the u test there.  The other geometries stage sc[d][col]
 // and each warp folds 64 tests per word into a uint64 with two
 // __ballot_sync, lane w keeps word w, and a row's words leave in one
-// coalesced store.  Must be called by all 256 threads.
+// coalesced store.  zero_from >= 0: the block also zeroes each row's words
+// [zero_from, row_words) (padding past a row's last chunk).  Must be called
+// by all 256 threads.
 template <int G>
 __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords, int64_t n,
-                                             uint64_t* __restrict__ bits, int64_t row_words, int64_t rb, int64_t cg,
-                                             int32_t* sc, bool order2d = false) {
+                                             uint64_t* __restrict__ bits, int64_t row_words, int64_t rb, int64_t w0,
+                                             int32_t* sc, bool order2d = false, int64_t zero_from = -1) {
     constexpr int DIM = geom_dim(G);
-    const int64_t w0 = cg * kRelWordsPerBlock;
     const int64_t c0 = w0 * 64;
     if (w0 + kRelWordsPerBlock <= rb) return;  // wholly below the diagonal
     // first word of the block at or after the row tile (< 0: all of them)
@@ -203,8 +213,8 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
             }
         }
         __syncthreads();
-        if (order2d) relate_rows_cone<false>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
-        else relate_rows_cone<true>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc);
+        if (order2d) relate_rows_cone<false>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc, zero_from);
+        else relate_rows_cone<true>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc, zero_from);
     } else {
         auto sd = reinterpret_cast<int32_t(*)[kRelColsPerBlock]>(sc);
         // 2+1 and 3+1: when the block's columns and rows all lie within
@@ -257,7 +267,7 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
                         const uint32_t hi = __ballot_sync(0xffffffffu, b1);
                         if (lane == w) mine = (uint64_t(hi) << 32) | lo;
                     }
-                    if (lane >= wbeg && w0 + lane < row_words) bits[i * row_words + w0 + lane] = mine;
+                    store_row_words(bits, i, row_words, w0, lane, wbeg, mine, zero_from);
                 }
                 return;
             }
@@ -276,7 +286,7 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
                 const uint32_t hi = __ballot_sync(0xffffffffu, b1);
                 if (lane == w) mine = (uint64_t(hi) << 32) | lo;
             }
-            if (lane >= wbeg && w0 + lane < row_words) bits[i * row_words + w0 + lane] = mine;
+            store_row_words(bits, i, row_words, w0, lane, wbeg, mine, zero_from);
         }
     }
 }
