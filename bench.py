@@ -324,10 +324,12 @@ def batch_path(name):
 
 
 def launches_per_step(kind, path):
-    """Kernels of this library launched by one step (sprinkle, relate, count, actions)."""
+    """Kernels of this library launched by one step: sprinkle (keys, 4 bucket-rank
+    kernels per key stream, scatter), relate (upper part, mirror), count
+    (operand expansion first on the tensor paths) and actions (partial, final)."""
     sprinkle = 1 + (2 if kind == 0 else 1) * 4 + 1
-    count = 1 if path == 1 else 2  # the tensor paths expand the operands first
-    return sprinkle + 1 + count + 2
+    count = 1 if path == 1 else 2
+    return sprinkle + 2 + count + 2
 
 
 def cpu_baseline(kind, n, seed, target_s=15.0, max_rows=None):
