@@ -317,6 +317,13 @@ def serving_bench(path, rate=200.0, duration_s=5.0):
     return stats
 
 
+PROBE_REPS = {1: 1 << 16, 2: 1 << 16, 3: 1 << 16}
+PROBE_WHAT = {1: "independent popc.b32 chains in registers, all SMs",
+              2: "back-to-back tcgen05.mma kind::f8f6f4 M128 N256 K32, operands in shared memory, one CTA per SM",
+              3: "back-to-back tcgen05.mma cta_group::2 kind::mxf4 M256 N256 K64, operands in shared memory, "
+                 "CTA pairs on all SMs"}
+
+
 def batch_path(name):
     """The path the batch and serving entry points take for --path (their own
     AUTO choice for --path auto)."""
@@ -538,6 +545,11 @@ def main():
                                       "no capture for the current kernel sources")
     if args.compare_paths:
         roofline["paths_ms"] = compare_paths(cs, torch, buf, n, stream)
+    # context beside the contract's peak: the path's innermost operation timed
+    # alone on every SM (cs_peak_probe), and the count's fraction of it
+    probe = cs.peak_probe(resolved, PROBE_REPS[resolved]) / 1e12
+    roofline["probe"] = {"value": probe, "unit": roofline["unit"], "frac": roofline["achieved"] / probe,
+                         "what": PROBE_WHAT[resolved]}
     line = {
         "metric": f"interval-count Gpairs/s ({desc})", "value": value, "unit": "Gpairs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,

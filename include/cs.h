@@ -490,6 +490,27 @@ int cs_greedy_antichain(int64_t n, const uint64_t *bits_dev, int64_t row_words, 
                         uint64_t *members_dev, int64_t *size, void *workspace_dev, size_t workspace_bytes,
                         void *stream);
 
+/* ------------------------------------------------------------ peak probes */
+
+/*
+ * Peak probe for the roofline of a count path: runs `reps` repetitions
+ * (1..2^22) of the path's innermost operation on every SM, with nothing
+ * around it, and returns the device-wide rate in *rate:
+ *   CS_PATH_POPC  32-bit population counts per second (independent chains in
+ *                 registers);
+ *   CS_PATH_MMA   dense FP8 FLOP/s (2 per multiply-add) of the FP8 count
+ *                 kernel's MMA, M128 N256 K32 kind::f8f6f4 on one SM, four per
+ *                 repetition, operands resident in shared memory;
+ *   CS_PATH_MMA4  dense FP4 FLOP/s of the FP4 count kernel's MMA, M256 N256
+ *                 K64 block-scaled kind::mxf4 on CTA pairs (cta_group::2).
+ * workspace_dev: 256 bytes, 256-byte aligned (the status word).
+ * Synchronous: creates its own stream and events.  The thesis has no
+ * counterpart (measurement infrastructure of this library).
+ * Errors: CS_EINVAL, CS_EUNSUPPORTED (tensor paths without tcgen05),
+ * CS_ECUDA, CS_ETIMEOUT (a bounded wait gave up).
+ */
+int cs_peak_probe(int path, int64_t reps, void *workspace_dev, double *rate);
+
 /* ---------------------------------------------------- failure detection */
 
 /*

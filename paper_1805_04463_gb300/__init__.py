@@ -23,7 +23,7 @@ __all__ = [
     "set_auto_paths", "get_auto_paths",
     "sprinkle", "sprinkle_noalloc", "causal_matrix", "layer_sums", "dalembertian", "interval_abundance", "workspace_status", "action", "action_device",
     "evaluate", "Buffers", "allocate", "run", "SetDesc", "Batch", "CountJob", "count_items",
-    "operands_bytes", "prepare_operands", "count_jobs", "degrees", "sparse_relations", "longest_chain", "greedy_antichain", "BATCH_MAX_N", "FAULT_ALLOC", "FAULT_LAUNCH", "selftest_wait",
+    "operands_bytes", "prepare_operands", "peak_probe", "count_jobs", "degrees", "sparse_relations", "longest_chain", "greedy_antichain", "BATCH_MAX_N", "FAULT_ALLOC", "FAULT_LAUNCH", "selftest_wait",
     "inject_fault",
 ]
 
@@ -113,6 +113,7 @@ def lib() -> ctypes.CDLL:
             "cs_strerror": ([i32], ctypes.c_char_p),
             "cs_version": ([], ctypes.c_char_p),
             "cs_last_cuda_error": ([], ctypes.c_char_p),
+            "cs_peak_probe": ([i32, i64, vp, dp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -393,6 +394,16 @@ class CountJob(ctypes.Structure):
 
 def count_items(n: int, path: int = PATH_AUTO) -> int:
     return lib().cs_count_items(n, path)
+
+
+def peak_probe(path: int, reps: int, workspace=None) -> float:
+    """cs_peak_probe: device-wide rate of the path's innermost operation
+    (POPC: popc32/s; MMA: FP8 FLOP/s; MMA4: FP4 FLOP/s)."""
+    import torch
+    ws = workspace if workspace is not None else torch.zeros(256, dtype=torch.uint8, device="cuda")
+    out = ctypes.c_double(0.0)
+    _check(lib().cs_peak_probe(path, reps, _ptr(ws), ctypes.byref(out)), "cs_peak_probe")
+    return out.value
 
 
 def operands_bytes(n: int, path: int = PATH_MMA) -> int:

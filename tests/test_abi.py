@@ -161,6 +161,18 @@ def test_tuner_choice_logic():
     assert tune.choose([(1024, 0.5, None, 0.2), (2048, 0.4, 0.3, None)]) == [(0, 3), (2048, 2)]
 
 
+def test_peak_probe_rejects_bad_arguments(cslib):
+    import ctypes
+    L = cslib.lib()
+    out = ctypes.c_double(0.0)
+    assert L.cs_peak_probe(0, 10, 256, ctypes.byref(out)) == -1          # AUTO is not a probe
+    assert L.cs_peak_probe(4, 10, 256, ctypes.byref(out)) == -1          # no such path
+    assert L.cs_peak_probe(1, 0, 256, ctypes.byref(out)) == -1           # at least one repetition
+    assert L.cs_peak_probe(1, (1 << 22) + 1, 256, ctypes.byref(out)) == -1   # at most 2^22
+    assert L.cs_peak_probe(1, 10, 257, ctypes.byref(out)) == -1          # 256-byte aligned workspace
+    assert L.cs_peak_probe(1, 10, 256, None) == -1
+
+
 def test_failure_detection_entry_points_reject_bad_arguments(cslib):
     L = cslib.lib()
     assert L.cs_selftest_wait(None, 0.1, 0, None) == -1        # no workspace
