@@ -423,10 +423,11 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
     uint64_t* ebar = tempty + 2;
     uint64_t* ifull = ebar + 1;         // item ring: slot published by the producer
     uint64_t* iempty = ifull + kRing;   // item ring: slot read by its consumers
-    volatile int64_t* ring = reinterpret_cast<volatile int64_t*>(iempty + kRing);
+    uint64_t* done = iempty + kRing;    // the MMA thread's last commit: every MMA it issued has completed
+    volatile int64_t* ring = reinterpret_cast<volatile int64_t*>(done + 1);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(const_cast<int64_t*>(ring) + kRing);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    static_assert((2 * kNS + 5 + 2 * kRing) * 8 + kRing * 8 + 8 <= 256, "barriers fit their 256 bytes");
+    static_assert((2 * kNS + 6 + 2 * kRing) * 8 + kRing * 8 + 8 <= 256, "barriers fit their 256 bytes");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t total = src.total();
@@ -444,6 +445,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             mbar_init(&tempty[b], kCl * kEpiThreads);  // pair: both CTAs' epilogues, on rank 0
         }
         mbar_init(ebar, kEpiThreads);
+        mbar_init(done, 1);
         // Pair: rank 0's iempty counts its MMA thread and epilogue and rank
         // 1's producer and epilogue (rank 1's own iempty is unused).
         for (int r = 0; r < kRing; ++r) {
@@ -643,6 +645,13 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                     mma_commit(&tfull[buf]);
             }
         }
+        // Also after an abort: nothing this thread issued may still run when
+        // the CTA (or pair) frees its TMEM.
+        if constexpr (kPair)
+            mma_commit_pair_mc(done, 0x1);
+        else
+            mma_commit(done);
+        mbar_wait_bounded(done, 0, hdr, kWaitLimitNs / 40);
     } else if (warp >= 2) {
         // ---------------------------------------------------- epilogue
         const int q = warp & 3;            // TMEM lane quarter this warp may access
