@@ -164,7 +164,7 @@ __host__ __device__ __forceinline__ int64_t chunk_sum(int64_t x) {
 // One block per relate chunk of one set, the set read from a table built at
 // create time, the (row tile, chunk) by a binary search over row tiles.  The
 // last chunk of a row tile also zeroes the row's padding words.
-__global__ void __launch_bounds__(kRelThreads) k_batch_relate(const BatchSet* __restrict__ sets,
+__global__ void __launch_bounds__(kRelThreads, 5) k_batch_relate(const BatchSet* __restrict__ sets,
                                                               const int32_t* __restrict__ rblock_set) {
     __shared__ __align__(16) int32_t sc[kStageInts];
     {
