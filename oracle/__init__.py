@@ -33,6 +33,7 @@ _lock = threading.Lock()
 _lib = None
 
 KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND, KIND_2D_DS_SLAB = 0, 1, 2, 3, 4
+KIND_2D_SQUARE, KIND_2D_CYLINDER = 5, 6
 DS_CELLS = 83443  # coarse eta cells of 2 pi / 2^20 rad: eta_0 = 0.5 rad
 DS_SUB = 4096     # fine units (2 pi / 2^32 rad) per coarse cell
 GRID = 1 << 20

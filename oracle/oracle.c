@@ -48,7 +48,8 @@ typedef __float128 q128;  /* binary128 via libgcc soft-float */
 #define OR_HALF  (1LL << 19)
 #define OR_MAX_ATTEMPTS 16384
 
-enum { OR_2D_ORDER = 0, OR_2D_DIAMOND = 1, OR_4D_DIAMOND = 2, OR_3D_DIAMOND = 3, OR_2D_DS_SLAB = 4 };
+enum { OR_2D_ORDER = 0, OR_2D_DIAMOND = 1, OR_4D_DIAMOND = 2, OR_3D_DIAMOND = 3, OR_2D_DS_SLAB = 4,
+       OR_2D_SQUARE = 5, OR_2D_CYLINDER = 6 };
 
 /* de Sitter slab: eta is drawn in coarse cells of 2 pi / 2^20 rad, the cells
  * -OR_DS_G .. OR_DS_G, i.e. |eta| <= (OR_DS_G + 1/2) coarse units, and
@@ -91,7 +92,9 @@ uint64_t oracle_draw(uint64_t seed, uint32_t stream, uint64_t elem, uint32_t slo
 
 int oracle_dim(int kind)
 {
-    if (kind == OR_2D_ORDER || kind == OR_2D_DIAMOND || kind == OR_2D_DS_SLAB) return 2;
+    if (kind == OR_2D_ORDER || kind == OR_2D_DIAMOND || kind == OR_2D_DS_SLAB || kind == OR_2D_SQUARE ||
+        kind == OR_2D_CYLINDER)
+        return 2;
     if (kind == OR_3D_DIAMOND) return 3;
     if (kind == OR_4D_DIAMOND) return 4;
     return 0;
@@ -173,6 +176,19 @@ uint64_t oracle_ds_threshold(int64_t g)
  *   eta = 4096 g - 2048 + (draw(stream 5, slot 2) >> 52).  (sec^2 varies by
  *   less than 1e-5 across one cell.)  Coordinates: coords[0] = eta,
  *   coords[1] = theta, both in fine units.
+ * kind 5, 1+1 square (Appendix "Causal Set Sprinklings", 1+1 Dimensional
+ *   Square) with t0 = x0 = 1/2: t and x uniform on the grid of 2^30 per unit
+ *   length, t = (draw(stream 6, slot 0) >> 34) - 2^29 and
+ *   x = (draw(stream 6, slot 1) >> 34) - 2^29, stored in light-cone
+ *   coordinates shifted to be non-negative: coords[0] = u = t + x + 2^30,
+ *   coords[1] = v = t - x + 2^30 (so ds^2 = -du dv).  Time t.
+ * kind 6, 1+1 cylinder (same appendix, 1+1 Dimensional Cylinder) with
+ *   t0 = 1 and a circle of circumference 2 pi: theta uniform, a full turn
+ *   being 2^32 fine units, theta = draw(stream 7, slot 0) >> 32 (stored as
+ *   the int32 bit pattern); t uniform on [-T, T) in the same units,
+ *   T = floor(2^31 / pi) = 683565275 (one radian, so t0 = 1),
+ *   t = ((draw(stream 7, slot 1) >> 32) * 2T >> 32) - T.  Coordinates:
+ *   coords[0] = t, coords[1] = theta.
  * Elements are sorted by time with ties broken by generation index
  * (Section "Pairwise Relations": elements are sorted by their time
  * coordinate before relations are identified).
@@ -243,6 +259,34 @@ int oracle_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords)
         free(eta); free(th); free(t);
         return OR_OK;
     }
+    if (kind == OR_2D_SQUARE || kind == OR_2D_CYLINDER) {
+        int32_t *c0 = malloc((size_t)n * 4), *c1 = malloc((size_t)n * 4);
+        or_pair *t = malloc((size_t)n * sizeof *t);
+        if (!c0 || !c1 || !t) { free(c0); free(c1); free(t); return OR_ENOMEM; }
+        for (int64_t e = 0; e < n; e++) {
+            if (kind == OR_2D_SQUARE) {
+                int64_t tt = (int64_t)(oracle_draw(seed, 6, (uint64_t)e, 0) >> 34) - (1LL << 29);
+                int64_t xx = (int64_t)(oracle_draw(seed, 6, (uint64_t)e, 1) >> 34) - (1LL << 29);
+                c0[e] = (int32_t)(tt + xx + (1LL << 30));
+                c1[e] = (int32_t)(tt - xx + (1LL << 30));
+                t[e].key = tt;
+            } else {
+                const uint64_t T = 683565275ULL;
+                c1[e] = (int32_t)(uint32_t)(oracle_draw(seed, 7, (uint64_t)e, 0) >> 32);
+                uint64_t r = oracle_draw(seed, 7, (uint64_t)e, 1) >> 32;
+                c0[e] = (int32_t)((int64_t)((r * (2 * T)) >> 32) - (int64_t)T);
+                t[e].key = c0[e];
+            }
+            t[e].idx = e;
+        }
+        qsort(t, (size_t)n, sizeof *t, or_cmp_pair);
+        for (int64_t r = 0; r < n; r++) {
+            coords[r] = c0[t[r].idx];
+            coords[n + r] = c1[t[r].idx];
+        }
+        free(c0); free(c1); free(t);
+        return OR_OK;
+    }
     if (kind == OR_4D_DIAMOND || kind == OR_3D_DIAMOND) {
         const int d = oracle_dim(kind);
         const uint32_t stream = kind == OR_4D_DIAMOND ? 3 : 4;
@@ -289,15 +333,22 @@ int oracle_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords)
  */
 int oracle_precedes(int kind, int64_t n, const int32_t *coords, int64_t a, int64_t b)
 {
-    if (kind == OR_2D_DS_SLAB) {
+    if (kind == OR_2D_DS_SLAB || kind == OR_2D_CYLINDER) {
         /* timelike iff the angular separation on the circle is below the
-         * conformal-time separation: pi - |pi - |dtheta|| < |deta|, with a
+         * (conformal-)time separation: pi - |pi - |dtheta|| < |deta|, with a
          * full turn of 2^32 fine units */
         int64_t deta = (int64_t)coords[b] - coords[a];
         int64_t ta = (int64_t)(uint32_t)coords[n + a], tb = (int64_t)(uint32_t)coords[n + b];
         int64_t dth = tb > ta ? tb - ta : ta - tb;
         int64_t circ = dth < (1LL << 32) - dth ? dth : (1LL << 32) - dth;
         return deta > 0 && circ < deta;
+    }
+    if (kind == OR_2D_SQUARE) {
+        /* dt > |dx| with 2 dt = du + dv and 2 dx = du - dv */
+        int64_t du = (int64_t)coords[b] - coords[a];
+        int64_t dv = (int64_t)coords[n + b] - coords[n + a];
+        int64_t dt2 = du + dv, dx2 = du - dv;
+        return dt2 > 0 && dt2 > (dx2 < 0 ? -dx2 : dx2);
     }
     if (kind == OR_2D_ORDER || kind == OR_2D_DIAMOND) {
         int64_t du = (int64_t)coords[b] - coords[a];
