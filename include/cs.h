@@ -54,11 +54,17 @@ enum {
     CS_2D_DIAMOND = 1,  /* 1+1 Minkowski diamond, light-cone coordinates u, v on a 2^31 grid */
     CS_4D_DIAMOND = 2,  /* 3+1 Minkowski diamond of height 1, int32 grid of 2^20 per unit */
     CS_3D_DIAMOND = 3,  /* 2+1 Minkowski diamond of height 1, int32 grid of 2^20 per unit */
-    CS_2D_DS_SLAB = 4   /* 1+1 de Sitter slab |eta| <= 0.5 (spherical foliation, pseudo-radius 1),
+    CS_2D_DS_SLAB = 4,  /* 1+1 de Sitter slab |eta| <= 0.5 (spherical foliation, pseudo-radius 1),
                            Section "Spacetime Region Considered": coords[0] = eta (int32),
                            coords[1] = theta (uint32 bits, a full turn = 2^32), both in units of
                            2 pi / 2^32 rad.  The first sprinkle of this kind on a device uploads a
                            1.3 MB constant table synchronously (do it before any stream capture). */
+    CS_2D_SQUARE = 5,   /* 1+1 Minkowski square t, x in [-1/2, 1/2) (Appendix, Minkowski spacetime,
+                           1+1 Dimensional Square) on a grid of 2^30 per unit, stored in light-cone
+                           coordinates coords[0] = u = t + x + 2^30, coords[1] = v = t - x + 2^30 */
+    CS_2D_CYLINDER = 6  /* 1+1 Minkowski cylinder (same appendix, 1+1 Dimensional Cylinder):
+                           coords[0] = t in [-2^31/pi, 2^31/pi) (t0 = 1), coords[1] = theta (uint32
+                           bits, a full turn = 2^32), both in units of 2 pi / 2^32 */
 };
 
 /* Interval-count paths. */

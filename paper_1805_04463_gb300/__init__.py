@@ -17,7 +17,7 @@ import os
 import threading
 
 __all__ = [
-    "KIND_2D_ORDER", "KIND_2D_DIAMOND", "KIND_4D_DIAMOND", "KIND_3D_DIAMOND", "KIND_2D_DS_SLAB", "PATH_AUTO", "PATH_POPC", "PATH_MMA", "PATH_MMA4",
+    "KIND_2D_ORDER", "KIND_2D_DIAMOND", "KIND_4D_DIAMOND", "KIND_3D_DIAMOND", "KIND_2D_DS_SLAB", "KIND_2D_SQUARE", "KIND_2D_CYLINDER", "PATH_AUTO", "PATH_POPC", "PATH_MMA", "PATH_MMA4",
     "CsError", "lib", "dim", "coords_bytes", "row_words", "bitset_bytes", "hist_len",
     "sprinkle_workspace_bytes", "interval_abundance_workspace", "resolved_path", "action_workspace_bytes",
     "set_auto_paths", "get_auto_paths",
@@ -28,11 +28,13 @@ __all__ = [
 ]
 
 KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND, KIND_2D_DS_SLAB = 0, 1, 2, 3, 4
+KIND_2D_SQUARE, KIND_2D_CYLINDER = 5, 6
 PATH_AUTO, PATH_POPC, PATH_MMA, PATH_MMA4 = 0, 1, 2, 3
 FAULT_ALLOC, FAULT_LAUNCH = 1, 2
 BATCH_MAX_N = 8192  # CS_BATCH_MAX_N: largest set a batch takes
 KIND_NAMES = {KIND_2D_ORDER: "2d_order", KIND_2D_DIAMOND: "2d_diamond", KIND_4D_DIAMOND: "4d_diamond",
-              KIND_3D_DIAMOND: "3d_diamond", KIND_2D_DS_SLAB: "2d_ds_slab"}
+              KIND_3D_DIAMOND: "3d_diamond", KIND_2D_DS_SLAB: "2d_ds_slab", KIND_2D_SQUARE: "2d_square",
+              KIND_2D_CYLINDER: "2d_cylinder"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(_HERE, "libcausetgb.so")

@@ -61,7 +61,9 @@ using namespace cs;
 extern "C" {
 
 int cs_dim(int kind) {
-    if (kind == CS_2D_ORDER || kind == CS_2D_DIAMOND || kind == CS_2D_DS_SLAB) return 2;
+    if (kind == CS_2D_ORDER || kind == CS_2D_DIAMOND || kind == CS_2D_DS_SLAB || kind == CS_2D_SQUARE ||
+        kind == CS_2D_CYLINDER)
+        return 2;
     if (kind == CS_3D_DIAMOND) return 3;
     if (kind == CS_4D_DIAMOND) return 4;
     return 0;

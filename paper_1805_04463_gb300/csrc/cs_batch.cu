@@ -73,6 +73,10 @@ __global__ void __launch_bounds__(256) k_batch_keys(const BatchSet* __restrict__
                           b.key1[e]);
         } else if (b.kind == CS_2D_DIAMOND) {
             b.key0[e] = draw_2d_diamond(stream_key(b.seed, kStreamDiamond2), e, b.raw[e], b.raw[b.n + e]);
+        } else if (b.kind == CS_2D_SQUARE) {
+            b.key0[e] = draw_2d_square(stream_key(b.seed, kStreamSquare), e, b.raw[e], b.raw[b.n + e]);
+        } else if (b.kind == CS_2D_CYLINDER) {
+            b.key0[e] = draw_2d_cylinder(stream_key(b.seed, kStreamCylinder), e, b.raw[e], b.raw[b.n + e]);
         } else if (b.kind == CS_2D_DS_SLAB) {
             b.key0[e] = draw_ds_slab(stream_key(b.seed, kStreamDeSitter), e, ds_thr, b.raw[e], b.raw[b.n + e]);
         } else {
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(kRelThreads, 5) k_batch_relate(const BatchSet*
             relate_block<kGeom4>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, false, zero_from);
         else if (b.kind == CS_3D_DIAMOND)
             relate_block<kGeom3>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, false, zero_from);
-        else if (b.kind == CS_2D_DS_SLAB)
+        else if (b.kind == CS_2D_DS_SLAB || b.kind == CS_2D_CYLINDER)
             relate_block<kGeomDeSitter>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, false, zero_from);
         else
             relate_block<kGeomLightCone>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, b.kind == CS_2D_ORDER,

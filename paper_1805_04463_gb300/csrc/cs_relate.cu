@@ -39,7 +39,7 @@ cudaError_t launch_relate(int kind, int64_t n, const int32_t* coords, uint64_t* 
         k_relate<kGeom4><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words, false);
     else if (kind == CS_3D_DIAMOND)
         k_relate<kGeom3><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words, false);
-    else if (kind == CS_2D_DS_SLAB)
+    else if (kind == CS_2D_DS_SLAB || kind == CS_2D_CYLINDER)
         k_relate<kGeomDeSitter><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words, false);
     else
         k_relate<kGeomLightCone><<<grid, kRelThreads, 0, st>>>(coords, n, bits, row_words, kind == CS_2D_ORDER);

@@ -17,14 +17,15 @@ constexpr int geom_dim(int g) { return g == kGeomDeSitter ? 2 : g; }
 
 // Symmetric timelike test between row element ci and staged column `col`:
 // du * dv > 0 (1+1, light-cone coordinates), dt^2 - |dx|^2 > 0 (2+1, 3+1)
-// exact in int64, or, on the de Sitter slab's conformal grid (Eq. ds_metric), the
-// angular separation on the circle below the conformal-time separation.
+// exact in int64, or, on a circle (the de Sitter slab's conformal grid, Eq.
+// ds_metric, and the 1+1 cylinder), the angular separation below the
+// (conformal-)time separation.
 template <int G>
 __device__ __forceinline__ bool rel_related(const int32_t (&ci)[geom_dim(G)], const int32_t (*sc)[kRelColsPerBlock],
                                             int col) {
     if constexpr (G == kGeomDeSitter) {
-        // |eta| < 2^29, so de fits int32; theta differences wrap modulo 2^32,
-        // one full turn.
+        // |eta| < 2^30 (slab: < 2^29, cylinder: < 2^31 / pi), so de fits
+        // int32; theta differences wrap modulo 2^32, one full turn.
         const int32_t de = sc[0][col] - ci[0];
         const uint32_t d = uint32_t(sc[1][col]) - uint32_t(ci[1]);
         const uint32_t circ = min(d, 0u - d);

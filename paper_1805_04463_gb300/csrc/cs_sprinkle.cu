@@ -69,6 +69,19 @@ __global__ void k_keys_2d_diamond(int64_t n, uint64_t seed, int32_t* __restrict_
         key[e] = draw_2d_diamond(s, e, raw[e], raw[n + e]);
 }
 
+__global__ void k_keys_2d_square(int64_t n, uint64_t seed, int32_t* __restrict__ raw, uint64_t* __restrict__ key) {
+    const uint64_t s = stream_key(seed, kStreamSquare);
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+        key[e] = draw_2d_square(s, e, raw[e], raw[n + e]);
+}
+
+__global__ void k_keys_2d_cylinder(int64_t n, uint64_t seed, int32_t* __restrict__ raw,
+                                   uint64_t* __restrict__ key) {
+    const uint64_t s = stream_key(seed, kStreamCylinder);
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+        key[e] = draw_2d_cylinder(s, e, raw[e], raw[n + e]);
+}
+
 template <int D>
 __global__ void k_keys_diamond(int64_t n, uint64_t seed, int32_t* __restrict__ raw, uint64_t* __restrict__ key,
                                WsHeader* hdr) {
@@ -244,6 +257,10 @@ cudaError_t launch_sprinkle(int kind, int64_t n, uint64_t seed, int32_t* coords,
     }
     if (kind == CS_2D_DIAMOND) {
         k_keys_2d_diamond<<<g, kThreads, 0, st>>>(n, seed, raw, key0);
+    } else if (kind == CS_2D_SQUARE) {
+        k_keys_2d_square<<<g, kThreads, 0, st>>>(n, seed, raw, key0);
+    } else if (kind == CS_2D_CYLINDER) {
+        k_keys_2d_cylinder<<<g, kThreads, 0, st>>>(n, seed, raw, key0);
     } else if (kind == CS_2D_DS_SLAB) {
         const uint64_t* thr = ds_table_device();
         if (!thr) return cudaErrorInvalidValue;

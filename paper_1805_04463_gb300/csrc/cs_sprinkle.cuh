@@ -8,7 +8,7 @@ namespace cs {
 
 // Stream numbers of the generator specification.
 constexpr uint32_t kStreamOrderU = 0, kStreamOrderV = 1, kStreamDiamond2 = 2, kStreamDiamond4 = 3,
-                   kStreamDiamond3 = 4, kStreamDeSitter = 5;
+                   kStreamDiamond3 = 4, kStreamDeSitter = 5, kStreamSquare = 6, kStreamCylinder = 7;
 
 // de Sitter slab: eta is drawn in coarse cells -kDsCells .. kDsCells of
 // 2 pi / 2^20 rad (eta_0 = 0.5 rad), then uniformly among the kDsSub fine
@@ -90,6 +90,30 @@ __device__ __forceinline__ uint64_t draw_ds_slab(uint64_t s, int64_t e, const ui
     const int32_t off = int32_t(draw_from(s, uint64_t(e), 2) >> 52);
     eta = (lo - kDsCells) * kDsSub - kDsSub / 2 + off;
     return uint64_t(uint32_t(eta) ^ 0x80000000u) << 32;
+}
+
+// 1+1 square t in [-1/2, 1/2), x in [-1/2, 1/2) on a grid of 2^30 per unit,
+// stored in light-cone coordinates u = t + x + 2^30, v = t - x + 2^30 (both
+// in [0, 2^31), so the diamond's light-cone test applies); sort key
+// u + v = 2 t + 2^31 in the top 32 bits.
+__device__ __forceinline__ uint64_t draw_2d_square(uint64_t s, int64_t e, int32_t& u, int32_t& v) {
+    const int32_t t = int32_t(draw_from(s, uint64_t(e), 0) >> 34) - (1 << 29);
+    const int32_t x = int32_t(draw_from(s, uint64_t(e), 1) >> 34) - (1 << 29);
+    u = t + x + (1 << 30);
+    v = t - x + (1 << 30);
+    return uint64_t(uint32_t(u) + uint32_t(v)) << 32;
+}
+
+// 1+1 cylinder: theta uniform on 2^32 fine units (a full turn), t uniform on
+// [-T, T) fine units with T = floor(2^31 / pi), one radian (t0 = 1), by a
+// 32 x 32-bit multiply of a uniform word by 2T.  Sort key: t + 2^31 in the
+// top 32 bits.
+constexpr uint32_t kCylinderT = 683565275u;
+__device__ __forceinline__ uint64_t draw_2d_cylinder(uint64_t s, int64_t e, int32_t& t, int32_t& theta) {
+    theta = int32_t(uint32_t(draw_from(s, uint64_t(e), 0) >> 32));
+    const uint64_t r = draw_from(s, uint64_t(e), 1) >> 32;
+    t = int32_t(int64_t((r * uint64_t(2u * kCylinderT)) >> 32) - int64_t(kCylinderT));
+    return uint64_t(uint32_t(t) ^ 0x80000000u) << 32;
 }
 
 }  // namespace cs

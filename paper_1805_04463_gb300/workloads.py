@@ -12,6 +12,7 @@ import numpy as np
 
 SEED_BASE = 0xC5E70000
 KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND, KIND_2D_DS_SLAB = 0, 1, 2, 3, 4
+KIND_2D_SQUARE, KIND_2D_CYLINDER = 5, 6
 
 # name: (kind, n, seed, description)
 SINGLE = {

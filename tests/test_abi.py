@@ -51,7 +51,7 @@ def test_layout_helpers(cslib):
     assert cslib.hist_len(1) == 1 and cslib.hist_len(1024) == 1023
     assert cslib.coords_bytes(2, 10) == 160 and cslib.coords_bytes(0, 10) == 80
     assert cslib.sprinkle_workspace_bytes(0, 0) == 0       # invalid n
-    assert cslib.sprinkle_workspace_bytes(5, 10) == 0      # invalid kind
+    assert cslib.sprinkle_workspace_bytes(7, 10) == 0      # invalid kind
     assert cslib.interval_abundance_workspace(1000, 9) == 0
 
 

@@ -12,7 +12,8 @@ TOL = 1e-12
 
 MIXED = [(0, 1, 11), (0, 2, 12), (2, 3, 13), (1, 127, 14), (0, 129, 15), (2, 1000, 16), (1, 2049, 17),
          (0, 4096, 18), (2, 2048, 19), (1, 8192, 20), (0, 300, 21), (2, 4133, 22), (3, 2, 23), (3, 1500, 24),
-         (3, 4099, 25), (4, 3, 26), (4, 2222, 27), (4, 8000, 28)]
+         (3, 4099, 25), (4, 3, 26), (4, 2222, 27), (4, 8000, 28), (5, 1, 29), (5, 1777, 30), (6, 2, 31),
+         (6, 3001, 32)]
 
 
 @pytest.fixture(scope="module")

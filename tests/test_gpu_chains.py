@@ -41,7 +41,8 @@ def _lis(seq):
     return len(tails)
 
 
-@pytest.mark.parametrize("kind,n", [(0, 1), (0, 2), (0, 65), (0, 700), (1, 500), (2, 900), (3, 640), (4, 1500)])
+@pytest.mark.parametrize("kind,n", [(0, 1), (0, 2), (0, 65), (0, 700), (1, 500), (2, 900), (3, 640), (4, 1500),
+                                    (5, 800), (6, 900)])
 def test_chains_and_antichains_match_oracle(cs, oracle, kind, n):
     b = _set(cs, kind, n, 900 + n + kind)
     bits = b.bits.cpu().numpy().view(np.uint64)

@@ -48,7 +48,7 @@ def _np_bits(b):
     return b.bits.cpu().numpy().view(np.uint64)
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("n", [1, 2, 3, 63, 64, 65, 129, 1000, 4097])
 def test_sprinkle_and_relate_bit_exact(cs, oracle, kind, n):
     seed = 0xC5E70000 + 31 * n + kind
@@ -103,7 +103,7 @@ def test_full_chain_131072_counts_exact(cs, path):
     assert (h == np.arange(n - 1, 0, -1)).all()
 
 
-@pytest.mark.parametrize("kind,n", [(0, 1024), (2, 3000), (1, 2500), (3, 3000), (4, 4000)])
+@pytest.mark.parametrize("kind,n", [(0, 1024), (2, 3000), (1, 2500), (3, 3000), (4, 4000), (5, 3500), (6, 3500)])
 def test_action_device_and_host(cs, oracle, kind, n):
     import torch
     seed = 77 + n
@@ -298,7 +298,7 @@ def test_random_kinds_and_sizes(cs, oracle, path):
     import torch
     rng = np.random.default_rng(20261203 + path)
     for t in range(40):
-        kind = int(rng.integers(0, 5))
+        kind = int(rng.integers(0, 7))
         n = int(rng.integers(1, 3001))
         seed = int(rng.integers(0, 2 ** 62))
         b = _run(cs, kind, n, seed, path=path)

@@ -28,7 +28,7 @@ def _set(cs, kind, n, seed):
 
 
 @pytest.mark.parametrize("kind,n", [(0, 1), (0, 2), (0, 63), (0, 64), (0, 65), (0, 1000), (1, 129), (2, 3001),
-                                    (3, 2049), (4, 4100), (0, 5000)])
+                                    (3, 2049), (4, 4100), (0, 5000), (5, 2000), (6, 2100)])
 def test_degrees_and_lists_match_oracle(cs, oracle, kind, n):
     import torch
     b = _set(cs, kind, n, 700 + n + kind)

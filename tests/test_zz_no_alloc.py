@@ -47,7 +47,7 @@ def _no_alloc(cs, kind, n, seed):
     return coords
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4, 5, 6])
 def test_no_alloc_matches_workspace_entry_point_twice(cs, kind):
     import torch
     # Two calls in a row through the C ABI; the second is smaller, so stale
