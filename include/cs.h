@@ -131,7 +131,9 @@ int cs_sprinkle(int kind, int64_t n, uint64_t seed, int32_t *coords_dev,
  * Totally Ordered Sets": one bitset per row) from time-sorted coordinates.
  * Bit j of row i (word j/64, bit j%64, least significant bit first) is 1 iff
  * i and j are timelike related, Delta s^2 < 0 strictly (Section
- * "Lorentzian Geometry"); 1+1 diamond and 2D order: du * dv > 0; 3D and 4D:
+ * "Lorentzian Geometry"); 1+1 diamond, 1+1 square and 2D order: du * dv > 0,
+ * for coordinates in [0, 2^31) (cs_sprinkle's range for these kinds); 1+1
+ * cylinder: as the de Sitter slab, below; 3D and 4D:
  * dt^2 > |dx|^2, exact in int64 for |coordinates| < 2^29 (the sprinkled
  * diamonds stay within [-2^20, 2^20]); de Sitter slab: the angle around the circle
  * (mod 2^32) is below |d eta|.  For CS_2D_ORDER, coords[0] must increase

@@ -1,6 +1,7 @@
 // cs_api.cu -- the extern "C" entry points of include/cs.h: argument
 // validation, workspace bookkeeping and dispatch to the kernels.
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "cs_kernels.cuh"
@@ -252,16 +253,16 @@ int cs_evaluate(int kind, int64_t n, uint64_t seed, const int32_t* coords_host, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     // Keep freed blocks in the device's stream-ordered pool between calls.
-    static bool pool_set[64];
+    static std::atomic<bool> pool_set[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CS_ECUDA;
-    if (dev >= 0 && dev < 64 && !pool_set[dev]) {
+    if (dev >= 0 && dev < 64 && !pool_set[dev].load(std::memory_order_acquire)) {
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
             uint64_t keep = UINT64_MAX;
-            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);  // idempotent
         }
-        pool_set[dev] = true;
+        pool_set[dev].store(true, std::memory_order_release);
     }
 
     const int64_t rw = cs_row_words(n);

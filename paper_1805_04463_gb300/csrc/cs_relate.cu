@@ -19,7 +19,7 @@ template <int G>
 __global__ void __launch_bounds__(kRelThreads) k_relate(const int32_t* __restrict__ coords, int64_t n,
                                                         uint64_t* __restrict__ bits, int64_t row_words, bool order2d) {
     // the light-cone kinds stage (u, v) transposed: 64 x 33 int2
-    constexpr int kInts = G == kGeomLightCone ? 2 * 64 * kConePitch : geom_dim(G) * kRelColsPerBlock;
+    constexpr int kInts = G == kGeomLightCone ? kConeInts : geom_dim(G) * kRelColsPerBlock;
     __shared__ __align__(16) int32_t sc[kInts];
     relate_block<G>(coords, n, bits, row_words, blockIdx.x, int64_t(blockIdx.y) * kRelWordsPerBlock, sc, order2d);
 }

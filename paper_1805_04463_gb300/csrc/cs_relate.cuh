@@ -84,18 +84,32 @@ __device__ __forceinline__ bool rel_filtered(const float (&cf)[G], const float (
 // the row tile only the future cone can hold (u_j > u_i and v_j > v_i); for
 // a random 2D order labelled by u the u test is implied by j > i and only v
 // is compared (USE_U = false).  Each lane owns one word (64 columns) of the
-// block and tests its columns one by one, for four rows at a time, so a
-// test costs a compare (two with u) and a predicated OR, with no ballots.
+// block and tests its columns one by one, for four rows at a time, with no
+// ballots.  Coordinates lie in [0, 2^31), so x_j - x_i - 1 fits int32 and is
+// non-negative iff x_j > x_i: a test is one or two integer multiply-adds
+// (x_j * 1 + ~x_i, on the FMA pipe, the multiplier a runtime 1 so that the
+// compiler keeps the multiply-add), an OR of the two with u, and a funnel
+// shift that appends the sign bit to the half-word's accumulator; the
+// accumulated sign bits are the complement of the relation bits.  The
+// compare-and-OR form it replaces kept the integer ALU pipe saturated.
 // The column coordinates are staged transposed, st[c][w] = column 64 w + c
 // (row pitch kConePitch: the lanes' reads of one offset c hit consecutive
 // banks); columns at or beyond n are staged as 0, which no cone test
-// passes (coordinates are non-negative).  The row tile's own word (lane
-// ws) takes the full symmetric test by ballots; words before the row tile
-// are left to mirror_block.
+// passes.  The row tile's own word (lane ws) takes the full symmetric test
+// by ballots; words before the row tile are left to mirror_block.
 constexpr int kConePitch = kRelWordsPerBlock + 1;  // staged words per column offset
 constexpr int kConeRows = 4;                        // rows a lane tests together
 constexpr int kStageInts = 4 * kRelColsPerBlock;    // staging ints any geometry needs
-static_assert(kStageInts >= 2 * 64 * kConePitch, "the transposed (u, v) staging fits");
+constexpr int kConeOne = 2 * 64 * kConePitch;       // after the (u, v) staging: a runtime 1 (the multiplier)
+constexpr int kConeInts = kConeOne + 1;             // staging ints of the light-cone kinds
+static_assert(kStageInts >= kConeInts, "the transposed (u, v) staging and the 1 fit");
+
+// x * one + y as a multiply-add (one is 1 at run time).
+__device__ __forceinline__ int32_t cone_mad(int32_t x, int32_t one, int32_t y) {
+    int32_t d;
+    asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one), "r"(y));
+    return d;
+}
 
 // Lane `lane` stores word w0 + lane of row i (words before the row tile are
 // mirror_block's), and, when zero_from >= 0, zeroes word zero_from + lane
@@ -115,21 +129,24 @@ __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coo
     constexpr int kWarps = kRelThreads / 32;
     const int2* st2 = reinterpret_cast<const int2*>(st);  // USE_U: (u, v) pairs
     const int wbeg = ws > 0 ? ws : 0;
+    const int32_t one = st[kConeOne];
     for (int64_t ib = r0 + int64_t(warp) * kConeRows; ib < r1; ib += int64_t(kWarps) * kConeRows) {
-        int32_t ru[kConeRows], rv[kConeRows];
+        int32_t ru[kConeRows], rv[kConeRows], nu[kConeRows], nv[kConeRows];
         uint32_t lo[kConeRows], hi[kConeRows];
 #pragma unroll
         for (int r = 0; r < kConeRows; ++r) {
             const int64_t i = ib + r;
             ru[r] = i < r1 ? coords[i] : INT32_MAX;  // a missing row passes no test
             rv[r] = i < r1 ? coords[n + i] : INT32_MAX;
+            nu[r] = ~ru[r];  // -x_i - 1
+            nv[r] = ~rv[r];
             lo[r] = hi[r] = 0u;
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {  // the word's low and high halves
-            uint32_t m = 1u;           // bit of the current column in the half
+            // highest column first: after 32 shifts column 32 h is bit 0
 #pragma unroll 8
-            for (int c = 32 * h; c < 32 * h + 32; ++c) {
+            for (int c = 32 * h + 31; c >= 32 * h; --c) {
                 int32_t xu = 0, xv;
                 if constexpr (USE_U) {
                     const int2 x = st2[c * kConePitch + lane];
@@ -140,20 +157,19 @@ __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coo
                 }
 #pragma unroll
                 for (int r = 0; r < kConeRows; ++r) {
-                    const bool p = USE_U ? (xv > rv[r] && xu > ru[r]) : xv > rv[r];
-                    if (p) {
-                        if (h == 0) lo[r] |= m;
-                        else hi[r] |= m;
-                    }
+                    // sign bit set iff the column is not in the future cone
+                    const int32_t d = USE_U ? (cone_mad(xu, one, nu[r]) | cone_mad(xv, one, nv[r]))
+                                            : cone_mad(xv, one, nv[r]);
+                    if (h == 0) lo[r] = __funnelshift_l(uint32_t(d), lo[r], 1);
+                    else hi[r] = __funnelshift_l(uint32_t(d), hi[r], 1);
                 }
-                m <<= 1;
             }
         }
 #pragma unroll
         for (int r = 0; r < kConeRows; ++r) {
             const int64_t i = ib + r;
             if (i >= r1) break;  // warp-uniform
-            uint64_t word = (uint64_t(hi[r]) << 32) | lo[r];
+            uint64_t word = ~((uint64_t(hi[r]) << 32) | lo[r]);
             if (ws >= 0) {  // the row tile's own word: full test (warp-uniform)
                 bool b[2];
 #pragma unroll
@@ -213,6 +229,7 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
                     col < n ? make_int2(coords[col], coords[n + col]) : make_int2(0, 0);
             }
         }
+        if (threadIdx.x == 0) sc[kConeOne] = 1;
         __syncthreads();
         if (order2d) relate_rows_cone<false>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc, zero_from);
         else relate_rows_cone<true>(coords, n, bits, row_words, w0, c0, r0, r1, ws, sc, zero_from);
