@@ -18,8 +18,11 @@ namespace {
 template <int G>
 __global__ void __launch_bounds__(kRelThreads) k_relate(const int32_t* __restrict__ coords, int64_t n,
                                                         uint64_t* __restrict__ bits, int64_t row_words, bool order2d) {
-    // the light-cone kinds stage (u, v) transposed: 64 x 33 int2
-    constexpr int kInts = G == kGeomLightCone ? kConeInts : geom_dim(G) * kRelColsPerBlock;
+    // the light-cone kinds stage (u, v) transposed: 64 x 33 int2 and a 1; the
+    // filtered 2+1 and 3+1 tests one float4 per column
+    constexpr int kInts = G == kGeomLightCone                ? kConeInts
+                          : (G == kGeom3 || G == kGeom4)     ? kStageInts
+                                                             : geom_dim(G) * kRelColsPerBlock;
     __shared__ __align__(16) int32_t sc[kInts];
     relate_block<G>(coords, n, bits, row_words, blockIdx.x, int64_t(blockIdx.y) * kRelWordsPerBlock, sc, order2d);
 }

@@ -59,25 +59,41 @@ __device__ __forceinline__ bool rel_related(const int32_t (&ci)[geom_dim(G)], co
 constexpr int32_t kFilterRange = 1 << 20;
 constexpr float kFilterSlack = 8388608.0f;  // 2^23
 
-template <int G>
-__device__ __forceinline__ bool rel_filtered(const float (&cf)[G], const float (*sf)[kRelColsPerBlock], int col) {
-    const float dt = sf[0][col] - cf[0];
+// s2 = dt^2 - dx^2 - dy^2 (- dz^2) in FP32 between a row (rc) and a staged
+// column x = (t, x, y, z), z = 0 in 2+1; the same chain of roundings
+// everywhere, so that every test of a pair decides alike.
+template <int DIM>
+__device__ __forceinline__ float filter_s2(const float (&rc)[4], float4 x) {
+    const float dt = x.x - rc[0];
     float s2 = dt * dt;
-#pragma unroll
-    for (int d = 1; d < G; ++d) {
-        const float dx = sf[d][col] - cf[d];
-        s2 = fmaf(-dx, dx, s2);
+    const float dx = x.y - rc[1];
+    s2 = fmaf(-dx, dx, s2);
+    const float dy = x.z - rc[2];
+    s2 = fmaf(-dy, dy, s2);
+    if constexpr (DIM == 4) {
+        const float dz = x.w - rc[3];
+        s2 = fmaf(-dz, dz, s2);
     }
+    return s2;
+}
+
+// The exact int64 test on the same (integral) coordinates.
+template <int DIM>
+__device__ __forceinline__ bool exact_related(const float (&rc)[4], float4 x) {
+    const int32_t dt = int32_t(x.x) - int32_t(rc[0]), dx = int32_t(x.y) - int32_t(rc[1]),
+                  dy = int32_t(x.z) - int32_t(rc[2]), dz = int32_t(x.w) - int32_t(rc[3]);
+    int64_t e2 = int64_t(dt) * dt - int64_t(dx) * dx - int64_t(dy) * dy;
+    if constexpr (DIM == 4) e2 -= int64_t(dz) * dz;
+    return e2 > 0;
+}
+
+// The filtered test: the FP32 sign outside the band, the exact one inside.
+template <int DIM>
+__device__ __forceinline__ bool rel_filtered(const float (&rc)[4], float4 x) {
+    const float s2 = filter_s2<DIM>(rc, x);
     if (s2 > kFilterSlack) return true;
     if (s2 < -kFilterSlack) return false;
-    // near the light cone: the exact test on the same (integral) coordinates
-    int64_t e2 = 0;
-#pragma unroll
-    for (int d = 0; d < G; ++d) {
-        const int32_t dx = int32_t(sf[d][col]) - int32_t(cf[d]);
-        e2 += (d == 0 ? 1 : -1) * int64_t(dx) * dx;
-    }
-    return e2 > 0;
+    return exact_related<DIM>(rc, x);
 }
 
 // Light-cone kinds.  Labels are in time order, so in a word wholly after
@@ -193,6 +209,85 @@ __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coo
     }
 }
 
+// 2+1 and 3+1 with the FP32 filter, laid out like the light-cone kinds: each
+// lane owns one word and tests its 64 columns one by one against two rows
+// held in registers.  The columns are staged as float4 (t, x, y, z; z = 0 in
+// 2+1) at st4[c * 32 + (w ^ (c & 7))] for column 64 w + c of the block: one
+// 16-byte load per column and lane, conflict-free for the lanes' loads of
+// one offset c and for the staging stores of consecutive columns.  A test is
+// the filter chain and a funnel shift of the sign of kFilterSlack - s2 (set
+// iff s2 > kFilterSlack, related) into the half-word's accumulator; a word
+// that met any |s2| <= kFilterSlack (near the light cone, about one word in
+// a thousand) is recomputed exactly by its lane.  Columns at or beyond n are
+// staged 10^9 units away in space (far outside the cone and the band) and
+// masked off.  The row tile's own word (lane ws, which holds the diagonal)
+// takes the filtered test by ballots; words before the row tile are left to
+// mirror_block.
+constexpr int kFiltRows = 2;  // rows a lane tests together (the 48-register budget of the batched kernel)
+
+template <int DIM>
+__device__ __forceinline__ void relate_rows_filtered(const int32_t* __restrict__ coords, int64_t n,
+                                                     uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
+                                                     int64_t c0, int64_t r0, int64_t r1, int ws,
+                                                     const float4* __restrict__ st4, int64_t zero_from) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kWarps = kRelThreads / 32;
+    const int wbeg = ws > 0 ? ws : 0;
+    const int64_t cw = c0 + 64 * int64_t(lane);  // this lane's first column
+    const uint64_t valid = cw >= n ? 0ull : (n - cw >= 64 ? ~0ull : (~0ull >> (64 - (n - cw))));
+    for (int64_t ib = r0 + int64_t(warp) * kFiltRows; ib < r1; ib += int64_t(kWarps) * kFiltRows) {
+        float rc[kFiltRows][4];
+        uint32_t lo[kFiltRows], hi[kFiltRows];
+        bool amb[kFiltRows];
+#pragma unroll
+        for (int r = 0; r < kFiltRows; ++r) {
+            const int64_t i = ib + r;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) rc[r][d] = (d < DIM && i < r1) ? float(coords[d * n + i]) : 0.0f;
+            lo[r] = hi[r] = 0u;
+            amb[r] = false;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            // highest column first: after 32 shifts column 32 h is bit 0
+#pragma unroll 4
+            for (int c = 32 * h + 31; c >= 32 * h; --c) {
+                const float4 x = st4[c * 32 + (lane ^ (c & 7))];
+#pragma unroll
+                for (int r = 0; r < kFiltRows; ++r) {
+                    const float s2 = filter_s2<DIM>(rc[r], x);
+                    const uint32_t sgn = __float_as_uint(kFilterSlack - s2);
+                    if (h == 0) lo[r] = __funnelshift_l(sgn, lo[r], 1);
+                    else hi[r] = __funnelshift_l(sgn, hi[r], 1);
+                    amb[r] |= fabsf(s2) <= kFilterSlack;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kFiltRows; ++r) {
+            const int64_t i = ib + r;
+            if (i >= r1) break;  // warp-uniform
+            uint64_t word = ((uint64_t(hi[r]) << 32) | lo[r]) & valid;
+            if (amb[r] && lane != ws && lane >= wbeg) {  // near the light cone: the word exactly
+                word = 0ull;
+                for (int c = 0; c < 64 && cw + c < n; ++c)
+                    if (rel_filtered<DIM>(rc[r], st4[c * 32 + (lane ^ (c & 7))])) word |= 1ull << c;
+            }
+            if (ws >= 0) {  // the row tile's own word (warp-uniform)
+                bool b[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = lane + 32 * h;  // column offset in the word
+                    b[h] = c0 + int64_t(ws) * 64 + k < n && rel_filtered<DIM>(rc[r], st4[k * 32 + (ws ^ (k & 7))]);
+                }
+                const uint64_t d = (uint64_t(__ballot_sync(0xffffffffu, b[1])) << 32) | __ballot_sync(0xffffffffu, b[0]);
+                if (lane == ws) word = d;
+            }
+            store_row_words(bits, i, row_words, w0, lane, wbeg, word, zero_from);
+        }
+    }
+}
+
 // Rows [rb*64, rb*64+64) x words [w0, w0+32) of the bitset, less the
 // words wholly before the row tile (word < rb): the relation is symmetric,
 // so mirror_block fills those as transposes.  Column coordinates are staged
@@ -259,37 +354,35 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
             }
         }
         const bool fast = kFilter && !__syncthreads_or(out);
+        if constexpr (kFilter) {
+            if (fast) {
+                float4* st4 = reinterpret_cast<float4*>(sc);
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) {
+                    const int t = threadIdx.x + q * kRelThreads;
+                    if (t < 64 * wbeg) continue;
+                    const int c = t & 63, w = t >> 6;
+                    float f[4] = {0.0f, 1e9f, 0.0f, 0.0f};  // a column at or beyond n: far away in space
+                    if (c0 + t < n) {
+#pragma unroll
+                        for (int d = 0; d < 4; ++d) f[d] = d < DIM ? float(v[q][d < DIM ? d : 0]) : 0.0f;
+                    }
+                    st4[c * 32 + (w ^ (c & 7))] = make_float4(f[0], f[1], f[2], f[3]);
+                }
+                __syncthreads();
+                relate_rows_filtered<DIM>(coords, n, bits, row_words, w0, c0, r0, r1, ws, st4, zero_from);
+                return;
+            }
+        }
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int t = threadIdx.x + q * kRelThreads;
             if (t < 64 * wbeg) continue;
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) sd[d][t] = fast ? __float_as_int(float(v[q][d])) : v[q][d];
+            for (int d = 0; d < DIM; ++d) sd[d][t] = v[q][d];
         }
         __syncthreads();
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        if constexpr (kFilter) {
-            if (fast) {
-                auto sf = reinterpret_cast<const float(*)[kRelColsPerBlock]>(sc);
-                for (int64_t i = r0 + warp; i < r1; i += kRelThreads / 32) {
-                    float cf[DIM];
-#pragma unroll
-                    for (int d = 0; d < DIM; ++d) cf[d] = float(coords[d * n + i]);
-                    uint64_t mine = 0;
-#pragma unroll 4
-                    for (int w = wbeg; w < kRelWordsPerBlock; ++w) {
-                        const int col = w * 64 + lane;
-                        const bool b0 = c0 + col < n && rel_filtered<DIM>(cf, sf, col);
-                        const bool b1 = c0 + col + 32 < n && rel_filtered<DIM>(cf, sf, col + 32);
-                        const uint32_t lo = __ballot_sync(0xffffffffu, b0);
-                        const uint32_t hi = __ballot_sync(0xffffffffu, b1);
-                        if (lane == w) mine = (uint64_t(hi) << 32) | lo;
-                    }
-                    store_row_words(bits, i, row_words, w0, lane, wbeg, mine, zero_from);
-                }
-                return;
-            }
-        }
         for (int64_t i = r0 + warp; i < r1; i += kRelThreads / 32) {
             int32_t ci[DIM];
 #pragma unroll
