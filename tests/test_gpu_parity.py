@@ -169,6 +169,30 @@ def test_relate_near_light_cone(cs, oracle, kind, scale):
     assert (b.hist.cpu().numpy() == oracle.interval_abundance(want)).all()
 
 
+@pytest.mark.parametrize("kind", [0, 1, 5], ids=["2d_order", "diamond", "square"])
+def test_relate_light_cone_coordinate_extremes(cs, oracle, kind):
+    # Light-cone coordinates anywhere in [0, 2^31): values at both ends of
+    # the range (differences up to 2^31 - 1 either way), many equal values
+    # (null pairs) and a ragged tail; labels in time order (u + v, ties by
+    # index; for the 2D order u is the label itself).
+    rng = np.random.default_rng(7 + kind)
+    n = 2000
+    top = (1 << 31) - 1
+    pool = np.concatenate([np.arange(4), top - np.arange(4), rng.integers(0, 1 << 31, 64)])
+    v = rng.choice(pool, n)
+    if kind == 0:
+        c = np.stack([np.arange(n), v])
+    else:
+        u = rng.choice(pool, n)
+        order = np.lexsort((np.arange(n), u + v))
+        c = np.stack([u[order], v[order]])
+    c = c.astype(np.int64).astype(np.int32)
+    b = _run(cs, kind, n, 0, coords=c)
+    want = oracle.causal_matrix(kind, c)
+    assert (_np_bits(b) == want).all()
+    assert (b.hist.cpu().numpy() == oracle.interval_abundance(want)).all()
+
+
 def test_invalid_arguments_rejected(cs):
     import torch
     b = cs.allocate(0, 100)
