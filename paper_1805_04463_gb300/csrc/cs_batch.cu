@@ -91,23 +91,25 @@ __global__ void __launch_bounds__(256) k_batch_keys(const BatchSet* __restrict__
 }
 
 // Bitonic sort of P (a power of two) (key, index) pairs in shared memory,
-// ascending by key then index.  All threads of the block take part.
+// ascending by key then index.  All threads of the block take part; in each
+// step thread q handles compare-exchange pairs q, q + blockDim.x, ... of the
+// P / 2, pair q joining element i (q with a 0 inserted at bit log2 j) and
+// i + j.
 __device__ void bitonic_sort(uint64_t* key, uint32_t* idx, int P) {
     for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                const int p = i ^ j;
-                if (p > i) {
-                    const bool up = (i & k) == 0;
-                    const bool greater = key[i] > key[p] || (key[i] == key[p] && idx[i] > idx[p]);
-                    if (greater == up) {
-                        const uint64_t tk = key[i];
-                        key[i] = key[p];
-                        key[p] = tk;
-                        const uint32_t ti = idx[i];
-                        idx[i] = idx[p];
-                        idx[p] = ti;
-                    }
+            for (int q = threadIdx.x; q < P / 2; q += blockDim.x) {
+                const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+                const int p = i + j;
+                const bool up = (i & k) == 0;
+                const uint64_t ki = key[i], kp = key[p];
+                const uint32_t ii = idx[i], ip = idx[p];
+                const bool greater = ki > kp || (ki == kp && ii > ip);
+                if (greater == up) {
+                    key[i] = kp;
+                    key[p] = ki;
+                    idx[i] = ip;
+                    idx[p] = ii;
                 }
             }
             __syncthreads();
