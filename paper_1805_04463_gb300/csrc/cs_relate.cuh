@@ -77,6 +77,30 @@ __device__ __forceinline__ float filter_s2(const float (&rc)[4], float4 x) {
     return s2;
 }
 
+// The lane-per-word form's chain: 2^23 - s2 = 2^23 - dt^2 + dx^2 + dy^2
+// (+ dz^2), each square added by one fused multiply-add.  Every partial
+// result is below 2^44 in magnitude, so each of the (at most four) roundings
+// is at most 2^20 and the value lies within 2^22 of the exact one: negative
+// means s2 > 2^23 - 2^22 > 0 (related), above 2^24 means s2 < 0, and only
+// [0, 2^24] needs the exact test.
+template <int DIM>
+__device__ __forceinline__ float filter_offset(const float (&rc)[4], float4 x) {
+    const float dt = x.x - rc[0];
+    float s = fmaf(-dt, dt, kFilterSlack);
+    const float dx = x.y - rc[1];
+    s = fmaf(dx, dx, s);
+    const float dy = x.z - rc[2];
+    s = fmaf(dy, dy, s);
+    if constexpr (DIM == 4) {
+        const float dz = x.w - rc[3];
+        s = fmaf(dz, dz, s);
+    }
+    return s;
+}
+// Bits of the float 2^24: a value in [+0, 2^24] has bits at most this as an
+// unsigned integer, and every negative value (sign bit set) has more.
+constexpr uint32_t kBandBits = 0x4B800000u;
+
 // The exact int64 test on the same (integral) coordinates.
 template <int DIM>
 __device__ __forceinline__ bool exact_related(const float (&rc)[4], float4 x) {
@@ -215,9 +239,9 @@ __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coo
 // 2+1) at st4[c * 32 + (w ^ (c & 7))] for column 64 w + c of the block: one
 // 16-byte load per column and lane, conflict-free for the lanes' loads of
 // one offset c and for the staging stores of consecutive columns.  A test is
-// the filter chain and a funnel shift of the sign of kFilterSlack - s2 (set
-// iff s2 > kFilterSlack, related) into the half-word's accumulator; a word
-// that met any |s2| <= kFilterSlack (near the light cone, about one word in
+// filter_offset's chain, a funnel shift of its sign (set: related) into the
+// half-word's accumulator and an unsigned minimum of its bits; a word whose
+// minimum shows a value in [0, 2^24] (near the light cone, about one word in
 // a thousand) is recomputed exactly by its lane.  Columns at or beyond n are
 // staged 10^9 units away in space (far outside the cone and the band) and
 // masked off.  The row tile's own word (lane ws, which holds the diagonal)
@@ -238,14 +262,14 @@ __device__ __forceinline__ void relate_rows_filtered(const int32_t* __restrict__
     for (int64_t ib = r0 + int64_t(warp) * kFiltRows; ib < r1; ib += int64_t(kWarps) * kFiltRows) {
         float rc[kFiltRows][4];
         uint32_t lo[kFiltRows], hi[kFiltRows];
-        bool amb[kFiltRows];
+        uint32_t band[kFiltRows];  // unsigned minimum of the chain's bits
 #pragma unroll
         for (int r = 0; r < kFiltRows; ++r) {
             const int64_t i = ib + r;
 #pragma unroll
             for (int d = 0; d < 4; ++d) rc[r][d] = (d < DIM && i < r1) ? float(coords[d * n + i]) : 0.0f;
             lo[r] = hi[r] = 0u;
-            amb[r] = false;
+            band[r] = ~0u;
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -255,11 +279,10 @@ __device__ __forceinline__ void relate_rows_filtered(const int32_t* __restrict__
                 const float4 x = st4[c * 32 + (lane ^ (c & 7))];
 #pragma unroll
                 for (int r = 0; r < kFiltRows; ++r) {
-                    const float s2 = filter_s2<DIM>(rc[r], x);
-                    const uint32_t sgn = __float_as_uint(kFilterSlack - s2);
-                    if (h == 0) lo[r] = __funnelshift_l(sgn, lo[r], 1);
-                    else hi[r] = __funnelshift_l(sgn, hi[r], 1);
-                    amb[r] |= fabsf(s2) <= kFilterSlack;
+                    const uint32_t sb = __float_as_uint(filter_offset<DIM>(rc[r], x));
+                    if (h == 0) lo[r] = __funnelshift_l(sb, lo[r], 1);
+                    else hi[r] = __funnelshift_l(sb, hi[r], 1);
+                    band[r] = min(band[r], sb);
                 }
             }
         }
@@ -268,7 +291,7 @@ __device__ __forceinline__ void relate_rows_filtered(const int32_t* __restrict__
             const int64_t i = ib + r;
             if (i >= r1) break;  // warp-uniform
             uint64_t word = ((uint64_t(hi[r]) << 32) | lo[r]) & valid;
-            if (amb[r] && lane != ws && lane >= wbeg) {  // near the light cone: the word exactly
+            if (band[r] <= kBandBits && lane != ws && lane >= wbeg) {  // near the light cone: the word exactly
                 word = 0ull;
                 for (int c = 0; c < 64 && cw + c < n; ++c)
                     if (rel_filtered<DIM>(rc[r], st4[c * 32 + (lane ^ (c & 7))])) word |= 1ull << c;
