@@ -167,15 +167,28 @@ __host__ __device__ __forceinline__ int64_t chunk_sum(int64_t x) {
     return kRelWordsPerBlock * a * (a + 1) / 2 + b * (a + 1);
 }
 
+// Relation geometry of a kind.
+__host__ __device__ __forceinline__ int batch_geom(int kind) {
+    return kind == CS_4D_DIAMOND                               ? kGeom4
+           : kind == CS_3D_DIAMOND                             ? kGeom3
+           : (kind == CS_2D_DS_SLAB || kind == CS_2D_CYLINDER) ? kGeomDeSitter
+                                                               : kGeomLightCone;
+}
+
 // One block per relate chunk of one set, the set read from a table built at
 // create time, the (row tile, chunk) by a binary search over row tiles.  The
-// last chunk of a row tile also zeroes the row's padding words.
+// last chunk of a row tile also zeroes the row's padding words.  One
+// instance per geometry, each launched over all chunks (the other
+// geometries' blocks return at once), so that every geometry's code gets
+// the registers it needs for itself.
+template <int G>
 __global__ void __launch_bounds__(kRelThreads, 5) k_batch_relate(const BatchSet* __restrict__ sets,
                                                               const int32_t* __restrict__ rblock_set) {
     __shared__ __align__(16) int32_t sc[kStageInts];
     {
         const int64_t blk = blockIdx.x;
         const BatchSet& b = sets[rblock_set[blk]];
+        if (batch_geom(b.kind) != G) return;
         const int64_t local = blk - b.rblock_begin;
         const int64_t V = b.vwords, total = chunk_sum(V);
         int64_t lo = 0, hi = V - 1;  // last row tile whose first chunk is at or before `local`
@@ -186,15 +199,8 @@ __global__ void __launch_bounds__(kRelThreads, 5) k_batch_relate(const BatchSet*
         const int64_t rb = lo;
         const int64_t w0 = rb + (local - (total - chunk_sum(V - rb))) * kRelWordsPerBlock;
         const int64_t zero_from = w0 + kRelWordsPerBlock >= V ? w0 + kRelWordsPerBlock : -1;
-        if (b.kind == CS_4D_DIAMOND)
-            relate_block<kGeom4>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, false, zero_from);
-        else if (b.kind == CS_3D_DIAMOND)
-            relate_block<kGeom3>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, false, zero_from);
-        else if (b.kind == CS_2D_DS_SLAB || b.kind == CS_2D_CYLINDER)
-            relate_block<kGeomDeSitter>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, false, zero_from);
-        else
-            relate_block<kGeomLightCone>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, b.kind == CS_2D_ORDER,
-                                         zero_from);
+        relate_block<G>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, G == kGeomLightCone && b.kind == CS_2D_ORDER,
+                        zero_from);
     }
 }
 
@@ -312,6 +318,7 @@ struct cs_batch {
     int32_t* etab = nullptr;  // expansion chunk -> count-table entry
     int32_t* mtab = nullptr;  // mirror block -> set
     int64_t total_mblocks = 0;
+    unsigned geoms = 0;  // bit G: some set relates with geometry G
     int max_pow2 = 1;
     const uint64_t* ds_thr = nullptr;  // de Sitter thresholds, when a set needs them
     dd* coef = nullptr;                 // smeared-sum coefficient tables
@@ -502,6 +509,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     h->sets_dev = reinterpret_cast<BatchSet*>(ws + L.sets);
     h->total_elems = elem;
     h->total_rblocks = rblk;
+    for (int s = 0; s < n_sets; ++s) h->geoms |= 1u << batch_geom(sets[s].kind);
     h->total_items = items;
     h->total_chunks = chunks;
     h->rtab = reinterpret_cast<int32_t*>(ws + L.rtab);
@@ -581,7 +589,14 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
     k_batch_rank<<<unsigned(b->nsets), kRankThreads, rank_smem, st>>>(b->sets_dev);
 
     if (b->total_rblocks > int64_t(0x7fffffff)) return CS_EINVAL;
-    k_batch_relate<<<unsigned(b->total_rblocks), kRelThreads, 0, st>>>(b->sets_dev, b->rtab);
+    if (b->geoms & (1u << kGeomLightCone))
+        k_batch_relate<kGeomLightCone><<<unsigned(b->total_rblocks), kRelThreads, 0, st>>>(b->sets_dev, b->rtab);
+    if (b->geoms & (1u << kGeom3))
+        k_batch_relate<kGeom3><<<unsigned(b->total_rblocks), kRelThreads, 0, st>>>(b->sets_dev, b->rtab);
+    if (b->geoms & (1u << kGeom4))
+        k_batch_relate<kGeom4><<<unsigned(b->total_rblocks), kRelThreads, 0, st>>>(b->sets_dev, b->rtab);
+    if (b->geoms & (1u << kGeomDeSitter))
+        k_batch_relate<kGeomDeSitter><<<unsigned(b->total_rblocks), kRelThreads, 0, st>>>(b->sets_dev, b->rtab);
     if (b->total_mblocks > int64_t(0x7fffffff)) return CS_EINVAL;
     k_batch_mirror<<<unsigned(b->total_mblocks), kRelThreads, 0, st>>>(b->sets_dev, b->mtab);
     if ((err = cudaGetLastError()) != cudaSuccess) return CS_ECUDA;

@@ -160,6 +160,37 @@ __device__ __forceinline__ void store_row_words(uint64_t* __restrict__ bits, int
     if (zero_from >= 0 && zero_from + lane < row_words) bits[i * row_words + zero_from + lane] = 0ull;
 }
 
+// The lane layout of the lane-per-word forms: W words from w0 (a power of
+// two, at most 32, the fewest covering the chunk's valid words), lane l
+// testing word l % W for the rows of row group l / W.  A chunk at the end of
+// a row with few valid words then keeps its lanes busy on more rows instead
+// of on words past the row's end.
+__device__ __forceinline__ int lane_words(int64_t valid) {
+    int W = 1;
+    while (W < valid && W < kRelWordsPerBlock) W <<= 1;
+    return W;
+}
+
+// Per row of the block, all lanes of a warp: the row tile's own word when
+// ws >= 0 (own(i, k): the relation of row i with column offset k of word ws,
+// folded by two ballots) and the zero padding words [z0, z1) of the row.
+template <class Own>
+__device__ __forceinline__ void own_words_and_padding(uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
+                                                      int64_t r0, int64_t r1, int ws, int64_t z0, int64_t z1,
+                                                      Own own) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kWarps = kRelThreads / 32;
+    if (ws < 0 && z0 >= z1) return;
+    for (int64_t i = r0 + warp; i < r1; i += kWarps) {
+        if (ws >= 0) {
+            const bool b0 = own(i, lane), b1 = own(i, lane + 32);
+            const uint64_t d = (uint64_t(__ballot_sync(0xffffffffu, b1)) << 32) | __ballot_sync(0xffffffffu, b0);
+            if (lane == 0) bits[i * row_words + w0 + ws] = d;
+        }
+        for (int64_t w = z0 + lane; w < z1; w += 32) bits[i * row_words + w] = 0ull;
+    }
+}
+
 template <bool USE_U>
 __device__ __forceinline__ void relate_rows_cone(const int32_t* __restrict__ coords, int64_t n,
                                                  uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
@@ -252,20 +283,28 @@ constexpr int kFiltRows = 2;  // rows a lane tests together (the 48-register bud
 template <int DIM>
 __device__ __forceinline__ void relate_rows_filtered(const int32_t* __restrict__ coords, int64_t n,
                                                      uint64_t* __restrict__ bits, int64_t row_words, int64_t w0,
-                                                     int64_t c0, int64_t r0, int64_t r1, int ws,
-                                                     const float4* __restrict__ st4, int64_t zero_from) {
+                                                     int64_t c0, int64_t r0, int64_t r1, int ws, int W,
+                                                     const float4* __restrict__ st4) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kWarps = kRelThreads / 32;
     const int wbeg = ws > 0 ? ws : 0;
-    const int64_t cw = c0 + 64 * int64_t(lane);  // this lane's first column
+    const int wl = lane & (W - 1);                                   // this lane's word
+    const int64_t pass = int64_t(kFiltRows) * (kRelWordsPerBlock / W);  // rows of one warp pass
+    const int64_t g0 = int64_t(lane / W) * kFiltRows;                 // this lane's first row in a pass
+    // with W = 32 a pass's rows are the same in every lane, and the row
+    // tile's own word is folded by ballots right here; narrower layouts
+    // leave it to own_words_and_padding
+    const bool inline_own = W == kRelWordsPerBlock && ws >= 0;
+    const bool keep = wl >= wbeg && (wl != ws || inline_own) && w0 + wl < row_words;
+    const int64_t cw = c0 + 64 * int64_t(wl);  // this lane's first column
     const uint64_t valid = cw >= n ? 0ull : (n - cw >= 64 ? ~0ull : (~0ull >> (64 - (n - cw))));
-    for (int64_t ib = r0 + int64_t(warp) * kFiltRows; ib < r1; ib += int64_t(kWarps) * kFiltRows) {
+    for (int64_t ib = r0 + int64_t(warp) * pass; ib < r1; ib += int64_t(kWarps) * pass) {
         float rc[kFiltRows][4];
         uint32_t lo[kFiltRows], hi[kFiltRows];
         uint32_t band[kFiltRows];  // unsigned minimum of the chain's bits
 #pragma unroll
         for (int r = 0; r < kFiltRows; ++r) {
-            const int64_t i = ib + r;
+            const int64_t i = ib + g0 + r;
 #pragma unroll
             for (int d = 0; d < 4; ++d) rc[r][d] = (d < DIM && i < r1) ? float(coords[d * n + i]) : 0.0f;
             lo[r] = hi[r] = 0u;
@@ -276,7 +315,7 @@ __device__ __forceinline__ void relate_rows_filtered(const int32_t* __restrict__
             // highest column first: after 32 shifts column 32 h is bit 0
 #pragma unroll 4
             for (int c = 32 * h + 31; c >= 32 * h; --c) {
-                const float4 x = st4[c * 32 + (lane ^ (c & 7))];
+                const float4 x = st4[c * 32 + (wl ^ (c & 7))];
 #pragma unroll
                 for (int r = 0; r < kFiltRows; ++r) {
                     const uint32_t sb = __float_as_uint(filter_offset<DIM>(rc[r], x));
@@ -288,15 +327,15 @@ __device__ __forceinline__ void relate_rows_filtered(const int32_t* __restrict__
         }
 #pragma unroll
         for (int r = 0; r < kFiltRows; ++r) {
-            const int64_t i = ib + r;
-            if (i >= r1) break;  // warp-uniform
+            const int64_t i = ib + g0 + r;
             uint64_t word = ((uint64_t(hi[r]) << 32) | lo[r]) & valid;
-            if (band[r] <= kBandBits && lane != ws && lane >= wbeg) {  // near the light cone: the word exactly
+            if (keep && i < r1 && wl != ws && band[r] <= kBandBits) {  // near the light cone: the word exactly
                 word = 0ull;
                 for (int c = 0; c < 64 && cw + c < n; ++c)
-                    if (rel_filtered<DIM>(rc[r], st4[c * 32 + (lane ^ (c & 7))])) word |= 1ull << c;
+                    if (rel_filtered<DIM>(rc[r], st4[c * 32 + (wl ^ (c & 7))])) word |= 1ull << c;
             }
-            if (ws >= 0) {  // the row tile's own word (warp-uniform)
+            if (inline_own) {
+                if (i >= r1) break;  // warp-uniform (g0 = 0)
                 bool b[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -306,7 +345,7 @@ __device__ __forceinline__ void relate_rows_filtered(const int32_t* __restrict__
                 const uint64_t d = (uint64_t(__ballot_sync(0xffffffffu, b[1])) << 32) | __ballot_sync(0xffffffffu, b[0]);
                 if (lane == ws) word = d;
             }
-            store_row_words(bits, i, row_words, w0, lane, wbeg, word, zero_from);
+            if (keep && i < r1) bits[i * row_words + w0 + wl] = word;
         }
     }
 }
@@ -335,6 +374,15 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
     const int wbeg = ws > 0 ? ws : 0;
     const int64_t r0 = rb * kRelRowsPerBlock;
     const int64_t r1 = r0 + kRelRowsPerBlock < n ? r0 + kRelRowsPerBlock : n;
+    // The filtered 3+1 and 2+1 form tests W = lane_words(valid words) words
+    // from w0 and zeroes the row's words [w0 + W, z1) past them: the rest of
+    // the block's 32, and, at a row's last chunk (zero_from >= 0), the
+    // padding to row_words.  (The light-cone test, at a few instructions,
+    // gained less from narrow blocks than their fixed costs took, and keeps
+    // all 32 lanes on words.)
+    const int64_t z1 = zero_from >= 0 ? row_words : (w0 + kRelWordsPerBlock < row_words ? w0 + kRelWordsPerBlock
+                                                                                          : row_words);
+    auto pad_from = [&](int W) { return w0 + W < z1 ? w0 + W : z1; };
     if constexpr (G == kGeomLightCone) {  // time order: one cone per word, see above
         // transposed staging, word w of the block at row offset c: column 64 w + c
         for (int t = threadIdx.x + 64 * wbeg; t < kRelColsPerBlock; t += kRelThreads) {
@@ -393,7 +441,18 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
                     st4[c * 32 + (w ^ (c & 7))] = make_float4(f[0], f[1], f[2], f[3]);
                 }
                 __syncthreads();
-                relate_rows_filtered<DIM>(coords, n, bits, row_words, w0, c0, r0, r1, ws, st4, zero_from);
+                // the row tile's own word (it holds the diagonal): the filtered test
+                auto own = [&](int64_t i, int k) {
+                    if (c0 + int64_t(ws) * 64 + k >= n) return false;
+                    float rc[4];
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) rc[d] = d < DIM ? float(coords[d * n + i]) : 0.0f;
+                    return rel_filtered<DIM>(rc, st4[k * 32 + (ws ^ (k & 7))]);
+                };
+                const int W = lane_words((n + 63) / 64 - w0);
+                relate_rows_filtered<DIM>(coords, n, bits, row_words, w0, c0, r0, r1, ws, W, st4);
+                own_words_and_padding(bits, row_words, w0, r0, r1, W == kRelWordsPerBlock ? -1 : ws, pad_from(W), z1,
+                                      own);
                 return;
             }
         }
