@@ -45,7 +45,8 @@ typedef enum {
     CS_ECUDA = -3,         /* CUDA runtime / launch error */
     CS_ETIMEOUT = -4,      /* a bounded in-kernel wait gave up */
     CS_EUNSUPPORTED = -5,  /* path or feature not available on this device */
-    CS_ERANGE = -6         /* sampler exhausted its attempt budget */
+    CS_ERANGE = -6,        /* sampler exhausted its attempt budget */
+    CS_PENDING = 1         /* not an error: work that was polled has not finished yet */
 } cs_status;
 
 /* Causal-set kinds (Appendix "Causal Set Sprinklings"). */
@@ -149,9 +150,22 @@ int cs_causal_matrix(int kind, int64_t n, const int32_t *coords_dev,
 
 /* The path cs_interval_abundance runs for (n, path) on the current device:
  * CS_PATH_POPC, CS_PATH_MMA or CS_PATH_MMA4 (CS_PATH_AUTO follows the table
- * below; the tensor-core paths only where the device has tcgen05); -1 for
- * invalid arguments. */
+ * below; the tensor-core paths only where the device has tcgen05, and only
+ * while the set's bitset plus the path's workspace fit the AUTO memory limit
+ * -- a table entry of CS_PATH_MMA that does not fit falls back to
+ * CS_PATH_MMA4, one of CS_PATH_MMA4 to CS_PATH_POPC); -1 for invalid
+ * arguments.  The rule depends only on n, the table and the limit, so the
+ * workspace query and the count resolve alike. */
 int cs_resolved_path(int64_t n, int path);
+
+/* The device memory, in bytes, that CS_PATH_AUTO may plan a set's bitset and
+ * count workspace into (process-wide).  0 (the default) means 90% of the
+ * current device's memory.  Set it lower when other work shares the GPU.
+ * Returns CS_OK. */
+int cs_set_auto_memory_limit(size_t bytes);
+
+/* The limit in force on the current device (bytes). */
+size_t cs_get_auto_memory_limit(void);
 
 /*
  * The CS_PATH_AUTO table, process-wide: entry e selects paths[e]
@@ -341,6 +355,20 @@ int cs_batch_create(const cs_set_desc *sets, int n_sets, int path, void *workspa
  */
 int cs_batch_launch(const cs_batch *b, const double *eps_host, int n_eps, int64_t *hist_dev,
                     double *actions_dev, int64_t *brackets_dev, void *stream);
+
+/*
+ * Poll the plan's last launch without waiting: CS_PENDING while the work it
+ * enqueued (or the last replay of a CUDA graph that captured it) is still
+ * running; once it has finished, the in-kernel status word of that launch
+ * (CS_OK, or the first error a kernel recorded, e.g. CS_ETIMEOUT).  Each
+ * launch ends by copying the status word to pinned host memory owned by the
+ * plan and recording an event (an external event node under capture); the
+ * poll queries that event and reads the copy, so it never synchronises and
+ * enqueues nothing.  Before the first launch it returns CS_OK.  Do not
+ * destroy the plan while a launch may still be running.
+ * Errors: CS_EINVAL (NULL), CS_ECUDA (the event query failed).
+ */
+int cs_batch_poll(const cs_batch *b);
 
 /* The count path a plan runs (CS_PATH_POPC, CS_PATH_MMA or CS_PATH_MMA4;
  * CS_PATH_AUTO plans CS_PATH_MMA where the device has tcgen05), -1 for NULL. */

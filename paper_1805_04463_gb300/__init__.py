@@ -20,7 +20,7 @@ __all__ = [
     "KIND_2D_ORDER", "KIND_2D_DIAMOND", "KIND_4D_DIAMOND", "KIND_3D_DIAMOND", "KIND_2D_DS_SLAB", "KIND_2D_SQUARE", "KIND_2D_CYLINDER", "PATH_AUTO", "PATH_POPC", "PATH_MMA", "PATH_MMA4",
     "CsError", "lib", "dim", "coords_bytes", "row_words", "bitset_bytes", "hist_len",
     "sprinkle_workspace_bytes", "interval_abundance_workspace", "resolved_path", "action_workspace_bytes",
-    "set_auto_paths", "get_auto_paths",
+    "set_auto_paths", "get_auto_paths", "set_auto_memory_limit", "get_auto_memory_limit",
     "sprinkle", "sprinkle_noalloc", "causal_matrix", "layer_sums", "dalembertian", "interval_abundance", "workspace_status", "action", "action_device",
     "evaluate", "Buffers", "allocate", "run", "SetDesc", "Batch", "CountJob", "count_items",
     "operands_bytes", "prepare_operands", "peak_probe", "count_jobs", "degrees", "sparse_relations", "longest_chain", "greedy_antichain", "BATCH_MAX_N", "FAULT_ALLOC", "FAULT_LAUNCH", "selftest_wait",
@@ -30,6 +30,7 @@ __all__ = [
 KIND_2D_ORDER, KIND_2D_DIAMOND, KIND_4D_DIAMOND, KIND_3D_DIAMOND, KIND_2D_DS_SLAB = 0, 1, 2, 3, 4
 KIND_2D_SQUARE, KIND_2D_CYLINDER = 5, 6
 PATH_AUTO, PATH_POPC, PATH_MMA, PATH_MMA4 = 0, 1, 2, 3
+PENDING = 1  # CS_PENDING: polled work still running
 FAULT_ALLOC, FAULT_LAUNCH = 1, 2
 BATCH_MAX_N = 8192  # CS_BATCH_MAX_N: largest set a batch takes
 KIND_NAMES = {KIND_2D_ORDER: "2d_order", KIND_2D_DIAMOND: "2d_diamond", KIND_4D_DIAMOND: "4d_diamond",
@@ -80,6 +81,8 @@ def lib() -> ctypes.CDLL:
             "cs_resolved_path": ([i64, i32], i32),
             "cs_set_auto_paths": ([vp, vp, i32], i32),
             "cs_get_auto_paths": ([vp, vp, i32], i32),
+            "cs_set_auto_memory_limit": ([sz], i32),
+            "cs_get_auto_memory_limit": ([], sz),
             "cs_interval_abundance": ([i64, vp, i64, vp, i32, vp, sz, vp], i32),
             "cs_workspace_status": ([vp, vp], i32),
             "cs_layer_sums": ([i64, vp, i64, vp, i32, vp, i32, vp, vp, sz, vp], i32),
@@ -94,6 +97,7 @@ def lib() -> ctypes.CDLL:
             "cs_batch_create": ([vp, i32, i32, vp, sz, ctypes.POINTER(ctypes.c_void_p), vp], i32),
             "cs_batch_launch": ([vp, vp, i32, vp, vp, vp, vp], i32),
             "cs_batch_path": ([vp], i32),
+            "cs_batch_poll": ([vp], i32),
             "cs_batch_destroy": ([vp], None),
             "cs_count_items": ([i64, i32], i64),
             "cs_operands_bytes": ([i64, i32], sz),
@@ -193,6 +197,15 @@ def get_auto_paths():
     p = (ctypes.c_int * cnt)()
     lib().cs_get_auto_paths(n, p, cnt)
     return [(int(n[i]), int(p[i])) for i in range(cnt)]
+
+
+def set_auto_memory_limit(nbytes: int = 0):
+    """cs_set_auto_memory_limit: device bytes CS_PATH_AUTO may plan into (0 = 90% of the device)."""
+    _check(lib().cs_set_auto_memory_limit(int(nbytes)), "cs_set_auto_memory_limit")
+
+
+def get_auto_memory_limit() -> int:
+    return lib().cs_get_auto_memory_limit()
 
 
 def action_workspace_bytes() -> int:
@@ -377,6 +390,10 @@ class Batch:
 
     def status(self, stream=None) -> int:
         return lib().cs_workspace_status(self.ws_ptr, _stream(stream))
+
+    def poll(self) -> int:
+        """cs_batch_poll: PENDING (1) while the last launch runs, then its status (0 = ok); never waits."""
+        return lib().cs_batch_poll(self._h)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -44,6 +44,27 @@ int64_t g_auto_n[kMaxAuto] = {0, 1024, 4096};
 int g_auto_p[kMaxAuto] = {CS_PATH_POPC, CS_PATH_MMA, CS_PATH_MMA4};
 int g_auto_count = 3;
 
+// Device memory AUTO may plan for: the caller's limit, or 90% of the
+// device's memory when none is set.
+std::atomic<size_t> g_auto_mem_limit{0};
+
+size_t auto_memory_limit() {
+    const size_t lim = g_auto_mem_limit.load(std::memory_order_relaxed);
+    return lim ? lim : device_total_memory() / 10 * 9;
+}
+
+size_t tensor_workspace_bytes(int64_t n, int p) {
+    return p == CS_PATH_MMA ? mma_workspace_bytes(n) : mma4_workspace_bytes(n);
+}
+
+// A tensor path fits when the set's bitset and the path's workspace together
+// stay within the AUTO memory limit.  The rule reads the device's capacity,
+// not its free memory, so that the workspace query and the count call that
+// follows it (after the caller allocated that workspace) resolve alike.
+bool tensor_fits(int64_t n, int p) {
+    return cs_bitset_bytes(n) + tensor_workspace_bytes(n, p) <= auto_memory_limit();
+}
+
 int resolve_path(int64_t n, int path) {
     if (path != CS_PATH_AUTO) return path;
     int p = CS_PATH_POPC;
@@ -52,7 +73,12 @@ int resolve_path(int64_t n, int path) {
         for (int e = 0; e < g_auto_count; ++e)
             if (n >= g_auto_n[e]) p = g_auto_p[e];
     }
-    return ((p == CS_PATH_MMA || p == CS_PATH_MMA4) && !device_has_tcgen05()) ? CS_PATH_POPC : p;
+    if ((p == CS_PATH_MMA || p == CS_PATH_MMA4) && !device_has_tcgen05()) return CS_PATH_POPC;
+    // Too large for the table's tensor path: the FP4 path's smaller
+    // workspace, else the POPC path, which needs no operands.
+    if (p == CS_PATH_MMA && !tensor_fits(n, CS_PATH_MMA)) p = CS_PATH_MMA4;
+    if (p == CS_PATH_MMA4 && !tensor_fits(n, CS_PATH_MMA4)) p = CS_PATH_POPC;
+    return p;
 }
 
 }  // namespace cs
@@ -127,6 +153,13 @@ int cs_set_auto_paths(const int64_t* n_min, const int* paths, int count) {
     g_auto_count = count;
     return CS_OK;
 }
+
+int cs_set_auto_memory_limit(size_t bytes) {
+    g_auto_mem_limit.store(bytes, std::memory_order_relaxed);
+    return CS_OK;
+}
+
+size_t cs_get_auto_memory_limit(void) { return auto_memory_limit(); }
 
 int cs_get_auto_paths(int64_t* n_min, int* paths, int capacity) {
     std::lock_guard<std::mutex> lk(g_auto_mu);
@@ -336,6 +369,7 @@ const char* cs_strerror(int status) {
         case CS_ETIMEOUT: return "bounded in-kernel wait timed out";
         case CS_EUNSUPPORTED: return "unsupported on this device";
         case CS_ERANGE: return "sampler exhausted its attempt budget";
+        case CS_PENDING: return "pending: the polled work has not finished";
         default: return "unknown status";
     }
 }

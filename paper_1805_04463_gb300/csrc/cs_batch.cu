@@ -324,6 +324,14 @@ struct cs_batch {
     dd* coef = nullptr;                 // smeared-sum coefficient tables
     int64_t nmax[kDimSlots] = {0, 0, 0};  // largest n per dimension slot (0: absent)
     int64_t coef_base[kDimSlots] = {0, 0, 0};
+    // cs_batch_poll: each launch copies the status word here (pinned) and
+    // records `done` after it.
+    int32_t* status_host = nullptr;
+    cudaEvent_t done = nullptr;
+    ~cs_batch() {
+        if (done) cudaEventDestroy(done);
+        if (status_host) cudaFreeHost(status_host);
+    }
 };
 
 namespace {
@@ -502,6 +510,13 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     }
     cs_batch* h = new (std::nothrow) cs_batch;
     if (!h) return CS_ENOMEM;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&h->status_host), sizeof(int32_t), cudaHostAllocDefault) !=
+            cudaSuccess ||
+        cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) {
+        delete h;
+        return CS_ECUDA;
+    }
+    *h->status_host = CS_OK;
     h->nsets = n_sets;
     h->path = p;
     h->ws = ws;
@@ -641,7 +656,24 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
                                                                   actions_dev, brackets_dev);
         if (cudaGetLastError() != cudaSuccess) return CS_ECUDA;
     }
+    // For cs_batch_poll: the status word to the plan's pinned copy, then the
+    // event (recorded as an external event node when the stream is captured).
+    if (cudaMemcpyAsync(b->status_host, &b->hdr->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaEventRecordWithFlags(b->done, st, cudaEventRecordExternal) != cudaSuccess)
+        return CS_ECUDA;
     return CS_OK;
+}
+
+int cs_batch_poll(const cs_batch* b) {
+    if (!b) return CS_EINVAL;
+    const cudaError_t q = cudaEventQuery(b->done);
+    if (q == cudaErrorNotReady) {
+        cudaGetLastError();  // not sticky; keep it from the caller's next check
+        return CS_PENDING;
+    }
+    if (q != cudaSuccess) return CS_ECUDA;
+    return *static_cast<volatile int32_t*>(b->status_host);
 }
 
 int cs_batch_path(const cs_batch* b) { return b ? b->path : -1; }

@@ -12,6 +12,7 @@ namespace {
 struct DevProps {
     int sm_count = 0;
     int major = 0, minor = 0;
+    size_t total_mem = 0;
     bool valid = false;
 };
 
@@ -28,6 +29,8 @@ const DevProps& props() {
         cudaDeviceGetAttribute(&p.major, cudaDevAttrComputeCapabilityMajor, dev);
         cudaDeviceGetAttribute(&p.minor, cudaDevAttrComputeCapabilityMinor, dev);
         if (p.sm_count < 1) p.sm_count = 1;
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) p.total_mem = total_b;
         p.valid = true;
     }
     return p;
@@ -39,6 +42,8 @@ std::once_flag g_encode_once;
 }  // namespace
 
 int device_sm_count() { return props().sm_count; }
+
+size_t device_total_memory() { return props().total_mem; }
 
 // The kernels are built for sm_103a only; tcgen05 is present on compute
 // capability 10.x.

@@ -193,18 +193,6 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
     return ok != 0;
 }
 
-// 2D tiled TMA load multicast to the CTAs of `mask`: the box lands at the same
-// shared-memory offset in each, and each one's mbarrier at `bar`'s offset
-// receives the byte count.
-__device__ __forceinline__ void tma_load_2d_mc(void* smem_dst, const CUtensorMap* map, int32_t x, int32_t y,
-                                               uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%2, %3}], [%4], %5;"
-        ::"r"(smem_u32(smem_dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
 // Wait like mbar_wait_bounded, but also give up early once another warp of
 // the CTA has raised *abort (set after its own wait timed out).
 // kCluster: acquire at cluster scope (phases completed by other CTAs).

@@ -8,7 +8,8 @@ namespace cs {
 // cs_sprinkle.cu
 size_t sprinkle_workspace_bytes(int64_t n);
 // Device copy of the de Sitter slab's cumulative eta thresholds (uploaded
-// once per device, synchronously, on first use); nullptr on failure.
+// once per device, synchronously, on first use); nullptr on failure, and a
+// failed upload is tried again on the next call.
 const uint64_t* ds_table_device();
 cudaError_t launch_sprinkle(int kind, int64_t n, uint64_t seed, int32_t* coords, void* workspace,
                             cudaStream_t st);
@@ -115,6 +116,7 @@ bool fault_injected(int where);
 // Device properties cached per device.
 int device_sm_count();
 bool device_has_tcgen05();
+size_t device_total_memory();  // bytes of device memory (0 if unknown)
 
 // cuTensorMapEncodeTiled, resolved once through the runtime's driver entry point.
 CUresult encode_tensor_map_2d(CUtensorMap* map, CUtensorMapDataType type, void* base, uint64_t dim0,

@@ -3,11 +3,17 @@
 // row; Section "Lorentzian Geometry": related iff Delta s^2 < 0).
 //
 // A block owns 2048 columns (32 words) and 64 rows (relate_block): column
-// coordinates are staged once in shared memory, each warp folds 64 tests per
-// word into a uint64 with two __ballot_sync, and a row's 32 words leave in
-// one coalesced 256-byte store.  64 x 64 tiles wholly below the diagonal
-// are not tested: k_mirror fills them as transposes of the tiles above (the
-// relation is symmetric), which halves the tests.
+// coordinates are staged once in shared memory, and each lane owns one
+// 64-column word of a row.  For the words wholly after the row (labels are
+// in time order, so only the future cone can hold there) the lane builds
+// the word from the sign bits of integer multiply-adds (light cone) or of
+// an FP32 filter with an exact int64 recompute near the cone (2+1, 3+1),
+// funnel-shifting one sign per column into the word; the row's own word,
+// which holds the diagonal, takes the full symmetric test by two
+// __ballot_sync.  A row's words leave in coalesced stores.  64 x 64 tiles
+// wholly below the diagonal are not tested: k_mirror fills them as bit
+// transposes of the tiles above (the relation is symmetric), which halves
+// the tests.
 #include "cs_kernels.cuh"
 #include "cs_relate.cuh"
 

@@ -9,6 +9,7 @@
 // bits (a counting pass, a scan, a fill), and each element compares itself
 // only with its bucket -- O(n + 65536) work for the hashed / uniform keys used
 // here, and the same ranks for any bucket fill order.
+#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -29,8 +30,8 @@ constexpr int kMaxDevices = 64;
 // with the C library's tan, is part of the generator's definition, so the
 // table is built on the host.
 static __device__ uint64_t g_ds_thresholds[kDsTable];
-const uint64_t* g_ds_ptr[kMaxDevices];
-std::once_flag g_ds_once[kMaxDevices];
+std::atomic<const uint64_t*> g_ds_ptr[kMaxDevices];
+std::mutex g_ds_mu;
 
 std::vector<uint64_t> ds_thresholds_host() {
     std::vector<uint64_t> t(kDsTable);
@@ -224,14 +225,22 @@ cudaError_t rank_keys(int64_t n, const uint64_t* key, uint32_t* rank, uint8_t* w
 const uint64_t* ds_table_device() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-    std::call_once(g_ds_once[dev], [dev] {
-        static const std::vector<uint64_t> host = ds_thresholds_host();
-        void* p = nullptr;
-        if (cudaMemcpyToSymbol(g_ds_thresholds, host.data(), host.size() * sizeof(uint64_t)) == cudaSuccess &&
-            cudaGetSymbolAddress(&p, g_ds_thresholds) == cudaSuccess)
-            g_ds_ptr[dev] = static_cast<const uint64_t*>(p);
-    });
-    return g_ds_ptr[dev];
+    if (const uint64_t* p = g_ds_ptr[dev].load(std::memory_order_acquire)) return p;
+    // Upload under the lock; the pointer is published only after a
+    // successful upload, so a failed first attempt (e.g. made during stream
+    // capture, where the synchronous copy is not allowed) is retried by the
+    // next call instead of disabling the kind for the process.
+    std::lock_guard<std::mutex> lk(g_ds_mu);
+    if (const uint64_t* p = g_ds_ptr[dev].load(std::memory_order_acquire)) return p;
+    static const std::vector<uint64_t> host = ds_thresholds_host();
+    void* p = nullptr;
+    if (cudaMemcpyToSymbol(g_ds_thresholds, host.data(), host.size() * sizeof(uint64_t)) != cudaSuccess ||
+        cudaGetSymbolAddress(&p, g_ds_thresholds) != cudaSuccess) {
+        cudaGetLastError();  // not sticky: clear it for the caller's next call
+        return nullptr;
+    }
+    g_ds_ptr[dev].store(static_cast<const uint64_t*>(p), std::memory_order_release);
+    return static_cast<const uint64_t*>(p);
 }
 
 size_t sprinkle_workspace_bytes(int64_t n) { return sprinkle_layout(n).total; }

@@ -116,3 +116,35 @@ def test_ensemble_driver_resumes_on_the_gpu(cs, oracle, tmp_path):
         assert r["pairs"] == int(want.sum()) and r["hist_head"] == want[:64].tolist()
         s_or, br = oracle.action(oracle.dim(kind), n, want, 0.1)
         assert r["bracket"] == br and abs(r["actions"]["0.1"] - s_or) <= 1e-12 * max(1.0, abs(s_or))
+
+
+def test_batch_poll_reports_pending_then_status(cs):
+    # cs_batch_poll never waits: while the stream is held by a bounded
+    # self-test wait (0.5 s) the launch behind it is still pending; after a
+    # synchronise the poll reads the launch's status word (0).  The same
+    # holds for a CUDA-graph replay of the launch.
+    import torch
+    sets = [(1, 1200 + 50 * s, 700 + s) for s in range(4)] + [(2, 900, 760)]
+    b = cs.Batch(sets, path=0)
+    assert b.poll() == 0                         # nothing launched yet
+    s = torch.cuda.Stream()
+    hold = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(s):
+        cs.selftest_wait(hold, 0.5, complete=False, stream=s)
+        b.launch(EPS, stream=s)
+    assert b.poll() == cs.PENDING
+    s.synchronize()
+    assert b.poll() == 0
+    ref = b.hist.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            b.launch(EPS, stream=s)
+    s.synchronize()
+    with torch.cuda.stream(s):
+        cs.selftest_wait(hold, 0.5, complete=False, stream=s)
+        g.replay()
+    assert b.poll() == cs.PENDING
+    s.synchronize()
+    assert b.poll() == 0 and torch.equal(b.hist, ref)
+    assert cs.workspace_status(hold) == -4       # the hold itself timed out, as intended

@@ -67,6 +67,8 @@ def test_interval_abundance_bit_exact(cs, oracle, kind, n, path):
     seed = 0xC5E71000 + n + kind
     b = _run(cs, kind, n, seed, path=path)
     bits = _np_bits(b)
+    # the bitset the count read is the oracle's for this (kind, n, seed)
+    assert (bits == oracle.causal_matrix(kind, oracle.sprinkle(kind, n, seed))).all()
     want = oracle.interval_abundance(bits)
     assert (b.hist.cpu().numpy() == want).all()
     if n <= 256:
@@ -208,6 +210,31 @@ def test_invalid_arguments_rejected(cs):
 
 # ------------------------------------------------- full-size workloads
 
+def _check_actions(cs, oracle, kind, n, seed, b, want_hist, path):
+    """Local and smeared actions of a full-size set through every entry point
+    that forms them -- cs_action_device on the GPU histogram, cs_action on the
+    host, and cs_evaluate from host buffers -- against the oracle's action on
+    the oracle's own histogram (binary128): within 1e-12 relative, and the
+    integer bracket exact.  At these sizes the smeared sum cancels by orders
+    of magnitude (Eq. s2d_smeared, s4d_smeared), and the device sum's
+    truncation bound, derived from R <= n(n-1)/2, is exercised in full."""
+    import torch
+    d = cs.dim(kind)
+    cs.action_device(d, n, b.hist, list(EPS), b.actions, b.bracket, b.workspace)
+    torch.cuda.synchronize()
+    acts = b.actions.cpu().numpy()
+    _, ev_acts, ev_br = cs.evaluate(kind, n, seed, None, path, EPS)
+    br_or = oracle.action(d, n, want_hist, 0.0)[1]
+    assert int(b.bracket.item()) == br_or and ev_br == br_or
+    for e, eps in enumerate(EPS):
+        s_or, br = oracle.action(d, n, want_hist, eps)
+        tol = TOL * max(1.0, abs(s_or))
+        assert abs(acts[e] - s_or) <= tol, ("device", eps, acts[e], s_or)
+        s_h, br_h = cs.action(d, n, want_hist, eps)
+        assert abs(s_h - s_or) <= tol and br_h == br, ("host", eps, s_h, s_or)
+        assert abs(ev_acts[e] - s_or) <= tol, ("evaluate", eps, ev_acts[e], s_or)
+
+
 def test_full_2d_order_1024_exact(cs, oracle):
     n, seed = 1024, 0xC5E70001
     b = _run(cs, 0, n, seed)
@@ -226,7 +253,9 @@ def test_full_4d_diamond_16384_exact(cs, oracle, path):
     assert (b.coords.cpu().numpy() == c).all()
     bits = oracle.causal_matrix(2, c)
     assert (_np_bits(b) == bits).all()
-    assert (b.hist.cpu().numpy() == oracle.interval_abundance(bits)).all()
+    want = oracle.interval_abundance(bits)
+    assert (b.hist.cpu().numpy() == want).all()
+    _check_actions(cs, oracle, 2, n, seed, b, want, path)
 
 
 def _past_counts(v):
@@ -282,13 +311,21 @@ def test_full_2d_order_131072(cs, oracle, path):
         want[:packed.size // 8] = packed.view(np.uint64)
         assert (bits[i] == want).all(), i
     assert (h == h_dom).all()
+    _check_actions(cs, oracle, 0, n, seed, b, h_dom, path)
+
+
+@functools.lru_cache(maxsize=None)
+def _dominance(n, seed):
+    import oracle as o
+    return o.interval_abundance_dominance2d(o.sprinkle(0, n, seed)[1])
 
 
 @pytest.mark.parametrize("path", [2, 3], ids=["mma", "mma4"])
 def test_largest_set_262144(cs, oracle, path):
-    # n = 2^18, the largest 2D order whose FP8 tensor-core operands (137 GB;
-    # 69 GB in FP4) fit beside its bitset on one GPU: the total and the first moment of N_k from
-    # the coordinates (sum_k N_k = R, sum_k k N_k = chains of three), sampled
+    # n = 2^18, the largest 2D order whose FP8 tensor-core operands (137 GB)
+    # fit beside its bitset on one GPU: every N_k against the bitset-free
+    # dominance count, the total and the first moment of N_k from the
+    # coordinates (sum_k N_k = R, sum_k k N_k = chains of three), sampled
     # bitset rows from the definition, and a full chain at this size, whose
     # counts run up to n - 2 = 262142.
     import torch
@@ -302,6 +339,8 @@ def test_largest_set_262144(cs, oracle, path):
     h = b.hist.cpu().numpy()
     assert int(h.sum()) == int(past.sum())
     assert int((np.arange(h.size) * h).sum()) == int((past * future).sum())
+    # every N_k against the bitset-free dominance count
+    assert (h == _dominance(n, seed)).all()
     bits = b.bits.cpu().numpy().view(np.uint64)
     idx = np.arange(n)
     for i in range(0, n, 8191):

@@ -37,34 +37,44 @@ def _free_port():
 def _worker(rank, world, port, out):
     import torch
     import torch.distributed as dist
+    import oracle
     from paper_1805_04463_gb300.replicas import allreduce_hist, combine_timing, shard_chunks
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    # a fake per-item histogram contribution: item t adds 1 to bin t % 17
-    total = 1000
-    h = torch.zeros(17, dtype=torch.int64)
-    for b, e in shard_chunks(total, world, rank):
-        for t in range(b, e):
-            h[t % 17] += 1
+    # Every rank rebuilds the same seeded 2D order and counts only its share
+    # of the work items -- here the oracle's rows i (each row contributes the
+    # intervals of every pair (i, j > i)), taken in the interleaved ranges
+    # shard_chunks assigns -- and the one sum all-reduce gives every rank
+    # the whole set's N_k.
+    n, seed = 700, 0xC5E70011
+    bits = oracle.causal_matrix(0, oracle.sprinkle(0, n, seed))
+    h = torch.zeros(oracle.hist_len(n), dtype=torch.int64)
+    for b, e in shard_chunks(n, world, rank):
+        h += torch.from_numpy(oracle.interval_abundance(bits, threads=1, rows=(b, e, 1)))
+    mine = int(h.sum())
     allreduce_hist(h, dist)
     ms, work = combine_timing(10.0 + rank, 100.0 * (rank + 1), dist)
-    out[rank] = (h.tolist(), ms, work)
+    out[rank] = (h.tolist(), mine, ms, work)
     dist.destroy_process_group()
 
 
 @pytest.mark.timeout(120)
-def test_gloo_two_ranks_allreduce_and_timing():
+def test_gloo_two_ranks_allreduce_and_timing(oracle):
     world = 2
     mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     port = _free_port()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
-    want = np.bincount(np.arange(1000) % 17, minlength=17).tolist()
+    n, seed = 700, 0xC5E70011
+    want = oracle.interval_abundance(oracle.causal_matrix(0, oracle.sprinkle(0, n, seed)))
     for r in range(world):
-        h, ms, work = out[r]
-        assert h == want
+        h, mine, ms, work = out[r]
+        assert h == want.tolist()
+        # each rank counted a real, non-trivial part of the pairs, not all of them
+        assert 0 < mine < int(want.sum())
         assert ms == 11.0 and work == 300.0
+    assert out[0][1] + out[1][1] == int(want.sum())
 
 
 def test_combine_timing_without_group():

@@ -58,12 +58,16 @@ def test_no_alloc_matches_workspace_entry_point_twice(cs, kind):
         assert torch.equal(got, want), (kind, n)
 
 
-def test_no_alloc_at_its_size_limit_and_beyond(cs):
+@pytest.mark.parametrize("kind", [0, 2, 3, 4], ids=["2d_order", "4d_diamond", "3d_diamond", "ds_slab"])
+def test_no_alloc_at_its_size_limit_and_beyond(cs, kind):
+    # The largest accepted n for the permutation kind, both rejection-sampled
+    # diamonds (their attempt counters share the scratch) and the de Sitter
+    # slab (its table lookups), then one element more, which is refused.
     import torch
-    got = _no_alloc(cs, 0, MAX_N, 99)
-    want = _with_workspace(cs, 0, MAX_N, 99)
+    got = _no_alloc(cs, kind, MAX_N, 99 + kind)
+    want = _with_workspace(cs, kind, MAX_N, 99 + kind)
     assert torch.equal(got, want)
-    coords = torch.empty((2, MAX_N + 1), dtype=torch.int32, device="cuda")
+    coords = torch.empty((cs.dim(kind), MAX_N + 1), dtype=torch.int32, device="cuda")
     st = torch.cuda.current_stream().cuda_stream
-    assert cs.lib().cs_sprinkle_noalloc(0, MAX_N + 1, 1, ctypes.c_void_p(coords.data_ptr()),
+    assert cs.lib().cs_sprinkle_noalloc(kind, MAX_N + 1, 1, ctypes.c_void_p(coords.data_ptr()),
                                         ctypes.c_void_p(st)) == -1  # CS_EINVAL
