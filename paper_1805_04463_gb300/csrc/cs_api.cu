@@ -7,18 +7,22 @@
 #include "cs_kernels.cuh"
 
 namespace cs {
-namespace {
-
-inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // The last CUDA error an entry point turned into CS_ECUDA, per host thread.
 thread_local cudaError_t t_last_cuda = cudaSuccess;
 
-inline int from_cuda(cudaError_t e) {
+int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return CS_OK;
     t_last_cuda = e;
     return CS_ECUDA;
 }
+
+namespace {
+
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+
+inline int from_cuda(cudaError_t e) { return cuda_status(e); }
 
 inline bool valid_n(int64_t n) { return n >= 1 && n <= kMaxN; }
 

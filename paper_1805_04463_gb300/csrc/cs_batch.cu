@@ -658,11 +658,14 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
     }
     // For cs_batch_poll: the status word to the plan's pinned copy, then the
     // event (recorded as an external event node when the stream is captured).
-    if (cudaMemcpyAsync(b->status_host, &b->hdr->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess ||
-        cudaEventRecordWithFlags(b->done, st, cudaEventRecordExternal) != cudaSuccess)
-        return CS_ECUDA;
-    return CS_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((err = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_status(err);
+    if ((err = cudaMemcpyAsync(b->status_host, &b->hdr->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+        return cuda_status(err);
+    err = cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(b->done, st, cudaEventRecordExternal)
+                                               : cudaEventRecord(b->done, st);
+    return cuda_status(err);
 }
 
 int cs_batch_poll(const cs_batch* b) {

@@ -96,6 +96,10 @@ cudaError_t launch_count_mma4(int64_t n, const uint64_t* bits, int64_t row_words
                               void* workspace, cudaStream_t st, const double* phi = nullptr, double* layer = nullptr,
                               int kmax = -1);
 
+// CS_OK for cudaSuccess; otherwise CS_ECUDA, remembering the error for
+// cs_last_cuda_error (per host thread).
+int cuda_status(cudaError_t e);
+
 // Path chosen for CS_PATH_AUTO at size n.
 int resolve_path(int64_t n, int path);
 
