@@ -183,8 +183,9 @@ int cs_get_auto_paths(int64_t *n_min, int *paths, int capacity);
 
 /* Device workspace needed by cs_interval_abundance for (n, path).  The FP8
  * tensor-core path keeps two n x ceil(n/128)*128-byte operand matrices in it
- * (2 n^2 bytes, about 34 GB at n = 131072); the FP4 path two
- * n x ceil(n/256)*128-byte ones (n^2 bytes, about 17 GB at n = 131072). */
+ * (2 n^2 bytes, about 34 GB at n = 131072); the FP4 path one
+ * n x ceil(n/256)*128-byte matrix plus 256 bytes per row (n^2 / 2 bytes,
+ * about 8.6 GB at n = 131072, 137 GB at n = 2^19). */
 size_t cs_interval_abundance_workspace(int64_t n, int path);
 
 /*
@@ -294,7 +295,9 @@ int cs_action_device(int dim, int64_t n, const int64_t *hist_dev, int64_t len,
  * values of eps, and copies hist_host (cs_hist_len(n) int64), actions_host
  * (n_eps doubles) and *bracket_host back.  If coords_host is NULL the set is
  * sprinkled on the device from (kind, n, seed) instead.  Device memory comes
- * from the stream-ordered allocator and is returned before the call ends.
+ * from the device's default stream-ordered pool and is freed before the call
+ * ends; the pool keeps it for the next call, unless the call took more than
+ * a quarter of the device's memory, in which case the pool is trimmed.
  * Synchronous: returns after the results are on the host.
  * Errors: as the individual entry points, plus CS_ENOMEM.
  */
@@ -386,14 +389,16 @@ void cs_batch_destroy(cs_batch *b);
 int64_t cs_count_items(int64_t n, int path);
 
 /* Bytes of the tensor-core operands of a set of size n on `path`
- * (CS_PATH_MMA: two n x ceil(n/128)*128-byte FP8 matrices; CS_PATH_MMA4: two
- * n x ceil(n/256)*128-byte packed FP4 ones; 1024-byte aligned); 0 for
- * CS_PATH_POPC or invalid input. */
+ * (CS_PATH_MMA: two n x ceil(n/128)*128-byte FP8 matrices; CS_PATH_MMA4: one
+ * n x ceil(n/256)*128-byte packed FP4 matrix plus two n x 128-byte diagonal
+ * blocks; 1024-byte aligned); 0 for CS_PATH_POPC or invalid input. */
 size_t cs_operands_bytes(int64_t n, int path);
 
 /*
- * Expand a set's bitset into its tensor-core operands for `path` (0/1 values,
- * FP8 or packed FP4: U holds each row's future, L its past), once, for later
+ * Expand a set's bitset into its tensor-core operands for `path` (0/1 values;
+ * FP8: U holds each row's future, L its past; packed FP4: E holds every row
+ * of the symmetric matrix, DU / DL the future / past of each row within its
+ * own 256-column block), once, for later
  * cs_count_jobs slices on the same path.  operands_dev:
  * cs_operands_bytes(n, path), 1024-byte aligned.  Asynchronous.
  * Errors: CS_EINVAL (also for CS_PATH_POPC), CS_ENOMEM, CS_ECUDA.

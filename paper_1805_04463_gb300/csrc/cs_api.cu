@@ -359,6 +359,14 @@ int cs_evaluate(int kind, int64_t n, uint64_t seed, const int32_t* coords_host, 
     if (ws) cudaFreeAsync(ws, st);
     if (out) cudaFreeAsync(out, st);
     if (cudaStreamSynchronize(st) != cudaSuccess && rc == CS_OK) rc = CS_ECUDA;
+    // Freed blocks stay in the pool for the next call, except after a call
+    // that took more than a quarter of the device: those go back at once, so
+    // one very large evaluation does not hold its memory for the process.
+    const size_t took = cs_coords_bytes(kind, n) + cs_bitset_bytes(n) + size_t(hl) * 8 + ws_bytes;
+    if (took > device_total_memory() / 4) {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+    }
     if (rc == CS_OK && status_sprinkle != 0) rc = status_sprinkle;
     if (rc == CS_OK && status != 0) rc = status;
     return rc;

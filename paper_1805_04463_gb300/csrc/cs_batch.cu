@@ -338,7 +338,7 @@ namespace {
 
 struct Layout {
     size_t sets, entries, rtab, etab, mtab, coef, total;
-    std::vector<size_t> coords, bits, key0, key1, raw, U, L;
+    std::vector<size_t> coords, bits, key0, key1, raw, op0, op1;
 };
 
 bool batch_valid(const cs_set_desc* sets, int n_sets) {
@@ -394,9 +394,9 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
         L.raw.push_back(take(size_t(n) * 16));
         if (tensor_path(path)) {
             off = align_up(off, 1024);
-            L.U.push_back(take(mma_operand_bytes(n, path == CS_PATH_MMA4)));
+            L.op0.push_back(take(mma_operand_bytes(n, path == CS_PATH_MMA4, 0)));
             off = align_up(off, 1024);
-            L.L.push_back(take(mma_operand_bytes(n, path == CS_PATH_MMA4)));
+            L.op1.push_back(take(mma_operand_bytes(n, path == CS_PATH_MMA4, 1)));
         }
     }
     L.total = off;
@@ -485,7 +485,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
             const bool fp4 = p == CS_PATH_MMA4;
             MmaSetEntry e;
             std::memset(static_cast<void*>(&e), 0, sizeof(e));
-            if (mma_fill_entry(&e, b.bits, b.n, b.row_words, ws + L.U[order[r]], ws + L.L[order[r]], fp4) !=
+            if (mma_fill_entry(&e, b.bits, b.n, b.row_words, ws + L.op0[order[r]], ws + L.op1[order[r]], fp4) !=
                 CUDA_SUCCESS)
                 return CS_ECUDA;
             e.item_begin = items;

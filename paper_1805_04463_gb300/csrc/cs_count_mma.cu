@@ -3,14 +3,17 @@
 // interval of a related pair is the inner product of rows i and j between
 // columns i and j, i.e. (C.C)_ij for the strict upper triangle C).
 //
-// Operands.  The symmetric bitset is expanded once into two K-major byte
-// matrices of 0/1 values in FP8 E4M3 (1.0 = 0x38):
+// Operands (FP8 path).  The symmetric bitset is expanded once into two
+// K-major byte matrices of 0/1 values in FP8 E4M3 (1.0 = 0x38):
 //   U[i][k] = 1 iff k > i and i, k related   (row i = future of i, F_i)
 //   L[j][k] = 1 iff k < j and j, k related   (row j = past of j,  P_j)
 // so M = U . L^T holds |A_ij| = sum_k U_ik L_jk with no masking at all: the
 // zeros of U (k <= i) and L (k >= j) restrict k to i < k < j.  Products are 0
 // or 1 and every partial sum is an integer below 2^24, so FP32 accumulation
-// is exact.
+// is exact.  The FP4 pair path needs the masks only in the two K-blocks that
+// hold the supertile's own bands, so it keeps one unmasked matrix E of the
+// symmetric relation plus the masked diagonal blocks DU and DL (below, at
+// the FP4 expansion): half the operand memory.
 //
 // Kernel.  A persistent grid (one CTA per SM) walks 128 x 256 output tiles
 // (128 i-rows, 256 j-rows, i-block at or before the j-block), rasterised in
@@ -31,6 +34,7 @@
 // The K loop of a tile runs only over the K-blocks between the i-block and the
 // end of the j-block.  C.C is never written to memory.
 #include <atomic>
+#include <cstring>
 
 #include "cs_kernels.cuh"
 
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(256) k_expand_f8_multi(const MmaSetEntry* __re
                                                          const int32_t* __restrict__ chunk_set) {
     const MmaSetEntry& e = sets[chunk_set[blockIdx.x]];
     const int64_t r0 = (int64_t(blockIdx.x) - e.chunk_begin) * kExpandRows;
-    expand_rows(e.bits, e.row_words, e.kpad, e.U, e.L, r0, r0 + kExpandRows < e.n ? r0 + kExpandRows : e.n);
+    expand_rows(e.bits, e.row_words, e.kpad, e.op0, e.op1, r0, r0 + kExpandRows < e.n ? r0 + kExpandRows : e.n);
 }
 
 // ------------------------------------------------ packed FP4 operands
@@ -242,54 +246,64 @@ __device__ __forceinline__ uint4 spread32_e2m1(uint32_t b) {
     return make_uint4(spread8_e2m1(b), spread8_e2m1(b >> 8), spread8_e2m1(b >> 16), spread8_e2m1(b >> 24));
 }
 
-// The parts of the FP4 operands any tile reads: a K-block holds 256 columns,
-// so the A rows of the tiles at I0 = 128 floor(i / 128) start at column
-// 256 floor(i / 256), and the B rows of the tile at J0 = 256 floor(j / 256)
-// end at J0 + 256.  In 32-column pieces (one 32-bit half of a bitset word,
-// 16 operand bytes).
-__device__ __forceinline__ int64_t u4_first_piece(int64_t i) { return (i / 256) * 8; }
-__device__ __forceinline__ int64_t l4_end_piece(int64_t j) { return (j / 256 + 1) * 8; }
+// The FP4 operands.  A K-block holds 256 columns, the width of a supertile
+// band, so for the supertile of bands (sI, sJ), sI <= sJ, every K-block kb
+// strictly between the bands has sI*256 + 255 < k < sJ*256 for all its
+// columns k: there i < k < j holds for every pair of the supertile, and both
+// operands can be unmasked rows of the symmetric matrix, E[r][k] = C_rk.
+// Only the two bands' own blocks need masks: kb = sI reads DU (row i, own
+// block, columns k > i) for A, kb = sJ reads DL (row j, own block, columns
+// k < j) for B; a diagonal supertile (sI = sJ) reads both.  E's own blocks
+// are therefore never read and not written.  One operand matrix of n^2 / 2
+// bytes plus 256 bytes per row, where U and L took twice that.
+// Pieces of 32 columns (one 32-bit half of a bitset word, 16 operand bytes).
+__device__ __forceinline__ int64_t own_first_piece(int64_t i) { return (i / 256) * 8; }
 
-// Row i of the packed U and L (row bytes kpad / 2), pieces handed out to
-// thread t of a team of `size`.
+// Row i of E, DU and DL (E row bytes kpad / 2; DU and DL rows 128 bytes,
+// DL starting dl_off bytes after DU), pieces handed out to thread t of a
+// team of `size`.
 __device__ __forceinline__ void expand_row_f4(const uint64_t* __restrict__ bits, int64_t row_words, int64_t kpad,
-                                              uint8_t* __restrict__ U, uint8_t* __restrict__ L, int64_t i, int t,
-                                              int size) {
+                                              uint8_t* __restrict__ E, uint8_t* __restrict__ D, int64_t dl_off,
+                                              int64_t i, int t, int size) {
     const int ppr = int(kpad / 32);
     const uint32_t* brow = reinterpret_cast<const uint32_t*>(bits + i * row_words);
-    uint4* urow = reinterpret_cast<uint4*>(U + i * (kpad / 2));
-    uint4* lrow = reinterpret_cast<uint4*>(L + i * (kpad / 2));
+    uint4* erow = reinterpret_cast<uint4*>(E + i * (kpad / 2));
+    const int own = int(own_first_piece(i));
+    for (int c = t; c < ppr; c += size)
+        if (unsigned(c - own) >= 8u) erow[c] = spread32_e2m1(__ldg(brow + c));
+    uint4* du = reinterpret_cast<uint4*>(D + i * 128);
+    uint4* dl = reinterpret_cast<uint4*>(D + dl_off + i * 128);
     const int ii = int(i);  // n < 2^31
-    for (int c = int(u4_first_piece(i)) + t; c < ppr; c += size) {
+    for (int p = t; p < 16; p += size) {
+        const int c = own + (p & 7);
         const int d = ii - 32 * c;  // column i relative to the piece's first column
-        const uint32_t keep = d < 0 ? ~0u : (d >= 31 ? 0u : (~0u << (d + 1)));
-        urow[c] = spread32_e2m1(__ldg(brow + c) & keep);
-    }
-    const int le = int(l4_end_piece(i)) < ppr ? int(l4_end_piece(i)) : ppr;
-    for (int c = t; c < le; c += size) {
-        const int d = ii - 32 * c;
-        const uint32_t keep = d >= 32 ? ~0u : (d <= 0 ? 0u : (1u << d) - 1u);
-        lrow[c] = spread32_e2m1(__ldg(brow + c) & keep);
+        const uint32_t w = __ldg(brow + c);
+        if (p < 8)
+            du[p] = spread32_e2m1(w & (d < 0 ? ~0u : (d >= 31 ? 0u : (~0u << (d + 1)))));
+        else
+            dl[p - 8] = spread32_e2m1(w & (d >= 32 ? ~0u : (d <= 0 ? 0u : (1u << d) - 1u)));
     }
 }
 
-// Packed U and L rows [r0, r1) of one set: the block sweeps each long row,
-// one warp per short row.
+// FP4 operand rows [r0, r1) of one set: the block sweeps each long row, one
+// warp per short row.
 __device__ __forceinline__ void expand_rows_f4(const uint64_t* __restrict__ bits, int64_t row_words, int64_t kpad,
-                                               uint8_t* __restrict__ U, uint8_t* __restrict__ L, int64_t r0,
-                                               int64_t r1) {
+                                               uint8_t* __restrict__ E, uint8_t* __restrict__ D, int64_t dl_off,
+                                               int64_t r0, int64_t r1) {
     if (kpad / 32 >= 4 * int64_t(blockDim.x)) {
-        for (int64_t i = r0; i < r1; ++i) expand_row_f4(bits, row_words, kpad, U, L, i, threadIdx.x, blockDim.x);
+        for (int64_t i = r0; i < r1; ++i)
+            expand_row_f4(bits, row_words, kpad, E, D, dl_off, i, threadIdx.x, blockDim.x);
         return;
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int64_t i = r0 + warp; i < r1; i += nw) expand_row_f4(bits, row_words, kpad, U, L, i, lane, 32);
+    for (int64_t i = r0 + warp; i < r1; i += nw) expand_row_f4(bits, row_words, kpad, E, D, dl_off, i, lane, 32);
 }
 
 __global__ void __launch_bounds__(256) k_expand_f4(const uint64_t* __restrict__ bits, int64_t n, int64_t row_words,
-                                                   int64_t kpad, uint8_t* __restrict__ U, uint8_t* __restrict__ L) {
+                                                   int64_t kpad, uint8_t* __restrict__ E, uint8_t* __restrict__ D,
+                                                   int64_t dl_off) {
     for (int64_t r0 = int64_t(blockIdx.x) * kExpandRows; r0 < n; r0 += int64_t(gridDim.x) * kExpandRows)
-        expand_rows_f4(bits, row_words, kpad, U, L, r0, r0 + kExpandRows < n ? r0 + kExpandRows : n);
+        expand_rows_f4(bits, row_words, kpad, E, D, dl_off, r0, r0 + kExpandRows < n ? r0 + kExpandRows : n);
 }
 
 // The same over many sets, one block per chunk of kExpandRows rows.
@@ -297,7 +311,8 @@ __global__ void __launch_bounds__(256) k_expand_f4_multi(const MmaSetEntry* __re
                                                          const int32_t* __restrict__ chunk_set) {
     const MmaSetEntry& e = sets[chunk_set[blockIdx.x]];
     const int64_t r0 = (int64_t(blockIdx.x) - e.chunk_begin) * kExpandRows;
-    expand_rows_f4(e.bits, e.row_words, e.kpad, e.U, e.L, r0, r0 + kExpandRows < e.n ? r0 + kExpandRows : e.n);
+    expand_rows_f4(e.bits, e.row_words, e.kpad, e.op0, e.op1, mma4_dl_offset(e.n), r0,
+                   r0 + kExpandRows < e.n ? r0 + kExpandRows : e.n);
 }
 
 int expand_grid(int64_t rows) {
@@ -309,8 +324,7 @@ int expand_grid(int64_t rows) {
 
 // One causal set as the kernel sees it.
 struct MmaView {
-    const CUtensorMap* mapU;
-    const CUtensorMap* mapL;
+    const CUtensorMap* map;  // the set's operand maps (kMapU / kMapL, or kMapE / kMapDU / kMapDL)
     const uint64_t* bits;
     int64_t n, row_words, nsb, kblocks;
     unsigned long long* hist;
@@ -370,7 +384,7 @@ struct MmaMulti {
     }
     __device__ __forceinline__ MmaView view(int s) const {
         const MmaSetEntry& e = sets[s];
-        return MmaView{&e.mapU, &e.mapL, e.bits, e.n, e.row_words, e.nsb, e.kblocks,
+        return MmaView{e.maps.m, e.bits, e.n, e.row_words, e.nsb, e.kblocks,
                        reinterpret_cast<unsigned long long*>(hist_base + uintptr_t(e.hist_off)),
                        e.n > 1 ? e.n - 1 : 1, e.phi, e.layer, int(e.kmax)};
     }
@@ -412,7 +426,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
     constexpr int kMmaM = kPair ? 2 * kBM : kBM;
     static_assert(kNS * kSB <= kStages * kStageBytes, "the stages fit the shared-memory carve-out");
     static_assert(kSB % 1024 == 0, "stage buffers stay swizzle-atom aligned");
-    static_assert(!kPair || Fmt::kKE >= kBN, "both halves of a pair run the same K range");
+    static_assert(!kPair || Fmt::kKE == kBN, "a pair's K-block is one supertile band (E, DU, DL operands)");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes);
@@ -557,15 +571,20 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 if (!mbar_wait_or_abort(&empty[s], ph ^ 1u, hdr, abort_flag)) { ok = false; break; }
                 uint8_t* a = smem + s * kSB;
                 if constexpr (kPair) {
-                    // Both CTAs' bytes land on rank 0's full barrier.
+                    // Both CTAs' bytes land on rank 0's full barrier.  A
+                    // K-block holds one band: the i-band's own block comes
+                    // from DU, the j-band's from DL, every other from E.
                     const uint32_t fb = cluster_map(&full[s], 0);
                     if (leader) mbar_arrive_expect_tx(&full[s], 2 * kSB);
-                    tma_load_2d_pair(a, v.mapU, int32_t(kb * kBK), int32_t(it.I0 + row_off), fb);
-                    tma_load_2d_pair(a + kABytes, v.mapL, int32_t(kb * kBK), int32_t(it.J0 + row_off), fb);
+                    const bool a_own = kb == it.I0 / kBN, b_own = kb == it.J0 / kBN;
+                    tma_load_2d_pair(a, &v.map[a_own ? kMapDU : kMapE], a_own ? 0 : int32_t(kb * kBK),
+                                     int32_t(it.I0 + row_off), fb);
+                    tma_load_2d_pair(a + kABytes, &v.map[b_own ? kMapDL : kMapE], b_own ? 0 : int32_t(kb * kBK),
+                                     int32_t(it.J0 + row_off), fb);
                 } else {
                     mbar_arrive_expect_tx(&full[s], kSB);
-                    tma_load_2d(a, v.mapU, int32_t(kb * kBK), int32_t(it.I0), &full[s]);
-                    tma_load_2d(a + kABytes, v.mapL, int32_t(kb * kBK), int32_t(it.J0), &full[s]);
+                    tma_load_2d(a, &v.map[kMapU], int32_t(kb * kBK), int32_t(it.I0), &full[s]);
+                    tma_load_2d(a + kABytes, &v.map[kMapL], int32_t(kb * kBK), int32_t(it.J0), &full[s]);
                 }
                 ++issued;
                 if (++s == kNS) { s = 0; ph ^= 1u; }
@@ -811,11 +830,11 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_count_mma(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mapL,
-                const uint64_t* __restrict__ bits, int64_t n, int64_t row_words, int64_t nsb, int64_t nitems,
-                int64_t kblocks, unsigned long long* __restrict__ hist, int64_t hist_len, const double* phi,
-                double* layer, int kmax, WsHeader* hdr) {
-    const MmaSingle src{MmaView{&mapU, &mapL, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax},
+    k_count_mma(const __grid_constant__ MmaMaps maps, const uint64_t* __restrict__ bits, int64_t n,
+                int64_t row_words, int64_t nsb, int64_t nitems, int64_t kblocks,
+                unsigned long long* __restrict__ hist, int64_t hist_len, const double* phi, double* layer, int kmax,
+                WsHeader* hdr) {
+    const MmaSingle src{MmaView{maps.m, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax},
                         nitems};
     mma_body<FmtF8>(src, hdr);
 }
@@ -824,11 +843,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 // counts with layer sums.
 template <class Fmt>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_count_mma4(const __grid_constant__ CUtensorMap mapU, const __grid_constant__ CUtensorMap mapL,
-                 const uint64_t* __restrict__ bits, int64_t n, int64_t row_words, int64_t nsb, int64_t nitems,
-                 int64_t kblocks, unsigned long long* __restrict__ hist, int64_t hist_len, const double* phi,
-                 double* layer, int kmax, WsHeader* hdr) {
-    const MmaSingle src{MmaView{&mapU, &mapL, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax},
+    k_count_mma4(const __grid_constant__ MmaMaps maps, const uint64_t* __restrict__ bits, int64_t n,
+                 int64_t row_words, int64_t nsb, int64_t nitems, int64_t kblocks,
+                 unsigned long long* __restrict__ hist, int64_t hist_len, const double* phi, double* layer, int kmax,
+                 WsHeader* hdr) {
+    const MmaSingle src{MmaView{maps.m, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax},
                         nitems};
     mma_body<Fmt>(src, hdr);
 }
@@ -897,22 +916,50 @@ cudaError_t pair_config(K kernel, std::atomic<bool>* attr, std::atomic<int>* cac
     return cudaSuccess;
 }
 
-// Workspace: header, then U and L, each n rows of `row` bytes holding kpad
-// K elements (one byte each in FP8, two per byte in FP4).
+// Workspace: header, then the two operand buffers: FP8 U and L, each n rows
+// of kpad bytes; FP4 E (n rows of kpad / 2 bytes) and the diagonal blocks
+// (DU, then DL at mma4_dl_offset(n), n rows of 128 bytes each).
 struct MmaLayout {
-    int64_t kpad, row;
-    size_t u, l, total;
+    int64_t kpad, row;  // K elements per row, bytes per row of U, L or E
+    size_t op0, op1, total;
 };
+
+size_t operand_bytes(int64_t n, int64_t kpad, bool fp4, int which) {
+    if (!fp4) return size_t(n) * size_t(kpad);
+    return which == 0 ? size_t(n) * size_t(kpad / 2) : size_t(mma4_dl_offset(n)) + size_t(n) * 128;
+}
 
 MmaLayout mma_layout(int64_t n, bool fp4) {
     MmaLayout m;
     const int64_t ke = fp4 ? FmtF4::kKE : FmtF8::kKE;
     m.kpad = (n + ke - 1) / ke * ke;
     m.row = fp4 ? m.kpad / 2 : m.kpad;
-    m.u = sizeof(WsHeader);
-    m.l = align_up(m.u + size_t(n) * size_t(m.row), 1024);
-    m.total = align_up(m.l + size_t(n) * size_t(m.row), 256);
+    m.op0 = 1024;  // after the 256-byte header, 1024-byte aligned
+    m.op1 = align_up(m.op0 + operand_bytes(n, m.kpad, fp4, 0), 1024);
+    m.total = align_up(m.op1 + operand_bytes(n, m.kpad, fp4, 1), 256);
     return m;
+}
+
+// TMA maps of one set's operands (128B swizzle; boxes of one 128-byte
+// K-stage).  FP8: U (box 128 rows, the A slab) and L (box 256 rows, the B
+// slab).  FP4 pairs: each CTA of a pair loads 128 rows of A and of B, so E,
+// DU and DL all take 128-row boxes.
+CUresult encode_operand_maps(MmaMaps* maps, int64_t n, int64_t kpad, bool fp4, uint8_t* op0, uint8_t* op1) {
+    const uint64_t row = uint64_t(fp4 ? kpad / 2 : kpad);
+    CUresult r = encode_tensor_map_2d(&maps->m[0], CU_TENSOR_MAP_DATA_TYPE_UINT8, op0, row, uint64_t(n), row, kBK,
+                                      kBM, kSwizzle);
+    if (r != CUDA_SUCCESS) return r;
+    if (!fp4) {
+        std::memset(static_cast<void*>(&maps->m[2]), 0, sizeof(CUtensorMap));
+        return encode_tensor_map_2d(&maps->m[kMapL], CU_TENSOR_MAP_DATA_TYPE_UINT8, op1, row, uint64_t(n), row, kBK,
+                                    kBN, kSwizzle);
+    }
+    static_assert(kBK == 128, "a DU / DL row is one 128-byte K-stage");
+    if ((r = encode_tensor_map_2d(&maps->m[kMapDU], CU_TENSOR_MAP_DATA_TYPE_UINT8, op1, 128, uint64_t(n), 128, kBK,
+                                  kBN / 2, kSwizzle)) != CUDA_SUCCESS)
+        return r;
+    return encode_tensor_map_2d(&maps->m[kMapDL], CU_TENSOR_MAP_DATA_TYPE_UINT8, op1 + mma4_dl_offset(n), 128,
+                                uint64_t(n), 128, kBK, kBN / 2, kSwizzle);
 }
 
 }  // namespace
@@ -926,10 +973,7 @@ int64_t mma_kpad(int64_t n, bool fp4) {
     return (n + ke - 1) / ke * ke;
 }
 
-size_t mma_operand_bytes(int64_t n, bool fp4) {
-    const int64_t kpad = mma_kpad(n, fp4);
-    return size_t(n) * size_t(fp4 ? kpad / 2 : kpad);
-}
+size_t mma_operand_bytes(int64_t n, bool fp4, int which) { return operand_bytes(n, mma_kpad(n, fp4), fp4, which); }
 
 int64_t mma4_units(int64_t n) { return mma_items(n) / 2; }
 
@@ -939,8 +983,8 @@ int64_t mma_items(int64_t n) {
     return kSlotsPerBlock * nbg * (nbg + 1) / 2;
 }
 
-CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words, uint8_t* U,
-                        uint8_t* L, bool fp4) {
+CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words, uint8_t* op0,
+                        uint8_t* op1, bool fp4) {
     e->kmax = -1;
     e->bits = bits;
     e->n = n;
@@ -949,22 +993,19 @@ CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t
     e->kpad = mma_kpad(n, fp4);
     const int64_t row = fp4 ? e->kpad / 2 : e->kpad;  // operand row bytes
     e->kblocks = row / kBK;
-    e->U = U;
-    e->L = L;
-    // The FP4 pair path loads 128-row halves of the B slab.
-    CUresult r = encode_tensor_map_2d(&e->mapU, CU_TENSOR_MAP_DATA_TYPE_UINT8, U, uint64_t(row), uint64_t(n),
-                                      uint64_t(row), kBK, kBM, kSwizzle);
-    if (r != CUDA_SUCCESS) return r;
-    return encode_tensor_map_2d(&e->mapL, CU_TENSOR_MAP_DATA_TYPE_UINT8, L, uint64_t(row), uint64_t(n),
-                                uint64_t(row), kBK, fp4 ? kBN / 2 : kBN, kSwizzle);
+    e->op0 = op0;
+    e->op1 = op1;
+    return encode_operand_maps(&e->maps, n, e->kpad, fp4, op0, op1);
 }
 
 cudaError_t launch_expand_single(const MmaSetEntry* e, cudaStream_t st, bool fp4) {
     if (e->n < 1) return cudaSuccess;
     if (fp4)
-        k_expand_f4<<<unsigned(expand_grid(e->n)), 256, 0, st>>>(e->bits, e->n, e->row_words, e->kpad, e->U, e->L);
+        k_expand_f4<<<unsigned(expand_grid(e->n)), 256, 0, st>>>(e->bits, e->n, e->row_words, e->kpad, e->op0, e->op1,
+                                                                 mma4_dl_offset(e->n));
     else
-        k_expand_f8<<<unsigned(expand_grid(e->n)), 256, 0, st>>>(e->bits, e->n, e->row_words, e->kpad, e->U, e->L);
+        k_expand_f8<<<unsigned(expand_grid(e->n)), 256, 0, st>>>(e->bits, e->n, e->row_words, e->kpad, e->op0,
+                                                                 e->op1);
     return cudaGetLastError();
 }
 
@@ -1030,23 +1071,19 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
     if ((err = cudaMemsetAsync(&hdr->counter, 0, sizeof(hdr->counter), st)) != cudaSuccess) return err;
     if (n < 2) return cudaSuccess;
     const MmaLayout lay = mma_layout(n, kFp4);
-    uint8_t* U = static_cast<uint8_t*>(workspace) + lay.u;
-    uint8_t* L = static_cast<uint8_t*>(workspace) + lay.l;
+    uint8_t* op0 = static_cast<uint8_t*>(workspace) + lay.op0;
+    uint8_t* op1 = static_cast<uint8_t*>(workspace) + lay.op1;
 
     if constexpr (kFp4)
-        k_expand_f4<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, U, L);
+        k_expand_f4<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, op0, op1,
+                                                              mma4_dl_offset(n));
     else
-        k_expand_f8<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, U, L);
+        k_expand_f8<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, op0, op1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
 
-    // The B box is a whole 256-row slab, or in a CTA pair the half each CTA loads.
     constexpr int kCl = (kFp4 ? FmtF4::kPair : FmtF8::kPair) ? 2 : 1;
-    CUtensorMap mapU, mapL;
-    if (encode_tensor_map_2d(&mapU, CU_TENSOR_MAP_DATA_TYPE_UINT8, U, uint64_t(lay.row), uint64_t(n),
-                             uint64_t(lay.row), kBK, kBM, kSwizzle) != CUDA_SUCCESS ||
-        encode_tensor_map_2d(&mapL, CU_TENSOR_MAP_DATA_TYPE_UINT8, L, uint64_t(lay.row), uint64_t(n),
-                             uint64_t(lay.row), kBK, kBN / kCl, kSwizzle) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+    MmaMaps maps;
+    if (encode_operand_maps(&maps, n, lay.kpad, kFp4, op0, op1) != CUDA_SUCCESS) return cudaErrorInvalidValue;
 
     auto kernel = !kFp4 ? k_count_mma : kmax >= 0 ? k_count_mma4<FmtF4Layers> : k_count_mma4<FmtF4>;
     std::atomic<bool>* attr = !kFp4 ? g_attr_set : kmax >= 0 ? g_attr4l_set : g_attr4_set;
@@ -1065,7 +1102,7 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
     if constexpr (kCl == 1) {
         int64_t grid = device_sm_count();
         if (grid > nitems) grid = nitems;
-        kernel<<<unsigned(grid), kThreads, kSmemBytes, st>>>(mapU, mapL, bits, n, row_words, nsb, nitems, kblocks, h,
+        kernel<<<unsigned(grid), kThreads, kSmemBytes, st>>>(maps, bits, n, row_words, nsb, nitems, kblocks, h,
                                                              hist_len, phi, layer, kmax, hdr);
         return cudaGetLastError();
     } else {
@@ -1075,8 +1112,8 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
         if ((err = pair_config(kernel, attr, kmax >= 0 ? g_clusters4l : g_clusters4, nitems / kCl, st, at, &cfg,
                                &pairs)) != cudaSuccess)
             return err;
-        return cudaLaunchKernelEx(&cfg, kernel, mapU, mapL, bits, n, row_words, nsb, nitems, kblocks, h, hist_len,
-                                  phi, layer, kmax, hdr);
+        return cudaLaunchKernelEx(&cfg, kernel, maps, bits, n, row_words, nsb, nitems, kblocks, h, hist_len, phi,
+                                  layer, kmax, hdr);
     }
 }
 

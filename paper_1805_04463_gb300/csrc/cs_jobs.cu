@@ -41,8 +41,8 @@ size_t cs_operands_bytes(int64_t n, int path) {
     if (n < 1 || n > kMaxN || !valid_path(path)) return 0;
     const int p = jobs_path(path);
     if (!tensor_path(p)) return 0;
-    const size_t m = mma_operand_bytes(n, p == CS_PATH_MMA4);
-    return align_up(m, 1024) + m;
+    const bool fp4 = p == CS_PATH_MMA4;
+    return align_up(mma_operand_bytes(n, fp4, 0), 1024) + mma_operand_bytes(n, fp4, 1);
 }
 
 int cs_prepare_operands(int64_t n, int path, const uint64_t* bits_dev, int64_t row_words, void* operands_dev,
@@ -56,14 +56,12 @@ int cs_prepare_operands(int64_t n, int path, const uint64_t* bits_dev, int64_t r
     if (operands_bytes < cs_operands_bytes(n, path)) return CS_ENOMEM;
     MmaSetEntry e;
     std::memset(static_cast<void*>(&e), 0, sizeof(e));
-    uint8_t* U = static_cast<uint8_t*>(operands_dev);
-    uint8_t* L = U + align_up(mma_operand_bytes(n, fp4), 1024);
     e.bits = bits_dev;
     e.n = n;
     e.row_words = row_words;
     e.kpad = mma_kpad(n, fp4);
-    e.U = U;
-    e.L = L;
+    e.op0 = static_cast<uint8_t*>(operands_dev);
+    e.op1 = e.op0 + align_up(mma_operand_bytes(n, fp4, 0), 1024);
     return launch_expand_single(&e, static_cast<cudaStream_t>(stream), fp4) == cudaSuccess ? CS_OK : CS_ECUDA;
 }
 
@@ -99,9 +97,9 @@ int cs_count_jobs(const cs_count_job* jobs, int n_jobs, int path, void* table_ho
             const bool fp4 = p == CS_PATH_MMA4;
             MmaSetEntry& e = static_cast<MmaSetEntry*>(table_host)[j];
             std::memset(static_cast<void*>(&e), 0, sizeof(e));
-            uint8_t* U = static_cast<uint8_t*>(b.operands);
-            uint8_t* L = U + align_up(mma_operand_bytes(b.n, fp4), 1024);
-            if (mma_fill_entry(&e, b.bits, b.n, b.row_words, U, L, fp4) != CUDA_SUCCESS) return CS_ECUDA;
+            uint8_t* op0 = static_cast<uint8_t*>(b.operands);
+            uint8_t* op1 = op0 + align_up(mma_operand_bytes(b.n, fp4, 0), 1024);
+            if (mma_fill_entry(&e, b.bits, b.n, b.row_words, op0, op1, fp4) != CUDA_SUCCESS) return CS_ECUDA;
             e.item_begin = items;
             e.item_offset = b.item_begin;
             e.hist_off = int64_t(reinterpret_cast<uintptr_t>(b.hist));

@@ -43,18 +43,26 @@ cudaError_t launch_count_popc(int64_t n, const uint64_t* bits, int64_t row_words
                               int kmax = -1);
 
 // cs_count_mma.cu
-// One set of a multi-set tensor-core count: TMA maps of its U and L operands,
+// TMA maps of one set's operands.  FP8 (CS_PATH_MMA): U and L, the masked
+// future and past rows.  FP4 pairs (CS_PATH_MMA4): E, every row of the
+// symmetric matrix unmasked, and the masked diagonal blocks DU (each row's own
+// 256-column block, columns after the row) and DL (columns before it).
+constexpr int kMapU = 0, kMapL = 1;
+constexpr int kMapE = 0, kMapDU = 1, kMapDL = 2;
+struct MmaMaps {
+    CUtensorMap m[3];
+};
+// One set of a multi-set tensor-core count: TMA maps of its operands,
 // bitset, sizes, item range, histogram offset, and where its operands live.
 struct alignas(128) MmaSetEntry {
-    CUtensorMap mapU;
-    CUtensorMap mapL;
+    MmaMaps maps;
     const uint64_t* bits;
     int64_t n, row_words, nsb, kblocks;
     int64_t item_begin;   // first item of this set in the concatenated item list
     int64_t item_offset;  // item index (within the set) of that first item
     int64_t hist_off;     // byte offset of this set's histogram from the launch's histogram base
-    uint8_t* U;
-    uint8_t* L;
+    uint8_t* op0;         // FP8: U; FP4: E
+    uint8_t* op1;         // FP8: L; FP4: DU, then DL at mma4_dl_offset(n)
     int64_t kpad;
     int64_t chunk_begin;  // first expansion chunk of this set (multi-set expansion)
     const double* phi;   // d'Alembertian layer sums: field (NULL = 1),
@@ -68,12 +76,15 @@ size_t mma_workspace_bytes(int64_t n);
 int64_t mma_items(int64_t n);
 int64_t mma4_units(int64_t n);
 int64_t mma_kpad(int64_t n, bool fp4 = false);
-size_t mma_operand_bytes(int64_t n, bool fp4);  // bytes of one of U, L
+// Bytes of a set's first (U, or E) and second (L, or DU and DL) operand buffer.
+size_t mma_operand_bytes(int64_t n, bool fp4, int which);
+// DL within the second FP4 buffer: after n DU rows of 128 bytes, 1024-byte aligned.
+__host__ __device__ inline int64_t mma4_dl_offset(int64_t n) { return (n * 128 + 1023) / 1024 * 1024; }
 // Fill sizes, operand pointers and TMA maps of an entry (item_begin, hist_off,
-// chunk_begin are the caller's).
-CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words, uint8_t* U,
-                        uint8_t* L, bool fp4 = false);
-// uses bits, n, row_words, kpad, U, L
+// chunk_begin are the caller's).  op0, op1: 1024-byte aligned.
+CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words, uint8_t* op0,
+                        uint8_t* op1, bool fp4 = false);
+// uses bits, n, row_words, kpad, op0, op1
 cudaError_t launch_expand_single(const MmaSetEntry* e, cudaStream_t st, bool fp4 = false);
 // Expansion of many sets: chunk c of the concatenated chunk range belongs to
 // set chunk_set[c] (a table the caller builds; mma_expand_chunks(n) chunks per

@@ -102,8 +102,9 @@ class Server:
         if path == cs.PATH_AUTO:
             # the FP4 pair path wherever the device has tcgen05: the large
             # requests dominate the work, and there it runs 2.2x the FP8 rate
-            # (GB300, 200 req/s mix: p50 2.3 vs 6.8 ms, p99 31 vs 79 ms)
-            path = cs.PATH_MMA4 if cs.resolved_path(1 << 20) in (cs.PATH_MMA, cs.PATH_MMA4) else cs.PATH_POPC
+            # (GB300, 200 req/s mix: p50 2.3 vs 6.8 ms, p99 31 vs 79 ms).
+            # Asked at 2^16, the largest request size, whose operands fit.
+            path = cs.PATH_MMA4 if cs.resolved_path(1 << 16) in (cs.PATH_MMA, cs.PATH_MMA4) else cs.PATH_POPC
         self.count_path = path
         self.bitset_budget = bitset_budget
         self.operand_budget = operand_budget

@@ -186,14 +186,17 @@ def test_failure_detection_entry_points_reject_bad_arguments(cslib):
 
 def test_job_items_and_operand_sizes_on_host(cslib):
     # The FP4 pair path counts in 256 x 256 supertiles (half the FP8 tile
-    # slots) and keeps K-padded-to-256 nibble operands (half the FP8 bytes).
+    # slots) and keeps one K-padded-to-256 nibble matrix E plus two 128-byte
+    # diagonal-block rows per element (DU, DL): a quarter of the FP8 bytes
+    # and more.
     L = cslib.lib()
+    up = lambda x: (x + 1023) // 1024 * 1024
     for n in (1, 255, 256, 257, 4096, 100000):
         assert L.cs_count_items(n, 2) == 2 * L.cs_count_items(n, 3) > 0
         kp8, kp4 = (n + 127) // 128 * 128, (n + 255) // 256 * 256
-        b8, b4 = n * kp8, n * (kp4 // 2)
-        assert L.cs_operands_bytes(n, 2) == (b8 + 1023) // 1024 * 1024 + b8
-        assert L.cs_operands_bytes(n, 3) == (b4 + 1023) // 1024 * 1024 + b4
+        b8, e4, d4 = n * kp8, n * (kp4 // 2), up(n * 128) + n * 128
+        assert L.cs_operands_bytes(n, 2) == up(b8) + b8
+        assert L.cs_operands_bytes(n, 3) == up(e4) + d4
         assert L.cs_operands_bytes(n, 1) == 0
     assert L.cs_count_items(100, 4) == -1 and L.cs_operands_bytes(100, 4) == 0
     assert L.cs_count_jobs_table_bytes(3, 3) == L.cs_count_jobs_table_bytes(3, 2) > 0

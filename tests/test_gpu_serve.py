@@ -130,5 +130,5 @@ def test_autotuner_installs_a_measured_table(cs, tmp_path):
 def test_auto_server_counts_on_the_fp4_pair_path(cs):
     # On a tcgen05 device the server's AUTO choice is the FP4 pair job kernel.
     from paper_1805_04463_gb300 import serve
-    assert cs.resolved_path(1 << 20) == cs.PATH_MMA4
+    assert cs.resolved_path(1 << 16) == cs.PATH_MMA4
     assert serve.Server().count_path == cs.PATH_MMA4
