@@ -65,7 +65,6 @@ constexpr uint32_t kIdesc4 = idesc_mxf4_f32(kBM, kBN);
 constexpr uint32_t kSfCol = 256;         // FP4: scale factors of A at this TMEM column, of B 16 further
 constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;  // four UE8M0 scale factors 2^0 = 1
 constexpr int kRing = 4;                 // items in flight between the roles
-constexpr int kLocalBits = 40;           // ring entry = set << 40 | item within the set; -1 = no more items
 constexpr int kSmemBytes = kStages * kStageBytes + kHistBins * 4 + 256 + 1024;
 constexpr uint8_t kOne = 0x38;           // 1.0 in FP8 E4M3
 
@@ -106,6 +105,12 @@ struct FmtF4 {
 struct FmtF4Layers : FmtF4 {
     static constexpr bool kLayers = true;
 };
+// The multi-set form: its sets are small (a batch holds n <= 8192, a count
+// job any n), so it keeps the branch-free histogram of the FP8 kernel for
+// sets whose histogram fits in shared memory.
+struct FmtF4Multi : FmtF4 {
+    static constexpr bool kSmallSet = true;
+};
 constexpr CUtensorMapSwizzle kSwizzle = kBK == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
 static_assert(kBK == 128 || kBK == 64, "one 128- or 64-byte swizzle row per stage");
 static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "stage buffers stay swizzle-atom aligned");
@@ -117,7 +122,8 @@ static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "stage buffers sta
 // consecutive item indices.  CTAs that run at the same time therefore share
 // A panels (same si) and B panels (same sj) through L2 instead of each
 // streaming its own operands from HBM.  Slots with si > sj, or beyond n,
-// decode to nothing and are skipped by every role alike.
+// decode to nothing: the producer skips them, and hands the other roles
+// only the valid items, already decoded (pack_item).
 constexpr int kRaster = 8;
 constexpr int64_t kSlotsPerBlock = 2 * kRaster * kRaster;
 
@@ -126,8 +132,10 @@ struct Item {
     int64_t kb0, kb1;  // K-blocks [kb0, kb1)
 };
 
-template <int KE>
-__device__ __forceinline__ bool decode_item(int64_t t, int64_t nsb, int64_t n, int64_t kblocks, Item& it) {
+// Slot t of a set's item list -> supertile (si, sj) and its 128-row half;
+// false for a slot that holds no work.
+__device__ __forceinline__ bool decode_slot(int64_t t, int64_t nsb, int64_t n, int64_t& si, int64_t& sj,
+                                            int64_t& half) {
     const int64_t blk = t / kSlotsPerBlock, slot = t - blk * kSlotsPerBlock;
     const int64_t nbg = (nsb + kRaster - 1) / kRaster;
     int64_t m = int64_t((1.0f + sqrtf(1.0f + 8.0f * float(blk))) * 0.5f);  // corrected below
@@ -135,17 +143,30 @@ __device__ __forceinline__ bool decode_item(int64_t t, int64_t nsb, int64_t n, i
     while (m * (m + 1) / 2 <= blk) ++m;
     const int64_t gi = blk - m * (m - 1) / 2;
     const int64_t gj = gi + (nbg - m);
-    const int64_t si = gi * kRaster + slot / (2 * kRaster);
+    si = gi * kRaster + slot / (2 * kRaster);
     const int64_t rem = slot % (2 * kRaster);
-    const int64_t sj = gj * kRaster + rem / 2, half = rem & 1;
-    if (si > sj || sj >= nsb) return false;
-    it.I0 = si * 256 + half * kBM;
-    it.J0 = sj * kBN;
-    if (it.I0 >= n) return false;
+    sj = gj * kRaster + rem / 2;
+    half = rem & 1;
+    return si <= sj && sj < nsb && si * 256 + half * kBM < n;
+}
+
+// Ring entry of a valid item: set index << 33 | half << 32 | si << 16 | sj
+// (nsb <= 2^14 for n <= 2^22); -1 = no more items.
+__device__ __forceinline__ int64_t pack_item(int sidx, int64_t si, int64_t sj, int64_t half) {
+    return (int64_t(sidx) << 33) | (half << 32) | (si << 16) | sj;
+}
+
+__device__ __forceinline__ int item_set(int64_t e) { return int(e >> 33); }
+
+template <int KE>
+__device__ __forceinline__ Item unpack_item(int64_t e, int64_t kblocks) {
+    Item it;
+    it.I0 = ((e >> 16) & 0xFFFF) * 256 + ((e >> 32) & 1) * kBM;
+    it.J0 = (e & 0xFFFF) * kBN;
     it.kb0 = it.I0 / KE;
-    const int64_t e = (it.J0 + kBN + KE - 1) / KE;
-    it.kb1 = e < kblocks ? e : kblocks;
-    return true;
+    const int64_t end = (it.J0 + kBN + KE - 1) / KE;
+    it.kb1 = end < kblocks ? end : kblocks;
+    return it;
 }
 
 // Bits 0..3 of x -> 4 bytes of 0x00 / 0x38 (bit b -> byte b).  The product
@@ -161,7 +182,7 @@ __device__ __forceinline__ uint4 spread16(uint32_t b) {
     return make_uint4(spread4(b), spread4(b >> 4), spread4(b >> 8), spread4(b >> 12));
 }
 
-// The parts of the operands any tile reads (decode_item): row i of U is an A
+// The parts of the operands any tile reads (decode_slot): row i of U is an A
 // row of the tile starting at I0 = 128 * floor(i / 128), whose K range starts
 // at I0; row j of L is a B row of the tile starting at J0 = 256 * floor(j /
 // 256), whose K range ends at J0 + 256.  In 16-column pieces: U row i from
@@ -500,9 +521,10 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
     // and epilogue threads.  A pair: rank 0's producer publishes each
     // supertile to both CTAs (its own slot and, through the cluster window,
     // rank 1's), and every consumer of either CTA -- rank 1's producer too --
-    // releases the slot on rank 0's iempty.  A ring entry is
-    // set << kLocalBits | unit; the unit is an item (one CTA) or a supertile
-    // (a pair, which runs it as item 2 * unit, its upper half's index).
+    // releases the slot on rank 0's iempty.  A ring entry is a decoded item
+    // (pack_item): the unit the queue hands out is a slot (one CTA) or a
+    // supertile slot (a pair, which runs it as slot 2 * unit, its upper
+    // half), and the producer skips the units that hold no work.
     const uint32_t iempty0 = kPair ? cluster_map(iempty, 0) : 0u;
     const uint32_t tempty0 = kPair ? cluster_map(tempty, 0) : 0u;
     auto ring_wait = [&](uint32_t slot, uint32_t use) {
@@ -514,7 +536,6 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         else
             mbar_arrive(&iempty[slot]);
     };
-    constexpr int64_t kUnitMask = (int64_t(1) << kLocalBits) - 1;
     // This CTA's first A row and B row within an item.
     const int64_t row_off = kPair ? int64_t(crank) * kBM : 0;
 
@@ -531,21 +552,28 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         const int64_t units = total / kCl;
         for (uint32_t q = 0; ok; ++q) {
             const uint32_t slot = q % kRing, use = (q / kRing) & 1u;
-            int64_t e;
+            int64_t e = -1;
             if (leader) {
                 if (!mbar_wait_or_abort<kPair>(&iempty[slot], use ^ 1u, hdr, abort_flag)) { ok = false; break; }
-                if (next >= end) {
-                    next = int64_t(atomicAdd(&hdr->counter, 1ull)) * src.chunk();
-                    end = next + src.chunk();
-                }
-                const int64_t t = next++;
-                if (t >= units) {
-                    e = -1;
-                } else {
-                    // the producer alone finds the unit's set and hands it on
-                    int64_t lu;
+                // the producer alone finds the next unit that holds work,
+                // decodes it and hands it on
+                for (;;) {
+                    if (next >= end) {
+                        next = int64_t(atomicAdd(&hdr->counter, 1ull)) * src.chunk();
+                        end = next + src.chunk();
+                    }
+                    const int64_t t = next++;
+                    if (t >= units) break;
+                    int64_t lu, si, sj, half;
                     const int sidx = src.set_of(t, lu, cur);
-                    e = (int64_t(sidx) << kLocalBits) | lu;
+                    if (sidx != cur) {
+                        cur = sidx;
+                        v = src.view(sidx);
+                    }
+                    if (decode_slot(lu * kCl, v.nsb, v.n, si, sj, half)) {
+                        e = pack_item(sidx, si, sj, half);
+                        break;
+                    }
                 }
                 ring[slot] = e;
                 mbar_arrive(&ifull[slot]);
@@ -559,14 +587,12 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 ring_release(slot);
             }
             if (e < 0) break;
-            const int sidx = int(e >> kLocalBits);
-            const int64_t local = (e & kUnitMask) * kCl;
+            const int sidx = item_set(e);
             if (sidx != cur) {
                 cur = sidx;
                 v = src.view(sidx);
             }
-            Item it;
-            if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
+            const Item it = unpack_item<Fmt::kKE>(e, v.kblocks);
             for (int64_t kb = it.kb0; kb < it.kb1; ++kb) {
                 if (!mbar_wait_or_abort(&empty[s], ph ^ 1u, hdr, abort_flag)) { ok = false; break; }
                 uint8_t* a = smem + s * kSB;
@@ -621,14 +647,12 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             const int64_t e = ring[slot];
             ring_release(slot);
             if (e < 0) break;
-            const int sidx = int(e >> kLocalBits);
-            const int64_t local = (e & kUnitMask) * kCl;
+            const int sidx = item_set(e);
             if (sidx != cur) {
                 cur = sidx;
                 v = src.view(sidx);
             }
-            Item it;
-            if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
+            const Item it = unpack_item<Fmt::kKE>(e, v.kblocks);
             const uint32_t buf = uint32_t(local_count % Fmt::kAcc), bu = uint32_t((local_count / Fmt::kAcc) & 1);
             ++local_count;
             if (!mbar_wait_or_abort<kPair>(&tempty[buf], bu ^ 1u, hdr, abort_flag)) break;
@@ -685,18 +709,22 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         MmaView v{};
         // Release the accumulator to the MMA issuer (a pair: rank 0's), one
         // arrival of 32 per warp once all its lanes' TMEM reads are done.
+        // The accumulator's only users here are this warp's tcgen05.ld,
+        // complete once tcgen05.wait::ld returned, so the arrival orders no
+        // memory access and needs no fence (a release at cluster scope would
+        // wait for the bitset word's global load still in flight).
         auto acc_release = [&](uint32_t buf) {
             tc_fence_before();
             if constexpr (kPair) {
                 __syncwarp();
                 if (lane == 0) {
                     if (leader)
-                        mbar_arrive_cnt(&tempty[buf], 32u);
+                        mbar_arrive_relaxed_cnt(&tempty[buf], 32u);
                     else
-                        mbar_arrive_cluster(tempty0 + 8u * buf, 32u);
+                        mbar_arrive_cluster_relaxed(tempty0 + 8u * buf, 32u);
                 }
             } else {
-                mbar_arrive(&tempty[buf]);
+                mbar_arrive_relaxed_cnt(&tempty[buf], 1u);
             }
         };
         // Release an item-ring slot, likewise one arrival of 32 per warp in a pair.
@@ -719,16 +747,14 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             const int64_t e = ring[slot];
             epi_ring_release(slot);
             if (e < 0) break;
-            const int sidx = int(e >> kLocalBits);
-            const int64_t local = (e & kUnitMask) * kCl;
+            const int sidx = item_set(e);
             if (sidx != cur || since_flush == kFlushTiles) {
                 if (cur >= 0 && !epilogue_flush(shist, v, etid, ebar, ephase, hdr, abort_flag)) { ok = false; break; }
                 cur = sidx;
                 v = src.view(sidx);
                 since_flush = 0;
             }
-            Item it;
-            if (!decode_item<Fmt::kKE>(local, v.nsb, v.n, v.kblocks, it)) continue;
+            const Item it = unpack_item<Fmt::kKE>(e, v.kblocks);
             ++since_flush;
             const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
             const uint32_t buf = uint32_t(local_count % Fmt::kAcc), use = uint32_t((local_count / Fmt::kAcc) & 1);
@@ -866,7 +892,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_count_mma4_multi(const MmaSetEntry* __restrict__ sets, int nsets, int64_t nitems, uintptr_t hist_base,
                        int64_t run, WsHeader* hdr) {
     const MmaMulti src{sets, nsets, nitems, hist_base, run};
-    mma_body<FmtF4>(src, hdr);
+    mma_body<FmtF4Multi>(src, hdr);
 }
 
 std::atomic<bool> g_attr_set[64];  // per device: the large-shared-memory attribute is set

@@ -111,6 +111,14 @@ __device__ __forceinline__ void mbar_arrive_cnt(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
+// `count` arrivals without ordering earlier memory accesses (no fence): for
+// a signal whose precondition is an instruction that has already completed
+// (a tcgen05.ld after its tcgen05.wait::ld), not a memory access.
+__device__ __forceinline__ void mbar_arrive_relaxed_cnt(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -176,6 +184,13 @@ __device__ __forceinline__ void st_cluster_s64(uint32_t caddr, int64_t v) {
 // cluster scope (orders this thread's earlier accesses before them).
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr, uint32_t count) {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(caddr), "r"(count)
+                 : "memory");
+}
+
+// The same arrivals without ordering earlier memory accesses (see
+// mbar_arrive_relaxed_cnt).
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t caddr, uint32_t count) {
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(caddr), "r"(count)
                  : "memory");
 }
 
