@@ -431,6 +431,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the degree / sparse-list / d'Alembertian measurements")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner and keep the library's built-in path, tile and batch choices")
     ap.add_argument("--ensemble-sets", default="512,256",
                     help="ensemble size: number of 2D diamonds, number of 4D diamonds (profiling runs use a sample)")
     args = ap.parse_args()
@@ -451,6 +453,15 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     csbuild.build()
+    tuning = None
+    if not args.no_tune:
+        # measured path table, raster sides and multi-set tuning on this GPU,
+        # installed before anything is timed (not persisted)
+        from paper_1805_04463_gb300 import tune
+        r = tune.autotune(persist=False)
+        tuning = {"paths": r["paths"], "tiles": r["tiles"], "batch_path_run": r["batch"],
+                  "tile_measurements_ms": r["tile_measurements"],
+                  "batch_measurements_ms": r["batch_measurements"]}
     kind, n, seed0, desc = WORKLOADS[args.workload]
     seed = seed0 + rank  # weak scaling: one independent set per rank
     path = PATHS[args.path]
@@ -581,6 +592,9 @@ def main():
         "roofline": roofline,
         "clocks": clocks,
         "stages_ms": stages_ms,
+        "tuning": tuning if tuning is not None else {"paths": cs.get_auto_paths(), "tiles": cs.get_auto_tiles(),
+                                                    "batch_path_run": list(cs.get_batch_tuning()),
+                                                    "source": "built-in (--no-tune)"},
     }
     if not args.no_extras:
         line.update(extras_bench(cs, torch, buf, kind, n, path, stream, peaks))

@@ -76,7 +76,8 @@ enum {
     CS_PATH_MMA4 = 3    /* 0/1 operands as packed FP4 E2M1 (block-scaled kind::mxf4, every scale
                            factor 1) on CTA pairs running 2-SM MMAs: half the operand bytes,
                            the FP4 tensor rate.  Every count entry point takes it; on the batch
-                           and job entry points CS_PATH_AUTO stays CS_PATH_MMA. */
+                           and job entry points CS_PATH_AUTO means cs_set_batch_tuning's path
+                           (by default this one, where the device has tcgen05). */
 };
 
 /* ------------------------------------------------------------- layouts */
@@ -180,6 +181,36 @@ int cs_set_auto_paths(const int64_t *n_min, const int *paths, int count);
 /* Copy the AUTO table out; returns its entry count (nothing is copied when
  * capacity is smaller than the count). */
 int cs_get_auto_paths(int64_t *n_min, int *paths, int capacity);
+
+/*
+ * Tile order of the single-set tensor-core counts, process-wide: for
+ * n_min[e] <= n < n_min[e+1], cs_interval_abundance, cs_layer_sums and
+ * cs_evaluate on CS_PATH_MMA / CS_PATH_MMA4 hand out their 256 x 256
+ * supertiles in raster blocks of raster[e] x raster[e] supertiles, widest
+ * band first, so that the CTAs running at one time share operand panels in
+ * L2.  raster in 1..32; n_min starts at 0 and increases; at most 16
+ * entries.  The default is {0: 8}; the autotuner installs measured choices.
+ * Results do not depend on it.  Errors: CS_EINVAL.
+ */
+int cs_set_auto_tiles(const int64_t *n_min, const int *raster, int count);
+
+/* Copy the tile table out; returns its entry count (nothing is copied when
+ * capacity is smaller than the count). */
+int cs_get_auto_tiles(int64_t *n_min, int *raster, int capacity);
+
+/*
+ * Tuning of the multi-set counts, process-wide: `path` is what CS_PATH_AUTO
+ * means for cs_batch_* and cs_count_jobs (CS_PATH_AUTO = the built-in
+ * choice: CS_PATH_MMA4 where the device has tcgen05, else CS_PATH_POPC; a
+ * tensor path on a device without tcgen05 also falls back to POPC);
+ * max_run (1..64, default 16) is the longest run of consecutive work items
+ * one CTA (pair) takes from the shared queue, so that a small set is counted
+ * by few CTAs.  Results do not depend on either.  Errors: CS_EINVAL.
+ */
+int cs_set_batch_tuning(int path, int max_run);
+
+/* The settings of cs_set_batch_tuning.  Errors: CS_EINVAL (NULL). */
+int cs_get_batch_tuning(int *path, int *max_run);
 
 /* Device workspace needed by cs_interval_abundance for (n, path).  The FP8
  * tensor-core path keeps two n x ceil(n/128)*128-byte operand matrices in it
@@ -374,7 +405,8 @@ int cs_batch_launch(const cs_batch *b, const double *eps_host, int n_eps, int64_
 int cs_batch_poll(const cs_batch *b);
 
 /* The count path a plan runs (CS_PATH_POPC, CS_PATH_MMA or CS_PATH_MMA4;
- * CS_PATH_AUTO plans CS_PATH_MMA where the device has tcgen05), -1 for NULL. */
+ * CS_PATH_AUTO plans the batch path of cs_set_batch_tuning, by default
+ * CS_PATH_MMA4 where the device has tcgen05), -1 for NULL. */
 int cs_batch_path(const cs_batch *b);
 
 /* Free the host handle (the workspace stays the caller's). */
@@ -384,8 +416,9 @@ void cs_batch_destroy(cs_batch *b);
 
 /* Number of work items a set of size n splits into on `path` (tiles of its
  * interval count: 128 x 128 POPC tiles, 128 x 256 FP8 tile slots, or 256 x
- * 256 supertile slots on CS_PATH_MMA4; CS_PATH_AUTO means CS_PATH_MMA where
- * the device has tcgen05); -1 for invalid input. */
+ * 256 supertile slots on CS_PATH_MMA4, in raster blocks of side 8;
+ * CS_PATH_AUTO means the batch path of cs_set_batch_tuning, so change that
+ * setting only between whole sets of jobs); -1 for invalid input. */
 int64_t cs_count_items(int64_t n, int path);
 
 /* Bytes of the tensor-core operands of a set of size n on `path`

@@ -21,6 +21,7 @@ __all__ = [
     "CsError", "lib", "dim", "coords_bytes", "row_words", "bitset_bytes", "hist_len",
     "sprinkle_workspace_bytes", "interval_abundance_workspace", "resolved_path", "action_workspace_bytes",
     "set_auto_paths", "get_auto_paths", "set_auto_memory_limit", "get_auto_memory_limit",
+    "set_auto_tiles", "get_auto_tiles", "set_batch_tuning", "get_batch_tuning",
     "sprinkle", "sprinkle_noalloc", "causal_matrix", "layer_sums", "dalembertian", "interval_abundance", "workspace_status", "action", "action_device",
     "evaluate", "Buffers", "allocate", "run", "SetDesc", "Batch", "CountJob", "count_items",
     "operands_bytes", "prepare_operands", "peak_probe", "count_jobs", "degrees", "sparse_relations", "longest_chain", "greedy_antichain", "BATCH_MAX_N", "FAULT_ALLOC", "FAULT_LAUNCH", "selftest_wait",
@@ -82,6 +83,10 @@ def lib() -> ctypes.CDLL:
             "cs_set_auto_paths": ([vp, vp, i32], i32),
             "cs_get_auto_paths": ([vp, vp, i32], i32),
             "cs_set_auto_memory_limit": ([sz], i32),
+            "cs_set_auto_tiles": ([vp, vp, i32], i32),
+            "cs_get_auto_tiles": ([vp, vp, i32], i32),
+            "cs_set_batch_tuning": ([i32, i32], i32),
+            "cs_get_batch_tuning": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], i32),
             "cs_get_auto_memory_limit": ([], sz),
             "cs_interval_abundance": ([i64, vp, i64, vp, i32, vp, sz, vp], i32),
             "cs_workspace_status": ([vp, vp], i32),
@@ -197,6 +202,34 @@ def get_auto_paths():
     p = (ctypes.c_int * cnt)()
     lib().cs_get_auto_paths(n, p, cnt)
     return [(int(n[i]), int(p[i])) for i in range(cnt)]
+
+
+def set_auto_tiles(table):
+    """cs_set_auto_tiles: raster side per size bucket of the single-set tensor counts,
+    a sequence of (n_min, raster), n_min from 0 upward."""
+    n = (ctypes.c_int64 * len(table))(*[int(a) for a, _ in table])
+    r = (ctypes.c_int * len(table))(*[int(b) for _, b in table])
+    _check(lib().cs_set_auto_tiles(n, r, len(table)), "cs_set_auto_tiles")
+
+
+def get_auto_tiles():
+    cnt = lib().cs_get_auto_tiles(None, None, 0)
+    n = (ctypes.c_int64 * cnt)()
+    r = (ctypes.c_int * cnt)()
+    lib().cs_get_auto_tiles(n, r, cnt)
+    return [(int(n[i]), int(r[i])) for i in range(cnt)]
+
+
+def set_batch_tuning(path=PATH_AUTO, max_run=16):
+    """cs_set_batch_tuning: the path AUTO means for batches and count jobs, and the
+    multi-set queue's run length."""
+    _check(lib().cs_set_batch_tuning(int(path), int(max_run)), "cs_set_batch_tuning")
+
+
+def get_batch_tuning():
+    p, r = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().cs_get_batch_tuning(ctypes.byref(p), ctypes.byref(r)), "cs_get_batch_tuning")
+    return p.value, r.value
 
 
 def set_auto_memory_limit(nbytes: int = 0):

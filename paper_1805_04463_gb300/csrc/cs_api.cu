@@ -48,6 +48,35 @@ int64_t g_auto_n[kMaxAuto] = {0, 1024, 4096};
 int g_auto_p[kMaxAuto] = {CS_PATH_POPC, CS_PATH_MMA, CS_PATH_MMA4};
 int g_auto_count = 3;
 
+// Tile choices.  Raster side per size bucket of the single-set tensor
+// counts (default 8 everywhere: a GB300 sweep of 4..16 found 8 best or
+// within 1% from n = 2^15 to 2^17); the path CS_PATH_AUTO plans for batches
+// and count jobs (0 = the default: FP4 pairs where the device has tcgen05,
+// 9.8 vs 11.3 ms for the 768-set ensemble on GB300); the longest run of
+// consecutive items a CTA takes from a multi-set queue.
+constexpr int kMaxTiles = 16;
+int64_t g_tile_n[kMaxTiles] = {0};
+int g_tile_r[kMaxTiles] = {kRasterDefault};
+int g_tile_count = 1;
+std::atomic<int> g_batch_path{CS_PATH_AUTO};
+std::atomic<int> g_max_run{16};
+
+int auto_raster(int64_t n) {
+    std::lock_guard<std::mutex> lk(g_auto_mu);
+    int r = kRasterDefault;
+    for (int e = 0; e < g_tile_count; ++e)
+        if (n >= g_tile_n[e]) r = g_tile_r[e];
+    return r;
+}
+
+int batch_auto_path() {
+    const int p = g_batch_path.load(std::memory_order_relaxed);
+    if (p != CS_PATH_AUTO) return (p == CS_PATH_POPC || device_has_tcgen05()) ? p : CS_PATH_POPC;
+    return device_has_tcgen05() ? CS_PATH_MMA4 : CS_PATH_POPC;
+}
+
+int batch_max_run() { return g_max_run.load(std::memory_order_relaxed); }
+
 // Device memory AUTO may plan for: the caller's limit, or 90% of the
 // device's memory when none is set.
 std::atomic<size_t> g_auto_mem_limit{0};
@@ -155,6 +184,45 @@ int cs_set_auto_paths(const int64_t* n_min, const int* paths, int count) {
         g_auto_p[e] = paths[e];
     }
     g_auto_count = count;
+    return CS_OK;
+}
+
+int cs_set_auto_tiles(const int64_t* n_min, const int* raster, int count) {
+    if (!n_min || !raster || count < 1 || count > kMaxTiles || n_min[0] != 0) return CS_EINVAL;
+    for (int e = 0; e < count; ++e) {
+        if (raster[e] < 1 || raster[e] > 32) return CS_EINVAL;
+        if (e > 0 && n_min[e] <= n_min[e - 1]) return CS_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_auto_mu);
+    for (int e = 0; e < count; ++e) {
+        g_tile_n[e] = n_min[e];
+        g_tile_r[e] = raster[e];
+    }
+    g_tile_count = count;
+    return CS_OK;
+}
+
+int cs_get_auto_tiles(int64_t* n_min, int* raster, int capacity) {
+    std::lock_guard<std::mutex> lk(g_auto_mu);
+    if (!n_min || !raster || capacity < g_tile_count) return g_tile_count;
+    for (int e = 0; e < g_tile_count; ++e) {
+        n_min[e] = g_tile_n[e];
+        raster[e] = g_tile_r[e];
+    }
+    return g_tile_count;
+}
+
+int cs_set_batch_tuning(int path, int max_run) {
+    if (path < CS_PATH_AUTO || path > CS_PATH_MMA4 || max_run < 1 || max_run > 64) return CS_EINVAL;
+    g_batch_path.store(path, std::memory_order_relaxed);
+    g_max_run.store(max_run, std::memory_order_relaxed);
+    return CS_OK;
+}
+
+int cs_get_batch_tuning(int* path, int* max_run) {
+    if (!path || !max_run) return CS_EINVAL;
+    *path = g_batch_path.load(std::memory_order_relaxed);
+    *max_run = g_max_run.load(std::memory_order_relaxed);
     return CS_OK;
 }
 

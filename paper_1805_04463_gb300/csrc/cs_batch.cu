@@ -351,7 +351,7 @@ bool batch_valid(const cs_set_desc* sets, int n_sets) {
 
 int batch_path(const cs_set_desc* sets, int n_sets, int path) {
     if (path != CS_PATH_AUTO) return path;
-    return device_has_tcgen05() ? CS_PATH_MMA : CS_PATH_POPC;
+    return batch_auto_path();
 }
 
 bool tensor_path(int path) { return path == CS_PATH_MMA || path == CS_PATH_MMA4; }

@@ -117,15 +117,16 @@ static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "stage buffers sta
 
 // Items.  Pairs are covered by 256 x 256 supertiles (si <= sj), each split
 // into two 128-row halves (one MMA tile each).  Supertiles are grouped into
-// kRaster x kRaster raster blocks; blocks are served from the widest band
-// (longest K) to the diagonal, and the 2 * kRaster^2 slots of a block are
+// R x R raster blocks; blocks are served from the widest band
+// (longest K) to the diagonal, and the 2 * R^2 slots of a block are
 // consecutive item indices.  CTAs that run at the same time therefore share
 // A panels (same si) and B panels (same sj) through L2 instead of each
 // streaming its own operands from HBM.  Slots with si > sj, or beyond n,
 // decode to nothing: the producer skips them, and hands the other roles
 // only the valid items, already decoded (pack_item).
-constexpr int kRaster = 8;
-constexpr int64_t kSlotsPerBlock = 2 * kRaster * kRaster;
+// The raster side R is a runtime parameter of the single-set counts (the
+// autotuner may choose it per size); the multi-set counts (batches, count
+// jobs) keep kRasterDefault, so a set's item list is fixed for them.
 
 struct Item {
     int64_t I0, J0;
@@ -134,18 +135,19 @@ struct Item {
 
 // Slot t of a set's item list -> supertile (si, sj) and its 128-row half;
 // false for a slot that holds no work.
-__device__ __forceinline__ bool decode_slot(int64_t t, int64_t nsb, int64_t n, int64_t& si, int64_t& sj,
+__device__ __forceinline__ bool decode_slot(int64_t t, int64_t nsb, int64_t n, int64_t R, int64_t& si, int64_t& sj,
                                             int64_t& half) {
-    const int64_t blk = t / kSlotsPerBlock, slot = t - blk * kSlotsPerBlock;
-    const int64_t nbg = (nsb + kRaster - 1) / kRaster;
+    const int64_t spb = 2 * R * R;  // slots per raster block
+    const int64_t blk = t / spb, slot = t - blk * spb;
+    const int64_t nbg = (nsb + R - 1) / R;
     int64_t m = int64_t((1.0f + sqrtf(1.0f + 8.0f * float(blk))) * 0.5f);  // corrected below
     while (m * (m - 1) / 2 > blk) --m;
     while (m * (m + 1) / 2 <= blk) ++m;
     const int64_t gi = blk - m * (m - 1) / 2;
     const int64_t gj = gi + (nbg - m);
-    si = gi * kRaster + slot / (2 * kRaster);
-    const int64_t rem = slot % (2 * kRaster);
-    sj = gj * kRaster + rem / 2;
+    si = gi * R + slot / (2 * R);
+    const int64_t rem = slot % (2 * R);
+    sj = gj * R + rem / 2;
     half = rem & 1;
     return si <= sj && sj < nsb && si * 256 + half * kBM < n;
 }
@@ -353,6 +355,7 @@ struct MmaView {
     const double* phi;  // d'Alembertian field (NULL = 1)
     double* layer;      // layer sums [kmax+1][n], or NULL
     int kmax;           // < 0: no layer sums
+    int raster;         // raster block side of the item order
 };
 
 // Work source: a single set passed in kernel parameters.  The queue hands out
@@ -407,7 +410,7 @@ struct MmaMulti {
         const MmaSetEntry& e = sets[s];
         return MmaView{e.maps.m, e.bits, e.n, e.row_words, e.nsb, e.kblocks,
                        reinterpret_cast<unsigned long long*>(hist_base + uintptr_t(e.hist_off)),
-                       e.n > 1 ? e.n - 1 : 1, e.phi, e.layer, int(e.kmax)};
+                       e.n > 1 ? e.n - 1 : 1, e.phi, e.layer, int(e.kmax), kRasterDefault};
     }
 };
 
@@ -570,7 +573,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                         cur = sidx;
                         v = src.view(sidx);
                     }
-                    if (decode_slot(lu * kCl, v.nsb, v.n, si, sj, half)) {
+                    if (decode_slot(lu * kCl, v.nsb, v.n, v.raster, si, sj, half)) {
                         e = pack_item(sidx, si, sj, half);
                         break;
                     }
@@ -859,8 +862,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_count_mma(const __grid_constant__ MmaMaps maps, const uint64_t* __restrict__ bits, int64_t n,
                 int64_t row_words, int64_t nsb, int64_t nitems, int64_t kblocks,
                 unsigned long long* __restrict__ hist, int64_t hist_len, const double* phi, double* layer, int kmax,
-                WsHeader* hdr) {
-    const MmaSingle src{MmaView{maps.m, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax},
+                int raster, WsHeader* hdr) {
+    const MmaSingle src{MmaView{maps.m, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax, raster},
                         nitems};
     mma_body<FmtF8>(src, hdr);
 }
@@ -872,8 +875,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_count_mma4(const __grid_constant__ MmaMaps maps, const uint64_t* __restrict__ bits, int64_t n,
                  int64_t row_words, int64_t nsb, int64_t nitems, int64_t kblocks,
                  unsigned long long* __restrict__ hist, int64_t hist_len, const double* phi, double* layer, int kmax,
-                 WsHeader* hdr) {
-    const MmaSingle src{MmaView{maps.m, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax},
+                 int raster, WsHeader* hdr) {
+    const MmaSingle src{MmaView{maps.m, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax, raster},
                         nitems};
     mma_body<Fmt>(src, hdr);
 }
@@ -1001,12 +1004,13 @@ int64_t mma_kpad(int64_t n, bool fp4) {
 
 size_t mma_operand_bytes(int64_t n, bool fp4, int which) { return operand_bytes(n, mma_kpad(n, fp4), fp4, which); }
 
-int64_t mma4_units(int64_t n) { return mma_items(n) / 2; }
+int64_t mma4_units(int64_t n, int raster) { return mma_items(n, raster) / 2; }
 
-int64_t mma_items(int64_t n) {
+int64_t mma_items(int64_t n, int raster) {
     const int64_t nsb = (n + 255) / 256;
-    const int64_t nbg = (nsb + kRaster - 1) / kRaster;
-    return kSlotsPerBlock * nbg * (nbg + 1) / 2;
+    const int64_t R = raster;
+    const int64_t nbg = (nsb + R - 1) / R;
+    return 2 * R * R * nbg * (nbg + 1) / 2;
 }
 
 CUresult mma_fill_entry(MmaSetEntry* e, const uint64_t* bits, int64_t n, int64_t row_words, uint8_t* op0,
@@ -1059,9 +1063,10 @@ cudaError_t launch_count_mma4_multi(const MmaSetEntry* sets_dev, int nsets, int6
     if ((err = pair_config(k_count_mma4_multi, g_attr4m_set, g_clusters4m, nunits, st, at, &cfg, &pairs)) !=
         cudaSuccess)
         return err;
-    // runs of up to 16 consecutive supertiles, at least 8 runs per pair
+    // runs of up to max_run consecutive supertiles, at least 8 runs per pair
+    const int64_t cap = batch_max_run();
     int64_t run = nunits / (int64_t(pairs) * 8);
-    run = run < 1 ? 1 : (run > 16 ? 16 : run);
+    run = run < 1 ? 1 : (run > cap ? cap : run);
     return cudaLaunchKernelEx(&cfg, k_count_mma4_multi, sets_dev, nsets, 2 * nunits, hist_base, run, hdr);
 }
 
@@ -1079,8 +1084,9 @@ cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64
     }
     int64_t grid = max_ctas > 0 ? max_ctas : device_sm_count();
     if (grid > nitems) grid = nitems;
+    const int64_t cap = batch_max_run();
     int64_t run = nitems / (grid * 8);
-    run = run < 1 ? 1 : (run > 16 ? 16 : run);
+    run = run < 1 ? 1 : (run > cap ? cap : run);
     k_count_mma_multi<<<unsigned(grid), kThreads, kSmemBytes, st>>>(sets_dev, nsets, nitems, hist_base, run, hdr);
     return cudaGetLastError();
 }
@@ -1122,14 +1128,15 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
         attr[dev] = true;
     }
     const int64_t nsb = (n + 255) / 256;
-    const int64_t nitems = mma_items(n);
+    const int raster = auto_raster(n);
+    const int64_t nitems = mma_items(n, raster);
     const int64_t kblocks = lay.row / kBK;
     unsigned long long* h = reinterpret_cast<unsigned long long*>(hist);
     if constexpr (kCl == 1) {
         int64_t grid = device_sm_count();
         if (grid > nitems) grid = nitems;
         kernel<<<unsigned(grid), kThreads, kSmemBytes, st>>>(maps, bits, n, row_words, nsb, nitems, kblocks, h,
-                                                             hist_len, phi, layer, kmax, hdr);
+                                                             hist_len, phi, layer, kmax, raster, hdr);
         return cudaGetLastError();
     } else {
         cudaLaunchAttribute at[1];
@@ -1139,7 +1146,7 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
                                &pairs)) != cudaSuccess)
             return err;
         return cudaLaunchKernelEx(&cfg, kernel, maps, bits, n, row_words, nsb, nitems, kblocks, h, hist_len, phi,
-                                  layer, kmax, hdr);
+                                  layer, kmax, raster, hdr);
     }
 }
 

@@ -16,10 +16,7 @@ using namespace cs;
 
 namespace {
 
-int jobs_path(int path) {
-    if (path == CS_PATH_AUTO) return device_has_tcgen05() ? CS_PATH_MMA : CS_PATH_POPC;
-    return path;
-}
+int jobs_path(int path) { return path == CS_PATH_AUTO ? batch_auto_path() : path; }
 
 bool tensor_path(int path) { return path == CS_PATH_MMA || path == CS_PATH_MMA4; }
 

@@ -72,9 +72,13 @@ struct alignas(128) MmaSetEntry {
 // fp4 selects the packed-FP4 operand format of the pair path (CS_PATH_MMA4):
 // K padded to 256 elements, two per byte; its work unit is a 256 x 256
 // supertile (mma4_units per set) instead of a 128 x 256 tile (mma_items).
+// Work items of a set: slots of 128 x 256 tiles (FP8) or units of 256 x 256
+// supertiles (FP4 pairs) in raster blocks of side `raster`.  The multi-set
+// counts use kRasterDefault; the single-set counts auto_raster(n).
+constexpr int kRasterDefault = 8;
 size_t mma_workspace_bytes(int64_t n);
-int64_t mma_items(int64_t n);
-int64_t mma4_units(int64_t n);
+int64_t mma_items(int64_t n, int raster = kRasterDefault);
+int64_t mma4_units(int64_t n, int raster = kRasterDefault);
 int64_t mma_kpad(int64_t n, bool fp4 = false);
 // Bytes of a set's first (U, or E) and second (L, or DU and DL) operand buffer.
 size_t mma_operand_bytes(int64_t n, bool fp4, int which);
@@ -113,6 +117,13 @@ int cuda_status(cudaError_t e);
 
 // Path chosen for CS_PATH_AUTO at size n.
 int resolve_path(int64_t n, int path);
+// Tile choices (cs_set_auto_tiles, cs_set_batch_tuning): the raster side of
+// a single-set tensor count of size n; the path CS_PATH_AUTO plans for
+// batches and count jobs; the longest run of consecutive work items a CTA
+// takes from the queue of a multi-set count.
+int auto_raster(int64_t n);
+int batch_auto_path();
+int batch_max_run();
 
 // cs_action.cu
 int action_host(int dim, int64_t n, const int64_t* hist, int64_t len, double eps, double* out,

@@ -161,6 +161,42 @@ def test_tuner_choice_logic():
     assert tune.choose([(1024, 0.5, None, 0.2), (2048, 0.4, 0.3, None)]) == [(0, 3), (2048, 2)]
 
 
+def test_tuner_tile_choice_logic():
+    from paper_1805_04463_gb300 import tune
+    # the fastest raster side per size; the default side (8) wins within 1%
+    m = [(4096, {4: 1.00, 8: 1.005, 16: 1.2}), (16384, {4: 9.0, 8: 8.0, 16: 7.0}), (65536, {4: 50, 8: 40, 16: 45})]
+    assert tune.choose_tiles(m) == [(0, 8), (16384, 16), (65536, 8)]
+    assert tune.choose_tiles([(4096, {4: 1.0, 8: 2.0})]) == [(0, 4)]
+    assert tune.choose_tiles([]) == [(0, 8)]
+    # batches: the fastest (path, run) pair
+    assert tune.choose_batch([(2, 4, 9.0), (2, 16, 8.0), (3, 4, 7.5), (3, 16, 7.9)]) == (3, 4)
+
+
+def test_tile_and_batch_tuning_entry_points(cslib):
+    L = cslib.lib()
+    old_tiles, old_batch = cslib.get_auto_tiles(), cslib.get_batch_tuning()
+    assert old_tiles == [(0, 8)] and old_batch == (0, 16)
+    try:
+        cslib.set_auto_tiles([(0, 8), (32768, 16)])
+        assert cslib.get_auto_tiles() == [(0, 8), (32768, 16)]
+        cslib.set_batch_tuning(2, 4)
+        assert cslib.get_batch_tuning() == (2, 4)
+        with pytest.raises(cslib.CsError):
+            cslib.set_auto_tiles([(1, 8)])            # must start at 0
+        with pytest.raises(cslib.CsError):
+            cslib.set_auto_tiles([(0, 8), (0, 4)])    # must increase
+        with pytest.raises(cslib.CsError):
+            cslib.set_auto_tiles([(0, 33)])           # raster side 1..32
+        with pytest.raises(cslib.CsError):
+            cslib.set_batch_tuning(4, 16)             # no such path
+        with pytest.raises(cslib.CsError):
+            cslib.set_batch_tuning(0, 65)             # run 1..64
+        assert L.cs_get_batch_tuning(None, None) == -1
+    finally:
+        cslib.set_auto_tiles(old_tiles)
+        cslib.set_batch_tuning(*old_batch)
+
+
 def test_peak_probe_rejects_bad_arguments(cslib):
     import ctypes
     L = cslib.lib()

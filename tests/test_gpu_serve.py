@@ -105,16 +105,36 @@ def test_item_shards_sum_to_the_full_count(cs, path):
 
 
 def test_autotuner_installs_a_measured_table(cs, tmp_path):
+    # The tuner measures the path per size, the raster side of the tensor
+    # counts per size and the multi-set path and run length, installs them,
+    # persists them, and a later load installs the same choices; results do
+    # not depend on any of them.
     import torch
     from paper_1805_04463_gb300 import tune
-    old = cs.get_auto_paths()
+    old = (cs.get_auto_paths(), cs.get_auto_tiles(), cs.get_batch_tuning())
+    f = str(tmp_path / "tune.json")
     try:
-        table, m = tune.autotune(sizes=(1024, 4096, 16384), path=str(tmp_path / "tune.json"))
-        assert cs.get_auto_paths() == [tuple(x) for x in table]
-        assert [x[0] for x in m] == [1024, 4096, 16384] and all(x[1] > 0 and x[2] > 0 for x in m)
-        cs.set_auto_paths(old)
-        assert tune.load(str(tmp_path / "tune.json")) == [tuple(x) for x in table]
-        # AUTO under the tuned table gives the same counts as both explicit paths
+        r = tune.autotune(sizes=(1024, 4096, 16384), tile_sizes=(4096, 16384), rasters=(4, 8, 16),
+                          runs=(4, 16), batch_sample=(12, 6), path=f)
+        assert cs.get_auto_paths() == [tuple(x) for x in r["paths"]]
+        assert [x[0] for x in r["measurements"]] == [1024, 4096, 16384]
+        assert all(x[1] > 0 and x[2] > 0 for x in r["measurements"])
+        # tile order: every candidate raster side was timed at each tensor-path size
+        assert [n for n, _ in r["tile_measurements"]] == [4096, 16384]
+        assert all(set(ts) == {"4", "8", "16"} and min(ts.values()) > 0 for _, ts in r["tile_measurements"])
+        assert cs.get_auto_tiles() == [tuple(x) for x in r["tiles"]]
+        assert all(rs in (4, 8, 16) for _, rs in r["tiles"])
+        # multi-set tuning: both tensor paths and both run lengths timed
+        assert {(p, run) for p, run, _ in r["batch_measurements"]} == {(2, 4), (2, 16), (3, 4), (3, 16)}
+        assert cs.get_batch_tuning() == r["batch"]
+        cs.set_auto_paths(old[0])
+        cs.set_auto_tiles(old[1])
+        cs.set_batch_tuning(*old[2])
+        loaded = tune.load(f)
+        assert loaded["tiles"] == r["tiles"] and cs.get_auto_tiles() == [tuple(x) for x in r["tiles"]]
+        assert loaded["batch"] == r["batch"] and cs.get_batch_tuning() == r["batch"]
+        assert loaded["paths"] == r["paths"] and cs.get_auto_paths() == r["paths"]
+        # AUTO under the tuned choices gives the same counts as every explicit path
         for n in (1024, 16384):
             hs = []
             for p in (0, 1, 2, 3):
@@ -124,7 +144,9 @@ def test_autotuner_installs_a_measured_table(cs, tmp_path):
                 hs.append(b.hist.clone())
             assert all(torch.equal(hs[0], h) for h in hs[1:])
     finally:
-        cs.set_auto_paths(old)
+        cs.set_auto_paths(old[0])
+        cs.set_auto_tiles(old[1])
+        cs.set_batch_tuning(*old[2])
 
 
 def test_auto_server_counts_on_the_fp4_pair_path(cs):
