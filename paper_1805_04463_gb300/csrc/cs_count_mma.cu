@@ -56,7 +56,14 @@ constexpr int kHistBins = 8192;
 constexpr int64_t kFlushTiles = 32768;
 constexpr int kEpiWarps = 16;            // four epilogue warps per TMEM lane quarter
 constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kThreads = 64 + kEpiThreads;
+constexpr int kSchedWarp = 2 + kEpiWarps;  // the scheduler: finds, decodes and publishes the items
+constexpr int kThreads = 64 + kEpiThreads + 32;
+// Registers per thread of the count kernels, set explicitly (__maxnreg__):
+// the warps of a CTA spread over the SM's four register-file quarters of
+// 16384 registers, so the fullest quarter (ceil(19 / 4) = 5 warps) must hold
+// 5 x 32 x kMaxRegs; 104 registers would not launch.
+constexpr int kMaxRegs = 96;
+static_assert((kThreads / 32 + 3) / 4 * 32 * kMaxRegs <= 16384, "the fullest register-file quarter fits");
 constexpr int kEpiChunks = (kBN / 32) / (kEpiWarps / 4);  // 32-column chunks per epilogue warp
 static_assert(kEpiWarps % 4 == 0 && (kBN / 32) % (kEpiWarps / 4) == 0, "epilogue warps split the columns evenly");
 constexpr int kTmemCols = 512;           // two 256-column FP32 accumulators, or one and the FP4 scales
@@ -484,11 +491,12 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         }
         mbar_init(ebar, kEpiThreads);
         mbar_init(done, 1);
-        // Pair: rank 0's iempty counts its MMA thread and epilogue and rank
-        // 1's producer and epilogue (rank 1's own iempty is unused).
+        // iempty counts every consumer of an entry: the producer, MMA thread
+        // and epilogue; in a pair, rank 0's counts both CTAs' producers and
+        // epilogues and rank 0's MMA thread (rank 1's own iempty is unused).
         for (int r = 0; r < kRing; ++r) {
             mbar_init(&ifull[r], 1);
-            mbar_init(&iempty[r], kPair ? 2 * (1 + kEpiThreads) : 1 + kEpiThreads);
+            mbar_init(&iempty[r], kPair ? 2 * (1 + kEpiThreads) + 1 : 2 + kEpiThreads);
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -520,11 +528,16 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
     // The peer's barriers and TMEM are ready before anyone signals them.
     if constexpr (kPair) cluster_sync();
 
-    // Item ring.  One CTA: the producer publishes each item to its own MMA
-    // and epilogue threads.  A pair: rank 0's producer publishes each
-    // supertile to both CTAs (its own slot and, through the cluster window,
-    // rank 1's), and every consumer of either CTA -- rank 1's producer too --
-    // releases the slot on rank 0's iempty.  A ring entry is a decoded item
+    // Item ring.  The scheduler (warp kSchedWarp; in a pair, rank 0's)
+    // publishes each item to the producer, MMA and epilogue threads (in a
+    // pair to both CTAs: its own slot and, through the cluster window, rank
+    // 1's), and every consumer of either CTA releases the slot on rank 0's
+    // iempty.  Running ahead of the producer by up to kRing items, it keeps
+    // the search for work, its global queue atomic and the publication off
+    // the path between one tile's last load and the next tile's first
+    // (measured there: about 3500 SM cycles per tile when the producer did
+    // both, and the MMAs then waited 1.2-1.8 us for each tile's first
+    // K-block).  A ring entry is a decoded item
     // (pack_item): the unit the queue hands out is a slot (one CTA) or a
     // supertile slot (a pair, which runs it as slot 2 * unit, its upper
     // half), and the producer skips the units that hold no work.
@@ -544,51 +557,17 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------- TMA producer
-        // Pulls units from the global queue (consecutive indices are
-        // raster-local, so the CTAs running at any moment share operand
-        // panels in L2) and publishes each to the other roles.
+        // Takes each item from the ring and streams its K-blocks into the
+        // stages (a pair: each CTA its own rows).
         uint32_t s = 0, ph = 0, issued = 0;
         bool ok = true;
         int cur = -1;
         MmaView v{};
-        int64_t next = 0, end = 0;  // the current run of units from the queue
-        const int64_t units = total / kCl;
         for (uint32_t q = 0; ok; ++q) {
             const uint32_t slot = q % kRing, use = (q / kRing) & 1u;
-            int64_t e = -1;
-            if (leader) {
-                if (!mbar_wait_or_abort<kPair>(&iempty[slot], use ^ 1u, hdr, abort_flag)) { ok = false; break; }
-                // the producer alone finds the next unit that holds work,
-                // decodes it and hands it on
-                for (;;) {
-                    if (next >= end) {
-                        next = int64_t(atomicAdd(&hdr->counter, 1ull)) * src.chunk();
-                        end = next + src.chunk();
-                    }
-                    const int64_t t = next++;
-                    if (t >= units) break;
-                    int64_t lu, si, sj, half;
-                    const int sidx = src.set_of(t, lu, cur);
-                    if (sidx != cur) {
-                        cur = sidx;
-                        v = src.view(sidx);
-                    }
-                    if (decode_slot(lu * kCl, v.nsb, v.n, v.raster, si, sj, half)) {
-                        e = pack_item(sidx, si, sj, half);
-                        break;
-                    }
-                }
-                ring[slot] = e;
-                mbar_arrive(&ifull[slot]);
-                if constexpr (kPair) {
-                    st_cluster_s64(cluster_map(const_cast<int64_t*>(&ring[slot]), 1), e);
-                    mbar_arrive_cluster(cluster_map(&ifull[slot], 1), 1u);
-                }
-            } else {
-                if (!ring_wait(slot, use)) { ok = false; break; }
-                e = ring[slot];
-                ring_release(slot);
-            }
+            if (!ring_wait(slot, use)) { ok = false; break; }
+            const int64_t e = ring[slot];
+            ring_release(slot);
             if (e < 0) break;
             const int sidx = item_set(e);
             if (sidx != cur) {
@@ -635,6 +614,46 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 mbar_wait_bounded(&empty[s], ph ^ 1u, hdr, ok ? kWaitLimitNs : kWaitLimitNs / 40);
                 if (++s == kNS) { s = 0; ph ^= 1u; }
             }
+        }
+    } else if (warp == kSchedWarp && lane == 0 && leader) {
+        // ---------------------------------------------------- scheduler
+        // Pulls units from the global queue (consecutive indices are
+        // raster-local, so the CTAs running at any moment share operand
+        // panels in L2), skips the units that hold no work, and publishes
+        // the others decoded.
+        int cur = -1;
+        MmaView v{};
+        int64_t next = 0, end = 0;  // the current run of units from the queue
+        const int64_t units = total / kCl;
+        for (uint32_t q = 0;; ++q) {
+            const uint32_t slot = q % kRing, use = (q / kRing) & 1u;
+            if (!mbar_wait_or_abort<kPair>(&iempty[slot], use ^ 1u, hdr, abort_flag)) break;
+            int64_t e = -1;
+            for (;;) {
+                if (next >= end) {
+                    next = int64_t(atomicAdd(&hdr->counter, 1ull)) * src.chunk();
+                    end = next + src.chunk();
+                }
+                const int64_t t = next++;
+                if (t >= units) break;
+                int64_t lu, si, sj, half;
+                const int sidx = src.set_of(t, lu, cur);
+                if (sidx != cur) {
+                    cur = sidx;
+                    v = src.view(sidx);
+                }
+                if (decode_slot(lu * kCl, v.nsb, v.n, v.raster, si, sj, half)) {
+                    e = pack_item(sidx, si, sj, half);
+                    break;
+                }
+            }
+            ring[slot] = e;
+            mbar_arrive(&ifull[slot]);
+            if constexpr (kPair) {
+                st_cluster_s64(cluster_map(const_cast<int64_t*>(&ring[slot]), 1), e);
+                mbar_arrive_cluster(cluster_map(&ifull[slot], 1), 1u);
+            }
+            if (e < 0) break;
         }
     } else if (warp == 1 && lane == 0 && leader) {
         // ---------------------------------------------------- MMA issuer
@@ -698,7 +717,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
         else
             mma_commit(done);
         mbar_wait_bounded(done, 0, hdr, kWaitLimitNs / 40);
-    } else if (warp >= 2) {
+    } else if (warp >= 2 && warp < 2 + kEpiWarps) {
         // ---------------------------------------------------- epilogue
         const int q = warp & 3;            // TMEM lane quarter this warp may access
         const int c0 = ((warp - 2) >> 2) * kEpiChunks;  // first of its 32-column chunks
@@ -858,7 +877,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(kMaxRegs)
     k_count_mma(const __grid_constant__ MmaMaps maps, const uint64_t* __restrict__ bits, int64_t n,
                 int64_t row_words, int64_t nsb, int64_t nitems, int64_t kblocks,
                 unsigned long long* __restrict__ hist, int64_t hist_len, const double* phi, double* layer, int kmax,
@@ -871,7 +890,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // The same count on packed FP4 operands (kind::mxf4): counts only, and
 // counts with layer sums.
 template <class Fmt>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(kMaxRegs)
     k_count_mma4(const __grid_constant__ MmaMaps maps, const uint64_t* __restrict__ bits, int64_t n,
                  int64_t row_words, int64_t nsb, int64_t nitems, int64_t kblocks,
                  unsigned long long* __restrict__ hist, int64_t hist_len, const double* phi, double* layer, int kmax,
@@ -881,7 +900,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mma_body<Fmt>(src, hdr);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(kMaxRegs)
     k_count_mma_multi(const MmaSetEntry* __restrict__ sets, int nsets, int64_t nitems, uintptr_t hist_base,
                       int64_t run, WsHeader* hdr) {
     const MmaMulti src{sets, nsets, nitems, hist_base, run};
@@ -891,7 +910,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Many sets on the FP4 pair path.  The table's item_begin / item_offset and
 // `run` count supertiles (the pair's unit of work); nitems is twice the
 // number of supertiles.
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(kMaxRegs)
     k_count_mma4_multi(const MmaSetEntry* __restrict__ sets, int nsets, int64_t nitems, uintptr_t hist_base,
                        int64_t run, WsHeader* hdr) {
     const MmaMulti src{sets, nsets, nitems, hist_base, run};
