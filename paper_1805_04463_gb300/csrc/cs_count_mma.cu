@@ -46,11 +46,9 @@ constexpr int kBM = 128;                 // i rows per tile (TMEM lanes)
 constexpr int kBN = 256;                 // j rows per tile (accumulator columns)
 constexpr int kBK = 128;                 // K bytes per stage and operand row = one swizzle row (128 or 64)
 constexpr int kUK = 32;                  // K bytes per tcgen05.mma (K32 FP8 or K64 packed FP4)
-constexpr int kStages = 4;
 constexpr int kABytes = kBM * kBK;       // 16 KiB
 constexpr int kBBytes = kBN * kBK;       // 32 KiB
 constexpr int kStageBytes = kABytes + kBBytes;
-constexpr int kHistBins = 8192;
 // A tile adds at most 128 x 256 to a CTA's shared bin; flushing every 32768
 // tiles keeps the 32-bit bins below 2^30 whatever the order.
 constexpr int64_t kFlushTiles = 32768;
@@ -72,7 +70,7 @@ constexpr uint32_t kIdesc4 = idesc_mxf4_f32(kBM, kBN);
 constexpr uint32_t kSfCol = 256;         // FP4: scale factors of A at this TMEM column, of B 16 further
 constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;  // four UE8M0 scale factors 2^0 = 1
 constexpr int kRing = 4;                 // items in flight between the roles
-constexpr int kSmemBytes = kStages * kStageBytes + kHistBins * 4 + 256 + 1024;
+constexpr int kBarrierBytes = 512;       // mbarriers, item ring, TMEM address, abort flag
 constexpr uint8_t kOne = 0x38;           // 1.0 in FP8 E4M3
 
 // Operand formats.  A stage holds one 128-byte swizzle row of K per operand
@@ -97,17 +95,23 @@ constexpr uint8_t kOne = 0x38;           // 1.0 in FP8 E4M3
 // kernels are bound by shared-memory traffic per MAC (TMA writes plus
 // tensor-core reads), and six stages fit instead of four.  Both halves run
 // the same K range, which wastes nothing when K-blocks hold 256 elements.
+// kStages and kHistBins split the shared memory between the operand ring
+// and the privatised histogram (bins at or above kHistBins go to global
+// atomics).  Both stay at their largest joint size: a seventh FP4 stage with
+// 256 shared bins (96% of the counts of a 2^17 order then global atomics,
+// against 52% with 8192 bins) made the count 24% slower at n = 2^17 and
+// 2.9x slower at 2^15, the L2 atomics competing with the operand loads.
 struct FmtF8 {
     static constexpr int kKE = kBK;      // K elements per stage
     static constexpr int kAcc = 2;
     static constexpr bool kLayers = true, kSmallSet = true, kPair = false;
-    static constexpr int kStages = 4;
+    static constexpr int kStages = 4, kHistBins = 8192;
 };
 struct FmtF4 {
     static constexpr int kKE = 2 * kBK;
     static constexpr int kAcc = 1;
     static constexpr bool kLayers = false, kSmallSet = false, kPair = true;
-    static constexpr int kStages = 6;
+    static constexpr int kStages = 6, kHistBins = 8192;
 };
 struct FmtF4Layers : FmtF4 {
     static constexpr bool kLayers = true;
@@ -118,6 +122,14 @@ struct FmtF4Layers : FmtF4 {
 struct FmtF4Multi : FmtF4 {
     static constexpr bool kSmallSet = true;
 };
+// Bytes of one operand stage in each CTA, and the dynamic shared memory of
+// a kernel on format Fmt (the base is rounded up to 1024 inside).
+template <class Fmt>
+constexpr int stage_bytes() { return kABytes + (Fmt::kPair ? kBN / 2 : kBN) * kBK; }
+template <class Fmt>
+constexpr int smem_bytes() { return Fmt::kStages * stage_bytes<Fmt>() + Fmt::kHistBins * 4 + kBarrierBytes + 1024; }
+static_assert(smem_bytes<FmtF8>() <= 232448 && smem_bytes<FmtF4>() <= 232448 && smem_bytes<FmtF4Multi>() <= 232448,
+              "227 KiB of shared memory per CTA");
 constexpr CUtensorMapSwizzle kSwizzle = kBK == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
 static_assert(kBK == 128 || kBK == 64, "one 128- or 64-byte swizzle row per stage");
 static_assert(kStageBytes % 1024 == 0 && kABytes % 1024 == 0, "stage buffers stay swizzle-atom aligned");
@@ -299,8 +311,22 @@ __device__ __forceinline__ void expand_row_f4(const uint64_t* __restrict__ bits,
     const uint32_t* brow = reinterpret_cast<const uint32_t*>(bits + i * row_words);
     uint4* erow = reinterpret_cast<uint4*>(E + i * (kpad / 2));
     const int own = int(own_first_piece(i));
-    for (int c = t; c < ppr; c += size)
-        if (unsigned(c - own) >= 8u) erow[c] = spread32_e2m1(__ldg(brow + c));
+    // four pieces per step, their loads issued together (memory-level
+    // parallelism: one load, spread and store at a time left the expansion
+    // latency-bound)
+    for (int c0 = t; c0 < ppr; c0 += 4 * size) {
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = c0 + k * size;
+            w[k] = c < ppr ? __ldg(brow + c) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = c0 + k * size;
+            if (c < ppr && unsigned(c - own) >= 8u) erow[c] = spread32_e2m1(w[k]);
+        }
+    }
     uint4* du = reinterpret_cast<uint4*>(D + i * 128);
     uint4* dl = reinterpret_cast<uint4*>(D + dl_off + i * 128);
     const int ii = int(i);  // n < 2^31
@@ -430,12 +456,12 @@ __device__ __forceinline__ bool epilogue_sync(uint64_t* ebar, uint32_t& phase, W
     return ok;
 }
 
-// Epilogue threads add the shared histogram to the set's histogram and clear
-// it.  Returns false if the CTA aborted.
-__device__ __forceinline__ bool epilogue_flush(uint32_t* shist, const MmaView& v, int etid, uint64_t* ebar,
-                                               uint32_t& phase, WsHeader* hdr, volatile int* abort) {
+// Epilogue threads add the shared histogram (its first `bins` bins) to the
+// set's histogram and clear it.  Returns false if the CTA aborted.
+__device__ __forceinline__ bool epilogue_flush(uint32_t* shist, int64_t bins, const MmaView& v, int etid,
+                                               uint64_t* ebar, uint32_t& phase, WsHeader* hdr, volatile int* abort) {
     if (!epilogue_sync(ebar, phase, hdr, abort)) return false;
-    const int64_t hb = v.hist_len < kHistBins ? v.hist_len : kHistBins;
+    const int64_t hb = v.hist_len < bins ? v.hist_len : bins;
     for (int64_t k = etid; k < hb; k += kEpiThreads) {
         const uint32_t c = shist[k];
         if (c) {
@@ -455,12 +481,13 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
     constexpr int kBRows = kPair ? kBN / 2 : kBN;             // B rows each CTA holds per stage
     constexpr int kSB = kABytes + kBRows * kBK;               // stage bytes per CTA
     constexpr int kMmaM = kPair ? 2 * kBM : kBM;
-    static_assert(kNS * kSB <= kStages * kStageBytes, "the stages fit the shared-memory carve-out");
+    constexpr int kHistBins = Fmt::kHistBins;
+    static_assert(kSB == stage_bytes<Fmt>(), "stage layout");
     static_assert(kSB % 1024 == 0, "stage buffers stay swizzle-atom aligned");
     static_assert(!kPair || Fmt::kKE == kBN, "a pair's K-block is one supertile band (E, DU, DL operands)");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes);
+    uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kNS * kSB);
     uint64_t* full = reinterpret_cast<uint64_t*>(shist + kHistBins);
     uint64_t* empty = full + kNS;
     uint64_t* tfull = empty + kNS;
@@ -472,7 +499,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
     volatile int64_t* ring = reinterpret_cast<volatile int64_t*>(done + 1);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(const_cast<int64_t*>(ring) + kRing);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    static_assert((2 * kNS + 6 + 2 * kRing) * 8 + kRing * 8 + 8 <= 256, "barriers fit their 256 bytes");
+    static_assert((2 * kNS + 6 + 2 * kRing) * 8 + kRing * 8 + 8 <= kBarrierBytes, "barriers fit their area");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t total = src.total();
@@ -771,7 +798,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
             if (e < 0) break;
             const int sidx = item_set(e);
             if (sidx != cur || since_flush == kFlushTiles) {
-                if (cur >= 0 && !epilogue_flush(shist, v, etid, ebar, ephase, hdr, abort_flag)) { ok = false; break; }
+                if (cur >= 0 && !epilogue_flush(shist, kHistBins, v, etid, ebar, ephase, hdr, abort_flag)) { ok = false; break; }
                 cur = sidx;
                 v = src.view(sidx);
                 since_flush = 0;
@@ -862,7 +889,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                 acc_release(buf);
             }
         }
-        if (ok && cur >= 0) epilogue_flush(shist, v, etid, ebar, ephase, hdr, abort_flag);
+        if (ok && cur >= 0) epilogue_flush(shist, kHistBins, v, etid, ebar, ephase, hdr, abort_flag);
     }
     __syncthreads();
     // No CTA of a pair leaves (or frees the pair's TMEM) while the other
@@ -930,15 +957,14 @@ std::atomic<int> g_clusters4m[64];
 // of two as fit at once (queried once per device and kernel), at most
 // `units` of them.
 template <class K>
-cudaError_t pair_config(K kernel, std::atomic<bool>* attr, std::atomic<int>* cached, int64_t units,
+cudaError_t pair_config(K kernel, int smem, std::atomic<bool>* attr, std::atomic<int>* cached, int64_t units,
                         cudaStream_t st, cudaLaunchAttribute* at, cudaLaunchConfig_t* cfg, int* pairs) {
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr[dev]) {
-        if ((err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
-            cudaSuccess)
+        if ((err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
             return err;
         attr[dev] = true;
     }
@@ -949,7 +975,7 @@ cudaError_t pair_config(K kernel, std::atomic<bool>* attr, std::atomic<int>* cac
     *cfg = cudaLaunchConfig_t{};
     cfg->gridDim = dim3(unsigned(device_sm_count() / 2 * 2));
     cfg->blockDim = dim3(kThreads);
-    cfg->dynamicSmemBytes = kSmemBytes;
+    cfg->dynamicSmemBytes = smem;
     cfg->stream = st;
     cfg->attrs = at;
     cfg->numAttrs = 1;
@@ -1079,8 +1105,8 @@ cudaError_t launch_count_mma4_multi(const MmaSetEntry* sets_dev, int nsets, int6
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg;
     int pairs = 0;
-    if ((err = pair_config(k_count_mma4_multi, g_attr4m_set, g_clusters4m, nunits, st, at, &cfg, &pairs)) !=
-        cudaSuccess)
+    if ((err = pair_config(k_count_mma4_multi, smem_bytes<FmtF4Multi>(), g_attr4m_set, g_clusters4m, nunits, st, at,
+                           &cfg, &pairs)) != cudaSuccess)
         return err;
     // runs of up to max_run consecutive supertiles, at least 8 runs per pair
     const int64_t cap = batch_max_run();
@@ -1097,7 +1123,8 @@ cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64
     int dev = 0;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if (dev >= 0 && dev < 64 && !g_attr_multi_set[dev]) {
-        err = cudaFuncSetAttribute(k_count_mma_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        err = cudaFuncSetAttribute(k_count_mma_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   smem_bytes<FmtF8>());
         if (err != cudaSuccess) return err;
         g_attr_multi_set[dev] = true;
     }
@@ -1106,7 +1133,8 @@ cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64
     const int64_t cap = batch_max_run();
     int64_t run = nitems / (grid * 8);
     run = run < 1 ? 1 : (run > cap ? cap : run);
-    k_count_mma_multi<<<unsigned(grid), kThreads, kSmemBytes, st>>>(sets_dev, nsets, nitems, hist_base, run, hdr);
+    k_count_mma_multi<<<unsigned(grid), kThreads, smem_bytes<FmtF8>(), st>>>(sets_dev, nsets, nitems, hist_base, run,
+                                                                            hdr);
     return cudaGetLastError();
 }
 
@@ -1141,8 +1169,10 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
     int dev = 0;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    constexpr int kSmem = kFp4 ? smem_bytes<FmtF4>() : smem_bytes<FmtF8>();
+    static_assert(smem_bytes<FmtF4Layers>() == smem_bytes<FmtF4>(), "one shared-memory size per format family");
     if (!attr[dev]) {
-        err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
         if (err != cudaSuccess) return err;
         attr[dev] = true;
     }
@@ -1154,15 +1184,15 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
     if constexpr (kCl == 1) {
         int64_t grid = device_sm_count();
         if (grid > nitems) grid = nitems;
-        kernel<<<unsigned(grid), kThreads, kSmemBytes, st>>>(maps, bits, n, row_words, nsb, nitems, kblocks, h,
-                                                             hist_len, phi, layer, kmax, raster, hdr);
+        kernel<<<unsigned(grid), kThreads, kSmem, st>>>(maps, bits, n, row_words, nsb, nitems, kblocks, h, hist_len,
+                                                        phi, layer, kmax, raster, hdr);
         return cudaGetLastError();
     } else {
         cudaLaunchAttribute at[1];
         cudaLaunchConfig_t cfg;
         int pairs = 0;
-        if ((err = pair_config(kernel, attr, kmax >= 0 ? g_clusters4l : g_clusters4, nitems / kCl, st, at, &cfg,
-                               &pairs)) != cudaSuccess)
+        if ((err = pair_config(kernel, kSmem, attr, kmax >= 0 ? g_clusters4l : g_clusters4, nitems / kCl, st, at,
+                               &cfg, &pairs)) != cudaSuccess)
             return err;
         return cudaLaunchKernelEx(&cfg, kernel, maps, bits, n, row_words, nsb, nitems, kblocks, h, hist_len, phi,
                                   layer, kmax, raster, hdr);
