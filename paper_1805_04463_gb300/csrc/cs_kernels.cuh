@@ -69,6 +69,25 @@ struct alignas(128) MmaSetEntry {
     double* layer;       //   sums [kmax+1][n],
     int64_t kmax;        //   highest layer (< 0: none)
 };
+// Packed FP4 (E2M1) 0/1 operands.  Bits 0..7 of x -> 8 nibbles of 0x0 / 0x2
+// (bit b -> nibble b): three shift-and-mask steps move bit groups of 4, 2
+// and 1 apart (no carries), then the shift by one turns each 1 into 0x2 = 1.0
+// in E2M1.  Element k of a row sits in byte k/2, low nibble for even k; A
+// and B use the same packing, so every product pairs the same columns
+// whatever nibble order the MMA reads.
+__device__ __forceinline__ uint32_t spread8_e2m1(uint32_t x) {
+    x &= 0xFFu;
+    x = (x | (x << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    x = (x | (x << 3)) & 0x11111111u;
+    return x << 1;
+}
+
+// 32 bits of a bitset row -> 16 operand bytes.
+__device__ __forceinline__ uint4 spread32_e2m1(uint32_t b) {
+    return make_uint4(spread8_e2m1(b), spread8_e2m1(b >> 8), spread8_e2m1(b >> 16), spread8_e2m1(b >> 24));
+}
+
 // fp4 selects the packed-FP4 operand format of the pair path (CS_PATH_MMA4):
 // K padded to 256 elements, two per byte; its work unit is a 256 x 256
 // supertile (mma4_units per set) instead of a 128 x 256 tile (mma_items).
