@@ -5,9 +5,13 @@
 // Pipeline per launch, every kernel covering all sets at once:
 //   k_batch_keys    per element: random keys / raw coordinates (same draws as
 //                   cs_sprinkle, so every set equals its single-set result);
-//   k_batch_rank    one CTA per set: bitonic sort of (key, index) in shared
-//                   memory gives the exact time order; scatter coordinates;
-//   k_batch_relate  every (set, 64-row, 2048-column) block of every bitset;
+//   k_batch_rank    one CTA per set: exact ranks of the keys by a bucket
+//                   count in shared memory give the time order; scatter
+//                   coordinates;
+//   k_batch_relate  every relate chunk (32 words of a 64-row tile, from its
+//                   diagonal word) of every bitset, one launch per geometry;
+//   k_batch_mirror  the lower triangle of every bitset, the transpose of the
+//                   upper one (the past rows);
 //   count           the multi-set POPC kernel, or expand + multi-set tcgen05
 //                   kernel: one persistent grid over the tiles of all sets,
 //                   largest sets first (longest-processing-time order);
