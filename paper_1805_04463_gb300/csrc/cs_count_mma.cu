@@ -100,7 +100,8 @@ constexpr uint8_t kOne = 0x38;           // 1.0 in FP8 E4M3
 // atomics).  Both stay at their largest joint size: a seventh FP4 stage with
 // 256 shared bins (96% of the counts of a 2^17 order then global atomics,
 // against 52% with 8192 bins) made the count 24% slower at n = 2^17 and
-// 2.9x slower at 2^15, the L2 atomics competing with the operand loads.
+// 2.9x slower at 2^15, the L2 atomics competing with the operand loads
+// (the multi-set form below, whose tiles are short, takes five stages).
 struct FmtF8 {
     static constexpr int kKE = kBK;      // K elements per stage
     static constexpr int kAcc = 2;
@@ -118,9 +119,13 @@ struct FmtF4Layers : FmtF4 {
 };
 // The multi-set form: its sets are small (a batch holds n <= 8192, a count
 // job any n), so it keeps the branch-free histogram of the FP8 kernel for
-// sets whose histogram fits in shared memory.
+// sets whose histogram fits in shared memory.  Its tiles hold few K-blocks
+// (4-6 at n = 4096), and five stages suit them best: a 768-set batch of
+// n ~ 2048-4096 replayed in 8.43 ms with 5, 8.45 with 4, 8.59 with 6,
+// 8.80 with 3 and 9.27 with 2.
 struct FmtF4Multi : FmtF4 {
     static constexpr bool kSmallSet = true;
+    static constexpr int kStages = 5;
 };
 // Bytes of one operand stage in each CTA, and the dynamic shared memory of
 // a kernel on format Fmt (the base is rounded up to 1024 inside).

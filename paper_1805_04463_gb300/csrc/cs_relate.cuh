@@ -527,11 +527,28 @@ __device__ __forceinline__ void mirror_block(uint64_t* __restrict__ bits, int64_
     const int64_t A0 = A8 * kMirTiles, B0 = B8 * kMirTiles;
     // anything to do here? (uniform: some tile with B < A < tiles)
     if (A0 >= tiles || B0 >= (A0 + kMirTiles - 1 < tiles ? A0 + kMirTiles - 1 : tiles - 1)) return;
-    // source rows 64 B0 .. + 512, source words A0 .. A0 + 8
-    for (int t = threadIdx.x; t < kMirRows * kMirTiles; t += blockDim.x) {
-        const int r = t / kMirTiles, w = t % kMirTiles;
-        const int64_t row = 64 * B0 + r, word = A0 + w;
-        sm[r][w] = (row < n && word < tiles) ? bits[row * row_words + word] : 0ull;
+    // source rows 64 B0 .. + 512, source words A0 .. A0 + 8, as 16-byte word
+    // pairs (A0 is even and rows are 16-word multiples), every load of a
+    // thread issued before the first shared-memory store: with one load in
+    // flight per thread the kernel waited on memory latency at a quarter of
+    // the HBM rate.  The second word of a pair at the last valid word is a
+    // padding word of the row (loaded, then replaced by 0).
+    constexpr int kPairs = kMirRows * kMirTiles / 2, kPerThread = kPairs / kRelThreads;
+    static_assert(kPairs % kRelThreads == 0 && kMirTiles % 2 == 0, "word pairs split evenly over the block");
+    ulonglong2 v[kPerThread];
+#pragma unroll
+    for (int s = 0; s < kPerThread; ++s) {
+        const int t = threadIdx.x + s * kRelThreads;
+        const int64_t row = 64 * B0 + t / (kMirTiles / 2), word = A0 + 2 * (t % (kMirTiles / 2));
+        v[s] = (row < n && word < tiles) ? __ldg(reinterpret_cast<const ulonglong2*>(bits + row * row_words + word))
+                                         : make_ulonglong2(0ull, 0ull);
+    }
+#pragma unroll
+    for (int s = 0; s < kPerThread; ++s) {
+        const int t = threadIdx.x + s * kRelThreads;
+        const int r = t / (kMirTiles / 2), w = 2 * (t % (kMirTiles / 2));
+        sm[r][w] = v[s].x;
+        sm[r][w + 1] = A0 + w + 1 < tiles ? v[s].y : 0ull;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
