@@ -492,8 +492,8 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
 // source words land in shared memory with 64-byte reads, each warp
 // transposes its output row tile's 8 tiles in registers (six butterfly
 // stages, five of them across lanes) and writes its row tile's words
-// below the diagonal, 64 contiguous bytes per output row off the diagonal
-// super-tiles.
+// below the diagonal back through shared memory, 64 contiguous bytes per
+// output row off the diagonal super-tiles, four lanes to a row.
 constexpr int kMirTiles = 8;                    // tiles per super-tile side
 constexpr int kMirRows = 64 * kMirTiles;        // 512 source / output rows
 
@@ -553,8 +553,9 @@ __device__ __forceinline__ void mirror_block(uint64_t* __restrict__ bits, int64_
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t A = A0 + warp;  // this warp's output row tile
-    if (A < tiles && B0 < A) {
-        uint64_t ox[kMirTiles], oy[kMirTiles];
+    const bool active = A < tiles && B0 < A;  // warp-uniform
+    uint64_t ox[kMirTiles], oy[kMirTiles];
+    if (active) {
 #pragma unroll
         for (int qb = 0; qb < kMirTiles; ++qb) {
             uint64_t x = sm[64 * qb + lane][warp], y = sm[64 * qb + lane + 32][warp];
@@ -562,23 +563,32 @@ __device__ __forceinline__ void mirror_block(uint64_t* __restrict__ bits, int64_
             ox[qb] = x;
             oy[qb] = y;
         }
-        const int64_t rx = 64 * A + lane, ry = rx + 32;
-        // words B0 + qb < A only (all inside the row: B < A < tiles); pairs
-        // of them as 16-byte stores
-        uint64_t* px = bits + rx * row_words + B0;
-        uint64_t* py = bits + ry * row_words + B0;
+    }
+    __syncthreads();  // every warp has read its column of the source words
+    if (active) {
+        // The warp's 64 output rows go through its own 64 rows of shared
+        // memory, then out with four lanes per row (16 bytes each): every
+        // row's 64 bytes leave as two whole 32-byte sectors.  Words B0 + w
+        // < A only (all inside the row: B < A < tiles).
+        uint64_t (*out)[kMirTiles + 1] = sm + 64 * warp;
 #pragma unroll
-        for (int h = 0; h < kMirTiles / 2; ++h) {
-            if (B0 + 2 * h + 1 < A) {
-                if (rx < n)
-                    reinterpret_cast<uint4*>(px)[h] = make_uint4(uint32_t(ox[2 * h]), uint32_t(ox[2 * h] >> 32),
-                                                                 uint32_t(ox[2 * h + 1]), uint32_t(ox[2 * h + 1] >> 32));
-                if (ry < n)
-                    reinterpret_cast<uint4*>(py)[h] = make_uint4(uint32_t(oy[2 * h]), uint32_t(oy[2 * h] >> 32),
-                                                                 uint32_t(oy[2 * h + 1]), uint32_t(oy[2 * h + 1] >> 32));
-            } else if (B0 + 2 * h < A) {
-                if (rx < n) px[2 * h] = ox[2 * h];
-                if (ry < n) py[2 * h] = oy[2 * h];
+        for (int qb = 0; qb < kMirTiles; ++qb) {
+            out[lane][qb] = ox[qb];
+            out[lane + 32][qb] = oy[qb];
+        }
+        __syncwarp();
+        const int w = 2 * (lane & 3);  // this lane's word pair
+        static_assert(kMirTiles == 8, "four lanes cover a row's eight words");
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int r = 8 * s + (lane >> 2);
+            const int64_t row = 64 * A + r;
+            if (row < n && B0 + w < A) {
+                uint64_t* dst = bits + row * row_words + B0 + w;
+                if (B0 + w + 1 < A)
+                    *reinterpret_cast<ulonglong2*>(dst) = make_ulonglong2(out[r][w], out[r][w + 1]);
+                else
+                    *dst = out[r][w];
             }
         }
     }
