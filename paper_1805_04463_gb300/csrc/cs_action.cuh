@@ -100,8 +100,14 @@ __host__ __device__ inline int64_t smear_cutoff(int dim, double eps, double R, i
     const double lhs0 = log(4.0 * fmax(R, 1.0) * C) + 34.6;  // ln(4 R C) - ln(1e-15)
     double k = fmax(deg, ceil(m / eps));
     // Fixed point of k = deg + (lhs0 + m ln(1 + k eps)) / (-ln q), approached
-    // from below; the map's slope there is about m / (1 + k eps) < 0.1.
-    for (int it = 0; it < 24; ++it) k = fmax(k, deg + (lhs0 + m * log1p(k * eps)) / -lq);
+    // from below; the map's slope there is about m / (1 + k eps) < 0.1.  The
+    // iterates never decrease, and once one repeats every later one does, so
+    // stopping there gives the same k as all 24 steps.
+    for (int it = 0; it < 24; ++it) {
+        const double kn = fmax(k, deg + (lhs0 + m * log1p(k * eps)) / -lq);
+        if (kn == k) break;
+        k = kn;
+    }
     k = ceil(k) + 8.0;
     return k < double(len) ? int64_t(k) : len;
 }

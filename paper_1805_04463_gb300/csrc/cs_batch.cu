@@ -262,9 +262,25 @@ struct CoefArgs {
     int64_t seg[kDimSlots * kMaxEps + 1];  // prefix sums of kcap in (slot, eps) order
 };
 
-__global__ void __launch_bounds__(256) k_batch_coef(dd* __restrict__ coef, CoefArgs c, EpsArgs eps) {
+// The same launch finds each (set, eps) cutoff once (kends), after the
+// table entries: a fixed-point iteration of about 1500 FP64 operations, too
+// costly to repeat in every thread of the action kernel.
+__global__ void __launch_bounds__(32) k_batch_coef(dd* __restrict__ coef, CoefArgs c, EpsArgs eps,
+                                                    const BatchSet* __restrict__ sets, int nsets,
+                                                    int64_t* __restrict__ kends) {
     const int64_t total = c.seg[kDimSlots * kMaxEps];
-    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t all = total + int64_t(nsets) * eps.n;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < all; t += int64_t(gridDim.x) * blockDim.x) {
+        if (t >= total) {
+            const int set = int((t - total) / eps.n), e = int((t - total) % eps.n);
+            const double ep = eps.v[e];
+            const BatchSet& b = sets[set];
+            const int64_t len = b.n > 1 ? b.n - 1 : 1;
+            const int64_t kc = is_local(ep) ? 0 : smear_cutoff(b.dim, ep, 0.5 * double(b.n) * double(b.n), len);
+            const int64_t cap = c.kcap[b.dim - 2][e];
+            kends[int64_t(set) * kMaxEps + e] = kc < cap ? kc : cap;  // never beyond the table
+            continue;
+        }
         int g = 0;
         while (c.seg[g + 1] <= t) ++g;  // at most 48 segments
         const int slot = g / kMaxEps, e = g % kMaxEps, dim = slot + 2;
@@ -276,59 +292,55 @@ __global__ void __launch_bounds__(256) k_batch_coef(dd* __restrict__ coef, CoefA
     }
 }
 
-// One CTA per set: bracket, local and smeared actions; the smeared sums take
-// their coefficients from the shared table.
+// One CTA per (set, eps): the set's bracket (written by its eps-0 CTA) and
+// one local or smeared action; the smeared sums take their coefficients from
+// the shared table.  Each sum keeps the per-thread order and the reduction
+// tree of the single-set action, so both give the same bits; a CTA per set
+// walking its eps values one after another left the FP64 pipe waiting on
+// the sums' dependency chains (0.29 ms for 768 sets and three smeared eps).
 __global__ void __launch_bounds__(kActThreads) k_batch_action(const BatchSet* __restrict__ sets,
                                                               const int64_t* __restrict__ hist_base, EpsArgs eps,
                                                               const dd* __restrict__ coef, CoefArgs c,
+                                                              const int64_t* __restrict__ kends,
                                                               double* __restrict__ actions,
                                                               int64_t* __restrict__ brackets) {
     __shared__ dd red[kActThreads];
-    __shared__ int64_t kends[kMaxEps];
-    const BatchSet& b = sets[blockIdx.x];
+    const int per = eps.n > 0 ? eps.n : 1;  // no eps: one CTA per set for the bracket
+    const int set = blockIdx.x / per, e = blockIdx.x % per;
+    const BatchSet& b = sets[set];
     const int dim = b.dim, slot = dim - 2;
     const int64_t n = b.n, len = n > 1 ? n - 1 : 1;
-    // cutoffs of this set, one thread per eps (the first barrier below
-    // publishes them); never beyond the table
-    if (threadIdx.x < eps.n) {
-        const double ep = eps.v[threadIdx.x];
-        const int64_t k = is_local(ep) ? 0 : smear_cutoff(dim, ep, 0.5 * double(n) * double(n), len);
-        kends[threadIdx.x] = k < c.kcap[slot][threadIdx.x] ? k : c.kcap[slot][threadIdx.x];
-    }
-    __syncthreads();
     const int64_t* hist = hist_base + b.hist_off;
     const int tid = threadIdx.x;
     int64_t h4[4] = {0, 0, 0, 0};
     for (int k = 0; k < 4 && k < len; ++k) h4[k] = hist[k];
     const int64_t br = bracket_of(dim, n, h4);
-    if (tid == 0 && brackets) brackets[blockIdx.x] = br;
-    for (int e = 0; e < eps.n; ++e) {
-        const double ep = eps.v[e];
-        if (is_local(ep)) {
-            if (tid == 0 && actions) {
-                const dd s = local_action(dim, br);
-                actions[blockIdx.x * eps.n + e] = s.hi + s.lo;
-            }
-            continue;
-        }
-        const dd* f = coef + c.base[slot] + e * c.stride[slot];
-        const int64_t kend = kends[e];
-        dd sum = dd_from(0.0);
-        for (int64_t k = tid; k < kend; k += kActThreads) {
-            const int64_t hk = hist[k];
-            if (hk != 0) sum = dd_add(sum, dd_mul(dd_from_i64(hk), f[k]));
-        }
-        red[tid] = sum;
-        __syncthreads();
-        for (int s = kActThreads / 2; s > 0; s >>= 1) {
-            if (tid < s) red[tid] = dd_add(red[tid], red[tid + s]);
-            __syncthreads();
-        }
+    if (tid == 0 && e == 0 && brackets) brackets[set] = br;
+    if (e >= eps.n) return;
+    const double ep = eps.v[e];
+    if (is_local(ep)) {  // uniform across the CTA
         if (tid == 0 && actions) {
-            const dd s = smeared_action(dim, n, ep, red[0]);
-            actions[blockIdx.x * eps.n + e] = s.hi + s.lo;
+            const dd s = local_action(dim, br);
+            actions[int64_t(set) * eps.n + e] = s.hi + s.lo;
         }
+        return;
+    }
+    const int64_t kend = kends[int64_t(set) * kMaxEps + e];  // k_batch_coef's cutoff
+    const dd* f = coef + c.base[slot] + e * c.stride[slot];
+    dd sum = dd_from(0.0);
+    for (int64_t k = tid; k < kend; k += kActThreads) {
+        const int64_t hk = hist[k];
+        if (hk != 0) sum = dd_add(sum, dd_mul(dd_from_i64(hk), f[k]));
+    }
+    red[tid] = sum;
+    __syncthreads();
+    for (int s = kActThreads / 2; s > 0; s >>= 1) {
+        if (tid < s) red[tid] = dd_add(red[tid], red[tid + s]);
         __syncthreads();
+    }
+    if (tid == 0 && actions) {
+        const dd s = smeared_action(dim, n, ep, red[0]);
+        actions[int64_t(set) * eps.n + e] = s.hi + s.lo;
     }
 }
 
@@ -358,6 +370,7 @@ struct cs_batch {
     int max_pow2 = 1;
     const uint64_t* ds_thr = nullptr;  // de Sitter thresholds, when a set needs them
     dd* coef = nullptr;                 // smeared-sum coefficient tables
+    int64_t* kends = nullptr;           // per (set, eps): smeared-sum cutoff [set * kMaxEps + e]
     int64_t nmax[kDimSlots] = {0, 0, 0};  // largest n per dimension slot (0: absent)
     int64_t coef_base[kDimSlots] = {0, 0, 0};
     // cs_batch_poll: each launch copies the status word here (pinned) and
@@ -373,7 +386,7 @@ struct cs_batch {
 namespace {
 
 struct Layout {
-    size_t sets, entries, rtab, etab, mtab, coef, total;
+    size_t sets, entries, rtab, etab, mtab, coef, kends, total;
     std::vector<size_t> coords, bits, key0, key1, raw, op0, op1;
 };
 
@@ -420,6 +433,7 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
         m = sets[s].n > m ? sets[s].n : m;
     }
     L.coef = take(size_t(nmax[0] + nmax[1] + nmax[2]) * kMaxEps * sizeof(dd));  // coefficient tables
+    L.kends = take(size_t(n_sets) * kMaxEps * 8);                                 // smeared-sum cutoffs
     for (int s = 0; s < n_sets; ++s) {
         const int64_t n = sets[s].n;
         const int dim = cs_dim(sets[s].kind);
@@ -571,6 +585,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     h->max_pow2 = max_pow2;
     h->ds_thr = ds_thr;
     h->coef = reinterpret_cast<dd*>(ws + L.coef);
+    h->kends = reinterpret_cast<int64_t*>(ws + L.kends);
     for (int s = 0; s < n_sets; ++s) {
         int64_t& m = h->nmax[bs[s].dim - 2];
         m = bs[s].n > m ? bs[s].n : m;
@@ -684,12 +699,14 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
         }
         c.seg[kDimSlots * kMaxEps] = at;
         if (at > 0) {
-            int64_t g = (at + 255) / 256;
-            if (g > int64_t(sms) * 4) g = int64_t(sms) * 4;
-            k_batch_coef<<<unsigned(g), 256, 0, st>>>(b->coef, c, a);
+            // one warp per block: the FP64 work (table entries, then the
+            // cutoffs) spreads over every SM's FP64 pipe
+            int64_t g = (at + int64_t(b->nsets) * a.n + 31) / 32;
+            if (g > int64_t(sms) * 16) g = int64_t(sms) * 16;
+            k_batch_coef<<<unsigned(g), 32, 0, st>>>(b->coef, c, a, b->sets_dev, b->nsets, b->kends);
         }
-        k_batch_action<<<unsigned(b->nsets), kActThreads, 0, st>>>(b->sets_dev, hist_dev, a, b->coef, c,
-                                                                  actions_dev, brackets_dev);
+        k_batch_action<<<unsigned(b->nsets * (a.n > 0 ? a.n : 1)), kActThreads, 0, st>>>(
+            b->sets_dev, hist_dev, a, b->coef, c, b->kends, actions_dev, brackets_dev);
         if (cudaGetLastError() != cudaSuccess) return CS_ECUDA;
     }
     // For cs_batch_poll: the status word to the plan's pinned copy, then the

@@ -69,6 +69,20 @@ def test_batch_equals_single_set_calls(cs, path):
         assert torch.equal(buf.actions[:len(EPS)].cpu(), b.actions[s].cpu())
 
 
+def test_brackets_without_eps(cs, oracle):
+    """A batch with no eps still writes every set's exact bracket (one CTA per set)."""
+    import torch
+    sets = [(1, 900 + 41 * s, 700 + s) for s in range(3)] + [(2, 600, 710), (0, 1024, 711)]
+    b = cs.Batch(sets, path=3, n_eps=0)
+    b.launch(())
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    brs = b.brackets.cpu().numpy()
+    for s, (kind, n, seed) in enumerate(sets):
+        want = oracle.interval_abundance(oracle.causal_matrix(kind, oracle.sprinkle(kind, n, seed)))
+        assert brs[s] == oracle.action(oracle.dim(kind), n, want, 0.0)[1], s
+
+
 @pytest.mark.parametrize("path", [0, 3], ids=["auto", "mma4"])
 def test_batch_graph_replay(cs, oracle, path):
     import torch
