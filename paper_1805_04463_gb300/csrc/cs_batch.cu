@@ -53,6 +53,8 @@ struct BatchSet {
     int64_t mblock_begin;  // first mirror block (lower part by symmetry)
     int64_t mir_side;      // mirror super-tiles per side
     int64_t hist_off;      // offset of this set's histogram in the batch histogram
+    ConeTable* ctab;       // light-cone kinds: one column table per column tile (else null)
+    int64_t tile_begin;    // first column tile of this set in the concatenated tile range
 };
 
 constexpr int kRankThreads = 1024;
@@ -192,6 +194,21 @@ __global__ void __launch_bounds__(kRankThreads) k_batch_rank(const BatchSet* __r
     }
 }
 
+// Column tables of the light-cone sets (after k_batch_rank has written the
+// time-sorted coordinates), one warp per column tile of the concatenated
+// tile range, the set found by a binary search.
+__global__ void __launch_bounds__(256) k_batch_ctab(const BatchSet* __restrict__ sets, int nsets, int64_t tiles) {
+    const int64_t g = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;  // warp-uniform
+    if (g >= tiles) return;
+    int lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sets[mid].tile_begin <= g) lo = mid; else hi = mid - 1;
+    }
+    const BatchSet& b = sets[lo];
+    if (b.ctab) build_cone_table(b.coords, b.n, g - b.tile_begin, b.kind == CS_2D_ORDER, b.ctab + (g - b.tile_begin));
+}
+
 // Relate chunks.  Row tile rb of a set with V valid words needs words
 // [rb, V) (the words before it are mirrored); they are covered by
 // ceil((V - rb) / 32) chunks of 32 words starting at the diagonal word, so
@@ -217,27 +234,45 @@ __host__ __device__ __forceinline__ int batch_geom(int kind) {
 // instance per geometry, each launched over all chunks (the other
 // geometries' blocks return at once), so that every geometry's code gets
 // the registers it needs for itself.
+// Relate block `local` of a set: its row tile rb, first word w0 and, for a
+// row tile's last chunk, the first padding word to zero (else -1).
+__device__ __forceinline__ void decode_rblock(const BatchSet& b, int64_t local, int64_t& rb, int64_t& w0,
+                                              int64_t& zero_from) {
+    const int64_t V = b.vwords, total = chunk_sum(V);
+    int64_t lo = 0, hi = V - 1;  // last row tile whose first chunk is at or before `local`
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (total - chunk_sum(V - mid) <= local) lo = mid; else hi = mid - 1;
+    }
+    rb = lo;
+    w0 = rb + (local - (total - chunk_sum(V - rb))) * kRelWordsPerBlock;
+    zero_from = w0 + kRelWordsPerBlock >= V ? w0 + kRelWordsPerBlock : -1;
+}
+
 template <int G>
 __global__ void __launch_bounds__(kRelThreads, 5) k_batch_relate(const BatchSet* __restrict__ sets,
                                                               const int32_t* __restrict__ rblock_set) {
     __shared__ __align__(16) int32_t sc[kStageInts];
-    {
-        const int64_t blk = blockIdx.x;
-        const BatchSet& b = sets[rblock_set[blk]];
-        if (batch_geom(b.kind) != G) return;
-        const int64_t local = blk - b.rblock_begin;
-        const int64_t V = b.vwords, total = chunk_sum(V);
-        int64_t lo = 0, hi = V - 1;  // last row tile whose first chunk is at or before `local`
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (total - chunk_sum(V - mid) <= local) lo = mid; else hi = mid - 1;
-        }
-        const int64_t rb = lo;
-        const int64_t w0 = rb + (local - (total - chunk_sum(V - rb))) * kRelWordsPerBlock;
-        const int64_t zero_from = w0 + kRelWordsPerBlock >= V ? w0 + kRelWordsPerBlock : -1;
-        relate_block<G>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, G == kGeomLightCone && b.kind == CS_2D_ORDER,
-                        zero_from);
-    }
+    const BatchSet& b = sets[rblock_set[blockIdx.x]];
+    if (batch_geom(b.kind) != G) return;
+    int64_t rb, w0, zero_from;
+    decode_rblock(b, blockIdx.x - b.rblock_begin, rb, w0, zero_from);
+    relate_block<G>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, G == kGeomLightCone && b.kind == CS_2D_ORDER,
+                    zero_from);
+}
+
+// The light-cone kinds, from the column tables k_batch_rank built (one
+// look-up per word instead of 64 cone tests).
+__global__ void __launch_bounds__(kRelThreads, 4) k_batch_relate_cone(const BatchSet* __restrict__ sets,
+                                                                   const int32_t* __restrict__ rblock_set,
+                                                                   WsHeader* hdr) {
+    extern __shared__ __align__(16) uint8_t smem_rel[];
+    const BatchSet& b = sets[rblock_set[blockIdx.x]];
+    if (batch_geom(b.kind) != kGeomLightCone) return;
+    int64_t rb, w0, zero_from;
+    decode_rblock(b, blockIdx.x - b.rblock_begin, rb, w0, zero_from);
+    relate_block_tables(b.coords, b.n, b.bits, b.row_words, rb, w0, b.ctab, smem_rel, b.kind == CS_2D_ORDER,
+                        zero_from, hdr);
 }
 
 // One block per mirror super-tile of one set (the lower part of its bitset
@@ -344,7 +379,8 @@ __global__ void __launch_bounds__(kActThreads) k_batch_action(const BatchSet* __
     }
 }
 
-std::atomic<bool> g_rank_attr[64];  // per device: the sort kernel's shared-memory attribute is set
+std::atomic<bool> g_rank_attr[64];  // per device: the rank kernel's shared-memory attribute is set
+std::atomic<bool> g_cone_attr[64];  // per device: the light-cone relate's shared-memory attribute is set
 
 }  // namespace
 
@@ -366,6 +402,7 @@ struct cs_batch {
     int32_t* etab = nullptr;  // expansion chunk -> count-table entry
     int32_t* mtab = nullptr;  // mirror block -> set
     int64_t total_mblocks = 0;
+    int64_t total_tiles = 0;  // column tiles of all sets (k_batch_ctab's warps)
     unsigned geoms = 0;  // bit G: some set relates with geometry G
     int max_pow2 = 1;
     const uint64_t* ds_thr = nullptr;  // de Sitter thresholds, when a set needs them
@@ -387,7 +424,7 @@ namespace {
 
 struct Layout {
     size_t sets, entries, rtab, etab, mtab, coef, kends, total;
-    std::vector<size_t> coords, bits, key0, key1, raw, op0, op1;
+    std::vector<size_t> coords, bits, key0, key1, raw, ctab, op0, op1;
 };
 
 bool batch_valid(const cs_set_desc* sets, int n_sets) {
@@ -442,6 +479,8 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
         L.key0.push_back(take(size_t(n) * 8));
         L.key1.push_back(take(size_t(n) * 8));
         L.raw.push_back(take(size_t(n) * 16));
+        L.ctab.push_back(batch_geom(sets[s].kind) == kGeomLightCone ? take(size_t((n + 63) / 64) * sizeof(ConeTable))
+                                                                    : 0);
         if (tensor_path(path)) {
             off = align_up(off, 1024);
             L.op0.push_back(take(mma_operand_bytes(n, path == CS_PATH_MMA4, 0)));
@@ -488,7 +527,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     uint8_t* ws = static_cast<uint8_t*>(workspace_dev);
 
     std::vector<BatchSet> bs(static_cast<size_t>(n_sets));
-    int64_t elem = 0, rblk = 0, mblk = 0, hoff = 0;
+    int64_t elem = 0, rblk = 0, mblk = 0, hoff = 0, tiles = 0;
     int max_pow2 = 1;
     for (int s = 0; s < n_sets; ++s) {
         BatchSet& b = bs[s];
@@ -502,6 +541,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
         b.key0 = reinterpret_cast<uint64_t*>(ws + L.key0[s]);
         b.key1 = reinterpret_cast<uint64_t*>(ws + L.key1[s]);
         b.raw = reinterpret_cast<int32_t*>(ws + L.raw[s]);
+        b.ctab = L.ctab[s] ? reinterpret_cast<ConeTable*>(ws + L.ctab[s]) : nullptr;
         b.elem_begin = elem;
         elem += b.n;
         b.vwords = (b.n + 63) / 64;
@@ -509,6 +549,8 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
         rblk += chunk_sum(b.vwords);
         b.mir_side = ((b.n + 63) / 64 + kMirTiles - 1) / kMirTiles;
         b.mblock_begin = mblk;
+        b.tile_begin = tiles;
+        tiles += b.vwords;
         mblk += b.mir_side * b.mir_side;
         b.hist_off = hoff;
         hoff += cs_hist_len(b.n);
@@ -580,6 +622,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     h->rtab = reinterpret_cast<int32_t*>(ws + L.rtab);
     h->mtab = reinterpret_cast<int32_t*>(ws + L.mtab);
     h->total_mblocks = mblk;
+    h->total_tiles = tiles;
     h->etab = reinterpret_cast<int32_t*>(ws + L.etab);
     h->total_hist = hoff;
     h->max_pow2 = max_pow2;
@@ -652,11 +695,21 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
             return CS_ECUDA;
         g_rank_attr[dev] = true;
     }
+    if ((b->geoms & (1u << kGeomLightCone)) && dev >= 0 && dev < 64 && !g_cone_attr[dev]) {
+        if (cudaFuncSetAttribute(k_batch_relate_cone, cudaFuncAttributeMaxDynamicSharedMemorySize, kConeTableSmem) !=
+            cudaSuccess)
+            return CS_ECUDA;
+        g_cone_attr[dev] = true;
+    }
     k_batch_rank<<<unsigned(b->nsets), kRankThreads, rank_smem, st>>>(b->sets_dev);
+    if (b->geoms & (1u << kGeomLightCone))
+        k_batch_ctab<<<unsigned((b->total_tiles * 32 + 255) / 256), 256, 0, st>>>(b->sets_dev, b->nsets,
+                                                                                 b->total_tiles);
 
     if (b->total_rblocks > int64_t(0x7fffffff)) return CS_EINVAL;
     if (b->geoms & (1u << kGeomLightCone))
-        k_batch_relate<kGeomLightCone><<<unsigned(b->total_rblocks), kRelThreads, 0, st>>>(b->sets_dev, b->rtab);
+        k_batch_relate_cone<<<unsigned(b->total_rblocks), kRelThreads, kConeTableSmem, st>>>(b->sets_dev, b->rtab,
+                                                                                              b->hdr);
     if (b->geoms & (1u << kGeom3))
         k_batch_relate<kGeom3><<<unsigned(b->total_rblocks), kRelThreads, 0, st>>>(b->sets_dev, b->rtab);
     if (b->geoms & (1u << kGeom4))

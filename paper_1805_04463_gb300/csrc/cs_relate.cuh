@@ -484,6 +484,181 @@ __device__ __forceinline__ void relate_block(const int32_t* __restrict__ coords,
     }
 }
 
+// ------------------------------------------------ light-cone column tables
+//
+// In the light-cone kinds a row i and a column tile C wholly after i's row
+// tile relate exactly where u_j > u_i and v_j > v_i (the future cone; labels
+// are in time order).  Sorting the tile's 64 values of one coordinate turns
+// "the columns whose value exceeds y" into a suffix of the sorted order, so
+// with the suffix masks precomputed the whole 64-bit word is
+//   above_u[#{p : us[p] <= u_i}] & above_v[#{p : vs[p] <= v_i}],
+// two binary searches of six steps instead of 64 tests (for a random 2D
+// order, whose u increases with the label, the v term alone).  Columns at or
+// beyond n hold -1, which exceeds no coordinate (all lie in [0, 2^31)).
+struct alignas(16) ConeTable {
+    int32_t xs[2][64];      // u and v of the tile's columns, each sorted ascending
+    uint64_t above[2][66];  // above[x][m], m <= 64: the columns at sorted positions >= m of coordinate x
+    uint32_t pad[4];        // 1584 bytes: consecutive tables start at different 16-byte offsets of
+};                          // a 128-byte line, so the lanes' bucket loads spread over the banks
+static_assert(sizeof(ConeTable) == 1584, "cone table layout");
+
+// Table of column tile C, one full warp.  The 64 keys (value + 1) << 6 |
+// column, two per lane (element lane + 32 h), go through a bitonic network
+// (partners at distance 32 inside the lane, the others by shuffles); after
+// it element e is the e-th smallest, and a suffix OR over the elements gives
+// the masks.  order2d: only the v table (its u is the label order).
+__device__ __forceinline__ void build_cone_table(const int32_t* __restrict__ coords, int64_t n, int64_t C,
+                                                 bool order2d, ConeTable* __restrict__ t) {
+    const int lane = threadIdx.x & 31;
+    for (int x = order2d ? 1 : 0; x < 2; ++x) {
+        uint64_t k[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t col = 64 * C + lane + 32 * h;
+            const int32_t v = col < n ? coords[x * n + col] : -1;
+            k[h] = (uint64_t(uint32_t(v + 1)) << 6) | uint64_t(lane + 32 * h);
+        }
+#pragma unroll
+        for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+            for (int j = size >> 1; j > 0; j >>= 1) {
+                if (j == 32) {  // size 64: ascending, partner e + 32 in the same lane
+                    const uint64_t lo = k[0] < k[1] ? k[0] : k[1], hi = k[0] < k[1] ? k[1] : k[0];
+                    k[0] = lo;
+                    k[1] = hi;
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int e = lane + 32 * h;
+                        const uint64_t p = __shfl_xor_sync(0xffffffffu, k[h], j);
+                        const bool keep_min = ((e & j) == 0) == ((e & size) == 0);
+                        k[h] = keep_min ? (k[h] < p ? k[h] : p) : (k[h] < p ? p : k[h]);
+                    }
+                }
+            }
+        }
+        t->xs[x][lane] = int32_t(uint32_t(k[0] >> 6)) - 1;
+        t->xs[x][lane + 32] = int32_t(uint32_t(k[1] >> 6)) - 1;
+        uint64_t s0 = 1ull << (k[0] & 63), s1 = 1ull << (k[1] & 63);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t a = __shfl_down_sync(0xffffffffu, s0, o), b = __shfl_down_sync(0xffffffffu, s1, o);
+            if (lane + o < 32) {
+                s0 |= a;
+                s1 |= b;
+            }
+        }
+        s0 |= __shfl_sync(0xffffffffu, s1, 0);  // every element of the upper half follows the lower half
+        t->above[x][lane] = s0;
+        t->above[x][lane + 32] = s1;
+        if (lane == 0) t->above[x][64] = 0ull;
+    }
+}
+
+// #{p : xs[p] <= y} over 64 ascending values, and the mask of the columns
+// above y.  s[m] = xs[8 m + 7] (m < 7) are the bucket splitters, kept in
+// registers: the buckets wholly at or below y are counted by seven compares,
+// then the one 32-byte bucket that may straddle y is loaded and counted.
+__device__ __forceinline__ uint64_t cone_above(const int32_t* __restrict__ xs, const uint64_t* __restrict__ above,
+                                               const int32_t (&s)[7], int32_t y) {
+    int c1 = 0;
+#pragma unroll
+    for (int m = 0; m < 7; ++m) c1 += s[m] <= y ? 1 : 0;
+    const int4 a = reinterpret_cast<const int4*>(xs)[2 * c1], b = reinterpret_cast<const int4*>(xs)[2 * c1 + 1];
+    const int c = 8 * c1 + (a.x <= y) + (a.y <= y) + (a.z <= y) + (a.w <= y) + (b.x <= y) + (b.y <= y) + (b.z <= y) +
+                  (b.w <= y);
+    return above[c];
+}
+
+// Bytes of dynamic shared memory of relate_block_tables: 32 tables, the own
+// tile's columns, the copy's mbarrier.
+constexpr int kConeTableSmem = kRelWordsPerBlock * int(sizeof(ConeTable)) + 128 * 4 + 16;
+
+// Rows [64 rb, 64 rb + 64) x words [w0, w0 + 32) (w0 >= rb) of a light-cone
+// set from its column tables (tables[C] for column tile C): the row tile's
+// own word rb by the exact symmetric test folded with ballots, every word
+// after it by the table look-ups, words at or past the last valid one zeroed
+// (and, with zero_from >= 0, the row's words [zero_from, row_words)).  The
+// block's tables arrive by one bulk copy.  smem: kConeTableSmem bytes,
+// 16-byte aligned.  All 256 threads.  Returns false (status recorded) if the
+// copy did not complete in time.
+__device__ __forceinline__ bool relate_block_tables(const int32_t* __restrict__ coords, int64_t n,
+                                                    uint64_t* __restrict__ bits, int64_t row_words, int64_t rb,
+                                                    int64_t w0, const ConeTable* __restrict__ tables, uint8_t* smem,
+                                                    bool order2d, int64_t zero_from, WsHeader* hdr) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kWarps = kRelThreads / 32;
+    ConeTable* st = reinterpret_cast<ConeTable*>(smem);
+    int32_t* own = reinterpret_cast<int32_t*>(smem + kRelWordsPerBlock * sizeof(ConeTable));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kRelWordsPerBlock * sizeof(ConeTable) + 128 * 4);
+    const int64_t V = (n + 63) >> 6;
+    const int64_t r0 = rb * 64, r1 = r0 + 64 < n ? r0 + 64 : n;
+    const int64_t wt = w0 > rb ? w0 : rb + 1;                                      // first table word
+    const int64_t we = w0 + kRelWordsPerBlock < V ? w0 + kRelWordsPerBlock : V;  // end of the valid words
+    const int nt = wt < we ? int(we - wt) : 0;
+    const bool has_own = rb >= w0;  // then rb == w0: chunks start at the diagonal word
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = uint32_t(nt) * uint32_t(sizeof(ConeTable));
+        mbar_arrive_expect_tx(bar, bytes);
+        if (bytes) bulk_load(st, tables + wt, bytes, bar);
+    }
+    if (has_own && threadIdx.x < 128) {
+        const int64_t col = r0 + (threadIdx.x & 63);
+        own[threadIdx.x] = col < n ? coords[(threadIdx.x >> 6) * n + col] : 0;
+    }
+    __syncthreads();
+    if (has_own) {
+        for (int64_t i = r0 + warp; i < r1; i += kWarps) {
+            const int32_t ui = coords[i], vi = coords[n + i];
+            bool b[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = lane + 32 * h;
+                const int64_t j = r0 + k;
+                const int32_t du = own[k] - ui, dv = own[64 + k] - vi;
+                b[h] = j < n && (order2d ? (j > i ? dv > 0 : (j < i && dv < 0))
+                                         : ((du ^ dv) >= 0 && du != 0 && dv != 0));
+            }
+            const uint64_t d = (uint64_t(__ballot_sync(0xffffffffu, b[1])) << 32) | __ballot_sync(0xffffffffu, b[0]);
+            if (lane == 0) bits[i * row_words + rb] = d;
+        }
+    }
+    if (!mbar_wait_bounded(bar, 0, hdr)) {
+        mbar_wait_bounded(bar, 0, hdr);  // the copy may still be writing: wait once more before leaving
+        return false;
+    }
+    // lane l: word w0 + l of each of the warp's rows, 32 consecutive words per row and warp
+    const int64_t w = w0 + lane;
+    const bool tab = w >= wt && w < we;
+    if (tab || (w >= V && w < row_words)) {
+        const ConeTable& T = st[tab ? int(w - wt) : 0];
+        int32_t su[7], sv[7];
+#pragma unroll
+        for (int m = 0; m < 7; ++m) {
+            sv[m] = tab ? T.xs[1][8 * m + 7] : 0;
+            su[m] = tab && !order2d ? T.xs[0][8 * m + 7] : 0;
+        }
+#pragma unroll 2
+        for (int64_t i = r0 + warp; i < r1; i += kWarps) {
+            uint64_t word = 0ull;
+            if (tab) {
+                word = cone_above(T.xs[1], T.above[1], sv, coords[n + i]);
+                if (!order2d) word &= cone_above(T.xs[0], T.above[0], su, coords[i]);
+            }
+            bits[i * row_words + w] = word;
+        }
+    }
+    if (zero_from >= 0)
+        for (int64_t i = r0 + warp; i < r1; i += kWarps)
+            for (int64_t z = zero_from + lane; z < row_words; z += 32) bits[i * row_words + z] = 0ull;
+    return true;
+}
+
 // ------------------------------------------------ the lower part by symmetry
 //
 // A 64 x 64 tile wholly below the diagonal (row tile A, word B < A) is the
