@@ -196,16 +196,12 @@ __global__ void __launch_bounds__(kRankThreads) k_batch_rank(const BatchSet* __r
 
 // Column tables of the light-cone sets (after k_batch_rank has written the
 // time-sorted coordinates), one warp per column tile of the concatenated
-// tile range, the set found by a binary search.
-__global__ void __launch_bounds__(256) k_batch_ctab(const BatchSet* __restrict__ sets, int nsets, int64_t tiles) {
+// tile range, the set read from a table built at create time.
+__global__ void __launch_bounds__(256) k_batch_ctab(const BatchSet* __restrict__ sets,
+                                                    const int32_t* __restrict__ tile_set, int64_t tiles) {
     const int64_t g = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;  // warp-uniform
     if (g >= tiles) return;
-    int lo = 0, hi = nsets - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (sets[mid].tile_begin <= g) lo = mid; else hi = mid - 1;
-    }
-    const BatchSet& b = sets[lo];
+    const BatchSet& b = sets[tile_set[g]];
     if (b.ctab) build_cone_table(b.coords, b.n, g - b.tile_begin, b.kind == CS_2D_ORDER, b.ctab + (g - b.tile_begin));
 }
 
@@ -403,6 +399,7 @@ struct cs_batch {
     int32_t* mtab = nullptr;  // mirror block -> set
     int64_t total_mblocks = 0;
     int64_t total_tiles = 0;  // column tiles of all sets (k_batch_ctab's warps)
+    int32_t* ttab = nullptr;  // column tile -> set
     unsigned geoms = 0;  // bit G: some set relates with geometry G
     int max_pow2 = 1;
     const uint64_t* ds_thr = nullptr;  // de Sitter thresholds, when a set needs them
@@ -423,7 +420,7 @@ struct cs_batch {
 namespace {
 
 struct Layout {
-    size_t sets, entries, rtab, etab, mtab, coef, kends, total;
+    size_t sets, entries, rtab, etab, mtab, ttab, coef, kends, total;
     std::vector<size_t> coords, bits, key0, key1, raw, ctab, op0, op1;
 };
 
@@ -453,10 +450,11 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
     L.sets = take(sizeof(BatchSet) * size_t(n_sets));
     off = align_up(off, 128);
     L.entries = take((tensor_path(path) ? sizeof(MmaSetEntry) : sizeof(PopcSetEntry)) * size_t(n_sets));
-    int64_t rblocks = 0, chunks = 0, mblocks = 0;
+    int64_t rblocks = 0, chunks = 0, mblocks = 0, tiles = 0;
     for (int s = 0; s < n_sets; ++s) {
         const int64_t n = sets[s].n;
         rblocks += chunk_sum((n + 63) / 64);
+        tiles += (n + 63) / 64;
         const int64_t side = ((n + 63) / 64 + kMirTiles - 1) / kMirTiles;
         mblocks += side * side;
         if (tensor_path(path)) chunks += mma_expand_chunks(n);
@@ -464,6 +462,7 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
     L.rtab = take(size_t(rblocks) * 4);  // relate block -> set
     L.etab = take(size_t(chunks) * 4);   // expansion chunk -> set
     L.mtab = take(size_t(mblocks) * 4);  // mirror block -> set
+    L.ttab = take(size_t(tiles) * 4);    // column tile -> set
     int64_t nmax[kDimSlots] = {0, 0, 0};
     for (int s = 0; s < n_sets; ++s) {
         int64_t& m = nmax[cs_dim(sets[s].kind) - 2];
@@ -561,7 +560,10 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bs[a].n > bs[b].n; });
     int64_t items = 0, chunks = 0;
-    std::vector<int32_t> rtab(static_cast<size_t>(rblk)), etab, mtab(static_cast<size_t>(mblk));
+    std::vector<int32_t> rtab(static_cast<size_t>(rblk)), etab, mtab(static_cast<size_t>(mblk)),
+        ttab(static_cast<size_t>(tiles));
+    for (int s = 0; s < n_sets; ++s)
+        std::fill(ttab.begin() + bs[s].tile_begin, ttab.begin() + bs[s].tile_begin + bs[s].vwords, int32_t(s));
     for (int s = 0; s < n_sets; ++s)
         std::fill(mtab.begin() + bs[s].mblock_begin, mtab.begin() + bs[s].mblock_begin + bs[s].mir_side * bs[s].mir_side,
                   int32_t(s));
@@ -623,6 +625,7 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     h->mtab = reinterpret_cast<int32_t*>(ws + L.mtab);
     h->total_mblocks = mblk;
     h->total_tiles = tiles;
+    h->ttab = reinterpret_cast<int32_t*>(ws + L.ttab);
     h->etab = reinterpret_cast<int32_t*>(ws + L.etab);
     h->total_hist = hoff;
     h->max_pow2 = max_pow2;
@@ -643,6 +646,8 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
         e = cudaMemcpyAsync(h->rtab, rtab.data(), rtab.size() * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !mtab.empty())
         e = cudaMemcpyAsync(h->mtab, mtab.data(), mtab.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !ttab.empty())
+        e = cudaMemcpyAsync(h->ttab, ttab.data(), ttab.size() * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !etab.empty())
         e = cudaMemcpyAsync(h->etab, etab.data(), etab.size() * 4, cudaMemcpyHostToDevice, st);
     if (tensor_path(p)) {
@@ -703,7 +708,7 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
     }
     k_batch_rank<<<unsigned(b->nsets), kRankThreads, rank_smem, st>>>(b->sets_dev);
     if (b->geoms & (1u << kGeomLightCone))
-        k_batch_ctab<<<unsigned((b->total_tiles * 32 + 255) / 256), 256, 0, st>>>(b->sets_dev, b->nsets,
+        k_batch_ctab<<<unsigned((b->total_tiles * 32 + 255) / 256), 256, 0, st>>>(b->sets_dev, b->ttab,
                                                                                  b->total_tiles);
 
     if (b->total_rblocks > int64_t(0x7fffffff)) return CS_EINVAL;
