@@ -224,12 +224,6 @@ __host__ __device__ __forceinline__ int batch_geom(int kind) {
                                                                : kGeomLightCone;
 }
 
-// One block per relate chunk of one set, the set read from a table built at
-// create time, the (row tile, chunk) by a binary search over row tiles.  The
-// last chunk of a row tile also zeroes the row's padding words.  One
-// instance per geometry, each launched over all chunks (the other
-// geometries' blocks return at once), so that every geometry's code gets
-// the registers it needs for itself.
 // Relate block `local` of a set: its row tile rb, first word w0 and, for a
 // row tile's last chunk, the first padding word to zero (else -1).
 __device__ __forceinline__ void decode_rblock(const BatchSet& b, int64_t local, int64_t& rb, int64_t& w0,
@@ -245,14 +239,23 @@ __device__ __forceinline__ void decode_rblock(const BatchSet& b, int64_t local, 
     zero_from = w0 + kRelWordsPerBlock >= V ? w0 + kRelWordsPerBlock : -1;
 }
 
+// One block per relate chunk of one set, the set read from a table built at
+// create time, the (row tile, chunk) by a binary search over row tiles.  The
+// last chunk of a row tile also zeroes the row's padding words.  One
+// instance per geometry, each launched over that geometry's chunks only (a
+// table groups the chunks by geometry), so that every geometry's code gets
+// the registers it needs for itself.  Block x of a geometry's launch: relate block order[x] (the launch's slice
+// of the blocks grouped by geometry), of set rblock_set[order[x]].
 template <int G>
 __global__ void __launch_bounds__(kRelThreads, 5) k_batch_relate(const BatchSet* __restrict__ sets,
-                                                              const int32_t* __restrict__ rblock_set) {
+                                                              const int32_t* __restrict__ rblock_set,
+                                                              const int32_t* __restrict__ order) {
     __shared__ __align__(16) int32_t sc[kStageInts];
-    const BatchSet& b = sets[rblock_set[blockIdx.x]];
-    if (batch_geom(b.kind) != G) return;
+    const int64_t blk = order[blockIdx.x];
+    const BatchSet& b = sets[rblock_set[blk]];
+    if (batch_geom(b.kind) != G) return;  // never, by the order's construction
     int64_t rb, w0, zero_from;
-    decode_rblock(b, blockIdx.x - b.rblock_begin, rb, w0, zero_from);
+    decode_rblock(b, blk - b.rblock_begin, rb, w0, zero_from);
     relate_block<G>(b.coords, b.n, b.bits, b.row_words, rb, w0, sc, G == kGeomLightCone && b.kind == CS_2D_ORDER,
                     zero_from);
 }
@@ -261,12 +264,14 @@ __global__ void __launch_bounds__(kRelThreads, 5) k_batch_relate(const BatchSet*
 // look-up per word instead of 64 cone tests).
 __global__ void __launch_bounds__(kRelThreads, 4) k_batch_relate_cone(const BatchSet* __restrict__ sets,
                                                                    const int32_t* __restrict__ rblock_set,
+                                                                   const int32_t* __restrict__ order,
                                                                    WsHeader* hdr) {
     extern __shared__ __align__(16) uint8_t smem_rel[];
-    const BatchSet& b = sets[rblock_set[blockIdx.x]];
-    if (batch_geom(b.kind) != kGeomLightCone) return;
+    const int64_t blk = order[blockIdx.x];
+    const BatchSet& b = sets[rblock_set[blk]];
+    if (batch_geom(b.kind) != kGeomLightCone) return;  // never, by the order's construction
     int64_t rb, w0, zero_from;
-    decode_rblock(b, blockIdx.x - b.rblock_begin, rb, w0, zero_from);
+    decode_rblock(b, blk - b.rblock_begin, rb, w0, zero_from);
     relate_block_tables(b.coords, b.n, b.bits, b.row_words, rb, w0, b.ctab, smem_rel, b.kind == CS_2D_ORDER,
                         zero_from, hdr);
 }
@@ -395,6 +400,8 @@ struct cs_batch {
     MmaSetEntry* mma_dev = nullptr;
     int64_t total_elems = 0, total_rblocks = 0, total_items = 0, total_chunks = 0, total_hist = 0;
     int32_t* rtab = nullptr;  // relate block -> set
+    int32_t* rorder = nullptr;  // relate blocks grouped by geometry (each launch covers its own)
+    int64_t geo_begin[8] = {0, 0, 0, 0, 0, 0, 0, 0}, geo_count[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int32_t* etab = nullptr;  // expansion chunk -> count-table entry
     int32_t* mtab = nullptr;  // mirror block -> set
     int64_t total_mblocks = 0;
@@ -420,7 +427,7 @@ struct cs_batch {
 namespace {
 
 struct Layout {
-    size_t sets, entries, rtab, etab, mtab, ttab, coef, kends, total;
+    size_t sets, entries, rtab, rorder, etab, mtab, ttab, coef, kends, total;
     std::vector<size_t> coords, bits, key0, key1, raw, ctab, op0, op1;
 };
 
@@ -460,6 +467,7 @@ Layout batch_layout(const cs_set_desc* sets, int n_sets, int path) {
         if (tensor_path(path)) chunks += mma_expand_chunks(n);
     }
     L.rtab = take(size_t(rblocks) * 4);  // relate block -> set
+    L.rorder = take(size_t(rblocks) * 4);  // relate blocks by geometry
     L.etab = take(size_t(chunks) * 4);   // expansion chunk -> set
     L.mtab = take(size_t(mblocks) * 4);  // mirror block -> set
     L.ttab = take(size_t(tiles) * 4);    // column tile -> set
@@ -570,6 +578,19 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     for (int s = 0; s < n_sets; ++s)
         std::fill(rtab.begin() + bs[s].rblock_begin, rtab.begin() + bs[s].rblock_begin + chunk_sum(bs[s].vwords),
                   int32_t(s));
+    // the relate blocks grouped by geometry, so that each geometry's launch
+    // covers only its own blocks (blocks of the other geometries returning at
+    // once had cost their dispatch)
+    std::vector<int32_t> rorder;
+    rorder.reserve(rtab.size());
+    int64_t geo_begin[8], geo_count[8];
+    for (int g = 0; g < 8; ++g) {
+        geo_begin[g] = int64_t(rorder.size());
+        for (int s = 0; s < n_sets; ++s)
+            if (batch_geom(bs[s].kind) == g)
+                for (int64_t k = 0; k < chunk_sum(bs[s].vwords); ++k) rorder.push_back(int32_t(bs[s].rblock_begin + k));
+        geo_count[g] = int64_t(rorder.size()) - geo_begin[g];
+    }
     std::vector<PopcSetEntry> pe;
     std::vector<MmaSetEntry> me;
     for (int r = 0; r < n_sets; ++r) {
@@ -622,6 +643,11 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     h->total_items = items;
     h->total_chunks = chunks;
     h->rtab = reinterpret_cast<int32_t*>(ws + L.rtab);
+    h->rorder = reinterpret_cast<int32_t*>(ws + L.rorder);
+    for (int g = 0; g < 8; ++g) {
+        h->geo_begin[g] = geo_begin[g];
+        h->geo_count[g] = geo_count[g];
+    }
     h->mtab = reinterpret_cast<int32_t*>(ws + L.mtab);
     h->total_mblocks = mblk;
     h->total_tiles = tiles;
@@ -644,6 +670,8 @@ int cs_batch_create(const cs_set_desc* sets, int n_sets, int path, void* workspa
     cudaError_t e = cudaMemcpyAsync(h->sets_dev, bs.data(), sizeof(BatchSet) * bs.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !rtab.empty())
         e = cudaMemcpyAsync(h->rtab, rtab.data(), rtab.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !rorder.empty())
+        e = cudaMemcpyAsync(h->rorder, rorder.data(), rorder.size() * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !mtab.empty())
         e = cudaMemcpyAsync(h->mtab, mtab.data(), mtab.size() * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !ttab.empty())
@@ -712,15 +740,20 @@ int cs_batch_launch(const cs_batch* b, const double* eps_host, int n_eps, int64_
                                                                                  b->total_tiles);
 
     if (b->total_rblocks > int64_t(0x7fffffff)) return CS_EINVAL;
-    if (b->geoms & (1u << kGeomLightCone))
-        k_batch_relate_cone<<<unsigned(b->total_rblocks), kRelThreads, kConeTableSmem, st>>>(b->sets_dev, b->rtab,
-                                                                                              b->hdr);
-    if (b->geoms & (1u << kGeom3))
-        k_batch_relate<kGeom3><<<unsigned(b->total_rblocks), kRelThreads, 0, st>>>(b->sets_dev, b->rtab);
-    if (b->geoms & (1u << kGeom4))
-        k_batch_relate<kGeom4><<<unsigned(b->total_rblocks), kRelThreads, 0, st>>>(b->sets_dev, b->rtab);
-    if (b->geoms & (1u << kGeomDeSitter))
-        k_batch_relate<kGeomDeSitter><<<unsigned(b->total_rblocks), kRelThreads, 0, st>>>(b->sets_dev, b->rtab);
+    // one launch per geometry present, over that geometry's blocks only
+    auto range = [&](int g) { return b->rorder + b->geo_begin[g]; };
+    if (b->geo_count[kGeomLightCone])
+        k_batch_relate_cone<<<unsigned(b->geo_count[kGeomLightCone]), kRelThreads, kConeTableSmem, st>>>(
+            b->sets_dev, b->rtab, range(kGeomLightCone), b->hdr);
+    if (b->geo_count[kGeom3])
+        k_batch_relate<kGeom3><<<unsigned(b->geo_count[kGeom3]), kRelThreads, 0, st>>>(b->sets_dev, b->rtab,
+                                                                                     range(kGeom3));
+    if (b->geo_count[kGeom4])
+        k_batch_relate<kGeom4><<<unsigned(b->geo_count[kGeom4]), kRelThreads, 0, st>>>(b->sets_dev, b->rtab,
+                                                                                     range(kGeom4));
+    if (b->geo_count[kGeomDeSitter])
+        k_batch_relate<kGeomDeSitter><<<unsigned(b->geo_count[kGeomDeSitter]), kRelThreads, 0, st>>>(
+            b->sets_dev, b->rtab, range(kGeomDeSitter));
     if (b->total_mblocks > int64_t(0x7fffffff)) return CS_EINVAL;
     k_batch_mirror<<<unsigned(b->total_mblocks), kRelThreads, 0, st>>>(b->sets_dev, b->mtab);
     if ((err = cudaGetLastError()) != cudaSuccess) return CS_ECUDA;
