@@ -139,9 +139,17 @@ cudaError_t launch_action_device(int dim, int64_t n, const int64_t* hist, int64_
         a.kend[e] = is_local(a.v[e]) ? 0 : smear_cutoff(dim, a.v[e], 0.5 * double(n) * double(n), len);
         if (e < n_eps && !is_local(a.v[e])) any_smeared = true;
     }
+    // Blocks that hold terms only: block b's threads take k = 256 b + t (one
+    // term each while the grid covers the longest cutoff), and the blocks
+    // past the last term would only add exact zeros (FP64 is scarce here:
+    // their reductions had made both kernels about 0.1 ms each).
+    int64_t kmax = 0;
+    for (int e = 0; e < n_eps; ++e) kmax = a.kend[e] > kmax ? a.kend[e] : kmax;
+    int64_t blocks = (kmax + kActThreads - 1) / kActThreads;
+    blocks = blocks < 1 ? 1 : (blocks > kActBlocks ? kActBlocks : blocks);
     dd* partial = reinterpret_cast<dd*>(static_cast<uint8_t*>(workspace) + sizeof(WsHeader));
-    if (any_smeared) k_action_partial<<<kActBlocks, kActThreads, 0, st>>>(dim, n, hist, len, a, partial);
-    k_action_final<<<1, 32, 0, st>>>(dim, n, hist, len, a, partial, kActBlocks, out, bracket);
+    if (any_smeared) k_action_partial<<<unsigned(blocks), kActThreads, 0, st>>>(dim, n, hist, len, a, partial);
+    k_action_final<<<1, 32, 0, st>>>(dim, n, hist, len, a, partial, int(blocks), out, bracket);
     return cudaGetLastError();
 }
 
