@@ -58,6 +58,30 @@ def test_sprinkle_and_relate_bit_exact(cs, oracle, kind, n):
     assert (_np_bits(b) == oracle.causal_matrix(kind, want)).all()
 
 
+@pytest.mark.parametrize("kind", [0, 1, 5])
+@pytest.mark.parametrize("n", [12876, 12877, 16384, 20011])
+def test_relate_light_cone_large_bit_exact(cs, oracle, kind, n):
+    """Light-cone sets above the sizes of the all-kinds test, several row
+    tiles of relate chunks and mirror super-tiles deep, ragged and exact
+    multiples of 64: every bit, both triangles, against the oracle."""
+    seed = 0xC5E72000 + n + kind
+    b = _run(cs, kind, n, seed)
+    want = oracle.sprinkle(kind, n, seed)
+    assert (b.coords.cpu().numpy() == want).all()
+    assert (_np_bits(b) == oracle.causal_matrix(kind, want)).all()
+
+
+@pytest.mark.parametrize("n", [12877, 16384])
+def test_relate_chain_antichain_large(cs, oracle, n):
+    """Extreme relations at size: a chain (every pair related, every word
+    after the diagonal all ones) and an antichain (none)."""
+    chain = np.stack([np.arange(n), np.arange(n)]).astype(np.int32)
+    anti = np.stack([np.arange(n), np.arange(n)[::-1]]).astype(np.int32)
+    for coords in (chain, anti):
+        b = _run(cs, 0, n, 0, coords=coords)
+        assert (_np_bits(b) == oracle.causal_matrix(0, coords)).all()
+
+
 @pytest.mark.parametrize("path", [1, 2, 3], ids=["popc", "mma", "mma4"])
 @pytest.mark.parametrize("kind,n", [(0, 2), (0, 3), (0, 127), (0, 128), (0, 129), (0, 255), (0, 256), (0, 257),
                                     (0, 300), (0, 511), (0, 1000), (0, 1024), (0, 2049), (0, 4133), (1, 129),
