@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kRelThreads) k_relate(const int32_t* __restric
     relate_block<G>(coords, n, bits, row_words, blockIdx.x, int64_t(blockIdx.y) * kRelWordsPerBlock, sc, order2d);
 }
 
-__global__ void __launch_bounds__(kRelThreads) k_mirror(uint64_t* __restrict__ bits, int64_t n, int64_t row_words) {
+__global__ void __launch_bounds__(kRelThreads, 4) k_mirror(uint64_t* __restrict__ bits, int64_t n, int64_t row_words) {
     __shared__ uint64_t sm[kMirRows][kMirTiles + 1];
     mirror_block(bits, n, row_words, blockIdx.x, blockIdx.y, sm);
 }

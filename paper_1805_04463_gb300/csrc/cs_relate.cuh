@@ -680,26 +680,52 @@ __device__ __forceinline__ bool relate_block_tables(const int32_t* __restrict__ 
 constexpr int kMirTiles = 8;                    // tiles per super-tile side
 constexpr int kMirRows = 64 * kMirTiles;        // 512 source / output rows
 
-__device__ __forceinline__ uint64_t tr_step(uint64_t v, int j, uint64_t m, bool low) {
-    const uint64_t p = __shfl_xor_sync(0xffffffffu, v, j);
-    return low ? v ^ ((((v >> j) ^ p) & m) << j) : v ^ (((p >> j) ^ v) & m);
+// Transposes of bit tiles held one row per lane (bit c = column c).  Stage
+// j of the recursive block swap exchanges, between lanes l and l ^ j, the
+// j-bit groups that lie off the diagonal: the lane with (l & j) == 0 keeps
+// its low groups and takes its partner's low groups into its high ones, the
+// other keeps its high groups and takes its partner's high groups into its
+// low ones.  Per lane constants make every stage lane-uniform: for j = 16
+// and 8 a byte permute of the lane's word and its partner's; for j = 4, 2, 1
+// each lane sends its word rotated toward its partner's positions (right by
+// j, or by 32 - j, i.e. left by j) and masked to the groups the partner
+// takes, and keeps (own & mask) | received.
+struct Tr32 {
+    uint32_t s16, s8;       // byte-permute selectors
+    uint32_t r[3], m[3];    // rotations and kept masks for j = 4, 2, 1
+};
+__device__ __forceinline__ Tr32 tr32_consts(int lane) {
+    Tr32 c;
+    c.s16 = (lane & 16) ? 0x3276u : 0x5410u;  // high: partner's bytes 2,3 then own 2,3; low: own 0,1 then partner's 0,1
+    c.s8 = (lane & 8) ? 0x3715u : 0x6240u;    // high: p1 v1 p3 v3; low: v0 p0 v2 p2
+    const uint32_t mk[3] = {0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int j = 4 >> s;
+        const bool high = (lane & j) != 0;
+        c.r[s] = high ? uint32_t(32 - j) : uint32_t(j);
+        c.m[s] = high ? ~mk[s] : mk[s];
+    }
+    return c;
+}
+__device__ __forceinline__ uint32_t transpose32(uint32_t v, const Tr32& c) {
+    v = __byte_perm(v, __shfl_xor_sync(0xffffffffu, v, 16), c.s16);
+    v = __byte_perm(v, __shfl_xor_sync(0xffffffffu, v, 8), c.s8);
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+        v = (v & c.m[s]) | __shfl_xor_sync(0xffffffffu, __funnelshift_r(v, v, c.r[s]) & c.m[s], 4 >> s);
+    return v;
 }
 
-// Transpose the 64 x 64 bit tile whose rows l and l + 32 lane l holds.
-__device__ __forceinline__ void transpose64(uint64_t& x, uint64_t& y) {
-    const int lane = threadIdx.x & 31;
+// Transpose the 64 x 64 bit tile whose rows l and l + 32 lane l holds: the
+// stage j = 32 inside the lane (x's high half with y's low half), then the
+// four 32 x 32 quarters independently.
+__device__ __forceinline__ void transpose64(uint64_t& x, uint64_t& y, const Tr32& c) {
     const uint64_t t = ((x >> 32) ^ y) & 0x00000000FFFFFFFFull;
     y ^= t;
     x ^= t << 32;
-    const uint64_t masks[5] = {0x0000FFFF0000FFFFull, 0x00FF00FF00FF00FFull, 0x0F0F0F0F0F0F0F0Full,
-                               0x3333333333333333ull, 0x5555555555555555ull};
-#pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const int j = 16 >> s;
-        const bool low = (lane & j) == 0;
-        x = tr_step(x, j, masks[s], low);
-        y = tr_step(y, j, masks[s], low);
-    }
+    x = uint64_t(transpose32(uint32_t(x), c)) | (uint64_t(transpose32(uint32_t(x >> 32), c)) << 32);
+    y = uint64_t(transpose32(uint32_t(y), c)) | (uint64_t(transpose32(uint32_t(y >> 32), c)) << 32);
 }
 
 // Super-tile (A8, B8): output rows [512 A8, 512 A8 + 512), output words
@@ -739,10 +765,11 @@ __device__ __forceinline__ void mirror_block(uint64_t* __restrict__ bits, int64_
     const bool active = A < tiles && B0 < A;  // warp-uniform
     uint64_t ox[kMirTiles], oy[kMirTiles];
     if (active) {
+        const Tr32 tc = tr32_consts(lane);
 #pragma unroll
         for (int qb = 0; qb < kMirTiles; ++qb) {
             uint64_t x = sm[64 * qb + lane][warp], y = sm[64 * qb + lane + 32][warp];
-            transpose64(x, y);
+            transpose64(x, y, tc);
             ox[qb] = x;
             oy[qb] = y;
         }
