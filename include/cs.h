@@ -352,7 +352,12 @@ typedef struct {
 /* Opaque host-side plan of a batch (its device tables live in the workspace). */
 typedef struct cs_batch cs_batch;
 
-/* Device workspace for a batch of n_sets sets on `path` (0 for invalid input). */
+/* Device workspace for a batch of n_sets sets on `path` (0 for invalid input):
+ * per set its coordinates, keys, bitset (n * cs_row_words(n) * 8 bytes) and,
+ * on the tensor paths, its count operands (cs_operands_bytes); for the
+ * light-cone kinds one 1584-byte relation table per 64 elements; the plan's
+ * device tables (per set, per relate / mirror / expansion block, per column
+ * tile) and the smeared-sum coefficients and cutoffs. */
 size_t cs_batch_workspace_bytes(const cs_set_desc *sets, int n_sets, int path);
 
 /* Entries of the batch histogram: sum over sets of cs_hist_len(n); set s
