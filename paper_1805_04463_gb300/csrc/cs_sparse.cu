@@ -8,10 +8,11 @@
 // bitset with time-sorted labels, so both come from row scans: the future
 // list of i is the set bits of row i above column i, the past list the set
 // bits below it.  One warp owns a row: each lane loads one 64-bit word per
-// step (coalesced) and popcounts give the degrees; for the lists, the warp
-// takes the words one 32-bit half at a time, every lane owning one bit, so
-// each half's column indices leave in one coalesced run of stores.  The row
-// offsets are an exclusive scan of the degrees (three small kernels).
+// step (coalesced) and popcounts give the degrees; for the lists, a warp
+// scan of those popcounts places each word's columns, every lane writes its
+// own word's columns into a shared-memory run in order, and the run leaves
+// in coalesced stores.  The row offsets are an exclusive scan of the
+// degrees (three small kernels).
 #include "cs_kernels.cuh"
 
 namespace cs {
@@ -163,44 +164,89 @@ __global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* 
 
 // Column indices of each row's relations on one side, in increasing order,
 // at cols[offsets[i] ..).  A row whose list would end past cols_capacity is
-// skipped and CS_ENOMEM recorded.  The warp walks its row 32 words at a time;
-// for each 32-bit half-word in turn every lane owns one bit, so the set bits
-// of a half-word go out as one coalesced run of stores (rank of a bit = the
-// popcount of the lower lanes' bits).
-__global__ void __launch_bounds__(256) k_side_columns(const uint64_t* __restrict__ bits, int64_t n,
-                                                      int64_t row_words, bool future,
-                                                      const int64_t* __restrict__ offsets, int32_t* __restrict__ cols,
-                                                      int64_t cols_capacity, WsHeader* hdr) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t below = (1u << lane) - 1u;  // lanes under this one
-    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
-    for (int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
-        if (offsets[i + 1] > cols_capacity || offsets[i + 1] < offsets[i]) {
+// skipped and CS_ENOMEM recorded.  The warp walks its row 32 words at a
+// time, lane l owning word l: an inclusive warp scan of the words'
+// popcounts gives each word's first place in the step's run, each lane
+// writes its word's set columns (lowest bit first) into the warp's shared
+// buffer there, and the warp copies the run out in coalesced stores.  (One
+// lane per bit of each half-word in turn, with a popcount, a rank and a
+// predicated store per half-word, held the integer pipe at three times the
+// instructions per relation: 0.42 of the HBM rate at N = 2^17.)
+constexpr int kColsWarps = 4;                      // warps per block
+constexpr int kColsRun = 32 * 64 + 4;              // the most columns one step emits, and an alignment shift
+__global__ void __launch_bounds__(kColsWarps * 32) k_side_columns(const uint64_t* __restrict__ bits, int64_t n,
+                                                                   int64_t row_words, bool future,
+                                                                   const int64_t* __restrict__ offsets,
+                                                                   int32_t* __restrict__ cols,
+                                                                   int64_t cols_capacity, WsHeader* hdr) {
+    __shared__ __align__(16) int32_t stage[kColsWarps][kColsRun];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t* run = stage[warp];
+    const int64_t warps = int64_t(gridDim.x) * kColsWarps;
+    for (int64_t i = int64_t(blockIdx.x) * kColsWarps + warp; i < n; i += warps) {
+        const int64_t end = offsets[i + 1];
+        if (end > cols_capacity || end < offsets[i]) {
             if (lane == 0) set_status(hdr, CS_ENOMEM);
             continue;
         }
         const int64_t wi = i >> 6;
         const int64_t wlo = future ? wi : 0, whi = future ? (n + 63) >> 6 : wi + 1;
         int64_t pos = offsets[i];
-        const int64_t end = offsets[i + 1];
+        const uint64_t* row = bits + i * row_words;
+        uint64_t xn = wlo + lane < whi ? __ldg(row + wlo + lane) : 0ull;  // the next step's word, in flight
         for (int64_t w0 = wlo; w0 < whi; w0 += 32) {
             const int64_t w = w0 + lane;
-            const uint64_t x = w < whi ? __ldg(bits + i * row_words + w) & side_mask(i, w, future) : 0ull;
-            const int64_t nword = whi - w0 < 32 ? whi - w0 : 32;
-            for (int q = 0; q < nword; ++q) {  // warp-uniform
-                const uint64_t y = __shfl_sync(0xffffffffu, x, q);
+            uint64_t x = w < whi ? xn & side_mask(i, w, future) : 0ull;
+            xn = w + 32 < whi ? __ldg(row + w + 32) : 0ull;
+            const int c = __popcll(x);
+            int incl = c;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t half = uint32_t(y >> (32 * h));
-                    if (half == 0u) continue;  // warp-uniform
-                    const int64_t p = pos + __popc(half & below);
-                    if (((half >> lane) & 1u) && p < end)  // p < end unless the bitset changed
-                        cols[p] = int32_t(64 * (w0 + q) + 32 * h + lane);
-                    pos += __popc(half);
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            // element k of the run goes to cols[pos + k] and to run[s0 + k],
+            // s0 = that position's 4-byte slot in its 16-byte group, so the
+            // run's 16-byte groups are the output's
+            const int s0 = int((reinterpret_cast<uintptr_t>(cols + pos) >> 2) & 3);
+            int at = s0 + incl - c;
+            const int32_t base = int32_t(64 * w);  // n <= 2^22
+            // lowest bit first, one 32-bit half at a time (cheaper steps than
+            // 64-bit find-first and clear-lowest)
+            for (uint32_t h = uint32_t(x); h; h &= h - 1u) run[at++] = base + (__ffs(int(h)) - 1);
+            for (uint32_t h = uint32_t(x >> 32); h; h &= h - 1u) run[at++] = base + 31 + __ffs(int(h));
+            __syncwarp();
+            // a head up to the first 16-byte boundary, whole groups as
+            // 16-byte stores, then a tail; positions at or past `end` are
+            // skipped (only if the bitset changed since the offsets)
+            const int h0 = (4 - s0) & 3;
+            const int head = h0 < total ? h0 : total;
+            const int groups = (total - head) >> 2;
+            if (lane < head && pos + lane < end) cols[pos + lane] = run[s0 + lane];
+            for (int g = lane; g < groups; g += 32) {
+                const int k = head + 4 * g;
+                const int4 v = *reinterpret_cast<const int4*>(run + s0 + k);
+                if (pos + k + 3 < end) {
+                    *reinterpret_cast<int4*>(cols + pos + k) = v;
+                } else {
+                    const int32_t e4[4] = {v.x, v.y, v.z, v.w};
+                    for (int e = 0; e < 4; ++e)
+                        if (pos + k + e < end) cols[pos + k + e] = e4[e];
                 }
             }
+            for (int k = head + 4 * groups + lane; k < total; k += 32)
+                if (pos + k < end) cols[pos + k] = run[s0 + k];
+            __syncwarp();
+            pos += total;
         }
     }
+}
+
+int cols_grid(int64_t n) {
+    int64_t g = (n + kColsWarps - 1) / kColsWarps;
+    const int64_t cap = int64_t(device_sm_count()) * 32;
+    return int(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
 int row_grid(int64_t n) {
@@ -269,7 +315,7 @@ extern "C" int cs_sparse_columns(int64_t n, const uint64_t* bits_dev, int64_t ro
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     WsHeader* hdr = static_cast<WsHeader*>(workspace_dev);
     if (cudaMemsetAsync(&hdr->status, 0, sizeof(int32_t), st) != cudaSuccess) return CS_ECUDA;
-    k_side_columns<<<row_grid(n), 256, 0, st>>>(bits_dev, n, row_words, direction == 1, offsets_dev, cols_dev,
+    k_side_columns<<<cols_grid(n), kColsWarps * 32, 0, st>>>(bits_dev, n, row_words, direction == 1, offsets_dev, cols_dev,
                                                cols_capacity, hdr);
     return cudaGetLastError() == cudaSuccess ? CS_OK : CS_ECUDA;
 }
