@@ -154,7 +154,9 @@ int cs_causal_matrix(int kind, int64_t n, const int32_t *coords_dev,
  * below; the tensor-core paths only where the device has tcgen05, and only
  * while the set's bitset plus the path's workspace fit the AUTO memory limit
  * -- a table entry of CS_PATH_MMA that does not fit falls back to
- * CS_PATH_MMA4, one of CS_PATH_MMA4 to CS_PATH_POPC); -1 for invalid
+ * CS_PATH_MMA4; one of CS_PATH_MMA4 runs in bands (cs_mma4_band_panels) when
+ * the whole operand matrix does not fit, and falls back to CS_PATH_POPC only
+ * when not even bands of 32 supertile rows (8192 rows) do); -1 for invalid
  * arguments.  The rule depends only on n, the table and the limit, so the
  * workspace query and the count resolve alike. */
 int cs_resolved_path(int64_t n, int path);
@@ -215,9 +217,29 @@ int cs_get_batch_tuning(int *path, int *max_run);
 /* Device workspace needed by cs_interval_abundance for (n, path).  The FP8
  * tensor-core path keeps two n x ceil(n/128)*128-byte operand matrices in it
  * (2 n^2 bytes, about 34 GB at n = 131072); the FP4 path one
- * n x ceil(n/256)*128-byte matrix plus 256 bytes per row (n^2 / 2 bytes,
- * about 8.6 GB at n = 131072, 137 GB at n = 2^19). */
+ * n x ceil(n/256)*128-byte matrix E plus 256 bytes per row (n^2 / 2 bytes,
+ * about 8.6 GB at n = 131072, 137 GB at n = 2^19) when that fits beside the
+ * set's bitset within the AUTO memory limit, else a band buffer of the
+ * widest bands that do (see cs_mma4_band_panels; at least one-panel bands,
+ * 512 rows of E).  The FP4 count also runs with less than this, down to the
+ * workspace of one-panel bands, in narrower bands. */
 size_t cs_interval_abundance_workspace(int64_t n, int path);
+
+/*
+ * The FP4 pair path (CS_PATH_MMA4) with a workspace of workspace_bytes:
+ * how many supertile rows (panels of 256 rows) each operand group holds.
+ * The count covers the pairs i < j with 256 x 256 supertiles (si, sj), si <=
+ * sj, whose MMAs read E rows of panels si and sj; when the whole E does not
+ * fit, the panels fall into groups of g, and for each pair of groups a <= b
+ * the kernel counts the supertiles with si in group a and sj in group b from
+ * a band buffer holding those two groups' rows (2 g panels, each row only
+ * over the columns the band's K ranges reach), re-expanded from the bitset
+ * per band: (m + 1) m / 2 launches for m = ceil(nsb / g) groups.  Results do
+ * not depend on g.  Returns nsb = ceil(n / 256) when the whole E fits (one
+ * launch), 0 when not even g = 1 does, -1 for an invalid n.  The count call
+ * takes the widest bands its workspace_bytes holds.
+ */
+int64_t cs_mma4_band_panels(int64_t n, size_t workspace_bytes);
 
 /*
  * Interval abundances of a time-sorted causal matrix (Algorithm "Optimized
@@ -229,7 +251,8 @@ size_t cs_interval_abundance_workspace(int64_t n, int path);
  * every path gives identical, exact results (the tensor paths multiply 0/1
  * values and accumulate integers below 2^23 in FP32).
  * Errors: CS_EINVAL (n < 1, n > 2^22, bad row_words, NULL or unaligned pointers), CS_ENOMEM
- * (workspace too small), CS_EUNSUPPORTED (CS_PATH_MMA or CS_PATH_MMA4 on a
+ * (workspace below cs_interval_abundance_workspace; on CS_PATH_MMA4 below the
+ * workspace of one-panel bands), CS_EUNSUPPORTED (CS_PATH_MMA or CS_PATH_MMA4 on a
  * device without tcgen05), CS_ECUDA.  A timed-out in-kernel wait sets CS_ETIMEOUT in the
  * workspace status word.
  */

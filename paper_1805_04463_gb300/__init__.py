@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
             "cs_sprinkle": ([i32, i64, u64, vp, vp, sz, vp], i32),
             "cs_causal_matrix": ([i32, i64, vp, vp, i64, vp], i32),
             "cs_interval_abundance_workspace": ([i64, i32], sz),
+            "cs_mma4_band_panels": ([i64, sz], i64),
             "cs_resolved_path": ([i64, i32], i32),
             "cs_set_auto_paths": ([vp, vp, i32], i32),
             "cs_get_auto_paths": ([vp, vp, i32], i32),
@@ -182,6 +183,12 @@ def sprinkle_workspace_bytes(kind: int, n: int) -> int:
 
 def interval_abundance_workspace(n: int, path: int = PATH_AUTO) -> int:
     return lib().cs_interval_abundance_workspace(n, path)
+
+
+def mma4_band_panels(n: int, workspace_bytes: int) -> int:
+    """Supertile rows per band of the FP4 count with this workspace: (n + 255) // 256
+    when the whole operand matrix fits, 0 when not even one-panel bands do."""
+    return lib().cs_mma4_band_panels(n, workspace_bytes)
 
 
 def resolved_path(n: int, path: int = PATH_AUTO) -> int:

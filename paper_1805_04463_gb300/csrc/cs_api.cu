@@ -86,16 +86,35 @@ size_t auto_memory_limit() {
     return lim ? lim : device_total_memory() / 10 * 9;
 }
 
-size_t tensor_workspace_bytes(int64_t n, int p) {
-    return p == CS_PATH_MMA ? mma_workspace_bytes(n) : mma4_workspace_bytes(n);
+// Memory the AUTO limit leaves for a count workspace beside the set's bitset.
+size_t auto_workspace_room(int64_t n) {
+    const size_t lim = auto_memory_limit(), bits = cs_bitset_bytes(n);
+    return lim > bits ? lim - bits : 0;
 }
 
+// The FP4 path's workspace: the whole set's operands when they fit beside the
+// bitset within the AUTO limit, else the widest bands of supertile rows that
+// do (at least bands of one panel).
+size_t mma4_planned_bytes(int64_t n) {
+    const int64_t g = mma4_band_panels(n, auto_workspace_room(n));
+    return mma4_band_bytes(n, g < 1 ? 1 : g);
+}
+
+// Bands narrower than this many supertile rows (or the whole set, if it has
+// fewer) make AUTO take the POPC path: each band is one launch and one
+// expansion of its rows, and narrow bands would spend more on those than the
+// tensor cores save.
+constexpr int64_t kMinBandPanels = 32;
+
 // A tensor path fits when the set's bitset and the path's workspace together
-// stay within the AUTO memory limit.  The rule reads the device's capacity,
-// not its free memory, so that the workspace query and the count call that
-// follows it (after the caller allocated that workspace) resolve alike.
+// stay within the AUTO memory limit (FP4: bands of kMinBandPanels rows at
+// least).  The rule reads the device's capacity, not its free memory, so that
+// the workspace query and the count call that follows it (after the caller
+// allocated that workspace) resolve alike.
 bool tensor_fits(int64_t n, int p) {
-    return cs_bitset_bytes(n) + tensor_workspace_bytes(n, p) <= auto_memory_limit();
+    if (p == CS_PATH_MMA) return cs_bitset_bytes(n) + mma_workspace_bytes(n) <= auto_memory_limit();
+    const int64_t nsb = (n + 255) / 256;
+    return mma4_band_panels(n, auto_workspace_room(n)) >= (nsb < kMinBandPanels ? nsb : kMinBandPanels);
 }
 
 int resolve_path(int64_t n, int path) {
@@ -251,17 +270,29 @@ int cs_resolved_path(int64_t n, int path) {
 size_t cs_interval_abundance_workspace(int64_t n, int path) {
     if (!valid_n(n) || path < CS_PATH_AUTO || path > CS_PATH_MMA4) return 0;
     const int p = resolve_path(n, path);
-    return p == CS_PATH_MMA ? mma_workspace_bytes(n) : p == CS_PATH_MMA4 ? mma4_workspace_bytes(n)
+    return p == CS_PATH_MMA ? mma_workspace_bytes(n) : p == CS_PATH_MMA4 ? mma4_planned_bytes(n)
                                                                           : popc_workspace_bytes(n);
+}
+
+int64_t cs_mma4_band_panels(int64_t n, size_t workspace_bytes) {
+    if (!valid_n(n)) return -1;
+    return mma4_band_panels(n, workspace_bytes);
 }
 
 namespace {
 
+// The least workspace a count runs with: the planned one, except on the FP4
+// path, which takes narrower bands down to one panel.
+size_t min_count_workspace(int64_t n, int path) {
+    return resolve_path(n, path) == CS_PATH_MMA4 ? mma4_band_bytes(n, 1) : cs_interval_abundance_workspace(n, path);
+}
+
 // The count kernels of a resolved path.
 cudaError_t launch_count(int p, int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* ws,
-                         cudaStream_t st, const double* phi = nullptr, double* layer = nullptr, int kmax = -1) {
+                         size_t ws_bytes, cudaStream_t st, const double* phi = nullptr, double* layer = nullptr,
+                         int kmax = -1) {
     if (p == CS_PATH_MMA) return launch_count_mma(n, bits, row_words, hist, ws, st, phi, layer, kmax);
-    if (p == CS_PATH_MMA4) return launch_count_mma4(n, bits, row_words, hist, ws, st, phi, layer, kmax);
+    if (p == CS_PATH_MMA4) return launch_count_mma4(n, bits, row_words, hist, ws, ws_bytes, st, phi, layer, kmax);
     return launch_count_popc(n, bits, row_words, hist, ws, st, phi, layer, kmax);
 }
 
@@ -274,13 +305,13 @@ int cs_interval_abundance(int64_t n, const uint64_t* bits_dev, int64_t row_words
         row_words < cs_row_words(n) || row_words % 16 != 0 || !workspace_dev || !aligned(workspace_dev, 256) ||
         path < CS_PATH_AUTO || path > CS_PATH_MMA4)
         return CS_EINVAL;
-    if (workspace_bytes < cs_interval_abundance_workspace(n, path)) return CS_ENOMEM;
+    if (workspace_bytes < min_count_workspace(n, path)) return CS_ENOMEM;
     const int p = resolve_path(n, path);
     if ((p == CS_PATH_MMA || p == CS_PATH_MMA4) && !device_has_tcgen05()) return CS_EUNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (fault_injected(CS_FAULT_LAUNCH)) return CS_ECUDA;
     cudaError_t e = clear_status(workspace_dev, st);
-    if (e == cudaSuccess) e = launch_count(p, n, bits_dev, row_words, hist_dev, workspace_dev, st);
+    if (e == cudaSuccess) e = launch_count(p, n, bits_dev, row_words, hist_dev, workspace_dev, workspace_bytes, st);
     return from_cuda(e);
 }
 
@@ -293,14 +324,15 @@ int cs_layer_sums(int64_t n, const uint64_t* bits_dev, int64_t row_words, int64_
         path < CS_PATH_AUTO || path > CS_PATH_MMA4 || kmax < 0 || kmax > 15 || !layer_dev ||
         !aligned(layer_dev, 8) || (phi_dev && !aligned(phi_dev, 8)))
         return CS_EINVAL;
-    if (workspace_bytes < cs_interval_abundance_workspace(n, path)) return CS_ENOMEM;
+    if (workspace_bytes < min_count_workspace(n, path)) return CS_ENOMEM;
     const int p = resolve_path(n, path);
     if ((p == CS_PATH_MMA || p == CS_PATH_MMA4) && !device_has_tcgen05()) return CS_EUNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = clear_status(workspace_dev, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(layer_dev, 0, size_t(kmax + 1) * size_t(n) * 8, st);
     if (e == cudaSuccess)
-        e = launch_count(p, n, bits_dev, row_words, hist_dev, workspace_dev, st, phi_dev, layer_dev, kmax);
+        e = launch_count(p, n, bits_dev, row_words, hist_dev, workspace_dev, workspace_bytes, st, phi_dev, layer_dev,
+                         kmax);
     return from_cuda(e);
 }
 

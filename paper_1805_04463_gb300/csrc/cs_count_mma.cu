@@ -176,6 +176,42 @@ __device__ __forceinline__ bool decode_slot(int64_t t, int64_t nsb, int64_t n, i
     return si <= sj && sj < nsb && si * 256 + half * kBM < n;
 }
 
+// A band of the FP4 pair count, for sets whose full operand matrix does not
+// fit the workspace: the supertiles with si in panels [i0, i0 + ni) and sj in
+// [j0, j0 + nj) -- a triangle when the two ranges are the same (diag), else
+// a rectangle wholly above the diagonal -- whose E rows sit in a band buffer
+// (row I of the set at band row I - erow_i as an A row, J - erow_j as a B
+// row).  The whole set is the one band {0, 0, nsb, nsb, 0, 0, 1}.
+struct MmaBand {
+    int64_t i0, j0, ni, nj;
+    int64_t erow_i, erow_j;
+    int diag;
+};
+
+// Slot t of a band's item list -> supertile (si, sj) of the set and its half.
+// The rectangle is rasterised like the triangle: R x R blocks, row by row.
+__device__ __forceinline__ bool decode_band(int64_t t, const MmaBand& b, int64_t n, int64_t R, int64_t& si,
+                                            int64_t& sj, int64_t& half) {
+    if (b.diag) {
+        if (!decode_slot(t, b.ni, n - b.i0 * 256, R, si, sj, half)) return false;
+        si += b.i0;
+        sj += b.i0;
+        return true;
+    }
+    const int64_t spb = 2 * R * R;
+    const int64_t blk = t / spb, slot = t - blk * spb;
+    const int64_t nbj = (b.nj + R - 1) / R;
+    const int64_t gi = blk / nbj, gj = blk - gi * nbj;
+    si = gi * R + slot / (2 * R);
+    const int64_t rem = slot % (2 * R);
+    sj = gj * R + rem / 2;
+    half = rem & 1;
+    if (si >= b.ni || sj >= b.nj) return false;
+    si += b.i0;
+    sj += b.j0;
+    return si * 256 + half * kBM < n;
+}
+
 // Ring entry of a valid item: set index << 33 | half << 32 | si << 16 | sj
 // (nsb <= 2^14 for n <= 2^22); -1 = no more items.
 __device__ __forceinline__ int64_t pack_item(int sidx, int64_t si, int64_t sj, int64_t half) {
@@ -290,32 +326,31 @@ __global__ void __launch_bounds__(256) k_expand_f8_multi(const MmaSetEntry* __re
 // Pieces of 32 columns (one 32-bit half of a bitset word, 16 operand bytes).
 __device__ __forceinline__ int64_t own_first_piece(int64_t i) { return (i / 256) * 8; }
 
-// Row i of E, DU and DL (E row bytes kpad / 2; DU and DL rows 128 bytes,
-// DL starting dl_off bytes after DU), pieces handed out to thread t of a
-// team of `size`.
-__device__ __forceinline__ void expand_row_f4(const uint64_t* __restrict__ bits, int64_t row_words, int64_t kpad,
-                                              uint8_t* __restrict__ E, uint8_t* __restrict__ D, int64_t dl_off,
-                                              int64_t i, int t, int size) {
-    const int ppr = int(kpad / 32);
+// Row i of E, pieces [p0, p1) of it (E row bytes kpad / 2), into erow, and,
+// when D is not NULL, row i of DU and DL (rows of 128 bytes, DL starting
+// dl_off bytes after DU); pieces handed out to thread t of a team of `size`.
+__device__ __forceinline__ void expand_row_f4(const uint64_t* __restrict__ bits, int64_t row_words, uint4* erow,
+                                              int p0, int p1, uint8_t* __restrict__ D, int64_t dl_off, int64_t i,
+                                              int t, int size) {
     const uint32_t* brow = reinterpret_cast<const uint32_t*>(bits + i * row_words);
-    uint4* erow = reinterpret_cast<uint4*>(E + i * (kpad / 2));
     const int own = int(own_first_piece(i));
     // four pieces per step, their loads issued together (memory-level
     // parallelism: one load, spread and store at a time left the expansion
     // latency-bound)
-    for (int c0 = t; c0 < ppr; c0 += 4 * size) {
+    for (int c0 = p0 + t; c0 < p1; c0 += 4 * size) {
         uint32_t w[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int c = c0 + k * size;
-            w[k] = c < ppr ? __ldg(brow + c) : 0u;
+            w[k] = c < p1 ? __ldg(brow + c) : 0u;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int c = c0 + k * size;
-            if (c < ppr && unsigned(c - own) >= 8u) erow[c] = spread32_e2m1(w[k]);
+            if (c < p1 && unsigned(c - own) >= 8u) erow[c] = spread32_e2m1(w[k]);
         }
     }
+    if (D == nullptr) return;
     uint4* du = reinterpret_cast<uint4*>(D + i * 128);
     uint4* dl = reinterpret_cast<uint4*>(D + dl_off + i * 128);
     const int ii = int(i);  // n < 2^31
@@ -330,25 +365,41 @@ __device__ __forceinline__ void expand_row_f4(const uint64_t* __restrict__ bits,
     }
 }
 
-// FP4 operand rows [r0, r1) of one set: the block sweeps each long row, one
-// warp per short row.
+// FP4 operand rows [r0, r1) of one set: row i of E at E + (i - ebase) rows,
+// its pieces [p0, p1); DU and DL too unless D is NULL.  The block sweeps each
+// long row, one warp takes each short one.
 __device__ __forceinline__ void expand_rows_f4(const uint64_t* __restrict__ bits, int64_t row_words, int64_t kpad,
-                                               uint8_t* __restrict__ E, uint8_t* __restrict__ D, int64_t dl_off,
-                                               int64_t r0, int64_t r1) {
-    if (kpad / 32 >= 4 * int64_t(blockDim.x)) {
+                                               uint8_t* __restrict__ E, int64_t ebase, int p0, int p1,
+                                               uint8_t* __restrict__ D, int64_t dl_off, int64_t r0, int64_t r1) {
+    auto erow = [&](int64_t i) { return reinterpret_cast<uint4*>(E + (i - ebase) * (kpad / 2)); };
+    if (p1 - p0 >= 4 * int(blockDim.x)) {
         for (int64_t i = r0; i < r1; ++i)
-            expand_row_f4(bits, row_words, kpad, E, D, dl_off, i, threadIdx.x, blockDim.x);
+            expand_row_f4(bits, row_words, erow(i), p0, p1, D, dl_off, i, threadIdx.x, blockDim.x);
         return;
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int64_t i = r0 + warp; i < r1; i += nw) expand_row_f4(bits, row_words, kpad, E, D, dl_off, i, lane, 32);
+    for (int64_t i = r0 + warp; i < r1; i += nw)
+        expand_row_f4(bits, row_words, erow(i), p0, p1, D, dl_off, i, lane, 32);
 }
 
 __global__ void __launch_bounds__(256) k_expand_f4(const uint64_t* __restrict__ bits, int64_t n, int64_t row_words,
                                                    int64_t kpad, uint8_t* __restrict__ E, uint8_t* __restrict__ D,
                                                    int64_t dl_off) {
+    const int ppr = int(kpad / 32);
     for (int64_t r0 = int64_t(blockIdx.x) * kExpandRows; r0 < n; r0 += int64_t(gridDim.x) * kExpandRows)
-        expand_rows_f4(bits, row_words, kpad, E, D, dl_off, r0, r0 + kExpandRows < n ? r0 + kExpandRows : n);
+        expand_rows_f4(bits, row_words, kpad, E, 0, 0, ppr, D, dl_off, r0, r0 + kExpandRows < n ? r0 + kExpandRows : n);
+}
+
+// Rows [r_begin, r_end) of a band: E row i at band row e_row0 + (i - r_begin),
+// 32-column pieces [p0, p1); DU and DL too unless D is NULL.
+__global__ void __launch_bounds__(256) k_expand_f4_band(const uint64_t* __restrict__ bits, int64_t row_words,
+                                                        int64_t kpad, uint8_t* __restrict__ E, int64_t r_begin,
+                                                        int64_t r_end, int64_t e_row0, int p0, int p1,
+                                                        uint8_t* __restrict__ D, int64_t dl_off) {
+    for (int64_t r0 = r_begin + int64_t(blockIdx.x) * kExpandRows; r0 < r_end;
+         r0 += int64_t(gridDim.x) * kExpandRows)
+        expand_rows_f4(bits, row_words, kpad, E, r_begin - e_row0, p0, p1, D, dl_off, r0,
+                       r0 + kExpandRows < r_end ? r0 + kExpandRows : r_end);
 }
 
 // The same over many sets, one block per chunk of kExpandRows rows.
@@ -356,7 +407,7 @@ __global__ void __launch_bounds__(256) k_expand_f4_multi(const MmaSetEntry* __re
                                                          const int32_t* __restrict__ chunk_set) {
     const MmaSetEntry& e = sets[chunk_set[blockIdx.x]];
     const int64_t r0 = (int64_t(blockIdx.x) - e.chunk_begin) * kExpandRows;
-    expand_rows_f4(e.bits, e.row_words, e.kpad, e.op0, e.op1, mma4_dl_offset(e.n), r0,
+    expand_rows_f4(e.bits, e.row_words, e.kpad, e.op0, 0, 0, int(e.kpad / 32), e.op1, mma4_dl_offset(e.n), r0,
                    r0 + kExpandRows < e.n ? r0 + kExpandRows : e.n);
 }
 
@@ -378,6 +429,7 @@ struct MmaView {
     double* layer;      // layer sums [kmax+1][n], or NULL
     int kmax;           // < 0: no layer sums
     int raster;         // raster block side of the item order
+    MmaBand band;       // the supertiles this launch counts (the whole set, or one band)
 };
 
 // Work source: a single set passed in kernel parameters.  The queue hands out
@@ -432,7 +484,8 @@ struct MmaMulti {
         const MmaSetEntry& e = sets[s];
         return MmaView{e.maps.m, e.bits, e.n, e.row_words, e.nsb, e.kblocks,
                        reinterpret_cast<unsigned long long*>(hist_base + uintptr_t(e.hist_off)),
-                       e.n > 1 ? e.n - 1 : 1, e.phi, e.layer, int(e.kmax), kRasterDefault};
+                       e.n > 1 ? e.n - 1 : 1, e.phi, e.layer, int(e.kmax), kRasterDefault,
+                       MmaBand{0, 0, e.nsb, e.nsb, 0, 0, 1}};
     }
 };
 
@@ -602,9 +655,9 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                     if (leader) mbar_arrive_expect_tx(&full[s], 2 * kSB);
                     const bool a_own = kb == it.I0 / kBN, b_own = kb == it.J0 / kBN;
                     tma_load_2d_pair(a, &v.map[a_own ? kMapDU : kMapE], a_own ? 0 : int32_t(kb * kBK),
-                                     int32_t(it.I0 + row_off), fb);
+                                     int32_t(it.I0 + row_off - (a_own ? 0 : v.band.erow_i)), fb);
                     tma_load_2d_pair(a + kABytes, &v.map[b_own ? kMapDL : kMapE], b_own ? 0 : int32_t(kb * kBK),
-                                     int32_t(it.J0 + row_off), fb);
+                                     int32_t(it.J0 + row_off - (b_own ? 0 : v.band.erow_j)), fb);
                 } else {
                     mbar_arrive_expect_tx(&full[s], kSB);
                     tma_load_2d(a, &v.map[kMapU], int32_t(kb * kBK), int32_t(it.I0), &full[s]);
@@ -658,7 +711,7 @@ __device__ __forceinline__ void mma_body(const Src& src, WsHeader* hdr) {
                     cur = sidx;
                     v = src.view(sidx);
                 }
-                if (decode_slot(lu * kCl, v.nsb, v.n, v.raster, si, sj, half)) {
+                if (decode_band(lu * kCl, v.band, v.n, v.raster, si, sj, half)) {
                     e = pack_item(sidx, si, sj, half);
                     break;
                 }
@@ -904,8 +957,9 @@ __global__ void __maxnreg__(kMaxRegs)
     k_count_mma(const __grid_constant__ MmaMaps maps, const uint64_t* __restrict__ bits, int64_t n,
                 int64_t row_words, int64_t nsb, int64_t nitems, int64_t kblocks,
                 unsigned long long* __restrict__ hist, int64_t hist_len, const double* phi, double* layer, int kmax,
-                int raster, WsHeader* hdr) {
-    const MmaSingle src{MmaView{maps.m, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax, raster},
+                int raster, MmaBand band, WsHeader* hdr) {
+    const MmaSingle src{MmaView{maps.m, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax, raster,
+                                band},
                         nitems};
     mma_body<FmtF8>(src, hdr);
 }
@@ -917,8 +971,9 @@ __global__ void __maxnreg__(kMaxRegs)
     k_count_mma4(const __grid_constant__ MmaMaps maps, const uint64_t* __restrict__ bits, int64_t n,
                  int64_t row_words, int64_t nsb, int64_t nitems, int64_t kblocks,
                  unsigned long long* __restrict__ hist, int64_t hist_len, const double* phi, double* layer, int kmax,
-                 int raster, WsHeader* hdr) {
-    const MmaSingle src{MmaView{maps.m, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax, raster},
+                 int raster, MmaBand band, WsHeader* hdr) {
+    const MmaSingle src{MmaView{maps.m, bits, n, row_words, nsb, kblocks, hist, hist_len, phi, layer, kmax, raster,
+                                band},
                         nitems};
     mma_body<Fmt>(src, hdr);
 }
@@ -1010,14 +1065,36 @@ MmaLayout mma_layout(int64_t n, bool fp4) {
     return m;
 }
 
+// The FP4 layout when the set's E does not fit: header, a band buffer of
+// 2 g panels of 256 E rows (two groups of g supertile rows), then DU and DL
+// for every row.
+MmaLayout mma4_band_layout(int64_t n, int64_t g) {
+    MmaLayout m;
+    m.kpad = (n + FmtF4::kKE - 1) / FmtF4::kKE * FmtF4::kKE;
+    m.row = m.kpad / 2;
+    m.op0 = 1024;
+    m.op1 = align_up(m.op0 + size_t(2 * g * 256) * size_t(m.row), 1024);
+    m.total = align_up(m.op1 + operand_bytes(n, m.kpad, true, 1), 256);
+    return m;
+}
+
 // TMA maps of one set's operands (128B swizzle; boxes of one 128-byte
 // K-stage).  FP8: U (box 128 rows, the A slab) and L (box 256 rows, the B
 // slab).  FP4 pairs: each CTA of a pair loads 128 rows of A and of B, so E,
 // DU and DL all take 128-row boxes.
+// E (FP4): `rows` rows of kpad / 2 bytes (the rows of the set, or of a band
+// buffer up to its last row of the set: the map reads zeros past them).
+CUresult encode_e_map(CUtensorMap* map, int64_t kpad, uint8_t* op0, int64_t rows) {
+    const uint64_t row = uint64_t(kpad / 2);
+    return encode_tensor_map_2d(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, op0, row, uint64_t(rows), row, kBK, kBM,
+                                kSwizzle);
+}
+
 CUresult encode_operand_maps(MmaMaps* maps, int64_t n, int64_t kpad, bool fp4, uint8_t* op0, uint8_t* op1) {
     const uint64_t row = uint64_t(fp4 ? kpad / 2 : kpad);
-    CUresult r = encode_tensor_map_2d(&maps->m[0], CU_TENSOR_MAP_DATA_TYPE_UINT8, op0, row, uint64_t(n), row, kBK,
-                                      kBM, kSwizzle);
+    CUresult r = fp4 ? encode_e_map(&maps->m[kMapE], kpad, op0, n)
+                     : encode_tensor_map_2d(&maps->m[kMapU], CU_TENSOR_MAP_DATA_TYPE_UINT8, op0, row, uint64_t(n),
+                                            row, kBK, kBM, kSwizzle);
     if (r != CUDA_SUCCESS) return r;
     if (!fp4) {
         std::memset(static_cast<void*>(&maps->m[2]), 0, sizeof(CUtensorMap));
@@ -1037,6 +1114,22 @@ CUresult encode_operand_maps(MmaMaps* maps, int64_t n, int64_t kpad, bool fp4, u
 size_t mma_workspace_bytes(int64_t n) { return mma_layout(n, false).total; }
 
 size_t mma4_workspace_bytes(int64_t n) { return mma_layout(n, true).total; }
+
+int64_t mma4_band_panels(int64_t n, size_t bytes) {
+    if (n < 1) return 0;
+    const int64_t nsb = (n + 255) / 256;
+    if (mma_layout(n, true).total <= bytes) return nsb;
+    const MmaLayout one = mma4_band_layout(n, 1);
+    if (one.total > bytes) return 0;
+    int64_t g = 1 + int64_t((bytes - one.total) / (size_t(2 * 256) * size_t(one.row)));
+    while (g > 1 && mma4_band_layout(n, g).total > bytes) --g;
+    return g < nsb ? g : nsb;
+}
+
+size_t mma4_band_bytes(int64_t n, int64_t g) {
+    const int64_t nsb = (n + 255) / 256;
+    return g >= nsb ? mma_layout(n, true).total : mma4_band_layout(n, g < 1 ? 1 : g).total;
+}
 
 int64_t mma_kpad(int64_t n, bool fp4) {
     const int64_t ke = fp4 ? FmtF4::kKE : FmtF8::kKE;
@@ -1136,29 +1229,30 @@ cudaError_t launch_count_mma_multi(const MmaSetEntry* sets_dev, int nsets, int64
 
 namespace {
 
+// Items of a band: the triangle's raster blocks, or the rectangle's.
+int64_t band_items(const MmaBand& b, int raster) {
+    const int64_t R = raster;
+    const int64_t nbi = (b.ni + R - 1) / R, nbj = (b.nj + R - 1) / R;
+    return 2 * R * R * (b.diag ? nbi * (nbi + 1) / 2 : nbi * nbj);
+}
+
 template <bool kFp4>
 cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* workspace,
-                                cudaStream_t st, const double* phi, double* layer, int kmax) {
+                                size_t ws_bytes, cudaStream_t st, const double* phi, double* layer, int kmax) {
     WsHeader* hdr = static_cast<WsHeader*>(workspace);
     const int64_t hist_len = n > 1 ? n - 1 : 1;
     cudaError_t err = cudaMemsetAsync(hist, 0, size_t(hist_len) * 8, st);
     if (err != cudaSuccess) return err;
     if ((err = cudaMemsetAsync(&hdr->counter, 0, sizeof(hdr->counter), st)) != cudaSuccess) return err;
     if (n < 2) return cudaSuccess;
-    const MmaLayout lay = mma_layout(n, kFp4);
+    const int64_t nsb = (n + 255) / 256;
+    // FP4: the whole E when it fits the workspace, else bands of g panels
+    const int64_t g = kFp4 ? mma4_band_panels(n, ws_bytes) : nsb;
+    if (g < 1) return cudaErrorMemoryAllocation;
+    const bool banded = g < nsb;
+    const MmaLayout lay = banded ? mma4_band_layout(n, g) : mma_layout(n, kFp4);
     uint8_t* op0 = static_cast<uint8_t*>(workspace) + lay.op0;
     uint8_t* op1 = static_cast<uint8_t*>(workspace) + lay.op1;
-
-    if constexpr (kFp4)
-        k_expand_f4<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, op0, op1,
-                                                              mma4_dl_offset(n));
-    else
-        k_expand_f8<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, op0, op1);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
-
-    constexpr int kCl = (kFp4 ? FmtF4::kPair : FmtF8::kPair) ? 2 : 1;
-    MmaMaps maps;
-    if (encode_operand_maps(&maps, n, lay.kpad, kFp4, op0, op1) != CUDA_SUCCESS) return cudaErrorInvalidValue;
 
     auto kernel = !kFp4 ? k_count_mma : kmax >= 0 ? k_count_mma4<FmtF4Layers> : k_count_mma4<FmtF4>;
     std::atomic<bool>* attr = !kFp4 ? g_attr_set : kmax >= 0 ? g_attr4l_set : g_attr4_set;
@@ -1172,26 +1266,87 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
         if (err != cudaSuccess) return err;
         attr[dev] = true;
     }
-    const int64_t nsb = (n + 255) / 256;
     const int raster = auto_raster(n);
-    const int64_t nitems = mma_items(n, raster);
     const int64_t kblocks = lay.row / kBK;
     unsigned long long* h = reinterpret_cast<unsigned long long*>(hist);
-    if constexpr (kCl == 1) {
+
+    if constexpr (!kFp4) {
+        k_expand_f8<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, op0, op1);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        MmaMaps maps;
+        if (encode_operand_maps(&maps, n, lay.kpad, false, op0, op1) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        const int64_t nitems = mma_items(n, raster);
         int64_t grid = device_sm_count();
         if (grid > nitems) grid = nitems;
         kernel<<<unsigned(grid), kThreads, kSmem, st>>>(maps, bits, n, row_words, nsb, nitems, kblocks, h, hist_len,
-                                                        phi, layer, kmax, raster, hdr);
+                                                        phi, layer, kmax, raster, MmaBand{0, 0, nsb, nsb, 0, 0, 1},
+                                                        hdr);
         return cudaGetLastError();
     } else {
-        cudaLaunchAttribute at[1];
-        cudaLaunchConfig_t cfg;
-        int pairs = 0;
-        if ((err = pair_config(kernel, kSmem, attr, kmax >= 0 ? g_clusters4l : g_clusters4, nitems / kCl, st, at,
-                               &cfg, &pairs)) != cudaSuccess)
-            return err;
-        return cudaLaunchKernelEx(&cfg, kernel, maps, bits, n, row_words, nsb, nitems, kblocks, h, hist_len, phi,
-                                  layer, kmax, raster, hdr);
+        // One persistent pair grid per band; its queue counter restarts at 0.
+        auto count_band = [&](const MmaMaps& maps, const MmaBand& band, bool reset) -> cudaError_t {
+            const int64_t nitems = band_items(band, raster);
+            cudaError_t e = reset ? cudaMemsetAsync(&hdr->counter, 0, sizeof(hdr->counter), st) : cudaSuccess;
+            if (e != cudaSuccess) return e;
+            cudaLaunchAttribute at[1];
+            cudaLaunchConfig_t cfg;
+            int pairs = 0;
+            if ((e = pair_config(kernel, kSmem, attr, kmax >= 0 ? g_clusters4l : g_clusters4, nitems / 2, st, at,
+                                 &cfg, &pairs)) != cudaSuccess)
+                return e;
+            return cudaLaunchKernelEx(&cfg, kernel, maps, bits, n, row_words, nsb, nitems, kblocks, h, hist_len, phi,
+                                      layer, kmax, raster, band, hdr);
+        };
+        if (!banded) {
+            k_expand_f4<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, n, row_words, lay.kpad, op0, op1,
+                                                                  mma4_dl_offset(n));
+            if ((err = cudaGetLastError()) != cudaSuccess) return err;
+            MmaMaps maps;
+            if (encode_operand_maps(&maps, n, lay.kpad, true, op0, op1) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+            return count_band(maps, MmaBand{0, 0, nsb, nsb, 0, 0, 1}, false);
+        }
+        // Bands.  Supertile rows fall into groups of g panels; for each group
+        // a, its E rows (the A rows of every band (a, b), and the B rows of
+        // the triangle (a, a)) take band rows [0, 256 g), from column 256 g a
+        // on; for each later group b, its rows take band rows [256 g, 512 g),
+        // columns 256 g a up to the end of group b (the K range of the bands
+        // (a, b)).  DU and DL hold every row, written once.  Each band's E map
+        // ends at the last band row that holds a row of the set, so the
+        // rows past n read as zeros, as in the whole-set map.
+        const int ppr = int(lay.kpad / 32);
+        const int64_t dl_off = mma4_dl_offset(n);
+        k_expand_f4_band<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, row_words, lay.kpad, op0, 0, n, 0, 0, 0,
+                                                                   op1, dl_off);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        const int64_t m = (nsb + g - 1) / g;
+        auto band_maps = [&](MmaMaps* maps, int64_t rows) -> cudaError_t {
+            if (encode_operand_maps(maps, n, lay.kpad, true, op0, op1) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+            return encode_e_map(&maps->m[kMapE], lay.kpad, op0, rows) == CUDA_SUCCESS ? cudaSuccess
+                                                                                     : cudaErrorInvalidValue;
+        };
+        for (int64_t a = 0; a < m; ++a) {
+            const int64_t a0 = a * g, ga = nsb - a0 < g ? nsb - a0 : g;
+            const int64_t ra = (a0 + ga) * 256 < n ? (a0 + ga) * 256 : n;  // rows of group a end here
+            k_expand_f4_band<<<unsigned(expand_grid(ra - a0 * 256)), 256, 0, st>>>(
+                bits, row_words, lay.kpad, op0, a0 * 256, ra, 0, int(a0 * 8), ppr, nullptr, 0);
+            if ((err = cudaGetLastError()) != cudaSuccess) return err;
+            MmaMaps maps;
+            if ((err = band_maps(&maps, ra - a0 * 256)) != cudaSuccess) return err;
+            if ((err = count_band(maps, MmaBand{a0, a0, ga, ga, a0 * 256, a0 * 256, 1}, a > 0)) != cudaSuccess)
+                return err;
+            for (int64_t b = a + 1; b < m; ++b) {
+                const int64_t b0 = b * g, gb = nsb - b0 < g ? nsb - b0 : g;
+                const int64_t rb = (b0 + gb) * 256 < n ? (b0 + gb) * 256 : n;
+                const int p1 = int((b0 + gb) * 8) < ppr ? int((b0 + gb) * 8) : ppr;
+                k_expand_f4_band<<<unsigned(expand_grid(rb - b0 * 256)), 256, 0, st>>>(
+                    bits, row_words, lay.kpad, op0, b0 * 256, rb, g * 256, int(a0 * 8), p1, nullptr, 0);
+                if ((err = cudaGetLastError()) != cudaSuccess) return err;
+                if ((err = band_maps(&maps, g * 256 + (rb - b0 * 256))) != cudaSuccess) return err;
+                const MmaBand band{a0, b0, ga, gb, a0 * 256, b0 * 256 - g * 256, 0};
+                if ((err = count_band(maps, band, true)) != cudaSuccess) return err;
+            }
+        }
+        return cudaSuccess;
     }
 }
 
@@ -1199,12 +1354,13 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
 
 cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* workspace,
                              cudaStream_t st, const double* phi, double* layer, int kmax) {
-    return launch_count_tensor<false>(n, bits, row_words, hist, workspace, st, phi, layer, kmax);
+    return launch_count_tensor<false>(n, bits, row_words, hist, workspace, mma_workspace_bytes(n), st, phi, layer,
+                                      kmax);
 }
 
 cudaError_t launch_count_mma4(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* workspace,
-                              cudaStream_t st, const double* phi, double* layer, int kmax) {
-    return launch_count_tensor<true>(n, bits, row_words, hist, workspace, st, phi, layer, kmax);
+                              size_t ws_bytes, cudaStream_t st, const double* phi, double* layer, int kmax) {
+    return launch_count_tensor<true>(n, bits, row_words, hist, workspace, ws_bytes, st, phi, layer, kmax);
 }
 
 }  // namespace cs

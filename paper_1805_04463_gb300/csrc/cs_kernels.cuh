@@ -125,10 +125,18 @@ cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words,
                              void* workspace, cudaStream_t st, const double* phi = nullptr, double* layer = nullptr,
                              int kmax = -1);
 // The single-set count on packed FP4 operands (kind::mxf4, unit scales).
+// mma4_workspace_bytes: the whole set's operands.  mma4_band_panels: the
+// supertile rows per group when the operands go through a band buffer of
+// `bytes` (nsb = (n + 255) / 256 when the whole set fits, 0 when not even a
+// band of one panel does); mma4_band_bytes: the workspace of bands of g
+// panels (the whole set's for g >= nsb).  The count takes the widest bands
+// its workspace holds.
 size_t mma4_workspace_bytes(int64_t n);
+int64_t mma4_band_panels(int64_t n, size_t bytes);
+size_t mma4_band_bytes(int64_t n, int64_t g);
 cudaError_t launch_count_mma4(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist,
-                              void* workspace, cudaStream_t st, const double* phi = nullptr, double* layer = nullptr,
-                              int kmax = -1);
+                              void* workspace, size_t ws_bytes, cudaStream_t st, const double* phi = nullptr,
+                              double* layer = nullptr, int kmax = -1);
 
 // CS_OK for cudaSuccess; otherwise CS_ECUDA, remembering the error for
 // cs_last_cuda_error (per host thread).

@@ -55,6 +55,40 @@ def test_layout_helpers(cslib):
     assert cslib.interval_abundance_workspace(1000, 9) == 0
 
 
+def test_fp4_band_planner(cslib):
+    """The FP4 count's band width for a workspace size (host arithmetic only):
+    the whole matrix E (n rows of ceil(n/256)*128 bytes) plus the masked
+    diagonal blocks (256 bytes a row) when it fits; else groups of g
+    supertile rows whose band buffer (2 g * 256 rows of E) fits beside the
+    diagonal blocks; 0 below one-panel bands."""
+    band = cslib.mma4_band_panels
+    for n in (256, 1000, 20011, 131072, 1 << 20):
+        nsb = (n + 255) // 256
+        row = nsb * 128
+        up = lambda x, a: -(-x // a) * a
+        diag = up(n * 128, 1024) + n * 128              # DU, then DL at a 1024-byte aligned offset
+        full = up(1024 + up(n * row, 1024) + diag, 256)
+        assert band(n, full + 4096) == nsb
+        assert band(n, 1 << 62) == nsb
+        assert band(n, 0) == 0 and band(n, 1024 + diag) == 0
+        if nsb < 2:
+            continue
+        one = up(1024 + 512 * row + diag, 256)          # bands of one panel: 512 rows of E
+        assert band(n, one) == 1 and band(n, one - 1) == 0
+        for g in (1, 2, 3, 7, 32, 100):
+            if 2 * g >= nsb:
+                continue
+            need = up(1024 + 2 * g * 256 * row + diag, 256)
+            assert band(n, need) == g and band(n, need - 1) == g - 1, (n, g)
+            if need + 2 * 256 * row - 1 < full:
+                assert band(n, need + 2 * 256 * row - 1) == g, (n, g)
+        # wider workspaces never give narrower bands
+        sizes = np.linspace(one, full + 1, 40).astype(np.int64)
+        gs = [band(n, int(b)) for b in sizes]
+        assert gs == sorted(gs) and gs[-1] == nsb
+    assert band(0, 1 << 40) == -1
+
+
 def test_strerror_and_version(cslib):
     L = cslib.lib()
     assert L.cs_strerror(0) == b"ok"
