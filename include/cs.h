@@ -242,6 +242,19 @@ size_t cs_interval_abundance_workspace(int64_t n, int path);
 int64_t cs_mma4_band_panels(int64_t n, size_t workspace_bytes);
 
 /*
+ * Host-side check of that band plan (no device work, no GPU needed): runs the
+ * band list and the work-item decode the FP4 count's launches use, for bands
+ * of `panels` supertile rows (>= ceil(n/256): the whole set as one launch)
+ * and raster side `raster` (1..32), and writes to counts_host[si * nsb + sj]
+ * (nsb = ceil(n/256); nsb^2 int64 entries, caller-owned, zeroed by the
+ * callee) how many work items decode to the supertile (si, sj).  Every
+ * supertile si <= sj must come out exactly once, none with si > sj.
+ * Returns the number of work items; -1 for invalid arguments (n above 2^20,
+ * panels < 1, raster out of range, NULL counts).
+ */
+int64_t cs_mma4_band_cover(int64_t n, int64_t panels, int raster, int64_t *counts_host);
+
+/*
  * Interval abundances of a time-sorted causal matrix (Algorithm "Optimized
  * Interval Abundance Measurement" and Figure "Proper distance and the order
  * intervals": for every related pair i < j, |A_ij| is the popcount of the

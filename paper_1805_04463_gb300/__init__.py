@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
             "cs_causal_matrix": ([i32, i64, vp, vp, i64, vp], i32),
             "cs_interval_abundance_workspace": ([i64, i32], sz),
             "cs_mma4_band_panels": ([i64, sz], i64),
+            "cs_mma4_band_cover": ([i64, i64, i32, vp], i64),
             "cs_resolved_path": ([i64, i32], i32),
             "cs_set_auto_paths": ([vp, vp, i32], i32),
             "cs_get_auto_paths": ([vp, vp, i32], i32),
@@ -189,6 +190,16 @@ def mma4_band_panels(n: int, workspace_bytes: int) -> int:
     """Supertile rows per band of the FP4 count with this workspace: (n + 255) // 256
     when the whole operand matrix fits, 0 when not even one-panel bands do."""
     return lib().cs_mma4_band_panels(n, workspace_bytes)
+
+
+def mma4_band_cover(n: int, panels: int, raster: int = 8):
+    """(items, counts): the FP4 count's work items over all bands of `panels`
+    supertile rows, and how many decode to each supertile (si, sj) (host only)."""
+    import numpy as np
+    nsb = (n + 255) // 256
+    counts = np.zeros((nsb, nsb), dtype=np.int64)
+    items = lib().cs_mma4_band_cover(n, panels, raster, counts.ctypes.data_as(ctypes.c_void_p))
+    return items, counts
 
 
 def resolved_path(n: int, path: int = PATH_AUTO) -> int:

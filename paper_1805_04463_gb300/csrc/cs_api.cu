@@ -274,6 +274,11 @@ size_t cs_interval_abundance_workspace(int64_t n, int path) {
                                                                           : popc_workspace_bytes(n);
 }
 
+int64_t cs_mma4_band_cover(int64_t n, int64_t panels, int raster, int64_t* counts_host) {
+    if (!valid_n(n) || n > (int64_t(1) << 20) || panels < 1 || raster < 1 || raster > 32 || !counts_host) return -1;
+    return mma4_band_cover(n, panels, raster, counts_host);
+}
+
 int64_t cs_mma4_band_panels(int64_t n, size_t workspace_bytes) {
     if (!valid_n(n)) return -1;
     return mma4_band_panels(n, workspace_bytes);

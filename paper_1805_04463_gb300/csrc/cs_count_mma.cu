@@ -35,6 +35,7 @@
 // end of the j-block.  C.C is never written to memory.
 #include <atomic>
 #include <cstring>
+#include <vector>
 
 #include "cs_kernels.cuh"
 
@@ -159,7 +160,7 @@ struct Item {
 
 // Slot t of a set's item list -> supertile (si, sj) and its 128-row half;
 // false for a slot that holds no work.
-__device__ __forceinline__ bool decode_slot(int64_t t, int64_t nsb, int64_t n, int64_t R, int64_t& si, int64_t& sj,
+__host__ __device__ __forceinline__ bool decode_slot(int64_t t, int64_t nsb, int64_t n, int64_t R, int64_t& si, int64_t& sj,
                                             int64_t& half) {
     const int64_t spb = 2 * R * R;  // slots per raster block
     const int64_t blk = t / spb, slot = t - blk * spb;
@@ -190,7 +191,7 @@ struct MmaBand {
 
 // Slot t of a band's item list -> supertile (si, sj) of the set and its half.
 // The rectangle is rasterised like the triangle: R x R blocks, row by row.
-__device__ __forceinline__ bool decode_band(int64_t t, const MmaBand& b, int64_t n, int64_t R, int64_t& si,
+__host__ __device__ __forceinline__ bool decode_band(int64_t t, const MmaBand& b, int64_t n, int64_t R, int64_t& si,
                                             int64_t& sj, int64_t& half) {
     if (b.diag) {
         if (!decode_slot(t, b.ni, n - b.i0 * 256, R, si, sj, half)) return false;
@@ -1236,6 +1237,30 @@ int64_t band_items(const MmaBand& b, int raster) {
     return 2 * R * R * (b.diag ? nbi * (nbi + 1) / 2 : nbi * nbj);
 }
 
+// The bands of a set counted in groups of g panels, in launch order: for
+// each group a the triangle (a, a), then the rectangles (a, b), b > a; the
+// whole set as one band when g >= nsb.  The E rows of the triangle's group
+// sit in band rows [0, 256 g), those of a rectangle's second group in
+// [256 g, 512 g).
+std::vector<MmaBand> mma4_bands(int64_t n, int64_t g) {
+    const int64_t nsb = (n + 255) / 256;
+    std::vector<MmaBand> out;
+    if (g >= nsb) {
+        out.push_back(MmaBand{0, 0, nsb, nsb, 0, 0, 1});
+        return out;
+    }
+    const int64_t m = (nsb + g - 1) / g;
+    for (int64_t a = 0; a < m; ++a) {
+        const int64_t a0 = a * g, ga = nsb - a0 < g ? nsb - a0 : g;
+        out.push_back(MmaBand{a0, a0, ga, ga, a0 * 256, a0 * 256, 1});
+        for (int64_t b = a + 1; b < m; ++b) {
+            const int64_t b0 = b * g, gb = nsb - b0 < g ? nsb - b0 : g;
+            out.push_back(MmaBand{a0, b0, ga, gb, a0 * 256, b0 * 256 - g * 256, 0});
+        }
+    }
+    return out;
+}
+
 template <bool kFp4>
 cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* workspace,
                                 size_t ws_bytes, cudaStream_t st, const double* phi, double* layer, int kmax) {
@@ -1318,39 +1343,46 @@ cudaError_t launch_count_tensor(int64_t n, const uint64_t* bits, int64_t row_wor
         k_expand_f4_band<<<unsigned(expand_grid(n)), 256, 0, st>>>(bits, row_words, lay.kpad, op0, 0, n, 0, 0, 0,
                                                                    op1, dl_off);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        const int64_t m = (nsb + g - 1) / g;
-        auto band_maps = [&](MmaMaps* maps, int64_t rows) -> cudaError_t {
-            if (encode_operand_maps(maps, n, lay.kpad, true, op0, op1) != CUDA_SUCCESS) return cudaErrorInvalidValue;
-            return encode_e_map(&maps->m[kMapE], lay.kpad, op0, rows) == CUDA_SUCCESS ? cudaSuccess
-                                                                                     : cudaErrorInvalidValue;
-        };
-        for (int64_t a = 0; a < m; ++a) {
-            const int64_t a0 = a * g, ga = nsb - a0 < g ? nsb - a0 : g;
-            const int64_t ra = (a0 + ga) * 256 < n ? (a0 + ga) * 256 : n;  // rows of group a end here
-            k_expand_f4_band<<<unsigned(expand_grid(ra - a0 * 256)), 256, 0, st>>>(
-                bits, row_words, lay.kpad, op0, a0 * 256, ra, 0, int(a0 * 8), ppr, nullptr, 0);
+        MmaMaps maps;
+        if (encode_operand_maps(&maps, n, lay.kpad, true, op0, op1) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        bool first = true;
+        for (const MmaBand& band : mma4_bands(n, g)) {
+            // the rows this band brings into the buffer: a triangle's group
+            // (the A rows of its group's later bands too), or a rectangle's
+            // second group, over the columns from the first group's start
+            const int64_t p0 = band.diag ? band.i0 : band.j0, np = band.diag ? band.ni : band.nj;
+            const int64_t r0 = p0 * 256, r1 = (p0 + np) * 256 < n ? (p0 + np) * 256 : n;
+            const int c1 = band.diag ? ppr : (int((p0 + np) * 8) < ppr ? int((p0 + np) * 8) : ppr);
+            const int64_t e0 = band.diag ? 0 : g * 256;  // first band row written
+            k_expand_f4_band<<<unsigned(expand_grid(r1 - r0)), 256, 0, st>>>(
+                bits, row_words, lay.kpad, op0, r0, r1, e0, int(band.i0 * 8), c1, nullptr, 0);
             if ((err = cudaGetLastError()) != cudaSuccess) return err;
-            MmaMaps maps;
-            if ((err = band_maps(&maps, ra - a0 * 256)) != cudaSuccess) return err;
-            if ((err = count_band(maps, MmaBand{a0, a0, ga, ga, a0 * 256, a0 * 256, 1}, a > 0)) != cudaSuccess)
-                return err;
-            for (int64_t b = a + 1; b < m; ++b) {
-                const int64_t b0 = b * g, gb = nsb - b0 < g ? nsb - b0 : g;
-                const int64_t rb = (b0 + gb) * 256 < n ? (b0 + gb) * 256 : n;
-                const int p1 = int((b0 + gb) * 8) < ppr ? int((b0 + gb) * 8) : ppr;
-                k_expand_f4_band<<<unsigned(expand_grid(rb - b0 * 256)), 256, 0, st>>>(
-                    bits, row_words, lay.kpad, op0, b0 * 256, rb, g * 256, int(a0 * 8), p1, nullptr, 0);
-                if ((err = cudaGetLastError()) != cudaSuccess) return err;
-                if ((err = band_maps(&maps, g * 256 + (rb - b0 * 256))) != cudaSuccess) return err;
-                const MmaBand band{a0, b0, ga, gb, a0 * 256, b0 * 256 - g * 256, 0};
-                if ((err = count_band(maps, band, true)) != cudaSuccess) return err;
-            }
+            if (encode_e_map(&maps.m[kMapE], lay.kpad, op0, e0 + (r1 - r0)) != CUDA_SUCCESS)
+                return cudaErrorInvalidValue;
+            if ((err = count_band(maps, band, !first)) != cudaSuccess) return err;
+            first = false;
         }
         return cudaSuccess;
     }
 }
 
 }  // namespace
+
+int64_t mma4_band_cover(int64_t n, int64_t g, int raster, int64_t* counts) {
+    const int64_t nsb = (n + 255) / 256;
+    std::memset(counts, 0, size_t(nsb) * size_t(nsb) * sizeof(int64_t));
+    int64_t items = 0;
+    for (const MmaBand& band : mma4_bands(n, g)) {
+        const int64_t slots = band_items(band, raster);
+        for (int64_t t = 0; t < slots; t += 2) {  // a pair's unit u is slot 2 u
+            int64_t si, sj, half;
+            if (!decode_band(t, band, n, raster, si, sj, half)) continue;
+            ++counts[si * nsb + sj];
+            ++items;
+        }
+    }
+    return items;
+}
 
 cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist, void* workspace,
                              cudaStream_t st, const double* phi, double* layer, int kmax) {

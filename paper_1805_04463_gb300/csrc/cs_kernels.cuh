@@ -134,6 +134,10 @@ cudaError_t launch_count_mma(int64_t n, const uint64_t* bits, int64_t row_words,
 size_t mma4_workspace_bytes(int64_t n);
 int64_t mma4_band_panels(int64_t n, size_t bytes);
 size_t mma4_band_bytes(int64_t n, int64_t g);
+// Host check of the band plan: counts[si * nsb + sj] (nsb^2 entries, zeroed
+// here) = how many work items of all band launches of bands of g panels and
+// raster side `raster` decode to supertile (si, sj); returns the item count.
+int64_t mma4_band_cover(int64_t n, int64_t g, int raster, int64_t* counts);
 cudaError_t launch_count_mma4(int64_t n, const uint64_t* bits, int64_t row_words, int64_t* hist,
                               void* workspace, size_t ws_bytes, cudaStream_t st, const double* phi = nullptr,
                               double* layer = nullptr, int kmax = -1);

@@ -89,6 +89,24 @@ def test_fp4_band_planner(cslib):
     assert band(0, 1 << 40) == -1
 
 
+def test_fp4_band_plan_covers_every_supertile_once(cslib):
+    """The band list and the work-item decode of the FP4 count, run on the
+    host: over all bands every supertile (si, sj), si <= sj, is counted by
+    exactly one work item and none below the diagonal is -- for ragged sizes,
+    one-panel groups, a last group of one panel, raster sides that do not
+    divide the groups, and the whole set as one band."""
+    for n in (256, 257, 2000, 2304, 20011, 65536):
+        nsb = (n + 255) // 256
+        upper, lower = np.triu_indices(nsb), np.tril_indices(nsb, -1)
+        for g in sorted({1, 2, 3, 7, 13, 39, max(1, nsb - 1), nsb, nsb + 5}):
+            for raster in (1, 3, 8):
+                items, c = cslib.mma4_band_cover(n, g, raster)
+                assert items == nsb * (nsb + 1) // 2, (n, g, raster)
+                assert (c[upper] == 1).all() and (c[lower] == 0).all(), (n, g, raster)
+    L = cslib.lib()
+    assert L.cs_mma4_band_cover(1000, 0, 8, None) == -1 and L.cs_mma4_band_cover((1 << 20) + 1, 4, 8, None) == -1
+
+
 def test_strerror_and_version(cslib):
     L = cslib.lib()
     assert L.cs_strerror(0) == b"ok"
